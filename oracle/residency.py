@@ -1,0 +1,198 @@
+"""ORACLE (test infrastructure only): LOD choice, page table and LOD controller.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this package; it shares no code with the CUDA library.
+
+Follows Sec. 4.1 ("Level of Detail", "Page Table Management") and the
+evaluation's "Page determination details":
+  * one flat array of physical-page entries, each with its LOD, the frame it
+    was last required, and one (virtual page, required) pair per contained
+    virtual page (fanout^lod of them);
+  * stage one marks required entries and drops requests already resident at
+    the requested LOD; entries with nothing required are free and remember
+    when they were last used;
+  * stage two places the remaining requests, least-recently-used free
+    entries first, within the copy budget of the staging buffer;
+  * LOD thresholds move to keep usage between 50% and 80%; the step grows by
+    1% after successive moves in the same direction and shrinks by 1% after
+    a quick reversal.
+
+Readings where the paper is silent, written out as a sequential definition
+(all float arithmetic float32, correctly rounded):
+  LOD     d = float(0xFFFFFFFF - enc); level = the largest l >= 1 with
+          (f_px * e_l(p)) / d <= tau, else 0 (screen-space error in pixels).
+  order   unmatched requests by (direct desc, enc desc, page asc).
+  budget  the longest prefix of that order whose level-page bytes fit the
+          budget; everything after it is missing.
+  place   per level, admitted requests first fill non-required sub-slots of
+          entries already required this frame at that level (entry asc,
+          sub-slot asc); the rest go to fresh entries taken from the free
+          list ordered by (last used asc, index asc), levels served in
+          ascending order, packed fanout^l per entry; no free entry left ->
+          missing.  A fresh entry forgets everything it held.
+  draw    stage-one matches plus placements, ascending virtual page.
+  usage   drawn Gaussian capacity / (entries * page size).
+  control usage > hi: tau += step; usage < lo and a level > 0 drawn:
+          tau = max(0, tau - step); before moving, step *= 1.01 when the last
+          move (within 10 frames) had the same direction, *= 0.99 when it
+          had the opposite one.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+F32 = np.float32
+
+
+@dataclass
+class ResidencyParams:
+    n_entries: int
+    page_size: int
+    levels: int
+    fanout: int
+    record_bytes: int
+    budget_bytes: int
+    lod: bool = True
+    usage_lo: float = 0.5
+    usage_hi: float = 0.8
+    tau0: float = 1.0
+    step0: float = 0.1
+
+    def m(self, l):
+        return self.page_size // (self.fanout ** l)
+
+    def page_bytes(self, l):
+        return self.m(l) * self.record_bytes
+
+
+class PageTable:
+    def __init__(self, rp: ResidencyParams):
+        self.rp = rp
+        smax = rp.fanout ** (rp.levels - 1)
+        self.lod = np.full(rp.n_entries, -1, np.int64)
+        self.last_used = np.full(rp.n_entries, -1, np.int64)
+        self.slot = np.full((rp.n_entries, smax), -1, np.int64)
+        self.tau = F32(rp.tau0)
+        self.step = F32(rp.step0)
+        self.last_dir = 0
+        self.last_move = -1000
+        self.frame = 0
+
+
+def float_from_bits(u):
+    return np.asarray(u, np.uint32).view(np.float32)
+
+
+def lod_select(pages, enc, err, f_px, tau, lod_on):
+    """Level per request by screen-space error (fp32)."""
+    lv = np.zeros(len(pages), np.int64)
+    if not lod_on or err.shape[1] <= 1:
+        return lv
+    d = float_from_bits(np.uint32(0xFFFFFFFF) - np.asarray(enc, np.uint32))
+    f = F32(f_px)
+    for i, p in enumerate(pages):
+        for l in range(err.shape[1] - 1, 0, -1):
+            sse = F32(f * err[p, l]) / d[i]
+            if sse <= F32(tau):
+                lv[i] = l
+                break
+    return lv
+
+
+def update(pt: PageTable, pages, enc, direct, levels):
+    """One page-table update.  Returns dict with copies [(p,l,e,s)] in
+    priority order, draw [(p,l,e,s)] ascending p, missing [p], usage and counts."""
+    rp = pt.rp
+    P = rp.n_entries
+    frame = pt.frame
+    req_level = {int(p): int(l) for p, l in zip(pages, levels)}
+    # ---- stage 1
+    required = np.zeros_like(pt.slot, dtype=bool)
+    matched = set()
+    for e in range(P):
+        l = pt.lod[e]
+        if l < 0:
+            continue
+        for s in range(rp.fanout ** l):
+            p = int(pt.slot[e, s])
+            if p >= 0 and req_level.get(p, -1) == l:
+                required[e, s] = True
+                matched.add(p)
+    any_req = required.any(1)
+    pt.last_used[any_req] = frame
+    # ---- stage 2
+    U = [(int(p), int(en), int(d), int(l)) for p, en, d, l in zip(pages, enc, direct, levels) if int(p) not in matched]
+    U.sort(key=lambda r: (-r[2], -r[1], r[0]))
+    admitted, cum = [], 0
+    for r in U:
+        c = rp.page_bytes(r[3])
+        if cum + c > rp.budget_bytes:
+            break
+        cum += c
+        admitted.append(r)
+    missing = [r[0] for r in U[len(admitted):]]
+    rank = {r[0]: i for i, r in enumerate(admitted)}
+    placed = []
+    rest = {}
+    for l in range(rp.levels):
+        R = [r for r in admitted if r[3] == l]
+        O = [(e, s) for e in range(P) if pt.lod[e] == l and any_req[e] for s in range(rp.fanout ** l)
+             if not required[e, s]]
+        k = min(len(R), len(O))
+        for i in range(k):
+            e, s = O[i]
+            pt.slot[e, s] = R[i][0]
+            placed.append((R[i][0], l, e, s))
+        rest[l] = R[k:]
+    free = sorted([e for e in range(P) if not any_req[e]], key=lambda e: (pt.last_used[e], e))
+    fi = 0
+    for l in range(rp.levels):
+        R = rest[l]
+        S = rp.fanout ** l
+        for f in range((len(R) + S - 1) // S):
+            chunk = R[f * S:(f + 1) * S]
+            if fi >= len(free):
+                missing.extend(r[0] for r in chunk)
+                continue
+            e = free[fi]
+            fi += 1
+            pt.slot[e, :] = -1
+            pt.lod[e] = l
+            pt.last_used[e] = frame
+            for s, r in enumerate(chunk):
+                pt.slot[e, s] = r[0]
+                placed.append((r[0], l, e, s))
+    placed.sort(key=lambda t: rank[t[0]])
+    draw = [(int(pt.slot[e, s]), int(pt.lod[e]), e, s) for e in range(P) for s in range(rp.fanout ** max(pt.lod[e], 0))
+            if pt.lod[e] >= 0 and required[e, s]]
+    draw += placed
+    draw.sort(key=lambda t: t[0])
+    used = sum(rp.m(t[1]) for t in draw)
+    usage = F32(used) / F32(P * rp.page_size) if P > 0 else F32(0)
+    streamed_bytes = sum(rp.page_bytes(t[1]) for t in placed)
+    return dict(copies=placed, draw=draw, missing=sorted(missing), usage=usage, resident=len(matched),
+                streamed_pages=len(placed), streamed_bytes=streamed_bytes, required=len(pages),
+                direct=int(np.sum(np.asarray(direct) != 0)))
+
+
+def control(pt: PageTable, usage, draw):
+    """LOD threshold controller, applied after the frame's update; advances the frame."""
+    rp = pt.rp
+    if rp.lod and rp.levels > 1:
+        d = 0
+        if usage > F32(rp.usage_hi):
+            d = 1
+        elif usage < F32(rp.usage_lo) and any(t[1] > 0 for t in draw):
+            d = -1
+        if d != 0:
+            recent = pt.frame - pt.last_move <= 10
+            if recent and pt.last_dir == d:
+                pt.step = F32(pt.step * F32(1.01))
+            elif recent and pt.last_dir == -d:
+                pt.step = F32(pt.step * F32(0.99))
+            pt.tau = F32(pt.tau + pt.step) if d > 0 else max(F32(0), F32(pt.tau - pt.step))
+            pt.last_dir = d
+            pt.last_move = pt.frame
+    pt.frame += 1

@@ -1,0 +1,235 @@
+"""Pins of the render oracle against closed forms, finite differences,
+quadrature and brute force (none of them re-runs the oracle's own formula)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+
+def _one(pos, s, rgb_dc=(0.3, 0.5, 0.7), op=0.8, rot=(1, 0, 0, 0), K=1):
+    sh = np.zeros((1, K, 3), np.float32)
+    sh[0, 0] = rgb_dc
+    return dict(pos=np.array([pos], np.float32), scale=np.array([[s, s, s]], np.float32),
+                rot=np.array([rot], np.float32), opacity=np.array([op], np.float32), sh=sh)
+
+
+def _cam(w=64, h=64, f=50.0, tile=(16, 16)):
+    c = scenegen.Camera(view=np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], np.float32),
+                        campos=np.zeros(3, np.float32), fx=np.float32(f), fy=np.float32(f), cx=np.float32(w / 2),
+                        cy=np.float32(h / 2), width=w, height=h, tile_w=tile[0], tile_h=tile[1])
+    return c
+
+
+C0 = 1.0 / (2.0 * math.sqrt(math.pi))   # Y_00 = 1 / sqrt(4 pi)
+
+
+def test_isotropic_on_axis_closed_form():
+    """One isotropic Gaussian on the optical axis: Sigma2 = ((f s / z)^2 + 0.3) I,
+    so the pixel value is rgb * min(.99, o exp(-r^2 / (2 sigma^2))) inside the
+    tile rectangle wherever alpha >= 1/255; the radius is
+    ceil(3 sqrt(sigma^2 + sqrt(0.1)))."""
+    z, s, f, o = 4.0, 0.05, 50.0, 0.8
+    cam = _cam(f=f)
+    g = _one((0, 0, z), s, op=o)
+    out = oracle.render(g, np.zeros(1, np.int64), cam)
+    sig2 = (f * s / z) ** 2 + 0.3
+    rgb = np.array([0.3, 0.5, 0.7]) * C0 + 0.5
+    yy, xx = np.mgrid[0:64, 0:64] + 0.5
+    r2 = (xx - 32) ** 2 + (yy - 32) ** 2
+    alpha = np.minimum(0.99, o * np.exp(-r2 / (2 * sig2)))
+    # isotropic: the eigenvalue discriminant is 0, floored at 0.1 (3DGS convention)
+    radius = math.ceil(3 * math.sqrt(sig2 + math.sqrt(0.1)))
+    # tile rectangle in pixels
+    t0, t1 = math.floor((32 - radius) / 16) * 16, (math.floor((32 + radius) / 16) + 1) * 16
+    inrect = (xx >= t0) & (xx < t1) & (yy >= t0) & (yy < t1)
+    a = np.where(inrect & (alpha >= 1 / 255), alpha, 0)
+    expect = rgb[:, None, None] * a[None]
+    assert out["proj"]["radius"][0] == radius
+    np.testing.assert_allclose(out["image"], expect, atol=1e-12)
+    np.testing.assert_allclose(out["proj"]["centre"][0], [32, 32], atol=1e-12)
+
+
+def test_isotropic_off_axis_conic_closed_form():
+    """Off-axis isotropic Gaussian at (x0, 0, z): J = [[f/z, 0, -f x0/z^2], [0, f/z, 0]],
+    Sigma2 = s^2 J J^T + 0.3 I; the conic is its inverse."""
+    x0, z, s, f = 0.7, 5.0, 0.08, 60.0
+    cam = _cam(w=128, h=128, f=f)
+    pr = oracle.project(_one((x0, 0, z), s), cam)
+    a = s * s * (f * f / z ** 2 + f * f * x0 * x0 / z ** 4) + 0.3
+    c = s * s * f * f / z ** 2 + 0.3
+    expect = np.array([1 / a, 0.0, 1 / c])
+    np.testing.assert_allclose(pr["conic"][0], expect, rtol=1e-6)   # fp32 inputs
+    np.testing.assert_allclose(pr["centre"][0], [f * np.float32(x0) / z + 64, 64], rtol=1e-7)
+
+
+def test_ewa_jacobian_matches_finite_differences():
+    """The conic's Sigma2 equals J Sigma3 J^T + 0.3 I with J the finite-difference
+    Jacobian of the pinhole map (x, y, z) -> (f x/z + cx, f y/z + cy), for a rotated
+    anisotropic Gaussian seen by a rotated camera (inside the guard band)."""
+    rng = np.random.default_rng(3)
+    ang = 0.3
+    Rc = np.array([[math.cos(ang), 0, math.sin(ang)], [0, 1, 0], [-math.sin(ang), 0, math.cos(ang)]])
+    t = np.array([0.2, -0.1, 3.0])
+    cam = _cam(w=256, h=256, f=180.0)
+    cam.view = np.concatenate([Rc, t[:, None]], 1).astype(np.float32)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    mu = np.array([0.4, 0.3, 1.0])
+    s = np.array([0.05, 0.1, 0.02])
+    g = dict(pos=mu[None].astype(np.float32), scale=s[None].astype(np.float32), rot=q[None].astype(np.float32),
+             opacity=np.array([0.9], np.float32), sh=np.zeros((1, 1, 3), np.float32))
+    pr = oracle.project(g, cam)
+    V = cam.view.astype(np.float64)
+    pc = V[:, :3] @ g["pos"][0].astype(np.float64) + V[:, 3]
+
+    def pin(p):
+        return np.array([180.0 * p[0] / p[2] + 128, 180.0 * p[1] / p[2] + 128])
+    h = 1e-6
+    J = np.stack([(pin(pc + h * e) - pin(pc - h * e)) / (2 * h) for e in np.eye(3)], 1)
+    qq = g["rot"][0].astype(np.float64)
+    w, x, y, z = qq
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-6) and abs(np.linalg.det(R) - 1) < 1e-6
+    S3 = R @ np.diag(g["scale"][0].astype(np.float64) ** 2) @ R.T
+    W = V[:, :3]
+    S2 = J @ W @ S3 @ W.T @ J.T + 0.3 * np.eye(2)
+    A, B, C = pr["conic"][0]
+    np.testing.assert_allclose(np.linalg.inv(np.array([[A, B], [B, C]])), S2, rtol=2e-6)
+
+
+def test_quaternion_rotation_matches_hamilton_product():
+    """Kerbl's rotation matrix of q equals the Hamilton conjugation v -> q v q*."""
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        v = rng.normal(size=3)
+
+        def hm(a, b):
+            return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                             a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                             a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                             a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+        rv = hm(hm(q, np.r_[0, v]), q * np.array([1, -1, -1, -1]))[1:]
+        from oracle.build import quat_to_rot
+        np.testing.assert_allclose(quat_to_rot(q) @ v, rv, atol=1e-12)
+
+
+def test_sh_basis_orthonormal_by_quadrature():
+    """Gauss-Legendre in cos(theta) x uniform phi: <Y_i, Y_j> = delta_ij (16 functions)."""
+    nth, nph = 24, 48
+    xg, wg = np.polynomial.legendre.leggauss(nth)
+    ph = (np.arange(nph) + 0.5) * 2 * np.pi / nph
+    ct = xg[:, None]
+    st = np.sqrt(1 - ct ** 2)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), np.broadcast_to(ct, (nth, nph))], -1).reshape(-1, 3)
+    w = (wg[:, None] * np.full(nph, 2 * np.pi / nph)).reshape(-1)
+    Y = oracle.sh_basis(d)
+    G = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_degree1_is_linear_in_direction():
+    """Degree-1 real SH are sqrt(3/(4 pi)) times (-y, z, -x) (Condon-Shortley)."""
+    d = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    Y = oracle.sh_basis(d)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    np.testing.assert_allclose(Y[:, 1:4], c1 * np.array([[0, 1, 0], [0, 0, -1], [-1, 0, 0]]), atol=1e-15)
+
+
+def test_two_gaussian_composite_closed_form():
+    """Two on-axis isotropic Gaussians: the pixel at the centre is
+    a1 c1 + (1 - a1) a2 c2 with the nearer one first, whatever the input order."""
+    f = 50.0
+    cam = _cam(f=f)
+    g1 = _one((0, 0, 3.0), 0.05, rgb_dc=(1, 0, 0), op=0.6)
+    g2 = _one((0, 0, 6.0), 0.08, rgb_dc=(0, 1, 0), op=0.7)
+    g = {k: np.concatenate([g2[k], g1[k]]) for k in g1}
+    out = oracle.render(g, np.array([0, 1], np.int64), cam)
+    # pixel (31,31) centre at (31.5,31.5): r^2 = 0.5
+    def a(z, s, o):
+        return min(0.99, o * math.exp(-0.5 / (2 * ((f * s / z) ** 2 + 0.3))))
+    a1, a2 = a(3.0, 0.05, 0.6), a(6.0, 0.08, 0.7)
+    c1 = np.array([1, 0, 0]) * C0 + 0.5
+    c2 = np.array([0, 1, 0]) * C0 + 0.5
+    expect = a1 * c1 + (1 - a1) * a2 * c2
+    np.testing.assert_allclose(out["image"][:, 31, 31], expect, atol=1e-12)
+
+
+def _brute_force_image(g, vid, cam, pr):
+    """Per pixel: every visible splat whose tile rectangle holds the pixel's tile,
+    sorted by (depth, virtual id), blended front to back in FP64."""
+    H, W = cam.height, cam.width
+    img = np.zeros((3, H, W))
+    vis = np.nonzero(pr["vis"])[0]
+    for py in range(H):
+        for px in range(W):
+            tx, ty = px // cam.tile_w, py // cam.tile_h
+            cand = [i for i in vis if pr["rect"][i, 0] <= tx < pr["rect"][i, 2] and pr["rect"][i, 1] <= ty < pr["rect"][i, 3]]
+            cand.sort(key=lambda i: (float(pr["depth"][i]), int(vid[i])))
+            T, C = 1.0, np.zeros(3)
+            for i in cand:
+                dx = pr["centre"][i, 0] - (px + 0.5)
+                dy = pr["centre"][i, 1] - (py + 0.5)
+                A, B, Cc = pr["conic"][i]
+                pw = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy
+                if pw > 0:
+                    continue
+                al = min(0.99, float(g["opacity"][i]) * math.exp(pw))
+                if al < 1 / 255:
+                    continue
+                if T * (1 - al) < 1e-4:
+                    break
+                C += pr["rgb"][i] * al * T
+                T *= 1 - al
+            img[:, py, px] = C
+    return img
+
+
+@pytest.mark.parametrize("seed,tile", [(11, (8, 8)), (12, (16, 16)), (13, (32, 8))])
+def test_brute_force_per_pixel_sort(seed, tile):
+    raw = scenegen.uniform_scene(n=300, seed=seed, lo=-1.5, hi=1.5, ls_mu=-3.0, sh_degree=1)
+    from oracle.build import decode
+    g = decode(raw, (-2, -2, -2), (2, 2, 2))
+    vid = np.random.default_rng(seed).permutation(len(g["opacity"])).astype(np.int64)
+    cam = scenegen.tiny_camera(width=40, height=36, dist=4.0, tile=tile)
+    out = oracle.render(g, vid, cam)
+    ref = _brute_force_image(g, vid, cam, out["proj"])
+    np.testing.assert_allclose(out["image"], ref, atol=1e-12)
+
+
+def test_sort_order_and_ranges_are_consistent():
+    raw = scenegen.uniform_scene(n=2000, seed=5)
+    from oracle.build import decode
+    g = decode(raw, (-5, -5, -5), (5, 5, 5))
+    cam = scenegen.tiny_camera(width=96, height=80)
+    vid = np.arange(len(g["opacity"]), dtype=np.int64)[::-1].copy()
+    out = oracle.render(g, vid, cam)
+    keys, idx, rng = out["keys"], out["idx"], out["ranges"]
+    # independent order: lexsort on (vid, depth bits, tile)
+    tiles = keys >> np.uint64(32)
+    dbits = keys & np.uint64(0xFFFFFFFF)
+    order = np.lexsort((vid[idx], dbits, tiles))
+    assert np.array_equal(order, np.arange(len(keys)))
+    # ranges cover exactly the pairs of each tile
+    for t in range(len(rng)):
+        s, e = rng[t]
+        assert np.all(tiles[s:e] == t)
+    assert rng[:, 1].max() == len(keys)
+    # pairs per splat equal its touched tile count
+    counts = np.bincount(idx, minlength=len(vid))
+    np.testing.assert_array_equal(counts, np.where(out["proj"]["vis"] != 0, out["proj"]["touched"], 0))
+
+
+def test_culling_rules():
+    cam = _cam()
+    # behind the near plane, zero opacity (padding), fully off-screen
+    g = {k: np.concatenate([_one((0, 0, 0.19), 0.05)[k], _one((0, 0, 2.0), 0.05, op=0.0)[k],
+                            _one((50.0, 0, 2.0), 0.01)[k], _one((0, 0, 0.21), 0.001)[k]]) for k in _one((0, 0, 1), 1)}
+    pr = oracle.project(g, cam)
+    np.testing.assert_array_equal(pr["vis"], [0, 0, 0, 1])
