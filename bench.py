@@ -1,0 +1,390 @@
+"""Benchmark: frames/s of the virtual-memory 3DGS per-frame path.
+
+A step is one frame: page determination (visibility buffer + reduction) ->
+page-table update with host->pool streaming -> render of the resident
+Gaussians, for one camera of a seeded flythrough.  Two arms on the same scene
+and path:
+  plain     fp32 page pool, copies in line with the frame (the paper's
+            synchronous transfers)
+  headline  fp16 page pool, copies on a separate copy stream
+`value` is the headline arm's whole-job frames/s; `plain_vm` carries the plain
+arm.  Default workload: 50M Gaussians on a 2 km x 2 km city (5,000 boxes),
+SH degree 3, pages of 4096 with 3 LOD levels, whole scene in page-locked host
+memory, 2 GiB device pool, 1000-frame walking-speed flythrough at 1920x1080.
+Synthetic, seeded inputs (scenegen); no dataset.
+
+  python bench.py [--gpus N --steps K --warmup W] [--config city50m|blobs1m|tiny]
+  python bench.py --impl reference ...   (the CPU oracle, bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload(name):
+    import scenegen
+    if name == "city50m":
+        ext = 2000.0
+        return dict(
+            name="city 50M Gaussians, 2 km x 2 km, 5000 boxes, SH3, pages 4096 x 3 LOD (fanout 8), 2 GiB pool, "
+                 "1080p walking flythrough",
+            gen=lambda: scenegen.city_scene(n=50_000_000, n_boxes=5000, extent=ext),
+            build=dict(page_size=4096, paging="octree", lod_levels=3, lod_fanout=8, lo=(-4, -4, -4),
+                       hi=(ext + 4, ext + 4, 88), voxel=2.0, kappa=0.5, link_samples=4, fp16=True),
+            path=lambda n: scenegen.city_walk_path(n_frames=n),
+            frames=1000, pool_bytes=2 << 30, lod=True, gaussians=50_000_000,
+            sample=dict(extent=150.0, n=int(50_000_000 * (150.0 / ext) ** 2), n_boxes=max(1, int(5000 * (150.0 / ext) ** 2))))
+    if name == "blobs1m":
+        return dict(
+            name="1M Gaussians in 200 blobs (sigma 0.5 m) in a 50 m cube, SH3, octree pages 4096, 64 MiB pool, 1080p "
+                 "orbit + flythrough",
+            gen=lambda: scenegen.blob_scene(n=1_000_000),
+            build=dict(page_size=4096, paging="octree", lod_levels=1, lo=(-5, -5, -5), hi=(55, 55, 55),
+                       voxel=60.0 / 64, kappa=2.0, link_samples=4, fp16=True),
+            path=lambda n: scenegen.orbit_fly_path(n_frames=n),
+            frames=300, pool_bytes=64 << 20, lod=False, gaussians=1_000_000, sample=None)
+    if name == "tiny":
+        return dict(
+            name="16,384 Gaussians uniform in a 10 m cube, SH0, 64 Morton pages of 256, all resident, 256x256",
+            gen=lambda: scenegen.uniform_scene(),
+            build=dict(page_size=256, paging="morton", lo=(-5, -5, -5), hi=(5, 5, 5), voxel=10 / 32, kappa=0.5,
+                       link_samples=8, fp16=True),
+            path=lambda n: [scenegen.tiny_camera()] * n,
+            frames=1, pool_bytes=None, lod=False, gaussians=16384, sample=None)
+    raise SystemExit("unknown config " + name)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 8]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def build_scene(W):
+    import paper_2506_19415_b300 as v
+    t0 = time.time()
+    raw = W["gen"]()
+    t1 = time.time()
+    scene = v.vm3dgs_build_pages(raw, v.BuildConfig(**W["build"], seed=77))
+    del raw
+    return scene, t1 - t0, time.time() - t1
+
+
+def make_renderer(v, scene, W, fp16, width, height):
+    cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=fp16,
+                         max_width=width, max_height=height, tau0=1.0, step0=0.1)
+    if W["pool_bytes"] is None:
+        return v.Renderer(scene, cfg, pool_slots=scene.info.n_pages)
+    return v.Renderer(scene, cfg, pool_bytes=W["pool_bytes"])
+
+
+def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None):
+    import torch
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream()
+    H, W = cams[0].height, cams[0].width
+    images = [torch.empty((3, H, W), dtype=torch.float32, device=dev)]
+    host = torch.empty((3, H, W), dtype=torch.float32, pin_memory=True) if e2e else None
+    n = len(cams)
+
+    def frame(i):
+        c = [cams[i % n]]
+        r.render_feedback(c, st)
+        r.update_residency(st, copy_stream)
+        r.render(c, images, st)
+        if e2e:
+            host.copy_(images[0], non_blocking=True)
+
+    for i in range(warmup):
+        frame(i)
+    torch.cuda.synchronize()
+    r.reset_sums(st)
+    if timing:
+        r.timing(True)
+        r.timing_read()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(st)
+    for i in range(warmup, warmup + steps):
+        frame(i)
+    e1.record(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    stage = r.timing_read() if timing else None
+    if timing:
+        r.timing(False)
+    stats = r.stats(st)
+    return dict(ms=ms, wall=wall, stage=stage, stats=stats)
+
+
+def roofline(v, stage, stats, peaks, rec16, K):
+    """Dominant stage (by GPU time) against its bound, per launch."""
+    ms, launches = stage
+    names = v.STAGES
+    frames = max(stats["acc_frames"], 1)
+    views = max(stats["acc_views"], 1)
+    order = sorted(range(len(ms)), key=lambda i: -ms[i])
+    top = names[order[0]]
+    per_view_pairs = stats["acc_pairs"] / views
+    per_frame_gauss = stats["acc_drawn_gaussians"] / frames
+    # algorithmic bytes per launch (rooflines)
+    bytes_per = {
+        "project": per_frame_gauss * (rec16 + 56),
+        "sort": per_view_pairs * (8 + 24 * math.ceil((32 + 13) / 8)),
+        "blend": per_view_pairs * (4 + 36) + 1920 * 1080 * 12,
+        "scan_emit": per_frame_gauss * 16 + per_view_pairs * 12,
+        "ranges": per_view_pairs * 8,
+        "stream": stats["acc_streamed_bytes"] / frames * 2,
+    }
+    n_launch = {"project": frames, "sort": views, "blend": views, "scan_emit": views, "ranges": views,
+                "stream": frames}
+    out = {"kernel": top, "stage_ms": {names[i]: round(ms[i], 3) for i in range(len(ms))},
+           "stage_launches": {names[i]: int(launches[i]) for i in range(len(ms))}}
+    kt = top if top in bytes_per else "project"
+    t_launch = ms[names.index(kt)] / max(n_launch[kt], 1) / 1e3
+    achieved = bytes_per[kt] / t_launch / 1e9 if t_launch > 0 else 0.0
+    peak = peaks.get("hbm_gbs", 6400.0)
+    out.update({"bound": "hbm" if kt != "blend" else "alu", "kernel_measured": kt, "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
+    if kt == "blend":
+        out["note"] = ("blend is bound by FP32/MUFU issue, not HBM; achieved is its algorithmic bytes over its time")
+    return out
+
+
+def gpu_main(args):
+    import torch
+    import paper_2506_19415_b300 as v
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    W = workload(args.config)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    scene, t_gen, t_build = build_scene(W)
+    n_frames = W["frames"]
+    cams = W["path"](n_frames)
+    if rank:
+        cams = cams[rank % len(cams):] + cams[:rank % len(cams)]
+    width, height = cams[0].width, cams[0].height
+    K = (scene.info.sh_degree + 1) ** 2
+    # plain arm
+    rp = make_renderer(v, scene, W, False, width, height)
+    plain = run_arm(v, rp, cams, args.warmup, args.steps, None, dist=dist)
+    del rp
+    torch.cuda.empty_cache()
+    # headline arm
+    rh = make_renderer(v, scene, W, True, width, height)
+    copy_stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist)
+    clk = clocks.stop()
+    # end to end through the public API: the rendered image returns to pinned host memory every frame
+    e2e = run_arm(v, rh, cams, 0, args.steps, copy_stream, e2e=True, dist=dist)
+
+    def agg(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    ms_head, ms_plain, ms_e2e = agg(head["ms"]), agg(plain["ms"]), agg(e2e["ms"])
+    fps = world * args.steps / (ms_head / 1e3)
+    fps_plain = world * args.steps / (ms_plain / 1e3)
+    fps_e2e = world * args.steps / (ms_e2e / 1e3)
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    hs = head["stats"]
+    frames = max(hs["acc_frames"], 1)
+    rl = roofline(v, head["stage"], hs, peaks, scene.info.record_bytes16, K)
+    launches_per_frame = sum(head["stage"][1]) / frames
+    line = {
+        "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
+        "value": round(fps, 2),
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_head / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 math, f16 pool storage",
+        "data": "synthetic (seeded scenegen), no dataset",
+        "config": {"workload": W["name"], "config": args.config, "gaussians": W["gaussians"],
+                   "pages": scene.info.n_pages, "resolution": [width, height], "frames_in_path": n_frames,
+                   "pool_bytes": W["pool_bytes"], "staging_bytes": 40 * 2048 * 236,
+                   "l2": "per-frame inputs (2 GiB pool, splat and pair buffers) exceed the 126 MB L2",
+                   "arm": "fp16 pool + copy stream", "parallelism": "replicas, one renderer per GPU"},
+        "plain_vm": {"value": round(fps_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain / args.steps, 4),
+                     "arm": "fp32 pool, in-line copies",
+                     "missing_per_frame": plain["stats"]["acc_missing"] / max(plain["stats"]["acc_frames"], 1)},
+        "per_frame": {"missing": hs["acc_missing"] / frames, "requested": hs["acc_requested"] / frames,
+                      "drawn_gaussians": hs["acc_drawn_gaussians"] / frames, "pairs": hs["acc_pairs"] / frames,
+                      "streamed_bytes": hs["acc_streamed_bytes"] / frames, "tau": hs["tau"], "usage": hs["usage"]},
+        "e2e": {"value": round(fps_e2e, 2), "unit": "frames/s", "h2d_bytes_per_step": int(76 + hs["acc_streamed_bytes"] / frames),
+                "d2h_bytes_per_step": 3 * width * height * 4},
+        "gpu_launches": int(round(launches_per_frame * args.steps)),
+        "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+        "roofline_detail": rl,
+        "clocks": clk,
+        "scene_build_s": {"generate": round(t_gen, 1), "prepare": round(t_build, 1)},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, W, quick=True)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+def cpu_sample(W, n_frames):
+    """Bounded sample of the workload for the oracle: the same generator and
+    density on a small patch (city) or the same scene (others), same camera
+    model and resolution; returns (oracle scene, page table, cameras)."""
+    import scenegen
+    from oracle import build as ob
+    from oracle import residency as rs
+    b = dict(W["build"])
+    b.pop("fp16", None)
+    if W["sample"] is not None:
+        s = W["sample"]
+        raw = scenegen.city_scene(n=s["n"], n_boxes=s["n_boxes"], extent=s["extent"])
+        b["hi"] = (s["extent"] + 4, s["extent"] + 4, 88)
+        cams = scenegen.city_walk_path(n_frames=n_frames, n_boxes=s["n_boxes"], extent=s["extent"])
+        pool_bytes = int(W["pool_bytes"] * s["n"] / W["gaussians"])
+    else:
+        raw = W["gen"]()
+        cams = W["path"](max(n_frames, 1))[:n_frames]
+        pool_bytes = W["pool_bytes"]
+    sc = ob.build_scene(raw, ob.BuildParams(**b, seed=77))
+    rec = 4 * (11 + 3 * (raw.sh_degree + 1) ** 2)
+    P = sc.n_pages if pool_bytes is None else max(1, pool_bytes // (sc.params.page_size * rec))
+    pt = rs.PageTable(rs.ResidencyParams(n_entries=P, page_size=sc.params.page_size, levels=len(sc.levels),
+                                         fanout=sc.params.lod_fanout, record_bytes=rec,
+                                         budget_bytes=40 * 2048 * 236, lod=W["lod"]))
+    return sc, pt, cams
+
+
+def cpu_baseline(args, W, quick=False, steps=None):
+    import oracle
+    n = 2 if quick else max(1, steps or 1)
+    sc, pt, cams = cpu_sample(W, n)
+    t0 = time.perf_counter()
+    for c in cams[:n]:
+        oracle.frame(sc, pt, c, ds=4, links=True)
+    dt = time.perf_counter() - t0
+    s = W["sample"]
+    desc = ("%d oracle frames of the full per-frame path at %dx%d on %s" %
+            (n, cams[0].width, cams[0].height,
+             ("a %.0f m x %.0f m patch of the city at the same density (%d Gaussians, %d boxes)" %
+              (s["extent"], s["extent"], s["n"], s["n_boxes"])) if s else "the same scene"))
+    return {"value": round(n / dt, 5), "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W = workload(args.config)
+    cb = cpu_baseline(args, W, steps=args.steps)
+    line = {"impl": "reference", "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
+            "value": cb["value"], "unit": "frames/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (oracle)", "data": "synthetic (seeded scenegen), no dataset",
+            "config": {"workload": W["name"], "config": args.config}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--config", default="city50m")
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_main(args)
+    else:
+        gpu_main(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * vm3dgs — virtual-memory 3D Gaussian Splatting, per-frame path on one GPU.
+ *
+ * C ABI of the library libvm3dgs.so.  Every function is extern "C", takes
+ * plain pointers and sizes, and returns 0 (VM3DGS_OK) or a negative error
+ * code; vm3dgs_last_error() then holds a one-line, thread-local message.
+ * Streams are cudaStream_t values passed as void*.  The library never calls
+ * cudaMalloc: device memory (the page pool, the scratch area, the images) is
+ * owned by the caller and only borrowed.  Host input arrays are borrowed for
+ * the duration of a call and copied.
+ *
+ * The calls follow the problem the paper (Haberl et al., "Virtual Memory for
+ * 3D Gaussian Splatting", arXiv 2506.19415) sets: a trained scene in the
+ * Kerbl 3DGS format is prepared once into pages with links, levels of detail
+ * and a proxy mesh (Sec. 3), then every frame determines the visible pages
+ * from a page-ID visibility buffer (Sec. 4.1 "Page Determination"), updates
+ * a page table and streams missing pages into a fixed device buffer
+ * (Sec. 4.1 "Page Table Management"), and renders only the resident
+ * Gaussians (Sec. 4.2 "Rendering").
+ *
+ * Frame protocol: vm3dgs_render_feedback -> vm3dgs_update_residency ->
+ * vm3dgs_render.  Calls on one renderer are not thread safe.
+ */
+#ifndef VM3DGS_H
+#define VM3DGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- errors */
+#define VM3DGS_OK 0
+#define VM3DGS_E_INVAL (-1)    /* null pointer, out-of-range size, NaN camera */
+#define VM3DGS_E_CAPACITY (-2) /* pool, scratch or pair capacity too small */
+#define VM3DGS_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define VM3DGS_E_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define VM3DGS_E_STATE (-5)    /* call order violated */
+#define VM3DGS_E_NOMEM (-6)    /* host allocation failed */
+
+typedef struct vm3dgs_scene vm3dgs_scene;       /* built pages in host memory */
+typedef struct vm3dgs_renderer vm3dgs_renderer; /* page table, pool view, scratch view */
+
+/* Raw Gaussians in the layout of the 3DGS PLY export (Kerbl et al.), with
+ * the normals already dropped.  K = (sh_degree+1)^2. */
+typedef struct {
+  int64_t n;
+  int32_t sh_degree;       /* 0..3 */
+  const float *pos;        /* [n][3] world position */
+  const float *log_scale;  /* [n][3] log of the axis scales */
+  const float *rot;        /* [n][4] quaternion (w,x,y,z), any non-zero norm */
+  const float *op_logit;   /* [n] opacity before the logistic function */
+  const float *f_dc;       /* [n][3] degree-0 SH coefficient per colour channel */
+  const float *f_rest;     /* [n][3][K-1] higher SH, channel-major; NULL if K == 1 */
+} vm3dgs_gaussians;
+
+/* Offline preparation parameters (Sec. 3). */
+typedef struct {
+  int32_t page_size;       /* Gaussians per level-0 page (Sec. 3.2) */
+  int32_t paging;          /* 0: Morton order in chunks; 1: octree leaves merged greedily */
+  int32_t lod_levels;      /* levels incl. level 0 (Sec. 3.4); 1 = no LOD */
+  int32_t lod_fanout;      /* children merged per parent; page size shrinks by it per level */
+  double lo[3], hi[3];     /* scene box: crop (Sec. 3.5), Morton quantisation, voxel grid */
+  double voxel;            /* proxy voxel edge in world units */
+  double kappa;            /* voxel occupied when its means' opacities sum to >= kappa */
+  int32_t closing;         /* 1: one 3x3x3 closing of the occupancy */
+  int32_t link_samples;    /* random points per Gaussian for page linking (Sec. 3.3) */
+  double link_sigma;       /* ellipsoid extent of the samples, in standard deviations */
+  uint64_t seed;           /* SplitMix64 key of the link samples */
+  int32_t links;           /* 0: build no links */
+  int32_t fp16;            /* 1: also build the fp16 page records */
+  int32_t n_threads;       /* host threads, 0 = all */
+} vm3dgs_build_params;
+
+/* Pinhole camera, OpenCV axes (+x right, +y down, +z forward). */
+typedef struct {
+  float view[12];          /* world -> camera [R|t], rows */
+  float campos[3];         /* camera centre, world */
+  float fx, fy, cx, cy;    /* pixels; pixel (i,j) covers [i,i+1) x [j,j+1) */
+  int32_t width, height;
+  int32_t tile_w, tile_h;  /* splat tile: 8x8, 16x16 or 32x8 */
+} vm3dgs_camera;
+
+/* Renderer parameters. */
+typedef struct {
+  int64_t staging_bytes;   /* bytes streamed per update at most (the staging budget) */
+  int32_t feedback_ds;     /* visibility buffer is ceil(W/ds) x ceil(H/ds) */
+  int32_t links;           /* follow page links in the reduction */
+  int32_t lod;             /* choose levels by screen-space error, adapt the threshold */
+  int32_t fp16_pool;       /* pool holds fp16 records (scene built with fp16 = 1) */
+  float usage_lo, usage_hi;/* target band of pool usage (0.5, 0.8) */
+  float tau0, step0;       /* initial screen-space error threshold and step, pixels */
+  int32_t max_width, max_height; /* largest view rendered */
+  int32_t max_views;       /* largest n_cams passed to vm3dgs_render */
+  int64_t max_pairs;       /* (Gaussian, tile) pairs per view; 0 = 8 x pool Gaussians */
+  float bg[3];             /* background colour */
+} vm3dgs_params;
+
+typedef struct {
+  int32_t frame;
+  int32_t requested;       /* pages in the request list */
+  int32_t direct;          /* of which seen directly (not only through links) */
+  int32_t resident;        /* requested and already resident at the chosen level */
+  int32_t missing;         /* requested but neither resident nor streamed */
+  int32_t streamed_pages;
+  int64_t streamed_bytes;
+  int32_t drawn_pages;
+  int64_t drawn_gaussians;
+  int64_t pairs;           /* (Gaussian, tile) pairs of the last rendered view */
+  float usage;             /* drawn Gaussian capacity / pool capacity */
+  float tau;               /* threshold used for the next frame */
+  int32_t status;          /* device error word: 0 ok, else VM3DGS_E_* */
+  /* running sums since the renderer was created or the sums were reset */
+  int64_t acc_frames, acc_views, acc_pairs, acc_drawn_gaussians, acc_streamed_bytes, acc_streamed_pages,
+      acc_missing, acc_requested;
+} vm3dgs_stats;
+
+typedef struct {
+  int32_t n_pages;         /* virtual pages */
+  int32_t page_size, lod_levels, lod_fanout, sh_degree;
+  int64_t n_gaussians;     /* real level-0 Gaussians after cropping */
+  int32_t record_bytes;    /* fp32 record: 4*(11 + 3K) */
+  int32_t record_bytes16;  /* fp16 record, 0 if not built */
+  int64_t n_tris;          /* proxy triangles */
+  int64_t n_verts;
+  int64_t n_links;
+  int64_t host_bytes;      /* all page data held */
+} vm3dgs_scene_info;
+
+/* Offline preparation (Sec. 3): decode (Sec. 3.5), page (Sec. 3.2), LOD
+ * (Sec. 3.4), voxel proxy with page-marked faces (Sec. 3.1 stand-in), links
+ * (Sec. 3.3).  Runs on the host; needs no GPU.  *out owns its memory. */
+int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build_params *bp, vm3dgs_scene **out);
+
+/* Wraps already-prepared pages (for example from another preparation tool)
+ * into a scene.  Arrays are per level l, [n_pages][m_l][...] with
+ * m_l = page_size / fanout^l; sh is [..][K][3]; err is [n_pages][levels];
+ * the proxy is verts[n_verts][3], tris[n_tris][3], face_page[n_tris] (-1 =
+ * none); links are a CSR link_ptr[n_pages+1], link_col[n_links]. */
+typedef struct {
+  int32_t n_pages, page_size, lod_levels, lod_fanout, sh_degree, fp16;
+  const float *const *pos;      /* [levels] */
+  const float *const *scale;    /* [levels] */
+  const float *const *rot;      /* [levels] */
+  const float *const *opacity;  /* [levels] */
+  const float *const *sh;       /* [levels] */
+  const float *err;
+  const int64_t *count;         /* [n_pages] real level-0 Gaussians */
+  int64_t n_verts, n_tris, n_links;
+  const float *verts;
+  const int32_t *tris;
+  const int32_t *face_page;
+  const int64_t *link_ptr;
+  const int32_t *link_col;
+} vm3dgs_scene_desc;
+int vm3dgs_scene_import(const vm3dgs_scene_desc *d, vm3dgs_scene **out);
+
+int vm3dgs_scene_info_get(const vm3dgs_scene *s, vm3dgs_scene_info *out);
+
+/* Copies one internal array of the scene to host memory for inspection.
+ * what: see VM3DGS_SCENE_*; level selects the LOD level where it applies.
+ * Returns E_CAPACITY (with *needed set) when bytes is too small. */
+enum {
+  VM3DGS_SCENE_PAGE_COUNT = 0,  /* int64 [n_pages] */
+  VM3DGS_SCENE_PAGE_SRC = 1,    /* int64 [n_pages][page_size] input index, -1 padding */
+  VM3DGS_SCENE_PAGES = 2,       /* the level's page blocks, fp32 SoA, [n_pages][rec*m_l] bytes */
+  VM3DGS_SCENE_PAGES16 = 3,     /* same in the fp16 record */
+  VM3DGS_SCENE_ERR = 4,         /* float [n_pages][levels] */
+  VM3DGS_SCENE_VERTS = 5,       /* float [n_verts][3] */
+  VM3DGS_SCENE_TRIS = 6,        /* int32 [n_tris][3] */
+  VM3DGS_SCENE_FACE_PAGE = 7,   /* int32 [n_tris] */
+  VM3DGS_SCENE_LINK_PTR = 8,    /* int64 [n_pages+1] */
+  VM3DGS_SCENE_LINK_COL = 9     /* int32 [n_links] */
+};
+int vm3dgs_scene_export(const vm3dgs_scene *s, int32_t what, int32_t level, void *dst, int64_t bytes,
+                        int64_t *needed);
+void vm3dgs_scene_destroy(vm3dgs_scene *s);
+
+/* Device memory the caller must provide for a renderer. */
+int vm3dgs_pool_slot_bytes(const vm3dgs_scene *s, int32_t fp16_pool, int64_t *out);
+int vm3dgs_scratch_bytes(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t pool_bytes, int64_t *out);
+
+/* Creates a renderer over caller-owned device memory: pool (whole slots of
+ * vm3dgs_pool_slot_bytes each) and scratch (vm3dgs_scratch_bytes).  Makes the
+ * scene's host pages readable by the GPU (page-locks them) on first use.
+ * Clears the page table; returns E_CAPACITY if the pool holds no slot. */
+int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params *p, void *pool_dev, int64_t pool_bytes,
+                           void *scratch_dev, int64_t scratch_bytes, void *stream, vm3dgs_renderer **out);
+void vm3dgs_renderer_destroy(vm3dgs_renderer *r);
+
+/* Page determination (Sec. 4.1): rasterises the proxy with per-face page
+ * IDs into the low-resolution visibility buffer of each camera and reduces
+ * it to one word per page, the maximum over its pixels (and over pixels of
+ * pages linking to it) of a code that decreases with depth. */
+int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, void *stream);
+
+/* Requests every page at level 0 with the nearest depth (the no-virtual-
+ * memory reference, when the pool holds the scene). */
+int vm3dgs_request_all(vm3dgs_renderer *r, void *stream);
+
+/* Page-table update (Sec. 4.1 "Page Table Management"): compaction of the
+ * request words, LOD choice by screen-space error, the two-stage table
+ * update with LRU replacement within the staging budget, the copy of the
+ * new pages from host memory into the pool on copy_stream (which may equal
+ * stream; the render on stream waits for it), and the LOD controller. */
+int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *copy_stream);
+
+/* Renders the resident, required Gaussians (Sec. 4.2) for each camera into
+ * images[v], a caller-owned device float array [3][height][width] (CHW):
+ * projection + SH colour, tile binning, (tile, depth) radix sort, tile
+ * ranges, front-to-back blending. */
+int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images, void *stream);
+
+/* Copies the last frame's statistics (synchronises stream). */
+int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *stream);
+/* Clears the running sums of the statistics (enqueued on stream). */
+int vm3dgs_reset_sums(vm3dgs_renderer *r, void *stream);
+
+/* Copies one device array of the renderer to host memory for inspection
+ * (synchronises stream).  *needed receives the byte size of the array. */
+enum {
+  VM3DGS_DBG_FEEDBACK = 0,   /* uint64 [Hf][Wf] visibility buffer of the last feedback view */
+  VM3DGS_DBG_REQ = 1,        /* uint32 [n_pages] request words */
+  VM3DGS_DBG_DIRECT = 2,     /* uint8 [n_pages] */
+  VM3DGS_DBG_REQUESTS = 3,   /* int32 [n][4] (page, enc, direct, level) request list */
+  VM3DGS_DBG_PT_LOD = 4,     /* int32 [entries] */
+  VM3DGS_DBG_PT_LAST = 5,    /* int32 [entries] */
+  VM3DGS_DBG_PT_SLOT = 6,    /* int32 [entries][fanout^(levels-1)] */
+  VM3DGS_DBG_COPIES = 7,     /* int32 [n][4] (page, level, entry, subslot), priority order */
+  VM3DGS_DBG_DRAW = 8,       /* int32 [n][4] (page, level, entry, subslot), ascending page */
+  VM3DGS_DBG_MISSING = 9,    /* int32 [n] ascending page */
+  VM3DGS_DBG_SPLAT_RECT = 10,/* int32 [N][4] tile rectangle per drawn Gaussian (0s if culled) */
+  VM3DGS_DBG_SPLAT_DEPTH = 11, /* float [N] view z (0 if culled) */
+  VM3DGS_DBG_SPLAT_RADIUS = 12,/* float [N] (0 if culled) */
+  VM3DGS_DBG_KEYS = 13,      /* uint64 [M] sorted keys of the last rendered view */
+  VM3DGS_DBG_VALUES = 14,    /* uint32 [M] drawn-Gaussian index per sorted key */
+  VM3DGS_DBG_RANGES = 15,    /* uint32 [tiles][2] */
+  VM3DGS_DBG_SPLAT_XY = 16,  /* float [N][2] centre */
+  VM3DGS_DBG_SPLAT_CONIC = 17, /* float [N][4] (A, B, C, opacity) */
+  VM3DGS_DBG_SPLAT_RGB = 18, /* float [N][3] */
+  VM3DGS_DBG_POOL = 19       /* the pool bytes */
+};
+int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *host_dst, int64_t bytes, int64_t *needed, void *stream);
+
+/* Per-stage GPU time.  When enabled, each stage of every later frame call is
+ * bracketed by CUDA events on the stream it runs on, and its kernel launches
+ * are counted.  vm3dgs_timing_read synchronises the device, adds the elapsed
+ * milliseconds and launch counts of each stage since the last read into
+ * ms_total[stage] and launches[stage] (arrays of n entries, n <= 8), and
+ * forgets them.  Stages: */
+enum {
+  VM3DGS_STAGE_FEEDBACK = 0,  /* visibility buffer raster + reduction */
+  VM3DGS_STAGE_RESIDENCY = 1, /* request compaction, LOD, page table, controller */
+  VM3DGS_STAGE_STREAM = 2,    /* host -> pool page copies */
+  VM3DGS_STAGE_PROJECT = 3,   /* gather + projection + SH */
+  VM3DGS_STAGE_SCAN_EMIT = 4, /* tiles-touched scan, pair emission */
+  VM3DGS_STAGE_SORT = 5,      /* radix sort of the pairs */
+  VM3DGS_STAGE_RANGES = 6,    /* tile ranges */
+  VM3DGS_STAGE_BLEND = 7,     /* per-tile blending */
+  VM3DGS_N_STAGES = 8
+};
+int vm3dgs_timing_enable(vm3dgs_renderer *r, int32_t on);
+int vm3dgs_timing_read(vm3dgs_renderer *r, double *ms_total, int64_t *launches, int32_t n);
+
+const char *vm3dgs_last_error(void);
+const char *vm3dgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,416 @@
+// Page-table update (Sec. 4.1 "Level of Detail" and "Page Table
+// Management"; evaluation "Page determination details"), run by one CTA of
+// 1024 threads so that the whole update is one deterministic device step:
+//
+//   compact    request words != 0 -> request list, ascending page
+//   LOD        d = float(0xFFFFFFFF - enc) is the page's nearest depth;
+//              level = the largest l >= 1 with (f * e_l(p)) / d <= tau
+//              (screen-space error in pixels), else 0
+//   stage 1    entries holding a requested page at the requested level mark
+//              it required and record the frame; entries with nothing
+//              required are free
+//   stage 2    unmatched requests ordered by (seen directly first, nearest
+//              first, page id); the longest prefix whose level-page bytes
+//              fit the staging budget is admitted, the rest is missing;
+//              per level, admitted requests first fill non-required
+//              sub-slots of entries already required at that level (entry
+//              order, sub-slot order), then fresh entries taken least
+//              recently used first (ties: index), levels in ascending order,
+//              fanout^l per entry; a fresh entry forgets what it held
+//   lists      copy list (priority order) with 64 KiB copy segments, missing
+//              list and draw list (ascending page) with Gaussian offsets
+//   control    usage = drawn Gaussian capacity / pool capacity; above the
+//              band tau grows by step, below it (with a level > 0 drawn) tau
+//              shrinks (not below 0); step *1.01 after a same-direction move
+//              within 10 frames, *0.99 after a reversal within 10 frames.
+// Compiled with -fmad=false (the LOD test and the controller are fp32
+// formulas evaluated exactly as written).
+#include "renderer.cuh"
+
+namespace vm {
+namespace {
+
+constexpr int RT = 1024;
+
+struct ScanSmem {
+  int64_t warp[32];
+  int64_t total;
+};
+
+// exclusive block scan (all 1024 threads call it); returns prefix, sets total
+__device__ int64_t bscan(int64_t v, int64_t *total, ScanSmem &sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm.warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = sm.warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sm.warp[lane] = t;
+  }
+  __syncthreads();
+  const int64_t pre = (warp ? sm.warp[warp - 1] : 0) + x - v;
+  *total = sm.warp[31];
+  __syncthreads();
+  return pre;
+}
+
+__device__ void bitonic(uint64_t *a, int n_pow2) {
+  for (int k = 2; k <= n_pow2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n_pow2; i += RT) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t x = a[i], y = a[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ int pow2_at_least(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+__global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
+  __shared__ ScanSmem sm;
+  __shared__ int m_l[kMaxLevels], S_l[kMaxLevels];
+  __shared__ int n_lvl[kMaxLevels], open_cnt[kMaxLevels], open_base[kMaxLevels], fresh_start[kMaxLevels + 1];
+  __shared__ int s_nfree;
+  Ctl *ctl = a.ctl;
+  const int tid = threadIdx.x;
+  const int NP = a.NP, P = a.P, Smax = a.Smax, L = a.levels;
+  const int frame = ctl->frame;
+  const float tau = ctl->tau;
+  if (tid < kMaxLevels) {
+    int m = a.page_size, S = 1;
+    for (int l = 0; l < tid; ++l) { m /= a.fanout; S *= a.fanout; }
+    m_l[tid] = m;
+    S_l[tid] = S;
+  }
+  __syncthreads();
+
+  // ---- 1. request list; per-page scratch reset
+  int64_t nreq = 0, ndir = 0, tot;
+  for (int c = 0; c < NP; c += RT) {
+    const int p = c + tid;
+    const uint32_t r = p < NP ? a.req[p] : 0u;
+    const int dflag = (p < NP && r != 0u) ? (int)a.direct[p] : 0;
+    if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; }
+    const int64_t pos = bscan(r != 0u, &tot, sm);
+    if (r != 0u) a.requests[nreq + pos] = make_int4(p, (int)r, dflag, 0);
+    nreq += tot;
+    int64_t t2;
+    bscan(dflag, &t2, sm);
+    ndir += t2;
+  }
+  __syncthreads();
+  // ---- 2. LOD choice
+  for (int i = tid; i < nreq; i += RT) {
+    const int4 q = a.requests[i];
+    int lev = 0;
+    if (a.lod_on && L > 1) {
+      const float d = __uint_as_float(0xFFFFFFFFu - (uint32_t)q.y);
+      for (int l = L - 1; l >= 1; --l) {
+        const float sse = (a.f_px * a.err[(int64_t)q.x * L + l]) / d;
+        if (sse <= tau) { lev = l; break; }
+      }
+    }
+    a.requests[i].w = lev;
+    a.reqlev[q.x] = lev;
+  }
+  __syncthreads();
+  // ---- 3. stage 1
+  for (int e = tid; e < P; e += RT) {
+    const int l = a.pt_lod[e];
+    int any = 0;
+    if (l >= 0) {
+      for (int s = 0; s < S_l[l]; ++s) {
+        const int64_t k = (int64_t)e * Smax + s;
+        const int p = a.pt_slot[k];
+        const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
+        a.required[k] = (uint8_t)r;
+        if (r) { a.matched[p] = 1; a.draw_info[p] = (int)k; any = 1; }
+      }
+    }
+    a.any_req[e] = (uint8_t)any;
+    if (any) a.pt_last[e] = frame;
+  }
+  __syncthreads();
+  // ---- 4. unmatched requests as priority keys
+  int64_t nu = 0;
+  for (int c = 0; c < nreq; c += RT) {
+    const int i = c + tid;
+    int4 q = make_int4(0, 0, 0, 0);
+    int f = 0;
+    if (i < nreq) { q = a.requests[i]; f = a.matched[q.x] ? 0 : 1; }
+    const int64_t pos = bscan(f, &tot, sm);
+    if (f)
+      a.ukeys[nu + pos] = ((uint64_t)(q.z ? 0u : 1u) << 63) | ((uint64_t)(~(uint32_t)q.y) << 31) | (uint64_t)q.x;
+    nu += tot;
+  }
+  __syncthreads();
+  const int nu_pow = pow2_at_least((int)nu);
+  const bool sort_ok = nu_pow <= a.ukey_cap;
+  if (sort_ok) {
+    for (int i = (int)nu + tid; i < nu_pow; i += RT) a.ukeys[i] = ~0ull;
+    __syncthreads();
+    bitonic(a.ukeys, nu_pow);
+  } else if (tid == 0) {
+    atomicCAS(&ctl->status, 0, VM3DGS_E_CAPACITY);
+  }
+  __syncthreads();
+  // ---- 5. admission by the staging budget (longest prefix that fits)
+  int64_t nadm = 0, cum = 0;
+  for (int c = 0; c < nu && sort_ok; c += RT) {
+    const int i = c + tid;
+    int64_t cost = 0;
+    if (i < nu) {
+      const int p = (int)(a.ukeys[i] & 0x7FFFFFFFull);
+      cost = (int64_t)m_l[a.reqlev[p]] * a.rec;
+    }
+    const int64_t pre = bscan(cost, &tot, sm);
+    const int ok = (i < nu && cum + pre + cost <= a.budget) ? 1 : 0;
+    int64_t t2;
+    bscan(ok, &t2, sm);
+    nadm += t2;
+    cum += tot;
+  }
+  // ---- 6. per-level rank of the admitted requests
+  for (int l = 0; l < L; ++l) {
+    int64_t base = 0;
+    for (int c = 0; c < nadm; c += RT) {
+      const int i = c + tid;
+      int f = 0;
+      if (i < nadm) f = a.reqlev[(int)(a.ukeys[i] & 0x7FFFFFFFull)] == l;
+      const int64_t pos = bscan(f, &tot, sm);
+      if (f) a.admitted_pos[i] = (int)(base + pos);
+      base += tot;
+    }
+    if (tid == 0) n_lvl[l] = (int)base;
+  }
+  // ---- 7. open sub-slots: entries required this frame at level l
+  int64_t obase = 0;
+  for (int l = 0; l < L; ++l) {
+    int64_t cnt_e = 0, cnt_s = 0;
+    for (int c = 0; c < P; c += RT) {
+      const int e = c + tid;
+      int avail = 0, elig = 0;
+      if (e < P && a.any_req[e] && a.pt_lod[e] == l) {
+        elig = 1;
+        for (int s = 0; s < S_l[l]; ++s) avail += a.required[(int64_t)e * Smax + s] ? 0 : 1;
+      }
+      int64_t te, ts;
+      const int64_t pe = bscan(elig, &te, sm);
+      const int64_t ps = bscan(avail, &ts, sm);
+      if (elig) {
+        a.open_list[obase + cnt_e + pe] = e;
+        a.open_off[obase + cnt_e + pe] = (int)(cnt_s + ps);
+      }
+      cnt_e += te;
+      cnt_s += ts;
+    }
+    if (tid == 0) { open_base[l] = (int)obase; open_cnt[l] = (int)cnt_s; }
+    // sentinel count of eligible entries stored after the list
+    obase += cnt_e;
+    if (tid == 0) a.open_off[P + l] = (int)cnt_e;
+  }
+  __syncthreads();
+  // ---- 8. free entries, least recently used first
+  int64_t nfree = 0;
+  for (int c = 0; c < P; c += RT) {
+    const int e = c + tid;
+    const int f = (e < P && !a.any_req[e]) ? 1 : 0;
+    const int64_t pos = bscan(f, &tot, sm);
+    if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
+    nfree += tot;
+  }
+  __syncthreads();
+  {
+    const int fp = pow2_at_least((int)nfree);
+    for (int i = (int)nfree + tid; i < fp; i += RT) a.free_keys[i] = ~0ull;
+    __syncthreads();
+    bitonic(a.free_keys, fp);
+  }
+  if (tid == 0) {
+    int acc = 0;
+    for (int l = 0; l < L; ++l) {
+      const int rest = n_lvl[l] > open_cnt[l] ? n_lvl[l] - open_cnt[l] : 0;
+      fresh_start[l] = acc;
+      acc += (rest + S_l[l] - 1) / S_l[l];
+    }
+    fresh_start[L] = acc;
+    s_nfree = (int)nfree;
+  }
+  __syncthreads();
+  // ---- 9. initialise the fresh entries
+  {
+    const int nf = fresh_start[L] < s_nfree ? fresh_start[L] : s_nfree;
+    for (int64_t x = tid; x < (int64_t)nf * Smax; x += RT) {
+      const int k = (int)(x / Smax), s = (int)(x % Smax);
+      const int e = (int)(a.free_keys[k] & 0xFFFFFFFFull);
+      a.pt_slot[(int64_t)e * Smax + s] = -1;
+      if (s == 0) {
+        int l = 0;
+        while (l + 1 < L && fresh_start[l + 1] <= k) ++l;
+        a.pt_lod[e] = l;
+        a.pt_last[e] = frame;
+      }
+    }
+  }
+  __syncthreads();
+  // ---- 10. placement of the admitted requests
+  for (int i = tid; i < nadm; i += RT) {
+    const int p = (int)(a.ukeys[i] & 0x7FFFFFFFull);
+    const int l = a.reqlev[p];
+    const int rho = a.admitted_pos[i];
+    int64_t slot = -1;
+    if (rho < open_cnt[l]) {
+      const int ob = open_base[l], ne = a.open_off[P + l];
+      int lo = 0, hi = ne - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.open_off[ob + mid] <= rho) lo = mid; else hi = mid - 1;
+      }
+      const int e = a.open_list[ob + lo];
+      int want = rho - a.open_off[ob + lo];
+      for (int s = 0; s < S_l[l]; ++s) {
+        if (a.required[(int64_t)e * Smax + s]) continue;
+        if (want == 0) { slot = (int64_t)e * Smax + s; break; }
+        --want;
+      }
+    } else {
+      const int j = rho - open_cnt[l];
+      const int k = fresh_start[l] + j / S_l[l];
+      if (k < s_nfree) {
+        const int e = (int)(a.free_keys[k] & 0xFFFFFFFFull);
+        slot = (int64_t)e * Smax + j % S_l[l];
+      }
+    }
+    if (slot >= 0) {
+      a.pt_slot[slot] = p;
+      a.draw_info[p] = (int)slot;
+    } else {
+      a.matched[p] = 2;
+    }
+  }
+  __syncthreads();
+  // ---- 11. copy list in priority order, with copy segments
+  int64_t ncopy = 0, nseg = 0, sbytes = 0;
+  for (int c = 0; c < nadm; c += RT) {
+    const int i = c + tid;
+    int f = 0, p = 0, l = 0;
+    int64_t segs = 0, bytes = 0;
+    if (i < nadm) {
+      p = (int)(a.ukeys[i] & 0x7FFFFFFFull);
+      l = a.reqlev[p];
+      f = a.matched[p] != 2;
+      bytes = f ? (int64_t)m_l[l] * a.rec : 0;
+      segs = (bytes + kCopySeg - 1) / kCopySeg;
+    }
+    int64_t ts, tb;
+    const int64_t pos = bscan(f, &tot, sm);
+    const int64_t spos = bscan(segs, &ts, sm);
+    bscan(bytes, &tb, sm);
+    if (f) {
+      const int slot = a.draw_info[p];
+      a.copies[ncopy + pos] = make_int4(p, l, slot / Smax, slot % Smax);
+      a.copy_seg[ncopy + pos] = nseg + spos;
+    }
+    ncopy += tot;
+    nseg += ts;
+    sbytes += tb;
+  }
+  if (tid == 0) a.copy_seg[ncopy] = nseg;
+  // non-admitted requests are missing too
+  for (int i = (int)nadm + tid; i < nu; i += RT) a.matched[(int)(a.ukeys[i] & 0x7FFFFFFFull)] = 2;
+  __syncthreads();
+  // ---- 12. missing list and draw list, ascending page; draw offsets
+  int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0;
+  for (int c = 0; c < NP; c += RT) {
+    const int p = c + tid;
+    int fm = 0, fd = 0, fl = 0;
+    int64_t g = 0;
+    if (p < NP) {
+      fm = a.matched[p] == 2;
+      fd = a.draw_info[p] >= 0 && !fm;
+      if (fd) { g = m_l[a.reqlev[p]]; fl = a.reqlev[p] > 0; }
+    }
+    int64_t tm, td, tg, tl;
+    const int64_t pm = bscan(fm, &tm, sm);
+    const int64_t pd = bscan(fd, &td, sm);
+    const int64_t pg = bscan(g, &tg, sm);
+    bscan(fl, &tl, sm);
+    nlod += tl;
+    if (fm) a.missing[nmiss + pm] = p;
+    if (fd) {
+      const int slot = a.draw_info[p];
+      a.draw[ndraw + pd] = make_int4(p, a.reqlev[p], slot / Smax, slot % Smax);
+      a.draw_off[ndraw + pd] = gsum + pg;
+    }
+    nmiss += tm;
+    ndraw += td;
+    gsum += tg;
+  }
+  if (tid == 0) {
+    a.draw_off[ndraw] = gsum;
+    ctl->n_req = (int)nreq;
+    ctl->n_direct = (int)ndir;
+    ctl->n_unmatched = (int)nu;
+    ctl->n_admitted = (int)nadm;
+    ctl->n_copies = (int)ncopy;
+    ctl->copy_segments = nseg;
+    ctl->streamed_bytes = sbytes;
+    ctl->n_draw = (int)ndraw;
+    ctl->n_missing = (int)nmiss;
+    ctl->n_resident = (int)(nreq - nu);
+    ctl->n_free = s_nfree;
+    ctl->draw_gauss = gsum;
+    ctl->acc_frames += 1;
+    ctl->acc_draw_gauss += gsum;
+    ctl->acc_streamed_bytes += sbytes;
+    ctl->acc_streamed_pages += ncopy;
+    ctl->acc_missing += nmiss;
+    ctl->acc_requested += nreq;
+    const float usage = P > 0 ? (float)gsum / (float)((int64_t)P * a.page_size) : 0.0f;
+    ctl->usage = usage;
+    // ---- 13. LOD controller
+    if (a.lod_on && L > 1) {
+      const int any_lod = nlod > 0;
+      int dir = 0;
+      if (usage > a.usage_hi) dir = 1;
+      else if (usage < a.usage_lo && any_lod) dir = -1;
+      if (dir != 0) {
+        const bool recent = frame - ctl->last_move <= 10;
+        float step = ctl->step;
+        if (recent && ctl->last_dir == dir) step = step * 1.01f;
+        else if (recent && ctl->last_dir == -dir) step = step * 0.99f;
+        ctl->step = step;
+        float t = dir > 0 ? tau + step : tau - step;
+        ctl->tau = t > 0.0f ? t : 0.0f;
+        ctl->last_dir = dir;
+        ctl->last_move = frame;
+      }
+    }
+    ctl->frame = frame + 1;
+  }
+}
+
+}  // namespace
+
+void launch_residency(const ResidencyArgs &a, cudaStream_t st) { residency_kernel<<<1, RT, 0, st>>>(a); }
+
+}  // namespace vm

@@ -1,0 +1,351 @@
+// Tile binning and depth sort of the splats (Sec. 4.2: the paper sorts its
+// index buffer globally by camera distance with a radix sort before drawing;
+// here the sort key is (tile, depth) so each image tile receives its splats
+// front to back, as in the tiled renderer of Kerbl et al.).
+//
+//   scan + emit   exclusive scan of tiles-touched per splat, then one
+//                 (tile << 32 | float bits of depth, splat index) pair per
+//                 (splat, tile of its rectangle), in ascending splat order.
+//   onesweep      stable LSD radix sort, 8-bit digits, one pass per digit
+//                 over the significant key bits: a histogram kernel counts
+//                 every digit position at once, then each pass ranks a tile
+//                 of keys in shared memory (warp match + per-warp counters),
+//                 obtains its global digit offsets by decoupled look-back
+//                 over predecessor tiles and scatters through shared memory.
+//                 Every look-back wait is bounded: on expiry the kernel
+//                 records VM3DGS_E_TIMEOUT in the control block and goes on.
+//   ranges        [first, last+1) of every tile in the sorted keys.
+// Stability plus ascending emission order gives the order (tile, depth,
+// drawn index), and the drawn index ascends with the virtual Gaussian id.
+#include "renderer.cuh"
+
+namespace vm {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = kScanItems / kScanThreads;   // 4
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 30, kValMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int64_t n_drawn(const Ctl *c, int64_t cap) { return c->draw_gauss < cap ? c->draw_gauss : cap; }
+
+// exclusive scan across a 1024-thread block (64-bit); returns the block total in *total
+__device__ uint64_t block_excl_scan_1024(uint64_t v, uint64_t *total) {
+  __shared__ uint64_t warp_tot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  uint64_t wpre = warp == 0 ? 0 : warp_tot[warp - 1];
+  *total = warp_tot[31];
+  __syncthreads();
+  return wpre + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Ctl *ctl, const uint32_t *touched, int64_t ncap,
+                                                                  uint64_t *block_sums) {
+  const int64_t N = n_drawn(ctl, ncap);
+  const int64_t base = (int64_t)blockIdx.x * kScanItems;
+  if (base >= N) return;
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < N) s += touched[i];
+  }
+  uint64_t tot;
+  block_excl_scan_1024(s, &tot);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int64_t ncap, uint64_t *block_sums) {
+  const int64_t N = n_drawn(ctl, ncap);
+  const int64_t nb = (N + kScanItems - 1) / kScanItems;
+  uint64_t carry = 0;
+  for (int64_t c = 0; c < nb; c += kScanThreads) {
+    int64_t i = c + threadIdx.x;
+    uint64_t v = i < nb ? block_sums[i] : 0, tot;
+    uint64_t ex = block_excl_scan_1024(v, &tot);
+    if (i < nb) block_sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    ctl->pairs = (int64_t)carry;
+    ctl->acc_pairs += (int64_t)carry;
+    ctl->acc_views += 1;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap,
+                                                           const uint64_t *block_off, uint64_t *keys, uint32_t *vals,
+                                                           int64_t pair_cap, int gx) {
+  const int64_t N = n_drawn(ctl, ncap);
+  const int64_t base = (int64_t)blockIdx.x * kScanItems;
+  if (base >= N) return;
+  // blocked arrangement: thread t owns items base + t*4 .. +3
+  const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+  uint32_t cnt[kScanPer];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    cnt[k] = (i0 + k < N) ? sp.touched[i0 + k] : 0;
+    s += cnt[k];
+  }
+  uint64_t tot;
+  uint64_t off = block_off[blockIdx.x] + block_excl_scan_1024(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (!cnt[k]) continue;
+    const int64_t i = i0 + k;
+    const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
+    const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16, y0 = ry & 0xFFFFu, y1 = ry >> 16;
+    const uint64_t dep = sp.depth[i];
+    for (uint32_t ty = y0; ty < y1; ++ty)
+      for (uint32_t tx = x0; tx < x1; ++tx) {
+        if ((int64_t)off < pair_cap) {
+          keys[off] = ((uint64_t)(ty * (uint32_t)gx + tx) << 32) | dep;
+          vals[off] = (uint32_t)i;
+        }
+        ++off;
+      }
+  }
+}
+
+// ------------------------------------------------------------------ onesweep
+__global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, int passes,
+                                                        uint32_t *hist, uint32_t *lookback, int64_t max_tiles,
+                                                        uint32_t *tile_ctr) {
+  __shared__ uint32_t h[kMaxPasses][256];
+  const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    const uint64_t k = keys[j];
+    for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    uint32_t v = (&h[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+  // clear the look-back words this sort will use (pass d owns words
+  // [d * max_tiles * 256, +ntiles * 256)), and the tile counters
+  const int64_t ntiles = (M + kSortTile - 1) / kSortTile;
+  for (int d = 0; d < passes; ++d) {
+    uint32_t *lb = lookback + (int64_t)d * max_tiles * 256;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ntiles * 256; j += stride) lb[j] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < kMaxPasses) tile_ctr[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(256) sort_bases_kernel(uint32_t *hist, int passes) {
+  __shared__ uint32_t tmp[256];
+  for (int d = 0; d < passes; ++d) {
+    tmp[threadIdx.x] = hist[d * 256 + threadIdx.x];
+    __syncthreads();
+    // Hillis-Steele inclusive scan over 256 entries
+    for (int o = 1; o < 256; o <<= 1) {
+      uint32_t v = threadIdx.x >= o ? tmp[threadIdx.x - o] : 0;
+      __syncthreads();
+      tmp[threadIdx.x] += v;
+      __syncthreads();
+    }
+    hist[d * 256 + threadIdx.x] = threadIdx.x == 0 ? 0 : tmp[threadIdx.x - 1];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
+                                                                uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
+                                                                const uint32_t *bases, uint32_t *status,
+                                                                uint32_t *tile_ctr) {
+  constexpr int W = kSortThreads / 32;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
+  uint32_t *s_wc = s_vals + kSortTile;          // [W][256]
+  uint32_t *s_doff = s_wc + W * 256;            // [256]
+  uint32_t *s_glob = s_doff + 256;              // [256]
+  __shared__ int64_t s_tile;
+  __shared__ uint32_t s_scan[W];
+  const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
+  const int64_t ntiles = (M + kSortTile - 1) / kSortTile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  for (;;) {
+    if (tid == 0) s_tile = (int64_t)atomicAdd(tile_ctr, 1u);
+    for (int i = tid; i < W * 256; i += kSortThreads) s_wc[i] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t t0 = tile * kSortTile;
+    uint64_t k[kSortItems];
+    uint32_t v[kSortItems], rk[kSortItems];
+    int dg[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const int64_t idx = t0 + (int64_t)warp * 32 * kSortItems + it * 32 + lane;
+      const bool valid = idx < M;
+      k[it] = valid ? kin[idx] : 0ull;
+      v[it] = valid ? vin[idx] : 0u;
+      dg[it] = valid ? (int)((k[it] >> shift) & 255u) : -1;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const int d = dg[it];
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = 0;
+      if (d >= 0) before = s_wc[warp * 256 + d];
+      rk[it] = before + __popc(peers & lt);
+      __syncwarp();
+      if (d >= 0 && (peers & lt) == 0) s_wc[warp * 256 + d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, tile count
+    uint32_t cnt = 0;
+    for (int w = 0; w < W; ++w) {
+      const uint32_t c = s_wc[w * 256 + tid];
+      s_wc[w * 256 + tid] = cnt;
+      cnt += c;
+    }
+    volatile uint32_t *st = status + tile * 256 + tid;
+    *st = (tile == 0 ? kFlagInc : kFlagAgg) | cnt;
+    // tile-local exclusive scan of the digit counts
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_scan[w];
+    s_doff[tid] = wpre + x - cnt;
+    // decoupled look-back
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int64_t j = tile - 1;
+      for (;;) {
+        const volatile uint32_t *p = status + j * 256 + tid;
+        uint32_t w = *p;
+        int spins = 0;
+        while ((w & kFlagMask) == 0) {
+          if (++spins > kSpinLimit) {
+            atomicCAS(&ctl->status, 0, VM3DGS_E_TIMEOUT);
+            w = kFlagInc;
+            break;
+          }
+          __nanosleep(32);
+          w = *p;
+        }
+        excl += w & kValMask;
+        if ((w & kFlagMask) == kFlagInc) break;
+        --j;
+      }
+      *st = kFlagInc | ((excl + cnt) & kValMask);
+    }
+    s_glob[tid] = bases[tid] + excl;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const int d = dg[it];
+      if (d < 0) continue;
+      const uint32_t pos = s_doff[d] + s_wc[warp * 256 + d] + rk[it];
+      s_keys[pos] = k[it];
+      s_vals[pos] = v[it];
+    }
+    __syncthreads();
+    const int nvalid = (int)((M - t0) < kSortTile ? (M - t0) : kSortTile);
+    for (int i = tid; i < nvalid; i += kSortThreads) {
+      const uint64_t key = s_keys[i];
+      const int d = (int)((key >> shift) & 255u);
+      const uint32_t o = s_glob[d] + (uint32_t)i - s_doff[d];
+      if ((int64_t)o < M) {  // always true unless a look-back wait timed out
+        kout[o] = key;
+        vout[o] = s_vals[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, uint2 *ranges, uint32_t ntiles) {
+  const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
+    const uint32_t t = (uint32_t)(keys[j] >> 32);
+    if (t >= ntiles) continue;  // only after a timed-out sort
+    if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = (uint32_t)j;
+    if (j == M - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = (uint32_t)(j + 1);
+  }
+}
+
+}  // namespace
+
+void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st) {
+  (void)offsets;
+  const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
+  uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, bs);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, bs);
+  emit_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp, ncap, bs, keys, vals, pair_cap, gx);
+}
+
+int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,
+                uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st) {
+  const int passes = (bits + 7) / 8;
+  static bool attr_set = false;
+  const int smem = kSortTile * 12 + (kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return -2;
+    attr_set = true;
+  }
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+  const int64_t max_tiles = (pair_cap + kSortTile - 1) / kSortTile;
+  if ((int64_t)passes * max_tiles * 256 > lookback_words) return -1;
+  sort_hist_kernel<<<148 * 4, 256, 0, st>>>(ctl, keys[0], pair_cap, passes, hist, lookback, max_tiles, tile_ctr);
+  sort_bases_kernel<<<1, 256, 0, st>>>(hist, passes);
+  int grid = 148 * 3;
+  if (grid > max_tiles) grid = (int)(max_tiles > 0 ? max_tiles : 1);
+  int cur = 0;
+  for (int d = 0; d < passes; ++d) {
+    const int64_t lb_off = (int64_t)d * max_tiles * 256;
+    onesweep_kernel<<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], pair_cap,
+                                                       8 * d, hist + d * 256, lookback + lb_off, tile_ctr + d);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, cudaStream_t st) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
+  ranges_kernel<<<148 * 8, 256, 0, st>>>(ctl, keys, pair_cap, ranges, (uint32_t)ntiles);
+}
+
+}  // namespace vm

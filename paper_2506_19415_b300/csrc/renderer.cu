@@ -1,0 +1,581 @@
+// C ABI of the per-frame path: renderer set-up over caller-owned device
+// memory and the three frame calls (page determination, page-table update
+// with streaming, rendering).  Every step runs in the kernels of this
+// library; the host only validates arguments and enqueues work.
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "renderer.cuh"
+
+namespace vm {
+
+namespace {
+int64_t pow2_at_least(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+int64_t al(int64_t x) { return (x + 255) & ~int64_t(255); }
+
+bool cuda_ok(cudaError_t e, const char *what, int *rc) {
+  if (e == cudaSuccess) return true;
+  *rc = fail(VM3DGS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return false;
+}
+
+int check_cams(const vm3dgs_renderer *r, const vm3dgs_camera *cams, int n) {
+  if (!cams || n <= 0) return fail(VM3DGS_E_INVAL, "no cameras");
+  for (int v = 0; v < n; ++v) {
+    const vm3dgs_camera &c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > r->prm.max_width || c.height > r->prm.max_height)
+      return fail(VM3DGS_E_INVAL, "camera size outside the renderer's maximum");
+    const bool tiles_ok = (c.tile_w == 16 && c.tile_h == 16) || (c.tile_w == 8 && c.tile_h == 8) ||
+                          (c.tile_w == 32 && c.tile_h == 8);
+    if (!tiles_ok) return fail(VM3DGS_E_INVAL, "tile shape must be 16x16, 8x8 or 32x8");
+    const float *f = &c.view[0];
+    for (int i = 0; i < 12; ++i)
+      if (!std::isfinite(f[i])) return fail(VM3DGS_E_INVAL, "camera matrix is not finite");
+    if (!(c.fx > 0) || !(c.fy > 0) || !std::isfinite(c.cx) || !std::isfinite(c.cy) || !std::isfinite(c.campos[0]) ||
+        !std::isfinite(c.campos[1]) || !std::isfinite(c.campos[2]))
+      return fail(VM3DGS_E_INVAL, "camera intrinsics are not finite");
+  }
+  return VM3DGS_OK;
+}
+}  // namespace
+
+Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
+  Dims d{};
+  d.NP = s->n_pages;
+  d.P = P;
+  d.Smax = 1;
+  for (int l = 1; l < s->levels; ++l) d.Smax *= s->fanout;
+  const int ds = p->feedback_ds > 0 ? p->feedback_ds : 1;
+  d.fb_pixels = (int64_t)((p->max_width + ds - 1) / ds) * ((p->max_height + ds - 1) / ds);
+  d.ncap = P * s->page_size;
+  d.pair_cap = p->max_pairs > 0 ? p->max_pairs : 8 * d.ncap;
+  if (d.pair_cap > (int64_t(1) << 30) - 1) d.pair_cap = (int64_t(1) << 30) - 1;
+  d.tile_cap = (int64_t)((p->max_width + 7) / 8) * ((p->max_height + 7) / 8);
+  d.ntri = (int64_t)s->face_page.size();
+  d.nvert = (int64_t)s->verts.size() / 3;
+  d.nlink = (int64_t)s->link_col.size();
+  d.scan_blocks = (d.ncap + kScanItems - 1) / kScanItems;
+  d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
+  d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
+  d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
+  return d;
+}
+
+Layout make_layout(const Dims &d) {
+  Layout L{};
+  int64_t o = 0;
+  auto take = [&](int64_t bytes) {
+    int64_t r = o;
+    o = al(o + (bytes > 0 ? bytes : 1));
+    return r;
+  };
+  const int64_t NP = d.NP, P = d.P, N = d.ncap;
+  L.ctl = take(sizeof(Ctl));
+  L.fb = take(8 * d.fb_pixels);
+  L.req = take(4 * NP);
+  L.direct = take(NP);
+  L.reqlev = take(4 * NP);
+  L.matched = take(NP);
+  L.draw_info = take(4 * NP);
+  L.requests = take(16 * NP);
+  L.ukeys = take(8 * (int64_t)d.ukey_cap);
+  L.free_keys = take(8 * (int64_t)d.free_cap);
+  L.open_list = take(4 * (P + kMaxLevels));
+  L.open_off = take(4 * (P + kMaxLevels));
+  L.admitted_pos = take(4 * NP);
+  L.copies = take(16 * NP);
+  L.copy_seg = take(8 * (NP + 1));
+  L.draw = take(16 * NP);
+  L.draw_off = take(8 * (NP + 1));
+  L.missing = take(4 * NP);
+  L.pt_lod = take(4 * P);
+  L.pt_last = take(4 * P);
+  L.pt_slot = take(4 * P * d.Smax);
+  L.required = take(P * d.Smax);
+  L.any_req = take(P);
+  L.verts = take(12 * d.nvert);
+  L.tris = take(12 * d.ntri);
+  L.face_page = take(4 * d.ntri);
+  L.link_ptr = take(8 * (NP + 1));
+  L.link_col = take(4 * d.nlink);
+  L.err = take(4 * NP * kMaxLevels);
+  L.splat_s0 = take(16 * N);
+  L.splat_s1 = take(16 * N);
+  L.splat_s2 = take(4 * N);
+  L.splat_depth = take(4 * N);
+  L.splat_rect = take(8 * N);
+  L.splat_touched = take(4 * N);
+  L.splat_radius = take(4 * N);
+  L.block_sums = take(8 * d.scan_blocks);
+  L.offsets = take(0);
+  L.keys0 = take(8 * d.pair_cap);
+  L.keys1 = take(8 * d.pair_cap);
+  L.vals0 = take(4 * d.pair_cap);
+  L.vals1 = take(4 * d.pair_cap);
+  L.ranges = take(8 * d.tile_cap);
+  L.hist = take(4 * kMaxPasses * 256);
+  L.lookback = take(4 * d.lookback_words);
+  L.tile_ctr = take(4 * kMaxPasses);
+  L.total = o;
+  return L;
+}
+
+static Splats splats_of(const vm3dgs_renderer *r) {
+  Splats s;
+  s.s0 = r->at<float4>(r->lay.splat_s0);
+  s.s1 = r->at<float4>(r->lay.splat_s1);
+  s.s2 = r->at<float>(r->lay.splat_s2);
+  s.depth = r->at<uint32_t>(r->lay.splat_depth);
+  s.rect = r->at<uint32_t>(r->lay.splat_rect);
+  s.touched = r->at<uint32_t>(r->lay.splat_touched);
+  s.radius = r->at<float>(r->lay.splat_radius);
+  return s;
+}
+
+}  // namespace vm
+
+using namespace vm;
+
+extern "C" int vm3dgs_pool_slot_bytes(const vm3dgs_scene *s, int32_t fp16_pool, int64_t *out) {
+  if (!s || !out) return fail(VM3DGS_E_INVAL, "null argument");
+  if (fp16_pool && !s->rec16) return fail(VM3DGS_E_STATE, "scene built without fp16 records");
+  *out = (int64_t)s->page_size * (fp16_pool ? s->rec16 : s->rec32);
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_scratch_bytes(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t pool_bytes, int64_t *out) {
+  if (!s || !p || !out) return fail(VM3DGS_E_INVAL, "null argument");
+  int64_t slot;
+  int rc = vm3dgs_pool_slot_bytes(s, p->fp16_pool, &slot);
+  if (rc) return rc;
+  const int64_t P = pool_bytes / slot;
+  Dims d = make_dims(s, p, P);
+  *out = make_layout(d).total;
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params *p, void *pool_dev,
+                                      int64_t pool_bytes, void *scratch_dev, int64_t scratch_bytes, void *stream,
+                                      vm3dgs_renderer **out) {
+  if (!s || !p || !out || !pool_dev || !scratch_dev) return fail(VM3DGS_E_INVAL, "null argument");
+  *out = nullptr;
+  if (p->feedback_ds < 1 || p->max_width < 1 || p->max_height < 1 || p->staging_bytes < 0 ||
+      !(p->usage_lo >= 0) || !(p->usage_hi >= p->usage_lo) || !(p->tau0 >= 0) || !(p->step0 > 0))
+    return fail(VM3DGS_E_INVAL, "bad renderer parameters");
+  if (s->m(s->levels - 1) % 4 != 0) return fail(VM3DGS_E_INVAL, "smallest level page must hold a multiple of 4");
+  int64_t slot;
+  int rc = vm3dgs_pool_slot_bytes(s, p->fp16_pool, &slot);
+  if (rc) return rc;
+  const int64_t P = pool_bytes / slot;
+  if (P < 1) return fail(VM3DGS_E_CAPACITY, "pool holds no page slot (" + std::to_string(slot) + " bytes each)");
+  if (P * (int64_t)s->page_size >= (int64_t(1) << 31) / 1) return fail(VM3DGS_E_CAPACITY, "pool too large");
+  Dims d = make_dims(s, p, P);
+  Layout L = make_layout(d);
+  if (scratch_bytes < L.total)
+    return fail(VM3DGS_E_CAPACITY, "scratch needs " + std::to_string(L.total) + " bytes");
+  auto *r = new (std::nothrow) vm3dgs_renderer();
+  if (!r) return fail(VM3DGS_E_NOMEM, "renderer");
+  r->scene = s;
+  r->prm = *p;
+  r->pool = (uint8_t *)pool_dev;
+  r->pool_bytes = pool_bytes;
+  r->slot_bytes = slot;
+  r->P = (int32_t)P;
+  r->fp16 = p->fp16_pool != 0;
+  r->rec = r->fp16 ? s->rec16 : s->rec32;
+  r->scratch = (uint8_t *)scratch_dev;
+  r->dims = d;
+  r->lay = L;
+  cudaStream_t st = (cudaStream_t)stream;
+  // page-lock the pages the GPU will pull, once per scene
+  auto *ms = const_cast<vm3dgs_scene *>(s);
+  uint8_t *data = r->fp16 ? ms->data16 : ms->data32;
+  const int64_t bytes = r->fp16 ? ms->bytes16 : ms->bytes32;
+  bool &reg = r->fp16 ? ms->registered16 : ms->registered32;
+  if (!reg) {
+    if (!cuda_ok(cudaHostRegister(data, (size_t)((bytes + 4095) / 4096 * 4096),
+                                  cudaHostRegisterMapped | cudaHostRegisterPortable),
+                 "cudaHostRegister", &rc)) {
+      delete r;
+      return rc;
+    }
+    reg = true;
+  }
+  void *dp = nullptr;
+  if (!cuda_ok(cudaHostGetDevicePointer(&dp, data, 0), "cudaHostGetDevicePointer", &rc)) { delete r; return rc; }
+  r->host_dev = (const uint8_t *)dp;
+  // static scene arrays
+  bool ok = true;
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.verts), s->verts.data(), 4 * s->verts.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.tris), s->tris.data(), 4 * s->tris.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.face_page), s->face_page.data(), 4 * s->face_page.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.link_ptr), s->link_ptr.data(), 8 * s->link_ptr.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  if (!s->link_col.empty())
+    ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.link_col), s->link_col.data(), 4 * s->link_col.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.err), s->err.data(), 4 * s->err.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_lod), 0xFF, 4 * P, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_last), 0xFF, 4 * P, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_slot), 0xFF, 4 * P * d.Smax, st), "memset", &rc);
+  Ctl c{};
+  c.tau = p->tau0;
+  c.step = p->step0;
+  c.last_move = -1000;
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.ctl), &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "copy", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->copy_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaStreamSynchronize(st), "sync", &rc);
+  if (!ok) { delete r; return rc; }
+  *out = r;
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_timing_enable(vm3dgs_renderer *r, int32_t on) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  r->timing = on != 0;
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_timing_read(vm3dgs_renderer *r, double *ms_total, int64_t *launches, int32_t n) {
+  if (!r || !ms_total || !launches || n < 0) return fail(VM3DGS_E_INVAL, "null argument");
+  int rc = 0;
+  if (!cuda_ok(cudaDeviceSynchronize(), "timing sync", &rc)) return rc;
+  for (auto &t : r->spans) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) ms = 0.0f;
+    if (t.stage < n) {
+      ms_total[t.stage] += ms;
+      launches[t.stage] += t.launches;
+    }
+    r->spare_events.push_back(t.a);
+    r->spare_events.push_back(t.b);
+  }
+  r->spans.clear();
+  cudaGetLastError();
+  return VM3DGS_OK;
+}
+
+extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
+  if (!r) return;
+  cudaDeviceSynchronize();
+  for (auto &t : r->spans) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  for (auto e : r->spare_events) cudaEventDestroy(e);
+  if (r->copy_done) cudaEventDestroy(r->copy_done);
+  delete r;
+}
+
+extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, void *stream) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  int rc = check_cams(r, cams, n_cams);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t NP = r->dims.NP;
+  cudaMemsetAsync(r->at<void>(r->lay.req), 0, 4 * NP, st);
+  cudaMemsetAsync(r->at<void>(r->lay.direct), 0, NP, st);
+  const int ds = r->prm.feedback_ds;
+  float fpx = 0.0f;
+  const int sp_fb = r->span_begin(VM3DGS_STAGE_FEEDBACK, st);
+  for (int v = 0; v < n_cams; ++v) {
+    const vm3dgs_camera &c = cams[v];
+    const int64_t npix = (int64_t)((c.width + ds - 1) / ds) * ((c.height + ds - 1) / ds);
+    uint64_t *fb = r->at<uint64_t>(r->lay.fb);
+    launch_feedback_clear(fb, npix, st);
+    launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
+                           r->dims.ntri, c, ds, fb, st);
+    launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
+                           r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
+    r->last_fb_pixels = npix;
+    if (c.fy > fpx) fpx = c.fy;
+  }
+  r->span_end(sp_fb, 3 * n_cams, st);
+  r->f_px = fpx;
+  r->state = 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("feedback: ") + cudaGetErrorString(e));
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_request_all(r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), r->dims.NP, st);
+  r->f_px = 1.0f;
+  r->state = 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("request_all: ") + cudaGetErrorString(e));
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *copy_stream) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  if (r->state < 1) return fail(VM3DGS_E_STATE, "update_residency before render_feedback");
+  cudaStream_t st = (cudaStream_t)stream, cst = copy_stream ? (cudaStream_t)copy_stream : st;
+  const vm3dgs_scene *s = r->scene;
+  ResidencyArgs a{};
+  a.ctl = r->at<Ctl>(r->lay.ctl);
+  a.req = r->at<uint32_t>(r->lay.req);
+  a.direct = r->at<uint8_t>(r->lay.direct);
+  a.reqlev = r->at<int32_t>(r->lay.reqlev);
+  a.draw_info = r->at<int32_t>(r->lay.draw_info);
+  a.matched = r->at<uint8_t>(r->lay.matched);
+  a.requests = r->at<int4>(r->lay.requests);
+  a.ukeys = r->at<uint64_t>(r->lay.ukeys);
+  a.free_keys = r->at<uint64_t>(r->lay.free_keys);
+  a.open_list = r->at<int32_t>(r->lay.open_list);
+  a.open_off = r->at<int32_t>(r->lay.open_off);
+  a.admitted_pos = r->at<int32_t>(r->lay.admitted_pos);
+  a.copies = r->at<int4>(r->lay.copies);
+  a.copy_seg = r->at<int64_t>(r->lay.copy_seg);
+  a.draw = r->at<int4>(r->lay.draw);
+  a.draw_off = r->at<int64_t>(r->lay.draw_off);
+  a.missing = r->at<int32_t>(r->lay.missing);
+  a.pt_lod = r->at<int32_t>(r->lay.pt_lod);
+  a.pt_last = r->at<int32_t>(r->lay.pt_last);
+  a.pt_slot = r->at<int32_t>(r->lay.pt_slot);
+  a.required = r->at<uint8_t>(r->lay.required);
+  a.any_req = r->at<uint8_t>(r->lay.any_req);
+  a.err = r->at<float>(r->lay.err);
+  a.NP = (int32_t)r->dims.NP;
+  a.P = r->P;
+  a.Smax = (int32_t)r->dims.Smax;
+  a.levels = s->levels;
+  a.fanout = s->fanout;
+  a.page_size = s->page_size;
+  a.lod_on = r->prm.lod;
+  a.budget = r->prm.staging_bytes;
+  a.rec = r->rec;
+  a.f_px = r->f_px;
+  a.usage_lo = r->prm.usage_lo;
+  a.usage_hi = r->prm.usage_hi;
+  a.ukey_cap = r->dims.ukey_cap;
+  a.free_cap = r->dims.free_cap;
+  const int sp_res = r->span_begin(VM3DGS_STAGE_RESIDENCY, st);
+  launch_residency(a, st);
+  r->span_end(sp_res, 1, st);
+  StreamArgs sa{};
+  sa.ctl = a.ctl;
+  sa.copies = a.copies;
+  sa.copy_seg = a.copy_seg;
+  sa.host = r->host_dev;
+  for (int l = 0; l < s->levels; ++l) sa.level_off[l] = r->fp16 ? s->off16[l] : s->off32[l];
+  sa.page_size = s->page_size;
+  sa.fanout = s->fanout;
+  sa.rec = r->rec;
+  sa.pool = r->pool;
+  sa.slot_bytes = r->slot_bytes;
+  if (cst == st) {
+    const int sp = r->span_begin(VM3DGS_STAGE_STREAM, st);
+    launch_stream(sa, st);
+    r->span_end(sp, 1, st);
+    r->copy_pending = false;
+  } else {
+    cudaEventRecord(r->copy_done, st);
+    cudaStreamWaitEvent(cst, r->copy_done, 0);
+    const int sp = r->span_begin(VM3DGS_STAGE_STREAM, cst);
+    launch_stream(sa, cst);
+    r->span_end(sp, 1, cst);
+    cudaEventRecord(r->copy_done, cst);
+    r->copy_pending = true;
+  }
+  r->state = 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("update_residency: ") + cudaGetErrorString(e));
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images,
+                             void *stream) {
+  if (!r || !images) return fail(VM3DGS_E_INVAL, "null argument");
+  if (r->state < 2) return fail(VM3DGS_E_STATE, "render before update_residency");
+  int rc = check_cams(r, cams, n_cams);
+  if (rc) return rc;
+  if (n_cams > (r->prm.max_views > 0 ? r->prm.max_views : 1)) return fail(VM3DGS_E_INVAL, "more views than max_views");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (r->copy_pending) {
+    cudaStreamWaitEvent(st, r->copy_done, 0);
+    r->copy_pending = false;
+  }
+  const vm3dgs_scene *s = r->scene;
+  Ctl *ctl = r->at<Ctl>(r->lay.ctl);
+  Splats sp = splats_of(r);
+  ProjectArgs pa{};
+  pa.ctl = ctl;
+  pa.draw = r->at<int4>(r->lay.draw);
+  pa.draw_off = r->at<int64_t>(r->lay.draw_off);
+  pa.pool = r->pool;
+  pa.slot_bytes = r->slot_bytes;
+  pa.page_size = s->page_size;
+  pa.fanout = s->fanout;
+  pa.K = s->K;
+  pa.fp16 = r->fp16;
+  pa.ncap = r->dims.ncap;
+  pa.sp = sp;
+  uint64_t *keys[2] = {r->at<uint64_t>(r->lay.keys0), r->at<uint64_t>(r->lay.keys1)};
+  uint32_t *vals[2] = {r->at<uint32_t>(r->lay.vals0), r->at<uint32_t>(r->lay.vals1)};
+  for (int v = 0; v < n_cams; ++v) {
+    const vm3dgs_camera &c = cams[v];
+    if (!images[v]) return fail(VM3DGS_E_INVAL, "null image");
+    const int gx = (c.width + c.tile_w - 1) / c.tile_w, gy = (c.height + c.tile_h - 1) / c.tile_h;
+    const int ntiles = gx * gy;
+    if (ntiles > r->dims.tile_cap) return fail(VM3DGS_E_CAPACITY, "too many tiles");
+    int tbits = 0;
+    while ((1 << tbits) < ntiles) ++tbits;
+    int t = r->span_begin(VM3DGS_STAGE_PROJECT, st);
+    launch_project(pa, c, st);
+    r->span_end(t, 1, st);
+    t = r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st);
+    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), nullptr, keys[0], vals[0],
+                     r->dims.pair_cap, gx, st);
+    r->span_end(t, 3, st);
+    const int bits = 32 + tbits;
+    t = r->span_begin(VM3DGS_STAGE_SORT, st);
+    const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, bits, r->at<uint32_t>(r->lay.hist),
+                                r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
+                                r->at<uint32_t>(r->lay.tile_ctr), st);
+    r->span_end(t, 2 + (bits + 7) / 8, st);
+    if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
+    if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
+    uint2 *ranges = r->at<uint2>(r->lay.ranges);
+    t = r->span_begin(VM3DGS_STAGE_RANGES, st);
+    launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, st);
+    r->span_end(t, 1, st);
+    t = r->span_begin(VM3DGS_STAGE_BLEND, st);
+    launch_blend(ranges, vals[cur], sp, r->dims.ncap, c, r->prm.bg, images[v], st);
+    r->span_end(t, 1, st);
+    r->sorted_buf = cur;
+    r->last_ntiles = ntiles;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("render: ") + cudaGetErrorString(e));
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *stream) {
+  if (!r || !out) return fail(VM3DGS_E_INVAL, "null argument");
+  Ctl c;
+  int rc = 0;
+  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+               "stats", &rc))
+    return rc;
+  if (!cuda_ok(cudaStreamSynchronize((cudaStream_t)stream), "stats sync", &rc)) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->frame = c.frame;
+  out->requested = c.n_req;
+  out->direct = c.n_direct;
+  out->resident = c.n_resident;
+  out->missing = c.n_missing;
+  out->streamed_pages = c.n_copies;
+  out->streamed_bytes = c.streamed_bytes;
+  out->drawn_pages = c.n_draw;
+  out->drawn_gaussians = c.draw_gauss;
+  out->pairs = c.pairs;
+  out->usage = c.usage;
+  out->tau = c.tau;
+  out->status = c.status;
+  if (c.status == 0 && c.pairs > r->dims.pair_cap) out->status = VM3DGS_E_CAPACITY;
+  out->acc_frames = c.acc_frames;
+  out->acc_views = c.acc_views;
+  out->acc_pairs = c.acc_pairs;
+  out->acc_drawn_gaussians = c.acc_draw_gauss;
+  out->acc_streamed_bytes = c.acc_streamed_bytes;
+  out->acc_streamed_pages = c.acc_streamed_pages;
+  out->acc_missing = c.acc_missing;
+  out->acc_requested = c.acc_requested;
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_reset_sums(vm3dgs_renderer *r, void *stream) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  int rc = 0;
+  const size_t off = offsetof(Ctl, acc_frames);
+  if (!cuda_ok(cudaMemsetAsync(r->scratch + r->lay.ctl + off, 0, sizeof(Ctl) - off, (cudaStream_t)stream), "reset", &rc))
+    return rc;
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, int64_t bytes, int64_t *needed,
+                                 void *stream) {
+  if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctl c;
+  int rc = 0;
+  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc))
+    return rc;
+  if (!cuda_ok(cudaStreamSynchronize(st), "debug sync", &rc)) return rc;
+  const Layout &L = r->lay;
+  const int64_t NP = r->dims.NP, P = r->P, N = c.draw_gauss < r->dims.ncap ? c.draw_gauss : r->dims.ncap;
+  const int64_t M = c.pairs < r->dims.pair_cap ? c.pairs : r->dims.pair_cap;
+  const void *src = nullptr;
+  int64_t n = 0;
+  switch (what) {
+    case VM3DGS_DBG_FEEDBACK: src = r->at<void>(L.fb); n = 8 * r->last_fb_pixels; break;
+    case VM3DGS_DBG_REQ: src = r->at<void>(L.req); n = 4 * NP; break;
+    case VM3DGS_DBG_DIRECT: src = r->at<void>(L.direct); n = NP; break;
+    case VM3DGS_DBG_REQUESTS: src = r->at<void>(L.requests); n = 16 * (int64_t)c.n_req; break;
+    case VM3DGS_DBG_PT_LOD: src = r->at<void>(L.pt_lod); n = 4 * P; break;
+    case VM3DGS_DBG_PT_LAST: src = r->at<void>(L.pt_last); n = 4 * P; break;
+    case VM3DGS_DBG_PT_SLOT: src = r->at<void>(L.pt_slot); n = 4 * P * r->dims.Smax; break;
+    case VM3DGS_DBG_COPIES: src = r->at<void>(L.copies); n = 16 * (int64_t)c.n_copies; break;
+    case VM3DGS_DBG_DRAW: src = r->at<void>(L.draw); n = 16 * (int64_t)c.n_draw; break;
+    case VM3DGS_DBG_MISSING: src = r->at<void>(L.missing); n = 4 * (int64_t)c.n_missing; break;
+    case VM3DGS_DBG_SPLAT_RECT: {
+      // unpack (x0 | x1 << 16, y0 | y1 << 16) into int32 x0, y0, x1, y1
+      n = 16 * N;
+      if (needed) *needed = n;
+      if (!dst) return VM3DGS_OK;
+      if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
+      std::vector<uint32_t> packed(2 * N);
+      if (N && !cuda_ok(cudaMemcpy(packed.data(), r->at<void>(L.splat_rect), 8 * N, cudaMemcpyDeviceToHost), "debug", &rc))
+        return rc;
+      int32_t *o = (int32_t *)dst;
+      for (int64_t i = 0; i < N; ++i) {
+        o[4 * i + 0] = (int32_t)(packed[2 * i] & 0xFFFFu);
+        o[4 * i + 1] = (int32_t)(packed[2 * i + 1] & 0xFFFFu);
+        o[4 * i + 2] = (int32_t)(packed[2 * i] >> 16);
+        o[4 * i + 3] = (int32_t)(packed[2 * i + 1] >> 16);
+      }
+      return VM3DGS_OK;
+    }
+    case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(L.splat_depth); n = 4 * N; break;
+    case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(L.splat_radius); n = 4 * N; break;
+    case VM3DGS_DBG_KEYS: src = r->at<void>(r->sorted_buf ? L.keys1 : L.keys0); n = 8 * M; break;
+    case VM3DGS_DBG_VALUES: src = r->at<void>(r->sorted_buf ? L.vals1 : L.vals0); n = 4 * M; break;
+    case VM3DGS_DBG_RANGES: src = r->at<void>(L.ranges); n = 8 * (int64_t)r->last_ntiles; break;
+    case VM3DGS_DBG_SPLAT_XY:
+    case VM3DGS_DBG_SPLAT_CONIC:
+    case VM3DGS_DBG_SPLAT_RGB: {
+      n = (what == VM3DGS_DBG_SPLAT_XY ? 8 : what == VM3DGS_DBG_SPLAT_CONIC ? 16 : 12) * N;
+      if (needed) *needed = n;
+      if (!dst) return VM3DGS_OK;
+      if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
+      std::vector<float4> a(N), b(N);
+      std::vector<float> cc(N);
+      if (N) {
+        bool ok = cuda_ok(cudaMemcpy(a.data(), r->at<void>(L.splat_s0), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
+                  cuda_ok(cudaMemcpy(b.data(), r->at<void>(L.splat_s1), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
+                  cuda_ok(cudaMemcpy(cc.data(), r->at<void>(L.splat_s2), 4 * N, cudaMemcpyDeviceToHost), "debug", &rc);
+        if (!ok) return rc;
+      }
+      float *o = (float *)dst;
+      for (int64_t i = 0; i < N; ++i) {
+        if (what == VM3DGS_DBG_SPLAT_XY) { o[2 * i] = a[i].x; o[2 * i + 1] = a[i].y; }
+        else if (what == VM3DGS_DBG_SPLAT_CONIC) { o[4 * i] = a[i].z; o[4 * i + 1] = a[i].w; o[4 * i + 2] = b[i].x; o[4 * i + 3] = b[i].y; }
+        else { o[3 * i] = b[i].z; o[3 * i + 1] = b[i].w; o[3 * i + 2] = cc[i]; }
+      }
+      return VM3DGS_OK;
+    }
+    case VM3DGS_DBG_POOL: src = r->pool; n = (int64_t)r->P * r->slot_bytes; break;
+    default: return fail(VM3DGS_E_INVAL, "unknown debug item");
+  }
+  if (needed) *needed = n;
+  if (!dst) return VM3DGS_OK;
+  if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
+  if (n && !cuda_ok(cudaMemcpy(dst, src, (size_t)n, cudaMemcpyDeviceToHost), "debug copy", &rc)) return rc;
+  return VM3DGS_OK;
+}

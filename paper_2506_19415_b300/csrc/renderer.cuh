@@ -1,0 +1,181 @@
+// Internal renderer state, scratch layout and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "scene.h"
+
+namespace vm {
+
+// Device control block: per-frame counters, controller state, error word.
+struct Ctl {
+  int32_t n_req, n_direct, n_unmatched, n_admitted, n_copies, n_draw, n_missing, n_resident;
+  int32_t n_free, pad0;
+  int64_t draw_gauss;      // Gaussians of the draw list
+  int64_t pairs;           // pairs of the last rendered view
+  int64_t streamed_bytes;
+  int64_t copy_segments;   // 64 KiB copy segments of this frame
+  float usage, tau, step;
+  int32_t last_dir, last_move, frame;
+  int32_t status;          // 0 or a VM3DGS_E_* code written by a kernel
+  int32_t depth_lo;        // unused
+  int32_t pad1;
+  // running sums since the last reset (read without per-frame syncs)
+  int64_t acc_frames, acc_views, acc_pairs, acc_draw_gauss, acc_streamed_bytes, acc_streamed_pages, acc_missing,
+      acc_requested;
+};
+
+struct Splats {
+  float4 *s0;        // (x, y, A, B)
+  float4 *s1;        // (C, opacity, r, g)
+  float *s2;         // b
+  uint32_t *depth;   // float bits of view z
+  uint32_t *rect;    // [2] per splat: x0 | x1 << 16, y0 | y1 << 16
+  uint32_t *touched; // tiles touched (0 = culled)
+  float *radius;     // pixels
+};
+
+// Layout of the scratch area; offsets in bytes.
+struct Layout {
+  int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
+      admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
+      face_page, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
+      splat_radius, block_sums, offsets, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+};
+
+struct Dims {
+  int64_t NP, P, Smax, fb_pixels, ncap, pair_cap, tile_cap, ntri, nvert, nlink, scan_blocks, lookback_words;
+  int ukey_cap, free_cap;
+};
+
+Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P);
+Layout make_layout(const Dims &d);
+
+constexpr int kScanItems = 4096;     // elements per scan block
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxPasses = 8;
+constexpr int64_t kCopySeg = 65536;
+
+// ----- launchers (one per kernel family)
+void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
+void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
+                            const vm3dgs_camera &cam, int ds, uint64_t *fb, cudaStream_t st);
+void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
+                            int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
+void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
+
+struct ResidencyArgs {
+  Ctl *ctl;
+  const uint32_t *req;
+  const uint8_t *direct;
+  int32_t *reqlev, *draw_info;
+  uint8_t *matched;
+  int4 *requests;
+  uint64_t *ukeys, *free_keys;
+  int32_t *open_list, *open_off, *admitted_pos;
+  int4 *copies;
+  int64_t *copy_seg;
+  int4 *draw;
+  int64_t *draw_off;
+  int32_t *missing;
+  int32_t *pt_lod, *pt_last, *pt_slot;
+  uint8_t *required, *any_req;
+  const float *err;
+  int32_t NP, P, Smax, levels, fanout, page_size;
+  int32_t lod_on;
+  int64_t budget;
+  int32_t rec;        // bytes per Gaussian in the pool
+  float f_px;
+  float usage_lo, usage_hi;
+  int32_t ukey_cap, free_cap;
+};
+void launch_residency(const ResidencyArgs &a, cudaStream_t st);
+
+struct StreamArgs {
+  const Ctl *ctl;
+  const int4 *copies;
+  const int64_t *copy_seg;
+  const uint8_t *host;          // device-visible pointer to the scene's page data (fp32 or fp16)
+  int64_t level_off[kMaxLevels];
+  int32_t page_size, fanout, rec;
+  uint8_t *pool;
+  int64_t slot_bytes;
+};
+void launch_stream(const StreamArgs &a, cudaStream_t st);
+
+struct ProjectArgs {
+  const Ctl *ctl;
+  const int4 *draw;
+  const int64_t *draw_off;
+  const uint8_t *pool;
+  int64_t slot_bytes;
+  int32_t page_size, fanout, K, fp16;
+  int64_t ncap;
+  Splats sp;
+};
+void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st);
+
+void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st);
+
+// sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
+// returns the index (0 or 1) of the buffer holding the result
+int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,
+                uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
+
+void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, cudaStream_t st);
+
+void launch_blend(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap, const vm3dgs_camera &cam,
+                  const float bg[3], float *image, cudaStream_t st);
+
+}  // namespace vm
+
+struct vm3dgs_renderer {
+  const vm3dgs_scene *scene = nullptr;
+  vm3dgs_params prm{};
+  uint8_t *pool = nullptr;
+  int64_t pool_bytes = 0, slot_bytes = 0;
+  int32_t P = 0;
+  int32_t rec = 0;
+  bool fp16 = false;
+  uint8_t *scratch = nullptr;
+  vm::Dims dims{};
+  vm::Layout lay{};
+  const uint8_t *host_dev = nullptr;   // device-visible pointer to the pages streamed
+  int state = 0;                        // 0 idle, 1 feedback done, 2 residency done
+  float f_px = 0.0f;
+  cudaEvent_t copy_done = nullptr;
+  bool copy_pending = false;
+  int64_t last_fb_pixels = 0;
+  int sorted_buf = 0;     // pair buffer (0/1) holding the last view's sorted pairs
+  int last_ntiles = 0;
+  // per-stage timing
+  struct TimedSpan { int stage; int launches; cudaEvent_t a, b; };
+  bool timing = false;
+  std::vector<TimedSpan> spans;
+  std::vector<cudaEvent_t> spare_events;
+  cudaEvent_t take_event() {
+    cudaEvent_t e = nullptr;
+    if (!spare_events.empty()) { e = spare_events.back(); spare_events.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+  }
+  int span_begin(int stage, cudaStream_t st) {
+    if (!timing) return -1;
+    TimedSpan t{stage, 0, take_event(), take_event()};
+    cudaEventRecord(t.a, st);
+    spans.push_back(t);
+    return (int)spans.size() - 1;
+  }
+  void span_end(int idx, int launches, cudaStream_t st) {
+    if (idx < 0) return;
+    spans[idx].launches = launches;
+    cudaEventRecord(spans[idx].b, st);
+  }
+  template <class T>
+  T *at(int64_t off) const { return reinterpret_cast<T *>(scratch + off); }
+};

@@ -1,0 +1,186 @@
+// Scene object: error reporting, import of prepared pages, inspection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "scene.h"
+
+namespace vm {
+thread_local std::string g_last_error;
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+}  // namespace vm
+
+vm3dgs_scene::~vm3dgs_scene() {
+  if (registered32 && data32) cudaHostUnregister(data32);
+  if (registered16 && data16) cudaHostUnregister(data16);
+  std::free(data32);
+  std::free(data16);
+}
+
+extern "C" const char *vm3dgs_last_error(void) { return vm::g_last_error.c_str(); }
+extern "C" const char *vm3dgs_version(void) { return "vm3dgs 0.1 sm_103a"; }
+
+extern "C" void vm3dgs_scene_destroy(vm3dgs_scene *s) { delete s; }
+
+extern "C" int vm3dgs_scene_info_get(const vm3dgs_scene *s, vm3dgs_scene_info *o) {
+  if (!s || !o) return vm::fail(VM3DGS_E_INVAL, "null argument");
+  o->n_pages = s->n_pages;
+  o->page_size = s->page_size;
+  o->lod_levels = s->levels;
+  o->lod_fanout = s->fanout;
+  o->sh_degree = s->sh_degree;
+  o->n_gaussians = s->n_gauss;
+  o->record_bytes = s->rec32;
+  o->record_bytes16 = s->rec16;
+  o->n_tris = (int64_t)s->face_page.size();
+  o->n_verts = (int64_t)s->verts.size() / 3;
+  o->n_links = (int64_t)s->link_col.size();
+  o->host_bytes = s->bytes32 + s->bytes16;
+  return VM3DGS_OK;
+}
+
+namespace {
+int copy_out(const void *src, int64_t n, void *dst, int64_t bytes, int64_t *needed) {
+  if (needed) *needed = n;
+  if (!dst) return VM3DGS_OK;
+  if (bytes < n) return vm::fail(VM3DGS_E_CAPACITY, "destination too small");
+  if (n) std::memcpy(dst, src, (size_t)n);
+  return VM3DGS_OK;
+}
+}  // namespace
+
+extern "C" int vm3dgs_scene_export(const vm3dgs_scene *s, int32_t what, int32_t level, void *dst, int64_t bytes,
+                                   int64_t *needed) {
+  if (!s) return vm::fail(VM3DGS_E_INVAL, "null scene");
+  if (level < 0 || level >= s->levels) return vm::fail(VM3DGS_E_INVAL, "level out of range");
+  const int64_t NP = s->n_pages;
+  switch (what) {
+    case VM3DGS_SCENE_PAGE_COUNT: return copy_out(s->count.data(), 8 * NP, dst, bytes, needed);
+    case VM3DGS_SCENE_PAGE_SRC: return copy_out(s->src.data(), 8 * (int64_t)s->src.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_PAGES:
+      return copy_out(s->data32 + s->off32[level], NP * s->m(level) * (int64_t)s->rec32, dst, bytes, needed);
+    case VM3DGS_SCENE_PAGES16:
+      if (!s->data16) return vm::fail(VM3DGS_E_STATE, "scene built without fp16 records");
+      return copy_out(s->data16 + s->off16[level], NP * s->m(level) * (int64_t)s->rec16, dst, bytes, needed);
+    case VM3DGS_SCENE_ERR: return copy_out(s->err.data(), 4 * (int64_t)s->err.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_VERTS: return copy_out(s->verts.data(), 4 * (int64_t)s->verts.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_TRIS: return copy_out(s->tris.data(), 4 * (int64_t)s->tris.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_FACE_PAGE:
+      return copy_out(s->face_page.data(), 4 * (int64_t)s->face_page.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_LINK_PTR: return copy_out(s->link_ptr.data(), 8 * (int64_t)s->link_ptr.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_LINK_COL: return copy_out(s->link_col.data(), 4 * (int64_t)s->link_col.size(), dst, bytes, needed);
+    default: return vm::fail(VM3DGS_E_INVAL, "unknown export item");
+  }
+}
+
+namespace {
+uint16_t to_half(float f) {
+  // IEEE binary32 -> binary16, round to nearest even
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  uint32_t sign = (x >> 16) & 0x8000u, mant = x & 0x7FFFFFu;
+  int exp = (int)((x >> 23) & 0xFF);
+  if (exp == 0xFF) return (uint16_t)(sign | 0x7C00u | (mant ? 0x200u : 0));
+  int e = exp - 127 + 15;
+  if (e >= 31) return (uint16_t)(sign | 0x7C00u);
+  if (e <= 0) {
+    if (e < -10) return (uint16_t)sign;
+    mant |= 0x800000u;
+    int shift = 14 - e;
+    uint32_t h = mant >> shift, rem = mant & ((1u << shift) - 1), half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (h & 1))) ++h;
+    return (uint16_t)(sign | h);
+  }
+  uint32_t h = ((uint32_t)e << 10) | (mant >> 13), rem = mant & 0x1FFFu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1))) ++h;
+  return (uint16_t)(sign | h);
+}
+}  // namespace
+
+extern "C" int vm3dgs_scene_import(const vm3dgs_scene_desc *d, vm3dgs_scene **out) {
+  using namespace vm;
+  if (!d || !out) return fail(VM3DGS_E_INVAL, "null argument");
+  *out = nullptr;
+  if (d->n_pages <= 0 || d->page_size <= 0 || d->lod_levels < 1 || d->lod_levels > kMaxLevels || d->lod_fanout < 2 ||
+      d->sh_degree < 0 || d->sh_degree > 3 || !d->pos || !d->scale || !d->rot || !d->opacity || !d->sh || !d->err ||
+      !d->count || !d->link_ptr || (d->n_tris > 0 && (!d->verts || !d->tris || !d->face_page)))
+    return fail(VM3DGS_E_INVAL, "bad scene description");
+  auto *S = new (std::nothrow) vm3dgs_scene();
+  if (!S) return fail(VM3DGS_E_NOMEM, "scene");
+  const int K = (d->sh_degree + 1) * (d->sh_degree + 1), NA = n_attr32(K);
+  S->n_pages = d->n_pages; S->page_size = d->page_size; S->levels = d->lod_levels; S->fanout = d->lod_fanout;
+  S->sh_degree = d->sh_degree; S->K = K;
+  S->rec32 = rec_bytes32(K); S->rec16 = d->fp16 ? rec_bytes16(K) : 0;
+  const int64_t NP = d->n_pages;
+  S->count.assign(d->count, d->count + NP);
+  S->n_gauss = 0;
+  for (int64_t p = 0; p < NP; ++p) S->n_gauss += S->count[p];
+  S->src.assign(NP * d->page_size, -1);
+  int64_t total = 0;
+  for (int l = 0; l < S->levels; ++l) { S->off32[l] = total; total += NP * (int64_t)S->m(l) * S->rec32; }
+  S->bytes32 = total;
+  S->data32 = (uint8_t *)std::aligned_alloc(4096, (size_t)((total + 4095) / 4096 * 4096));
+  if (!S->data32) { delete S; return fail(VM3DGS_E_NOMEM, "page data"); }
+  for (int l = 0; l < S->levels; ++l) {
+    const int64_t m = S->m(l);
+    for (int64_t p = 0; p < NP; ++p) {
+      float *blk = (float *)(S->data32 + S->off32[l]) + p * m * NA;
+      for (int64_t g = 0; g < m; ++g) {
+        const int64_t i = p * m + g;
+        for (int a = 0; a < 3; ++a) blk[a * m + g] = d->pos[l][3 * i + a];
+        for (int a = 0; a < 3; ++a) blk[(3 + a) * m + g] = d->scale[l][3 * i + a];
+        for (int a = 0; a < 4; ++a) blk[(6 + a) * m + g] = d->rot[l][4 * i + a];
+        blk[10 * m + g] = d->opacity[l][i];
+        for (int k = 0; k < 3 * K; ++k) blk[(11 + k) * m + g] = d->sh[l][(size_t)i * 3 * K + k];
+      }
+    }
+  }
+  if (d->fp16) {
+    const int NH = n_half16(K);
+    int64_t t16 = 0;
+    for (int l = 0; l < S->levels; ++l) { S->off16[l] = t16; t16 += NP * (int64_t)S->m(l) * S->rec16; }
+    S->bytes16 = t16;
+    S->data16 = (uint8_t *)std::aligned_alloc(4096, (size_t)((t16 + 4095) / 4096 * 4096));
+    if (!S->data16) { delete S; return fail(VM3DGS_E_NOMEM, "fp16 page data"); }
+    for (int l = 0; l < S->levels; ++l) {
+      const int64_t m = S->m(l);
+      for (int64_t p = 0; p < NP; ++p) {
+        const float *src = (const float *)(S->data32 + S->off32[l]) + p * m * NA;
+        uint8_t *dst = S->data16 + S->off16[l] + p * m * S->rec16;
+        float *f = (float *)dst;
+        uint16_t *h = (uint16_t *)(dst + 16 * m);
+        for (int64_t g = 0; g < m; ++g) {
+          for (int a = 0; a < 3; ++a) f[a * m + g] = src[a * m + g];
+          f[3 * m + g] = src[10 * m + g];
+          for (int a = 0; a < 3; ++a) h[a * m + g] = to_half(src[(3 + a) * m + g]);
+          for (int a = 0; a < 4; ++a) h[(3 + a) * m + g] = to_half(src[(6 + a) * m + g]);
+          for (int k = 0; k < 3 * K; ++k) h[(7 + k) * m + g] = to_half(src[(11 + k) * m + g]);
+          for (int k = 7 + 3 * K; k < NH; ++k) h[k * m + g] = 0;
+        }
+      }
+    }
+  }
+  S->err.assign(d->err, d->err + NP * S->levels);
+  S->verts.assign(d->verts, d->verts + 3 * d->n_verts);
+  S->tris.assign(d->tris, d->tris + 3 * d->n_tris);
+  S->face_page.assign(d->face_page, d->face_page + d->n_tris);
+  S->link_ptr.assign(d->link_ptr, d->link_ptr + NP + 1);
+  if (S->link_ptr[NP] != d->n_links) { delete S; return fail(VM3DGS_E_INVAL, "link_ptr does not end at n_links"); }
+  S->link_col.assign(d->link_col, d->link_col + d->n_links);
+  for (int64_t t = 0; t < d->n_tris; ++t) {
+    for (int k = 0; k < 3; ++k)
+      if (S->tris[3 * t + k] < 0 || S->tris[3 * t + k] >= d->n_verts) { delete S; return fail(VM3DGS_E_INVAL, "triangle index"); }
+    if (S->face_page[t] < -1 || S->face_page[t] >= NP) { delete S; return fail(VM3DGS_E_INVAL, "face page out of range"); }
+  }
+  for (int64_t k = 0; k < d->n_links; ++k)
+    if (S->link_col[k] < 0 || S->link_col[k] >= NP) { delete S; return fail(VM3DGS_E_INVAL, "link column out of range"); }
+  *out = S;
+  return VM3DGS_OK;
+}

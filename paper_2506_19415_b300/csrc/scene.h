@@ -1,0 +1,60 @@
+// Internal scene representation shared by the host builder and the renderer.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vm3dgs.h"
+
+#ifdef __CUDACC__
+#define VM_HD __host__ __device__
+#else
+#define VM_HD
+#endif
+
+namespace vm {
+
+constexpr int kMaxLevels = 6;
+
+// Error reporting: a thread-local message plus the return code.
+int fail(int code, const std::string &msg);
+
+// fp32 record: attributes of one Gaussian as float arrays of a page block.
+//   0..2 pos, 3..5 scale, 6..9 rot (w,x,y,z), 10 opacity, 11 + 3k + c  SH coefficient k, channel c
+VM_HD constexpr int n_attr32(int K) { return 11 + 3 * K; }
+// fp16 record: float arrays pos x,y,z, opacity; then half arrays
+//   0..2 scale, 3..6 rot, 7 + 3k + c SH, padded to an even count.
+VM_HD constexpr int n_half16(int K) { return ((7 + 3 * K) + 1) & ~1; }
+VM_HD constexpr int rec_bytes32(int K) { return 4 * n_attr32(K); }
+VM_HD constexpr int rec_bytes16(int K) { return 16 + 2 * n_half16(K); }
+
+}  // namespace vm
+
+struct vm3dgs_scene {
+  int32_t n_pages = 0, page_size = 0, levels = 1, fanout = 8, sh_degree = 0, K = 1;
+  int64_t n_gauss = 0;
+  int32_t rec32 = 0, rec16 = 0;
+  std::vector<int64_t> count;    // real level-0 Gaussians per page
+  std::vector<int64_t> src;      // [n_pages * page_size] input index or -1
+  // page blocks: level l page p occupies bytes [off32[l] + p * m_l * rec32, +m_l * rec32)
+  uint8_t *data32 = nullptr;
+  int64_t bytes32 = 0;
+  int64_t off32[vm::kMaxLevels] = {0};
+  uint8_t *data16 = nullptr;
+  int64_t bytes16 = 0;
+  int64_t off16[vm::kMaxLevels] = {0};
+  std::vector<float> err;        // [n_pages * levels]
+  std::vector<float> verts;      // [n_verts * 3]
+  std::vector<int32_t> tris;     // [n_tris * 3]
+  std::vector<int32_t> face_page;
+  std::vector<int64_t> link_ptr; // [n_pages + 1]
+  std::vector<int32_t> link_col;
+  bool registered32 = false, registered16 = false;
+
+  int32_t m(int l) const {
+    int32_t v = page_size;
+    for (int i = 0; i < l; ++i) v /= fanout;
+    return v;
+  }
+  ~vm3dgs_scene();
+};

@@ -1,0 +1,146 @@
+"""GPU parity of the virtual-memory frame (page determination, page table,
+streaming, LOD) against the oracle over camera trajectories, bit-exact:
+visibility buffer, request words and list, page-table state, copy, draw and
+missing lists, controller state; the pool holds exactly the host pages the
+table says; images within the FP32 tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from _common import city_cam, city_scene, compare_image, import_scene, tiny_scene
+from oracle import residency as rs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def v():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2506_19415_b300 as mod
+    return mod
+
+
+def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=True, tau0=1.0, check_images=(),
+                    fp16=False):
+    scene = import_scene(v, raw, sc, fp16=fp16)
+    W, H = cams[0].width, cams[0].height
+    rec = scene.info.record_bytes16 if fp16 else scene.info.record_bytes
+    budget = budget_pages * sc.params.page_size * rec
+    cfg = v.RenderConfig(max_width=W, max_height=H, lod=lod, links=links, staging_bytes=budget, tau0=tau0,
+                         fp16_pool=fp16)
+    r = v.Renderer(scene, cfg, pool_slots=pool_slots)
+    rp = rs.ResidencyParams(n_entries=pool_slots, page_size=sc.params.page_size, levels=len(sc.levels),
+                            fanout=sc.params.lod_fanout, record_bytes=rec, budget_bytes=budget, lod=lod, tau0=tau0)
+    pt = rs.PageTable(rp)
+    smax = sc.params.lod_fanout ** (len(sc.levels) - 1)
+    host_pages = [scene.pages(l, fp16=fp16) for l in range(len(sc.levels))]
+    for f, cam in enumerate(cams):
+        r.render_feedback([cam])
+        r.update_residency()
+        img = r.render([cam])[0].cpu().numpy()
+        ref = oracle.frame(sc, pt, cam, ds=4, links=links, render_image=f in check_images)
+        st = r.stats()
+        assert st["status"] == 0
+        # page determination
+        np.testing.assert_array_equal(r.debug(v.DBG_FEEDBACK, np.uint64).reshape(ref["buf"].shape), ref["buf"])
+        np.testing.assert_array_equal(r.debug(v.DBG_REQ, np.uint32), ref["req"])
+        np.testing.assert_array_equal(r.debug(v.DBG_DIRECT, np.uint8), ref["direct"])
+        reqs = r.debug(v.DBG_REQUESTS, np.int32).reshape(-1, 4)
+        np.testing.assert_array_equal(reqs[:, 0], ref["pages"])
+        np.testing.assert_array_equal(reqs[:, 1].view(np.uint32), ref["enc"])
+        np.testing.assert_array_equal(reqs[:, 2], ref["direct"][ref["pages"]])
+        np.testing.assert_array_equal(reqs[:, 3], ref["levels"])
+        # page table
+        up = ref["update"]
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_LOD, np.int32), pt.lod)
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_LAST, np.int32), pt.last_used)
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_SLOT, np.int32).reshape(pool_slots, smax), pt.slot)
+        np.testing.assert_array_equal(r.debug(v.DBG_COPIES, np.int32).reshape(-1, 4),
+                                      np.array(up["copies"], np.int32).reshape(-1, 4))
+        draw = r.debug(v.DBG_DRAW, np.int32).reshape(-1, 4)
+        np.testing.assert_array_equal(draw, np.array(up["draw"], np.int32).reshape(-1, 4))
+        np.testing.assert_array_equal(r.debug(v.DBG_MISSING, np.int32), np.array(up["missing"], np.int32))
+        assert st["usage"] == np.float32(up["usage"])
+        assert st["tau"] == np.float32(pt.tau)
+        assert st["streamed_bytes"] == up["streamed_bytes"]
+        # the pool holds the host bytes of every drawn page
+        pool = r.debug(v.DBG_POOL, np.uint8).reshape(pool_slots, -1)
+        for (p, l, e, s) in draw:
+            blk = host_pages[l][p]
+            np.testing.assert_array_equal(pool[e, s * len(blk):(s + 1) * len(blk)], blk)
+        if f in check_images:
+            compare_image(img, ref["render"])
+    return r
+
+
+def test_tiny_scene_feedback_frames(v):
+    raw, sc = tiny_scene()
+    cams = [scenegen.look_at((12 * np.cos(a), 3.0, 12 * np.sin(a)), (0, 0, 0), (0, -1, 0), 128, 96, 60.0)
+            for a in np.linspace(0, 1.5, 8)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=20, budget_pages=6, lod=False, check_images=(0, 7))
+
+
+@pytest.mark.parametrize("links", [True, False])
+def test_city_lod_trajectory(v, links):
+    raw, sc = city_scene()
+    cams = [city_cam(160.0, k) for k in range(14)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=8, budget_pages=5, lod=True, links=links, tau0=2.0,
+                    check_images=(0, 13))
+
+
+def test_city_lod_trajectory_fp16(v):
+    raw, sc = city_scene(levels=3, fanout=8, page_size=512)
+    cams = [city_cam(160.0, k, width=200, height=120) for k in range(6)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=5, budget_pages=3, lod=True, tau0=1.0, fp16=True)
+
+
+def test_halving_lod_four_levels(v):
+    """The paper's own LOD shape: four levels, each halving the page."""
+    raw, sc = city_scene(levels=4, fanout=2, page_size=256, n=30000)
+    cams = [city_cam(160.0, k, width=160, height=96) for k in range(8)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=10, budget_pages=4, lod=True, tau0=4.0)
+
+
+def test_fully_resident_vm_render_equals_full_scene(v):
+    """Pool holding the whole scene, LOD off: after feedback-driven streaming
+    frames (pages land in arbitrary slots), requesting every page renders the
+    same bits as a renderer that loaded the scene in page order."""
+    raw, sc = tiny_scene()
+    scene = import_scene(v, raw, sc)
+    cam = scenegen.tiny_camera(width=192, height=160)
+    cfg = v.RenderConfig(max_width=192, max_height=160, lod=False, staging_bytes=1 << 40)
+    a = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    walk = [scenegen.look_at((12 * np.cos(t), -4.0, 12 * np.sin(t)), (0, 0, 0), (0, -1, 0), 192, 160, 60.0)
+            for t in np.linspace(0.3, 5.0, 10)]
+    for c in walk:
+        a.render_feedback([c])
+        a.update_residency()
+        a.render([c])
+    a.request_all()
+    a.update_residency()
+    img_a = a.render([cam])[0].cpu().numpy()
+    b = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    b.request_all()
+    b.update_residency()
+    img_b = b.render([cam])[0].cpu().numpy()
+    assert a.stats()["missing"] == 0
+    assert np.array_equal(img_a, img_b)
+    g, vid = oracle.full_scene(sc)
+    compare_image(img_a, oracle.render(g, vid, cam))
+
+
+def test_zero_budget_streams_nothing(v):
+    raw, sc = tiny_scene()
+    scene = import_scene(v, raw, sc)
+    cfg = v.RenderConfig(max_width=128, max_height=96, lod=False, staging_bytes=0)
+    r = v.Renderer(scene, cfg, pool_slots=4)
+    cam = scenegen.tiny_camera(width=128, height=96)
+    r.render_feedback([cam])
+    r.update_residency()
+    img = r.render([cam])[0].cpu().numpy()
+    st = r.stats()
+    assert st["streamed_pages"] == 0 and st["drawn_pages"] == 0 and st["missing"] == st["requested"] > 0
+    assert np.all(img == 0)
