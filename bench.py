@@ -47,6 +47,16 @@ def workload(name):
             path=lambda n: scenegen.city_walk_path(n_frames=n),
             frames=1000, pool_bytes=2 << 30, lod=True, gaussians=50_000_000,
             sample=dict(extent=150.0, n=int(50_000_000 * (150.0 / ext) ** 2), n_boxes=max(1, int(5000 * (150.0 / ext) ** 2))))
+    if name == "citypatch":
+        ext = 1000.0
+        return dict(
+            name="city patch 12.5M Gaussians, 1 km x 1 km, 1250 boxes, SH3, pages 4096 x 3 LOD, 512 MiB pool, 1080p "
+                 "walking flythrough (profiling size)",
+            gen=lambda: scenegen.city_scene(n=12_500_000, n_boxes=1250, extent=ext),
+            build=dict(page_size=4096, paging="octree", lod_levels=3, lod_fanout=8, lo=(-4, -4, -4),
+                       hi=(ext + 4, ext + 4, 88), voxel=2.0, kappa=0.5, link_samples=4, fp16=True),
+            path=lambda n: scenegen.city_walk_path(n_frames=n, n_boxes=1250, extent=ext),
+            frames=1000, pool_bytes=512 << 20, lod=True, gaussians=12_500_000, sample=None)
     if name == "blobs1m":
         return dict(
             name="1M Gaussians in 200 blobs (sigma 0.5 m) in a 50 m cube, SH3, octree pages 4096, 64 MiB pool, 1080p "

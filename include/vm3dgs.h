@@ -93,7 +93,7 @@ typedef struct {
   float tau0, step0;       /* initial screen-space error threshold and step, pixels */
   int32_t max_width, max_height; /* largest view rendered */
   int32_t max_views;       /* largest n_cams passed to vm3dgs_render */
-  int64_t max_pairs;       /* (Gaussian, tile) pairs per view; 0 = 8 x pool Gaussians */
+  int64_t max_pairs;       /* (Gaussian, tile) pairs per view; 0 = max(8 x pool Gaussians, 2^22) */
   float bg[3];             /* background colour */
 } vm3dgs_params;
 

@@ -31,9 +31,48 @@ __device__ __forceinline__ int64_t floordiv256(int64_t a) { return a >= 0 ? a / 
 
 __device__ __forceinline__ bool owns(int64_t dx, int64_t dy) { return dy < 0 || (dy == 0 && dx > 0); }
 
-// all 32 lanes call this with identical arguments; lanes split the pixels
-__device__ void raster_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
-                           uint64_t *fb, int lane) {
+// A snapped, oriented (area > 0) triangle with its clamped pixel box.
+struct Tri {
+  int32_t X[3], Y[3];
+  float Z[3];
+  uint32_t page1;
+  int32_t i0, i1, j0, j1;
+};
+
+// coverage test and depth write of pixel (i, j)
+__device__ __forceinline__ void shade(const Tri &t, const int64_t *dxe, const int64_t *dye, const bool *own,
+                                      float farea, int64_t i, int64_t j, int Wf, uint64_t *fb) {
+  const int ea[3] = {1, 2, 0};
+  const int64_t px = i * 256 + 128, py = j * 256 + 128;
+  int64_t E[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    E[k] = dxe[k] * (py - (int64_t)t.Y[ea[k]]) - dye[k] * (px - (int64_t)t.X[ea[k]]);
+    if (!(E[k] > 0 || (E[k] == 0 && own[k]))) return;
+  }
+  float b0 = __ll2float_rn(E[0]) / farea, b1 = __ll2float_rn(E[1]) / farea, b2 = __ll2float_rn(E[2]) / farea;
+  float s = (b0 / t.Z[0] + b1 / t.Z[1]) + b2 / t.Z[2];
+  float zp = 1.0f / s;
+  const uint64_t key = ((uint64_t)__float_as_uint(zp) << 32) | t.page1;
+  atomicMin(reinterpret_cast<unsigned long long *>(fb + j * Wf + i), (unsigned long long)key);
+}
+
+__device__ __forceinline__ void edges(const Tri &t, int64_t *dxe, int64_t *dye, bool *own, float *farea) {
+  const int ea[3] = {1, 2, 0}, eb[3] = {2, 0, 1};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dxe[k] = (int64_t)t.X[eb[k]] - t.X[ea[k]];
+    dye[k] = (int64_t)t.Y[eb[k]] - t.Y[ea[k]];
+    own[k] = owns(dxe[k], dye[k]);
+  }
+  const int64_t area = dxe[2] * ((int64_t)t.Y[2] - t.Y[0]) - dye[2] * ((int64_t)t.X[2] - t.X[0]);
+  *farea = __ll2float_rn(area);
+}
+
+// Snaps and orients one (clipped) triangle; small ones are rasterised by the
+// calling thread, larger ones go to the queue for whole-CTA rasterisation.
+__device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
+                          uint64_t *fb, Tri *queue, uint32_t *qcount, uint32_t qcap) {
   int64_t X[3], Y[3];
   float Z[3];
 #pragma unroll
@@ -52,7 +91,6 @@ __device__ void raster_tri(const V3 *c, uint32_t page1, float fxf, float fyf, fl
     int64_t t = X[1]; X[1] = X[2]; X[2] = t;
     t = Y[1]; Y[1] = Y[2]; Y[2] = t;
     float tf = Z[1]; Z[1] = Z[2]; Z[2] = tf;
-    area = -area;
   }
   int64_t xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
   int64_t ymin = min(Y[0], min(Y[1], Y[2])), ymax = max(Y[0], max(Y[1], Y[2]));
@@ -63,46 +101,33 @@ __device__ void raster_tri(const V3 *c, uint32_t page1, float fxf, float fyf, fl
   if (i1 > Wf - 1) i1 = Wf - 1;
   if (j1 > Hf - 1) j1 = Hf - 1;
   if (i1 < i0 || j1 < j0) return;
-  const int ea[3] = {1, 2, 0}, eb[3] = {2, 0, 1};
-  bool own[3];
-  int64_t dxe[3], dye[3];
+  Tri t;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dxe[k] = X[eb[k]] - X[ea[k]];
-    dye[k] = Y[eb[k]] - Y[ea[k]];
-    own[k] = owns(dxe[k], dye[k]);
-  }
-  const float farea = __ll2float_rn(area);
+  for (int k = 0; k < 3; ++k) { t.X[k] = (int32_t)X[k]; t.Y[k] = (int32_t)Y[k]; t.Z[k] = Z[k]; }
+  t.page1 = page1;
+  t.i0 = (int32_t)i0; t.i1 = (int32_t)i1; t.j0 = (int32_t)j0; t.j1 = (int32_t)j1;
   const int64_t bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
-  for (int64_t q = lane; q < npx; q += 32) {
-    const int64_t i = i0 + q % bw, j = j0 + q / bw;
-    const int64_t px = i * 256 + 128, py = j * 256 + 128;
-    int64_t E[3];
-    bool in = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      E[k] = dxe[k] * (py - Y[ea[k]]) - dye[k] * (px - X[ea[k]]);
-      in = in && (E[k] > 0 || (E[k] == 0 && own[k]));
-    }
-    if (!in) continue;
-    float b0 = __ll2float_rn(E[0]) / farea, b1 = __ll2float_rn(E[1]) / farea, b2 = __ll2float_rn(E[2]) / farea;
-    float s = (b0 / Z[0] + b1 / Z[1]) + b2 / Z[2];
-    float zp = 1.0f / s;
-    const uint64_t key = ((uint64_t)__float_as_uint(zp) << 32) | page1;
-    atomicMin(reinterpret_cast<unsigned long long *>(fb + j * Wf + i), (unsigned long long)key);
+  if (npx > 16) {
+    const uint32_t q = atomicAdd(qcount, 1u);
+    if (q < qcap) { queue[q] = t; return; }
   }
+  int64_t dxe[3], dye[3];
+  bool own[3];
+  float farea;
+  edges(t, dxe, dye, own, &farea);
+  for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, i0 + q % bw, j0 + q / bw, Wf, fb);
 }
 
-__global__ void __launch_bounds__(256) raster_kernel(const float *verts, const int32_t *tris, const int32_t *face_page,
-                                                     int64_t ntri, vm3dgs_camera cam, int ds, uint64_t *fb) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
+                                                           const int32_t *face_page, int64_t ntri, vm3dgs_camera cam,
+                                                           int ds, uint64_t *fb, Tri *queue, uint32_t *qcount,
+                                                           uint32_t qcap) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
   const float zn = 0.2f;
-  for (int64_t t = w0; t < ntri; t += nw) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
     V3 c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
@@ -112,7 +137,10 @@ __global__ void __launch_bounds__(256) raster_kernel(const float *verts, const i
 #pragma unroll
     for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
     if (nin == 0) continue;
-    if (nin == 3) { raster_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, lane); continue; }
+    if (nin == 3) {
+      setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
+      continue;
+    }
     V3 poly[4];
     int m = 0;
 #pragma unroll
@@ -131,8 +159,23 @@ __global__ void __launch_bounds__(256) raster_kernel(const float *verts, const i
     }
     for (int k = 1; k + 1 < m; ++k) {
       V3 tri[3] = {poly[0], poly[k], poly[k + 1]};
-      raster_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, lane);
+      setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
     }
+  }
+}
+
+// one CTA per queued triangle at a time, threads over its pixel box
+__global__ void __launch_bounds__(256) raster_large_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
+                                                           int Wf, uint64_t *fb) {
+  const uint32_t n = min(*qcount, qcap);
+  for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+    const Tri t = queue[q];
+    int64_t dxe[3], dye[3];
+    bool own[3];
+    float farea;
+    edges(t, dxe, dye, own, &farea);
+    const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
+    for (int64_t p = threadIdx.x; p < npx; p += blockDim.x) shade(t, dxe, dye, own, farea, t.i0 + p % bw, t.j0 + p / bw, Wf, fb);
   }
 }
 
@@ -179,11 +222,16 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
 }
 
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
-                            const vm3dgs_camera &cam, int ds, uint64_t *fb, cudaStream_t st) {
+                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
+                            uint32_t qcap, cudaStream_t st) {
   if (ntri <= 0) return;
-  int64_t blocks = (ntri * 32 + 255) / 256;
-  if (blocks > 148 * 16) blocks = 148 * 16;
-  raster_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, face_page, ntri, cam, ds, fb);
+  cudaMemsetAsync(qcount, 0, sizeof(uint32_t), st);
+  int64_t blocks = (ntri + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  raster_setup_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, face_page, ntri, cam, ds, fb,
+                                                        reinterpret_cast<Tri *>(queue), qcount, qcap);
+  const int Wf = (cam.width + ds - 1) / ds;
+  raster_large_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
 }
 
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,

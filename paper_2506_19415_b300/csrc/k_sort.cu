@@ -91,13 +91,18 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int
   }
 }
 
+// Pair emission balanced over the block: every thread computes the pair
+// offsets of its 4 splats, the block's offsets go to shared memory, then the
+// block's pairs are written in order, pair j by thread j mod 1024, each thread
+// finding its splat by binary search: consecutive threads write consecutive
+// keys whatever the splat sizes.
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap,
                                                            const uint64_t *block_off, uint64_t *keys, uint32_t *vals,
                                                            int64_t pair_cap, int gx) {
+  __shared__ uint32_t s_off[kScanItems + 1];
   const int64_t N = n_drawn(ctl, ncap);
   const int64_t base = (int64_t)blockIdx.x * kScanItems;
   if (base >= N) return;
-  // blocked arrangement: thread t owns items base + t*4 .. +3
   const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
   uint32_t cnt[kScanPer];
   uint64_t s = 0;
@@ -107,22 +112,34 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const Ctl *ctl, Spla
     s += cnt[k];
   }
   uint64_t tot;
-  uint64_t off = block_off[blockIdx.x] + block_excl_scan_1024(s, &tot);
+  uint64_t pre = block_excl_scan_1024(s, &tot);
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
-    if (!cnt[k]) continue;
-    const int64_t i = i0 + k;
+    s_off[threadIdx.x * kScanPer + k] = (uint32_t)pre;
+    pre += cnt[k];
+  }
+  if (threadIdx.x == 0) s_off[kScanItems] = (uint32_t)tot;
+  __syncthreads();
+  const uint64_t out0 = block_off[blockIdx.x];
+  const uint32_t T = (uint32_t)tot;
+  for (uint32_t j = threadIdx.x; j < T; j += kScanThreads) {
+    // last item with s_off[item] <= j (items with no pairs share offsets; the
+    // search lands on the last of them, which is the one owning pair j)
+    int lo = 0, hi = kScanItems - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int64_t i = base + lo;
+    const uint32_t q = j - s_off[lo];
     const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-    const uint32_t x0 = rx & 0xFFFFu, x1 = rx >> 16, y0 = ry & 0xFFFFu, y1 = ry >> 16;
-    const uint64_t dep = sp.depth[i];
-    for (uint32_t ty = y0; ty < y1; ++ty)
-      for (uint32_t tx = x0; tx < x1; ++tx) {
-        if ((int64_t)off < pair_cap) {
-          keys[off] = ((uint64_t)(ty * (uint32_t)gx + tx) << 32) | dep;
-          vals[off] = (uint32_t)i;
-        }
-        ++off;
-      }
+    const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+    const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
+    const uint64_t o = out0 + j;
+    if ((int64_t)o < pair_cap) {
+      keys[o] = ((uint64_t)tile << 32) | sp.depth[i];
+      vals[o] = (uint32_t)i;
+    }
   }
 }
 

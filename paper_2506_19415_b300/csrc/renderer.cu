@@ -57,6 +57,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.fb_pixels = (int64_t)((p->max_width + ds - 1) / ds) * ((p->max_height + ds - 1) / ds);
   d.ncap = P * s->page_size;
   d.pair_cap = p->max_pairs > 0 ? p->max_pairs : 8 * d.ncap;
+  if (p->max_pairs <= 0 && d.pair_cap < (int64_t(1) << 22)) d.pair_cap = int64_t(1) << 22;
   if (d.pair_cap > (int64_t(1) << 30) - 1) d.pair_cap = (int64_t(1) << 30) - 1;
   d.tile_cap = (int64_t)((p->max_width + 7) / 8) * ((p->max_height + 7) / 8);
   d.ntri = (int64_t)s->face_page.size();
@@ -64,6 +65,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.nlink = (int64_t)s->link_col.size();
   d.scan_blocks = (d.ncap + kScanItems - 1) / kScanItems;
   d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
+  d.raster_cap = d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20);
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
   return d;
@@ -116,6 +118,8 @@ Layout make_layout(const Dims &d) {
   L.splat_radius = take(4 * N);
   L.block_sums = take(8 * d.scan_blocks);
   L.offsets = take(0);
+  L.raster_queue = take(kRasterRecord * d.raster_cap);
+  L.raster_count = take(16);
   L.keys0 = take(8 * d.pair_cap);
   L.keys1 = take(8 * d.pair_cap);
   L.vals0 = take(4 * d.pair_cap);
@@ -287,13 +291,14 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     uint64_t *fb = r->at<uint64_t>(r->lay.fb);
     launch_feedback_clear(fb, npix, st);
     launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
-                           r->dims.ntri, c, ds, fb, st);
+                           r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
+                           r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap, st);
     launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
                            r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
     r->last_fb_pixels = npix;
     if (c.fy > fpx) fpx = c.fy;
   }
-  r->span_end(sp_fb, 3 * n_cams, st);
+  r->span_end(sp_fb, 4 * n_cams, st);
   r->f_px = fpx;
   r->state = 1;
   cudaError_t e = cudaGetLastError();

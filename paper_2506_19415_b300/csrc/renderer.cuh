@@ -42,12 +42,13 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
       face_page, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, block_sums, offsets, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+      splat_radius, block_sums, offsets, raster_queue, raster_count, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
 
 struct Dims {
   int64_t NP, P, Smax, fb_pixels, ncap, pair_cap, tile_cap, ntri, nvert, nlink, scan_blocks, lookback_words;
   int ukey_cap, free_cap;
+  int64_t raster_cap;
 };
 
 Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P);
@@ -62,8 +63,12 @@ constexpr int64_t kCopySeg = 65536;
 
 // ----- launchers (one per kernel family)
 void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
+// large triangles (more than 16 pixels) are queued: queue holds qcap records of
+// kRasterRecord bytes, qcount is one device word
+constexpr int64_t kRasterRecord = 64;
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
-                            const vm3dgs_camera &cam, int ds, uint64_t *fb, cudaStream_t st);
+                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
+                            uint32_t qcap, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
