@@ -45,6 +45,7 @@ def workload(name):
             build=dict(page_size=4096, paging="octree", lod_levels=3, lod_fanout=8, lo=(-4, -4, -4),
                        hi=(ext + 4, ext + 4, 88), voxel=2.0, kappa=0.5, link_samples=4, fp16=True),
             path=lambda n: scenegen.city_walk_path(n_frames=n),
+            train_path=lambda n, seed: scenegen.city_walk_path(n_frames=n, seed=seed),
             frames=1000, pool_bytes=2 << 30, lod=True, gaussians=50_000_000,
             sample=dict(extent=150.0, n=int(50_000_000 * (150.0 / ext) ** 2), n_boxes=max(1, int(5000 * (150.0 / ext) ** 2))))
     if name == "citypatch":
@@ -56,6 +57,7 @@ def workload(name):
             build=dict(page_size=4096, paging="octree", lod_levels=3, lod_fanout=8, lo=(-4, -4, -4),
                        hi=(ext + 4, ext + 4, 88), voxel=2.0, kappa=0.5, link_samples=4, fp16=True),
             path=lambda n: scenegen.city_walk_path(n_frames=n, n_boxes=1250, extent=ext),
+            train_path=lambda n, seed: scenegen.city_walk_path(n_frames=n, seed=seed, n_boxes=1250, extent=ext),
             frames=1000, pool_bytes=512 << 20, lod=True, gaussians=12_500_000, sample=None)
     if name == "blobs1m":
         return dict(
@@ -65,6 +67,7 @@ def workload(name):
             build=dict(page_size=4096, paging="octree", lod_levels=1, lo=(-5, -5, -5), hi=(55, 55, 55),
                        voxel=60.0 / 64, kappa=2.0, link_samples=4, fp16=True),
             path=lambda n: scenegen.orbit_fly_path(n_frames=n),
+            train_path=lambda n, seed: scenegen.random_fly_path(n, seed=seed, speed=0.5),
             frames=300, pool_bytes=64 << 20, lod=False, gaussians=1_000_000, sample=None)
     if name == "tiny":
         return dict(
@@ -142,7 +145,25 @@ def make_renderer(v, scene, W, fp16, width, height):
     return v.Renderer(scene, cfg, pool_bytes=W["pool_bytes"])
 
 
-def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None):
+def train_prefetcher(v, scene, W, width, height, n_paths=16, frames=60, steps=600):
+    """The learned prefetcher for this scene, trained on the renderer's own
+    feedback over seeded walks that do not include the benchmark path."""
+    from paper_2506_19415_b300 import prefetch_train as ptr
+    import torch
+    n_out = 4096 if scene.info.n_pages >= 4096 else max(16, (scene.info.n_pages + 15) // 16 * 16)
+    r = make_renderer(v, scene, W, True, width, height)
+    paths = [W["train_path"](frames, 3000 + k) for k in range(n_paths)]
+    t0 = time.time()
+    X, Y, M = ptr.make_dataset(v, r, paths, n_out, 12 + n_out // 16)
+    p = v.Prefetcher(v.MlpShape(n_in=12 + n_out // 16, n_hidden=256, n_out=n_out, max_batch=256, seed=5, lr=1e-3))
+    curve = ptr.train(p, X, Y, M, steps=steps, batch=256)
+    del X, Y, M, r
+    torch.cuda.empty_cache()
+    return p, {"train_paths": n_paths, "frames_per_path": frames, "steps": steps, "window_pages": n_out,
+               "loss_first": round(curve[0], 4), "loss_last": round(curve[-1], 4), "seconds": round(time.time() - t0, 1)}
+
+
+def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None, pf=None, pf_thr=0.0):
     import torch
     dev = torch.device("cuda")
     st = torch.cuda.current_stream()
@@ -156,6 +177,8 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
         r.render_feedback(c, st)
         r.update_residency(st, copy_stream)
         r.render(c, images, st)
+        if pf is not None:
+            v.vm3dgs_prefetch(r, pf, c[0], cams[(i - 1) % n], pf_thr, st, copy_stream)
         if e2e:
             host.copy_(images[0], non_blocking=True)
 
@@ -251,15 +274,24 @@ def gpu_main(args):
     plain = run_arm(v, rp, cams, args.warmup, args.steps, None, dist=dist)
     del rp
     torch.cuda.empty_cache()
-    # headline arm
+    # headline arm: fp16 pool, copies on a copy stream, learned prefetch
+    pf, pf_info = (None, None)
+    if W.get("train_path") is not None and not args.no_prefetch:
+        pf, pf_info = train_prefetcher(v, scene, W, width, height)
     rh = make_renderer(v, scene, W, True, width, height)
     copy_stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist)
+    head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist, pf=pf)
     clk = clocks.stop()
     # end to end through the public API: the rendered image returns to pinned host memory every frame
-    e2e = run_arm(v, rh, cams, 0, args.steps, copy_stream, e2e=True, dist=dist)
+    e2e = run_arm(v, rh, cams, 0, args.steps, copy_stream, e2e=True, dist=dist, pf=pf)
+    # same fp16 arm without the prefetcher, for its misses and copy stall
+    nopf = None
+    if pf is not None:
+        rn = make_renderer(v, scene, W, True, width, height)
+        nopf = run_arm(v, rn, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist)
+        del rn
 
     def agg(x):
         t = torch.tensor([x], dtype=torch.float64, device="cuda")
@@ -290,13 +322,13 @@ def gpu_main(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 math, f16 pool storage",
+        "dtype": "f32 math, f16 pool storage, bf16 prefetcher",
         "data": "synthetic (seeded scenegen), no dataset",
         "config": {"workload": W["name"], "config": args.config, "gaussians": W["gaussians"],
                    "pages": scene.info.n_pages, "resolution": [width, height], "frames_in_path": n_frames,
                    "pool_bytes": W["pool_bytes"], "staging_bytes": 40 * 2048 * 236,
                    "l2": "per-frame inputs (2 GiB pool, splat and pair buffers) exceed the 126 MB L2",
-                   "arm": "fp16 pool + copy stream", "parallelism": "replicas, one renderer per GPU"},
+                   "arm": "fp16 pool + copy stream + learned prefetch", "parallelism": "replicas, one renderer per GPU"},
         "plain_vm": {"value": round(fps_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain / args.steps, 4),
                      "arm": "fp32 pool, in-line copies",
                      "missing_per_frame": plain["stats"]["acc_missing"] / max(plain["stats"]["acc_frames"], 1)},
@@ -306,6 +338,15 @@ def gpu_main(args):
         "e2e": {"value": round(fps_e2e, 2), "unit": "frames/s", "h2d_bytes_per_step": int(76 + hs["acc_streamed_bytes"] / frames),
                 "d2h_bytes_per_step": 3 * width * height * 4},
         "gpu_launches": int(round(launches_per_frame * args.steps)),
+        "prefetcher": None if pf is None else dict(pf_info, **{
+            "with": {"missing_per_frame": hs["acc_missing"] / frames,
+                     "stall_ms_per_frame": head["stage"][0][v.STAGES.index("stream")] / frames,
+                     "prefetched_pages_per_frame": hs["acc_prefetched_pages"] / frames,
+                     "prefetch_hits_per_frame": hs["acc_prefetch_hits"] / frames,
+                     "ms_per_step": round(ms_head / args.steps, 4)},
+            "without": {"missing_per_frame": nopf["stats"]["acc_missing"] / max(nopf["stats"]["acc_frames"], 1),
+                        "stall_ms_per_frame": nopf["stage"][0][v.STAGES.index("stream")] / max(nopf["stats"]["acc_frames"], 1),
+                        "ms_per_step": round(nopf["ms"] / args.steps, 4)}}),
         "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
         "roofline_detail": rl,
         "clocks": clk,
@@ -387,6 +428,7 @@ def main():
     ap.add_argument("--config", default="city50m")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-prefetch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -114,6 +114,8 @@ typedef struct {
   /* running sums since the renderer was created or the sums were reset */
   int64_t acc_frames, acc_views, acc_pairs, acc_drawn_gaussians, acc_streamed_bytes, acc_streamed_pages,
       acc_missing, acc_requested;
+  int64_t acc_prefetched_pages, acc_prefetched_bytes, acc_prefetch_hits;  /* hits: requested pages found resident
+                                                                            because a prefetch brought them */
 } vm3dgs_stats;
 
 typedef struct {
@@ -247,8 +249,8 @@ int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *host_dst, int64_t 
  * bracketed by CUDA events on the stream it runs on, and its kernel launches
  * are counted.  vm3dgs_timing_read synchronises the device, adds the elapsed
  * milliseconds and launch counts of each stage since the last read into
- * ms_total[stage] and launches[stage] (arrays of n entries, n <= 8), and
- * forgets them.  Stages: */
+ * ms_total[stage] and launches[stage] (arrays of n entries), and
+ * forgets them (n <= 9).  Stages: */
 enum {
   VM3DGS_STAGE_FEEDBACK = 0,  /* visibility buffer raster + reduction */
   VM3DGS_STAGE_RESIDENCY = 1, /* request compaction, LOD, page table, controller */
@@ -258,10 +260,67 @@ enum {
   VM3DGS_STAGE_SORT = 5,      /* radix sort of the pairs */
   VM3DGS_STAGE_RANGES = 6,    /* tile ranges */
   VM3DGS_STAGE_BLEND = 7,     /* per-tile blending */
-  VM3DGS_N_STAGES = 8
+  VM3DGS_STAGE_PREFETCH = 8,  /* prefetch input, network, placement and copies */
+  VM3DGS_N_STAGES = 9
 };
 int vm3dgs_timing_enable(vm3dgs_renderer *r, int32_t on);
 int vm3dgs_timing_read(vm3dgs_renderer *r, double *ms_total, int64_t *launches, int32_t n);
+
+/* ------------------------------------------------------------ prefetcher
+ * A learned page prefetcher (the paper has none; its limitations, Sec. 4.3,
+ * ask to copy earlier and with priorities).  Network: n_in inputs -> ReLU
+ * n_hidden -> ReLU n_hidden -> n_out logits, one per page of a window of
+ * n_out consecutive pages; bf16 weights and activations on the tensor cores,
+ * FP32 accumulation, FP32 master weights and Adam state.  Device memory is
+ * the caller's (vm3dgs_prefetcher_bytes). */
+typedef struct vm3dgs_prefetcher vm3dgs_prefetcher;
+typedef struct {
+  int32_t n_in, n_hidden, n_out, max_batch;
+  uint64_t seed;           /* weights U(-1/sqrt(fan_in), +1/sqrt(fan_in)) from SplitMix64(seed ^ index); biases 0 */
+  float lr, beta1, beta2, eps;  /* Adam */
+} vm3dgs_mlp_config;
+enum { VM3DGS_PARAMS_GET = 0, VM3DGS_PARAMS_SET = 1, VM3DGS_PARAMS_GRAD = 2 };
+int vm3dgs_prefetcher_bytes(const vm3dgs_mlp_config *c, int64_t *out);
+int vm3dgs_prefetcher_create(const vm3dgs_mlp_config *c, void *dev, int64_t bytes, void *stream,
+                             vm3dgs_prefetcher **out);
+void vm3dgs_prefetcher_destroy(vm3dgs_prefetcher *p);
+/* logits_dev[batch][n_out] = net(x_dev[batch][n_in]) (device pointers, fp32) */
+int vm3dgs_prefetcher_forward(vm3dgs_prefetcher *p, const float *x_dev, int32_t batch, float *logits_dev, void *stream);
+/* One Adam step on mean binary cross-entropy with logits over the entries
+ * where mask = 1 (mask_sum = number of such entries); *loss_dev (optional)
+ * receives the loss before the step.  Gradients stay readable until the next
+ * step (VM3DGS_PARAMS_GRAD).  With lr = 0 no update is made. */
+int vm3dgs_prefetcher_train_step(vm3dgs_prefetcher *p, const float *x_dev, const float *target_dev,
+                                 const float *mask_dev, int32_t batch, float mask_sum, float *loss_dev, void *stream);
+/* Host exchange of the packed fp32 parameters W1[n_in][h] b1 W2[h][h] b2
+ * W3[h][n_out] b3 (GET / SET, SET also resets Adam) or of the last gradients
+ * (GRAD).  n must equal the parameter count.  Synchronises stream. */
+int vm3dgs_prefetcher_params(vm3dgs_prefetcher *p, int32_t what, float *host, int64_t n, void *stream);
+
+/* Network input for the current frame, on the device: x_dev[0..11] = camera
+ * position relative to the scene centre in units of the scene half-extent,
+ * forward axis, velocity (position change since prev, in 1% of the half-
+ * extent), change of the forward axis times 10; x_dev[12 + b] = fraction of
+ * the 16 pages of window bin b requested by the last vm3dgs_render_feedback.
+ * The window is the n_out pages centred, in page order, on the page whose
+ * centroid is nearest the camera; its first page goes to *base_dev (device
+ * int32, may be null).  prev may equal cam (no motion). */
+int vm3dgs_prefetch_features(vm3dgs_renderer *r, int32_t n_out, const vm3dgs_camera *cam, const vm3dgs_camera *prev,
+                             float *x_dev, int32_t *base_dev, void *stream);
+/* Training targets from the last vm3dgs_render_feedback for a window:
+ * y_dev[j] = 1 if page base + j was requested, else 0; mask_dev[j] = 1 if
+ * base + j is a page of the scene, else 0 (base read from base_dev). */
+int vm3dgs_prefetch_labels(vm3dgs_renderer *r, int32_t n_out, const int32_t *base_dev, float *y_dev, float *mask_dev,
+                           void *stream);
+/* Prefetch for the next frame, after vm3dgs_render of this one: builds the
+ * input as vm3dgs_prefetch_features does, runs the network, and spends the
+ * staging budget this frame left unused on the window pages whose logit
+ * exceeds threshold, highest first, that are neither requested this frame
+ * nor resident at the level the screen-space-error rule gives for their
+ * distance: they take entries not used this frame, least recently used first,
+ * and are copied on copy_stream (the next vm3dgs_render waits for them). */
+int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const vm3dgs_camera *cam, const vm3dgs_camera *prev,
+                    float threshold, void *stream, void *copy_stream);
 
 const char *vm3dgs_last_error(void);
 const char *vm3dgs_version(void);

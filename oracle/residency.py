@@ -196,3 +196,93 @@ def control(pt: PageTable, usage, draw):
             pt.last_dir = d
             pt.last_move = pt.frame
     pt.frame += 1
+
+
+# --------------------------------------------------------------------------- prefetch
+def page_centroids(scene):
+    """Per page: mean of the level-0 means (FP64, stored fp32) and a radius =
+    max over its Gaussians of distance to the mean + 3 x largest scale."""
+    L0 = scene.levels[0]
+    out = np.zeros((scene.n_pages, 4), np.float32)
+    for p in range(scene.n_pages):
+        n = int(scene.count[p])
+        pos = L0["pos"][p, :n].astype(np.float64)
+        c = pos.mean(0) if n else np.zeros(3)
+        r = 0.0
+        if n:
+            d = np.sqrt(((pos - c) ** 2).sum(1)) + 3.0 * L0["scale"][p, :n].astype(np.float64).max(1)
+            r = d.max()
+        out[p, :3] = c
+        out[p, 3] = r
+    return out
+
+
+def prefetch(pt: PageTable, logits, base, threshold, req, err, centroid, campos, f_px, budget_left, frame_now):
+    """Placement of predicted pages for the next frame (sequential definition).
+
+    Candidates: window pages p = base + j (j < len(logits), p < n_pages) with
+    logit > threshold, not requested this frame, not resident at their level
+    (SSE rule with d = max(|campos - centroid| - radius, 0.2) when LOD is on).
+    Order (logit desc, level asc, page asc); the longest prefix fitting
+    budget_left is admitted; per level in ascending order they take fresh
+    entries from those not used this frame (last used < frame_now), least
+    recently used first, packed fanout^l per entry.  Returns the copy list
+    [(p, l, e, s)] in admitted order."""
+    rp = pt.rp
+    P = rp.n_entries
+    n_vp = len(req)
+    resident = set()
+    for e in range(P):
+        if pt.lod[e] < 0:
+            continue
+        for s in range(rp.fanout ** pt.lod[e]):
+            if pt.slot[e, s] >= 0:
+                resident.add((int(pt.slot[e, s]), int(pt.lod[e])))
+    F = np.float32
+    cands = []
+    for j in range(len(logits)):
+        p = base + j
+        if p >= n_vp:
+            continue
+        lev = 0
+        if rp.lod and rp.levels > 1:
+            c = centroid[p]
+            dx, dy, dz = F(c[0] - F(campos[0])), F(c[1] - F(campos[1])), F(c[2] - F(campos[2]))
+            d = max(F(np.sqrt(F(F(F(dx * dx) + F(dy * dy)) + F(dz * dz))) - c[3]), F(0.2))
+            for l in range(rp.levels - 1, 0, -1):
+                if F(F(F(f_px) * err[p, l]) / d) <= pt.tau:
+                    lev = l
+                    break
+        if F(logits[j]) > F(threshold) and req[p] == 0 and (p, lev) not in resident:
+            cands.append((-float(logits[j]), lev, p))
+    cands.sort()
+    adm, cum = [], 0
+    for c in cands:
+        cost = rp.page_bytes(c[1])
+        if cum + cost > budget_left:
+            break
+        cum += cost
+        adm.append(c)
+    free = sorted([e for e in range(P) if pt.last_used[e] < frame_now], key=lambda e: (pt.last_used[e], e))
+    n_l = [sum(1 for c in adm if c[1] == l) for l in range(rp.levels)]
+    fresh_start, acc = [], 0
+    for l in range(rp.levels):
+        fresh_start.append(acc)
+        acc += (n_l[l] + rp.fanout ** l - 1) // rp.fanout ** l
+    for k in range(min(acc, len(free))):
+        e = free[k]
+        l = max(i for i in range(rp.levels) if fresh_start[i] <= k and (i + 1 == rp.levels or fresh_start[i + 1] > k))
+        pt.slot[e, :] = -1
+        pt.lod[e] = l
+        pt.last_used[e] = frame_now
+    copies, rank = [], [0] * rp.levels
+    for (_, l, p) in adm:
+        S = rp.fanout ** l
+        k = fresh_start[l] + rank[l] // S
+        s = rank[l] % S
+        rank[l] += 1
+        if k < len(free):
+            e = free[k]
+            pt.slot[e, s] = p
+            copies.append((p, l, e, s))
+    return copies

@@ -64,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("drawn_gaussians", c_i64), ("pairs", c_i64), ("usage", c_f), ("tau", c_f), ("status", c_i32),
                 ("acc_frames", c_i64), ("acc_views", c_i64), ("acc_pairs", c_i64), ("acc_drawn_gaussians", c_i64),
                 ("acc_streamed_bytes", c_i64), ("acc_streamed_pages", c_i64), ("acc_missing", c_i64),
-                ("acc_requested", c_i64)]
+                ("acc_requested", c_i64), ("acc_prefetched_pages", c_i64), ("acc_prefetched_bytes", c_i64),
+                ("acc_prefetch_hits", c_i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +83,11 @@ class SceneDesc(ctypes.Structure):
                 ("rot", ctypes.POINTER(c_p)), ("opacity", ctypes.POINTER(c_p)), ("sh", ctypes.POINTER(c_p)),
                 ("err", c_p), ("count", c_p), ("n_verts", c_i64), ("n_tris", c_i64), ("n_links", c_i64),
                 ("verts", c_p), ("tris", c_p), ("face_page", c_p), ("link_ptr", c_p), ("link_col", c_p)]
+
+
+class MlpConfig(ctypes.Structure):
+    _fields_ = [("n_in", c_i32), ("n_hidden", c_i32), ("n_out", c_i32), ("max_batch", c_i32), ("seed", c_u64),
+                ("lr", c_f), ("beta1", c_f), ("beta2", c_f), ("eps", c_f)]
 
 
 _SIGS = {
@@ -103,6 +109,15 @@ _SIGS = {
     "vm3dgs_debug_read": [c_p, c_i32, c_p, c_i64, ctypes.POINTER(c_i64), c_p],
     "vm3dgs_timing_enable": [c_p, c_i32],
     "vm3dgs_timing_read": [c_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_i64), c_i32],
+    "vm3dgs_prefetcher_bytes": [ctypes.POINTER(MlpConfig), ctypes.POINTER(c_i64)],
+    "vm3dgs_prefetcher_create": [ctypes.POINTER(MlpConfig), c_p, c_i64, c_p, ctypes.POINTER(c_p)],
+    "vm3dgs_prefetcher_destroy": [c_p],
+    "vm3dgs_prefetcher_forward": [c_p, c_p, c_i32, c_p, c_p],
+    "vm3dgs_prefetcher_train_step": [c_p, c_p, c_p, c_p, c_i32, c_f, c_p, c_p],
+    "vm3dgs_prefetcher_params": [c_p, c_i32, c_p, c_i64, c_p],
+    "vm3dgs_prefetch_features": [c_p, c_i32, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_p, c_p, c_p],
+    "vm3dgs_prefetch_labels": [c_p, c_i32, c_p, c_p, c_p, c_p],
+    "vm3dgs_prefetch": [c_p, c_p, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_f, c_p, c_p],
     "vm3dgs_last_error": [],
     "vm3dgs_version": [],
 }
@@ -122,7 +137,7 @@ SCENE_PAGE_COUNT, SCENE_PAGE_SRC, SCENE_PAGES, SCENE_PAGES16, SCENE_ERR, SCENE_V
  DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL) = range(20)
 
 
-STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend")
+STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend", "prefetch")
 N_STAGES = len(STAGES)
 
 
@@ -409,3 +424,101 @@ def vm3dgs_get_stats(r: Renderer, stream=None):
 
 def vm3dgs_debug_read(r: Renderer, what, dtype=np.uint8, stream=None):
     return r.debug(what, dtype, stream)
+
+
+# --------------------------------------------------------------------------- prefetcher
+PARAMS_GET, PARAMS_SET, PARAMS_GRAD = 0, 1, 2
+
+
+@dataclass
+class MlpShape:
+    n_in: int = 12 + 256
+    n_hidden: int = 256
+    n_out: int = 4096
+    max_batch: int = 256
+    seed: int = 5
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def struct(self) -> MlpConfig:
+        return MlpConfig(self.n_in, self.n_hidden, self.n_out, self.max_batch, self.seed, self.lr, self.beta1,
+                         self.beta2, self.eps)
+
+
+class Prefetcher:
+    """The learned page prefetcher over a torch-allocated device buffer."""
+
+    def __init__(self, shape: MlpShape = MlpShape(), device="cuda"):
+        import torch
+        self.shape = shape
+        self.cfg = shape.struct()
+        n = c_i64()
+        _check(_lib.vm3dgs_prefetcher_bytes(ctypes.byref(self.cfg), ctypes.byref(n)))
+        self.mem = torch.empty(n.value, dtype=torch.uint8, device=device)
+        self.h = c_p()
+        _check(_lib.vm3dgs_prefetcher_create(ctypes.byref(self.cfg), c_p(self.mem.data_ptr()), n.value,
+                                             _stream_ptr(None), ctypes.byref(self.h)))
+        I, H, O = shape.n_in, shape.n_hidden, shape.n_out
+        self.sizes = [("W1", (I, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, O)), ("b3", (O,))]
+        self.n_params = sum(int(np.prod(sz)) for _, sz in self.sizes)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.vm3dgs_prefetcher_destroy(self.h)
+            self.h = None
+
+    def _unpack(self, flat):
+        out, o = {}, 0
+        for k, sz in self.sizes:
+            n = int(np.prod(sz))
+            out[k] = flat[o:o + n].reshape(sz)
+            o += n
+        return out
+
+    def params(self):
+        buf = np.empty(self.n_params, np.float32)
+        _check(_lib.vm3dgs_prefetcher_params(self.h, PARAMS_GET, _ptr(buf), self.n_params, _stream_ptr(None)))
+        return self._unpack(buf)
+
+    def grads(self):
+        buf = np.empty(self.n_params, np.float32)
+        _check(_lib.vm3dgs_prefetcher_params(self.h, PARAMS_GRAD, _ptr(buf), self.n_params, _stream_ptr(None)))
+        return self._unpack(buf)
+
+    def set_params(self, P):
+        flat = np.concatenate([np.asarray(P[k], np.float32).reshape(-1) for k, _ in self.sizes])
+        _check(_lib.vm3dgs_prefetcher_params(self.h, PARAMS_SET, _ptr(flat), self.n_params, _stream_ptr(None)))
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((x.shape[0], self.shape.n_out), dtype=torch.float32, device=x.device)
+        _check(_lib.vm3dgs_prefetcher_forward(self.h, c_p(x.data_ptr()), x.shape[0], c_p(out.data_ptr()),
+                                              _stream_ptr(stream)))
+        return out
+
+    def train_step(self, x, y, mask, loss_out=None, stream=None):
+        ms = float(mask.sum().item()) if not hasattr(self, "_fixed_mask_sum") else self._fixed_mask_sum
+        _check(_lib.vm3dgs_prefetcher_train_step(self.h, c_p(x.data_ptr()), c_p(y.data_ptr()), c_p(mask.data_ptr()),
+                                                 x.shape[0], ms, c_p(loss_out.data_ptr()) if loss_out is not None else None,
+                                                 _stream_ptr(stream)))
+
+
+def vm3dgs_prefetch_features(r: "Renderer", n_out, cam, prev, x_out, base_out=None, stream=None):
+    c, pc = camera_struct(cam), camera_struct(prev)
+    _check(_lib.vm3dgs_prefetch_features(r.h, n_out, ctypes.byref(c), ctypes.byref(pc), c_p(x_out.data_ptr()),
+                                         c_p(base_out.data_ptr()) if base_out is not None else None,
+                                         _stream_ptr(stream)))
+
+
+def vm3dgs_prefetch_labels(r: "Renderer", n_out, base_dev, y_out, mask_out, stream=None):
+    _check(_lib.vm3dgs_prefetch_labels(r.h, n_out, c_p(base_dev.data_ptr()), c_p(y_out.data_ptr()),
+                                       c_p(mask_out.data_ptr()), _stream_ptr(stream)))
+
+
+def vm3dgs_prefetch(r: "Renderer", p: Prefetcher, cam, prev, threshold=0.0, stream=None, copy_stream=None):
+    c, pc = camera_struct(cam), camera_struct(prev)
+    _check(_lib.vm3dgs_prefetch(r.h, p.h, ctypes.byref(c), ctypes.byref(pc), float(threshold), _stream_ptr(stream),
+                                _stream_ptr(copy_stream) if copy_stream is not None else None))

@@ -723,6 +723,7 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
       S->face_page.push_back(sp[si][qd]);
     }
   }
+  finish_scene(S);
   *out = S;
   return VM3DGS_OK;
 }

@@ -73,6 +73,8 @@ __device__ __forceinline__ void edges(const Tri &t, int64_t *dxe, int64_t *dye, 
 // calling thread, larger ones go to the queue for whole-CTA rasterisation.
 __device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
                           uint64_t *fb, Tri *queue, uint32_t *qcount, uint32_t qcap) {
+  // queue layout: medium triangles (17..1024 pixels) from the front, huge ones
+  // (more) from the back; qcount[0], qcount[1] count them
   int64_t X[3], Y[3];
   float Z[3];
 #pragma unroll
@@ -108,8 +110,9 @@ __device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, flo
   t.i0 = (int32_t)i0; t.i1 = (int32_t)i1; t.j0 = (int32_t)j0; t.j1 = (int32_t)j1;
   const int64_t bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
   if (npx > 16) {
-    const uint32_t q = atomicAdd(qcount, 1u);
-    if (q < qcap) { queue[q] = t; return; }
+    const bool huge = npx > 1024;
+    const uint32_t q = atomicAdd(qcount + (huge ? 1 : 0), 1u);
+    if (q < qcap / 2) { queue[huge ? qcap - 1 - q : q] = t; return; }
   }
   int64_t dxe[3], dye[3];
   bool own[3];
@@ -126,6 +129,9 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
   const float zn = 0.2f;
+  // side planes of the buffer widened by 2 pixels, as x / z (resp. y / z) limits
+  const float kr = ((float)Wf + 2.0f - cxf) / fxf, kl = (-2.0f - cxf) / fxf;
+  const float kb = ((float)Hf + 2.0f - cyf) / fyf, kt = (-2.0f - cyf) / fyf;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
     V3 c[3];
@@ -138,6 +144,16 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
     for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
     if (nin == 0) continue;
     if (nin == 3) {
+      // whole triangle more than 2 pixels beyond one side of the buffer: no pixel centre is covered
+      bool out = true;
+      for (int k = 0; k < 3 && out; ++k) out = c[k].x > kr * c[k].z;
+      bool o2 = true;
+      for (int k = 0; k < 3 && o2; ++k) o2 = c[k].x < kl * c[k].z;
+      bool o3 = true;
+      for (int k = 0; k < 3 && o3; ++k) o3 = c[k].y > kb * c[k].z;
+      bool o4 = true;
+      for (int k = 0; k < 3 && o4; ++k) o4 = c[k].y < kt * c[k].z;
+      if (out || o2 || o3 || o4) continue;
       setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
       continue;
     }
@@ -164,12 +180,29 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
   }
 }
 
-// one CTA per queued triangle at a time, threads over its pixel box
-__global__ void __launch_bounds__(256) raster_large_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
-                                                           int Wf, uint64_t *fb) {
-  const uint32_t n = min(*qcount, qcap);
-  for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+// medium triangles: one warp each, lanes over the pixel box
+__global__ void __launch_bounds__(256) raster_medium_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
+                                                            int Wf, uint64_t *fb) {
+  const uint32_t n = min(qcount[0], qcap / 2);
+  const int lane = threadIdx.x & 31;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t q = w0; q < n; q += nw) {
     const Tri t = queue[q];
+    int64_t dxe[3], dye[3];
+    bool own[3];
+    float farea;
+    edges(t, dxe, dye, own, &farea);
+    const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
+    for (int64_t p = lane; p < npx; p += 32) shade(t, dxe, dye, own, farea, t.i0 + p % bw, t.j0 + p / bw, Wf, fb);
+  }
+}
+
+// huge triangles: one CTA each, threads over the pixel box
+__global__ void __launch_bounds__(256) raster_huge_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
+                                                          int Wf, uint64_t *fb) {
+  const uint32_t n = min(qcount[1], qcap / 2);
+  for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+    const Tri t = queue[qcap - 1 - q];
     int64_t dxe[3], dye[3];
     bool own[3];
     float farea;
@@ -225,13 +258,14 @@ void launch_feedback_raster(const float *verts, const int32_t *tris, const int32
                             const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
                             uint32_t qcap, cudaStream_t st) {
   if (ntri <= 0) return;
-  cudaMemsetAsync(qcount, 0, sizeof(uint32_t), st);
+  cudaMemsetAsync(qcount, 0, 2 * sizeof(uint32_t), st);
   int64_t blocks = (ntri + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
   raster_setup_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, face_page, ntri, cam, ds, fb,
                                                         reinterpret_cast<Tri *>(queue), qcount, qcap);
   const int Wf = (cam.width + ds - 1) / ds;
-  raster_large_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
+  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
+  raster_huge_kernel<<<148 * 2, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
 }
 
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,

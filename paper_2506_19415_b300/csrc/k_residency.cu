@@ -64,7 +64,52 @@ __device__ int64_t bscan(int64_t v, int64_t *total, ScanSmem &sm) {
   return pre;
 }
 
-__device__ void bitonic(uint64_t *a, int n_pow2) {
+// N exclusive block scans at once (one set of barriers)
+template <int N>
+struct MScan {
+  int64_t warp[N][32];
+};
+template <int N>
+__device__ void bscan_n(const int64_t *v, int64_t *pre, int64_t *total, MScan<N> &sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    x[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x[q], o);
+      if (lane >= o) x[q] += y;
+    }
+    if (lane == 31) sm.warp[q][warp] = x[q];
+  }
+  __syncthreads();
+  if (warp < N) {
+    int64_t t = sm.warp[warp][lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sm.warp[warp][lane] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    pre[q] = (warp ? sm.warp[q][warp - 1] : 0) + x[q] - v[q];
+    total[q] = sm.warp[q][31];
+  }
+  __syncthreads();
+}
+
+// bitonic sort of n_pow2 keys, staged through shared memory when they fit
+constexpr int kSmemKeys = 16384;
+__device__ void bitonic(uint64_t *g, int n_pow2, uint64_t *sh) {
+  uint64_t *a = n_pow2 <= kSmemKeys ? sh : g;
+  if (a == sh) {
+    for (int i = threadIdx.x; i < n_pow2; i += RT) sh[i] = g[i];
+    __syncthreads();
+  }
   for (int k = 2; k <= n_pow2; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < n_pow2; i += RT) {
@@ -77,6 +122,10 @@ __device__ void bitonic(uint64_t *a, int n_pow2) {
       }
       __syncthreads();
     }
+  if (a == sh) {
+    for (int i = threadIdx.x; i < n_pow2; i += RT) g[i] = sh[i];
+    __syncthreads();
+  }
 }
 
 __device__ int pow2_at_least(int n) {
@@ -86,15 +135,18 @@ __device__ int pow2_at_least(int n) {
 }
 
 __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
+  extern __shared__ uint64_t s_keys[];
   __shared__ ScanSmem sm;
+  __shared__ MScan<4> sm4;
   __shared__ int m_l[kMaxLevels], S_l[kMaxLevels];
   __shared__ int n_lvl[kMaxLevels], open_cnt[kMaxLevels], open_base[kMaxLevels], fresh_start[kMaxLevels + 1];
-  __shared__ int s_nfree;
+  __shared__ int s_nfree, s_hits;
   Ctl *ctl = a.ctl;
   const int tid = threadIdx.x;
   const int NP = a.NP, P = a.P, Smax = a.Smax, L = a.levels;
   const int frame = ctl->frame;
   const float tau = ctl->tau;
+  if (tid == 0) s_hits = 0;
   if (tid < kMaxLevels) {
     int m = a.page_size, S = 1;
     for (int l = 0; l < tid; ++l) { m /= a.fanout; S *= a.fanout; }
@@ -110,12 +162,12 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     const uint32_t r = p < NP ? a.req[p] : 0u;
     const int dflag = (p < NP && r != 0u) ? (int)a.direct[p] : 0;
     if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; }
-    const int64_t pos = bscan(r != 0u, &tot, sm);
-    if (r != 0u) a.requests[nreq + pos] = make_int4(p, (int)r, dflag, 0);
-    nreq += tot;
-    int64_t t2;
-    bscan(dflag, &t2, sm);
-    ndir += t2;
+    const int64_t v2[2] = {r != 0u, dflag};
+    int64_t pre2[2], tot2[2];
+    bscan_n<2>(v2, pre2, tot2, *reinterpret_cast<MScan<2> *>(&sm4));
+    if (r != 0u) a.requests[nreq + pre2[0]] = make_int4(p, (int)r, dflag, 0);
+    nreq += tot2[0];
+    ndir += tot2[1];
   }
   __syncthreads();
   // ---- 2. LOD choice
@@ -143,7 +195,12 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
         const int p = a.pt_slot[k];
         const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
         a.required[k] = (uint8_t)r;
-        if (r) { a.matched[p] = 1; a.draw_info[p] = (int)k; any = 1; }
+        if (r) {
+          a.matched[p] = 1;
+          a.draw_info[p] = (int)k;
+          any = 1;
+          if (a.pf_flag[k]) { atomicAdd(&s_hits, 1); a.pf_flag[k] = 0; }
+        }
       }
     }
     a.any_req[e] = (uint8_t)any;
@@ -168,7 +225,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   if (sort_ok) {
     for (int i = (int)nu + tid; i < nu_pow; i += RT) a.ukeys[i] = ~0ull;
     __syncthreads();
-    bitonic(a.ukeys, nu_pow);
+    bitonic(a.ukeys, nu_pow, s_keys);
   } else if (tid == 0) {
     atomicCAS(&ctl->status, 0, VM3DGS_E_CAPACITY);
   }
@@ -184,9 +241,8 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     }
     const int64_t pre = bscan(cost, &tot, sm);
     const int ok = (i < nu && cum + pre + cost <= a.budget) ? 1 : 0;
-    int64_t t2;
-    bscan(ok, &t2, sm);
-    nadm += t2;
+    // admitted entries form a prefix: count them with a block reduction
+    nadm += __syncthreads_count(ok);
     cum += tot;
   }
   // ---- 6. per-level rank of the admitted requests
@@ -213,15 +269,15 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
         elig = 1;
         for (int s = 0; s < S_l[l]; ++s) avail += a.required[(int64_t)e * Smax + s] ? 0 : 1;
       }
-      int64_t te, ts;
-      const int64_t pe = bscan(elig, &te, sm);
-      const int64_t ps = bscan(avail, &ts, sm);
+      const int64_t v2[2] = {elig, avail};
+      int64_t pre2[2], tot2[2];
+      bscan_n<2>(v2, pre2, tot2, *reinterpret_cast<MScan<2> *>(&sm4));
       if (elig) {
-        a.open_list[obase + cnt_e + pe] = e;
-        a.open_off[obase + cnt_e + pe] = (int)(cnt_s + ps);
+        a.open_list[obase + cnt_e + pre2[0]] = e;
+        a.open_off[obase + cnt_e + pre2[0]] = (int)(cnt_s + pre2[1]);
       }
-      cnt_e += te;
-      cnt_s += ts;
+      cnt_e += tot2[0];
+      cnt_s += tot2[1];
     }
     if (tid == 0) { open_base[l] = (int)obase; open_cnt[l] = (int)cnt_s; }
     // sentinel count of eligible entries stored after the list
@@ -229,22 +285,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     if (tid == 0) a.open_off[P + l] = (int)cnt_e;
   }
   __syncthreads();
-  // ---- 8. free entries, least recently used first
-  int64_t nfree = 0;
-  for (int c = 0; c < P; c += RT) {
-    const int e = c + tid;
-    const int f = (e < P && !a.any_req[e]) ? 1 : 0;
-    const int64_t pos = bscan(f, &tot, sm);
-    if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
-    nfree += tot;
-  }
-  __syncthreads();
-  {
-    const int fp = pow2_at_least((int)nfree);
-    for (int i = (int)nfree + tid; i < fp; i += RT) a.free_keys[i] = ~0ull;
-    __syncthreads();
-    bitonic(a.free_keys, fp);
-  }
+  // ---- 8. fresh entries needed per level; free entries, least recently used first
   if (tid == 0) {
     int acc = 0;
     for (int l = 0; l < L; ++l) {
@@ -253,8 +294,23 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       acc += (rest + S_l[l] - 1) / S_l[l];
     }
     fresh_start[L] = acc;
-    s_nfree = (int)nfree;
   }
+  __syncthreads();
+  int64_t nfree = 0;
+  if (fresh_start[L] > 0) {
+    for (int c = 0; c < P; c += RT) {
+      const int e = c + tid;
+      const int f = (e < P && !a.any_req[e]) ? 1 : 0;
+      const int64_t pos = bscan(f, &tot, sm);
+      if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
+      nfree += tot;
+    }
+    const int fp = pow2_at_least((int)nfree);
+    for (int i = (int)nfree + tid; i < fp; i += RT) a.free_keys[i] = ~0ull;
+    __syncthreads();
+    bitonic(a.free_keys, fp, s_keys);
+  }
+  if (tid == 0) s_nfree = (int)nfree;
   __syncthreads();
   // ---- 9. initialise the fresh entries
   {
@@ -263,6 +319,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       const int k = (int)(x / Smax), s = (int)(x % Smax);
       const int e = (int)(a.free_keys[k] & 0xFFFFFFFFull);
       a.pt_slot[(int64_t)e * Smax + s] = -1;
+      a.pf_flag[(int64_t)e * Smax + s] = 0;
       if (s == 0) {
         int l = 0;
         while (l + 1 < L && fresh_start[l + 1] <= k) ++l;
@@ -302,6 +359,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     }
     if (slot >= 0) {
       a.pt_slot[slot] = p;
+      a.pf_flag[slot] = 0;
       a.draw_info[p] = (int)slot;
     } else {
       a.matched[p] = 2;
@@ -321,18 +379,17 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       bytes = f ? (int64_t)m_l[l] * a.rec : 0;
       segs = (bytes + kCopySeg - 1) / kCopySeg;
     }
-    int64_t ts, tb;
-    const int64_t pos = bscan(f, &tot, sm);
-    const int64_t spos = bscan(segs, &ts, sm);
-    bscan(bytes, &tb, sm);
+    const int64_t v3[3] = {f, segs, bytes};
+    int64_t pre3[3], tot3[3];
+    bscan_n<3>(v3, pre3, tot3, *reinterpret_cast<MScan<3> *>(&sm4));
     if (f) {
       const int slot = a.draw_info[p];
-      a.copies[ncopy + pos] = make_int4(p, l, slot / Smax, slot % Smax);
-      a.copy_seg[ncopy + pos] = nseg + spos;
+      a.copies[ncopy + pre3[0]] = make_int4(p, l, slot / Smax, slot % Smax);
+      a.copy_seg[ncopy + pre3[0]] = nseg + pre3[1];
     }
-    ncopy += tot;
-    nseg += ts;
-    sbytes += tb;
+    ncopy += tot3[0];
+    nseg += tot3[1];
+    sbytes += tot3[2];
   }
   if (tid == 0) a.copy_seg[ncopy] = nseg;
   // non-admitted requests are missing too
@@ -349,12 +406,12 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       fd = a.draw_info[p] >= 0 && !fm;
       if (fd) { g = m_l[a.reqlev[p]]; fl = a.reqlev[p] > 0; }
     }
-    int64_t tm, td, tg, tl;
-    const int64_t pm = bscan(fm, &tm, sm);
-    const int64_t pd = bscan(fd, &td, sm);
-    const int64_t pg = bscan(g, &tg, sm);
-    bscan(fl, &tl, sm);
-    nlod += tl;
+    const int64_t v4[4] = {fm, fd, g, fl};
+    int64_t pre4[4], tot4[4];
+    bscan_n<4>(v4, pre4, tot4, sm4);
+    const int64_t pm = pre4[0], pd = pre4[1], pg = pre4[2];
+    const int64_t tm = tot4[0], td = tot4[1], tg = tot4[2];
+    nlod += tot4[3];
     if (fm) a.missing[nmiss + pm] = p;
     if (fd) {
       const int slot = a.draw_info[p];
@@ -385,6 +442,8 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     ctl->acc_streamed_pages += ncopy;
     ctl->acc_missing += nmiss;
     ctl->acc_requested += nreq;
+    ctl->n_hits = s_hits;
+    ctl->acc_prefetch_hits += s_hits;
     const float usage = P > 0 ? (float)gsum / (float)((int64_t)P * a.page_size) : 0.0f;
     ctl->usage = usage;
     // ---- 13. LOD controller
@@ -411,6 +470,14 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
 
 }  // namespace
 
-void launch_residency(const ResidencyArgs &a, cudaStream_t st) { residency_kernel<<<1, RT, 0, st>>>(a); }
+void launch_residency(const ResidencyArgs &a, cudaStream_t st) {
+  static bool attr = false;
+  const int smem = kSmemKeys * (int)sizeof(uint64_t);
+  if (!attr) {
+    cudaFuncSetAttribute(residency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  residency_kernel<<<1, RT, smem, st>>>(a);
+}
 
 }  // namespace vm

@@ -91,15 +91,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int
   }
 }
 
-// Pair emission balanced over the block: every thread computes the pair
-// offsets of its 4 splats, the block's offsets go to shared memory, then the
-// block's pairs are written in order, pair j by thread j mod 1024, each thread
-// finding its splat by binary search: consecutive threads write consecutive
-// keys whatever the splat sizes.
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap,
-                                                           const uint64_t *block_off, uint64_t *keys, uint32_t *vals,
-                                                           int64_t pair_cap, int gx) {
-  __shared__ uint32_t s_off[kScanItems + 1];
+// Per-splat exclusive pair offsets (saturated to 32 bits: offsets past the
+// pair capacity are never written).
+__global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *ctl, const uint32_t *touched,
+                                                                   int64_t ncap, const uint64_t *block_off,
+                                                                   uint32_t *offsets) {
   const int64_t N = n_drawn(ctl, ncap);
   const int64_t base = (int64_t)blockIdx.x * kScanItems;
   if (base >= N) return;
@@ -108,37 +104,51 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const Ctl *ctl, Spla
   uint64_t s = 0;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
-    cnt[k] = (i0 + k < N) ? sp.touched[i0 + k] : 0;
+    cnt[k] = (i0 + k < N) ? touched[i0 + k] : 0;
     s += cnt[k];
   }
   uint64_t tot;
-  uint64_t pre = block_excl_scan_1024(s, &tot);
+  uint64_t off = block_off[blockIdx.x] + block_excl_scan_1024(s, &tot);
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
-    s_off[threadIdx.x * kScanPer + k] = (uint32_t)pre;
-    pre += cnt[k];
+    if (i0 + k < N) offsets[i0 + k] = off < 0xFFFFFFFFull ? (uint32_t)off : 0xFFFFFFFFu;
+    off += cnt[k];
   }
-  if (threadIdx.x == 0) s_off[kScanItems] = (uint32_t)tot;
-  __syncthreads();
-  const uint64_t out0 = block_off[blockIdx.x];
-  const uint32_t T = (uint32_t)tot;
-  for (uint32_t j = threadIdx.x; j < T; j += kScanThreads) {
-    // last item with s_off[item] <= j (items with no pairs share offsets; the
-    // search lands on the last of them, which is the one owning pair j)
-    int lo = 0, hi = kScanItems - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= j) lo = mid; else hi = mid - 1;
+}
+
+// Pair emission balanced over the whole grid: warp w writes pairs
+// [1024 w, 1024 w + 1024), lane l the pairs 1024 w + 32 k + l, so stores are
+// coalesced whatever the splat sizes.  The splat of a pair is found by
+// walking the offsets forward from the splat of the chunk's first pair.
+__global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
+                                                   uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx) {
+  const int64_t N = n_drawn(ctl, ncap);
+  int64_t M = ctl->pairs;
+  if (M > pair_cap) M = pair_cap;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp0; c * 1024 < M; c += nwarps) {
+    const uint32_t j0 = (uint32_t)(c * 1024);
+    // last splat with offset <= j0
+    int64_t lo = 0, hi = N - 1;
+    if (lane == 0) {
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= j0) lo = mid; else hi = mid - 1;
+      }
     }
-    const int64_t i = base + lo;
-    const uint32_t q = j - s_off[lo];
-    const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-    const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
-    const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
-    const uint64_t o = out0 + j;
-    if ((int64_t)o < pair_cap) {
-      keys[o] = ((uint64_t)tile << 32) | sp.depth[i];
-      vals[o] = (uint32_t)i;
+    int64_t i = __shfl_sync(0xffffffffu, lo, 0);
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t j = j0 + 32u * k + lane;
+      if ((int64_t)j >= M) break;
+      while (i + 1 < N && offsets[i + 1] <= j) ++i;
+      const uint32_t q = j - offsets[i];
+      const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
+      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+      const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
+      keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
+      vals[j] = (uint32_t)i;
     }
   }
 }
@@ -194,7 +204,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
+__global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
                                                                 uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
                                                                 const uint32_t *bases, uint32_t *status,
                                                                 uint32_t *tile_ctr) {
@@ -325,12 +335,12 @@ __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap,
 
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st) {
-  (void)offsets;
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, bs);
   scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, bs);
-  emit_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp, ncap, bs, keys, vals, pair_cap, gx);
+  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, bs, offsets);
+  emit_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap, gx);
 }
 
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,
@@ -348,7 +358,7 @@ int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap
   if ((int64_t)passes * max_tiles * 256 > lookback_words) return -1;
   sort_hist_kernel<<<148 * 4, 256, 0, st>>>(ctl, keys[0], pair_cap, passes, hist, lookback, max_tiles, tile_ctr);
   sort_bases_kernel<<<1, 256, 0, st>>>(hist, passes);
-  int grid = 148 * 3;
+  int grid = 148 * 4;
   if (grid > max_tiles) grid = (int)(max_tiles > 0 ? max_tiles : 1);
   int cur = 0;
   for (int d = 0; d < passes; ++d) {

@@ -11,7 +11,7 @@ namespace vm {
 namespace {
 
 __global__ void __launch_bounds__(512) stream_kernel(StreamArgs a) {
-  const int n = a.ctl->n_copies;
+  const int n = *a.count;
   const int64_t nseg = a.copy_seg[n];
   for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     // copy holding this segment

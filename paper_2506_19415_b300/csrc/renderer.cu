@@ -65,7 +65,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.nlink = (int64_t)s->link_col.size();
   d.scan_blocks = (d.ncap + kScanItems - 1) / kScanItems;
   d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
-  d.raster_cap = d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20);
+  d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
   return d;
@@ -117,9 +117,17 @@ Layout make_layout(const Dims &d) {
   L.splat_touched = take(4 * N);
   L.splat_radius = take(4 * N);
   L.block_sums = take(8 * d.scan_blocks);
-  L.offsets = take(0);
+  L.offsets = take(4 * N);
   L.raster_queue = take(kRasterRecord * d.raster_cap);
   L.raster_count = take(16);
+  L.centroid = take(16 * NP);
+  L.pf_flag = take(P * d.Smax);
+  L.pf_mask = take((NP + 3) / 4 * 4);
+  L.pf_cand = take(8 * (int64_t)d.ukey_cap);
+  L.pf_copies = take(16 * NP);
+  L.pf_copy_seg = take(8 * (NP + 1));
+  L.pf_count = take(16);
+  L.pf_base = take(16);
   L.keys0 = take(8 * d.pair_cap);
   L.keys1 = take(8 * d.pair_cap);
   L.vals0 = take(4 * d.pair_cap);
@@ -228,6 +236,12 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_lod), 0xFF, 4 * P, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_last), 0xFF, 4 * P, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_slot), 0xFF, 4 * P * d.Smax, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_flag), 0, P * d.Smax, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_count), 0, 16, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.centroid), s->centroid.data(), 4 * s->centroid.size(),
+                                     cudaMemcpyHostToDevice, st), "copy", &rc);
+  for (int k = 0; k < 3; ++k) r->scene_center[k] = s->box_center[k];
+  r->scene_half = s->box_half;
   Ctl c{};
   c.tau = p->tau0;
   c.step = p->step0;
@@ -298,7 +312,7 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     r->last_fb_pixels = npix;
     if (c.fy > fpx) fpx = c.fy;
   }
-  r->span_end(sp_fb, 4 * n_cams, st);
+  r->span_end(sp_fb, 5 * n_cams, st);
   r->f_px = fpx;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -345,6 +359,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   a.pt_slot = r->at<int32_t>(r->lay.pt_slot);
   a.required = r->at<uint8_t>(r->lay.required);
   a.any_req = r->at<uint8_t>(r->lay.any_req);
+  a.pf_flag = r->at<uint8_t>(r->lay.pf_flag);
   a.err = r->at<float>(r->lay.err);
   a.NP = (int32_t)r->dims.NP;
   a.P = r->P;
@@ -364,7 +379,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   launch_residency(a, st);
   r->span_end(sp_res, 1, st);
   StreamArgs sa{};
-  sa.ctl = a.ctl;
+  sa.count = &a.ctl->n_copies;
   sa.copies = a.copies;
   sa.copy_seg = a.copy_seg;
   sa.host = r->host_dev;
@@ -435,9 +450,9 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     launch_project(pa, c, st);
     r->span_end(t, 1, st);
     t = r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st);
-    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), nullptr, keys[0], vals[0],
-                     r->dims.pair_cap, gx, st);
-    r->span_end(t, 3, st);
+    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), r->at<uint32_t>(r->lay.offsets),
+                     keys[0], vals[0], r->dims.pair_cap, gx, st);
+    r->span_end(t, 4, st);
     const int bits = 32 + tbits;
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
     const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, bits, r->at<uint32_t>(r->lay.hist),
@@ -492,6 +507,9 @@ extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *str
   out->acc_streamed_pages = c.acc_streamed_pages;
   out->acc_missing = c.acc_missing;
   out->acc_requested = c.acc_requested;
+  out->acc_prefetched_pages = c.acc_prefetched_pages;
+  out->acc_prefetched_bytes = c.acc_prefetched_bytes;
+  out->acc_prefetch_hits = c.acc_prefetch_hits;
   return VM3DGS_OK;
 }
 

@@ -7,6 +7,8 @@
 
 #include "scene.h"
 
+struct vm3dgs_renderer;
+
 namespace vm {
 
 // Device control block: per-frame counters, controller state, error word.
@@ -22,9 +24,11 @@ struct Ctl {
   int32_t status;          // 0 or a VM3DGS_E_* code written by a kernel
   int32_t depth_lo;        // unused
   int32_t pad1;
+  int32_t n_hits;          // requested pages found resident thanks to a prefetch, this frame
+  int32_t pad2;
   // running sums since the last reset (read without per-frame syncs)
   int64_t acc_frames, acc_views, acc_pairs, acc_draw_gauss, acc_streamed_bytes, acc_streamed_pages, acc_missing,
-      acc_requested;
+      acc_requested, acc_prefetched_pages, acc_prefetched_bytes, acc_prefetch_hits;
 };
 
 struct Splats {
@@ -42,7 +46,8 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
       face_page, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, block_sums, offsets, raster_queue, raster_count, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+      splat_radius, block_sums, offsets, raster_queue, raster_count, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
+      pf_copy_seg, pf_count, pf_base, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
 
 struct Dims {
@@ -56,7 +61,7 @@ Layout make_layout(const Dims &d);
 
 constexpr int kScanItems = 4096;     // elements per scan block
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxPasses = 8;
 constexpr int64_t kCopySeg = 65536;
@@ -88,7 +93,7 @@ struct ResidencyArgs {
   int64_t *draw_off;
   int32_t *missing;
   int32_t *pt_lod, *pt_last, *pt_slot;
-  uint8_t *required, *any_req;
+  uint8_t *required, *any_req, *pf_flag;
   const float *err;
   int32_t NP, P, Smax, levels, fanout, page_size;
   int32_t lod_on;
@@ -101,7 +106,7 @@ struct ResidencyArgs {
 void launch_residency(const ResidencyArgs &a, cudaStream_t st);
 
 struct StreamArgs {
-  const Ctl *ctl;
+  const int32_t *count;         // number of copies (device)
   const int4 *copies;
   const int64_t *copy_seg;
   const uint8_t *host;          // device-visible pointer to the scene's page data (fp32 or fp16)
@@ -134,6 +139,9 @@ int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap
 
 void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, cudaStream_t st);
 
+void launch_prefetch_features(const vm3dgs_renderer *r, int n_out, const vm3dgs_camera &cam,
+                              const vm3dgs_camera &prev, float *x, int32_t *base, cudaStream_t st);
+
 void launch_blend(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap, const vm3dgs_camera &cam,
                   const float bg[3], float *image, cudaStream_t st);
 
@@ -156,6 +164,7 @@ struct vm3dgs_renderer {
   cudaEvent_t copy_done = nullptr;
   bool copy_pending = false;
   int64_t last_fb_pixels = 0;
+  float scene_center[3] = {0, 0, 0}, scene_half = 1.0f;
   int sorted_buf = 0;     // pair buffer (0/1) holding the last view's sorted pairs
   int last_ntiles = 0;
   // per-stage timing

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -14,6 +15,45 @@ thread_local std::string g_last_error;
 int fail(int code, const std::string &msg) {
   g_last_error = msg;
   return code;
+}
+void finish_scene(vm3dgs_scene *S) {
+  const int64_t NP = S->n_pages, ps = S->page_size;
+  const int NA = n_attr32(S->K);
+  S->centroid.assign(4 * NP, 0.0f);
+  const float *L0 = (const float *)(S->data32 + S->off32[0]);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t p = 0; p < NP; ++p) {
+    const float *b = L0 + p * ps * NA;
+    const int64_t n = S->count[p];
+    double c[3] = {0, 0, 0};
+    for (int64_t g = 0; g < n; ++g)
+      for (int a = 0; a < 3; ++a) c[a] += b[a * ps + g];
+    for (int a = 0; a < 3; ++a) c[a] /= (n > 0 ? n : 1);
+    double r = 0;
+    for (int64_t g = 0; g < n; ++g) {
+      double d2 = 0, smax = 0;
+      for (int a = 0; a < 3; ++a) {
+        const double d = b[a * ps + g] - c[a];
+        d2 += d * d;
+        smax = std::max(smax, (double)b[(3 + a) * ps + g]);
+      }
+      r = std::max(r, std::sqrt(d2) + 3.0 * smax);
+    }
+    for (int a = 0; a < 3; ++a) S->centroid[4 * p + a] = (float)c[a];
+    S->centroid[4 * p + 3] = (float)r;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t p = 0; p < NP; ++p)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], (double)S->centroid[4 * p + a]);
+      hi[a] = std::max(hi[a], (double)S->centroid[4 * p + a]);
+    }
+  double half = 0;
+  for (int a = 0; a < 3; ++a) {
+    S->box_center[a] = NP ? (float)(0.5 * (lo[a] + hi[a])) : 0.0f;
+    half = std::max(half, NP ? 0.5 * (hi[a] - lo[a]) : 0.0);
+  }
+  S->box_half = (float)(half > 0 ? half : 1.0);
 }
 }  // namespace vm
 
@@ -181,6 +221,7 @@ extern "C" int vm3dgs_scene_import(const vm3dgs_scene_desc *d, vm3dgs_scene **ou
   }
   for (int64_t k = 0; k < d->n_links; ++k)
     if (S->link_col[k] < 0 || S->link_col[k] >= NP) { delete S; return fail(VM3DGS_E_INVAL, "link column out of range"); }
+  finish_scene(S);
   *out = S;
   return VM3DGS_OK;
 }

@@ -6,6 +6,8 @@
 
 #include "../../include/vm3dgs.h"
 
+struct vm3dgs_scene;
+
 #ifdef __CUDACC__
 #define VM_HD __host__ __device__
 #else
@@ -18,6 +20,10 @@ constexpr int kMaxLevels = 6;
 
 // Error reporting: a thread-local message plus the return code.
 int fail(int code, const std::string &msg);
+
+// Page centroids and the box around them (for the prefetch window and LOD of
+// prefetched pages); called at the end of every scene construction.
+void finish_scene(vm3dgs_scene *s);
 
 // fp32 record: attributes of one Gaussian as float arrays of a page block.
 //   0..2 pos, 3..5 scale, 6..9 rot (w,x,y,z), 10 opacity, 11 + 3k + c  SH coefficient k, channel c
@@ -49,6 +55,8 @@ struct vm3dgs_scene {
   std::vector<int32_t> face_page;
   std::vector<int64_t> link_ptr; // [n_pages + 1]
   std::vector<int32_t> link_col;
+  std::vector<float> centroid;   // [n_pages * 4]: mean of the level-0 means, radius incl. 3 sigma
+  float box_center[3] = {0, 0, 0}, box_half = 1.0f;
   bool registered32 = false, registered16 = false;
 
   int32_t m(int l) const {
