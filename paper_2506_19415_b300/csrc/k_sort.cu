@@ -118,8 +118,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *c
 
 // Pair emission balanced over the whole grid: warp w writes pairs
 // [1024 w, 1024 w + 1024), lane l the pairs 1024 w + 32 k + l, so stores are
-// coalesced whatever the splat sizes.  The splat of a pair is found by
-// walking the offsets forward from the splat of the chunk's first pair.
+// coalesced whatever the splat sizes.  The splat of a pair is the last one
+// whose offset is <= the pair index, found from the previous pair's splat by
+// a galloping search (runs of culled splats share one offset).
 __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
                                                    uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx) {
   const int64_t N = n_drawn(ctl, ncap);
@@ -142,7 +143,17 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     for (int k = 0; k < 32; ++k) {
       const uint32_t j = j0 + 32u * k + lane;
       if ((int64_t)j >= M) break;
-      while (i + 1 < N && offsets[i + 1] <= j) ++i;
+      if (i + 1 < N && offsets[i + 1] <= j) {
+        // gallop over the splats without pairs, then bisect
+        int64_t lo2 = i + 1, step = 1;
+        while (lo2 + step < N && offsets[lo2 + step] <= j) { lo2 += step; step <<= 1; }
+        int64_t hi2 = lo2 + step < N ? lo2 + step - 1 : N - 1;
+        while (lo2 < hi2) {
+          const int64_t mid = (lo2 + hi2 + 1) >> 1;
+          if (offsets[mid] <= j) lo2 = mid; else hi2 = mid - 1;
+        }
+        i = lo2;
+      }
       const uint32_t q = j - offsets[i];
       const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
       const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
