@@ -322,6 +322,29 @@ int vm3dgs_prefetch_labels(vm3dgs_renderer *r, int32_t n_out, const int32_t *bas
 int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const vm3dgs_camera *cam, const vm3dgs_camera *prev,
                     float threshold, void *stream, void *copy_stream);
 
+/* ------------------------------------------------- sort without allocation
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: a host application that reserves the device's
+ * memory for itself and hands libraries only its own buffers, or a frame loop
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * Sorts n (key, value) pairs in place, stably, by the low key_bits bits of the
+ * keys (the renderer's onesweep radix sort), enqueued on stream.  keys_dev and
+ * vals_dev are the caller's device arrays (input and output).  All scratch is
+ * a fixed array inside the library (about 8.4 MB, held on every device that
+ * loads the library until the process exits); n above
+ * VM3DGS_NOALLOC_MAX_PAIRS is rejected with VM3DGS_E_CAPACITY before any
+ * work.  The first call on a device looks up the array's device address (do
+ * it once before time-critical use).  Every call shares the array and the
+ * array keeps the last call's contents (each call clears what must start at
+ * zero); calls that overlap on one device race.  If status_dev is not null it
+ * receives 0, or VM3DGS_E_TIMEOUT if a bounded wait of the sort gave up (the
+ * output is then not sorted).  Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+#define VM3DGS_NOALLOC_MAX_PAIRS (1 << 19)
+int vm3dgs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, int64_t n, int32_t key_bits,
+                              int32_t *status_dev, void *stream);
+
 const char *vm3dgs_last_error(void);
 const char *vm3dgs_version(void);
 

@@ -118,6 +118,7 @@ _SIGS = {
     "vm3dgs_prefetch_features": [c_p, c_i32, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_p, c_p, c_p],
     "vm3dgs_prefetch_labels": [c_p, c_i32, c_p, c_p, c_p, c_p],
     "vm3dgs_prefetch": [c_p, c_p, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_f, c_p, c_p],
+    "vm3dgs_sort_pairs_noalloc": [c_p, c_p, c_i64, c_i32, c_p, c_p],
     "vm3dgs_last_error": [],
     "vm3dgs_version": [],
 }
@@ -522,3 +523,15 @@ def vm3dgs_prefetch(r: "Renderer", p: Prefetcher, cam, prev, threshold=0.0, stre
     c, pc = camera_struct(cam), camera_struct(prev)
     _check(_lib.vm3dgs_prefetch(r.h, p.h, ctypes.byref(c), ctypes.byref(pc), float(threshold), _stream_ptr(stream),
                                 _stream_ptr(copy_stream) if copy_stream is not None else None))
+
+
+NOALLOC_MAX_PAIRS = 1 << 19
+
+
+def vm3dgs_sort_pairs_noalloc(keys, vals, n, key_bits, status=None, stream=None):
+    """Stable in-place sort of device tensors keys (uint64 as int64) / vals
+    (int32) by the low key_bits bits, with the library's fixed scratch (no
+    allocation).  status: optional 1-element int32 device tensor."""
+    _check(_lib.vm3dgs_sort_pairs_noalloc(c_p(keys.data_ptr()), c_p(vals.data_ptr()), int(n), int(key_bits),
+                                          c_p(status.data_ptr()) if status is not None else None,
+                                          _stream_ptr(stream)))
