@@ -245,6 +245,66 @@ def roofline(v, stage, stats, peaks, rec16, K):
     return out
 
 
+def batched_views_eval(v, reps=5):
+    """64 cameras of uneven resolution (512x512 .. 1920x1080, fov 40-90 deg)
+    on the 1M-Gaussian blob scene sharing one 64 MiB fp16 pool: views/s of 64
+    sequential single-view renders vs the autotuned, graph-captured batch."""
+    import scenegen
+    import torch
+    W2 = workload("blobs1m")
+    raw = W2["gen"]()
+    scene = v.vm3dgs_build_pages(raw, v.BuildConfig(**W2["build"], seed=77))
+    del raw
+    cams = scenegen.batched_views(n_views=64)
+    cfg = v.RenderConfig(staging_bytes=64 << 20, lod=False, fp16_pool=True, max_width=1920, max_height=1080,
+                         max_views=64, max_pairs=1 << 27)
+    r = v.Renderer(scene, cfg, pool_bytes=64 << 20)
+    st = torch.cuda.current_stream()
+    r.render_feedback(cams, st)
+    r.update_residency(st)
+    images = [torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda") for c in cams]
+    for _ in range(2):
+        for k, c in enumerate(cams):
+            r.render([c], [images[k]], st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        for k, c in enumerate(cams):
+            r.render([c], [images[k]], st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / reps
+    t0 = time.time()
+    tuned = r.autotune_tiles(cams, images, repeats=3)
+    tune_s = time.time() - t0
+    shapes = {}
+    for c in tuned:
+        shapes["%dx%d" % (c.tile_w, c.tile_h)] = shapes.get("%dx%d" % (c.tile_w, c.tile_h), 0) + 1
+    r.render_batched(tuned, images, st)
+    s = torch.cuda.Stream()
+    s.wait_stream(st)
+    with torch.cuda.stream(s):
+        r.batch_graph_capture(tuned, images, s)
+        for _ in range(2):
+            r.batch_graph_launch(tuned, s)
+    s.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        r.batch_graph_launch(tuned, s)
+    e1.record(s)
+    s.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    st_ = r.stats(st)
+    pix = sum(c.width * c.height for c in cams)
+    return {"workload": "64 views 512x512..1920x1080 (%.1f Mpx), fov 40-90 deg, 1M-Gaussian blob scene, shared 64 MiB "
+                        "fp16 pool" % (pix / 1e6),
+            "views_per_s_batched_graph": round(64 / (batch_ms / 1e3), 1),
+            "views_per_s_sequential": round(64 / (seq_ms / 1e3), 1),
+            "ms_batch": round(batch_ms, 3), "ms_sequential": round(seq_ms, 3), "tile_shapes": shapes,
+            "autotune_s": round(tune_s, 2), "pairs_per_batch": st_["pairs"], "status": st_["status"]}
+
+
 def gpu_main(args):
     import torch
     import paper_2506_19415_b300 as v
@@ -352,6 +412,8 @@ def gpu_main(args):
         "clocks": clk,
         "scene_build_s": {"generate": round(t_gen, 1), "prepare": round(t_build, 1)},
     }
+    if not args.no_batched and world == 1:
+        line["batched_views"] = batched_views_eval(v)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, W, quick=True)
     print(json.dumps(line), flush=True)
@@ -429,6 +491,7 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefetch", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -214,6 +214,27 @@ int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *copy_stream)
  * ranges, front-to-back blending. */
 int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images, void *stream);
 
+/* Many views at once over the same resident pages (the union of their
+ * requests was made resident by render_feedback on all of them): one
+ * projection over (view, Gaussian), one pair sort over all views (the key's
+ * tile field is a global tile id), one persistent blend over every (view,
+ * tile) with each view's own tile shape.  n_cams <= max_views (<= 64). */
+int vm3dgs_render_batched(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images,
+                          void *stream);
+/* Captures vm3dgs_render_batched for these views (their resolutions, tile
+ * shapes and images) into a CUDA graph held by the renderer; stream must not
+ * be the legacy default stream.  vm3dgs_batch_graph_launch replays it with
+ * new camera poses (same count, sizes and tile shapes). */
+int vm3dgs_batch_graph_capture(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images,
+                               void *stream);
+int vm3dgs_batch_graph_launch(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, void *stream);
+/* Tile-shape autotuner: per resolution class (< 0.5, < 1, < 1.5, >= 1.5
+ * megapixels) tries 16x16, 8x8 and 32x8 on the batch (median of `repeats`
+ * timed runs), keeps the fastest, and writes the choice into cams[].tile_w /
+ * tile_h.  Renders into images; synchronises stream. */
+int vm3dgs_autotune_tiles(vm3dgs_renderer *r, vm3dgs_camera *cams, int32_t n_cams, float *const *images,
+                          int32_t repeats, void *stream);
+
 /* Copies the last frame's statistics (synchronises stream). */
 int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *stream);
 /* Clears the running sums of the statistics (enqueued on stream). */

@@ -119,6 +119,10 @@ _SIGS = {
     "vm3dgs_prefetch_labels": [c_p, c_i32, c_p, c_p, c_p, c_p],
     "vm3dgs_prefetch": [c_p, c_p, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_f, c_p, c_p],
     "vm3dgs_sort_pairs_noalloc": [c_p, c_p, c_i64, c_i32, c_p, c_p],
+    "vm3dgs_render_batched": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_p],
+    "vm3dgs_batch_graph_capture": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_p],
+    "vm3dgs_batch_graph_launch": [c_p, ctypes.POINTER(Camera), c_i32, c_p],
+    "vm3dgs_autotune_tiles": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_i32, c_p],
     "vm3dgs_last_error": [],
     "vm3dgs_version": [],
 }
@@ -371,6 +375,38 @@ class Renderer:
         ptrs = (c_p * len(images))(*[im.data_ptr() for im in images])
         _check(_lib.vm3dgs_render(self.h, arr, len(cams), ptrs, _stream_ptr(stream)))
         return images
+
+    def _images(self, cams, images):
+        import torch
+        if images is None:
+            images = [torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.pool.device) for c in cams]
+        return images, (c_p * len(images))(*[im.data_ptr() for im in images])
+
+    def render_batched(self, cams, images=None, stream=None):
+        images, ptrs = self._images(cams, images)
+        _check(_lib.vm3dgs_render_batched(self.h, camera_array(cams), len(cams), ptrs, _stream_ptr(stream)))
+        return images
+
+    def batch_graph_capture(self, cams, images=None, stream=None):
+        images, ptrs = self._images(cams, images)
+        _check(_lib.vm3dgs_batch_graph_capture(self.h, camera_array(cams), len(cams), ptrs, _stream_ptr(stream)))
+        return images
+
+    def batch_graph_launch(self, cams, stream=None):
+        _check(_lib.vm3dgs_batch_graph_launch(self.h, camera_array(cams), len(cams), _stream_ptr(stream)))
+
+    def autotune_tiles(self, cams, images=None, repeats=3, stream=None):
+        """Returns the cameras with the tile shapes the autotuner chose."""
+        import copy
+        images, ptrs = self._images(cams, images)
+        arr = camera_array(cams)
+        _check(_lib.vm3dgs_autotune_tiles(self.h, arr, len(cams), ptrs, repeats, _stream_ptr(stream)))
+        out = []
+        for i, c in enumerate(cams):
+            c2 = copy.copy(c)
+            c2.tile_w, c2.tile_h = arr[i].tile_w, arr[i].tile_h
+            out.append(c2)
+        return out
 
     def stats(self, stream=None) -> dict:
         s = Stats()

@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EXACT = {"k_project.cu", "k_feedback.cu", "k_residency.cu", "k_prefetch.cu"}
 CU = ["k_project.cu", "k_feedback.cu", "k_residency.cu", "k_stream.cu", "k_sort.cu", "k_blend.cu", "renderer.cu",
       "k_mlp.cu", "prefetcher.cu", "k_prefetch.cu",
-      "sort_noalloc.cu"]
+      "sort_noalloc.cu", "batch.cu"]
 CPP = ["build_pages.cpp", "scene.cpp"]
 HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh"]
 

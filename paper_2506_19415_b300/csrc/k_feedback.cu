@@ -121,19 +121,66 @@ __device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, flo
   for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, i0 + q % bw, j0 + q / bw, Wf, fb);
 }
 
-__global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
-                                                           const int32_t *face_page, int64_t ntri, vm3dgs_camera cam,
-                                                           int ds, uint64_t *fb, Tri *queue, uint32_t *qcount,
-                                                           uint32_t qcap) {
+// Pass 1: triangles entirely behind the near plane, or entirely more than 2
+// pixels beyond one side of the buffer, cover no pixel centre; the others are
+// appended (warp-aggregated) to a dense list so that pass 2 runs without idle
+// lanes.
+__global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, const int32_t *tris, int64_t ntri,
+                                                          vm3dgs_camera cam, int ds, uint32_t *vis,
+                                                          uint32_t *nvis) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
   const float zn = 0.2f;
-  // side planes of the buffer widened by 2 pixels, as x / z (resp. y / z) limits
   const float kr = ((float)Wf + 2.0f - cxf) / fxf, kl = (-2.0f - cxf) / fxf;
   const float kb = ((float)Hf + 2.0f - cyf) / fyf, kt = (-2.0f - cyf) / fyf;
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ntri; base += stride) {
+    const int64_t t = base + lane;
+    bool keep = false;
+    if (t < ntri) {
+      V3 c[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
+      int nin = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) nin += c[k].z >= zn;
+      keep = nin > 0;
+      if (nin == 3) {
+        bool o1 = true, o2 = true, o3 = true, o4 = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          o1 = o1 && c[k].x > kr * c[k].z;
+          o2 = o2 && c[k].x < kl * c[k].z;
+          o3 = o3 && c[k].y > kb * c[k].z;
+          o4 = o4 && c[k].y < kt * c[k].z;
+        }
+        keep = !(o1 || o2 || o3 || o4);
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    uint32_t off = 0;
+    if (lane == 0 && m) off = atomicAdd(nvis, (uint32_t)__popc(m));
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (keep) vis[off + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+  }
+}
+
+// Pass 2: clip, snap and rasterise the listed triangles (small ones here,
+// larger ones queued).
+__global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
+                                                           const int32_t *face_page, const uint32_t *vis,
+                                                           const uint32_t *nvis, vm3dgs_camera cam, int ds,
+                                                           uint64_t *fb, Tri *queue, uint32_t *qcount, uint32_t qcap) {
+  const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
+  const float fds = (float)ds;
+  const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
+  const float zn = 0.2f;
+  const int64_t n = *nvis;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int64_t t = vis[q];
     V3 c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
@@ -142,18 +189,7 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
     int nin = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
-    if (nin == 0) continue;
     if (nin == 3) {
-      // whole triangle more than 2 pixels beyond one side of the buffer: no pixel centre is covered
-      bool out = true;
-      for (int k = 0; k < 3 && out; ++k) out = c[k].x > kr * c[k].z;
-      bool o2 = true;
-      for (int k = 0; k < 3 && o2; ++k) o2 = c[k].x < kl * c[k].z;
-      bool o3 = true;
-      for (int k = 0; k < 3 && o3; ++k) o3 = c[k].y > kb * c[k].z;
-      bool o4 = true;
-      for (int k = 0; k < 3 && o4; ++k) o4 = c[k].y < kt * c[k].z;
-      if (out || o2 || o3 || o4) continue;
       setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
       continue;
     }
@@ -256,13 +292,15 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
 
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
                             const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
-                            uint32_t qcap, cudaStream_t st) {
+                            uint32_t qcap, uint32_t *vis, cudaStream_t st) {
   if (ntri <= 0) return;
-  cudaMemsetAsync(qcount, 0, 2 * sizeof(uint32_t), st);
+  // qcount[0..1]: queued medium / huge triangles, qcount[2]: listed triangles
+  cudaMemsetAsync(qcount, 0, 3 * sizeof(uint32_t), st);
   int64_t blocks = (ntri + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  raster_setup_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, face_page, ntri, cam, ds, fb,
-                                                        reinterpret_cast<Tri *>(queue), qcount, qcap);
+  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, ntri, cam, ds, vis, qcount + 2);
+  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 2, cam, ds, fb,
+                                               reinterpret_cast<Tri *>(queue), qcount, qcap);
   const int Wf = (cam.width + ds - 1) / ds;
   raster_medium_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
   raster_huge_kernel<<<148 * 2, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);

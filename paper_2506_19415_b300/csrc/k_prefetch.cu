@@ -129,7 +129,14 @@ __device__ int64_t bscan(int64_t v, int64_t *total, ScanSmem &sm) {
   return pre;
 }
 
-__device__ void bitonic(uint64_t *a, int n) {
+constexpr int kSmemKeys = 16384;
+// bitonic sort of n (a power of two) keys, in shared memory when they fit
+__device__ void bitonic(uint64_t *g, int n, uint64_t *sh) {
+  uint64_t *a = n <= kSmemKeys ? sh : g;
+  if (a == sh) {
+    for (int i = threadIdx.x; i < n; i += RT) sh[i] = g[i];
+    __syncthreads();
+  }
   for (int k = 2; k <= n; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < n; i += RT) {
@@ -141,6 +148,10 @@ __device__ void bitonic(uint64_t *a, int n) {
       }
       __syncthreads();
     }
+  if (a == sh) {
+    for (int i = threadIdx.x; i < n; i += RT) g[i] = sh[i];
+    __syncthreads();
+  }
 }
 
 __device__ int pow2_at_least(int n) {
@@ -156,6 +167,7 @@ __device__ __forceinline__ uint32_t ordered(float f) {
 }
 
 __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
+  extern __shared__ uint64_t s_keys[];
   __shared__ ScanSmem sm;
   __shared__ int m_l[kMaxLevels], S_l[kMaxLevels], fresh_start[kMaxLevels + 1], n_lvl[kMaxLevels];
   Ctl *ctl = a.ctl;
@@ -205,10 +217,14 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
     nc += tot;
   }
   if (nc > a.cand_cap) nc = a.cand_cap;
+  if (nc == 0) {
+    if (tid == 0) { a.copy_seg[0] = 0; *a.count = 0; }
+    return;
+  }
   const int np2 = pow2_at_least((int)nc);
   for (int i = (int)nc + tid; i < np2; i += RT) a.cand[i] = ~0ull;
   __syncthreads();
-  bitonic(a.cand, np2);
+  bitonic(a.cand, np2, s_keys);
   // budget left by this frame
   const int64_t remaining = a.budget - ctl->streamed_bytes;
   int64_t nadm = 0, cum = 0;
@@ -222,6 +238,10 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
     nadm += t2;
     cum += tot;
   }
+  if (nadm == 0) {
+    if (tid == 0) { a.copy_seg[0] = 0; *a.count = 0; }
+    return;
+  }
   // free entries: not used this frame, least recently used first
   int64_t nfree = 0;
   for (int c = 0; c < a.P; c += RT) {
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
   const int fp2 = pow2_at_least((int)nfree);
   for (int i = (int)nfree + tid; i < fp2; i += RT) a.free_keys[i] = ~0ull;
   __syncthreads();
-  bitonic(a.free_keys, fp2);
+  bitonic(a.free_keys, fp2, s_keys);
   // per-level ranks (stored in the low bits' place: reuse cand's page field order)
   for (int l = 0; l < L; ++l) {
     int64_t b0 = 0;
@@ -366,7 +386,13 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   const int n_out = p->cfg.n_out;
   if (n_out % 16 || p->cfg.n_in != 12 + n_out / 16)
     return fail(VM3DGS_E_INVAL, "network must have n_in = 12 + n_out / 16 and n_out a multiple of 16");
-  cudaStream_t st = (cudaStream_t)stream, cst = copy_stream ? (cudaStream_t)copy_stream : st;
+  // The whole step runs on the copy stream after this frame's page-table
+  // update, concurrently with the frame's render: it reads this frame's
+  // requests and writes only entries the frame does not use.  The next
+  // feedback or update waits for it.
+  cudaStream_t cst = copy_stream ? (cudaStream_t)copy_stream : (cudaStream_t)stream;
+  cudaStreamWaitEvent(cst, r->res_done, 0);
+  cudaStream_t st = cst;
   const int span = r->span_begin(VM3DGS_STAGE_PREFETCH, st);
   const PfLayout &PL = p->lay;
   float *x = p->at<float>(PL.feat);
@@ -407,7 +433,13 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   a.threshold = threshold;
   a.f_px = cam->fy;
   for (int k = 0; k < 3; ++k) a.campos[k] = cam->campos[k];
-  place_kernel<<<1, RT, 0, st>>>(a);
+  static bool attr = false;
+  const int smem = kSmemKeys * (int)sizeof(uint64_t);
+  if (!attr) {
+    cudaFuncSetAttribute(place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  place_kernel<<<1, RT, smem, st>>>(a);
   StreamArgs sa{};
   sa.count = a.count;
   sa.copies = a.copies;
@@ -419,16 +451,12 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   sa.rec = r->rec;
   sa.pool = r->pool;
   sa.slot_bytes = r->slot_bytes;
-  r->span_end(span, 6, st);
-  if (cst != st) {
-    cudaEventRecord(r->copy_done, st);
-    cudaStreamWaitEvent(cst, r->copy_done, 0);
-  }
-  const int span2 = r->span_begin(VM3DGS_STAGE_PREFETCH, cst);
   launch_stream(sa, cst);
-  r->span_end(span2, 1, cst);
+  r->span_end(span, 7, cst);
+  cudaEventRecord(r->pf_done, cst);
   cudaEventRecord(r->copy_done, cst);
-  r->copy_pending = cst != st;
+  r->pf_pending = true;
+  r->copy_pending = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, cudaGetErrorString(e));
 }

@@ -64,16 +64,130 @@ struct Rec {
 #define SHC3D 0.3731763325901154f
 #define SHC3E 1.445305721320277f
 
+// Projects Gaussian g of the level block blk (m Gaussians) for one camera and
+// writes splat record o.
+template <int K, bool F16>
+__device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const uint8_t *blk, int m,
+                                            int g, int64_t out) {
+  using R = Rec<K, F16>;
+  const float *V = cam.view;
+  const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w;
+  const int gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
+  const float TW = (float)cam.tile_w, TH = (float)cam.tile_h;
+    float x = R::pos(blk, m, g, 0), y = R::pos(blk, m, g, 1), z = R::pos(blk, m, g, 2);
+  float o = R::opac(blk, m, g);
+  sp.touched[out] = 0;
+  sp.rect[2 * out] = 0;
+  sp.rect[2 * out + 1] = 0;
+  sp.depth[out] = 0;
+  sp.radius[out] = 0.0f;
+  float tx = ((V[0] * x + V[1] * y) + V[2] * z) + V[3];
+  float ty = ((V[4] * x + V[5] * y) + V[6] * z) + V[7];
+  float tz = ((V[8] * x + V[9] * y) + V[10] * z) + V[11];
+  if (!(o > 0.0f) || !(tz > 0.2f)) return;
+  float qw = R::rot(blk, m, g, 0), qx = R::rot(blk, m, g, 1), qy = R::rot(blk, m, g, 2), qz = R::rot(blk, m, g, 3);
+  float sc[3] = {R::scale(blk, m, g, 0), R::scale(blk, m, g, 1), R::scale(blk, m, g, 2)};
+  float xx = qx * qx, yy = qy * qy, zz = qz * qz;
+  float xy = qx * qy, xz = qx * qz, yz = qy * qz;
+  float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+  float Rm[3][3];
+  Rm[0][0] = 1.0f - 2.0f * (yy + zz); Rm[0][1] = 2.0f * (xy - wz); Rm[0][2] = 2.0f * (xz + wy);
+  Rm[1][0] = 2.0f * (xy + wz); Rm[1][1] = 1.0f - 2.0f * (xx + zz); Rm[1][2] = 2.0f * (yz - wx);
+  Rm[2][0] = 2.0f * (xz - wy); Rm[2][1] = 2.0f * (yz + wx); Rm[2][2] = 1.0f - 2.0f * (xx + yy);
+  float M[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[r][c] = Rm[r][c] * sc[c];
+  float S[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S[r][c] = (M[r][0] * M[c][0] + M[r][1] * M[c][1]) + M[r][2] * M[c][2];
+  float limx = 1.3f * ((0.5f * (float)cam.width) / cam.fx);
+  float limy = 1.3f * ((0.5f * (float)cam.height) / cam.fy);
+  float txtz = tx / tz, tytz = ty / tz;
+  float clx = fminf(limx, fmaxf(-limx, txtz)) * tz;
+  float cly = fminf(limy, fmaxf(-limy, tytz)) * tz;
+  float tz2 = tz * tz;
+  float J00 = cam.fx / tz, J02 = -(cam.fx * clx) / tz2;
+  float J11 = cam.fy / tz, J12 = -(cam.fy * cly) / tz2;
+  float T0[3], T1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T0[c] = J00 * V[c] + J02 * V[8 + c];
+    T1[c] = J11 * V[4 + c] + J12 * V[8 + c];
+  }
+  float u[3], w[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    u[r] = (S[r][0] * T0[0] + S[r][1] * T0[1]) + S[r][2] * T0[2];
+    w[r] = (S[r][0] * T1[0] + S[r][1] * T1[1]) + S[r][2] * T1[2];
+  }
+  float ca = (T0[0] * u[0] + T0[1] * u[1]) + T0[2] * u[2];
+  float cb = (T1[0] * u[0] + T1[1] * u[1]) + T1[2] * u[2];
+  float cc = (T1[0] * w[0] + T1[1] * w[1]) + T1[2] * w[2];
+  ca = ca + 0.3f;
+  cc = cc + 0.3f;
+  float det = fmaxf(ca * cc - cb * cb, 1e-12f);
+  float mid = 0.5f * (ca + cc);
+  float disc = fmaxf(0.1f, mid * mid - det);
+  float lam = mid + sqrtf(disc);
+  float r = ceilf(3.0f * sqrtf(lam));
+  float pu = cam.fx * txtz + cam.cx;
+  float pv = cam.fy * tytz + cam.cy;
+  float fx0 = floorf((pu - r) / TW), fx1 = floorf((pu + r) / TW) + 1.0f;
+  float fy0 = floorf((pv - r) / TH), fy1 = floorf((pv + r) / TH) + 1.0f;
+  fx0 = fminf(fmaxf(fx0, 0.0f), (float)gx); fx1 = fminf(fmaxf(fx1, 0.0f), (float)gx);
+  fy0 = fminf(fmaxf(fy0, 0.0f), (float)gy); fy1 = fminf(fmaxf(fy1, 0.0f), (float)gy);
+  const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+  if (x0 >= x1 || y0 >= y1) return;
+  // continuous outputs
+  float ia = cc / det, ib = -cb / det, ic = ca / det;
+  float dx = x - cam.campos[0], dy = y - cam.campos[1], dz = z - cam.campos[2];
+  float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+  dx *= inv; dy *= inv; dz *= inv;
+  float Y[16];
+  Y[0] = SHC0;
+  if (K > 1) {
+    Y[1] = -SHC1 * dy; Y[2] = SHC1 * dz; Y[3] = -SHC1 * dx;
+  }
+  if (K > 4) {
+    float x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
+    Y[4] = SHC2A * dx * dy; Y[5] = -SHC2A * dy * dz; Y[6] = SHC2B * (2.0f * z2 - x2 - y2);
+    Y[7] = -SHC2A * dx * dz; Y[8] = SHC2C * (x2 - y2);
+    if (K > 9) {
+      Y[9] = -SHC3A * dy * (3.0f * x2 - y2); Y[10] = SHC3B * dx * dy * dz;
+      Y[11] = -SHC3C * dy * (4.0f * z2 - x2 - y2); Y[12] = SHC3D * dz * (2.0f * z2 - 3.0f * x2 - 3.0f * y2);
+      Y[13] = -SHC3C * dx * (4.0f * z2 - x2 - y2); Y[14] = SHC3E * dz * (x2 - y2);
+      Y[15] = -SHC3A * dx * (x2 - 3.0f * y2);
+    }
+  }
+  float rgb[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s += R::sh(blk, m, g, k, c) * Y[k];
+    s += 0.5f;
+    rgb[c] = s > 0.0f ? s : 0.0f;
+  }
+  sp.s0[out] = make_float4(pu, pv, ia, ib);
+  sp.s1[out] = make_float4(ic, o, rgb[0], rgb[1]);
+  sp.s2[out] = rgb[2];
+  sp.depth[out] = __float_as_uint(tz);
+  sp.radius[out] = r;
+  sp.rect[2 * out] = (uint32_t)x0 | ((uint32_t)x1 << 16);
+  sp.rect[2 * out + 1] = (uint32_t)y0 | ((uint32_t)y1 << 16);
+  sp.touched[out] = (uint32_t)((x1 - x0) * (y1 - y0));
+}
+
 template <int K, bool F16>
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_camera cam) {
   using R = Rec<K, F16>;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
   const int nd = a.ctl->n_draw;
   const int lane = threadIdx.x & 31;
-  const float *V = cam.view;
-  const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w;
-  const int gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
-  const float TW = (float)cam.tile_w, TH = (float)cam.tile_h;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N; base += stride) {
     // lane 0 finds the draw item holding the warp's first Gaussian
@@ -95,114 +209,56 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_came
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-
-    float x = R::pos(blk, m, g, 0), y = R::pos(blk, m, g, 1), z = R::pos(blk, m, g, 2);
-    float o = R::opac(blk, m, g);
-    a.sp.touched[i] = 0;
-    a.sp.rect[2 * i] = 0;
-    a.sp.rect[2 * i + 1] = 0;
-    a.sp.depth[i] = 0;
-    a.sp.radius[i] = 0.0f;
-    float tx = ((V[0] * x + V[1] * y) + V[2] * z) + V[3];
-    float ty = ((V[4] * x + V[5] * y) + V[6] * z) + V[7];
-    float tz = ((V[8] * x + V[9] * y) + V[10] * z) + V[11];
-    if (!(o > 0.0f) || !(tz > 0.2f)) continue;
-    float qw = R::rot(blk, m, g, 0), qx = R::rot(blk, m, g, 1), qy = R::rot(blk, m, g, 2), qz = R::rot(blk, m, g, 3);
-    float sc[3] = {R::scale(blk, m, g, 0), R::scale(blk, m, g, 1), R::scale(blk, m, g, 2)};
-    float xx = qx * qx, yy = qy * qy, zz = qz * qz;
-    float xy = qx * qy, xz = qx * qz, yz = qy * qz;
-    float wx = qw * qx, wy = qw * qy, wz = qw * qz;
-    float Rm[3][3];
-    Rm[0][0] = 1.0f - 2.0f * (yy + zz); Rm[0][1] = 2.0f * (xy - wz); Rm[0][2] = 2.0f * (xz + wy);
-    Rm[1][0] = 2.0f * (xy + wz); Rm[1][1] = 1.0f - 2.0f * (xx + zz); Rm[1][2] = 2.0f * (yz - wx);
-    Rm[2][0] = 2.0f * (xz - wy); Rm[2][1] = 2.0f * (yz + wx); Rm[2][2] = 1.0f - 2.0f * (xx + yy);
-    float M[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) M[r][c] = Rm[r][c] * sc[c];
-    float S[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) S[r][c] = (M[r][0] * M[c][0] + M[r][1] * M[c][1]) + M[r][2] * M[c][2];
-    float limx = 1.3f * ((0.5f * (float)cam.width) / cam.fx);
-    float limy = 1.3f * ((0.5f * (float)cam.height) / cam.fy);
-    float txtz = tx / tz, tytz = ty / tz;
-    float clx = fminf(limx, fmaxf(-limx, txtz)) * tz;
-    float cly = fminf(limy, fmaxf(-limy, tytz)) * tz;
-    float tz2 = tz * tz;
-    float J00 = cam.fx / tz, J02 = -(cam.fx * clx) / tz2;
-    float J11 = cam.fy / tz, J12 = -(cam.fy * cly) / tz2;
-    float T0[3], T1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T0[c] = J00 * V[c] + J02 * V[8 + c];
-      T1[c] = J11 * V[4 + c] + J12 * V[8 + c];
-    }
-    float u[3], w[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      u[r] = (S[r][0] * T0[0] + S[r][1] * T0[1]) + S[r][2] * T0[2];
-      w[r] = (S[r][0] * T1[0] + S[r][1] * T1[1]) + S[r][2] * T1[2];
-    }
-    float ca = (T0[0] * u[0] + T0[1] * u[1]) + T0[2] * u[2];
-    float cb = (T1[0] * u[0] + T1[1] * u[1]) + T1[2] * u[2];
-    float cc = (T1[0] * w[0] + T1[1] * w[1]) + T1[2] * w[2];
-    ca = ca + 0.3f;
-    cc = cc + 0.3f;
-    float det = fmaxf(ca * cc - cb * cb, 1e-12f);
-    float mid = 0.5f * (ca + cc);
-    float disc = fmaxf(0.1f, mid * mid - det);
-    float lam = mid + sqrtf(disc);
-    float r = ceilf(3.0f * sqrtf(lam));
-    float pu = cam.fx * txtz + cam.cx;
-    float pv = cam.fy * tytz + cam.cy;
-    float fx0 = floorf((pu - r) / TW), fx1 = floorf((pu + r) / TW) + 1.0f;
-    float fy0 = floorf((pv - r) / TH), fy1 = floorf((pv + r) / TH) + 1.0f;
-    fx0 = fminf(fmaxf(fx0, 0.0f), (float)gx); fx1 = fminf(fmaxf(fx1, 0.0f), (float)gx);
-    fy0 = fminf(fmaxf(fy0, 0.0f), (float)gy); fy1 = fminf(fmaxf(fy1, 0.0f), (float)gy);
-    const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-    if (x0 >= x1 || y0 >= y1) continue;
-    // continuous outputs
-    float ia = cc / det, ib = -cb / det, ic = ca / det;
-    float dx = x - cam.campos[0], dy = y - cam.campos[1], dz = z - cam.campos[2];
-    float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= inv; dy *= inv; dz *= inv;
-    float Y[16];
-    Y[0] = SHC0;
-    if (K > 1) {
-      Y[1] = -SHC1 * dy; Y[2] = SHC1 * dz; Y[3] = -SHC1 * dx;
-    }
-    if (K > 4) {
-      float x2 = dx * dx, y2 = dy * dy, z2 = dz * dz;
-      Y[4] = SHC2A * dx * dy; Y[5] = -SHC2A * dy * dz; Y[6] = SHC2B * (2.0f * z2 - x2 - y2);
-      Y[7] = -SHC2A * dx * dz; Y[8] = SHC2C * (x2 - y2);
-      if (K > 9) {
-        Y[9] = -SHC3A * dy * (3.0f * x2 - y2); Y[10] = SHC3B * dx * dy * dz;
-        Y[11] = -SHC3C * dy * (4.0f * z2 - x2 - y2); Y[12] = SHC3D * dz * (2.0f * z2 - 3.0f * x2 - 3.0f * y2);
-        Y[13] = -SHC3C * dx * (4.0f * z2 - x2 - y2); Y[14] = SHC3E * dz * (x2 - y2);
-        Y[15] = -SHC3A * dx * (x2 - 3.0f * y2);
-      }
-    }
-    float rgb[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float s = 0.0f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) s += R::sh(blk, m, g, k, c) * Y[k];
-      s += 0.5f;
-      rgb[c] = s > 0.0f ? s : 0.0f;
-    }
-    a.sp.s0[i] = make_float4(pu, pv, ia, ib);
-    a.sp.s1[i] = make_float4(ic, o, rgb[0], rgb[1]);
-    a.sp.s2[i] = rgb[2];
-    a.sp.depth[i] = __float_as_uint(tz);
-    a.sp.radius[i] = r;
-    a.sp.rect[2 * i] = (uint32_t)x0 | ((uint32_t)x1 << 16);
-    a.sp.rect[2 * i + 1] = (uint32_t)y0 | ((uint32_t)y1 << 16);
-    a.sp.touched[i] = (uint32_t)((x1 - x0) * (y1 - y0));
+    project_one<K, F16>(a.sp, cam, blk, m, g, i);
   }
+}
+
+// All views at once: blockIdx.y is the view; splat record v * N + i.
+template <int K, bool F16>
+__global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, const ViewTable *views) {
+  using R = Rec<K, F16>;
+  const int v = blockIdx.y;
+  if (v >= views->n) return;
+  const vm3dgs_camera cam = views->cam[v];
+  const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
+  const int nd = a.ctl->n_draw;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N; base += stride) {
+    int j = 0;
+    if (lane == 0) {
+      int lo = 0, hi = nd - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.draw_off[mid] <= base) lo = mid; else hi = mid - 1;
+      }
+      j = lo;
+    }
+    j = __shfl_sync(0xffffffffu, j, 0);
+    const int64_t i = base + lane;
+    if (i >= N) continue;
+    while (j + 1 < nd && a.draw_off[j + 1] <= i) ++j;
+    const int4 it = a.draw[j];
+    int m = a.page_size;
+    for (int l = 0; l < it.y; ++l) m /= a.fanout;
+    const int g = (int)(i - a.draw_off[j]);
+    const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
+    project_one<K, F16>(a.sp, cam, blk, m, g, (int64_t)v * N + i);
+  }
+}
+
+template <int K>
+void launch_kb(const ProjectArgs &a, const ViewTable *views, int n_views, cudaStream_t st) {
+  int64_t blocks = (a.ncap + 255) / 256;
+  int64_t cap = (148 * 16 + n_views - 1) / n_views;
+  if (cap < 8) cap = 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  dim3 grid((unsigned)blocks, (unsigned)n_views);
+  if (a.fp16)
+    project_batched_kernel<K, true><<<grid, 256, 0, st>>>(a, views);
+  else
+    project_batched_kernel<K, false><<<grid, 256, 0, st>>>(a, views);
 }
 
 template <int K>
@@ -217,6 +273,15 @@ void launch_k(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
 }
 
 }  // namespace
+
+void launch_project_batched(const ProjectArgs &a, const ViewTable *views, int n_views, cudaStream_t st) {
+  switch (a.K) {
+    case 1: launch_kb<1>(a, views, n_views, st); break;
+    case 4: launch_kb<4>(a, views, n_views, st); break;
+    case 9: launch_kb<9>(a, views, n_views, st); break;
+    default: launch_kb<16>(a, views, n_views, st); break;
+  }
+}
 
 void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
   switch (a.K) {

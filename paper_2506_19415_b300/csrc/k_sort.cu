@@ -28,6 +28,8 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 3
 constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ int64_t n_drawn(const Ctl *c, int64_t cap) { return c->draw_gauss < cap ? c->draw_gauss : cap; }
+// splat records of all views (views x drawn)
+__device__ __forceinline__ int64_t n_total(const Ctl *c, int64_t cap, int views) { return n_drawn(c, cap) * views; }
 
 // exclusive scan across a 1024-thread block (64-bit); returns the block total in *total
 __device__ uint64_t block_excl_scan_1024(uint64_t v, uint64_t *total) {
@@ -58,8 +60,8 @@ __device__ uint64_t block_excl_scan_1024(uint64_t v, uint64_t *total) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Ctl *ctl, const uint32_t *touched, int64_t ncap,
-                                                                  uint64_t *block_sums) {
-  const int64_t N = n_drawn(ctl, ncap);
+                                                                  int views, uint64_t *block_sums) {
+  const int64_t N = n_total(ctl, ncap, views);
   const int64_t base = (int64_t)blockIdx.x * kScanItems;
   if (base >= N) return;
   uint64_t s = 0;
@@ -73,8 +75,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Ctl *ct
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int64_t ncap, uint64_t *block_sums) {
-  const int64_t N = n_drawn(ctl, ncap);
+__global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int64_t ncap, int views,
+                                                                  uint64_t *block_sums) {
+  const int64_t N = n_total(ctl, ncap, views);
   const int64_t nb = (N + kScanItems - 1) / kScanItems;
   uint64_t carry = 0;
   for (int64_t c = 0; c < nb; c += kScanThreads) {
@@ -87,16 +90,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int
   if (threadIdx.x == 0) {
     ctl->pairs = (int64_t)carry;
     ctl->acc_pairs += (int64_t)carry;
-    ctl->acc_views += 1;
+    ctl->acc_views += views;
   }
 }
 
 // Per-splat exclusive pair offsets (saturated to 32 bits: offsets past the
 // pair capacity are never written).
 __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *ctl, const uint32_t *touched,
-                                                                   int64_t ncap, const uint64_t *block_off,
+                                                                   int64_t ncap, int views, const uint64_t *block_off,
                                                                    uint32_t *offsets) {
-  const int64_t N = n_drawn(ctl, ncap);
+  const int64_t N = n_total(ctl, ncap, views);
   const int64_t base = (int64_t)blockIdx.x * kScanItems;
   if (base >= N) return;
   const int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
@@ -158,6 +161,52 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
       const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
       const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
       const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
+      keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
+      vals[j] = (uint32_t)i;
+    }
+  }
+}
+
+// Pairs of all views of a batch: splat record v * N + i belongs to view v;
+// the key's tile field is the view's first global tile plus its local tile.
+__global__ void __launch_bounds__(256) emit_batched_kernel(const Ctl *ctl, Splats sp, int64_t ncap, int views,
+                                                           const ViewTable *vt, const uint32_t *offsets,
+                                                           uint64_t *keys, uint32_t *vals, int64_t pair_cap) {
+  const int64_t Nv = n_drawn(ctl, ncap);
+  const int64_t N = Nv * views;
+  int64_t M = ctl->pairs;
+  if (M > pair_cap) M = pair_cap;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp0; c * 1024 < M; c += nwarps) {
+    const uint32_t j0 = (uint32_t)(c * 1024);
+    int64_t lo = 0, hi = N - 1;
+    if (lane == 0) {
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= j0) lo = mid; else hi = mid - 1;
+      }
+    }
+    int64_t i = __shfl_sync(0xffffffffu, lo, 0);
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t j = j0 + 32u * k + lane;
+      if ((int64_t)j >= M) break;
+      if (i + 1 < N && offsets[i + 1] <= j) {
+        int64_t lo2 = i + 1, step = 1;
+        while (lo2 + step < N && offsets[lo2 + step] <= j) { lo2 += step; step <<= 1; }
+        int64_t hi2 = lo2 + step < N ? lo2 + step - 1 : N - 1;
+        while (lo2 < hi2) {
+          const int64_t mid = (lo2 + hi2 + 1) >> 1;
+          if (offsets[mid] <= j) lo2 = mid; else hi2 = mid - 1;
+        }
+        i = lo2;
+      }
+      const int v = (int)(i / Nv);
+      const uint32_t q = j - offsets[i];
+      const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
+      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+      const uint32_t tile = (uint32_t)vt->tile_off[v] + (y0 + q / w) * (uint32_t)vt->gx[v] + x0 + q % w;
       keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
       vals[j] = (uint32_t)i;
     }
@@ -348,10 +397,21 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, bs);
-  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, bs);
-  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, bs, offsets);
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs);
+  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
   emit_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap, gx);
+}
+
+void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
+                              uint32_t *block_sums, uint32_t *offsets, uint64_t *keys, uint32_t *vals,
+                              int64_t pair_cap, cudaStream_t st) {
+  const int64_t nb = (ncap * views + kScanItems - 1) / kScanItems;
+  uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl, ncap, views, bs);
+  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs, offsets);
+  emit_batched_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, views, vt, offsets, keys, vals, pair_cap);
 }
 
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,

@@ -56,6 +56,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   const int ds = p->feedback_ds > 0 ? p->feedback_ds : 1;
   d.fb_pixels = (int64_t)((p->max_width + ds - 1) / ds) * ((p->max_height + ds - 1) / ds);
   d.ncap = P * s->page_size;
+  d.nviews = p->max_views > 1 ? (p->max_views < kMaxViews ? p->max_views : kMaxViews) : 1;
   d.pair_cap = p->max_pairs > 0 ? p->max_pairs : 8 * d.ncap;
   if (p->max_pairs <= 0 && d.pair_cap < (int64_t(1) << 22)) d.pair_cap = int64_t(1) << 22;
   if (d.pair_cap > (int64_t(1) << 30) - 1) d.pair_cap = (int64_t(1) << 30) - 1;
@@ -63,7 +64,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.ntri = (int64_t)s->face_page.size();
   d.nvert = (int64_t)s->verts.size() / 3;
   d.nlink = (int64_t)s->link_col.size();
-  d.scan_blocks = (d.ncap + kScanItems - 1) / kScanItems;
+  d.scan_blocks = (d.ncap * d.nviews + kScanItems - 1) / kScanItems;
   d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
   d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
@@ -79,7 +80,7 @@ Layout make_layout(const Dims &d) {
     o = al(o + (bytes > 0 ? bytes : 1));
     return r;
   };
-  const int64_t NP = d.NP, P = d.P, N = d.ncap;
+  const int64_t NP = d.NP, P = d.P, N = d.ncap * d.nviews;
   L.ctl = take(sizeof(Ctl));
   L.fb = take(8 * d.fb_pixels);
   L.req = take(4 * NP);
@@ -120,6 +121,7 @@ Layout make_layout(const Dims &d) {
   L.offsets = take(4 * N);
   L.raster_queue = take(kRasterRecord * d.raster_cap);
   L.raster_count = take(16);
+  L.raster_vis = take(4 * d.ntri);
   L.centroid = take(16 * NP);
   L.pf_flag = take(P * d.Smax);
   L.pf_mask = take((NP + 3) / 4 * 4);
@@ -132,7 +134,9 @@ Layout make_layout(const Dims &d) {
   L.keys1 = take(8 * d.pair_cap);
   L.vals0 = take(4 * d.pair_cap);
   L.vals1 = take(4 * d.pair_cap);
-  L.ranges = take(8 * d.tile_cap);
+  L.ranges = take(8 * d.tile_cap * d.nviews);
+  L.views = take(sizeof(ViewTable));
+  L.work = take(16);
   L.hist = take(4 * kMaxPasses * 256);
   L.lookback = take(4 * d.lookback_words);
   L.tile_ctr = take(4 * kMaxPasses);
@@ -248,6 +252,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   c.last_move = -1000;
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.ctl), &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "copy", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->copy_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->res_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaStreamSynchronize(st), "sync", &rc);
   if (!ok) { delete r; return rc; }
   *out = r;
@@ -285,6 +291,10 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   for (auto &t : r->spans) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   for (auto e : r->spare_events) cudaEventDestroy(e);
   if (r->copy_done) cudaEventDestroy(r->copy_done);
+  if (r->res_done) cudaEventDestroy(r->res_done);
+  if (r->graph_exec) cudaGraphExecDestroy(r->graph_exec);
+  if (r->graph) cudaGraphDestroy(r->graph);
+  if (r->pf_done) cudaEventDestroy(r->pf_done);
   delete r;
 }
 
@@ -294,6 +304,10 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t NP = r->dims.NP;
+  if (r->pf_pending) {  // a prefetch still reads the previous requests and the page table
+    cudaStreamWaitEvent(st, r->pf_done, 0);
+    r->pf_pending = false;
+  }
   cudaMemsetAsync(r->at<void>(r->lay.req), 0, 4 * NP, st);
   cudaMemsetAsync(r->at<void>(r->lay.direct), 0, NP, st);
   const int ds = r->prm.feedback_ds;
@@ -306,13 +320,14 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     launch_feedback_clear(fb, npix, st);
     launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
                            r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
-                           r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap, st);
+                           r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
+                           r->at<uint32_t>(r->lay.raster_vis), st);
     launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
                            r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
     r->last_fb_pixels = npix;
     if (c.fy > fpx) fpx = c.fy;
   }
-  r->span_end(sp_fb, 5 * n_cams, st);
+  r->span_end(sp_fb, 6 * n_cams, st);
   r->f_px = fpx;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -323,6 +338,10 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
 extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
+  if (r->pf_pending) {
+    cudaStreamWaitEvent(st, r->pf_done, 0);
+    r->pf_pending = false;
+  }
   launch_request_all(r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), r->dims.NP, st);
   r->f_px = 1.0f;
   r->state = 1;
@@ -335,6 +354,10 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   if (r->state < 1) return fail(VM3DGS_E_STATE, "update_residency before render_feedback");
   cudaStream_t st = (cudaStream_t)stream, cst = copy_stream ? (cudaStream_t)copy_stream : st;
+  if (r->pf_pending) {
+    cudaStreamWaitEvent(st, r->pf_done, 0);
+    r->pf_pending = false;
+  }
   const vm3dgs_scene *s = r->scene;
   ResidencyArgs a{};
   a.ctl = r->at<Ctl>(r->lay.ctl);
@@ -378,6 +401,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   const int sp_res = r->span_begin(VM3DGS_STAGE_RESIDENCY, st);
   launch_residency(a, st);
   r->span_end(sp_res, 1, st);
+  cudaEventRecord(r->res_done, st);
   StreamArgs sa{};
   sa.count = &a.ctl->n_copies;
   sa.copies = a.copies;

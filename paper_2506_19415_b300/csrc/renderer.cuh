@@ -46,14 +46,15 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
       face_page, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, block_sums, offsets, raster_queue, raster_count, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
-      pf_copy_seg, pf_count, pf_base, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+      splat_radius, block_sums, offsets, raster_queue, raster_count, raster_vis, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
+      pf_copy_seg, pf_count, pf_base, views, work, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
 
 struct Dims {
   int64_t NP, P, Smax, fb_pixels, ncap, pair_cap, tile_cap, ntri, nvert, nlink, scan_blocks, lookback_words;
   int ukey_cap, free_cap;
   int64_t raster_cap;
+  int64_t nviews;  // views a batch may hold (max_views)
 };
 
 Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P);
@@ -73,7 +74,7 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
 constexpr int64_t kRasterRecord = 64;
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
                             const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
-                            uint32_t qcap, cudaStream_t st);
+                            uint32_t qcap, uint32_t *vis, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
@@ -129,6 +130,22 @@ struct ProjectArgs {
 };
 void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st);
 
+// Cameras of a batched render, in device memory.
+constexpr int kMaxViews = 64;
+struct ViewTable {
+  vm3dgs_camera cam[kMaxViews];
+  int32_t tile_off[kMaxViews + 1];   // first global tile of each view
+  int32_t gx[kMaxViews];             // tiles per row
+  float *img[kMaxViews];
+  int32_t n;
+};
+void launch_project_batched(const ProjectArgs &a, const ViewTable *views, int n_views, cudaStream_t st);
+void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
+                              uint32_t *block_sums, uint32_t *offsets, uint64_t *keys, uint32_t *vals,
+                              int64_t pair_cap, cudaStream_t st);
+void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap_total,
+                          const ViewTable *vt, const float bg[3], uint32_t *work, cudaStream_t st);
+
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st);
 
@@ -163,8 +180,17 @@ struct vm3dgs_renderer {
   float f_px = 0.0f;
   cudaEvent_t copy_done = nullptr;
   bool copy_pending = false;
+  cudaEvent_t res_done = nullptr;   // recorded after each page-table update
+  cudaEvent_t pf_done = nullptr;    // recorded after a prefetch stopped reading this frame's requests
+  bool pf_pending = false;
   int64_t last_fb_pixels = 0;
   float scene_center[3] = {0, 0, 0}, scene_half = 1.0f;
+  // captured batch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphNode_t graph_views_node = nullptr;
+  vm::ViewTable graph_table{};
+  int tuned_shape[4] = {0, 0, 0, 0};
   int sorted_buf = 0;     // pair buffer (0/1) holding the last view's sorted pairs
   int last_ntiles = 0;
   // per-stage timing

@@ -8,7 +8,7 @@ vm3dgs_prefetch); torch tensors hold the dataset on the device.
 Dataset (from the renderer's own visibility feedback): for every frame t of
 a flythrough, x_t = network input of frame t (camera motion + histogram of the
 pages requested at t over the page window around the camera) and
-y_t = pages requested at t+1 over the same window.
+y_t = pages of that window requested in any of the frames t+1 .. t+horizon.
 """
 from __future__ import annotations
 
@@ -17,24 +17,29 @@ import time
 import numpy as np
 
 
-def make_dataset(v, r, paths, n_out, n_in):
+def make_dataset(v, r, paths, n_out, n_in, horizon=1):
     """Feedback-only passes over the paths; returns device tensors X, Y, M."""
     import torch
     dev = r.pool.device
     n = sum(len(p) - 1 for p in paths)
     X = torch.empty((n, n_in), dtype=torch.float32, device=dev)
-    Y = torch.empty((n, n_out), dtype=torch.float32, device=dev)
+    Y = torch.zeros((n, n_out), dtype=torch.float32, device=dev)
     M = torch.empty((n, n_out), dtype=torch.float32, device=dev)
-    base = torch.empty((len(paths) and max(len(p) for p in paths), 1), dtype=torch.int32, device=dev)
-    k = 0
+    T = max(len(p) for p in paths)
+    base = torch.empty((T, 1), dtype=torch.int32, device=dev)
+    ytmp = torch.empty((n_out,), dtype=torch.float32, device=dev)
+    k0 = 0
     for path in paths:
         for t, cam in enumerate(path):
             r.render_feedback([cam])
-            if t > 0:
-                v.vm3dgs_prefetch_labels(r, n_out, base[t - 1], Y[k], M[k])
-                k += 1
+            # frame t is within the horizon of the samples of frames t-horizon .. t-1
+            for s_ in range(max(0, t - horizon), t):
+                k = k0 + s_
+                v.vm3dgs_prefetch_labels(r, n_out, base[s_], ytmp, M[k])
+                torch.maximum(Y[k], ytmp, out=Y[k])
             if t + 1 < len(path):
-                v.vm3dgs_prefetch_features(r, n_out, cam, path[t - 1] if t > 0 else cam, X[k], base[t])
+                v.vm3dgs_prefetch_features(r, n_out, cam, path[t - 1] if t > 0 else cam, X[k0 + t], base[t])
+        k0 += len(path) - 1
     torch.cuda.synchronize()
     return X, Y, M
 
