@@ -358,6 +358,10 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
     cudaStreamWaitEvent(st, r->pf_done, 0);
     r->pf_pending = false;
   }
+  if (r->copy_pending) {  // the copy list is rewritten below: earlier copies must be done reading it
+    cudaStreamWaitEvent(st, r->copy_done, 0);
+    r->copy_pending = false;
+  }
   const vm3dgs_scene *s = r->scene;
   ResidencyArgs a{};
   a.ctl = r->at<Ctl>(r->lay.ctl);
