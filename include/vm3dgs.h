@@ -85,7 +85,7 @@ typedef struct {
 /* Renderer parameters. */
 typedef struct {
   int64_t staging_bytes;   /* bytes streamed per update at most (the staging budget) */
-  int32_t feedback_ds;     /* visibility buffer is ceil(W/ds) x ceil(H/ds) */
+  int32_t feedback_ds;     /* visibility buffer is ceil(W/ds) x ceil(H/ds); ceil(max_height/ds) <= 16000 */
   int32_t links;           /* follow page links in the reduction */
   int32_t lod;             /* choose levels by screen-space error, adapt the threshold */
   int32_t fp16_pool;       /* pool holds fp16 records (scene built with fp16 = 1) */
@@ -95,6 +95,9 @@ typedef struct {
   int32_t max_views;       /* largest n_cams passed to vm3dgs_render */
   int64_t max_pairs;       /* (Gaussian, tile) pairs per view; 0 = max(8 x pool Gaussians, 2^22) */
   float bg[3];             /* background colour */
+  int32_t separate_values; /* 0: the splat index rides in the low bits of the sort key whenever tile, depth and
+                              index bits fit in 64 (a keys-only sort); 1: always sort (key, splat) pairs.  The
+                              rendered image and the pairs read back are the same either way. */
 } vm3dgs_params;
 
 typedef struct {

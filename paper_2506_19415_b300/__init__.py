@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
     _fields_ = [("staging_bytes", c_i64), ("feedback_ds", c_i32), ("links", c_i32), ("lod", c_i32),
                 ("fp16_pool", c_i32), ("usage_lo", c_f), ("usage_hi", c_f), ("tau0", c_f), ("step0", c_f),
                 ("max_width", c_i32), ("max_height", c_i32), ("max_views", c_i32), ("max_pairs", c_i64),
-                ("bg", c_f * 3)]
+                ("bg", c_f * 3), ("separate_values", c_i32)]
 
 
 class Stats(ctypes.Structure):
@@ -309,6 +309,7 @@ class RenderConfig:
     max_views: int = 1
     max_pairs: int = 0
     bg: tuple = (0.0, 0.0, 0.0)
+    separate_values: bool = False   # True: always sort (key, splat) pairs instead of packed keys
 
     def struct(self) -> Params:
         p = Params()
@@ -316,6 +317,7 @@ class RenderConfig:
         p.fp16_pool, p.usage_lo, p.usage_hi, p.tau0, p.step0 = int(self.fp16_pool), self.usage_lo, self.usage_hi, self.tau0, self.step0
         p.max_width, p.max_height, p.max_views, p.max_pairs = self.max_width, self.max_height, self.max_views, self.max_pairs
         p.bg[:] = [float(v) for v in self.bg]
+        p.separate_values = int(self.separate_values)
         return p
 
 

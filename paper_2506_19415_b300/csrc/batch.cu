@@ -96,7 +96,7 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   int tbits = 0;
   while ((1 << tbits) < ntiles) ++tbits;
   span = timed ? r->span_begin(VM3DGS_STAGE_SORT, st) : -1;
-  const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, 32 + tbits, r->at<uint32_t>(r->lay.hist),
+  const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, 0, 32 + tbits, r->at<uint32_t>(r->lay.hist),
                               r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
                               r->at<uint32_t>(r->lay.tile_ctr), st);
   r->span_end(span, 2 + (32 + tbits + 7) / 8, st);
@@ -104,13 +104,14 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
   uint2 *ranges = r->at<uint2>(r->lay.ranges);
   span = timed ? r->span_begin(VM3DGS_STAGE_RANGES, st) : -1;
-  launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, st);
+  launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, 32, st);
   r->span_end(span, 1, st);
   span = timed ? r->span_begin(VM3DGS_STAGE_BLEND, st) : -1;
   launch_blend_batched(ranges, vals[cur], sp, r->dims.ncap * (int64_t)n, dvt, r->prm.bg,
                        r->at<uint32_t>(r->lay.work), st);
   r->span_end(span, 1, st);
   r->sorted_buf = cur;
+  r->kf = KeyFormat{32, 0, 32, 0u, false};
   r->last_ntiles = ntiles;
   return VM3DGS_OK;
 }

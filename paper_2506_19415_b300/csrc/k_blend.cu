@@ -1,68 +1,140 @@
 // Front-to-back alpha blending per image tile (Sec. 4.2: the paper blends
 // quads in hardware; the per-pixel Gaussian and the compositing rule are
-// those of Kerbl et al.).  One CTA per tile, one thread per pixel.  The
-// tile's splats are staged in shared memory in batches of one splat per
-// thread; a pixel stops when its transmittance would fall below 1e-4, the
-// CTA stops when every pixel has.  alpha = min(0.99, o exp(power)); splats
+// those of Kerbl et al.).  One CTA per tile.  The tile's splats are staged
+// in shared memory in batches; a pixel stops when its transmittance would
+// fall below 1e-4, the CTA stops when every pixel has.  alpha = min(0.99, o exp(power)); splats
 // with alpha < 1/255 are skipped; the image is C + T * background, CHW.
 #include "renderer.cuh"
 
 namespace vm {
 namespace {
 
+// Per staged splat the conic and opacity are rewritten once for the log2
+// domain: q = log2(e) * power = dx (a dx + b dy) + c dy^2 with a = -A/2 log2 e,
+// b = -B log2 e, c = -C/2 log2 e, and l = log2(opacity), so that
+// alpha = min(0.99, 2^(q + l)) and the skip test alpha < 1/255 becomes
+// q + l < log2(1/255), taken before the exponential.
+#define LOG2E 1.4426950408889634f
+#define LOG2_SKIP (-7.99435343685886f)  /* log2(1/255) */
+
+__device__ __forceinline__ void stage(const Splats &sp, uint32_t g, float4 &a, float4 &b, float &c) {
+  const float4 s0 = sp.s0[g], s1 = sp.s1[g];
+  a = make_float4(s0.x, s0.y, -0.5f * LOG2E * s0.z, -LOG2E * s0.w);
+  b = make_float4(-0.5f * LOG2E * s1.x, __log2f(s1.y), s1.z, s1.w);
+  c = sp.s2[g];
+}
+
+// Box (x0, x1, y0, y1) outside which a splat has alpha < 1/255 with a margin
+// wider than the rounding of the per-pixel test, so that skipping the pixels
+// outside changes nothing.  With conic M = [[A, B], [B, C]] the test is
+// d^T M d <= tau = 2 ln(255 o); the box of that ellipse is
+// |dx| <= sqrt(tau C / det M), |dy| <= sqrt(tau A / det M), taken here for
+// 1.01 tau + 0.05 and widened by 1% + 0.1 px.  Splats whose conic is too
+// ill-conditioned for that margin (eigenvalue ratio above 1e4) get an
+// unbounded box; those with o < 0.999 / 255 an empty one.
+__device__ __forceinline__ float4 alpha_box(const Splats &sp, uint32_t g) {
+  const float4 s0 = sp.s0[g], s1 = sp.s1[g];
+  const float A = s0.z, B = s0.w, C = s1.x, o = s1.y;
+  if (!(o * 255.0f >= 0.999f)) return make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+  const float det = A * C - B * B, m = 0.5f * (A + C);
+  const float lmax = m + sqrtf(fmaxf(m * m - det, 0.0f));
+  const float unbounded = INFINITY;
+  if (!(det > 0.0f) || !(lmax > 0.0f) || !(lmax * lmax <= 1e4f * det))
+    return make_float4(-unbounded, unbounded, -unbounded, unbounded);
+  const float tau = 2.0f * logf(255.0f * o) * 1.01f + 0.05f;
+  const float xr = sqrtf(tau * C / det) * 1.01f + 0.1f, yr = sqrtf(tau * A / det) * 1.01f + 0.1f;
+  return make_float4(s0.x - xr, s0.x + xr, s0.y - yr, s0.y + yr);
+}
+
+// one pixel against one staged splat
+__device__ __forceinline__ void blend_one(const float4 &a, const float4 &b, float c, float fx, float fy, float &T,
+                                          float &C0, float &C1, float &C2, bool &done) {
+  const float dx = a.x - fx, dy = a.y - fy;
+  const float q = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
+  if (q > 0.0f) return;
+  const float t = q + b.y;
+  if (t < LOG2_SKIP) return;
+  const float alpha = fminf(0.99f, exp2f(t));
+  const float tT = T * (1.0f - alpha);
+  if (tT < 1e-4f) { done = true; return; }
+  const float w = alpha * T;
+  C0 += b.z * w;
+  C1 += b.w * w;
+  C2 += c * w;
+  T = tT;
+}
+
+// One CTA per tile, TW*TH/2 threads.  Warp w owns the 8x8 pixel block
+// (w mod TW/8, w div TW/8) of the tile, lane l its pixels (l mod 8, l div 8)
+// and (l mod 8, l div 8 + 4); a warp passes over the staged splats whose
+// alpha box misses its block.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) blend_kernel(const uint2 *ranges, const uint32_t *vals, Splats sp,
-                                                      uint32_t ncap, vm3dgs_camera cam, float bg0, float bg1,
-                                                      float bg2, float *img) {
-  constexpr int BS = TW * TH;
+__global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, const uint32_t *vals,
+                                                          const uint64_t *packed, uint32_t idx_mask, Splats sp,
+                                                          uint32_t ncap, vm3dgs_camera cam, float bg0, float bg1,
+                                                          float bg2, float *img) {
+  static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are made of 8x8 blocks");
+  constexpr int NT = TW * TH / 2, BS = 2 * NT;
   __shared__ float4 s0[BS];
   __shared__ float4 s1[BS];
+  __shared__ float4 s3[BS];
   __shared__ float s2[BS];
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
   const int tile = blockIdx.x;
   const int tx = tile % gx, ty = tile / gx;
-  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
-  const bool inside = px < W && py < H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
+  const int px = bx + (lane & 7), py0 = by + (lane >> 3), py1 = py0 + 4;
+  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+  const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
+  // pixel centres of the warp's block
+  const float cx0 = (float)bx + 0.5f, cx1 = (float)bx + 7.5f, cy0 = (float)by + 0.5f, cy1 = (float)by + 7.5f;
   const uint2 rg = ranges[tile];
   const int n = (int)(rg.y - rg.x);
-  bool done = !inside;
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+  bool done0 = !in0, done1 = !in1;
+  float T0 = 1.0f, A0 = 0.0f, B0 = 0.0f, D0 = 0.0f;
+  float T1 = 1.0f, A1 = 0.0f, B1 = 0.0f, D1 = 0.0f;
   for (int r0 = 0; r0 < n; r0 += BS) {
-    if (__syncthreads_count(done) == BS) break;
-    const int idx = r0 + (int)threadIdx.x;
-    if (idx < n) {
-      uint32_t g = vals[rg.x + idx];
-      if (g >= ncap) g = 0;  // only after a timed-out sort
-      s0[threadIdx.x] = sp.s0[g];
-      s1[threadIdx.x] = sp.s1[g];
-      s2[threadIdx.x] = sp.s2[g];
+    if (__syncthreads_count(done0 && done1) == NT) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = (int)threadIdx.x + h * NT, idx = r0 + k;
+      if (idx < n) {
+        uint32_t g = packed ? (uint32_t)packed[rg.x + idx] & idx_mask : vals[rg.x + idx];
+        if (g >= ncap) g = 0;  // only after a timed-out sort
+        float4 a, b;
+        float c;
+        stage(sp, g, a, b, c);
+        s0[k] = a;
+        s1[k] = b;
+        s2[k] = c;
+        s3[k] = alpha_box(sp, g);
+      }
     }
     __syncthreads();
     const int cnt = min(BS, n - r0);
-    for (int j = 0; !done && j < cnt; ++j) {
-      const float4 a = s0[j];
-      const float4 b = s1[j];
-      const float dx = a.x - fx, dy = a.y - fy;
-      const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-      if (power > 0.0f) continue;
-      const float alpha = fminf(0.99f, b.y * __expf(power));
-      if (alpha < (1.0f / 255.0f)) continue;
-      const float tT = T * (1.0f - alpha);
-      if (tT < 1e-4f) { done = true; break; }
-      const float w = alpha * T;
-      C0 += b.z * w;
-      C1 += b.w * w;
-      C2 += s2[j] * w;
-      T = tT;
+    for (int j = 0; j < cnt && !(done0 && done1); ++j) {
+      const float4 bb = s3[j];
+      if (bb.y < cx0 || bb.x > cx1 || bb.w < cy0 || bb.z > cy1) continue;  // same for the whole warp
+      const float4 a = s0[j], b = s1[j];
+      const float c = s2[j];
+      if (!done0) blend_one(a, b, c, fx, fy0, T0, A0, B0, D0, done0);
+      if (!done1) blend_one(a, b, c, fx, fy1, T1, A1, B1, D1, done1);
     }
   }
-  if (inside) {
-    const int64_t HW = (int64_t)W * H, o = (int64_t)py * W + px;
-    img[o] = C0 + T * bg0;
-    img[HW + o] = C1 + T * bg1;
-    img[2 * HW + o] = C2 + T * bg2;
+  const int64_t HW = (int64_t)W * H;
+  if (in0) {
+    const int64_t o = (int64_t)py0 * W + px;
+    img[o] = A0 + T0 * bg0;
+    img[HW + o] = B0 + T0 * bg1;
+    img[2 * HW + o] = D0 + T0 * bg2;
+  }
+  if (in1) {
+    const int64_t o = (int64_t)py1 * W + px;
+    img[o] = A1 + T1 * bg0;
+    img[HW + o] = B1 + T1 * bg1;
+    img[2 * HW + o] = D1 + T1 * bg2;
   }
 }
 
@@ -107,28 +179,16 @@ __global__ void __launch_bounds__(256) blend_batched_kernel(const uint2 *ranges,
       if (idx < n) {
         uint32_t g = vals[rg.x + idx];
         if (g >= ncap) g = 0;  // only after a timed-out sort
-        s0[threadIdx.x] = sp.s0[g];
-        s1[threadIdx.x] = sp.s1[g];
-        s2[threadIdx.x] = sp.s2[g];
+        float4 a, b;
+        float c;
+        stage(sp, g, a, b, c);
+        s0[threadIdx.x] = a;
+        s1[threadIdx.x] = b;
+        s2[threadIdx.x] = c;
       }
       __syncthreads();
       const int cnt = min(BS, n - r0);
-      for (int j = 0; !done && j < cnt; ++j) {
-        const float4 a = s0[j];
-        const float4 b = s1[j];
-        const float dx = a.x - fx, dy = a.y - fy;
-        const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-        if (power > 0.0f) continue;
-        const float alpha = fminf(0.99f, b.y * __expf(power));
-        if (alpha < (1.0f / 255.0f)) continue;
-        const float tT = T * (1.0f - alpha);
-        if (tT < 1e-4f) { done = true; break; }
-        const float w = alpha * T;
-        C0 += b.z * w;
-        C1 += b.w * w;
-        C2 += s2[j] * w;
-        T = tT;
-      }
+      for (int j = 0; !done && j < cnt; ++j) blend_one(s0[j], s1[j], s2[j], fx, fy, T, C0, C1, C2, done);
     }
     if (inside) {
       float *img = vt->img[v];
@@ -149,16 +209,18 @@ void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splat
   blend_batched_kernel<<<148 * 6, 256, 0, st>>>(ranges, vals, sp, (uint32_t)ncap_total, vt, bg[0], bg[1], bg[2], work);
 }
 
-void launch_blend(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap, const vm3dgs_camera &cam,
-                  const float bg[3], float *image, cudaStream_t st) {
+void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
+                  const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
+                  cudaStream_t st) {
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w, gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
   const unsigned nt = (unsigned)(gx * gy);
+  const uint32_t nc = (uint32_t)ncap;
   if (cam.tile_w == 16 && cam.tile_h == 16)
-    blend_kernel<16, 16><<<nt, 256, 0, st>>>(ranges, vals, sp, (uint32_t)ncap, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<16, 16><<<nt, 128, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
   else if (cam.tile_w == 8 && cam.tile_h == 8)
-    blend_kernel<8, 8><<<nt, 64, 0, st>>>(ranges, vals, sp, (uint32_t)ncap, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<8, 8><<<nt, 32, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
   else
-    blend_kernel<32, 8><<<nt, 256, 0, st>>>(ranges, vals, sp, (uint32_t)ncap, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<32, 8><<<nt, 128, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
 }
 
 }  // namespace vm

@@ -12,6 +12,10 @@
 // on it if it runs up, or right when horizontal) so that shared edges cover
 // once; depth is perspective-correct z; the visibility word is
 // (bits(z) << 32) | (page + 1), minimum per pixel, all ones when empty.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "renderer.cuh"
 
 namespace vm {
@@ -38,6 +42,14 @@ struct Tri {
   uint32_t page1;
   int32_t i0, i1, j0, j1;
 };
+// A queued triangle; a huge one also carries its first band (kBand rows) in
+// the list of all queued huge triangles' bands, and its band count.
+struct QTri {
+  Tri t;
+  uint32_t band0, nband;
+};
+static_assert(sizeof(QTri) <= kRasterRecord, "raster record");
+constexpr int kBand = 4;
 
 // coverage test and depth write of pixel (i, j)
 __device__ __forceinline__ void shade(const Tri &t, const int64_t *dxe, const int64_t *dye, const bool *own,
@@ -69,12 +81,23 @@ __device__ __forceinline__ void edges(const Tri &t, int64_t *dxe, int64_t *dye, 
   *farea = __ll2float_rn(area);
 }
 
-// Snaps and orients one (clipped) triangle; small ones are rasterised by the
-// calling thread, larger ones go to the queue for whole-CTA rasterisation.
-__device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
-                          uint64_t *fb, Tri *queue, uint32_t *qcount, uint32_t qcap) {
-  // queue layout: medium triangles (17..1024 pixels) from the front, huge ones
-  // (more) from the back; qcount[0], qcount[1] count them
+// serial coverage of a whole triangle's pixel box by the calling thread
+__device__ void raster_serial(const Tri &t, int Wf, uint64_t *fb) {
+  int64_t dxe[3], dye[3];
+  bool own[3];
+  float farea;
+  edges(t, dxe, dye, own, &farea);
+  const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
+  for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, t.i0 + q % bw, t.j0 + q / bw, Wf, fb);
+}
+
+// Snaps and orients one (clipped) triangle.  Returns the number of pixels of
+// its box when the caller is to rasterise it (at most 16), 0 otherwise:
+// culled, or queued for a warp (17..1024 pixels) or a CTA (more).
+__device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
+                         uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap, Tri &t) {
+  // queue layout: medium triangles from the front (qcount[0] counts them),
+  // huge ones from the back (the 64-bit word at qcount + 2)
   int64_t X[3], Y[3];
   float Z[3];
 #pragma unroll
@@ -88,10 +111,10 @@ __device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, flo
     Z[k] = c[k].z;
   }
   int64_t area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
-  if (area == 0) return;
+  if (area == 0) return 0;
   if (area < 0) {
-    int64_t t = X[1]; X[1] = X[2]; X[2] = t;
-    t = Y[1]; Y[1] = Y[2]; Y[2] = t;
+    int64_t tmp = X[1]; X[1] = X[2]; X[2] = tmp;
+    tmp = Y[1]; Y[1] = Y[2]; Y[2] = tmp;
     float tf = Z[1]; Z[1] = Z[2]; Z[2] = tf;
   }
   int64_t xmin = min(X[0], min(X[1], X[2])), xmax = max(X[0], max(X[1], X[2]));
@@ -102,31 +125,101 @@ __device__ void setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, flo
   if (j0 < 0) j0 = 0;
   if (i1 > Wf - 1) i1 = Wf - 1;
   if (j1 > Hf - 1) j1 = Hf - 1;
-  if (i1 < i0 || j1 < j0) return;
-  Tri t;
+  if (i1 < i0 || j1 < j0) return 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) { t.X[k] = (int32_t)X[k]; t.Y[k] = (int32_t)Y[k]; t.Z[k] = Z[k]; }
   t.page1 = page1;
   t.i0 = (int32_t)i0; t.i1 = (int32_t)i1; t.j0 = (int32_t)j0; t.j1 = (int32_t)j1;
-  const int64_t bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
-  if (npx > 16) {
-    const bool huge = npx > 1024;
-    const uint32_t q = atomicAdd(qcount + (huge ? 1 : 0), 1u);
-    if (q < qcap / 2) { queue[huge ? qcap - 1 - q : q] = t; return; }
+  const int64_t npx = (i1 - i0 + 1) * (j1 - j0 + 1);
+  if (npx <= 16) return (int)npx;
+  if (npx <= 1024) {
+    const uint32_t q = atomicAdd(qcount, 1u);
+    if (q < qcap / 2) queue[q] = QTri{t, 0u, 0u};
+    else raster_serial(t, Wf, fb);  // queue full
+  } else {
+    // one 64-bit word hands out the slot (high half) and the first band (low
+    // half), so band0 grows with the slot; it stops growing when the queue is
+    // full, which keeps the band count below (qcap / 2) * (Hf / kBand + 1)
+    const uint32_t nb = (uint32_t)((j1 - j0) / kBand + 1);
+    unsigned long long *hc = reinterpret_cast<unsigned long long *>(qcount + 2);
+    unsigned long long o = *reinterpret_cast<volatile unsigned long long *>(hc);
+    bool got = false;
+    while ((uint32_t)(o >> 32) < qcap / 2) {
+      const unsigned long long seen = atomicCAS(hc, o, o + ((1ull << 32) | (unsigned long long)nb));
+      if (seen == o) { got = true; break; }
+      o = seen;
+    }
+    if (got) {
+      queue[qcap - 1 - (uint32_t)(o >> 32)] = QTri{t, (uint32_t)o, nb};
+    } else {
+      raster_serial(t, Wf, fb);  // queue full
+    }
   }
-  int64_t dxe[3], dye[3];
-  bool own[3];
-  float farea;
-  edges(t, dxe, dye, own, &farea);
-  for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, i0 + q % bw, j0 + q / bw, Wf, fb);
+  return 0;
+}
+
+// The lanes of a warp rasterise their small triangles together: each lane
+// takes one (triangle, pixel) pair of the warp's list in turn, found by a
+// binary search over the inclusive pixel counts.
+__device__ __forceinline__ void raster_warp(const Tri &mine, int npx, Tri *wtri, int Wf, uint64_t *fb) {
+  const int lane = threadIdx.x & 31;
+  wtri[lane] = mine;
+  int incl = npx;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  for (int g0 = 0; g0 < total; g0 += 32) {
+    const int g = g0 + lane;
+    // owner = number of lanes whose inclusive count is <= g
+    int L = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, min(L + s - 1, 31));
+      if (L + s <= 32 && v <= g) L += s;
+    }
+    const int L_incl = __shfl_sync(0xffffffffu, incl, min(L, 31));
+    const int L_npx = __shfl_sync(0xffffffffu, npx, min(L, 31));
+    if (g < total) {
+      const Tri &t = wtri[L];
+      const int q = g - (L_incl - L_npx);
+      const int bw = t.i1 - t.i0 + 1;
+      int64_t dxe[3], dye[3];
+      bool own[3];
+      float farea;
+      edges(t, dxe, dye, own, &farea);
+      shade(t, dxe, dye, own, farea, t.i0 + q % bw, t.j0 + q / bw, Wf, fb);
+    }
+  }
+  __syncwarp();
+}
+
+// Smallest value over the box [lo, hi] of n.p + d, and a bound on its
+// rounding error.
+__device__ __forceinline__ void box_min(const float *n, float d, const float *lo, const float *hi, float &mn,
+                                        float &err) {
+  mn = d;
+  float mag = fabsf(d);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn += fminf(n[a] * lo[a], n[a] * hi[a]);
+    mag += fabsf(n[a]) * fmaxf(fabsf(lo[a]), fabsf(hi[a]));
+  }
+  err = 1e-5f * mag + 1e-2f;
 }
 
 // Pass 1: triangles entirely behind the near plane, or entirely more than 2
 // pixels beyond one side of the buffer, cover no pixel centre; the others are
 // appended (warp-aggregated) to a dense list so that pass 2 runs without idle
-// lanes.
-__global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, const int32_t *tris, int64_t ntri,
-                                                          vm3dgs_camera cam, int ds, uint32_t *vis,
+// lanes.  Whole clusters are dropped first when their box lies, with a margin
+// larger than the rounding of either test, behind the near plane or beyond one
+// of those side planes (planes through the eye, so every triangle inside is
+// beyond it too and covers no pixel centre).
+__global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, const int32_t *tris, const Cluster *cl,
+                                                          int64_t ncl, vm3dgs_camera cam, int ds, uint32_t *vis,
                                                           uint32_t *nvis) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
@@ -134,96 +227,139 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
   const float zn = 0.2f;
   const float kr = ((float)Wf + 2.0f - cxf) / fxf, kl = (-2.0f - cxf) / fxf;
   const float kb = ((float)Hf + 2.0f - cyf) / fyf, kt = (-2.0f - cyf) / fyf;
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ntri; base += stride) {
-    const int64_t t = base + lane;
-    bool keep = false;
-    if (t < ntri) {
-      V3 c[3];
+  const float *V = cam.view;
+  // the five planes as n.p + d > 0 on the culled side
+  float pn[5][3], pd[5];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
+  for (int a = 0; a < 3; ++a) {
+    pn[0][a] = V[a] - kr * V[8 + a];        // x > kr z
+    pn[1][a] = kl * V[8 + a] - V[a];        // x < kl z
+    pn[2][a] = V[4 + a] - kb * V[8 + a];    // y > kb z
+    pn[3][a] = kt * V[8 + a] - V[4 + a];    // y < kt z
+    pn[4][a] = -V[8 + a];                   // z < zn
+  }
+  pd[0] = V[3] - kr * V[11];
+  pd[1] = kl * V[11] - V[3];
+  pd[2] = V[7] - kb * V[11];
+  pd[3] = kt * V[11] - V[7];
+  pd[4] = zn - V[11];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // one cluster per warp: every lane tests the box, then one triangle each
+  for (int64_t ci = w0; ci < ncl; ci += nw) {
+    const Cluster c = cl[ci];
+    bool live = true;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      float mn, err;
+      box_min(pn[k], pd[k], c.lo, c.hi, mn, err);
+      if (mn > err) live = false;
+    }
+    if (!live) continue;
+    const int64_t t = (int64_t)c.first + lane;
+    bool keep = false;
+    if ((uint32_t)lane < c.count) {
+      V3 q[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q[k] = to_cam(V, verts + 3 * (int64_t)tris[3 * t + k]);
       int nin = 0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) nin += c[k].z >= zn;
+      for (int k = 0; k < 3; ++k) nin += q[k].z >= zn;
       keep = nin > 0;
       if (nin == 3) {
         bool o1 = true, o2 = true, o3 = true, o4 = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          o1 = o1 && c[k].x > kr * c[k].z;
-          o2 = o2 && c[k].x < kl * c[k].z;
-          o3 = o3 && c[k].y > kb * c[k].z;
-          o4 = o4 && c[k].y < kt * c[k].z;
+          o1 = o1 && q[k].x > kr * q[k].z;
+          o2 = o2 && q[k].x < kl * q[k].z;
+          o3 = o3 && q[k].y > kb * q[k].z;
+          o4 = o4 && q[k].y < kt * q[k].z;
         }
         keep = !(o1 || o2 || o3 || o4);
       }
     }
-    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    const uint32_t km = __ballot_sync(0xffffffffu, keep);
     uint32_t off = 0;
-    if (lane == 0 && m) off = atomicAdd(nvis, (uint32_t)__popc(m));
+    if (lane == 0 && km) off = atomicAdd(nvis, (uint32_t)__popc(km));
     off = __shfl_sync(0xffffffffu, off, 0);
-    if (keep) vis[off + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t;
+    if (keep) vis[off + __popc(km & ((1u << lane) - 1u))] = (uint32_t)t;
   }
 }
 
-// Pass 2: clip, snap and rasterise the listed triangles (small ones here,
-// larger ones queued).
+// Pass 2: clip, snap and rasterise the listed triangles (small ones by the
+// warp together, larger ones queued).
 __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
                                                            const int32_t *face_page, const uint32_t *vis,
                                                            const uint32_t *nvis, vm3dgs_camera cam, int ds,
-                                                           uint64_t *fb, Tri *queue, uint32_t *qcount, uint32_t qcap) {
+                                                           uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap) {
+  __shared__ Tri s_tri[8][32];
+  Tri *wtri = s_tri[threadIdx.x >> 5];
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
   const float zn = 0.2f;
   const int64_t n = *nvis;
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-    const int64_t t = vis[q];
-    V3 c[3];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t q = base + lane;
+    Tri t0{}, t1{};
+    int n0 = 0, n1 = 0;
+    if (q < n) {
+      const int64_t t = vis[q];
+      V3 c[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
-    const uint32_t page1 = (uint32_t)(face_page[t] + 1);
-    bool inside[3];
-    int nin = 0;
+      for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
+      const uint32_t page1 = (uint32_t)(face_page[t] + 1);
+      bool inside[3];
+      int nin = 0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
-    if (nin == 3) {
-      setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
-      continue;
-    }
-    V3 poly[4];
-    int m = 0;
+      for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
+      if (nin == 3) {
+        n0 = setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t0);
+      } else {
+        // clipped against z = zn: a triangle (one vertex in front) or a quad
+        // (two), fanned from its first vertex
+        V3 poly[4];
+        int m = 0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const V3 a = c[k], b = c[(k + 1) % 3];
-      const bool ia = inside[k], ib = inside[(k + 1) % 3];
-      if (ia) poly[m++] = a;
-      if (ia != ib) {
-        const float tt = (zn - a.z) / (b.z - a.z);
-        V3 p;
-        p.x = a.x + tt * (b.x - a.x);
-        p.y = a.y + tt * (b.y - a.y);
-        p.z = zn;
-        poly[m++] = p;
+        for (int k = 0; k < 3; ++k) {
+          const V3 a = c[k], b = c[(k + 1) % 3];
+          const bool ia = inside[k], ib = inside[(k + 1) % 3];
+          if (ia) poly[m++] = a;
+          if (ia != ib) {
+            const float tt = (zn - a.z) / (b.z - a.z);
+            V3 p;
+            p.x = a.x + tt * (b.x - a.x);
+            p.y = a.y + tt * (b.y - a.y);
+            p.z = zn;
+            poly[m++] = p;
+          }
+        }
+        if (m >= 3) {
+          const V3 ta[3] = {poly[0], poly[1], poly[2]};
+          n0 = setup_tri(ta, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t0);
+        }
+        if (m == 4) {
+          const V3 tb[3] = {poly[0], poly[2], poly[3]};
+          n1 = setup_tri(tb, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t1);
+        }
       }
     }
-    for (int k = 1; k + 1 < m; ++k) {
-      V3 tri[3] = {poly[0], poly[k], poly[k + 1]};
-      setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap);
-    }
+    raster_warp(t0, n0, wtri, Wf, fb);
+    if (__any_sync(0xffffffffu, n1 > 0)) raster_warp(t1, n1, wtri, Wf, fb);
   }
 }
 
 // medium triangles: one warp each, lanes over the pixel box
-__global__ void __launch_bounds__(256) raster_medium_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
+__global__ void __launch_bounds__(256) raster_medium_kernel(const QTri *queue, const uint32_t *qcount, uint32_t qcap,
                                                             int Wf, uint64_t *fb) {
   const uint32_t n = min(qcount[0], qcap / 2);
   const int lane = threadIdx.x & 31;
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t q = w0; q < n; q += nw) {
-    const Tri t = queue[q];
+    const Tri t = queue[q].t;
     int64_t dxe[3], dye[3];
     bool own[3];
     float farea;
@@ -233,18 +369,65 @@ __global__ void __launch_bounds__(256) raster_medium_kernel(const Tri *queue, co
   }
 }
 
-// huge triangles: one CTA each, threads over the pixel box
-__global__ void __launch_bounds__(256) raster_huge_kernel(const Tri *queue, const uint32_t *qcount, uint32_t qcap,
+__device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {  // b > 0
+  return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// Huge triangles in bands of kBand rows, one band per warp task: the band's
+// triangle is the last queued one whose first band is <= the task (a
+// warp-wide search over the queue), and in each row only the pixels that can
+// pass all three edge tests (E_k >= 0, a superset of the covered centres) are
+// tested, with the same test as everywhere else.
+__global__ void __launch_bounds__(256) raster_huge_kernel(const QTri *queue, const uint32_t *qcount, uint32_t qcap,
                                                           int Wf, uint64_t *fb) {
-  const uint32_t n = min(qcount[1], qcap / 2);
-  for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
-    const Tri t = queue[qcap - 1 - q];
+  const unsigned long long hc = *reinterpret_cast<const unsigned long long *>(qcount + 2);
+  const int64_t n = min((int64_t)(hc >> 32), (int64_t)(qcap / 2));
+  if (n == 0) return;
+  const QTri *tail = queue + (qcap - 1);  // slot s at tail[-s]
+  const int64_t nbands = (int64_t)tail[-(n - 1)].band0 + tail[-(n - 1)].nband;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ea[3] = {1, 2, 0};
+  for (int64_t b = w0; b < nbands; b += nw) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+      const int64_t step = (hi - lo + 31) / 32;
+      const int64_t p = lo + lane * step;
+      const uint32_t m = __ballot_sync(0xffffffffu, p < hi && (int64_t)tail[-p].band0 <= b);
+      lo += (31 - __clz(m)) * step;
+      hi = min(hi, lo + step);
+    }
+    {
+      const int64_t p = lo + lane;
+      const uint32_t m = __ballot_sync(0xffffffffu, p < hi && (int64_t)tail[-p].band0 <= b);
+      lo += 31 - __clz(m);
+    }
+    const QTri qt = tail[-lo];
+    const Tri &t = qt.t;
     int64_t dxe[3], dye[3];
     bool own[3];
     float farea;
     edges(t, dxe, dye, own, &farea);
-    const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
-    for (int64_t p = threadIdx.x; p < npx; p += blockDim.x) shade(t, dxe, dye, own, farea, t.i0 + p % bw, t.j0 + p / bw, Wf, fb);
+    const int64_t ja = t.j0 + (b - (int64_t)qt.band0) * kBand, jb = min((int64_t)t.j1, ja + kBand - 1);
+    for (int64_t j = ja; j <= jb; ++j) {
+      // E_k(i) = A_k - B_k i at the centre of pixel (i, j)
+      const int64_t py = j * 256 + 128;
+      int64_t lo_i = t.i0, hi_i = t.i1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int64_t A = dxe[k] * (py - (int64_t)t.Y[ea[k]]) - dye[k] * (128 - (int64_t)t.X[ea[k]]);
+        const int64_t B = 256 * dye[k];
+        if (B == 0) {
+          if (A < 0) hi_i = lo_i - 1;
+        } else if (B > 0) {
+          hi_i = min(hi_i, floordiv(A, B));
+        } else {
+          lo_i = max(lo_i, -floordiv(A, -B));
+        }
+      }
+      for (int64_t i = lo_i + lane; i <= hi_i; i += 32) shade(t, dxe, dye, own, farea, i, j, Wf, fb);
+    }
   }
 }
 
@@ -290,20 +473,21 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
   clear_kernel<<<(unsigned)(b > 0 ? b : 1), 256, 0, st>>>(fb, n);
 }
 
-void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
-                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
-                            uint32_t qcap, uint32_t *vis, cudaStream_t st) {
-  if (ntri <= 0) return;
-  // qcount[0..1]: queued medium / huge triangles, qcount[2]: listed triangles
-  cudaMemsetAsync(qcount, 0, 3 * sizeof(uint32_t), st);
-  int64_t blocks = (ntri + 255) / 256;
+void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
+                            int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
+                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, cudaStream_t st) {
+  if (ntri <= 0 || ncl <= 0) return;
+  // qcount[0]: queued medium triangles, qcount[1]: listed triangles,
+  // qcount[2..3] (one 64-bit word): queued huge triangles << 32 | their bands
+  cudaMemsetAsync(qcount, 0, 4 * sizeof(uint32_t), st);
+  int64_t blocks = (ncl + 7) / 8;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, ntri, cam, ds, vis, qcount + 2);
-  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 2, cam, ds, fb,
-                                               reinterpret_cast<Tri *>(queue), qcount, qcap);
+  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, cl, ncl, cam, ds, vis, qcount + 1);
+  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 1, cam, ds, fb,
+                                               reinterpret_cast<QTri *>(queue), qcount, qcap);
   const int Wf = (cam.width + ds - 1) / ds;
-  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
-  raster_huge_kernel<<<148 * 2, 256, 0, st>>>(reinterpret_cast<const Tri *>(queue), qcount, qcap, Wf, fb);
+  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const QTri *>(queue), qcount, qcap, Wf, fb);
+  raster_huge_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const QTri *>(queue), qcount, qcap, Wf, fb);
 }
 
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
@@ -317,6 +501,40 @@ void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t
   int64_t b = (NP + 255) / 256;
   if (b > 148 * 4) b = 148 * 4;
   request_all_kernel<<<(unsigned)(b > 0 ? b : 1), 256, 0, st>>>(req, direct, NP);
+}
+
+int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri, int64_t NP,
+                       int32_t *tris_out, int32_t *face_page_out, Cluster *cl_out) {
+  // stable counting sort by page (ids outside [0, NP) sort last, together)
+  std::vector<int64_t> start((size_t)NP + 2, 0);
+  auto bucket = [&](int64_t t) { const int32_t p = face_page[t]; return (p >= 0 && p < NP) ? (int64_t)p : NP; };
+  for (int64_t t = 0; t < ntri; ++t) ++start[(size_t)bucket(t) + 1];
+  for (int64_t b = 0; b <= NP; ++b) start[(size_t)b + 1] += start[(size_t)b];
+  std::vector<int64_t> pos(start.begin(), start.end() - 1);
+  std::vector<int64_t> order((size_t)ntri);
+  for (int64_t t = 0; t < ntri; ++t) order[(size_t)pos[(size_t)bucket(t)]++] = t;
+  for (int64_t k = 0; k < ntri; ++k) {
+    const int64_t t = order[(size_t)k];
+    for (int c = 0; c < 3; ++c) tris_out[3 * k + c] = tris[3 * t + c];
+    face_page_out[k] = face_page[t];
+  }
+  int64_t ncl = 0;
+  for (int64_t b = 0; b <= NP; ++b) {
+    for (int64_t k0 = start[(size_t)b]; k0 < start[(size_t)b + 1]; k0 += 32) {
+      const int64_t k1 = std::min(k0 + 32, start[(size_t)b + 1]);
+      Cluster c;
+      for (int a = 0; a < 3; ++a) { c.lo[a] = INFINITY; c.hi[a] = -INFINITY; }
+      for (int64_t k = k0; k < k1; ++k)
+        for (int v = 0; v < 3; ++v) {
+          const float *p = verts + 3 * (int64_t)tris_out[3 * k + v];
+          for (int a = 0; a < 3; ++a) { c.lo[a] = std::min(c.lo[a], p[a]); c.hi[a] = std::max(c.hi[a], p[a]); }
+        }
+      c.first = (uint32_t)k0;
+      c.count = (uint32_t)(k1 - k0);
+      cl_out[ncl++] = c;
+    }
+  }
+  return ncl;
 }
 
 }  // namespace vm

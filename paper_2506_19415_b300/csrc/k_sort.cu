@@ -26,6 +26,7 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanPer = kScanItems / kScanThreads;   // 4
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookWindow = 8;  // look-back words read per round trip
 
 __device__ __forceinline__ int64_t n_drawn(const Ctl *c, int64_t cap) { return c->draw_gauss < cap ? c->draw_gauss : cap; }
 // splat records of all views (views x drawn)
@@ -119,31 +120,47 @@ __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *c
   }
 }
 
-// Pair emission balanced over the whole grid: warp w writes pairs
-// [1024 w, 1024 w + 1024), lane l the pairs 1024 w + 32 k + l, so stores are
+// Last index i in [0, N) with offsets[i] <= j (offsets ascending from 0),
+// found by the whole warp: each round probes 32 evenly spaced entries and
+// keeps the span between the last probe at or below j and the next one.
+__device__ __forceinline__ int64_t warp_find(const uint32_t *offsets, int64_t N, uint32_t j, int lane) {
+  int64_t lo = 0, hi = N;
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t p = lo + lane * step;
+    const bool ok = p < hi && offsets[p] <= j;
+    const uint32_t b = __ballot_sync(0xffffffffu, ok);
+    const int last = 31 - __clz(b);
+    lo += last * step;
+    hi = min(hi, lo + step);
+  }
+  const int64_t p = lo + lane;
+  const uint32_t b = __ballot_sync(0xffffffffu, p < hi && offsets[p] <= j);
+  return lo + (31 - __clz(b));
+}
+
+constexpr int kEmitChunk = 256;  // pairs per warp task
+
+// Pair emission balanced over the whole grid: warp task c writes pairs
+// [256 c, 256 c + 256), lane l the pairs 256 c + 32 k + l, so stores are
 // coalesced whatever the splat sizes.  The splat of a pair is the last one
-// whose offset is <= the pair index, found from the previous pair's splat by
-// a galloping search (runs of culled splats share one offset).
+// whose offset is <= the pair index: for the task's first pair by a
+// warp-wide search, then from the previous pair's splat by a galloping
+// search (runs of culled splats share one offset).
 __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
-                                                   uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx) {
+                                                   uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
+                                                   KeyFormat kf) {
+  const uint64_t dmax = (1ull << kf.R) - 1ull;
   const int64_t N = n_drawn(ctl, ncap);
   int64_t M = ctl->pairs;
   if (M > pair_cap) M = pair_cap;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp0; c * 1024 < M; c += nwarps) {
-    const uint32_t j0 = (uint32_t)(c * 1024);
-    // last splat with offset <= j0
-    int64_t lo = 0, hi = N - 1;
-    if (lane == 0) {
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (offsets[mid] <= j0) lo = mid; else hi = mid - 1;
-      }
-    }
-    int64_t i = __shfl_sync(0xffffffffu, lo, 0);
-    for (int k = 0; k < 32; ++k) {
+  for (int64_t c = warp0; c * kEmitChunk < M; c += nwarps) {
+    const uint32_t j0 = (uint32_t)(c * kEmitChunk);
+    int64_t i = warp_find(offsets, N, j0, lane);  // last splat with offset <= j0
+    for (int k = 0; k < kEmitChunk / 32; ++k) {
       const uint32_t j = j0 + 32u * k + lane;
       if ((int64_t)j >= M) break;
       if (i + 1 < N && offsets[i + 1] <= j) {
@@ -161,8 +178,15 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
       const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
       const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
       const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
-      keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
-      vals[j] = (uint32_t)i;
+      const uint32_t db = sp.depth[i];
+      const uint64_t doff = min((uint64_t)(db >= kf.base ? db - kf.base : 0u), dmax);
+      const uint64_t key = ((uint64_t)tile << kf.tshift) | (doff << kf.ib);
+      if (kf.packed) {
+        keys[j] = key | (uint64_t)i;
+      } else {
+        keys[j] = key;
+        vals[j] = (uint32_t)i;
+      }
     }
   }
 }
@@ -179,17 +203,10 @@ __global__ void __launch_bounds__(256) emit_batched_kernel(const Ctl *ctl, Splat
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp0; c * 1024 < M; c += nwarps) {
-    const uint32_t j0 = (uint32_t)(c * 1024);
-    int64_t lo = 0, hi = N - 1;
-    if (lane == 0) {
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (offsets[mid] <= j0) lo = mid; else hi = mid - 1;
-      }
-    }
-    int64_t i = __shfl_sync(0xffffffffu, lo, 0);
-    for (int k = 0; k < 32; ++k) {
+  for (int64_t c = warp0; c * kEmitChunk < M; c += nwarps) {
+    const uint32_t j0 = (uint32_t)(c * kEmitChunk);
+    int64_t i = warp_find(offsets, N, j0, lane);  // last splat with offset <= j0
+    for (int k = 0; k < kEmitChunk / 32; ++k) {
       const uint32_t j = j0 + 32u * k + lane;
       if ((int64_t)j >= M) break;
       if (i + 1 < N && offsets[i + 1] <= j) {
@@ -214,16 +231,16 @@ __global__ void __launch_bounds__(256) emit_batched_kernel(const Ctl *ctl, Splat
 }
 
 // ------------------------------------------------------------------ onesweep
-__global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, int passes,
-                                                        uint32_t *hist, uint32_t *lookback, int64_t max_tiles,
-                                                        uint32_t *tile_ctr) {
+__global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, int lo_bit,
+                                                        int passes, uint32_t *hist, uint32_t *lookback,
+                                                        int64_t max_tiles, uint32_t *tile_ctr) {
   __shared__ uint32_t h[kMaxPasses][256];
   const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const uint64_t k = keys[j];
+    const uint64_t k = keys[j] >> lo_bit;
     for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 255u], 1u);
   }
   __syncthreads();
@@ -264,6 +281,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+template <bool VALS>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
                                                                 uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
                                                                 const uint32_t *bases, uint32_t *status,
@@ -296,7 +314,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       const int64_t idx = t0 + (int64_t)warp * 32 * kSortItems + it * 32 + lane;
       const bool valid = idx < M;
       k[it] = valid ? kin[idx] : 0ull;
-      v[it] = valid ? vin[idx] : 0u;
+      v[it] = (VALS && valid) ? vin[idx] : 0u;
       dg[it] = valid ? (int)((k[it] >> shift) & 255u) : -1;
     }
 #pragma unroll
@@ -332,26 +350,39 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
     uint32_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_scan[w];
     s_doff[tid] = wpre + x - cnt;
-    // decoupled look-back
+    // decoupled look-back, kLookWindow predecessors per round trip: the
+    // words of tiles j, j-1, .. are read together and summed from the nearest
+    // until an inclusive one (done) or one not yet published (read again from
+    // there next round)
     uint32_t excl = 0;
     if (tile > 0) {
       int64_t j = tile - 1;
+      int spins = 0;
       for (;;) {
-        const volatile uint32_t *p = status + j * 256 + tid;
-        uint32_t w = *p;
-        int spins = 0;
-        while ((w & kFlagMask) == 0) {
+        uint32_t w[kLookWindow];
+#pragma unroll
+        for (int i = 0; i < kLookWindow; ++i)
+          w[i] = j - i >= 0 ? *(const volatile uint32_t *)(status + (j - i) * 256 + tid) : 0u;
+        int used = 0;
+        bool inc = false;
+#pragma unroll
+        for (int i = 0; i < kLookWindow; ++i) {
+          if (used != i || inc) break;
+          const uint32_t f = w[i] & kFlagMask;
+          if (f == 0) break;
+          excl += w[i] & kValMask;
+          ++used;
+          inc = f == kFlagInc;
+        }
+        if (inc) break;
+        j -= used;
+        if (used == 0) {
           if (++spins > kSpinLimit) {
             atomicCAS(&ctl->status, 0, VM3DGS_E_TIMEOUT);
-            w = kFlagInc;
             break;
           }
           __nanosleep(32);
-          w = *p;
         }
-        excl += w & kValMask;
-        if ((w & kFlagMask) == kFlagInc) break;
-        --j;
       }
       *st = kFlagInc | ((excl + cnt) & kValMask);
     }
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       if (d < 0) continue;
       const uint32_t pos = s_doff[d] + s_wc[warp * 256 + d] + rk[it];
       s_keys[pos] = k[it];
-      s_vals[pos] = v[it];
+      if (VALS) s_vals[pos] = v[it];
     }
     __syncthreads();
     const int nvalid = (int)((M - t0) < kSortTile ? (M - t0) : kSortTile);
@@ -373,34 +404,36 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       const uint32_t o = s_glob[d] + (uint32_t)i - s_doff[d];
       if ((int64_t)o < M) {  // always true unless a look-back wait timed out
         kout[o] = key;
-        vout[o] = s_vals[i];
+        if (VALS) vout[o] = s_vals[i];
       }
     }
     __syncthreads();
   }
 }
 
-__global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, uint2 *ranges, uint32_t ntiles) {
+__global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, uint2 *ranges, uint32_t ntiles,
+                              int tshift) {
   const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const uint32_t t = (uint32_t)(keys[j] >> 32);
+    const uint64_t t = keys[j] >> tshift;
     if (t >= ntiles) continue;  // only after a timed-out sort
-    if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = (uint32_t)j;
-    if (j == M - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = (uint32_t)(j + 1);
+    if (j == 0 || (keys[j - 1] >> tshift) != t) ranges[t].x = (uint32_t)j;
+    if (j == M - 1 || (keys[j + 1] >> tshift) != t) ranges[t].y = (uint32_t)(j + 1);
   }
 }
 
 }  // namespace
 
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
-                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st) {
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
+                      cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
   scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs);
   scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
-  emit_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap, gx);
+  emit_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap, gx, kf);
 }
 
 void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
@@ -414,36 +447,45 @@ void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int view
   emit_batched_kernel<<<148 * 8, 256, 0, st>>>(ctl, sp, ncap, views, vt, offsets, keys, vals, pair_cap);
 }
 
-int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,
-                uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st) {
-  const int passes = (bits + 7) / 8;
+int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
+                uint32_t *hist, uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st) {
+  const int passes = (hi_bit - lo_bit + 7) / 8;
+  if (passes < 1 || passes > kMaxPasses || lo_bit < 0) return -1;
   static bool attr_set = false;
   const int smem = kSortTile * 12 + (kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -2;
     attr_set = true;
   }
   cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
   const int64_t max_tiles = (pair_cap + kSortTile - 1) / kSortTile;
   if ((int64_t)passes * max_tiles * 256 > lookback_words) return -1;
-  sort_hist_kernel<<<148 * 4, 256, 0, st>>>(ctl, keys[0], pair_cap, passes, hist, lookback, max_tiles, tile_ctr);
+  sort_hist_kernel<<<148 * 4, 256, 0, st>>>(ctl, keys[0], pair_cap, lo_bit, passes, hist, lookback, max_tiles, tile_ctr);
   sort_bases_kernel<<<1, 256, 0, st>>>(hist, passes);
   int grid = 148 * 4;
   if (grid > max_tiles) grid = (int)(max_tiles > 0 ? max_tiles : 1);
   int cur = 0;
   for (int d = 0; d < passes; ++d) {
     const int64_t lb_off = (int64_t)d * max_tiles * 256;
-    onesweep_kernel<<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], pair_cap,
-                                                       8 * d, hist + d * 256, lookback + lb_off, tile_ctr + d);
+    if (vals[0])
+      onesweep_kernel<true><<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
+                                                              pair_cap, lo_bit + 8 * d, hist + d * 256,
+                                                              lookback + lb_off, tile_ctr + d);
+    else
+      onesweep_kernel<false><<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], nullptr, keys[cur ^ 1], nullptr,
+                                                               pair_cap, lo_bit + 8 * d, hist + d * 256,
+                                                               lookback + lb_off, tile_ctr + d);
     cur ^= 1;
   }
   return cur;
 }
 
-void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, cudaStream_t st) {
+void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, int tshift,
+                   cudaStream_t st) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
-  ranges_kernel<<<148 * 8, 256, 0, st>>>(ctl, keys, pair_cap, ranges, (uint32_t)ntiles);
+  ranges_kernel<<<148 * 8, 256, 0, st>>>(ctl, keys, pair_cap, ranges, (uint32_t)ntiles, tshift);
 }
 
 }  // namespace vm

@@ -2,6 +2,7 @@
 // memory and the three frame calls (page determination, page-table update
 // with streaming, rendering).  Every step runs in the kernels of this
 // library; the host only validates arguments and enqueues work.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -66,6 +67,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.nlink = (int64_t)s->link_col.size();
   d.scan_blocks = (d.ncap * d.nviews + kScanItems - 1) / kScanItems;
   d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
+  d.ncl_cap = (d.ntri + 31) / 32 + d.NP + 1;
   d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
@@ -107,6 +109,7 @@ Layout make_layout(const Dims &d) {
   L.verts = take(12 * d.nvert);
   L.tris = take(12 * d.ntri);
   L.face_page = take(4 * d.ntri);
+  L.clusters = take((int64_t)sizeof(Cluster) * d.ncl_cap);
   L.link_ptr = take(8 * (NP + 1));
   L.link_col = take(4 * d.nlink);
   L.err = take(4 * NP * kMaxLevels);
@@ -186,6 +189,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   if (p->feedback_ds < 1 || p->max_width < 1 || p->max_height < 1 || p->staging_bytes < 0 ||
       !(p->usage_lo >= 0) || !(p->usage_hi >= p->usage_lo) || !(p->tau0 >= 0) || !(p->step0 > 0))
     return fail(VM3DGS_E_INVAL, "bad renderer parameters");
+  if ((p->max_height + p->feedback_ds - 1) / p->feedback_ds > 16000)
+    return fail(VM3DGS_E_INVAL, "feedback buffer taller than 16000 rows (max_height / feedback_ds)");
   if (s->m(s->levels - 1) % 4 != 0) return fail(VM3DGS_E_INVAL, "smallest level page must hold a multiple of 4");
   int64_t slot;
   int rc = vm3dgs_pool_slot_bytes(s, p->fp16_pool, &slot);
@@ -231,8 +236,26 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   // static scene arrays
   bool ok = true;
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.verts), s->verts.data(), 4 * s->verts.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
-  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.tris), s->tris.data(), 4 * s->tris.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
-  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.face_page), s->face_page.data(), 4 * s->face_page.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
+  {
+    // proxy triangles regrouped by page, in clusters for the frustum test
+    std::vector<int32_t> tp(s->tris.size()), fp(s->face_page.size());
+    std::vector<Cluster> cl((size_t)d.ncl_cap);
+    r->ncl = build_clusters(s->verts.data(), s->tris.data(), s->face_page.data(), d.ntri, d.NP, tp.data(), fp.data(),
+                            cl.data());
+    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.tris), tp.data(), 4 * tp.size(), cudaMemcpyHostToDevice), "copy", &rc);
+    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.face_page), fp.data(), 4 * fp.size(), cudaMemcpyHostToDevice), "copy", &rc);
+    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.clusters), cl.data(), sizeof(Cluster) * (size_t)r->ncl,
+                                  cudaMemcpyHostToDevice), "copy", &rc);
+  }
+  // a box around every page's sphere (centroid, radius), hence around every
+  // Gaussian mean of every level: it bounds the depth of any splat
+  for (int a = 0; a < 3; ++a) { r->gbox_lo[a] = 0.0; r->gbox_hi[a] = 0.0; }
+  for (int64_t p2 = 0; p2 < d.NP; ++p2)
+    for (int a = 0; a < 3; ++a) {
+      const double c = s->centroid[4 * p2 + a], rad = s->centroid[4 * p2 + 3];
+      if (p2 == 0 || c - rad < r->gbox_lo[a]) r->gbox_lo[a] = c - rad;
+      if (p2 == 0 || c + rad > r->gbox_hi[a]) r->gbox_hi[a] = c + rad;
+    }
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.link_ptr), s->link_ptr.data(), 8 * s->link_ptr.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
   if (!s->link_col.empty())
     ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.link_col), s->link_col.data(), 4 * s->link_col.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
@@ -319,7 +342,7 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     uint64_t *fb = r->at<uint64_t>(r->lay.fb);
     launch_feedback_clear(fb, npix, st);
     launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
-                           r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
+                           r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
                            r->at<uint32_t>(r->lay.raster_vis), st);
     launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
@@ -437,6 +460,44 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   return VM3DGS_OK;
 }
 
+namespace {
+int bit_length(uint64_t x) {
+  int b = 0;
+  while (x) { ++b; x >>= 1; }
+  return b;
+}
+
+// Key layout for one view: the depth field spans bits(0.2f) .. bits(far),
+// far bounding the view depth of every Gaussian mean (box corners, plus a
+// margin above the rounding of the device's depth); splat indices are packed
+// below it when tile, depth and index bits fit in 64.
+KeyFormat key_format(const vm3dgs_renderer *r, const vm3dgs_camera &c, int tbits) {
+  const float *V = c.view;
+  double far = -1e300, mag = std::fabs((double)V[11]);
+  for (int k = 0; k < 8; ++k) {
+    double z = V[11];
+    for (int a = 0; a < 3; ++a) z += (double)V[8 + a] * ((k >> a) & 1 ? r->gbox_hi[a] : r->gbox_lo[a]);
+    far = std::max(far, z);
+  }
+  for (int a = 0; a < 3; ++a)
+    mag += std::fabs((double)V[8 + a]) * std::max(std::fabs(r->gbox_lo[a]), std::fabs(r->gbox_hi[a]));
+  far += 1e-3 * (1.0 + mag);
+  KeyFormat kf{};
+  uint32_t base_bits, far_bits;
+  const float near = 0.2f;
+  std::memcpy(&base_bits, &near, 4);
+  const float farf = far > 3.0e38 ? 3.0e38f : (float)far;
+  std::memcpy(&far_bits, &farf, 4);
+  kf.base = base_bits;
+  kf.R = farf > near ? std::max(1, bit_length((uint64_t)(far_bits - base_bits))) : 1;
+  const int ib = bit_length((uint64_t)(r->dims.ncap > 1 ? r->dims.ncap - 1 : 1));
+  kf.packed = !r->prm.separate_values && tbits + kf.R + ib <= 64;
+  kf.ib = kf.packed ? ib : 0;
+  kf.tshift = kf.R + kf.ib;
+  return kf;
+}
+}  // namespace
+
 extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int32_t n_cams, float *const *images,
                              void *stream) {
   if (!r || !images) return fail(VM3DGS_E_INVAL, "null argument");
@@ -478,24 +539,29 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     launch_project(pa, c, st);
     r->span_end(t, 1, st);
     t = r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st);
+    const KeyFormat kf = key_format(r, c, tbits);
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), r->at<uint32_t>(r->lay.offsets),
-                     keys[0], vals[0], r->dims.pair_cap, gx, st);
+                     keys[0], vals[0], r->dims.pair_cap, gx, kf, st);
     r->span_end(t, 4, st);
-    const int bits = 32 + tbits;
+    const int lo_bit = kf.ib, hi_bit = kf.tshift + tbits;
+    uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
-    const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, bits, r->at<uint32_t>(r->lay.hist),
-                                r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
+    const int cur = launch_sort(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
+                                r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
                                 r->at<uint32_t>(r->lay.tile_ctr), st);
-    r->span_end(t, 2 + (bits + 7) / 8, st);
+    r->span_end(t, 2 + (hi_bit - lo_bit + 7) / 8, st);
     if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
     if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
     uint2 *ranges = r->at<uint2>(r->lay.ranges);
     t = r->span_begin(VM3DGS_STAGE_RANGES, st);
-    launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, st);
+    launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, kf.tshift, st);
     r->span_end(t, 1, st);
     t = r->span_begin(VM3DGS_STAGE_BLEND, st);
-    launch_blend(ranges, vals[cur], sp, r->dims.ncap, c, r->prm.bg, images[v], st);
+    const uint32_t idx_mask = kf.ib >= 32 ? 0xFFFFFFFFu : (uint32_t)((1ull << kf.ib) - 1ull);
+    launch_blend(ranges, vals[cur], kf.packed ? keys[cur] : nullptr, idx_mask, sp, r->dims.ncap, c, r->prm.bg,
+                 images[v], st);
     r->span_end(t, 1, st);
+    r->kf = kf;
     r->sorted_buf = cur;
     r->last_ntiles = ntiles;
   }
@@ -595,8 +661,37 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
     }
     case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(L.splat_depth); n = 4 * N; break;
     case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(L.splat_radius); n = 4 * N; break;
-    case VM3DGS_DBG_KEYS: src = r->at<void>(r->sorted_buf ? L.keys1 : L.keys0); n = 8 * M; break;
-    case VM3DGS_DBG_VALUES: src = r->at<void>(r->sorted_buf ? L.vals1 : L.vals0); n = 4 * M; break;
+    case VM3DGS_DBG_KEYS:
+    case VM3DGS_DBG_VALUES: {
+      // the sorted pairs as (tile << 32 | bits(depth), splat), whatever the
+      // key layout of the last sort
+      n = (what == VM3DGS_DBG_KEYS ? 8 : 4) * M;
+      if (needed) *needed = n;
+      if (!dst) return VM3DGS_OK;
+      if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
+      const KeyFormat kf = r->kf;
+      std::vector<uint64_t> k(M);
+      if (M && !cuda_ok(cudaMemcpy(k.data(), r->at<void>(r->sorted_buf ? L.keys1 : L.keys0), 8 * M,
+                                   cudaMemcpyDeviceToHost), "debug", &rc))
+        return rc;
+      if (what == VM3DGS_DBG_VALUES && !kf.packed) {
+        if (M && !cuda_ok(cudaMemcpy(dst, r->at<void>(r->sorted_buf ? L.vals1 : L.vals0), 4 * M,
+                                     cudaMemcpyDeviceToHost), "debug", &rc))
+          return rc;
+        return VM3DGS_OK;
+      }
+      const uint64_t dmask = (1ull << kf.R) - 1ull, imask = (1ull << kf.ib) - 1ull;
+      for (int64_t j = 0; j < M; ++j) {
+        if (what == VM3DGS_DBG_VALUES) {
+          ((uint32_t *)dst)[j] = (uint32_t)(k[j] & imask);
+        } else {
+          const uint64_t tile = k[j] >> kf.tshift;
+          const uint32_t db = (uint32_t)(((k[j] >> kf.ib) & dmask) + kf.base);
+          ((uint64_t *)dst)[j] = (tile << 32) | db;
+        }
+      }
+      return VM3DGS_OK;
+    }
     case VM3DGS_DBG_RANGES: src = r->at<void>(L.ranges); n = 8 * (int64_t)r->last_ntiles; break;
     case VM3DGS_DBG_SPLAT_XY:
     case VM3DGS_DBG_SPLAT_CONIC:

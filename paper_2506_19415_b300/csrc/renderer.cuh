@@ -45,7 +45,7 @@ struct Splats {
 struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
-      face_page, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
+      face_page, clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
       splat_radius, block_sums, offsets, raster_queue, raster_count, raster_vis, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
       pf_copy_seg, pf_count, pf_base, views, work, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
@@ -54,6 +54,7 @@ struct Dims {
   int64_t NP, P, Smax, fb_pixels, ncap, pair_cap, tile_cap, ntri, nvert, nlink, scan_blocks, lookback_words;
   int ukey_cap, free_cap;
   int64_t raster_cap;
+  int64_t ncl_cap;  // proxy clusters (at most 32 triangles of one page each)
   int64_t nviews;  // views a batch may hold (max_views)
 };
 
@@ -69,12 +70,24 @@ constexpr int64_t kCopySeg = 65536;
 
 // ----- launchers (one per kernel family)
 void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
+// A run of at most 32 consecutive proxy triangles of one page with the
+// axis-aligned box of their vertices (world units).
+struct Cluster {
+  float lo[3];
+  uint32_t first;
+  float hi[3];
+  uint32_t count;
+};
+// Groups the triangles by page (stable), in clusters of at most 32; fills the
+// permuted triangle and face-page arrays and the clusters, returns their count.
+int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri, int64_t NP,
+                       int32_t *tris_out, int32_t *face_page_out, Cluster *cl_out);
 // large triangles (more than 16 pixels) are queued: queue holds qcap records of
-// kRasterRecord bytes, qcount is one device word
+// kRasterRecord bytes, qcount is four device words (16 bytes, 8-aligned)
 constexpr int64_t kRasterRecord = 64;
-void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri,
-                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue, uint32_t *qcount,
-                            uint32_t qcap, uint32_t *vis, cudaStream_t st);
+void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
+                            int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
+                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
@@ -146,21 +159,39 @@ void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int view
 void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap_total,
                           const ViewTable *vt, const float bg[3], uint32_t *work, cudaStream_t st);
 
+// Sort key of the single-view path (all fields unsigned):
+//   key = tile << tshift | min(bits(depth) - base, 2^R - 1) << ib | (packed ? splat : 0)
+// with depth > 0.2 for every drawn splat.  With base = bits(0.2f) and R wide
+// enough for the farthest possible depth, the depth field orders exactly like
+// the float bits; packed keys carry the splat index in their low ib bits and
+// need no value array (emission order is splat order, and the sort is stable).
+struct KeyFormat {
+  int tshift, ib, R;
+  uint32_t base;
+  bool packed;
+};
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
-                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, cudaStream_t st);
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
+                      cudaStream_t st);
 
 // sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
 // returns the index (0 or 1) of the buffer holding the result
-int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int bits, uint32_t *hist,
-                uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
+// Stable LSD sort of the pairs on key bits [lo_bit, hi_bit); vals[0] null
+// sorts the keys alone.  Returns the buffer holding the result.
+int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
+                uint32_t *hist, uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
 
-void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, cudaStream_t st);
+void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, int tshift,
+                   cudaStream_t st);
 
 void launch_prefetch_features(const vm3dgs_renderer *r, int n_out, const vm3dgs_camera &cam,
                               const vm3dgs_camera &prev, float *x, int32_t *base, cudaStream_t st);
 
-void launch_blend(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap, const vm3dgs_camera &cam,
-                  const float bg[3], float *image, cudaStream_t st);
+// The splat of pair j is vals[j], or the low bits (idx_mask) of packed[j]
+// when packed is not null.
+void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
+                  const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
+                  cudaStream_t st);
 
 }  // namespace vm
 
@@ -184,6 +215,9 @@ struct vm3dgs_renderer {
   cudaEvent_t pf_done = nullptr;    // recorded after a prefetch stopped reading this frame's requests
   bool pf_pending = false;
   int64_t last_fb_pixels = 0;
+  int64_t ncl = 0;  // proxy clusters in use
+  double gbox_lo[3] = {0, 0, 0}, gbox_hi[3] = {0, 0, 0};  // holds every Gaussian mean
+  vm::KeyFormat kf{32, 0, 32, 0u, false};  // of the last sort
   float scene_center[3] = {0, 0, 0}, scene_half = 1.0f;
   // captured batch
   cudaGraph_t graph = nullptr;

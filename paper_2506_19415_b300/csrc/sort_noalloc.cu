@@ -86,7 +86,7 @@ extern "C" int vm3dgs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev,
   if (n > 1) {
     uint64_t *keys[2] = {keys_dev, reinterpret_cast<uint64_t *>(base + kOffKeys)};
     uint32_t *vals[2] = {vals_dev, reinterpret_cast<uint32_t *>(base + kOffVals)};
-    const int cur = launch_sort(ctl, keys, vals, n, key_bits, reinterpret_cast<uint32_t *>(base + kOffHist),
+    const int cur = launch_sort(ctl, keys, vals, n, 0, key_bits, reinterpret_cast<uint32_t *>(base + kOffHist),
                                 reinterpret_cast<uint32_t *>(base + kOffLook), kLookbackWords,
                                 reinterpret_cast<uint32_t *>(base + kOffTiles), st);
     if (cur < 0) return fail(VM3DGS_E_CUDA, "sort launch refused");

@@ -20,10 +20,10 @@ def v():
     return mod
 
 
-def _full_render(v, raw, sc, cam, fp16=False):
+def _full_render(v, raw, sc, cam, fp16=False, separate_values=False):
     scene = import_scene(v, raw, sc, fp16=fp16)
     cfg = v.RenderConfig(max_width=cam.width, max_height=cam.height, lod=False, staging_bytes=1 << 40,
-                         fp16_pool=fp16)
+                         fp16_pool=fp16, separate_values=separate_values)
     r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
     r.request_all()
     r.update_residency()
@@ -33,19 +33,22 @@ def _full_render(v, raw, sc, cam, fp16=False):
     return r, img, st
 
 
+# the last two sort (key, splat) pairs instead of keys with the splat packed in
 CAMS = [
-    ("tiny_16x16", dict()),
-    ("tiny_8x8", dict(tile=(8, 8))),
-    ("tiny_32x8", dict(tile=(32, 8))),
-    ("ragged_250x131", dict(width=250, height=131)),
+    ("tiny_16x16", dict(), False),
+    ("tiny_8x8", dict(tile=(8, 8)), False),
+    ("tiny_32x8", dict(tile=(32, 8)), False),
+    ("ragged_250x131", dict(width=250, height=131), False),
+    ("tiny_16x16_pairs", dict(), True),
+    ("ragged_250x131_8x8_pairs", dict(width=250, height=131, tile=(8, 8)), True),
 ]
 
 
-@pytest.mark.parametrize("name,kw", CAMS)
-def test_full_scene_render_parity(v, name, kw):
+@pytest.mark.parametrize("name,kw,sep", CAMS)
+def test_full_scene_render_parity(v, name, kw, sep):
     raw, sc = tiny_scene()
     cam = scenegen.tiny_camera(**kw)
-    r, img, st = _full_render(v, raw, sc, cam)
+    r, img, st = _full_render(v, raw, sc, cam, separate_values=sep)
     g, vid = oracle.full_scene(sc)
     ref = oracle.render(g, vid, cam)
     pr = ref["proj"]
