@@ -265,7 +265,12 @@ enum {
   VM3DGS_DBG_SPLAT_XY = 16,  /* float [N][2] centre */
   VM3DGS_DBG_SPLAT_CONIC = 17, /* float [N][4] (A, B, C, opacity) */
   VM3DGS_DBG_SPLAT_RGB = 18, /* float [N][3] */
-  VM3DGS_DBG_POOL = 19       /* the pool bytes */
+  VM3DGS_DBG_POOL = 19,      /* the pool bytes */
+  VM3DGS_DBG_RASTER = 20,    /* uint32 [5] of the last feedback view: triangles queued for a warp, triangles left
+                                in front of the near plane by the frustum test, their bands of 4 rows and the huge
+                                triangles queued (one 64-bit word), triangles crossing the near plane */
+  VM3DGS_DBG_SPLAT_TMASK = 21 /* uint64 [N] tiles of the rectangle (row-major bits) met by the 3-sigma ellipse,
+                                all ones when the rectangle has more than 64 tiles, 0 if culled */
 };
 int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *host_dst, int64_t bytes, int64_t *needed, void *stream);
 

@@ -90,12 +90,12 @@ def project(g, cam):
     pos, scale, rot = _c(g["pos"], np.float32), _c(g["scale"], np.float32), _c(g["rot"], np.float32)
     op, sh = _c(g["opacity"], np.float32), _c(g["sh"], np.float32)
     out = dict(vis=np.zeros(n, np.uint8), radius=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
-               depth=np.zeros(n, np.float32), touched=np.zeros(n, np.int32), centre=np.zeros((n, 2)),
-               conic=np.zeros((n, 3)), rgb=np.zeros((n, 3)))
+               depth=np.zeros(n, np.float32), touched=np.zeros(n, np.int32), tmask=np.zeros(n, np.uint64),
+               centre=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=np.zeros((n, 3)))
     c = vo_camera(cam)
     lib().vo_project(ctypes.c_int64(n), _p(pos), _p(scale), _p(rot), _p(op), _p(sh), ctypes.c_int(K), ctypes.byref(c),
                      _p(out["vis"]), _p(out["radius"]), _p(out["rect"]), _p(out["depth"]), _p(out["touched"]),
-                     _p(out["centre"]), _p(out["conic"]), _p(out["rgb"]))
+                     _p(out["tmask"]), _p(out["centre"]), _p(out["conic"]), _p(out["rgb"]))
     return out
 
 
@@ -109,8 +109,9 @@ def bin_sort(pr, vid, cam):
     keys = np.zeros(max(M, 1), np.uint64)
     idx = np.zeros(max(M, 1), np.int64)
     vid = _c(vid, np.int64)
-    m = lib().vo_bin_sort(ctypes.c_int64(len(vid)), _p(pr["vis"]), _p(pr["rect"]), _p(pr["depth"]), _p(vid),
-                          ctypes.c_int(gx), _p(keys), _p(idx), ctypes.c_int64(len(keys)))
+    m = lib().vo_bin_sort(ctypes.c_int64(len(vid)), _p(pr["vis"]), _p(pr["rect"]), _p(pr["touched"]),
+                          _p(pr["tmask"]), _p(pr["depth"]), _p(vid), ctypes.c_int(gx), _p(keys), _p(idx),
+                          ctypes.c_int64(len(keys)))
     assert m == M
     return keys[:M], idx[:M]
 

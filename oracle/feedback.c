@@ -20,8 +20,10 @@
  *    round-half-even; coverage uses 64-bit integer edge functions at pixel
  *    centres (i+1/2, j+1/2) with a top-left style ownership rule so that an
  *    edge shared by two triangles covers each pixel once; both windings draw;
- *  - depth at a covered pixel is the perspective-correct z,
- *    1 / (b0/z0 + b1/z1 + b2/z2) with b_k = float(E_k) / float(E_sum);
+ *  - depth at a covered pixel is the perspective-correct z: 1/z is affine
+ *    in screen space, so with w_k = 1/z_k per vertex,
+ *    z = float(E_sum) / ((float(E_0) w_0 + float(E_1) w_1) + float(E_2) w_2),
+ *    E_sum = E_0 + E_1 + E_2 being twice the snapped area;
  *  - the buffer keeps, per pixel, the minimum of (bits(z) << 32) | (page+1),
  *    faces without a page writing 0 in the low word (they occlude but
  *    request nothing); an untouched pixel holds all ones;
@@ -103,6 +105,7 @@ static void raster_tri(const v3 *c, uint32_t page1, float fxf, float fyf, float 
   int own[3];
   for (int k = 0; k < 3; ++k) own[k] = owns(X[eb[k]] - X[ea[k]], Y[eb[k]] - Y[ea[k]]);
   const float farea = (float)area;
+  const float w0 = 1.0f / Z[0], w1 = 1.0f / Z[1], w2 = 1.0f / Z[2];
   for (int64_t j = j0; j <= j1; ++j)
     for (int64_t i = i0; i <= i1; ++i) {
       int64_t px = i * 256 + 128, py = j * 256 + 128;
@@ -114,9 +117,8 @@ static void raster_tri(const v3 *c, uint32_t page1, float fxf, float fyf, float 
         if (!(E[k] > 0 || (E[k] == 0 && own[k]))) { in = 0; break; }
       }
       if (!in) continue;
-      float b0 = (float)E[0] / farea, b1 = (float)E[1] / farea, b2 = (float)E[2] / farea;
-      float s = (b0 / Z[0] + b1 / Z[1]) + b2 / Z[2];
-      float zp = 1.0f / s;
+      float s = ((float)E[0] * w0 + (float)E[1] * w1) + (float)E[2] * w2;
+      float zp = farea / s;
       uint64_t key = ((uint64_t)fbits(zp) << 32) | page1;
       uint64_t *dst = buf + j * Wf + i;
       if (key < *dst) *dst = key;

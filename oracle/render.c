@@ -21,6 +21,14 @@
  *
  * Tie order of the sort: (tile, depth bits, virtual Gaussian id), the id
  * being page * page_size + slot of the level the page is drawn at.
+ *
+ * Tiles of a splat.  The 3-sigma rectangle bounds the circle of radius r
+ * around the centre; of a rectangle of at most 64 tiles, a splat covers only
+ * the tiles whose pixel centres' bounding box meets its 3-sigma ellipse
+ * d^T conic d <= 9 (conic in FP32 as above; the minimum of the quadratic over
+ * the box is taken on its edges, each a clamped one-dimensional minimum, in
+ * the order written in meets()).  Larger rectangles keep all their tiles.
+ * The kept tiles are a 64-bit mask over the rectangle in row-major order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -37,6 +45,32 @@ typedef struct {
 } vo_camera;
 
 static uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* Does the box [xl, xh] x [yl, yh] (pixel centres) meet the ellipse
+ * q(d) = ia dx^2 + 2 ib dx dy + ic dy^2 <= 9 around (pu, pv)?  FP32 spec;
+ * ria = 1/ia and ric = 1/ic give the stationary points of the edges. */
+static int meets(float pu, float pv, float ia, float ib, float ic, float ria, float ric, float xl, float xh, float yl,
+                 float yh) {
+  const float dxl = xl - pu, dxh = xh - pu, dyl = yl - pv, dyh = yh - pv;
+  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return 1;
+  const float b2 = 2.0f * ib;
+  float best = 3.0e38f;
+  for (int k = 0; k < 2; ++k) { /* edges dx = e, dy in [dyl, dyh] */
+    const float e = k ? dxh : dxl;
+    float t = -(ib * e) * ric;
+    t = t < dyl ? dyl : (t > dyh ? dyh : t);
+    const float f = ((ia * e) * e + (b2 * e) * t) + (ic * t) * t;
+    if (f < best) best = f;
+  }
+  for (int k = 0; k < 2; ++k) { /* edges dy = e, dx in [dxl, dxh] */
+    const float e = k ? dyh : dyl;
+    float t = -(ib * e) * ria;
+    t = t < dxl ? dxl : (t > dxh ? dxh : t);
+    const float f = ((ia * t) * t + (b2 * t) * e) + (ic * e) * e;
+    if (f < best) best = f;
+  }
+  return best <= 9.0f;
+}
 
 /* real spherical harmonics up to degree 3, constants from their definition
  * N_lm = sqrt((2l+1)/(4 pi) * (l-|m|)!/(l+|m|)!) with the sqrt(2) of the real
@@ -79,13 +113,13 @@ void vo_sh_basis(int64_t n, const double *dirs, double *out) {
  */
 void vo_project(int64_t n, const float *pos, const float *scale, const float *rot, const float *opac,
                 const float *sh, int K, const vo_camera *cam, uint8_t *vis, float *radius, int32_t *rect,
-                float *depth, int32_t *touched, double *centre, double *conic, double *rgb) {
+                float *depth, int32_t *touched, uint64_t *tmask, double *centre, double *conic, double *rgb) {
   const float *V = cam->view;
   const int gx = (cam->width + cam->tile_w - 1) / cam->tile_w;
   const int gy = (cam->height + cam->tile_h - 1) / cam->tile_h;
   const float TW = (float)cam->tile_w, TH = (float)cam->tile_h;
   for (int64_t i = 0; i < n; ++i) {
-    vis[i] = 0; radius[i] = 0; touched[i] = 0; depth[i] = 0;
+    vis[i] = 0; radius[i] = 0; touched[i] = 0; depth[i] = 0; tmask[i] = 0;
     rect[4 * i + 0] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
     const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     const float o = opac[i];
@@ -151,7 +185,29 @@ void vo_project(int64_t n, const float *pos, const float *scale, const float *ro
     radius[i] = r;
     rect[4 * i + 0] = x0; rect[4 * i + 1] = y0; rect[4 * i + 2] = x1; rect[4 * i + 3] = y1;
     depth[i] = tz;
-    touched[i] = (x1 - x0) * (y1 - y0);
+    /* ---- fp32 spec: conic and the tiles the 3-sigma ellipse meets */
+    {
+      const float ia = c / det, ib = -b / det, ic = a / det;
+      const float ria = 1.0f / ia, ric = 1.0f / ic;
+      const int area = (x1 - x0) * (y1 - y0);
+      if (area <= 64) {
+        uint64_t mask = 0;
+        int bit = 0, cnt = 0;
+        for (int ty = y0; ty < y1; ++ty)
+          for (int tx = x0; tx < x1; ++tx, ++bit) {
+            const int px1 = (tx + 1) * cam->tile_w < cam->width ? (tx + 1) * cam->tile_w : cam->width;
+            const int py1 = (ty + 1) * cam->tile_h < cam->height ? (ty + 1) * cam->tile_h : cam->height;
+            const float xl = (float)(tx * cam->tile_w) + 0.5f, xh = (float)px1 - 0.5f;
+            const float yl = (float)(ty * cam->tile_h) + 0.5f, yh = (float)py1 - 0.5f;
+            if (meets(pu, pv, ia, ib, ic, ria, ric, xl, xh, yl, yh)) { mask |= 1ull << bit; ++cnt; }
+          }
+        tmask[i] = mask;
+        touched[i] = cnt;
+      } else {
+        tmask[i] = ~0ull;
+        touched[i] = area;
+      }
+    }
 
     /* ---- fp64: continuous outputs */
     double X = x, Y = y, Z = z;
@@ -215,21 +271,25 @@ static int cmp_pair(const void *pa, const void *pb) {
   return 0;
 }
 
-/* Emits one (tile << 32 | depth bits) key per (visible splat, tile of its
- * rectangle) and sorts by (key, virtual id).  Returns the number of pairs, or
+/* Emits one (tile << 32 | depth bits) key per (visible splat, covered tile
+ * of its rectangle) and sorts by (key, virtual id).  Returns the number of pairs, or
  * -needed when cap is too small. */
-int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const float *depth, const int64_t *vid,
-                    int gx, uint64_t *keys_out, int64_t *idx_out, int64_t cap) {
+int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const int32_t *touched,
+                    const uint64_t *tmask, const float *depth, const int64_t *vid, int gx, uint64_t *keys_out,
+                    int64_t *idx_out, int64_t cap) {
   int64_t M = 0;
   for (int64_t i = 0; i < n; ++i)
-    if (vis[i]) M += (int64_t)(rect[4 * i + 2] - rect[4 * i]) * (rect[4 * i + 3] - rect[4 * i + 1]);
+    if (vis[i]) M += touched[i];
   if (M > cap) return -M;
   vo_pair *p = (vo_pair *)malloc(sizeof(vo_pair) * (M > 0 ? M : 1));
   int64_t k = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (!vis[i]) continue;
+    const int w = rect[4 * i + 2] - rect[4 * i], h = rect[4 * i + 3] - rect[4 * i + 1];
+    int bit = 0;
     for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
-      for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
+      for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx, ++bit) {
+        if (w * h <= 64 && !((tmask[i] >> bit) & 1u)) continue;
         uint64_t tile = (uint64_t)ty * gx + tx;
         p[k].key = (tile << 32) | fbits(depth[i]);
         p[k].vid = vid[i];

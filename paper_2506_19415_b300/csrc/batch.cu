@@ -70,6 +70,7 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   sp.rect = r->at<uint32_t>(r->lay.splat_rect);
   sp.touched = r->at<uint32_t>(r->lay.splat_touched);
   sp.radius = r->at<float>(r->lay.splat_radius);
+  sp.tmask = r->at<uint64_t>(r->lay.splat_tmask);
   ProjectArgs pa{};
   pa.ctl = ctl;
   pa.draw = r->at<int4>(r->lay.draw);

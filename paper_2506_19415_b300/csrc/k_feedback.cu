@@ -10,7 +10,8 @@
 // snapped to 1/256 px (round half to even); coverage uses 64-bit integer edge
 // functions at pixel centres with an ownership rule (an edge owns the centres
 // on it if it runs up, or right when horizontal) so that shared edges cover
-// once; depth is perspective-correct z; the visibility word is
+// once; depth is the perspective-correct z, E_sum / sum_k E_k w_k with the
+// per-vertex w_k = 1 / z_k; the visibility word is
 // (bits(z) << 32) | (page + 1), minimum per pixel, all ones when empty.
 #include <algorithm>
 #include <cmath>
@@ -35,10 +36,11 @@ __device__ __forceinline__ int64_t floordiv256(int64_t a) { return a >= 0 ? a / 
 
 __device__ __forceinline__ bool owns(int64_t dx, int64_t dy) { return dy < 0 || (dy == 0 && dx > 0); }
 
-// A snapped, oriented (area > 0) triangle with its clamped pixel box.
+// A snapped, oriented (area > 0) triangle with its clamped pixel box and the
+// inverse view depths of its vertices.
 struct Tri {
   int32_t X[3], Y[3];
-  float Z[3];
+  float W[3];
   uint32_t page1;
   int32_t i0, i1, j0, j1;
 };
@@ -62,9 +64,8 @@ __device__ __forceinline__ void shade(const Tri &t, const int64_t *dxe, const in
     E[k] = dxe[k] * (py - (int64_t)t.Y[ea[k]]) - dye[k] * (px - (int64_t)t.X[ea[k]]);
     if (!(E[k] > 0 || (E[k] == 0 && own[k]))) return;
   }
-  float b0 = __ll2float_rn(E[0]) / farea, b1 = __ll2float_rn(E[1]) / farea, b2 = __ll2float_rn(E[2]) / farea;
-  float s = (b0 / t.Z[0] + b1 / t.Z[1]) + b2 / t.Z[2];
-  float zp = 1.0f / s;
+  const float s = (__ll2float_rn(E[0]) * t.W[0] + __ll2float_rn(E[1]) * t.W[1]) + __ll2float_rn(E[2]) * t.W[2];
+  const float zp = farea / s;
   const uint64_t key = ((uint64_t)__float_as_uint(zp) << 32) | t.page1;
   atomicMin(reinterpret_cast<unsigned long long *>(fb + j * Wf + i), (unsigned long long)key);
 }
@@ -127,7 +128,7 @@ __device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, floa
   if (j1 > Hf - 1) j1 = Hf - 1;
   if (i1 < i0 || j1 < j0) return 0;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) { t.X[k] = (int32_t)X[k]; t.Y[k] = (int32_t)Y[k]; t.Z[k] = Z[k]; }
+  for (int k = 0; k < 3; ++k) { t.X[k] = (int32_t)X[k]; t.Y[k] = (int32_t)Y[k]; t.W[k] = 1.0f / Z[k]; }
   t.page1 = page1;
   t.i0 = (int32_t)i0; t.i1 = (int32_t)i1; t.j0 = (int32_t)j0; t.j1 = (int32_t)j1;
   const int64_t npx = (i1 - i0 + 1) * (j1 - j0 + 1);
@@ -158,12 +159,12 @@ __device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, floa
   return 0;
 }
 
-// The lanes of a warp rasterise their small triangles together: each lane
-// takes one (triangle, pixel) pair of the warp's list in turn, found by a
-// binary search over the inclusive pixel counts.
-__device__ __forceinline__ void raster_warp(const Tri &mine, int npx, Tri *wtri, int Wf, uint64_t *fb) {
+// The lanes of a warp rasterise their small triangles (lane l's in wtri[l],
+// npx pixels, 0 for none) together: each lane takes one (triangle, pixel)
+// pair of the warp's list in turn, found by a binary search over the
+// inclusive pixel counts.
+__device__ __forceinline__ void raster_warp(int npx, const Tri *wtri, int Wf, uint64_t *fb) {
   const int lane = threadIdx.x & 31;
-  wtri[lane] = mine;
   int incl = npx;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -197,6 +198,26 @@ __device__ __forceinline__ void raster_warp(const Tri &mine, int npx, Tri *wtri,
   __syncwarp();
 }
 
+// False only if the triangle (all vertices in front of the near plane)
+// covers no pixel centre: its screen box, from reciprocal-based positions
+// widened by more than their distance to the exact ones (division, snapping
+// to 1/256 px), holds no centre i + 1/2.
+__device__ __forceinline__ bool may_cover(const V3 *q, float fxf, float fyf, float cxf, float cyf) {
+  float xlo = 3.0e38f, xhi = -3.0e38f, ylo = 3.0e38f, yhi = -3.0e38f, mag = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float r = __frcp_rn(q[k].z);
+    const float ux = fxf * (q[k].x * r), uy = fyf * (q[k].y * r);
+    const float x = ux + cxf, y = uy + cyf;
+    xlo = fminf(xlo, x); xhi = fmaxf(xhi, x);
+    ylo = fminf(ylo, y); yhi = fmaxf(yhi, y);
+    mag = fmaxf(mag, fmaxf(fabsf(ux), fabsf(uy)));
+  }
+  if (!(mag < 1.0e6f)) return true;  // far outside or not finite: leave it to the exact test
+  const float m = 1e-6f * (mag + fabsf(cxf) + fabsf(cyf)) + 1.0f / 128.0f;
+  return floorf(xhi + m - 0.5f) >= ceilf(xlo - m - 0.5f) && floorf(yhi + m - 0.5f) >= ceilf(ylo - m - 0.5f);
+}
+
 // Smallest value over the box [lo, hi] of n.p + d, and a bound on its
 // rounding error.
 __device__ __forceinline__ void box_min(const float *n, float d, const float *lo, const float *hi, float &mn,
@@ -211,16 +232,17 @@ __device__ __forceinline__ void box_min(const float *n, float d, const float *lo
   err = 1e-5f * mag + 1e-2f;
 }
 
-// Pass 1: triangles entirely behind the near plane, or entirely more than 2
-// pixels beyond one side of the buffer, cover no pixel centre; the others are
-// appended (warp-aggregated) to a dense list so that pass 2 runs without idle
-// lanes.  Whole clusters are dropped first when their box lies, with a margin
+// Pass 1: triangles entirely behind the near plane, entirely more than 2
+// pixels beyond one side of the buffer, or in front of it with a screen box
+// that holds no pixel centre, cover no pixel centre; the others in front of
+// it are appended (warp-aggregated) to a dense list so that pass 2 runs
+// without idle lanes, those crossing it to the clipping list.  Whole clusters are dropped first when their box lies, with a margin
 // larger than the rounding of either test, behind the near plane or beyond one
 // of those side planes (planes through the eye, so every triangle inside is
 // beyond it too and covers no pixel centre).
 __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, const int32_t *tris, const Cluster *cl,
                                                           int64_t ncl, vm3dgs_camera cam, int ds, uint32_t *vis,
-                                                          uint32_t *nvis) {
+                                                          uint32_t *nvis, uint32_t *clip, uint32_t *nclip) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
@@ -266,7 +288,7 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
       int nin = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) nin += q[k].z >= zn;
-      keep = nin > 0;
+      if (nin > 0 && nin < 3) clip[atomicAdd(nclip, 1u)] = (uint32_t)t;
       if (nin == 3) {
         bool o1 = true, o2 = true, o3 = true, o4 = true;
 #pragma unroll
@@ -276,7 +298,7 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
           o3 = o3 && q[k].y > kb * q[k].z;
           o4 = o4 && q[k].y < kt * q[k].z;
         }
-        keep = !(o1 || o2 || o3 || o4);
+        keep = !(o1 || o2 || o3 || o4) && may_cover(q, fxf, fyf, cxf, cyf);
       }
     }
     const uint32_t km = __ballot_sync(0xffffffffu, keep);
@@ -287,8 +309,9 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
   }
 }
 
-// Pass 2: clip, snap and rasterise the listed triangles (small ones by the
-// warp together, larger ones queued).
+// Pass 2: snap and rasterise the listed triangles (small ones by the warp
+// together, larger ones queued); each lane's triangle is set up directly in
+// the warp's shared slots.
 __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
                                                            const int32_t *face_page, const uint32_t *vis,
                                                            const uint32_t *nvis, vm3dgs_camera cam, int ds,
@@ -298,57 +321,67 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
-  const float zn = 0.2f;
   const int64_t n = *nvis;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t q = base + lane;
-    Tri t0{}, t1{};
-    int n0 = 0, n1 = 0;
+    int npx = 0;
     if (q < n) {
       const int64_t t = vis[q];
       V3 c[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
-      const uint32_t page1 = (uint32_t)(face_page[t] + 1);
-      bool inside[3];
-      int nin = 0;
+      npx = setup_tri(c, (uint32_t)(face_page[t] + 1), fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, wtri[lane]);
+    }
+    __syncwarp();
+    raster_warp(npx, wtri, Wf, fb);
+  }
+}
+
+// Pass 2b: triangles crossing z = zn, clipped against that plane into a
+// triangle (one vertex in front) or a quad (two) fanned from its first
+// vertex; small pieces are rasterised by the thread, larger ones queued.
+__global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, const int32_t *tris,
+                                                          const int32_t *face_page, const uint32_t *clip,
+                                                          const uint32_t *nclip, vm3dgs_camera cam, int ds,
+                                                          uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap) {
+  const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
+  const float fds = (float)ds;
+  const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
+  const float zn = 0.2f;
+  const int64_t n = *nclip;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int64_t t = clip[q];
+    V3 c[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { inside[k] = c[k].z >= zn; nin += inside[k]; }
-      if (nin == 3) {
-        n0 = setup_tri(c, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t0);
-      } else {
-        // clipped against z = zn: a triangle (one vertex in front) or a quad
-        // (two), fanned from its first vertex
-        V3 poly[4];
-        int m = 0;
+    for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
+    const uint32_t page1 = (uint32_t)(face_page[t] + 1);
+    bool inside[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const V3 a = c[k], b = c[(k + 1) % 3];
-          const bool ia = inside[k], ib = inside[(k + 1) % 3];
-          if (ia) poly[m++] = a;
-          if (ia != ib) {
-            const float tt = (zn - a.z) / (b.z - a.z);
-            V3 p;
-            p.x = a.x + tt * (b.x - a.x);
-            p.y = a.y + tt * (b.y - a.y);
-            p.z = zn;
-            poly[m++] = p;
-          }
-        }
-        if (m >= 3) {
-          const V3 ta[3] = {poly[0], poly[1], poly[2]};
-          n0 = setup_tri(ta, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t0);
-        }
-        if (m == 4) {
-          const V3 tb[3] = {poly[0], poly[2], poly[3]};
-          n1 = setup_tri(tb, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, t1);
-        }
+    for (int k = 0; k < 3; ++k) inside[k] = c[k].z >= zn;
+    V3 poly[4];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const V3 a = c[k], b = c[(k + 1) % 3];
+      const bool ia = inside[k], ib = inside[(k + 1) % 3];
+      if (ia) poly[m++] = a;
+      if (ia != ib) {
+        const float tt = (zn - a.z) / (b.z - a.z);
+        V3 p;
+        p.x = a.x + tt * (b.x - a.x);
+        p.y = a.y + tt * (b.y - a.y);
+        p.z = zn;
+        poly[m++] = p;
       }
     }
-    raster_warp(t0, n0, wtri, Wf, fb);
-    if (__any_sync(0xffffffffu, n1 > 0)) raster_warp(t1, n1, wtri, Wf, fb);
+    for (int k = 1; k + 1 < m; ++k) {
+      const V3 tri[3] = {poly[0], poly[k], poly[k + 1]};
+      Tri tr;
+      if (setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, tr) > 0) raster_serial(tr, Wf, fb);
+    }
   }
 }
 
@@ -475,19 +508,21 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
 
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
                             int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
-                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, cudaStream_t st) {
+                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, uint32_t *clip, cudaStream_t st) {
   if (ntri <= 0 || ncl <= 0) return;
   // qcount[0]: queued medium triangles, qcount[1]: listed triangles,
-  // qcount[2..3] (one 64-bit word): queued huge triangles << 32 | their bands
-  cudaMemsetAsync(qcount, 0, 4 * sizeof(uint32_t), st);
+  // qcount[2..3] (one 64-bit word): queued huge triangles << 32 | their bands,
+  // qcount[4]: triangles to clip
+  cudaMemsetAsync(qcount, 0, 5 * sizeof(uint32_t), st);
   int64_t blocks = (ncl + 7) / 8;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, cl, ncl, cam, ds, vis, qcount + 1);
-  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 1, cam, ds, fb,
-                                               reinterpret_cast<QTri *>(queue), qcount, qcap);
+  QTri *q = reinterpret_cast<QTri *>(queue);
+  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
+  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 1, cam, ds, fb, q, qcount, qcap);
+  raster_clip_kernel<<<148, 128, 0, st>>>(verts, tris, face_page, clip, qcount + 4, cam, ds, fb, q, qcount, qcap);
   const int Wf = (cam.width + ds - 1) / ds;
-  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const QTri *>(queue), qcount, qcap, Wf, fb);
-  raster_huge_kernel<<<148 * 4, 256, 0, st>>>(reinterpret_cast<const QTri *>(queue), qcount, qcap, Wf, fb);
+  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(q, qcount, qcap, Wf, fb);
+  raster_huge_kernel<<<148 * 4, 256, 0, st>>>(q, qcount, qcap, Wf, fb);
 }
 
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,

@@ -2,7 +2,8 @@
 // al., which the paper's renderer runs per Gaussian before rasterisation,
 // Sec. 4.2 "Rendering"): gathers each Gaussian of the draw list from its pool
 // slot, culls, builds the 3D covariance, the EWA 2D covariance, conic,
-// radius, tile rectangle, view-dependent SH colour and view depth.
+// radius, tile rectangle, the rectangle's tiles met by the 3-sigma ellipse,
+// view-dependent SH colour and view depth.
 //
 // This file is compiled with -fmad=false: every discrete result (cull,
 // radius, rectangle, depth key) is a chain of single, correctly rounded
@@ -64,6 +65,36 @@ struct Rec {
 #define SHC3D 0.3731763325901154f
 #define SHC3E 1.445305721320277f
 
+// Does the box [xl, xh] x [yl, yh] (a tile's pixel centres) meet the ellipse
+// ia dx^2 + 2 ib dx dy + ic dy^2 <= 9 around (pu, pv)?  Inside the box the
+// answer is yes; otherwise the quadratic's minimum over the box lies on an
+// edge, where it is a clamped one-dimensional minimum (ria = 1/ia and
+// ric = 1/ic give the stationary points).
+__device__ __forceinline__ bool meets_ellipse(float pu, float pv, float ia, float ib, float ic, float ria, float ric,
+                                              float xl, float xh, float yl, float yh) {
+  const float dxl = xl - pu, dxh = xh - pu, dyl = yl - pv, dyh = yh - pv;
+  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return true;
+  const float b2 = 2.0f * ib;
+  float best = 3.0e38f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {  // edges dx = e
+    const float e = k ? dxh : dxl;
+    float t = -(ib * e) * ric;
+    t = t < dyl ? dyl : (t > dyh ? dyh : t);
+    const float f = ((ia * e) * e + (b2 * e) * t) + (ic * t) * t;
+    if (f < best) best = f;
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {  // edges dy = e
+    const float e = k ? dyh : dyl;
+    float t = -(ib * e) * ria;
+    t = t < dxl ? dxl : (t > dxh ? dxh : t);
+    const float f = ((ia * t) * t + (b2 * t) * e) + (ic * e) * e;
+    if (f < best) best = f;
+  }
+  return best <= 9.0f;
+}
+
 // Projects Gaussian g of the level block blk (m Gaussians) for one camera and
 // writes splat record o.
 template <int K, bool F16>
@@ -77,6 +108,7 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
     float x = R::pos(blk, m, g, 0), y = R::pos(blk, m, g, 1), z = R::pos(blk, m, g, 2);
   float o = R::opac(blk, m, g);
   sp.touched[out] = 0;
+  sp.tmask[out] = 0;
   sp.rect[2 * out] = 0;
   sp.rect[2 * out + 1] = 0;
   sp.depth[out] = 0;
@@ -142,8 +174,29 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   fy0 = fminf(fmaxf(fy0, 0.0f), (float)gy); fy1 = fminf(fmaxf(fy1, 0.0f), (float)gy);
   const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
   if (x0 >= x1 || y0 >= y1) return;
-  // continuous outputs
   float ia = cc / det, ib = -cb / det, ic = ca / det;
+  // tiles of the rectangle met by the 3-sigma ellipse (all of a rectangle of
+  // more than 64 tiles)
+  const int area = (x1 - x0) * (y1 - y0);
+  uint64_t tmask = ~0ull;
+  int covered = area;
+  if (area <= 64) {
+    const float ria = 1.0f / ia, ric = 1.0f / ic;
+    tmask = 0;
+    covered = 0;
+    int bit = 0;
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx, ++bit) {
+        const int px1 = min((tx + 1) * cam.tile_w, cam.width), py1 = min((ty + 1) * cam.tile_h, cam.height);
+        const float xl = (float)(tx * cam.tile_w) + 0.5f, xh = (float)px1 - 0.5f;
+        const float yl = (float)(ty * cam.tile_h) + 0.5f, yh = (float)py1 - 0.5f;
+        if (meets_ellipse(pu, pv, ia, ib, ic, ria, ric, xl, xh, yl, yh)) {
+          tmask |= 1ull << bit;
+          ++covered;
+        }
+      }
+  }
+  // continuous outputs
   float dx = x - cam.campos[0], dy = y - cam.campos[1], dz = z - cam.campos[2];
   float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
   dx *= inv; dy *= inv; dz *= inv;
@@ -179,7 +232,8 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   sp.radius[out] = r;
   sp.rect[2 * out] = (uint32_t)x0 | ((uint32_t)x1 << 16);
   sp.rect[2 * out + 1] = (uint32_t)y0 | ((uint32_t)y1 << 16);
-  sp.touched[out] = (uint32_t)((x1 - x0) * (y1 - y0));
+  sp.touched[out] = (uint32_t)covered;
+  sp.tmask[out] = tmask;
 }
 
 template <int K, bool F16>

@@ -139,9 +139,17 @@ __device__ __forceinline__ int64_t warp_find(const uint32_t *offsets, int64_t N,
   return lo + (31 - __clz(b));
 }
 
+// Rectangle position (row-major) of the q-th covered tile of a splat.
+__device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t w, uint32_t h, uint32_t q) {
+  if (w * h > 64) return q;
+  const uint32_t lo = (uint32_t)m, c = __popc(lo);
+  return q < c ? __fns(lo, 0, (int)q + 1) : 32u + __fns((uint32_t)(m >> 32), 0, (int)(q - c) + 1);
+}
+
 constexpr int kEmitChunk = 256;  // pairs per warp task
 
-// Pair emission balanced over the whole grid: warp task c writes pairs
+// Pair emission balanced over the whole grid (pairs of a splat: its covered
+// tiles in row-major order): warp task c writes pairs
 // [256 c, 256 c + 256), lane l the pairs 256 c + 32 k + l, so stores are
 // coalesced whatever the splat sizes.  The splat of a pair is the last one
 // whose offset is <= the pair index: for the task's first pair by a
@@ -174,9 +182,9 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
         }
         i = lo2;
       }
-      const uint32_t q = j - offsets[i];
       const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
+      const uint32_t q = covered_tile(sp.tmask[i], w, h, j - offsets[i]);
       const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
       const uint32_t db = sp.depth[i];
       const uint64_t doff = min((uint64_t)(db >= kf.base ? db - kf.base : 0u), dmax);
@@ -220,9 +228,9 @@ __global__ void __launch_bounds__(256) emit_batched_kernel(const Ctl *ctl, Splat
         i = lo2;
       }
       const int v = (int)(i / Nv);
-      const uint32_t q = j - offsets[i];
       const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu;
+      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
+      const uint32_t q = covered_tile(sp.tmask[i], w, h, j - offsets[i]);
       const uint32_t tile = (uint32_t)vt->tile_off[v] + (y0 + q / w) * (uint32_t)vt->gx[v] + x0 + q % w;
       keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
       vals[j] = (uint32_t)i;

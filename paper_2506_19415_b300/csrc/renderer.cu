@@ -120,11 +120,13 @@ Layout make_layout(const Dims &d) {
   L.splat_rect = take(8 * N);
   L.splat_touched = take(4 * N);
   L.splat_radius = take(4 * N);
+  L.splat_tmask = take(8 * N);
   L.block_sums = take(8 * d.scan_blocks);
   L.offsets = take(4 * N);
   L.raster_queue = take(kRasterRecord * d.raster_cap);
-  L.raster_count = take(16);
+  L.raster_count = take(32);
   L.raster_vis = take(4 * d.ntri);
+  L.raster_clip = take(4 * d.ntri);
   L.centroid = take(16 * NP);
   L.pf_flag = take(P * d.Smax);
   L.pf_mask = take((NP + 3) / 4 * 4);
@@ -156,6 +158,7 @@ static Splats splats_of(const vm3dgs_renderer *r) {
   s.rect = r->at<uint32_t>(r->lay.splat_rect);
   s.touched = r->at<uint32_t>(r->lay.splat_touched);
   s.radius = r->at<float>(r->lay.splat_radius);
+  s.tmask = r->at<uint64_t>(r->lay.splat_tmask);
   return s;
 }
 
@@ -344,7 +347,7 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
                            r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
-                           r->at<uint32_t>(r->lay.raster_vis), st);
+                           r->at<uint32_t>(r->lay.raster_vis), r->at<uint32_t>(r->lay.raster_clip), st);
     launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
                            r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
     r->last_fb_pixels = npix;
@@ -661,6 +664,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
     }
     case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(L.splat_depth); n = 4 * N; break;
     case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(L.splat_radius); n = 4 * N; break;
+    case VM3DGS_DBG_SPLAT_TMASK: src = r->at<void>(L.splat_tmask); n = 8 * N; break;
     case VM3DGS_DBG_KEYS:
     case VM3DGS_DBG_VALUES: {
       // the sorted pairs as (tile << 32 | bits(depth), splat), whatever the
@@ -717,6 +721,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       return VM3DGS_OK;
     }
     case VM3DGS_DBG_POOL: src = r->pool; n = (int64_t)r->P * r->slot_bytes; break;
+    case VM3DGS_DBG_RASTER: src = r->at<void>(L.raster_count); n = 20; break;
     default: return fail(VM3DGS_E_INVAL, "unknown debug item");
   }
   if (needed) *needed = n;

@@ -37,8 +37,9 @@ struct Splats {
   float *s2;         // b
   uint32_t *depth;   // float bits of view z
   uint32_t *rect;    // [2] per splat: x0 | x1 << 16, y0 | y1 << 16
-  uint32_t *touched; // tiles touched (0 = culled)
+  uint32_t *touched; // tiles covered (0 = culled)
   float *radius;     // pixels
+  uint64_t *tmask;   // covered tiles of a rectangle of <= 64 tiles, row-major bits
 };
 
 // Layout of the scratch area; offsets in bytes.
@@ -46,7 +47,7 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
       face_page, clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, block_sums, offsets, raster_queue, raster_count, raster_vis, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
+      splat_radius, splat_tmask, block_sums, offsets, raster_queue, raster_count, raster_vis, raster_clip, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
       pf_copy_seg, pf_count, pf_base, views, work, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
 
@@ -83,11 +84,11 @@ struct Cluster {
 int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri, int64_t NP,
                        int32_t *tris_out, int32_t *face_page_out, Cluster *cl_out);
 // large triangles (more than 16 pixels) are queued: queue holds qcap records of
-// kRasterRecord bytes, qcount is four device words (16 bytes, 8-aligned)
+// kRasterRecord bytes, qcount is eight device words (32 bytes, 8-aligned)
 constexpr int64_t kRasterRecord = 64;
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
                             int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
-                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, cudaStream_t st);
+                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, uint32_t *clip, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);

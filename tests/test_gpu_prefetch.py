@@ -182,31 +182,32 @@ def test_prefetch_placement_parity(v):
 
 
 def test_prefetcher_reduces_misses(v):
-    """Trained on feedback of seeded flythroughs, evaluated on held-out paths
-    with abrupt 90 degree turns: fewer misses per frame than feedback alone."""
+    """Trained on the renderer's own feedback over seeded flythroughs (half of
+    them with abrupt 90 degree turns every 15 frames), labels = pages needed in
+    the next 15 frames; evaluated on held-out turning paths with a small pool
+    (150 slots of 512 Gaussians) and a 10-page copy budget per frame: fewer
+    misses per frame than feedback alone, with some prefetched pages used."""
     import torch
     from paper_2506_19415_b300 import prefetch_train as ptr
     raw, sc = _blob_scene()
     scene = import_scene(v, raw, sc)
-    n_out = 256 if sc.n_pages > 128 else 128
+    n_out = 256
     W, H = 480, 270
     rec = scene.info.record_bytes
-    cfg = v.RenderConfig(max_width=W, max_height=H, lod=False, staging_bytes=3 * 512 * rec)
-    P = 24
+    cfg = v.RenderConfig(max_width=W, max_height=H, lod=False, staging_bytes=10 * 512 * rec)
+    P = 150
     r = v.Renderer(scene, cfg, pool_slots=P)
-    train_paths = [scenegen.random_fly_path(60, seed=100 + k, lo=0.0, hi=40.0, width=W, height_px=H, speed=1.0)
-                   for k in range(12)]
-    test_paths = [scenegen.random_fly_path(60, seed=900 + k, lo=0.0, hi=40.0, width=W, height_px=H, speed=1.0,
-                                           turn_every=15) for k in range(4)]
-    X, Y, M = ptr.make_dataset(v, r, train_paths, n_out, 12 + n_out // 16)
+    train_paths = [scenegen.random_fly_path(80, seed=100 + k, lo=0.0, hi=40.0, width=W, height_px=H, speed=0.3,
+                                            turn_every=(15 if k % 2 else 0)) for k in range(40)]
+    test_paths = [scenegen.random_fly_path(60, seed=900 + k, lo=0.0, hi=40.0, width=W, height_px=H, speed=0.3,
+                                           turn_every=15) for k in range(6)]
+    X, Y, M = ptr.make_dataset(v, r, train_paths, n_out, 12 + n_out // 16, horizon=15)
     p = v.Prefetcher(v.MlpShape(n_in=12 + n_out // 16, n_hidden=128, n_out=n_out, max_batch=128, seed=4, lr=2e-3))
-    curve = ptr.train(p, X, Y, M, steps=600, batch=128)
-    assert curve[-1] < curve[0]
-    base_r = v.Renderer(scene, cfg, pool_slots=P)
-    pf_r = v.Renderer(scene, cfg, pool_slots=P)
+    curve = ptr.train(p, X, Y, M, steps=800, batch=128)
+    assert curve[-1] < 0.5 * curve[0]
     cs = torch.cuda.Stream()
-    a = ptr.evaluate(v, base_r, test_paths, None, copy_stream=cs)
-    b = ptr.evaluate(v, pf_r, test_paths, p, threshold=0.0, copy_stream=cs)
+    a = ptr.evaluate(v, v.Renderer(scene, cfg, pool_slots=P), test_paths, None, copy_stream=cs)
+    b = ptr.evaluate(v, v.Renderer(scene, cfg, pool_slots=P), test_paths, p, threshold=-1.0, copy_stream=cs)
     print("feedback only", a, "with prefetcher", b)
-    assert b["prefetched_pages_per_frame"] > 0
-    assert b["misses_per_frame"] < a["misses_per_frame"]
+    assert b["prefetched_pages_per_frame"] > 0 and b["prefetch_hits_per_frame"] > 0
+    assert b["misses_per_frame"] < 0.95 * a["misses_per_frame"]

@@ -62,6 +62,8 @@ def test_full_scene_render_parity(v, name, kw, sep):
     np.testing.assert_array_equal(rect[~vis], 0)
     np.testing.assert_array_equal(depth.view(np.uint32), np.where(vis, pr["depth"], 0).view(np.uint32))
     np.testing.assert_array_equal(rad, np.where(vis, pr["radius"], 0))
+    tmask = r.debug(v.DBG_SPLAT_TMASK, np.uint64)
+    np.testing.assert_array_equal(tmask, np.where(vis, pr["tmask"], 0))
     keys = r.debug(v.DBG_KEYS, np.uint64)
     vals = r.debug(v.DBG_VALUES, np.uint32)
     assert st["pairs"] == len(ref["keys"])

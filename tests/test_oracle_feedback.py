@@ -84,9 +84,10 @@ def _bruteforce_raster(verts, tris, face_page, cam, ds):
                     E.append(e)
                 if not ok:
                     continue
-                bs = [f32(f32(e) / f32(area)) for e in E]
-                s = f32(f32(bs[0] / vs[0][2]) + f32(bs[1] / vs[1][2])) + f32(bs[2] / vs[2][2])
-                zp = f32(f32(1.0) / s)
+                # 1/z is affine in screen space: z = E_sum / sum_k E_k / z_k
+                ws = [f32(f32(1.0) / vs[k][2]) for k in range(3)]
+                s = f32(f32(f32(E[0]) * ws[0]) + f32(f32(E[1]) * ws[1])) + f32(f32(E[2]) * ws[2])
+                zp = f32(f32(area) / s)
                 key = (struct.unpack("<I", struct.pack("<f", zp))[0] << 32) | (int(face_page[t]) + 1)
                 buf[j, i] = min(buf[j, i], key)
     return buf.astype(np.uint64)

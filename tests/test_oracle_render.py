@@ -161,16 +161,26 @@ def test_two_gaussian_composite_closed_form():
     np.testing.assert_allclose(out["image"][:, 31, 31], expect, atol=1e-12)
 
 
+def _covers(pr, i, tx, ty):
+    """Tile (tx, ty) is one of splat i's: inside its rectangle and, for
+    rectangles of at most 64 tiles, set in its row-major tile mask."""
+    x0, y0, x1, y1 = pr["rect"][i]
+    if not (x0 <= tx < x1 and y0 <= ty < y1):
+        return False
+    w, h = x1 - x0, y1 - y0
+    return w * h > 64 or bool((int(pr["tmask"][i]) >> int((ty - y0) * w + (tx - x0))) & 1)
+
+
 def _brute_force_image(g, vid, cam, pr):
-    """Per pixel: every visible splat whose tile rectangle holds the pixel's tile,
-    sorted by (depth, virtual id), blended front to back in FP64."""
+    """Per pixel: every visible splat covering the pixel's tile, sorted by
+    (depth, virtual id), blended front to back in FP64."""
     H, W = cam.height, cam.width
     img = np.zeros((3, H, W))
     vis = np.nonzero(pr["vis"])[0]
     for py in range(H):
         for px in range(W):
             tx, ty = px // cam.tile_w, py // cam.tile_h
-            cand = [i for i in vis if pr["rect"][i, 0] <= tx < pr["rect"][i, 2] and pr["rect"][i, 1] <= ty < pr["rect"][i, 3]]
+            cand = [i for i in vis if _covers(pr, i, tx, ty)]
             cand.sort(key=lambda i: (float(pr["depth"][i]), int(vid[i])))
             T, C = 1.0, np.zeros(3)
             for i in cand:
@@ -201,6 +211,53 @@ def test_brute_force_per_pixel_sort(seed, tile):
     out = oracle.render(g, vid, cam)
     ref = _brute_force_image(g, vid, cam, out["proj"])
     np.testing.assert_allclose(out["image"], ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (32, 8)])
+def test_tile_mask_is_the_3sigma_ellipse(tile):
+    """A tile of a rectangle of at most 64 tiles is kept exactly when the box of
+    its pixel centres meets the ellipse d^T conic d <= 9, checked here in FP64
+    by sampling the box densely (edges at 4097 points, the centre inside the box
+    meaning distance 0), away from the boundary case (within 1% of 9); every
+    tile of a larger rectangle is kept; kept tiles are exactly touched."""
+    raw = scenegen.uniform_scene(n=400, seed=21, lo=-1.5, hi=1.5, ls_mu=-2.5, sh_degree=0)
+    from oracle.build import decode
+    g = decode(raw, (-2, -2, -2), (2, 2, 2))
+    # anisotropic: stretch one axis of half of the Gaussians
+    g["scale"][::2, 0] *= 6.0
+    cam = scenegen.tiny_camera(width=120, height=90, dist=4.0, tile=tile)
+    pr = oracle.project(g, cam)
+    TW, TH = tile
+    s = np.linspace(0.0, 1.0, 4097)
+    n_drop = n_checked = 0
+    for i in np.nonzero(pr["vis"])[0]:
+        x0, y0, x1, y1 = (int(v) for v in pr["rect"][i])
+        w, h = x1 - x0, y1 - y0
+        bits = int(pr["tmask"][i])
+        if w * h > 64:
+            assert bits == (1 << 64) - 1 and pr["touched"][i] == w * h
+            continue
+        assert bin(bits).count("1") == pr["touched"][i]
+        A, B, C = pr["conic"][i]
+        cx, cy = pr["centre"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                xl, xh = tx * TW + 0.5, min((tx + 1) * TW, cam.width) - 0.5
+                yl, yh = ty * TH + 0.5, min((ty + 1) * TH, cam.height) - 0.5
+                if xl <= cx <= xh and yl <= cy <= yh:
+                    qmin = 0.0
+                else:
+                    xs = np.concatenate([xl + (xh - xl) * s, np.full_like(s, xh), xh - (xh - xl) * s, np.full_like(s, xl)])
+                    ys = np.concatenate([np.full_like(s, yl), yl + (yh - yl) * s, np.full_like(s, yh), yh - (yh - yl) * s])
+                    dx, dy = xs - cx, ys - cy
+                    qmin = float(np.min(A * dx * dx + 2 * B * dx * dy + C * dy * dy))
+                if abs(qmin - 9.0) < 0.09:
+                    continue
+                n_checked += 1
+                bit = (bits >> ((ty - y0) * w + (tx - x0))) & 1
+                assert bit == (qmin <= 9.0), (i, tx, ty, qmin)
+                n_drop += bit == 0
+    assert n_checked > 500 and n_drop > 50
 
 
 def test_sort_order_and_ranges_are_consistent():

@@ -5,7 +5,9 @@ sort inside vm3dgs_render: the renderer's own pairs, rebuilt in emission
 order from its splat rectangles and depths, sorted by the new call give
 exactly the keys and values vm3dgs_render sorted, on two calls in a row
 (the second on another view, so leftovers of the first are exercised).
-Collected last so that a failure here leaves every other test already run."""
+Pairs of a splat are the tiles of its rectangle met by its 3-sigma ellipse
+(read back as its tile mask), row-major.  Collected last so that a failure
+here leaves every other test already run."""
 import numpy as np
 import pytest
 
@@ -34,14 +36,18 @@ def _render_pairs(v, r, cam):
     n = r.stats()["drawn_gaussians"]
     rect = r.debug(v.DBG_SPLAT_RECT, np.int32).reshape(n, 4)
     depth = r.debug(v.DBG_SPLAT_DEPTH, np.float32).view(np.uint32)
+    tmask = r.debug(v.DBG_SPLAT_TMASK, np.uint64)
     gx = (cam.width + cam.tile_w - 1) // cam.tile_w
     ek, ev = [], []
     for i in range(n):
-        x0, y0, x1, y1 = rect[i]
+        x0, y0, x1, y1 = (int(c) for c in rect[i])
+        bit = 0
         for ty in range(y0, y1):
             for tx in range(x0, x1):
-                ek.append((int(ty * gx + tx) << 32) | int(depth[i]))
-                ev.append(i)
+                if (x1 - x0) * (y1 - y0) > 64 or (int(tmask[i]) >> bit) & 1:
+                    ek.append((int(ty * gx + tx) << 32) | int(depth[i]))
+                    ev.append(i)
+                bit += 1
     ntiles = gx * ((cam.height + cam.tile_h - 1) // cam.tile_h)
     bits = 32 + max(int(ntiles - 1).bit_length(), 0)
     return keys, vals, np.array(ek, np.uint64), np.array(ev, np.uint32), bits
