@@ -154,13 +154,17 @@ def train_prefetcher(v, scene, W, width, height, n_paths=16, frames=60, steps=60
     r = make_renderer(v, scene, W, True, width, height)
     paths = [W["train_path"](frames, 3000 + k) for k in range(n_paths)]
     t0 = time.time()
-    X, Y, M = ptr.make_dataset(v, r, paths, n_out, 12 + n_out // 16)
+    X, Y, M = ptr.make_dataset(v, r, paths, n_out, 12 + n_out // 16, horizon=15)
     p = v.Prefetcher(v.MlpShape(n_in=12 + n_out // 16, n_hidden=256, n_out=n_out, max_batch=256, seed=5, lr=1e-3))
     curve = ptr.train(p, X, Y, M, steps=steps, batch=256)
     del X, Y, M, r
     torch.cuda.empty_cache()
     return p, {"train_paths": n_paths, "frames_per_path": frames, "steps": steps, "window_pages": n_out,
+               "label_horizon_frames": 15, "prefetch_every_frames": PREFETCH_EVERY,
                "loss_first": round(curve[0], 4), "loss_last": round(curve[-1], 4), "seconds": round(time.time() - t0, 1)}
+
+
+PREFETCH_EVERY = 4   # frames between prefetch steps (the network predicts the next 15 frames' pages)
 
 
 def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None, pf=None, pf_thr=0.0):
@@ -178,7 +182,8 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
         r.update_residency(st, copy_stream)
         r.render(c, images, st)
         if pf is not None:
-            v.vm3dgs_prefetch(r, pf, c[0], cams[(i - 1) % n], pf_thr, st, copy_stream)
+            if i % PREFETCH_EVERY == 0:
+                v.vm3dgs_prefetch(r, pf, c[0], cams[(i - 1) % n], pf_thr, st, copy_stream)
         if e2e:
             host.copy_(images[0], non_blocking=True)
 
@@ -210,38 +215,54 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     return dict(ms=ms, wall=wall, stage=stage, stats=stats)
 
 
-def roofline(v, stage, stats, peaks, rec16, K):
-    """Dominant stage (by GPU time) against its bound, per launch."""
+# DRAM bytes per onesweep pass per sorted pair, from the ncu capture summarised
+# in profiles/onesweep_kernel_citypatch.md (dram__bytes_read.sum +
+# dram__bytes_write.sum of one pass over the profiling workload divided by its
+# pairs); None until a capture of the current kernel exists.
+ONESWEEP_DRAM_BYTES_PER_PAIR = 8.4
+
+
+def roofline(v, stage, stats, peaks, rec16, width, height):
+    """Roofline of the dominant kernel (the onesweep sort pass) and of the
+    gather (projection) and blend kernels, from the CUDA-event spans of the
+    timed frames: algorithmic bytes per launch / mean launch time."""
     ms, launches = stage
     names = v.STAGES
     frames = max(stats["acc_frames"], 1)
     views = max(stats["acc_views"], 1)
-    order = sorted(range(len(ms)), key=lambda i: -ms[i])
-    top = names[order[0]]
-    per_view_pairs = stats["acc_pairs"] / views
-    per_frame_gauss = stats["acc_drawn_gaussians"] / frames
-    # algorithmic bytes per launch (see DESIGN.md, rooflines)
-    bytes_per = {
-        "project": per_frame_gauss * (rec16 + 56),
-        "sort": per_view_pairs * (8 + 24 * math.ceil((32 + 13) / 8)),
-        "blend": per_view_pairs * (4 + 36) + 1920 * 1080 * 12,
-        "scan_emit": per_frame_gauss * 16 + per_view_pairs * 12,
-        "ranges": per_view_pairs * 8,
-        "stream": stats["acc_streamed_bytes"] / frames * 2,
-    }
-    n_launch = {"project": frames, "sort": views, "blend": views, "scan_emit": views, "ranges": views,
-                "stream": frames}
-    out = {"kernel": top, "stage_ms": {names[i]: round(ms[i], 3) for i in range(len(ms))},
-           "stage_launches": {names[i]: int(launches[i]) for i in range(len(ms))}}
-    kt = top if top in bytes_per else "project"
-    t_launch = ms[names.index(kt)] / max(n_launch[kt], 1) / 1e3
-    achieved = bytes_per[kt] / t_launch / 1e9 if t_launch > 0 else 0.0
+    pairs = stats["acc_pairs"] / views              # per view
+    gauss = stats["acc_drawn_gaussians"] / frames   # per frame
     peak = peaks.get("hbm_gbs", 6400.0)
-    out.update({"bound": "hbm" if kt != "blend" else "alu", "kernel_measured": kt, "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
-    if kt == "blend":
-        out["note"] = ("blend is bound by FP32/MUFU issue, not HBM; achieved is its algorithmic bytes over its time")
+
+    def per_launch_s(stage_name, n):
+        return ms[names.index(stage_name)] / max(n, 1) / 1e3
+
+    passes = launches[names.index("sort")] / views
+    kern = {
+        # one pass reads and writes every 8-byte packed key once
+        "onesweep": (pairs * 16, per_launch_s("sort", launches[names.index("sort")]),
+                     "16 B per pair per pass (8 B key read + written)"),
+        # pool record (fp16) read + 64 B of splat outputs written per drawn Gaussian
+        "project": (gauss * (rec16 + 64), per_launch_s("project", frames),
+                    "%d B record read + 64 B splat record written per drawn Gaussian" % rec16),
+        # per pair: 8 B key + 36 B splat (s0, s1, s2) read; 12 B image written per pixel
+        "blend": (pairs * 44 + width * height * 12, per_launch_s("blend", views),
+                  "44 B per pair read + 12 B per pixel written"),
+    }
+    detail = {}
+    for k, (b, t, note) in kern.items():
+        a = b / t / 1e9 if t > 0 else 0.0
+        detail[k] = {"achieved": round(a, 1), "frac": round(a / peak, 4), "us_per_launch": round(t * 1e6, 2),
+                     "algorithmic_bytes_per_launch": int(b), "per_unit": note}
+    traffic = None if ONESWEEP_DRAM_BYTES_PER_PAIR is None else int(ONESWEEP_DRAM_BYTES_PER_PAIR * pairs)
+    out = {"bound": "hbm", "kernel": "onesweep_kernel (one sort pass)", "achieved": detail["onesweep"]["achieved"],
+           "peak": peak, "unit": "GB/s", "frac": detail["onesweep"]["frac"], "traffic": traffic,
+           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
+           "passes_per_view": passes, "kernels": detail,
+           "stage_ms": {names[i]: round(ms[i], 3) for i in range(len(ms))},
+           "stage_launches": {names[i]: int(launches[i]) for i in range(len(ms))},
+           "note": ("blend's inputs (sorted keys and splats, < 126 MB) stay in L2 and it is bound by FP32/ALU issue, "
+                    "so its HBM fraction is low by construction")}
     return out
 
 
@@ -305,6 +326,18 @@ def batched_views_eval(v, reps=5):
             "autotune_s": round(tune_s, 2), "pairs_per_batch": st_["pairs"], "status": st_["status"]}
 
 
+def aggregate_ranks(ms_list, steps, world, dist=None, device="cpu"):
+    """Replicas only: every rank renders `steps` frames of its own; the job's
+    time is the slowest rank's (max over ranks) and the job's frames/s counts
+    the frames of all ranks.  Returns (max ms per entry, frames/s per entry)."""
+    import torch
+    t = torch.tensor(ms_list, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = [float(x) for x in t.tolist()]
+    return ms, [world * steps / (m / 1e3) for m in ms]
+
+
 def gpu_main(args):
     import torch
     import paper_2506_19415_b300 as v
@@ -353,15 +386,8 @@ def gpu_main(args):
         nopf = run_arm(v, rn, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist)
         del rn
 
-    def agg(x):
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-    ms_head, ms_plain, ms_e2e = agg(head["ms"]), agg(plain["ms"]), agg(e2e["ms"])
-    fps = world * args.steps / (ms_head / 1e3)
-    fps_plain = world * args.steps / (ms_plain / 1e3)
-    fps_e2e = world * args.steps / (ms_e2e / 1e3)
+    (ms_head, ms_plain, ms_e2e), (fps, fps_plain, fps_e2e) = aggregate_ranks(
+        [head["ms"], plain["ms"], e2e["ms"]], args.steps, world, dist, "cuda")
     if rank != 0:
         if dist is not None:
             dist.barrier()
@@ -369,7 +395,7 @@ def gpu_main(args):
         return
     hs = head["stats"]
     frames = max(hs["acc_frames"], 1)
-    rl = roofline(v, head["stage"], hs, peaks, scene.info.record_bytes16, K)
+    rl = roofline(v, head["stage"], hs, peaks, scene.info.record_bytes16, width, height)
     launches_per_frame = sum(head["stage"][1]) / frames
     line = {
         "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
@@ -382,7 +408,8 @@ def gpu_main(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 math, f16 pool storage, bf16 prefetcher",
+        "dtype": "f32",
+        "storage": "f16 pool records (scale, rotation, SH); bf16 prefetcher weights",
         "data": "synthetic (seeded scenegen), no dataset",
         "config": {"workload": W["name"], "config": args.config, "gaussians": W["gaussians"],
                    "pages": scene.info.n_pages, "resolution": [width, height], "frames_in_path": n_frames,

@@ -119,6 +119,8 @@ typedef struct {
       acc_missing, acc_requested;
   int64_t acc_prefetched_pages, acc_prefetched_bytes, acc_prefetch_hits;  /* hits: requested pages found resident
                                                                             because a prefetch brought them */
+  int32_t staged_projection; /* 1: the projection stages records with tensor-map tile loads (every level block a
+                                multiple of 64 Gaussians); 0: it gathers them with plain loads */
 } vm3dgs_stats;
 
 typedef struct {
@@ -267,8 +269,8 @@ enum {
   VM3DGS_DBG_SPLAT_RGB = 18, /* float [N][3] */
   VM3DGS_DBG_POOL = 19,      /* the pool bytes */
   VM3DGS_DBG_RASTER = 20,    /* uint32 [5] of the last feedback view: triangles queued for a warp, triangles left
-                                in front of the near plane by the frustum test, their bands of 4 rows and the huge
-                                triangles queued (one 64-bit word), triangles crossing the near plane */
+                                in front of the near plane by the frustum test, huge triangles queued, their bands
+                                of 4 rows, triangles crossing the near plane */
   VM3DGS_DBG_SPLAT_TMASK = 21 /* uint64 [N] tiles of the rectangle (row-major bits) met by the 3-sigma ellipse,
                                 all ones when the rectangle has more than 64 tiles, 0 if culled */
 };
@@ -286,11 +288,12 @@ enum {
   VM3DGS_STAGE_STREAM = 2,    /* host -> pool page copies */
   VM3DGS_STAGE_PROJECT = 3,   /* gather + projection + SH */
   VM3DGS_STAGE_SCAN_EMIT = 4, /* tiles-touched scan, pair emission */
-  VM3DGS_STAGE_SORT = 5,      /* radix sort of the pairs */
-  VM3DGS_STAGE_RANGES = 6,    /* tile ranges */
+  VM3DGS_STAGE_SORT = 5,      /* radix sort passes over the pairs */
+  VM3DGS_STAGE_RANGES = 6,    /* tile ranges and the tiles' processing order */
   VM3DGS_STAGE_BLEND = 7,     /* per-tile blending */
   VM3DGS_STAGE_PREFETCH = 8,  /* prefetch input, network, placement and copies */
-  VM3DGS_N_STAGES = 9
+  VM3DGS_STAGE_SORT_PREP = 9, /* digit histograms of the sort and their bases (STAGE_SORT: the passes alone) */
+  VM3DGS_N_STAGES = 10
 };
 int vm3dgs_timing_enable(vm3dgs_renderer *r, int32_t on);
 int vm3dgs_timing_read(vm3dgs_renderer *r, double *ms_total, int64_t *launches, int32_t n);

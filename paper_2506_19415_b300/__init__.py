@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
                 ("acc_frames", c_i64), ("acc_views", c_i64), ("acc_pairs", c_i64), ("acc_drawn_gaussians", c_i64),
                 ("acc_streamed_bytes", c_i64), ("acc_streamed_pages", c_i64), ("acc_missing", c_i64),
                 ("acc_requested", c_i64), ("acc_prefetched_pages", c_i64), ("acc_prefetched_bytes", c_i64),
-                ("acc_prefetch_hits", c_i64)]
+                ("acc_prefetch_hits", c_i64), ("staged_projection", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -142,7 +142,7 @@ SCENE_PAGE_COUNT, SCENE_PAGE_SRC, SCENE_PAGES, SCENE_PAGES16, SCENE_ERR, SCENE_V
  DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK) = range(22)
 
 
-STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend", "prefetch")
+STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend", "prefetch", "sort_prep")
 N_STAGES = len(STAGES)
 
 

@@ -108,9 +108,9 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, 32, st);
   r->span_end(span, 1, st);
   span = timed ? r->span_begin(VM3DGS_STAGE_BLEND, st) : -1;
-  launch_blend_batched(ranges, vals[cur], sp, r->dims.ncap * (int64_t)n, dvt, r->prm.bg,
-                       r->at<uint32_t>(r->lay.work), st);
-  r->span_end(span, 1, st);
+  launch_blend_batched(ranges, vals[cur], sp, r->dims.ncap * (int64_t)n, dvt, ntiles, r->prm.bg,
+                       r->at<uint32_t>(r->lay.tile_order), r->at<uint32_t>(r->lay.work), st);
+  r->span_end(span, 2, st);
   r->sorted_buf = cur;
   r->kf = KeyFormat{32, 0, 32, 0u, false};
   r->last_ntiles = ntiles;

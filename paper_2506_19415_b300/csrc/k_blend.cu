@@ -64,25 +64,86 @@ __device__ __forceinline__ void blend_one(const float4 &a, const float4 &b, floa
   T = tT;
 }
 
-// One CTA per tile, TW*TH/2 threads.  Warp w owns the 8x8 pixel block
+// Persistent CTAs of TW*TH/2 threads take tiles in the given order from a
+// work counter, one tile at a time.  Warp w owns the 8x8 pixel block
 // (w mod TW/8, w div TW/8) of the tile, lane l its pixels (l mod 8, l div 8)
 // and (l mod 8, l div 8 + 4); a warp passes over the staged splats whose
 // alpha box misses its block.
+// Processing order of the tiles for the persistent kernels (segment sort,
+// blend): by descending pair count in power-of-two classes, empty tiles last,
+// so that the longest tiles start first and none is left for the end of the
+// launch.  Also resets the work counters work[0..2].
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint2 *ranges, int ntiles, uint32_t *order,
+                                                          uint32_t *work) {
+  __shared__ uint32_t cnt[33], off[33];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  // per warp, lanes of one class add once (match + leader)
+  for (int b = threadIdx.x & ~31; b < ntiles; b += blockDim.x) {
+    const int t = b + lane;
+    int cls = -1;
+    if (t < ntiles) {
+      const uint2 rg = ranges[t];
+      const uint32_t c = rg.y - rg.x;
+      cls = c ? 32 - __clz(c) : 0;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+    if (cls >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[cls], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t o = 0;
+    for (int k = 32; k >= 0; --k) {
+      off[k] = o;
+      o += cnt[k];
+    }
+    work[0] = 0;
+    work[1] = 0;
+    work[2] = 0;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x & ~31; b < ntiles; b += blockDim.x) {
+    const int t = b + lane;
+    int cls = -1;
+    if (t < ntiles) {
+      const uint2 rg = ranges[t];
+      const uint32_t c = rg.y - rg.x;
+      cls = c ? 32 - __clz(c) : 0;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (cls >= 0 && lane == leader) base = atomicAdd(&off[cls], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cls >= 0) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+  }
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, const uint32_t *vals,
                                                           const uint64_t *packed, uint32_t idx_mask, Splats sp,
                                                           uint32_t ncap, vm3dgs_camera cam, float bg0, float bg1,
-                                                          float bg2, float *img) {
+                                                          float bg2, float *img, const uint32_t *order,
+                                                          uint32_t ntiles, uint32_t *work) {
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are made of 8x8 blocks");
   constexpr int NT = TW * TH / 2, BS = 2 * NT;
   __shared__ float4 s0[BS];
   __shared__ float4 s1[BS];
   __shared__ float4 s3[BS];
   __shared__ float s2[BS];
+  __shared__ uint32_t s_tile;
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
-  const int tile = blockIdx.x;
-  const int tx = tile % gx, ty = tile / gx;
+  for (;;) {
+  if (threadIdx.x == 0) {
+    const uint32_t w = atomicAdd(work, 1u);
+    s_tile = w < ntiles ? order[w] : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile == 0xFFFFFFFFu) break;
+  const int tx = (int)tile % gx, ty = (int)tile / gx;
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
   const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
   const int px = bx + (lane & 7), py0 = by + (lane >> 3), py1 = py0 + 4;
@@ -136,6 +197,8 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
     img[HW + o] = B1 + T1 * bg1;
     img[2 * HW + o] = D1 + T1 * bg2;
   }
+  __syncthreads();  // the next tile reuses the staging arrays and s_tile
+  }
 }
 
 // All tiles of all views of a batch: a persistent grid takes (view, tile)
@@ -143,7 +206,7 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
 // 8x8; for 8x8 only 64 of the 256 threads own pixels) and image.
 __global__ void __launch_bounds__(256) blend_batched_kernel(const uint2 *ranges, const uint32_t *vals, Splats sp,
                                                            uint32_t ncap, const ViewTable *vt, float bg0, float bg1,
-                                                           float bg2, uint32_t *work) {
+                                                           float bg2, const uint32_t *order, uint32_t *work) {
   constexpr int BS = 256;
   __shared__ float4 s0[BS];
   __shared__ float4 s1[BS];
@@ -152,10 +215,13 @@ __global__ void __launch_bounds__(256) blend_batched_kernel(const uint2 *ranges,
   const int nv = vt->n;
   const int total = vt->tile_off[nv];
   for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(work, 1u);
+    if (threadIdx.x == 0) {
+      const int w = (int)atomicAdd(work, 1u);
+      s_item = w < total ? (int)order[w] : -1;
+    }
     __syncthreads();
     const int gt = s_item;
-    if (gt >= total) break;
+    if (gt < 0) break;
     int lo = 0, hi = nv - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -203,24 +269,37 @@ __global__ void __launch_bounds__(256) blend_batched_kernel(const uint2 *ranges,
 
 }  // namespace
 
+void launch_tile_order(const uint2 *ranges, int ntiles, uint32_t *order, uint32_t *work, cudaStream_t st) {
+  tile_order_kernel<<<1, 1024, 0, st>>>(ranges, ntiles, order, work);
+}
+
 void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap_total,
-                          const ViewTable *vt, const float bg[3], uint32_t *work, cudaStream_t st) {
-  cudaMemsetAsync(work, 0, sizeof(uint32_t), st);
-  blend_batched_kernel<<<148 * 6, 256, 0, st>>>(ranges, vals, sp, (uint32_t)ncap_total, vt, bg[0], bg[1], bg[2], work);
+                          const ViewTable *vt, int ntiles, const float bg[3], uint32_t *order, uint32_t *work,
+                          cudaStream_t st) {
+  tile_order_kernel<<<1, 1024, 0, st>>>(ranges, ntiles, order, work);
+  prefer_shared((const void *)blend_batched_kernel);
+  blend_batched_kernel<<<full_wave((const void *)blend_batched_kernel, 256, 0), 256, 0, st>>>(
+      ranges, vals, sp, (uint32_t)ncap_total, vt, bg[0], bg[1], bg[2], order, work);
 }
 
 void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
                   const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
-                  cudaStream_t st) {
+                  uint32_t *order, uint32_t *work, cudaStream_t st) {
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w, gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
-  const unsigned nt = (unsigned)(gx * gy);
+  const int nt = gx * gy;
   const uint32_t nc = (uint32_t)ncap;
+  prefer_shared((const void *)blend_kernel<16, 16>);
+  prefer_shared((const void *)blend_kernel<8, 8>);
+  prefer_shared((const void *)blend_kernel<32, 8>);
   if (cam.tile_w == 16 && cam.tile_h == 16)
-    blend_kernel<16, 16><<<nt, 128, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<16, 16><<<wave_grid((const void *)blend_kernel<16, 16>, 128, 0, nt, 1), 128, 0, st>>>(
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
   else if (cam.tile_w == 8 && cam.tile_h == 8)
-    blend_kernel<8, 8><<<nt, 32, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<8, 8><<<wave_grid((const void *)blend_kernel<8, 8>, 32, 0, nt, 1), 32, 0, st>>>(
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
   else
-    blend_kernel<32, 8><<<nt, 128, 0, st>>>(ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image);
+    blend_kernel<32, 8><<<wave_grid((const void *)blend_kernel<32, 8>, 128, 0, nt, 1), 128, 0, st>>>(
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
 }
 
 }  // namespace vm

@@ -44,13 +44,11 @@ struct Tri {
   uint32_t page1;
   int32_t i0, i1, j0, j1;
 };
-// A queued triangle; a huge one also carries its first band (kBand rows) in
-// the list of all queued huge triangles' bands, and its band count.
-struct QTri {
-  Tri t;
-  uint32_t band0, nband;
-};
+// Queued triangles are Tri records; a huge one is split into bands of kBand
+// rows, each band a 64-bit entry (slot << 32 | band) of the band list.
+using QTri = Tri;
 static_assert(sizeof(QTri) <= kRasterRecord, "raster record");
+constexpr uint64_t kNoBand = ~0ull;
 constexpr int kBand = 4;
 
 // coverage test and depth write of pixel (i, j)
@@ -95,10 +93,15 @@ __device__ void raster_serial(const Tri &t, int Wf, uint64_t *fb) {
 // Snaps and orients one (clipped) triangle.  Returns the number of pixels of
 // its box when the caller is to rasterise it (at most 16), 0 otherwise:
 // culled, or queued for a warp (17..1024 pixels) or a CTA (more).
+struct RasterQueues {
+  QTri *queue;         // medium triangles from the front, huge ones from the back
+  uint64_t *bands;     // bands of the huge triangles
+  uint32_t *count;     // [0] medium, [1] listed, [2] huge, [3] bands, [4] to clip
+  uint32_t qcap, bcap;
+};
+
 __device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
-                         uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap, Tri &t) {
-  // queue layout: medium triangles from the front (qcount[0] counts them),
-  // huge ones from the back (the 64-bit word at qcount + 2)
+                         uint64_t *fb, const RasterQueues &rq, Tri &t) {
   int64_t X[3], Y[3];
   float Z[3];
 #pragma unroll
@@ -134,27 +137,24 @@ __device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, floa
   const int64_t npx = (i1 - i0 + 1) * (j1 - j0 + 1);
   if (npx <= 16) return (int)npx;
   if (npx <= 1024) {
-    const uint32_t q = atomicAdd(qcount, 1u);
-    if (q < qcap / 2) queue[q] = QTri{t, 0u, 0u};
+    const uint32_t q = atomicAdd(rq.count, 1u);
+    if (q < rq.qcap / 2) rq.queue[q] = t;
     else raster_serial(t, Wf, fb);  // queue full
   } else {
-    // one 64-bit word hands out the slot (high half) and the first band (low
-    // half), so band0 grows with the slot; it stops growing when the queue is
-    // full, which keeps the band count below (qcap / 2) * (Hf / kBand + 1)
     const uint32_t nb = (uint32_t)((j1 - j0) / kBand + 1);
-    unsigned long long *hc = reinterpret_cast<unsigned long long *>(qcount + 2);
-    unsigned long long o = *reinterpret_cast<volatile unsigned long long *>(hc);
-    bool got = false;
-    while ((uint32_t)(o >> 32) < qcap / 2) {
-      const unsigned long long seen = atomicCAS(hc, o, o + ((1ull << 32) | (unsigned long long)nb));
-      if (seen == o) { got = true; break; }
-      o = seen;
+    const uint32_t q = atomicAdd(rq.count + 2, 1u);
+    bool queued = false;
+    if (q < rq.qcap / 2) {
+      const uint32_t b0 = atomicAdd(rq.count + 3, nb);
+      if ((uint64_t)b0 + nb <= rq.bcap) {
+        rq.queue[rq.qcap - 1 - q] = t;
+        for (uint32_t k = 0; k < nb; ++k) rq.bands[b0 + k] = ((uint64_t)q << 32) | k;
+        queued = true;
+      } else {
+        for (uint32_t k = 0; b0 + k < rq.bcap && k < nb; ++k) rq.bands[b0 + k] = kNoBand;
+      }
     }
-    if (got) {
-      queue[qcap - 1 - (uint32_t)(o >> 32)] = QTri{t, (uint32_t)o, nb};
-    } else {
-      raster_serial(t, Wf, fb);  // queue full
-    }
+    if (!queued) raster_serial(t, Wf, fb);  // queue or band list full
   }
   return 0;
 }
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
 __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
                                                            const int32_t *face_page, const uint32_t *vis,
                                                            const uint32_t *nvis, vm3dgs_camera cam, int ds,
-                                                           uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap) {
+                                                           uint64_t *fb, RasterQueues rq) {
   __shared__ Tri s_tri[8][32];
   Tri *wtri = s_tri[threadIdx.x >> 5];
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
       V3 c[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
-      npx = setup_tri(c, (uint32_t)(face_page[t] + 1), fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, wtri[lane]);
+      npx = setup_tri(c, (uint32_t)(face_page[t] + 1), fxf, fyf, cxf, cyf, Wf, Hf, fb, rq, wtri[lane]);
     }
     __syncwarp();
     raster_warp(npx, wtri, Wf, fb);
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
 __global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, const int32_t *tris,
                                                           const int32_t *face_page, const uint32_t *clip,
                                                           const uint32_t *nclip, vm3dgs_camera cam, int ds,
-                                                          uint64_t *fb, QTri *queue, uint32_t *qcount, uint32_t qcap) {
+                                                          uint64_t *fb, RasterQueues rq) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, co
     for (int k = 1; k + 1 < m; ++k) {
       const V3 tri[3] = {poly[0], poly[k], poly[k + 1]};
       Tri tr;
-      if (setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, queue, qcount, qcap, tr) > 0) raster_serial(tr, Wf, fb);
+      if (setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, rq, tr) > 0) raster_serial(tr, Wf, fb);
     }
   }
 }
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) raster_medium_kernel(const QTri *queue, c
   const int lane = threadIdx.x & 31;
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t q = w0; q < n; q += nw) {
-    const Tri t = queue[q].t;
+    const Tri t = queue[q];
     int64_t dxe[3], dye[3];
     bool own[3];
     float farea;
@@ -406,43 +406,26 @@ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {  // b > 0
   return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
-// Huge triangles in bands of kBand rows, one band per warp task: the band's
-// triangle is the last queued one whose first band is <= the task (a
-// warp-wide search over the queue), and in each row only the pixels that can
-// pass all three edge tests (E_k >= 0, a superset of the covered centres) are
-// tested, with the same test as everywhere else.
-__global__ void __launch_bounds__(256) raster_huge_kernel(const QTri *queue, const uint32_t *qcount, uint32_t qcap,
-                                                          int Wf, uint64_t *fb) {
-  const unsigned long long hc = *reinterpret_cast<const unsigned long long *>(qcount + 2);
-  const int64_t n = min((int64_t)(hc >> 32), (int64_t)(qcap / 2));
-  if (n == 0) return;
-  const QTri *tail = queue + (qcap - 1);  // slot s at tail[-s]
-  const int64_t nbands = (int64_t)tail[-(n - 1)].band0 + tail[-(n - 1)].nband;
+// Huge triangles in bands of kBand rows, one band per warp task; in each row
+// only the pixels that can pass all three edge tests (E_k >= 0, a superset of
+// the covered centres) are tested, with the same test as everywhere else.
+__global__ void __launch_bounds__(256) raster_huge_kernel(const QTri *queue, const uint64_t *bands,
+                                                          const uint32_t *qcount, uint32_t qcap, uint32_t bcap, int Wf,
+                                                          uint64_t *fb) {
+  const int64_t nb = min(qcount[3], bcap);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int ea[3] = {1, 2, 0};
-  for (int64_t b = w0; b < nbands; b += nw) {
-    int64_t lo = 0, hi = n;
-    while (hi - lo > 32) {
-      const int64_t step = (hi - lo + 31) / 32;
-      const int64_t p = lo + lane * step;
-      const uint32_t m = __ballot_sync(0xffffffffu, p < hi && (int64_t)tail[-p].band0 <= b);
-      lo += (31 - __clz(m)) * step;
-      hi = min(hi, lo + step);
-    }
-    {
-      const int64_t p = lo + lane;
-      const uint32_t m = __ballot_sync(0xffffffffu, p < hi && (int64_t)tail[-p].band0 <= b);
-      lo += 31 - __clz(m);
-    }
-    const QTri qt = tail[-lo];
-    const Tri &t = qt.t;
+  for (int64_t b = w0; b < nb; b += nw) {
+    const uint64_t e = bands[b];
+    if (e == kNoBand) continue;
+    const Tri t = queue[qcap - 1 - (uint32_t)(e >> 32)];
     int64_t dxe[3], dye[3];
     bool own[3];
     float farea;
     edges(t, dxe, dye, own, &farea);
-    const int64_t ja = t.j0 + (b - (int64_t)qt.band0) * kBand, jb = min((int64_t)t.j1, ja + kBand - 1);
+    const int64_t ja = t.j0 + (int64_t)(uint32_t)e * kBand, jb = min((int64_t)t.j1, ja + kBand - 1);
     for (int64_t j = ja; j <= jb; ++j) {
       // E_k(i) = A_k - B_k i at the centre of pixel (i, j)
       const int64_t py = j * 256 + 128;
@@ -501,35 +484,35 @@ __global__ void request_all_kernel(uint32_t *req, uint8_t *direct, int64_t NP) {
 }  // namespace
 
 void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
-  int64_t b = (n + 255) / 256;
-  if (b > 148 * 8) b = 148 * 8;
-  clear_kernel<<<(unsigned)(b > 0 ? b : 1), 256, 0, st>>>(fb, n);
+  clear_kernel<<<wave_grid((const void *)clear_kernel, 256, 0, n, 256), 256, 0, st>>>(fb, n);
 }
 
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
                             int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
-                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, uint32_t *clip, cudaStream_t st) {
+                            uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
+                            uint32_t *clip, cudaStream_t st) {
   if (ntri <= 0 || ncl <= 0) return;
-  // qcount[0]: queued medium triangles, qcount[1]: listed triangles,
-  // qcount[2..3] (one 64-bit word): queued huge triangles << 32 | their bands,
-  // qcount[4]: triangles to clip
+  // qcount: [0] queued medium triangles, [1] listed triangles, [2] queued
+  // huge triangles, [3] their bands, [4] triangles to clip
   cudaMemsetAsync(qcount, 0, 5 * sizeof(uint32_t), st);
-  int64_t blocks = (ncl + 7) / 8;
-  if (blocks > 148 * 8) blocks = 148 * 8;
-  QTri *q = reinterpret_cast<QTri *>(queue);
-  raster_cull_kernel<<<(unsigned)blocks, 256, 0, st>>>(verts, tris, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
-  raster_setup_kernel<<<148 * 4, 256, 0, st>>>(verts, tris, face_page, vis, qcount + 1, cam, ds, fb, q, qcount, qcap);
-  raster_clip_kernel<<<148, 128, 0, st>>>(verts, tris, face_page, clip, qcount + 4, cam, ds, fb, q, qcount, qcap);
+  const RasterQueues rq{reinterpret_cast<QTri *>(queue), bands, qcount, qcap, bcap};
+  // one full wave each: the list lengths are known only on the device
+  raster_cull_kernel<<<wave_grid((const void *)raster_cull_kernel, 256, 0, ncl, 8), 256, 0, st>>>(
+      verts, tris, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
+  raster_setup_kernel<<<full_wave((const void *)raster_setup_kernel, 256, 0), 256, 0, st>>>(
+      verts, tris, face_page, vis, qcount + 1, cam, ds, fb, rq);
+  raster_clip_kernel<<<148, 128, 0, st>>>(verts, tris, face_page, clip, qcount + 4, cam, ds, fb, rq);
   const int Wf = (cam.width + ds - 1) / ds;
-  raster_medium_kernel<<<148 * 4, 256, 0, st>>>(q, qcount, qcap, Wf, fb);
-  raster_huge_kernel<<<148 * 4, 256, 0, st>>>(q, qcount, qcap, Wf, fb);
+  raster_medium_kernel<<<full_wave((const void *)raster_medium_kernel, 256, 0), 256, 0, st>>>(rq.queue, qcount, qcap,
+                                                                                              Wf, fb);
+  raster_huge_kernel<<<full_wave((const void *)raster_huge_kernel, 256, 0), 256, 0, st>>>(rq.queue, bands, qcount, qcap,
+                                                                                          bcap, Wf, fb);
 }
 
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st) {
-  int64_t b = (npix + 255) / 256;
-  if (b > 148 * 8) b = 148 * 8;
-  reduce_kernel<<<(unsigned)(b > 0 ? b : 1), 256, 0, st>>>(fb, npix, link_ptr, link_col, links, req, direct);
+  reduce_kernel<<<wave_grid((const void *)reduce_kernel, 256, 0, npix, 256), 256, 0, st>>>(fb, npix, link_ptr, link_col,
+                                                                                           links, req, direct);
 }
 
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st) {

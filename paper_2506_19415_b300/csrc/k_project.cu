@@ -18,8 +18,10 @@
 // read consecutive words of every attribute.  fp16 pools keep position and
 // opacity in float and scale, rotation and SH in half.
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include "renderer.cuh"
+#include "tma.cuh"
 
 namespace vm {
 namespace {
@@ -95,18 +97,44 @@ __device__ __forceinline__ bool meets_ellipse(float pu, float pv, float ia, floa
   return best <= 9.0f;
 }
 
-// Projects Gaussian g of the level block blk (m Gaussians) for one camera and
-// writes splat record o.
+// Attributes of Gaussian g of a level block of m Gaussians in the pool.
 template <int K, bool F16>
-__device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const uint8_t *blk, int m,
-                                            int g, int64_t out) {
+struct GlobalSrc {
   using R = Rec<K, F16>;
+  const uint8_t *blk;
+  int m, g;
+  __device__ float pos(int a) const { return R::pos(blk, m, g, a); }
+  __device__ float opac() const { return R::opac(blk, m, g); }
+  __device__ float scale(int a) const { return R::scale(blk, m, g, a); }
+  __device__ float rot(int a) const { return R::rot(blk, m, g, a); }
+  __device__ float sh(int k, int c) const { return R::sh(blk, m, g, k, c); }
+};
+
+// The same attributes staged in shared memory: the record's float rows (A)
+// and half rows (B) of a chunk of kChunk Gaussians, row after row.
+constexpr int kChunk = 64;
+template <int K, bool F16>
+struct SharedSrc {
+  const float *A;
+  const __half *B;
+  int g;
+  __device__ float half_at(int h) const { return __half2float(B[h * kChunk + g]); }
+  __device__ float pos(int a) const { return A[a * kChunk + g]; }
+  __device__ float opac() const { return A[(F16 ? 3 : 10) * kChunk + g]; }
+  __device__ float scale(int a) const { return F16 ? half_at(a) : A[(3 + a) * kChunk + g]; }
+  __device__ float rot(int a) const { return F16 ? half_at(3 + a) : A[(6 + a) * kChunk + g]; }
+  __device__ float sh(int k, int c) const { return F16 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * kChunk + g]; }
+};
+
+// Projects one Gaussian for one camera and writes splat record out.
+template <int K, bool F16, class Src>
+__device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const Src &src, int64_t out) {
   const float *V = cam.view;
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w;
   const int gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
   const float TW = (float)cam.tile_w, TH = (float)cam.tile_h;
-    float x = R::pos(blk, m, g, 0), y = R::pos(blk, m, g, 1), z = R::pos(blk, m, g, 2);
-  float o = R::opac(blk, m, g);
+  float x = src.pos(0), y = src.pos(1), z = src.pos(2);
+  float o = src.opac();
   sp.touched[out] = 0;
   sp.tmask[out] = 0;
   sp.rect[2 * out] = 0;
@@ -117,8 +145,8 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   float ty = ((V[4] * x + V[5] * y) + V[6] * z) + V[7];
   float tz = ((V[8] * x + V[9] * y) + V[10] * z) + V[11];
   if (!(o > 0.0f) || !(tz > 0.2f)) return;
-  float qw = R::rot(blk, m, g, 0), qx = R::rot(blk, m, g, 1), qy = R::rot(blk, m, g, 2), qz = R::rot(blk, m, g, 3);
-  float sc[3] = {R::scale(blk, m, g, 0), R::scale(blk, m, g, 1), R::scale(blk, m, g, 2)};
+  float qw = src.rot(0), qx = src.rot(1), qy = src.rot(2), qz = src.rot(3);
+  float sc[3] = {src.scale(0), src.scale(1), src.scale(2)};
   float xx = qx * qx, yy = qy * qy, zz = qz * qz;
   float xy = qx * qy, xz = qx * qz, yz = qy * qz;
   float wx = qw * qx, wy = qw * qy, wz = qw * qz;
@@ -221,7 +249,7 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   for (int c = 0; c < 3; ++c) {
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) s += R::sh(blk, m, g, k, c) * Y[k];
+    for (int k = 0; k < K; ++k) s += src.sh(k, c) * Y[k];
     s += 0.5f;
     rgb[c] = s > 0.0f ? s : 0.0f;
   }
@@ -263,7 +291,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_came
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, F16>(a.sp, cam, blk, m, g, i);
+    project_one<K, F16>(a.sp, cam, GlobalSrc<K, F16>{blk, m, g}, i);
   }
 }
 
@@ -297,7 +325,129 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, F16>(a.sp, cam, blk, m, g, (int64_t)v * N + i);
+    project_one<K, F16>(a.sp, cam, GlobalSrc<K, F16>{blk, m, g}, (int64_t)v * N + i);
+  }
+}
+
+// Projection with the records staged by tile loads of the tensor memory
+// accelerator: a CTA of 128 threads takes items of two 64-Gaussian chunks
+// (every level block is a multiple of 64); warp 0 finds their draw entries
+// and issues the tile loads (float rows, and half rows for fp16 pools) of the
+// next item while the CTA projects the current one from shared memory (two
+// stages).  A wait that expires records VM3DGS_E_TIMEOUT and ends the CTA
+// after its copies in flight have landed.
+constexpr int kChunksPerCta = 2;
+constexpr int kMbarPolls = 1 << 20;
+
+template <int K, bool F16>
+struct TmaShape {
+  static constexpr int NA = F16 ? 4 : 11 + 3 * K;                // float rows
+  static constexpr int NH = F16 ? ((7 + 3 * K + 1) & ~1) : 0;    // half rows
+  static constexpr int ABYTES = NA * kChunk * 4, BBYTES = NH * kChunk * 2;
+  static constexpr int CHUNK = ABYTES + BBYTES;
+  static constexpr int STAGE = kChunksPerCta * CHUNK;
+  static constexpr int SMEM = 2 * STAGE + 64;                     // + barriers
+};
+
+template <int K, bool F16>
+__global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_camera cam,
+                                                          const __grid_constant__ ProjMaps maps) {
+  using S = TmaShape<K, F16>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
+  const int64_t nchunks = N / kChunk;
+  const int64_t nitems = (nchunks + kChunksPerCta - 1) / kChunksPerCta;
+  const int nd = a.ctl->n_draw;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // warp 0: loads of item `it` into stage `stg`
+  auto issue = [&](int64_t it, int stg) {
+    int64_t e[kChunksPerCta];
+    int valid = 0;
+#pragma unroll
+    for (int j = 0; j < kChunksPerCta; ++j) {
+      const int64_t c = it * kChunksPerCta + j;
+      e[j] = -1;
+      if (c < nchunks) {
+        // last draw entry whose first Gaussian is <= c * kChunk (warp-wide search)
+        const int64_t gi = c * kChunk;
+        int64_t lo = 0, hi = nd;
+        while (hi - lo > 32) {
+          const int64_t step = (hi - lo + 31) / 32;
+          const int64_t p = lo + lane * step;
+          const uint32_t m = __ballot_sync(0xffffffffu, p < hi && a.draw_off[p] <= gi);
+          lo += (31 - __clz(m)) * step;
+          hi = min(hi, lo + step);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, lo + lane < hi && a.draw_off[lo + lane] <= gi);
+        e[j] = lo + (31 - __clz(m));
+        ++valid;
+      }
+    }
+    if (lane == 0) {
+      uint8_t *buf = smem + stg * S::STAGE;
+      proxy_fence_shared();
+      mbar_arrive_expect(&bar[stg], (uint32_t)(valid * S::CHUNK));
+#pragma unroll
+      for (int j = 0; j < kChunksPerCta; ++j) {
+        if (e[j] < 0) continue;
+        const int4 d = a.draw[e[j]];
+        int sub = 1;
+        for (int l = 0; l < d.y; ++l) sub *= a.fanout;
+        const int u = d.z * sub + d.w;  // level block of the whole pool
+        const int g0 = (int)((it * kChunksPerCta + j) * kChunk - a.draw_off[e[j]]);
+        tma_load_3d(buf + j * S::CHUNK, &maps.a[d.y], g0, 0, u, &bar[stg]);
+        if (F16) tma_load_3d(buf + j * S::CHUNK + S::ABYTES, &maps.b[d.y], g0, 0, u, &bar[stg]);
+      }
+    }
+    __syncwarp();
+  };
+  int64_t item = blockIdx.x;
+  int pending = 0;  // bit s: stage s has loads in flight
+  if (item < nitems) {
+    if (warp == 0) issue(item, 0);
+    pending = 1;
+  }
+  uint32_t parity[2] = {0u, 0u};
+  bool timed_out = false;
+  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
+    const int stg = k & 1;
+    const int64_t next = item + gridDim.x;
+    if (next < nitems) {
+      if (warp == 0) issue(next, stg ^ 1);
+      pending |= 1 << (stg ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[stg], parity[stg], kMbarPolls);
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    parity[stg] ^= 1u;
+    pending &= ~(1 << stg);
+    const int ch = tid / kChunk, g = tid % kChunk;
+    const int64_t c = item * kChunksPerCta + ch;
+    if (c < nchunks) {
+      const uint8_t *buf = smem + stg * S::STAGE + ch * S::CHUNK;
+      const SharedSrc<K, F16> src{reinterpret_cast<const float *>(buf),
+                                  reinterpret_cast<const __half *>(buf + S::ABYTES), g};
+      project_one<K, F16>(a.sp, cam, src, c * kChunk + g);
+    }
+    __syncthreads();  // the stage is refilled by the next-but-one item
+  }
+  if (timed_out) {
+    if (tid == 0) {
+      atomicCAS(const_cast<int32_t *>(&a.ctl->status), 0, VM3DGS_E_TIMEOUT);
+      // let the copies still in flight land before the CTA's memory goes
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (pending & (1 << s2)) mbar_wait(&bar[s2], parity[s2], kMbarPolls);
+    }
+    __syncthreads();
   }
 }
 
@@ -317,6 +467,29 @@ void launch_kb(const ProjectArgs &a, const ViewTable *views, int n_views, cudaSt
 
 template <int K>
 void launch_k(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
+  if (a.maps) {
+    static bool attr[2] = {false, false};
+    if (a.fp16) {
+      using S = TmaShape<K, true>;
+      if (!attr[1]) {
+        cudaFuncSetAttribute(project_tma_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        prefer_shared((const void *)project_tma_kernel<K, true>);
+        attr[1] = true;
+      }
+      project_tma_kernel<K, true>
+          <<<full_wave((const void *)project_tma_kernel<K, true>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
+    } else {
+      using S = TmaShape<K, false>;
+      if (!attr[0]) {
+        cudaFuncSetAttribute(project_tma_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        prefer_shared((const void *)project_tma_kernel<K, false>);
+        attr[0] = true;
+      }
+      project_tma_kernel<K, false>
+          <<<full_wave((const void *)project_tma_kernel<K, false>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
+    }
+    return;
+  }
   int64_t blocks = (a.ncap + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
@@ -344,6 +517,47 @@ void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t
     case 9: launch_k<9>(a, cam, st); break;
     default: launch_k<16>(a, cam, st); break;
   }
+}
+
+bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, bool fp16, ProjMaps *out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  if (s->levels > kMaxLevels) return false;
+  const int K = s->K;
+  const cuuint32_t NA = fp16 ? 4u : (cuuint32_t)(11 + 3 * K);
+  const cuuint32_t NH = fp16 ? (cuuint32_t)((7 + 3 * K + 1) & ~1) : 0u;
+  const int64_t rec = fp16 ? s->rec16 : s->rec32;
+  int64_t sub = 1;
+  for (int l = 0; l < s->levels; ++l) {
+    const int64_t m = s->page_size / sub;
+    if (m % kChunk != 0 || m * sub != s->page_size) return false;
+    const cuuint64_t nsub = (cuuint64_t)(P * sub);
+    const cuuint32_t box[3] = {(cuuint32_t)kChunk, NA, 1}, estr[3] = {1, 1, 1};
+    const cuuint64_t dimA[3] = {(cuuint64_t)m, NA, nsub};
+    const cuuint64_t strA[2] = {(cuuint64_t)(m * 4), (cuuint64_t)(m * rec)};
+    if (enc(&out->a[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<uint8_t *>(pool), dimA, strA, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    if (fp16) {
+      const cuuint32_t boxB[3] = {(cuuint32_t)kChunk, NH, 1};
+      const cuuint64_t dimB[3] = {(cuuint64_t)m, NH, nsub};
+      const cuuint64_t strB[2] = {(cuuint64_t)(m * 2), (cuuint64_t)(m * rec)};
+      if (enc(&out->b[l], CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint8_t *>(pool + 16 * m), dimB, strB, boxB,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+    sub *= s->fanout;
+  }
+  return true;
 }
 
 }  // namespace vm

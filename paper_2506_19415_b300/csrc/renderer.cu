@@ -12,7 +12,50 @@
 
 #include "renderer.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace vm {
+
+int full_wave(const void *kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = (uint64_t)(uintptr_t)kernel ^ ((uint64_t)dev << 56) ^ ((uint64_t)threads << 40) ^ (uint64_t)smem;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int g = sms * per_sm;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = g;
+  return g;
+}
+
+void prefer_shared(const void *kernel) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, bool> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = (uint64_t)(uintptr_t)kernel ^ ((uint64_t)dev << 56);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  cudaGetLastError();
+  done[key] = true;
+}
+
+int wave_grid(const void *kernel, int threads, size_t smem, int64_t n, int64_t per_block) {
+  const int64_t need = per_block > 0 ? (n + per_block - 1) / per_block : 1;
+  const int64_t g = std::min<int64_t>(need, full_wave(kernel, threads, smem));
+  return (int)std::max<int64_t>(g, 1);
+}
 
 namespace {
 int64_t pow2_at_least(int64_t n) {
@@ -127,6 +170,7 @@ Layout make_layout(const Dims &d) {
   L.raster_count = take(32);
   L.raster_vis = take(4 * d.ntri);
   L.raster_clip = take(4 * d.ntri);
+  L.raster_bands = take(8 * d.raster_cap);
   L.centroid = take(16 * NP);
   L.pf_flag = take(P * d.Smax);
   L.pf_mask = take((NP + 3) / 4 * 4);
@@ -142,6 +186,7 @@ Layout make_layout(const Dims &d) {
   L.ranges = take(8 * d.tile_cap * d.nviews);
   L.views = take(sizeof(ViewTable));
   L.work = take(16);
+  L.tile_order = take(4 * d.tile_cap * d.nviews);
   L.hist = take(4 * kMaxPasses * 256);
   L.lookback = take(4 * d.lookback_words);
   L.tile_ctr = take(4 * kMaxPasses);
@@ -250,6 +295,7 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
     ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.clusters), cl.data(), sizeof(Cluster) * (size_t)r->ncl,
                                   cudaMemcpyHostToDevice), "copy", &rc);
   }
+  r->maps_ok = encode_proj_maps(s, r->pool, P, r->fp16, &r->maps);
   // a box around every page's sphere (centroid, radius), hence around every
   // Gaussian mean of every level: it bounds the depth of any splat
   for (int a = 0; a < 3; ++a) { r->gbox_lo[a] = 0.0; r->gbox_hi[a] = 0.0; }
@@ -347,6 +393,7 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
                            r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
+                           r->at<uint64_t>(r->lay.raster_bands), (uint32_t)r->dims.raster_cap,
                            r->at<uint32_t>(r->lay.raster_vis), r->at<uint32_t>(r->lay.raster_clip), st);
     launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
                            r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
@@ -528,6 +575,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
   pa.fp16 = r->fp16;
   pa.ncap = r->dims.ncap;
   pa.sp = sp;
+  pa.maps = r->maps_ok ? &r->maps : nullptr;
   uint64_t *keys[2] = {r->at<uint64_t>(r->lay.keys0), r->at<uint64_t>(r->lay.keys1)};
   uint32_t *vals[2] = {r->at<uint32_t>(r->lay.vals0), r->at<uint32_t>(r->lay.vals1)};
   for (int v = 0; v < n_cams; ++v) {
@@ -543,26 +591,34 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     r->span_end(t, 1, st);
     t = r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st);
     const KeyFormat kf = key_format(r, c, tbits);
-    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), r->at<uint32_t>(r->lay.offsets),
-                     keys[0], vals[0], r->dims.pair_cap, gx, kf, st);
-    r->span_end(t, 4, st);
     const int lo_bit = kf.ib, hi_bit = kf.tshift + tbits;
+    const int passes = (hi_bit - lo_bit + 7) / 8;
+    const int64_t max_tiles = (r->dims.pair_cap + kSortTile - 1) / kSortTile;
+    if (passes < 1 || passes > kMaxPasses || (int64_t)passes * max_tiles * 256 > r->dims.lookback_words)
+      return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
+    const SortHist sh{r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback), max_tiles,
+                      r->at<uint32_t>(r->lay.tile_ctr), lo_bit, passes};
+    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), r->at<uint32_t>(r->lay.offsets),
+                     keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, st);
+    r->span_end(t, 5, st);
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
-    const int cur = launch_sort(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
-                                r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
-                                r->at<uint32_t>(r->lay.tile_ctr), st);
-    r->span_end(t, 2 + (hi_bit - lo_bit + 7) / 8, st);
+    const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
+                                       r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback),
+                                       r->at<uint32_t>(r->lay.tile_ctr), st);
+    r->span_end(t, passes, st);
     if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
     if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
     uint2 *ranges = r->at<uint2>(r->lay.ranges);
+    uint32_t *order = r->at<uint32_t>(r->lay.tile_order), *work = r->at<uint32_t>(r->lay.work);
     t = r->span_begin(VM3DGS_STAGE_RANGES, st);
     launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, kf.tshift, st);
-    r->span_end(t, 1, st);
+    launch_tile_order(ranges, ntiles, order, work, st);
+    r->span_end(t, 2, st);
     t = r->span_begin(VM3DGS_STAGE_BLEND, st);
     const uint32_t idx_mask = kf.ib >= 32 ? 0xFFFFFFFFu : (uint32_t)((1ull << kf.ib) - 1ull);
     launch_blend(ranges, vals[cur], kf.packed ? keys[cur] : nullptr, idx_mask, sp, r->dims.ncap, c, r->prm.bg,
-                 images[v], st);
+                 images[v], order, work + 1, st);
     r->span_end(t, 1, st);
     r->kf = kf;
     r->sorted_buf = cur;
@@ -607,6 +663,7 @@ extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *str
   out->acc_prefetched_pages = c.acc_prefetched_pages;
   out->acc_prefetched_bytes = c.acc_prefetched_bytes;
   out->acc_prefetch_hits = c.acc_prefetch_hits;
+  out->staged_projection = r->maps_ok ? 1 : 0;
   return VM3DGS_OK;
 }
 

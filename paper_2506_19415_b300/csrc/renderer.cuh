@@ -1,5 +1,6 @@
 // Internal renderer state, scratch layout and kernel launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,8 +48,8 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
       face_page, clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, splat_tmask, block_sums, offsets, raster_queue, raster_count, raster_vis, raster_clip, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
-      pf_copy_seg, pf_count, pf_base, views, work, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+      splat_radius, splat_tmask, block_sums, offsets, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
+      pf_copy_seg, pf_count, pf_base, views, work, tile_order, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
 
 struct Dims {
@@ -69,6 +70,16 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxPasses = 8;
 constexpr int64_t kCopySeg = 65536;
 
+// Blocks of `threads` threads (and `smem` dynamic shared bytes) that all SMs
+// of the current device hold at once: the grid of a grid-stride kernel that
+// runs as one full wave, without a partial last wave.  Cached per kernel.
+int full_wave(const void *kernel, int threads, size_t smem);
+// Asks for the largest shared-memory carveout for a kernel that lives on
+// shared memory (so that as many CTAs fit as registers allow); once per kernel.
+void prefer_shared(const void *kernel);
+// min(blocks needed for n items at `per_block` items each, full_wave), >= 1
+int wave_grid(const void *kernel, int threads, size_t smem, int64_t n, int64_t per_block);
+
 // ----- launchers (one per kernel family)
 void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
 // A run of at most 32 consecutive proxy triangles of one page with the
@@ -88,7 +99,8 @@ int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *f
 constexpr int64_t kRasterRecord = 64;
 void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
                             int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
-                            uint32_t *qcount, uint32_t qcap, uint32_t *vis, uint32_t *clip, cudaStream_t st);
+                            uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
+                            uint32_t *clip, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
                             int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
@@ -132,6 +144,13 @@ struct StreamArgs {
 };
 void launch_stream(const StreamArgs &a, cudaStream_t st);
 
+// Tensor maps of the pool, one per level: the record's float rows (a) and,
+// for fp16 pools, its half rows (b), each as (Gaussian of the level block,
+// row, level block of the whole pool), loaded 64 Gaussians at a time.
+struct ProjMaps {
+  CUtensorMap a[kMaxLevels];
+  CUtensorMap b[kMaxLevels];
+};
 struct ProjectArgs {
   const Ctl *ctl;
   const int4 *draw;
@@ -141,7 +160,11 @@ struct ProjectArgs {
   int32_t page_size, fanout, K, fp16;
   int64_t ncap;
   Splats sp;
+  const ProjMaps *maps;  // host copy; null: gather from the pool with plain loads
 };
+// Encodes the pool's tensor maps; false when a level block is not a multiple
+// of 64 Gaussians or the driver refuses (the projection then gathers).
+bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, bool fp16, ProjMaps *out);
 void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st);
 
 // Cameras of a batched render, in device memory.
@@ -158,7 +181,8 @@ void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int view
                               uint32_t *block_sums, uint32_t *offsets, uint64_t *keys, uint32_t *vals,
                               int64_t pair_cap, cudaStream_t st);
 void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap_total,
-                          const ViewTable *vt, const float bg[3], uint32_t *work, cudaStream_t st);
+                          const ViewTable *vt, int ntiles, const float bg[3], uint32_t *order, uint32_t *work,
+                          cudaStream_t st);
 
 // Sort key of the single-view path (all fields unsigned):
 //   key = tile << tshift | min(bits(depth) - base, 2^R - 1) << ib | (packed ? splat : 0)
@@ -171,9 +195,19 @@ struct KeyFormat {
   uint32_t base;
   bool packed;
 };
+// The digit histograms of the coming sort (passes of 8 bits from lo_bit),
+// counted by the emission itself, which also clears the sort's look-back
+// words and tile counters; then the digits' bases.  hist null: none.
+struct SortHist {
+  uint32_t *hist;
+  uint32_t *lookback;
+  int64_t max_tiles;
+  uint32_t *tile_ctr;
+  int lo_bit, passes;
+};
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      cudaStream_t st);
+                      const SortHist &sh, cudaStream_t st);
 
 // sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
 // returns the index (0 or 1) of the buffer holding the result
@@ -181,18 +215,27 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
 // sorts the keys alone.  Returns the buffer holding the result.
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
                 uint32_t *hist, uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
+// the same in two steps: digit histograms and bases (0 or -1), then the passes
+int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bit, int hi_bit, uint32_t *hist,
+                     uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
+int launch_sort_passes(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
+                       uint32_t *hist, uint32_t *lookback, uint32_t *tile_ctr, cudaStream_t st);
 
 void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, int tshift,
                    cudaStream_t st);
+// Tile processing order by descending pair count (empty tiles last); also
+// resets the work counters work[0..2] (the blend uses work[1]).
+void launch_tile_order(const uint2 *ranges, int ntiles, uint32_t *order, uint32_t *work, cudaStream_t st);
 
 void launch_prefetch_features(const vm3dgs_renderer *r, int n_out, const vm3dgs_camera &cam,
                               const vm3dgs_camera &prev, float *x, int32_t *base, cudaStream_t st);
 
 // The splat of pair j is vals[j], or the low bits (idx_mask) of packed[j]
-// when packed is not null.
+// when packed is not null; tiles are taken in `order` from the counter *work
+// (reset by launch_tile_order).
 void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
                   const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
-                  cudaStream_t st);
+                  uint32_t *order, uint32_t *work, cudaStream_t st);
 
 }  // namespace vm
 
@@ -219,6 +262,8 @@ struct vm3dgs_renderer {
   int64_t ncl = 0;  // proxy clusters in use
   double gbox_lo[3] = {0, 0, 0}, gbox_hi[3] = {0, 0, 0};  // holds every Gaussian mean
   vm::KeyFormat kf{32, 0, 32, 0u, false};  // of the last sort
+  bool maps_ok = false;
+  vm::ProjMaps maps{};
   float scene_center[3] = {0, 0, 0}, scene_half = 1.0f;
   // captured batch
   cudaGraph_t graph = nullptr;

@@ -81,6 +81,23 @@ def test_full_scene_render_parity(v, name, kw, sep):
     assert nflag < 0.005 * cam.width * cam.height
 
 
+def test_crowded_tiles(v):
+    """The whole tiny scene seen from afar in a 40x40 view: a few tiles hold
+    thousands of pairs each (one over 4096); keys, values, ranges and the
+    image still equal the oracle's."""
+    raw, sc = tiny_scene()
+    cam = scenegen.look_at((0.0, 0.0, -70.0), (0, 0, 0), (0, -1, 0), 40, 40, 12.0, (16, 16))
+    r, img, st = _full_render(v, raw, sc, cam)
+    g, vid = oracle.full_scene(sc)
+    ref = oracle.render(g, vid, cam)
+    rng = ref["ranges"]
+    assert (rng[:, 1] - rng[:, 0]).max() > 4096
+    np.testing.assert_array_equal(r.debug(v.DBG_KEYS, np.uint64), ref["keys"])
+    np.testing.assert_array_equal(r.debug(v.DBG_VALUES, np.uint32).astype(np.int64), ref["idx"])
+    np.testing.assert_array_equal(r.debug(v.DBG_RANGES, np.uint32).reshape(-1, 2).astype(np.int64), rng)
+    compare_image(img, ref)
+
+
 def test_empty_and_degenerate_views(v):
     """A camera looking away from the scene draws nothing: zero pairs, background image."""
     raw, sc = tiny_scene()
