@@ -46,6 +46,22 @@ __device__ __forceinline__ float4 alpha_box(const Splats &sp, uint32_t g) {
   return make_float4(s0.x - xr, s0.x + xr, s0.y - yr, s0.y + yr);
 }
 
+// one pixel whose log2-alpha t passed the skip test
+__device__ __forceinline__ void accumulate(float t, const float4 &b, float c, float &T, float &C0, float &C1, float &C2,
+                                           bool &done) {
+  const float alpha = fminf(0.99f, exp2f(t));
+  const float tT = T * (1.0f - alpha);
+  if (tT < 1e-4f) {
+    done = true;
+    return;
+  }
+  const float w = alpha * T;
+  C0 += b.z * w;
+  C1 += b.w * w;
+  C2 += c * w;
+  T = tT;
+}
+
 // one pixel against one staged splat
 __device__ __forceinline__ void blend_one(const float4 &a, const float4 &b, float c, float fx, float fy, float &T,
                                           float &C0, float &C1, float &C2, bool &done) {
@@ -179,9 +195,20 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
       const float4 bb = s3[j];
       if (bb.y < cx0 || bb.x > cx1 || bb.w < cy0 || bb.z > cy1) continue;  // same for the whole warp
       const float4 a = s0[j], b = s1[j];
+      // both pixels share x: the exponents of the two in packed FP32 pairs
+      const float dx = a.x - fx;
+      const float2 dy = __fadd2_rn(make_float2(a.y, a.y), make_float2(-fy0, -fy1));
+      const float ad = a.z * dx;
+      const float2 inner = __ffma2_rn(make_float2(a.w, a.w), dy, make_float2(ad, ad));
+      const float2 cdy = __fmul2_rn(make_float2(b.x, b.x), dy);
+      const float2 q = __ffma2_rn(make_float2(dx, dx), inner, __fmul2_rn(cdy, dy));
+      const float2 t = __fadd2_rn(q, make_float2(b.y, b.y));
+      const bool go0 = !done0 && q.x <= 0.0f && t.x >= LOG2_SKIP;
+      const bool go1 = !done1 && q.y <= 0.0f && t.y >= LOG2_SKIP;
+      if (!(go0 || go1)) continue;
       const float c = s2[j];
-      if (!done0) blend_one(a, b, c, fx, fy0, T0, A0, B0, D0, done0);
-      if (!done1) blend_one(a, b, c, fx, fy1, T1, A1, B1, D1, done1);
+      if (go0) accumulate(t.x, b, c, T0, A0, B0, D0, done0);
+      if (go1) accumulate(t.y, b, c, T1, A1, B1, D1, done1);
     }
   }
   const int64_t HW = (int64_t)W * H;

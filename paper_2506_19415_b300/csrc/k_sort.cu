@@ -148,15 +148,15 @@ __device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t w, uint32_
 
 constexpr int kEmitChunk = 256;  // pairs per warp task
 
-// Pair emission, a warp per 32 consecutive splats: each lane reads one
-// splat (covered-tile count, offset, rectangle, tile mask, depth), the warp
-// scans the counts and then writes the group's pairs, which are contiguous in
-// the output, 32 at a time: lane l takes pair g of the group, finds its
-// splat by a binary search over the inclusive counts held in the lanes, and
-// fetches that splat's fields by shuffles.  The pairs of a splat are its
-// covered tiles in row-major order.  With sh.hist the kernel also counts the
-// sort's digits (shared-memory histograms merged into sh.hist) and clears the
-// sort's look-back words and tile counters.
+// Pair emission balanced over the whole grid (pairs of a splat: its covered
+// tiles in row-major order): warp task c writes pairs [256 c, 256 c + 256),
+// lane l the pairs 256 c + 32 k + l, so stores are coalesced whatever the
+// splat sizes.  The splat of a pair is the last one whose offset is <= the
+// pair index: for the task's first pair by a warp-wide search, then from the
+// previous pair's splat by a galloping search (runs of culled splats share one
+// offset).  With sh.hist the kernel also counts the sort's digits
+// (shared-memory histograms merged into sh.hist) and clears the sort's
+// look-back words and tile counters.
 __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
                                                    uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
                                                    KeyFormat kf, SortHist sh) {
@@ -172,56 +172,35 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = warp0 * 32; b < N; b += nwarps * 32) {
-    const int64_t i = b + lane;
-    uint32_t cnt = 0, off = 0, rx = 0, ry = 0, db = 0;
-    uint64_t tm = 0;
-    if (i < N) {
-      cnt = sp.touched[i];
-      if (cnt) {
-        off = offsets[i];
-        rx = sp.rect[2 * i];
-        ry = sp.rect[2 * i + 1];
-        tm = sp.tmask[i];
-        db = sp.depth[i];
+  for (int64_t c = warp0; c * kEmitChunk < M; c += nwarps) {
+    const uint32_t j0 = (uint32_t)(c * kEmitChunk);
+    int64_t i = warp_find(offsets, N, j0, lane);  // last splat with offset <= j0
+    for (int k = 0; k < kEmitChunk / 32; ++k) {
+      const uint32_t j = j0 + 32u * k + lane;
+      if ((int64_t)j >= M) break;
+      if (i + 1 < N && offsets[i + 1] <= j) {
+        // gallop over the splats without pairs, then bisect
+        int64_t lo2 = i + 1, step = 1;
+        while (lo2 + step < N && offsets[lo2 + step] <= j) { lo2 += step; step <<= 1; }
+        int64_t hi2 = lo2 + step < N ? lo2 + step - 1 : N - 1;
+        while (lo2 < hi2) {
+          const int64_t mid = (lo2 + hi2 + 1) >> 1;
+          if (offsets[mid] <= j) lo2 = mid; else hi2 = mid - 1;
+        }
+        i = lo2;
       }
-    }
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += o;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
-      const uint32_t g = g0 + lane;
-      int L = 0;  // owner: number of lanes whose inclusive count is <= g
-#pragma unroll
-      for (int st = 16; st >= 1; st >>= 1) {
-        const uint32_t v = __shfl_sync(0xffffffffu, incl, L + st - 1);
-        if (v <= g) L += st;
-      }
-      L = min(L, 31);
-      const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Lc = __shfl_sync(0xffffffffu, cnt, L);
-      const uint32_t Lo = __shfl_sync(0xffffffffu, off, L);
-      const uint32_t Lrx = __shfl_sync(0xffffffffu, rx, L), Lry = __shfl_sync(0xffffffffu, ry, L);
-      const uint32_t Ltl = __shfl_sync(0xffffffffu, (uint32_t)tm, L), Lth = __shfl_sync(0xffffffffu, (uint32_t)(tm >> 32), L);
-      const uint32_t Ldb = __shfl_sync(0xffffffffu, db, L);
-      if (g >= total) continue;
-      const uint32_t q0 = g - (Li - Lc);
-      const int64_t j = (int64_t)Lo + q0;
-      if (j >= M) continue;
-      const uint32_t x0 = Lrx & 0xFFFFu, w = (Lrx >> 16) - x0, y0 = Lry & 0xFFFFu, h = (Lry >> 16) - y0;
-      const uint32_t q = covered_tile(((uint64_t)Lth << 32) | Ltl, w, h, q0);
+      const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
+      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
+      const uint32_t q = covered_tile(sp.tmask[i], w, h, j - offsets[i]);
       const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
-      const uint64_t doff = min((uint64_t)(Ldb >= kf.base ? Ldb - kf.base : 0u), dmax);
+      const uint32_t db = sp.depth[i];
+      const uint64_t doff = min((uint64_t)(db >= kf.base ? db - kf.base : 0u), dmax);
       const uint64_t key = ((uint64_t)tile << kf.tshift) | (doff << kf.ib);
-      const uint64_t si = (uint64_t)(b + L);
       if (kf.packed) {
-        keys[j] = key | si;
+        keys[j] = key | (uint64_t)i;
       } else {
         keys[j] = key;
-        vals[j] = (uint32_t)si;
+        vals[j] = (uint32_t)i;
       }
       if (sh.hist) {
         const uint64_t kd = key >> sh.lo_bit;
@@ -465,6 +444,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
     __syncthreads();
   }
 }
+
 
 __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, uint2 *ranges, uint32_t ntiles,
                               int tshift) {
