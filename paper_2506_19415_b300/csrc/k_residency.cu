@@ -16,7 +16,9 @@
 //              sub-slots of entries already required at that level (entry
 //              order, sub-slot order), then fresh entries taken least
 //              recently used first (ties: index), levels in ascending order,
-//              fanout^l per entry; a fresh entry forgets what it held
+//              fanout^l per entry; a fresh entry forgets what it held (the
+//              few least recently used are found by a radix select, not a
+//              sort of all free entries)
 //   lists      copy list (priority order) with 64 KiB copy segments, missing
 //              list and draw list (ascending page) with Gaussian offsets
 //   control    usage = drawn Gaussian capacity / pool capacity; above the
@@ -99,6 +101,88 @@ __device__ void bscan_n(const int64_t *v, int64_t *pre, int64_t *total, MScan<N>
     pre[q] = (warp ? sm.warp[q][warp - 1] : 0) + x[q] - v[q];
     total[q] = sm.warp[q][31];
   }
+  __syncthreads();
+}
+
+// The k smallest of the distinct keys g[0, n) (0 < k < n, k <= kSmemKeys),
+// ascending, into g[0, k): a most-significant-digit radix select of the k-th
+// smallest key (8 bits a round), the keys at or below it compacted through
+// shared memory and sorted there.
+__device__ void select_smallest(uint64_t *g, int n, int k, uint64_t *sh, ScanSmem &sm) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t s_pref;
+  __shared__ int s_rank;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    s_pref = 0;
+    s_rank = k - 1;
+  }
+  uint64_t mask = 0;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += RT) hist[i] = 0;
+    __syncthreads();
+    const uint64_t pref = s_pref;
+    for (int i = tid; i < n; i += RT) {
+      const uint64_t key = g[i];
+      if ((key & mask) == pref) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        c[b] = hist[8 * lane + b];
+        sum += c[b];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int target = s_rank;
+      const uint32_t excl = incl - sum;
+      if ((int)excl <= target && target < (int)incl) {
+        int t = target - (int)excl, b = 0;
+        while (t >= (int)c[b]) {
+          t -= (int)c[b];
+          ++b;
+        }
+        s_pref = pref | ((uint64_t)(8 * lane + b) << shift);
+        s_rank = t;
+      }
+    }
+    mask |= 0xFFull << shift;
+    __syncthreads();
+  }
+  const uint64_t thr = s_pref;  // the k-th smallest key
+  int64_t base = 0, tot;
+  for (int c = 0; c < n; c += RT) {
+    const int i = c + tid;
+    const int f = (i < n && g[i] <= thr) ? 1 : 0;
+    const int64_t pos = bscan(f, &tot, sm);
+    if (f) sh[base + pos] = g[i];
+    base += tot;
+  }
+  int m = 1;
+  while (m < k) m <<= 1;
+  for (int i = k + tid; i < m; i += RT) sh[i] = ~0ull;
+  __syncthreads();
+  for (int kk = 2; kk <= m; kk <<= 1)
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < m; i += RT) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t x = sh[i], y = sh[ixj];
+          if ((x > y) == ((i & kk) == 0)) {
+            sh[i] = y;
+            sh[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = tid; i < k; i += RT) g[i] = sh[i];
   __syncthreads();
 }
 
@@ -305,10 +389,16 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
       nfree += tot;
     }
-    const int fp = pow2_at_least((int)nfree);
-    for (int i = (int)nfree + tid; i < fp; i += RT) a.free_keys[i] = ~0ull;
     __syncthreads();
-    bitonic(a.free_keys, fp, s_keys);
+    if (fresh_start[L] < nfree && fresh_start[L] <= kSmemKeys) {
+      // only the least recently used few are taken: select them
+      select_smallest(a.free_keys, (int)nfree, fresh_start[L], s_keys, sm);
+    } else {
+      const int fp = pow2_at_least((int)nfree);
+      for (int i = (int)nfree + tid; i < fp; i += RT) a.free_keys[i] = ~0ull;
+      __syncthreads();
+      bitonic(a.free_keys, fp, s_keys);
+    }
   }
   if (tid == 0) s_nfree = (int)nfree;
   __syncthreads();
