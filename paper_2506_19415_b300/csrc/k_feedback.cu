@@ -15,6 +15,7 @@
 // (bits(z) << 32) | (page + 1), minimum per pixel, all ones when empty.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "renderer.cuh"
@@ -24,12 +25,20 @@ namespace {
 
 struct V3 { float x, y, z; };
 
-__device__ __forceinline__ V3 to_cam(const float *V, const float *p) {
+__device__ __forceinline__ V3 to_cam(const float *V, float4 p) {
   V3 r;
-  r.x = ((V[0] * p[0] + V[1] * p[1]) + V[2] * p[2]) + V[3];
-  r.y = ((V[4] * p[0] + V[5] * p[1]) + V[6] * p[2]) + V[7];
-  r.z = ((V[8] * p[0] + V[9] * p[1]) + V[10] * p[2]) + V[11];
+  r.x = ((V[0] * p.x + V[1] * p.y) + V[2] * p.z) + V[3];
+  r.y = ((V[4] * p.x + V[5] * p.y) + V[6] * p.z) + V[7];
+  r.z = ((V[8] * p.x + V[9] * p.y) + V[10] * p.z) + V[11];
   return r;
+}
+
+// Triangle t of the de-indexed proxy: three planes of ntri float4 vertices
+// (x, y, z, w), the face's page id in the w of the first.
+__device__ __forceinline__ void load_tri(const float4 *tv, int64_t ntri, int64_t t, float4 (&p)[3]) {
+  p[0] = __ldg(tv + t);
+  p[1] = __ldg(tv + ntri + t);
+  p[2] = __ldg(tv + 2 * ntri + t);
 }
 
 __device__ __forceinline__ int64_t floordiv256(int64_t a) { return a >= 0 ? a / 256 : -((-a + 255) / 256); }
@@ -90,18 +99,20 @@ __device__ void raster_serial(const Tri &t, int Wf, uint64_t *fb) {
   for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, t.i0 + q % bw, t.j0 + q / bw, Wf, fb);
 }
 
-// Snaps and orients one (clipped) triangle.  Returns the number of pixels of
-// its box when the caller is to rasterise it (at most 16), 0 otherwise:
-// culled, or queued for a warp (17..1024 pixels) or a CTA (more).
 struct RasterQueues {
   QTri *queue;         // medium triangles from the front, huge ones from the back
   uint64_t *bands;     // bands of the huge triangles
   uint32_t *count;     // [0] medium, [1] listed, [2] huge, [3] bands, [4] to clip
   uint32_t qcap, bcap;
 };
+constexpr int64_t kSmallPx = 16, kMediumPx = 1024;
 
-__device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
-                         uint64_t *fb, const RasterQueues &rq, Tri &t) {
+// Snaps and orients one (clipped) triangle into t.  Returns the number of
+// pixels of its clamped box, 0 when it has none (zero area, off the buffer).
+// Boxes of at most kSmallPx pixels are rasterised by the warp's lanes
+// together, up to kMediumPx by a warp each, larger ones in bands.
+__device__ int64_t setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, float cxf, float cyf, int Wf, int Hf,
+                             Tri &t) {
   int64_t X[3], Y[3];
   float Z[3];
 #pragma unroll
@@ -134,29 +145,31 @@ __device__ int setup_tri(const V3 *c, uint32_t page1, float fxf, float fyf, floa
   for (int k = 0; k < 3; ++k) { t.X[k] = (int32_t)X[k]; t.Y[k] = (int32_t)Y[k]; t.W[k] = 1.0f / Z[k]; }
   t.page1 = page1;
   t.i0 = (int32_t)i0; t.i1 = (int32_t)i1; t.j0 = (int32_t)j0; t.j1 = (int32_t)j1;
-  const int64_t npx = (i1 - i0 + 1) * (j1 - j0 + 1);
-  if (npx <= 16) return (int)npx;
-  if (npx <= 1024) {
-    const uint32_t q = atomicAdd(rq.count, 1u);
-    if (q < rq.qcap / 2) rq.queue[q] = t;
-    else raster_serial(t, Wf, fb);  // queue full
-  } else {
-    const uint32_t nb = (uint32_t)((j1 - j0) / kBand + 1);
-    const uint32_t q = atomicAdd(rq.count + 2, 1u);
-    bool queued = false;
-    if (q < rq.qcap / 2) {
-      const uint32_t b0 = atomicAdd(rq.count + 3, nb);
-      if ((uint64_t)b0 + nb <= rq.bcap) {
-        rq.queue[rq.qcap - 1 - q] = t;
-        for (uint32_t k = 0; k < nb; ++k) rq.bands[b0 + k] = ((uint64_t)q << 32) | k;
-        queued = true;
-      } else {
-        for (uint32_t k = 0; b0 + k < rq.bcap && k < nb; ++k) rq.bands[b0 + k] = kNoBand;
-      }
+  return (i1 - i0 + 1) * (j1 - j0 + 1);
+}
+
+// a medium triangle into queue slot q (rasterised in place when full)
+__device__ __forceinline__ void queue_medium(const Tri &t, uint32_t q, const RasterQueues &rq, int Wf, uint64_t *fb) {
+  if (q < rq.qcap / 2) rq.queue[q] = t;
+  else raster_serial(t, Wf, fb);
+}
+
+// a huge triangle from the back of the queue, its bands to the band list
+__device__ void queue_huge(const Tri &t, const RasterQueues &rq, int Wf, uint64_t *fb) {
+  const uint32_t nb = (uint32_t)((t.j1 - t.j0) / kBand + 1);
+  const uint32_t q = atomicAdd(rq.count + 2, 1u);
+  bool queued = false;
+  if (q < rq.qcap / 2) {
+    const uint32_t b0 = atomicAdd(rq.count + 3, nb);
+    if ((uint64_t)b0 + nb <= rq.bcap) {
+      rq.queue[rq.qcap - 1 - q] = t;
+      for (uint32_t k = 0; k < nb; ++k) rq.bands[b0 + k] = ((uint64_t)q << 32) | k;
+      queued = true;
+    } else {
+      for (uint32_t k = 0; b0 + k < rq.bcap && k < nb; ++k) rq.bands[b0 + k] = kNoBand;
     }
-    if (!queued) raster_serial(t, Wf, fb);  // queue or band list full
   }
-  return 0;
+  if (!queued) raster_serial(t, Wf, fb);  // queue or band list full
 }
 
 // The lanes of a warp rasterise their small triangles (lane l's in wtri[l],
@@ -236,11 +249,12 @@ __device__ __forceinline__ void box_min(const float *n, float d, const float *lo
 // pixels beyond one side of the buffer, or in front of it with a screen box
 // that holds no pixel centre, cover no pixel centre; the others in front of
 // it are appended (warp-aggregated) to a dense list so that pass 2 runs
-// without idle lanes, those crossing it to the clipping list.  Whole clusters are dropped first when their box lies, with a margin
-// larger than the rounding of either test, behind the near plane or beyond one
-// of those side planes (planes through the eye, so every triangle inside is
-// beyond it too and covers no pixel centre).
-__global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, const int32_t *tris, const Cluster *cl,
+// without idle lanes, those crossing it to the clipping list.  Whole clusters
+// are dropped first when their box lies, with a margin larger than the
+// rounding of either test, behind the near plane or beyond one of those side
+// planes (planes through the eye, so every triangle inside is beyond it too
+// and covers no pixel centre); lane k < 5 tests plane k.
+__global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int64_t ntri, const Cluster *cl,
                                                           int64_t ncl, vm3dgs_camera cam, int ds, uint32_t *vis,
                                                           uint32_t *nvis, uint32_t *clip, uint32_t *nclip) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
@@ -250,41 +264,43 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
   const float kr = ((float)Wf + 2.0f - cxf) / fxf, kl = (-2.0f - cxf) / fxf;
   const float kb = ((float)Hf + 2.0f - cyf) / fyf, kt = (-2.0f - cyf) / fyf;
   const float *V = cam.view;
-  // the five planes as n.p + d > 0 on the culled side
-  float pn[5][3], pd[5];
+  const int lane = threadIdx.x & 31;
+  // this lane's plane as n.p + d > 0 on the culled side (lanes 5.. none)
+  float pn[3], pd;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    pn[0][a] = V[a] - kr * V[8 + a];        // x > kr z
-    pn[1][a] = kl * V[8 + a] - V[a];        // x < kl z
-    pn[2][a] = V[4 + a] - kb * V[8 + a];    // y > kb z
-    pn[3][a] = kt * V[8 + a] - V[4 + a];    // y < kt z
-    pn[4][a] = -V[8 + a];                   // z < zn
+    const float v0 = V[a], v1 = V[4 + a], v2 = V[8 + a];
+    pn[a] = lane == 0 ? v0 - kr * v2          // x > kr z
+          : lane == 1 ? kl * v2 - v0          // x < kl z
+          : lane == 2 ? v1 - kb * v2          // y > kb z
+          : lane == 3 ? kt * v2 - v1          // y < kt z
+          : lane == 4 ? -v2 : 0.0f;           // z < zn
   }
-  pd[0] = V[3] - kr * V[11];
-  pd[1] = kl * V[11] - V[3];
-  pd[2] = V[7] - kb * V[11];
-  pd[3] = kt * V[11] - V[7];
-  pd[4] = zn - V[11];
-  const int lane = threadIdx.x & 31;
+  pd = lane == 0 ? V[3] - kr * V[11]
+     : lane == 1 ? kl * V[11] - V[3]
+     : lane == 2 ? V[7] - kb * V[11]
+     : lane == 3 ? kt * V[11] - V[7]
+     : lane == 4 ? zn - V[11] : -1.0f;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // one cluster per warp: every lane tests the box, then one triangle each
+  // one cluster per warp (the next one's box already loading), then one
+  // triangle per lane
+  Cluster nx;
+  if (w0 < ncl) nx = cl[w0];
   for (int64_t ci = w0; ci < ncl; ci += nw) {
-    const Cluster c = cl[ci];
-    bool live = true;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      float mn, err;
-      box_min(pn[k], pd[k], c.lo, c.hi, mn, err);
-      if (mn > err) live = false;
-    }
-    if (!live) continue;
+    const Cluster c = nx;
+    if (ci + nw < ncl) nx = cl[ci + nw];
+    float mn, err;
+    box_min(pn, pd, c.lo, c.hi, mn, err);
+    if (__ballot_sync(0xffffffffu, lane < 5 && mn > err)) continue;
     const int64_t t = (int64_t)c.first + lane;
     bool keep = false;
     if ((uint32_t)lane < c.count) {
+      float4 p[3];
+      load_tri(tv, ntri, t, p);
       V3 q[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) q[k] = to_cam(V, verts + 3 * (int64_t)tris[3 * t + k]);
+      for (int k = 0; k < 3; ++k) q[k] = to_cam(V, p[k]);
       int nin = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) nin += q[k].z >= zn;
@@ -310,10 +326,10 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float *verts, co
 }
 
 // Pass 2: snap and rasterise the listed triangles (small ones by the warp
-// together, larger ones queued); each lane's triangle is set up directly in
-// the warp's shared slots.
-__global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, const int32_t *tris,
-                                                           const int32_t *face_page, const uint32_t *vis,
+// together, medium ones queued with one counter update per warp, huge ones
+// in bands); each lane's triangle is set up directly in the warp's shared
+// slots.
+__global__ void __launch_bounds__(256, 4) raster_setup_kernel(const float4 *tv, int64_t ntri, const uint32_t *vis,
                                                            const uint32_t *nvis, vm3dgs_camera cam, int ds,
                                                            uint64_t *fb, RasterQueues rq) {
   __shared__ Tri s_tri[8][32];
@@ -326,24 +342,38 @@ __global__ void __launch_bounds__(256) raster_setup_kernel(const float *verts, c
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t q = base + lane;
-    int npx = 0;
+    int64_t npx = 0;
     if (q < n) {
       const int64_t t = vis[q];
+      float4 p[3];
+      load_tri(tv, ntri, t, p);
       V3 c[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
-      npx = setup_tri(c, (uint32_t)(face_page[t] + 1), fxf, fyf, cxf, cyf, Wf, Hf, fb, rq, wtri[lane]);
+      for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, p[k]);
+      npx = setup_tri(c, (uint32_t)(__float_as_int(p[0].w) + 1), fxf, fyf, cxf, cyf, Wf, Hf, wtri[lane]);
+      if (npx > kMediumPx) {
+        queue_huge(wtri[lane], rq, Wf, fb);
+        npx = 0;
+      }
+    }
+    const bool med = npx > kSmallPx;
+    const uint32_t mm = __ballot_sync(0xffffffffu, med);
+    if (mm) {
+      const int leader = __ffs(mm) - 1;
+      uint32_t q0 = 0;
+      if (lane == leader) q0 = atomicAdd(rq.count, (uint32_t)__popc(mm));
+      q0 = __shfl_sync(0xffffffffu, q0, leader);
+      if (med) queue_medium(wtri[lane], q0 + __popc(mm & ((1u << lane) - 1u)), rq, Wf, fb);
     }
     __syncwarp();
-    raster_warp(npx, wtri, Wf, fb);
+    raster_warp(med ? 0 : (int)npx, wtri, Wf, fb);
   }
 }
 
 // Pass 2b: triangles crossing z = zn, clipped against that plane into a
 // triangle (one vertex in front) or a quad (two) fanned from its first
 // vertex; small pieces are rasterised by the thread, larger ones queued.
-__global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, const int32_t *tris,
-                                                          const int32_t *face_page, const uint32_t *clip,
+__global__ void __launch_bounds__(256) raster_clip_kernel(const float4 *tv, int64_t ntri, const uint32_t *clip,
                                                           const uint32_t *nclip, vm3dgs_camera cam, int ds,
                                                           uint64_t *fb, RasterQueues rq) {
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
@@ -354,10 +384,12 @@ __global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, co
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
     const int64_t t = clip[q];
+    float4 p[3];
+    load_tri(tv, ntri, t, p);
     V3 c[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, verts + 3 * (int64_t)tris[3 * t + k]);
-    const uint32_t page1 = (uint32_t)(face_page[t] + 1);
+    for (int k = 0; k < 3; ++k) c[k] = to_cam(cam.view, p[k]);
+    const uint32_t page1 = (uint32_t)(__float_as_int(p[0].w) + 1);
     bool inside[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) inside[k] = c[k].z >= zn;
@@ -380,7 +412,10 @@ __global__ void __launch_bounds__(256) raster_clip_kernel(const float *verts, co
     for (int k = 1; k + 1 < m; ++k) {
       const V3 tri[3] = {poly[0], poly[k], poly[k + 1]};
       Tri tr;
-      if (setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, fb, rq, tr) > 0) raster_serial(tr, Wf, fb);
+      const int64_t npx = setup_tri(tri, page1, fxf, fyf, cxf, cyf, Wf, Hf, tr);
+      if (npx > kMediumPx) queue_huge(tr, rq, Wf, fb);
+      else if (npx > kSmallPx) queue_medium(tr, atomicAdd(rq.count, 1u), rq, Wf, fb);
+      else if (npx > 0) raster_serial(tr, Wf, fb);
     }
   }
 }
@@ -487,8 +522,8 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
   clear_kernel<<<wave_grid((const void *)clear_kernel, 256, 0, n, 256), 256, 0, st>>>(fb, n);
 }
 
-void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
-                            int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
+void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, int64_t ntri,
+                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
                             uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
                             uint32_t *clip, cudaStream_t st) {
   if (ntri <= 0 || ncl <= 0) return;
@@ -498,10 +533,10 @@ void launch_feedback_raster(const float *verts, const int32_t *tris, const int32
   const RasterQueues rq{reinterpret_cast<QTri *>(queue), bands, qcount, qcap, bcap};
   // one full wave each: the list lengths are known only on the device
   raster_cull_kernel<<<wave_grid((const void *)raster_cull_kernel, 256, 0, ncl, 8), 256, 0, st>>>(
-      verts, tris, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
+      tv, ntri, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
   raster_setup_kernel<<<full_wave((const void *)raster_setup_kernel, 256, 0), 256, 0, st>>>(
-      verts, tris, face_page, vis, qcount + 1, cam, ds, fb, rq);
-  raster_clip_kernel<<<148, 128, 0, st>>>(verts, tris, face_page, clip, qcount + 4, cam, ds, fb, rq);
+      tv, ntri, vis, qcount + 1, cam, ds, fb, rq);
+  raster_clip_kernel<<<148, 128, 0, st>>>(tv, ntri, clip, qcount + 4, cam, ds, fb, rq);
   const int Wf = (cam.width + ds - 1) / ds;
   raster_medium_kernel<<<full_wave((const void *)raster_medium_kernel, 256, 0), 256, 0, st>>>(rq.queue, qcount, qcap,
                                                                                               Wf, fb);
@@ -522,7 +557,7 @@ void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t
 }
 
 int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri, int64_t NP,
-                       int32_t *tris_out, int32_t *face_page_out, Cluster *cl_out) {
+                       float *tv_out, Cluster *cl_out) {
   // stable counting sort by page (ids outside [0, NP) sort last, together)
   std::vector<int64_t> start((size_t)NP + 2, 0);
   auto bucket = [&](int64_t t) { const int32_t p = face_page[t]; return (p >= 0 && p < NP) ? (int64_t)p : NP; };
@@ -531,10 +566,16 @@ int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *f
   std::vector<int64_t> pos(start.begin(), start.end() - 1);
   std::vector<int64_t> order((size_t)ntri);
   for (int64_t t = 0; t < ntri; ++t) order[(size_t)pos[(size_t)bucket(t)]++] = t;
+  // vertex c of sorted triangle k at tv_out[4 * (c * ntri + k)], page id bits in w of vertex 0
   for (int64_t k = 0; k < ntri; ++k) {
     const int64_t t = order[(size_t)k];
-    for (int c = 0; c < 3; ++c) tris_out[3 * k + c] = tris[3 * t + c];
-    face_page_out[k] = face_page[t];
+    for (int c = 0; c < 3; ++c) {
+      const float *p = verts + 3 * (int64_t)tris[3 * t + c];
+      float *o = tv_out + 4 * ((int64_t)c * ntri + k);
+      o[0] = p[0]; o[1] = p[1]; o[2] = p[2];
+      o[3] = 0.0f;
+      if (c == 0) std::memcpy(o + 3, face_page + t, 4);
+    }
   }
   int64_t ncl = 0;
   for (int64_t b = 0; b <= NP; ++b) {
@@ -544,7 +585,7 @@ int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *f
       for (int a = 0; a < 3; ++a) { c.lo[a] = INFINITY; c.hi[a] = -INFINITY; }
       for (int64_t k = k0; k < k1; ++k)
         for (int v = 0; v < 3; ++v) {
-          const float *p = verts + 3 * (int64_t)tris_out[3 * k + v];
+          const float *p = tv_out + 4 * ((int64_t)v * ntri + k);
           for (int a = 0; a < 3; ++a) { c.lo[a] = std::min(c.lo[a], p[a]); c.hi[a] = std::max(c.hi[a], p[a]); }
         }
       c.first = (uint32_t)k0;

@@ -33,6 +33,7 @@ namespace vm {
 namespace {
 
 constexpr int RT = 1024;
+constexpr int kPer = 4;  // pages a thread takes per round of the page-indexed scans
 
 struct ScanSmem {
   int64_t warp[32];
@@ -239,17 +240,29 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   }
   __syncthreads();
 
-  // ---- 1. request list; per-page scratch reset
+  // ---- 1. request list; per-page scratch reset (kPer consecutive pages a
+  // thread, one block scan a round)
   int64_t nreq = 0, ndir = 0, tot;
-  for (int c = 0; c < NP; c += RT) {
-    const int p = c + tid;
-    const uint32_t r = p < NP ? a.req[p] : 0u;
-    const int dflag = (p < NP && r != 0u) ? (int)a.direct[p] : 0;
-    if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; }
-    const int64_t v2[2] = {r != 0u, dflag};
+  for (int c = 0; c < NP; c += RT * kPer) {
+    const int p0 = c + tid * kPer;
+    uint32_t r[kPer];
+    int dflag[kPer];
+    int64_t v2[2] = {0, 0};
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int p = p0 + k;
+      r[k] = p < NP ? a.req[p] : 0u;
+      dflag[k] = (p < NP && r[k] != 0u) ? (int)a.direct[p] : 0;
+      if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; }
+      v2[0] += r[k] != 0u;
+      v2[1] += dflag[k];
+    }
     int64_t pre2[2], tot2[2];
     bscan_n<2>(v2, pre2, tot2, *reinterpret_cast<MScan<2> *>(&sm4));
-    if (r != 0u) a.requests[nreq + pre2[0]] = make_int4(p, (int)r, dflag, 0);
+    int64_t o = nreq + pre2[0];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (r[k] != 0u) a.requests[o++] = make_int4(p0 + k, (int)r[k], dflag[k], 0);
     nreq += tot2[0];
     ndir += tot2[1];
   }
@@ -346,20 +359,33 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   int64_t obase = 0;
   for (int l = 0; l < L; ++l) {
     int64_t cnt_e = 0, cnt_s = 0;
-    for (int c = 0; c < P; c += RT) {
-      const int e = c + tid;
-      int avail = 0, elig = 0;
-      if (e < P && a.any_req[e] && a.pt_lod[e] == l) {
-        elig = 1;
-        for (int s = 0; s < S_l[l]; ++s) avail += a.required[(int64_t)e * Smax + s] ? 0 : 1;
+    for (int c = 0; c < P; c += RT * kPer) {
+      const int e0 = c + tid * kPer;
+      int avail[kPer], elig[kPer];
+      int64_t v2[2] = {0, 0};
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int e = e0 + k;
+        avail[k] = 0;
+        elig[k] = 0;
+        if (e < P && a.any_req[e] && a.pt_lod[e] == l) {
+          elig[k] = 1;
+          for (int s = 0; s < S_l[l]; ++s) avail[k] += a.required[(int64_t)e * Smax + s] ? 0 : 1;
+        }
+        v2[0] += elig[k];
+        v2[1] += avail[k];
       }
-      const int64_t v2[2] = {elig, avail};
       int64_t pre2[2], tot2[2];
       bscan_n<2>(v2, pre2, tot2, *reinterpret_cast<MScan<2> *>(&sm4));
-      if (elig) {
-        a.open_list[obase + cnt_e + pre2[0]] = e;
-        a.open_off[obase + cnt_e + pre2[0]] = (int)(cnt_s + pre2[1]);
-      }
+      int64_t oe = obase + cnt_e + pre2[0], os = cnt_s + pre2[1];
+#pragma unroll
+      for (int k = 0; k < kPer; ++k)
+        if (elig[k]) {
+          a.open_list[oe] = e0 + k;
+          a.open_off[oe] = (int)os;
+          ++oe;
+          os += avail[k];
+        }
       cnt_e += tot2[0];
       cnt_s += tot2[1];
     }
@@ -382,11 +408,18 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   __syncthreads();
   int64_t nfree = 0;
   if (fresh_start[L] > 0) {
-    for (int c = 0; c < P; c += RT) {
-      const int e = c + tid;
-      const int f = (e < P && !a.any_req[e]) ? 1 : 0;
-      const int64_t pos = bscan(f, &tot, sm);
-      if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
+    for (int c = 0; c < P; c += RT * kPer) {
+      const int e0 = c + tid * kPer;
+      int f[kPer], nf = 0;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        f[k] = (e0 + k < P && !a.any_req[e0 + k]) ? 1 : 0;
+        nf += f[k];
+      }
+      int64_t o = nfree + bscan(nf, &tot, sm);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k)
+        if (f[k]) a.free_keys[o++] = ((uint64_t)(uint32_t)(a.pt_last[e0 + k] + 1) << 32) | (uint32_t)(e0 + k);
       nfree += tot;
     }
     __syncthreads();
@@ -487,30 +520,47 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   __syncthreads();
   // ---- 12. missing list and draw list, ascending page; draw offsets
   int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0;
-  for (int c = 0; c < NP; c += RT) {
-    const int p = c + tid;
-    int fm = 0, fd = 0, fl = 0;
-    int64_t g = 0;
-    if (p < NP) {
-      fm = a.matched[p] == 2;
-      fd = a.draw_info[p] >= 0 && !fm;
-      if (fd) { g = m_l[a.reqlev[p]]; fl = a.reqlev[p] > 0; }
+  for (int c = 0; c < NP; c += RT * kPer) {
+    const int p0 = c + tid * kPer;
+    int fm[kPer], fd[kPer];
+    int64_t g[kPer];
+    int64_t v4[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int p = p0 + k;
+      fm[k] = 0; fd[k] = 0; g[k] = 0;
+      if (p < NP) {
+        fm[k] = a.matched[p] == 2;
+        fd[k] = a.draw_info[p] >= 0 && !fm[k];
+        if (fd[k]) {
+          const int lv = a.reqlev[p];
+          g[k] = m_l[lv];
+          v4[3] += lv > 0;
+        }
+      }
+      v4[0] += fm[k];
+      v4[1] += fd[k];
+      v4[2] += g[k];
     }
-    const int64_t v4[4] = {fm, fd, g, fl};
     int64_t pre4[4], tot4[4];
     bscan_n<4>(v4, pre4, tot4, sm4);
-    const int64_t pm = pre4[0], pd = pre4[1], pg = pre4[2];
-    const int64_t tm = tot4[0], td = tot4[1], tg = tot4[2];
-    nlod += tot4[3];
-    if (fm) a.missing[nmiss + pm] = p;
-    if (fd) {
-      const int slot = a.draw_info[p];
-      a.draw[ndraw + pd] = make_int4(p, a.reqlev[p], slot / Smax, slot % Smax);
-      a.draw_off[ndraw + pd] = gsum + pg;
+    int64_t om = nmiss + pre4[0], od = ndraw + pre4[1], og = gsum + pre4[2];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int p = p0 + k;
+      if (fm[k]) a.missing[om++] = p;
+      if (fd[k]) {
+        const int slot = a.draw_info[p];
+        a.draw[od] = make_int4(p, a.reqlev[p], slot / Smax, slot % Smax);
+        a.draw_off[od] = og;
+        ++od;
+        og += g[k];
+      }
     }
-    nmiss += tm;
-    ndraw += td;
-    gsum += tg;
+    nmiss += tot4[0];
+    ndraw += tot4[1];
+    gsum += tot4[2];
+    nlod += tot4[3];
   }
   if (tid == 0) {
     a.draw_off[ndraw] = gsum;

@@ -149,9 +149,7 @@ Layout make_layout(const Dims &d) {
   L.pt_slot = take(4 * P * d.Smax);
   L.required = take(P * d.Smax);
   L.any_req = take(P);
-  L.verts = take(12 * d.nvert);
-  L.tris = take(12 * d.ntri);
-  L.face_page = take(4 * d.ntri);
+  L.tri_v = take(48 * d.ntri);
   L.clusters = take((int64_t)sizeof(Cluster) * d.ncl_cap);
   L.link_ptr = take(8 * (NP + 1));
   L.link_col = take(4 * d.nlink);
@@ -283,15 +281,12 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   r->host_dev = (const uint8_t *)dp;
   // static scene arrays
   bool ok = true;
-  ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.verts), s->verts.data(), 4 * s->verts.size(), cudaMemcpyHostToDevice, st), "copy", &rc);
   {
-    // proxy triangles regrouped by page, in clusters for the frustum test
-    std::vector<int32_t> tp(s->tris.size()), fp(s->face_page.size());
+    // proxy triangles regrouped by page, de-indexed, in clusters for the frustum test
+    std::vector<float> tv((size_t)(12 * d.ntri));
     std::vector<Cluster> cl((size_t)d.ncl_cap);
-    r->ncl = build_clusters(s->verts.data(), s->tris.data(), s->face_page.data(), d.ntri, d.NP, tp.data(), fp.data(),
-                            cl.data());
-    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.tris), tp.data(), 4 * tp.size(), cudaMemcpyHostToDevice), "copy", &rc);
-    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.face_page), fp.data(), 4 * fp.size(), cudaMemcpyHostToDevice), "copy", &rc);
+    r->ncl = build_clusters(s->verts.data(), s->tris.data(), s->face_page.data(), d.ntri, d.NP, tv.data(), cl.data());
+    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.tri_v), tv.data(), 4 * tv.size(), cudaMemcpyHostToDevice), "copy", &rc);
     ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.clusters), cl.data(), sizeof(Cluster) * (size_t)r->ncl,
                                   cudaMemcpyHostToDevice), "copy", &rc);
   }
@@ -326,6 +321,7 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->copy_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->res_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->fb_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaStreamSynchronize(st), "sync", &rc);
   if (!ok) { delete r; return rc; }
   *out = r;
@@ -367,6 +363,7 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   if (r->graph_exec) cudaGraphExecDestroy(r->graph_exec);
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->pf_done) cudaEventDestroy(r->pf_done);
+  if (r->fb_done) cudaEventDestroy(r->fb_done);
   delete r;
 }
 
@@ -380,6 +377,8 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     cudaStreamWaitEvent(st, r->pf_done, 0);
     r->pf_pending = false;
   }
+  // the last page-table update has read the request words cleared below
+  if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
   cudaMemsetAsync(r->at<void>(r->lay.req), 0, 4 * NP, st);
   cudaMemsetAsync(r->at<void>(r->lay.direct), 0, NP, st);
   const int ds = r->prm.feedback_ds;
@@ -390,8 +389,8 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     const int64_t npix = (int64_t)((c.width + ds - 1) / ds) * ((c.height + ds - 1) / ds);
     uint64_t *fb = r->at<uint64_t>(r->lay.fb);
     launch_feedback_clear(fb, npix, st);
-    launch_feedback_raster(r->at<float>(r->lay.verts), r->at<int32_t>(r->lay.tris), r->at<int32_t>(r->lay.face_page),
-                           r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb, r->at<void>(r->lay.raster_queue),
+    launch_feedback_raster(r->at<float4>(r->lay.tri_v), r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb,
+                           r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
                            r->at<uint64_t>(r->lay.raster_bands), (uint32_t)r->dims.raster_cap,
                            r->at<uint32_t>(r->lay.raster_vis), r->at<uint32_t>(r->lay.raster_clip), st);
@@ -401,6 +400,8 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     if (c.fy > fpx) fpx = c.fy;
   }
   r->span_end(sp_fb, 6 * n_cams, st);
+  cudaEventRecord(r->fb_done, st);
+  r->fb_recorded = true;
   r->f_px = fpx;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -415,7 +416,10 @@ extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
     cudaStreamWaitEvent(st, r->pf_done, 0);
     r->pf_pending = false;
   }
+  if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
   launch_request_all(r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), r->dims.NP, st);
+  cudaEventRecord(r->fb_done, st);
+  r->fb_recorded = true;
   r->f_px = 1.0f;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -435,6 +439,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
     cudaStreamWaitEvent(st, r->copy_done, 0);
     r->copy_pending = false;
   }
+  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // page determination on another stream
   const vm3dgs_scene *s = r->scene;
   ResidencyArgs a{};
   a.ctl = r->at<Ctl>(r->lay.ctl);
@@ -479,6 +484,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   launch_residency(a, st);
   r->span_end(sp_res, 1, st);
   cudaEventRecord(r->res_done, st);
+  r->res_recorded = true;
   StreamArgs sa{};
   sa.count = &a.ctl->n_copies;
   sa.copies = a.copies;
@@ -680,6 +686,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
                                  void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
+  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // the visibility buffer may be on another stream
   Ctl c;
   int rc = 0;
   if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc))

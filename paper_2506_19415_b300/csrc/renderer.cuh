@@ -46,8 +46,8 @@ struct Splats {
 // Layout of the scratch area; offsets in bytes.
 struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
-      admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, verts, tris,
-      face_page, clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
+      admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
+      clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
       splat_radius, splat_tmask, block_sums, offsets, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
       pf_copy_seg, pf_count, pf_base, views, work, tile_order, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
 };
@@ -90,15 +90,17 @@ struct Cluster {
   float hi[3];
   uint32_t count;
 };
-// Groups the triangles by page (stable), in clusters of at most 32; fills the
-// permuted triangle and face-page arrays and the clusters, returns their count.
+// Groups the triangles by page (stable), in clusters of at most 32; writes
+// the regrouped triangles de-indexed (three planes of ntri float4 vertices,
+// the page id's bits in the w of the first) and the clusters, returns their
+// count.
 int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *face_page, int64_t ntri, int64_t NP,
-                       int32_t *tris_out, int32_t *face_page_out, Cluster *cl_out);
+                       float *tv_out, Cluster *cl_out);
 // large triangles (more than 16 pixels) are queued: queue holds qcap records of
 // kRasterRecord bytes, qcount is eight device words (32 bytes, 8-aligned)
 constexpr int64_t kRasterRecord = 64;
-void launch_feedback_raster(const float *verts, const int32_t *tris, const int32_t *face_page, const Cluster *cl,
-                            int64_t ncl, int64_t ntri, const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
+void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, int64_t ntri,
+                            const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
                             uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
                             uint32_t *clip, cudaStream_t st);
 void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
@@ -256,6 +258,8 @@ struct vm3dgs_renderer {
   cudaEvent_t copy_done = nullptr;
   bool copy_pending = false;
   cudaEvent_t res_done = nullptr;   // recorded after each page-table update
+  cudaEvent_t fb_done = nullptr;    // recorded after each page determination
+  bool res_recorded = false, fb_recorded = false;
   cudaEvent_t pf_done = nullptr;    // recorded after a prefetch stopped reading this frame's requests
   bool pf_pending = false;
   int64_t last_fb_pixels = 0;

@@ -157,3 +157,41 @@ def test_zero_budget_streams_nothing(v):
     st = r.stats()
     assert st["streamed_pages"] == 0 and st["drawn_pages"] == 0 and st["missing"] == st["requested"] > 0
     assert np.all(img == 0)
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_feedback_on_own_stream_matches_one_stream(v, fp16):
+    """Page determination of frame t+1 on its own stream, overlapping the
+    rendering of frame t (copies on a third stream), with no host sync between
+    frames: every image, the final page table and the running sums equal the
+    single-stream run bit for bit."""
+    import torch
+    raw, sc = city_scene(levels=3, fanout=4, page_size=1024)
+    scene = import_scene(v, raw, sc, fp16=fp16)
+    cams = [city_cam(160.0, k, width=200, height=120) for k in range(10)]
+    rec = scene.info.record_bytes16 if fp16 else scene.info.record_bytes
+    cfg = v.RenderConfig(max_width=200, max_height=120, lod=True, staging_bytes=3 * sc.params.page_size * rec,
+                         tau0=1.0, fp16_pool=fp16)
+    a = v.Renderer(scene, cfg, pool_slots=6)
+    ref = []
+    for c in cams:
+        a.render_feedback([c])
+        a.update_residency()
+        ref.append(a.render([c])[0].cpu().numpy())
+    b = v.Renderer(scene, cfg, pool_slots=6)
+    st, fst, cst = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    imgs = [torch.empty((3, 120, 200), dtype=torch.float32, device="cuda") for _ in cams]
+    for c, im in zip(cams, imgs):
+        b.render_feedback([c], fst)
+        b.update_residency(st, cst)
+        b.render([c], [im], st)
+    torch.cuda.synchronize()
+    for f, im in enumerate(imgs):
+        assert np.array_equal(im.cpu().numpy(), ref[f]), f"frame {f}"
+    for what, dt in ((v.DBG_PT_LOD, np.int32), (v.DBG_PT_LAST, np.int32), (v.DBG_PT_SLOT, np.int32),
+                     (v.DBG_REQ, np.uint32), (v.DBG_FEEDBACK, np.uint64)):
+        assert np.array_equal(a.debug(what, dt), b.debug(what, dt, st))
+    sa, sb = a.stats(), b.stats(st)
+    for k in ("acc_frames", "acc_pairs", "acc_drawn_gaussians", "acc_streamed_bytes", "acc_missing", "acc_requested"):
+        assert sa[k] == sb[k], k
+    assert sb["status"] == 0
