@@ -177,8 +177,9 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     images = [torch.empty((3, H, W), dtype=torch.float32, device=dev) for _ in range(2)]
     hosts = [torch.empty((3, H, W), dtype=torch.float32, pin_memory=True) for _ in range(2)] if e2e else None
     d2h = torch.cuda.Stream() if e2e else None
-    # page determination of frame i+1 runs on its own stream while frame i
-    # renders (the renderer orders it after frame i's page-table update)
+    # page determination and page-table update of frame i+1 run on their own
+    # stream while frame i renders (the renderer orders them with events:
+    # the update after frame i's projection, the render after the update)
     fst = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)] if e2e else None
     rendered = [torch.cuda.Event() for _ in range(2)] if e2e else None
@@ -188,7 +189,7 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
         c = [cams[i % n]]
         b = i & 1
         r.render_feedback(c, fst)
-        r.update_residency(st, copy_stream)
+        r.update_residency(fst, copy_stream)
         if e2e:
             st.wait_event(copied[b])   # the copy of frame i-2 out of this buffer is done
         r.render(c, [images[b]], st)
@@ -465,7 +466,7 @@ def gpu_main(args):
                    "pool_bytes": W["pool_bytes"], "staging_bytes": 40 * 2048 * 236,
                    "l2": "per-frame inputs (2 GiB pool, splat and pair buffers) exceed the 126 MB L2",
                    "arm": "fp16 pool + copy stream + learned prefetch", "parallelism": "replicas, one renderer per GPU",
-                   "streams": "page determination on its own stream, overlapping the previous frame's rendering"},
+                   "streams": "page determination and page-table update on their own stream, overlapping the previous frame's rendering"},
         "plain_vm": {"value": round(fps_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain / args.steps, 4),
                      "arm": "fp32 pool, in-line copies",
                      "missing_per_frame": plain["stats"]["acc_missing"] / max(plain["stats"]["acc_frames"], 1)},

@@ -19,11 +19,13 @@
  * Gaussians (Sec. 4.2 "Rendering").
  *
  * Frame protocol: vm3dgs_render_feedback -> vm3dgs_update_residency ->
- * vm3dgs_render.  Calls on one renderer are not thread safe.  The page
- * determination may be given a stream of its own: the renderer orders it
- * after the previous page-table update and the next update after it (CUDA
- * events), so that page determination of frame t+1 overlaps the rendering of
- * frame t with results identical to one stream.
+ * vm3dgs_render.  Calls on one renderer are not thread safe.  Page
+ * determination and the page-table update may be given a stream of their own
+ * (the "front" stream): the renderer orders, with CUDA events, page
+ * determination after the previous update, the update after the previous
+ * render's projection (its last read of the pool and draw list), and the
+ * render after the update, so that frame t+1's front work overlaps the
+ * sorting and blending of frame t with results identical to one stream.
  */
 #ifndef VM3DGS_H
 #define VM3DGS_H

@@ -134,8 +134,11 @@ extern "C" int vm3dgs_render_batched(vm3dgs_renderer *r, const vm3dgs_camera *ca
     cudaStreamWaitEvent(st, r->copy_done, 0);
     r->copy_pending = false;
   }
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
   rc = enqueue_batch(r, t, st, r->timing);
   if (rc) return rc;
+  cudaEventRecord(r->proj_done, st);  // conservatively after the whole batch
+  r->proj_recorded = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, std::string("render_batched: ") + cudaGetErrorString(e));
 }
@@ -207,6 +210,7 @@ extern "C" int vm3dgs_batch_graph_launch(vm3dgs_renderer *r, const vm3dgs_camera
     cudaStreamWaitEvent(st, r->copy_done, 0);
     r->copy_pending = false;
   }
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
   ViewTable *dvt = r->at<ViewTable>(r->lay.views);
   void *args[2] = {&t, &dvt};
   cudaKernelNodeParams kp{};
@@ -219,6 +223,8 @@ extern "C" int vm3dgs_batch_graph_launch(vm3dgs_renderer *r, const vm3dgs_camera
   if (cudaGraphExecKernelNodeSetParams(r->graph_exec, r->graph_views_node, &kp) != cudaSuccess)
     return fail(VM3DGS_E_CUDA, "graph node update failed");
   const cudaError_t e = cudaGraphLaunch(r->graph_exec, st);
+  cudaEventRecord(r->proj_done, st);
+  r->proj_recorded = true;
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
 }
 
@@ -235,6 +241,11 @@ extern "C" int vm3dgs_autotune_tiles(vm3dgs_renderer *r, vm3dgs_camera *cams, in
   };
   std::vector<vm3dgs_camera> cur(cams, cams + n_cams);
   for (auto &c : cur) { c.tile_w = 16; c.tile_h = 16; }
+  if (r->copy_pending) {
+    cudaStreamWaitEvent(st, r->copy_done, 0);
+    r->copy_pending = false;
+  }
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -280,6 +291,8 @@ extern "C" int vm3dgs_autotune_tiles(vm3dgs_renderer *r, vm3dgs_camera *cams, in
     r->tuned_shape[c] = best;
   }
   r->timing = was_timing;
+  cudaEventRecord(r->proj_done, st);
+  r->proj_recorded = true;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;

@@ -28,7 +28,7 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 3
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookWindow = 8;  // look-back words read per round trip
 
-__device__ __forceinline__ int64_t n_drawn(const Ctl *c, int64_t cap) { return c->draw_gauss < cap ? c->draw_gauss : cap; }
+__device__ __forceinline__ int64_t n_drawn(const Ctl *c, int64_t cap) { return c->r_drawn < cap ? c->r_drawn : cap; }
 // splat records of all views (views x drawn)
 __device__ __forceinline__ int64_t n_total(const Ctl *c, int64_t cap, int views) { return n_drawn(c, cap) * views; }
 

@@ -322,6 +322,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->res_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->fb_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->upd_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->proj_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaStreamSynchronize(st), "sync", &rc);
   if (!ok) { delete r; return rc; }
   *out = r;
@@ -364,6 +366,8 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->pf_done) cudaEventDestroy(r->pf_done);
   if (r->fb_done) cudaEventDestroy(r->fb_done);
+  if (r->upd_done) cudaEventDestroy(r->upd_done);
+  if (r->proj_done) cudaEventDestroy(r->proj_done);
   delete r;
 }
 
@@ -440,6 +444,8 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
     r->copy_pending = false;
   }
   if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // page determination on another stream
+  // the last render's projection has read the pool and the draw list
+  if (r->proj_recorded) cudaStreamWaitEvent(st, r->proj_done, 0);
   const vm3dgs_scene *s = r->scene;
   ResidencyArgs a{};
   a.ctl = r->at<Ctl>(r->lay.ctl);
@@ -510,6 +516,8 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
     cudaEventRecord(r->copy_done, cst);
     r->copy_pending = true;
   }
+  cudaEventRecord(r->upd_done, st);
+  r->upd_recorded = true;
   r->state = 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("update_residency: ") + cudaGetErrorString(e));
@@ -566,6 +574,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     cudaStreamWaitEvent(st, r->copy_done, 0);
     r->copy_pending = false;
   }
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);  // page-table update on another stream
   const vm3dgs_scene *s = r->scene;
   Ctl *ctl = r->at<Ctl>(r->lay.ctl);
   Splats sp = splats_of(r);
@@ -595,6 +604,10 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     int t = r->span_begin(VM3DGS_STAGE_PROJECT, st);
     launch_project(pa, c, st);
     r->span_end(t, 1, st);
+    if (v == n_cams - 1) {  // the next page-table update may start
+      cudaEventRecord(r->proj_done, st);
+      r->proj_recorded = true;
+    }
     t = r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st);
     const KeyFormat kf = key_format(r, c, tbits);
     const int lo_bit = kf.ib, hi_bit = kf.tshift + tbits;
@@ -639,6 +652,7 @@ extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *str
   if (!r || !out) return fail(VM3DGS_E_INVAL, "null argument");
   Ctl c;
   int rc = 0;
+  if (r->upd_recorded) cudaStreamWaitEvent((cudaStream_t)stream, r->upd_done, 0);
   if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
                "stats", &rc))
     return rc;
@@ -687,13 +701,14 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
   if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // the visibility buffer may be on another stream
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
   Ctl c;
   int rc = 0;
   if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc))
     return rc;
   if (!cuda_ok(cudaStreamSynchronize(st), "debug sync", &rc)) return rc;
   const Layout &L = r->lay;
-  const int64_t NP = r->dims.NP, P = r->P, N = c.draw_gauss < r->dims.ncap ? c.draw_gauss : r->dims.ncap;
+  const int64_t NP = r->dims.NP, P = r->P, N = c.r_drawn < r->dims.ncap ? c.r_drawn : r->dims.ncap;
   const int64_t M = c.pairs < r->dims.pair_cap ? c.pairs : r->dims.pair_cap;
   const void *src = nullptr;
   int64_t n = 0;

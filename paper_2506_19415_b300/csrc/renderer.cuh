@@ -18,6 +18,8 @@ struct Ctl {
   int32_t n_free, pad0;
   int64_t draw_gauss;      // Gaussians of the draw list
   int64_t pairs;           // pairs of the last rendered view
+  int64_t r_drawn;         // draw_gauss as the last projection read it: the scan and emission
+                           // read this copy while the next page-table update may rewrite draw_gauss
   int64_t streamed_bytes;
   int64_t copy_segments;   // 64 KiB copy segments of this frame
   float usage, tau, step;
@@ -259,7 +261,9 @@ struct vm3dgs_renderer {
   bool copy_pending = false;
   cudaEvent_t res_done = nullptr;   // recorded after each page-table update
   cudaEvent_t fb_done = nullptr;    // recorded after each page determination
-  bool res_recorded = false, fb_recorded = false;
+  cudaEvent_t upd_done = nullptr;   // recorded after each page-table update and its in-line copies
+  cudaEvent_t proj_done = nullptr;  // recorded after each render's last projection (pool reads done)
+  bool res_recorded = false, fb_recorded = false, upd_recorded = false, proj_recorded = false;
   cudaEvent_t pf_done = nullptr;    // recorded after a prefetch stopped reading this frame's requests
   bool pf_pending = false;
   int64_t last_fb_pixels = 0;

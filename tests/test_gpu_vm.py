@@ -159,12 +159,12 @@ def test_zero_budget_streams_nothing(v):
     assert np.all(img == 0)
 
 
-@pytest.mark.parametrize("fp16", [False, True])
-def test_feedback_on_own_stream_matches_one_stream(v, fp16):
-    """Page determination of frame t+1 on its own stream, overlapping the
-    rendering of frame t (copies on a third stream), with no host sync between
-    frames: every image, the final page table and the running sums equal the
-    single-stream run bit for bit."""
+@pytest.mark.parametrize("fp16,front", [(False, False), (True, False), (False, True), (True, True)])
+def test_feedback_on_own_stream_matches_one_stream(v, fp16, front):
+    """Page determination of frame t+1 (front: and its page-table update) on
+    its own stream, overlapping the rendering of frame t (copies on a third
+    stream), with no host sync between frames: every image, the final page
+    table and the running sums equal the single-stream run bit for bit."""
     import torch
     raw, sc = city_scene(levels=3, fanout=4, page_size=1024)
     scene = import_scene(v, raw, sc, fp16=fp16)
@@ -183,7 +183,7 @@ def test_feedback_on_own_stream_matches_one_stream(v, fp16):
     imgs = [torch.empty((3, 120, 200), dtype=torch.float32, device="cuda") for _ in cams]
     for c, im in zip(cams, imgs):
         b.render_feedback([c], fst)
-        b.update_residency(st, cst)
+        b.update_residency(fst if front else st, cst)
         b.render([c], [im], st)
     torch.cuda.synchronize()
     for f, im in enumerate(imgs):
