@@ -56,23 +56,18 @@ int make_table(const vm3dgs_renderer *r, const vm3dgs_camera *cams, int n, float
   return VM3DGS_OK;
 }
 
-// the batch's kernels, in stream order (also what a graph captures)
+// the batch's kernels, in stream order (also what a graph captures); batches
+// always take render context 0
 int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool timed) {
   const vm3dgs_scene *s = r->scene;
-  Ctl *ctl = r->at<Ctl>(r->lay.ctl);
+  const CtxLayout &C = r->lay.cx[0];
+  Ctl *ctl = r->at<Ctl>(C.ctl);
   ViewTable *dvt = r->at<ViewTable>(r->lay.views);
   load_views_kernel<<<1, 256, 0, st>>>(t, dvt);
-  Splats sp;
-  sp.s0 = r->at<float4>(r->lay.splat_s0);
-  sp.s1 = r->at<float4>(r->lay.splat_s1);
-  sp.s2 = r->at<float>(r->lay.splat_s2);
-  sp.depth = r->at<uint32_t>(r->lay.splat_depth);
-  sp.rect = r->at<uint32_t>(r->lay.splat_rect);
-  sp.touched = r->at<uint32_t>(r->lay.splat_touched);
-  sp.radius = r->at<float>(r->lay.splat_radius);
-  sp.tmask = r->at<uint64_t>(r->lay.splat_tmask);
+  const Splats sp = splats_of(r, 0);
   ProjectArgs pa{};
-  pa.ctl = ctl;
+  pa.ctl = r->at<Ctl>(r->lay.ctl);
+  pa.rctl = ctl;
   pa.draw = r->at<int4>(r->lay.draw);
   pa.draw_off = r->at<int64_t>(r->lay.draw_off);
   pa.pool = r->pool;
@@ -87,33 +82,34 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   int span = timed ? r->span_begin(VM3DGS_STAGE_PROJECT, st) : -1;
   launch_project_batched(pa, dvt, n, st);
   r->span_end(span, 2, st);
-  uint64_t *keys[2] = {r->at<uint64_t>(r->lay.keys0), r->at<uint64_t>(r->lay.keys1)};
-  uint32_t *vals[2] = {r->at<uint32_t>(r->lay.vals0), r->at<uint32_t>(r->lay.vals1)};
+  uint64_t *keys[2] = {r->at<uint64_t>(C.keys0), r->at<uint64_t>(C.keys1)};
+  uint32_t *vals[2] = {r->at<uint32_t>(C.vals0), r->at<uint32_t>(C.vals1)};
   span = timed ? r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st) : -1;
-  launch_scan_emit_batched(ctl, sp, r->dims.ncap, n, dvt, r->at<uint32_t>(r->lay.block_sums),
-                           r->at<uint32_t>(r->lay.offsets), keys[0], vals[0], r->dims.pair_cap, st);
+  launch_scan_emit_batched(ctl, sp, r->dims.ncap, n, dvt, r->at<uint32_t>(C.block_sums),
+                           r->at<uint32_t>(C.offsets), keys[0], vals[0], r->dims.pair_cap, st);
   r->span_end(span, 4, st);
   const int ntiles = t.tile_off[n];
   int tbits = 0;
   while ((1 << tbits) < ntiles) ++tbits;
   span = timed ? r->span_begin(VM3DGS_STAGE_SORT, st) : -1;
-  const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, 0, 32 + tbits, r->at<uint32_t>(r->lay.hist),
-                              r->at<uint32_t>(r->lay.lookback), r->dims.lookback_words,
-                              r->at<uint32_t>(r->lay.tile_ctr), st);
+  const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, 0, 32 + tbits, r->at<uint32_t>(C.hist),
+                              r->at<uint32_t>(C.lookback), r->dims.lookback_words,
+                              r->at<uint32_t>(C.tile_ctr), st);
   r->span_end(span, 2 + (32 + tbits + 7) / 8, st);
   if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
   if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
-  uint2 *ranges = r->at<uint2>(r->lay.ranges);
+  uint2 *ranges = r->at<uint2>(C.ranges);
   span = timed ? r->span_begin(VM3DGS_STAGE_RANGES, st) : -1;
   launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, 32, st);
   r->span_end(span, 1, st);
   span = timed ? r->span_begin(VM3DGS_STAGE_BLEND, st) : -1;
   launch_blend_batched(ranges, vals[cur], sp, r->dims.ncap * (int64_t)n, dvt, ntiles, r->prm.bg,
-                       r->at<uint32_t>(r->lay.tile_order), r->at<uint32_t>(r->lay.work), st);
+                       r->at<uint32_t>(C.tile_order), r->at<uint32_t>(C.work), st);
   r->span_end(span, 2, st);
   r->sorted_buf = cur;
   r->kf = KeyFormat{32, 0, 32, 0u, false};
   r->last_ntiles = ntiles;
+  r->last_ctx = 0;
   return VM3DGS_OK;
 }
 
@@ -135,10 +131,13 @@ extern "C" int vm3dgs_render_batched(vm3dgs_renderer *r, const vm3dgs_camera *ca
     r->copy_pending = false;
   }
   if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
+  if (r->ctx_recorded[0]) cudaStreamWaitEvent(st, r->ctx_free[0], 0);
   rc = enqueue_batch(r, t, st, r->timing);
   if (rc) return rc;
   cudaEventRecord(r->proj_done, st);  // conservatively after the whole batch
   r->proj_recorded = true;
+  cudaEventRecord(r->ctx_free[0], st);
+  r->ctx_recorded[0] = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, std::string("render_batched: ") + cudaGetErrorString(e));
 }
@@ -211,6 +210,7 @@ extern "C" int vm3dgs_batch_graph_launch(vm3dgs_renderer *r, const vm3dgs_camera
     r->copy_pending = false;
   }
   if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
+  if (r->ctx_recorded[0]) cudaStreamWaitEvent(st, r->ctx_free[0], 0);
   ViewTable *dvt = r->at<ViewTable>(r->lay.views);
   void *args[2] = {&t, &dvt};
   cudaKernelNodeParams kp{};
@@ -225,6 +225,9 @@ extern "C" int vm3dgs_batch_graph_launch(vm3dgs_renderer *r, const vm3dgs_camera
   const cudaError_t e = cudaGraphLaunch(r->graph_exec, st);
   cudaEventRecord(r->proj_done, st);
   r->proj_recorded = true;
+  cudaEventRecord(r->ctx_free[0], st);
+  r->ctx_recorded[0] = true;
+  r->last_ctx = 0;
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
 }
 
@@ -246,6 +249,7 @@ extern "C" int vm3dgs_autotune_tiles(vm3dgs_renderer *r, vm3dgs_camera *cams, in
     r->copy_pending = false;
   }
   if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
+  if (r->ctx_recorded[0]) cudaStreamWaitEvent(st, r->ctx_free[0], 0);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -293,6 +297,8 @@ extern "C" int vm3dgs_autotune_tiles(vm3dgs_renderer *r, vm3dgs_camera *cams, in
   r->timing = was_timing;
   cudaEventRecord(r->proj_done, st);
   r->proj_recorded = true;
+  cudaEventRecord(r->ctx_free[0], st);
+  r->ctx_recorded[0] = true;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;

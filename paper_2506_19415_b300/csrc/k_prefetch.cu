@@ -338,13 +338,13 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
 
 }  // namespace
 
-void launch_prefetch_features(const vm3dgs_renderer *r, int n_out, const vm3dgs_camera &cam,
+void launch_prefetch_features(const vm3dgs_renderer *r, const uint32_t *req, int n_out, const vm3dgs_camera &cam,
                               const vm3dgs_camera &prev, float *x, int32_t *base, cudaStream_t st) {
   FeatArgs a{};
   a.cam = cam;
   a.prev = prev;
   a.centroid = r->at<float4>(r->lay.centroid);
-  a.req = r->at<uint32_t>(r->lay.req);
+  a.req = req;
   a.NP = (int32_t)r->dims.NP;
   a.n_out = n_out;
   a.cx = r->scene_center[0]; a.cy = r->scene_center[1]; a.cz = r->scene_center[2];
@@ -363,7 +363,7 @@ extern "C" int vm3dgs_prefetch_features(vm3dgs_renderer *r, int32_t n_out, const
   if (!r || !cam || !prev || !x_dev) return fail(VM3DGS_E_INVAL, "null argument");
   if (n_out <= 0 || n_out % 16) return fail(VM3DGS_E_INVAL, "n_out must be a positive multiple of 16");
   if (r->state < 1) return fail(VM3DGS_E_STATE, "features before render_feedback");
-  launch_prefetch_features(r, n_out, *cam, *prev, x_dev, base_dev, (cudaStream_t)stream);
+  launch_prefetch_features(r, r->at<uint32_t>(r->lay.req), n_out, *cam, *prev, x_dev, base_dev, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, cudaGetErrorString(e));
 }
@@ -387,17 +387,22 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   if (n_out % 16 || p->cfg.n_in != 12 + n_out / 16)
     return fail(VM3DGS_E_INVAL, "network must have n_in = 12 + n_out / 16 and n_out a multiple of 16");
   // The whole step runs on the copy stream after this frame's page-table
-  // update, concurrently with the frame's render: it reads this frame's
-  // requests and writes only entries the frame does not use.  The next
-  // feedback or update waits for it.
+  // update, concurrently with the frame's render: it reads a copy of this
+  // frame's requests (so the next page determination waits only for the
+  // copy) and writes only entries the frame does not use.  The next update
+  // waits for it.
   cudaStream_t cst = copy_stream ? (cudaStream_t)copy_stream : (cudaStream_t)stream;
   cudaStreamWaitEvent(cst, r->res_done, 0);
   cudaStream_t st = cst;
   const int span = r->span_begin(VM3DGS_STAGE_PREFETCH, st);
+  uint32_t *req = r->at<uint32_t>(r->lay.pf_req);
+  cudaMemcpyAsync(req, r->at<uint32_t>(r->lay.req), 4 * r->dims.NP, cudaMemcpyDeviceToDevice, st);
+  cudaEventRecord(r->pf_req_done, st);
+  r->pf_req_pending = true;
   const PfLayout &PL = p->lay;
   float *x = p->at<float>(PL.feat);
   int32_t *base = r->at<int32_t>(r->lay.pf_base);
-  launch_prefetch_features(r, n_out, *cam, *prev, x, base, st);
+  launch_prefetch_features(r, req, n_out, *cam, *prev, x, base, st);
   float *logits = p->at<float>(PL.logits);
   pf_forward(p, x, 1, logits, st);
   const vm3dgs_scene *s = r->scene;
@@ -405,7 +410,7 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   a.ctl = r->at<Ctl>(r->lay.ctl);
   a.logits = logits;
   a.base_p = base;
-  a.req = r->at<uint32_t>(r->lay.req);
+  a.req = req;
   a.centroid = r->at<float4>(r->lay.centroid);
   a.err = r->at<float>(r->lay.err);
   a.pt_lod = r->at<int32_t>(r->lay.pt_lod);

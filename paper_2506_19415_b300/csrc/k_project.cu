@@ -268,7 +268,7 @@ template <int K, bool F16>
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_camera cam) {
   using R = Rec<K, F16>;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
-  if (blockIdx.x == 0 && threadIdx.x == 0) const_cast<Ctl *>(a.ctl)->r_drawn = a.ctl->draw_gauss;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.rctl->r_drawn = a.ctl->draw_gauss;
   const int nd = a.ctl->n_draw;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
   if (v >= views->n) return;
   const vm3dgs_camera cam = views->cam[v];
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
-  if (blockIdx.x == 0 && v == 0 && threadIdx.x == 0) const_cast<Ctl *>(a.ctl)->r_drawn = a.ctl->draw_gauss;
+  if (blockIdx.x == 0 && v == 0 && threadIdx.x == 0) a.rctl->r_drawn = a.ctl->draw_gauss;
   const int nd = a.ctl->n_draw;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
-  if (blockIdx.x == 0 && tid == 0) const_cast<Ctl *>(a.ctl)->r_drawn = a.ctl->draw_gauss;
+  if (blockIdx.x == 0 && tid == 0) a.rctl->r_drawn = a.ctl->draw_gauss;
   const int64_t nchunks = N / kChunk;
   const int64_t nitems = (nchunks + kChunksPerCta - 1) / kChunksPerCta;
   const int nd = a.ctl->n_draw;

@@ -154,16 +154,6 @@ Layout make_layout(const Dims &d) {
   L.link_ptr = take(8 * (NP + 1));
   L.link_col = take(4 * d.nlink);
   L.err = take(4 * NP * kMaxLevels);
-  L.splat_s0 = take(16 * N);
-  L.splat_s1 = take(16 * N);
-  L.splat_s2 = take(4 * N);
-  L.splat_depth = take(4 * N);
-  L.splat_rect = take(8 * N);
-  L.splat_touched = take(4 * N);
-  L.splat_radius = take(4 * N);
-  L.splat_tmask = take(8 * N);
-  L.block_sums = take(8 * d.scan_blocks);
-  L.offsets = take(4 * N);
   L.raster_queue = take(kRasterRecord * d.raster_cap);
   L.raster_count = take(32);
   L.raster_vis = take(4 * d.ntri);
@@ -177,31 +167,47 @@ Layout make_layout(const Dims &d) {
   L.pf_copy_seg = take(8 * (NP + 1));
   L.pf_count = take(16);
   L.pf_base = take(16);
-  L.keys0 = take(8 * d.pair_cap);
-  L.keys1 = take(8 * d.pair_cap);
-  L.vals0 = take(4 * d.pair_cap);
-  L.vals1 = take(4 * d.pair_cap);
-  L.ranges = take(8 * d.tile_cap * d.nviews);
+  L.pf_req = take(4 * NP);
   L.views = take(sizeof(ViewTable));
-  L.work = take(16);
-  L.tile_order = take(4 * d.tile_cap * d.nviews);
-  L.hist = take(4 * kMaxPasses * 256);
-  L.lookback = take(4 * d.lookback_words);
-  L.tile_ctr = take(4 * kMaxPasses);
+  for (int k = 0; k < kContexts; ++k) {
+    CtxLayout &C = L.cx[k];
+    C.ctl = take(sizeof(Ctl));
+    C.splat_s0 = take(16 * N);
+    C.splat_s1 = take(16 * N);
+    C.splat_s2 = take(4 * N);
+    C.splat_depth = take(4 * N);
+    C.splat_rect = take(8 * N);
+    C.splat_touched = take(4 * N);
+    C.splat_radius = take(4 * N);
+    C.splat_tmask = take(8 * N);
+    C.block_sums = take(8 * d.scan_blocks);
+    C.offsets = take(4 * N);
+    C.keys0 = take(8 * d.pair_cap);
+    C.keys1 = take(8 * d.pair_cap);
+    C.vals0 = take(4 * d.pair_cap);
+    C.vals1 = take(4 * d.pair_cap);
+    C.ranges = take(8 * d.tile_cap * d.nviews);
+    C.work = take(16);
+    C.tile_order = take(4 * d.tile_cap * d.nviews);
+    C.hist = take(4 * kMaxPasses * 256);
+    C.lookback = take(4 * d.lookback_words);
+    C.tile_ctr = take(4 * kMaxPasses);
+  }
   L.total = o;
   return L;
 }
 
-static Splats splats_of(const vm3dgs_renderer *r) {
+Splats splats_of(const vm3dgs_renderer *r, int k) {
+  const CtxLayout &C = r->lay.cx[k];
   Splats s;
-  s.s0 = r->at<float4>(r->lay.splat_s0);
-  s.s1 = r->at<float4>(r->lay.splat_s1);
-  s.s2 = r->at<float>(r->lay.splat_s2);
-  s.depth = r->at<uint32_t>(r->lay.splat_depth);
-  s.rect = r->at<uint32_t>(r->lay.splat_rect);
-  s.touched = r->at<uint32_t>(r->lay.splat_touched);
-  s.radius = r->at<float>(r->lay.splat_radius);
-  s.tmask = r->at<uint64_t>(r->lay.splat_tmask);
+  s.s0 = r->at<float4>(C.splat_s0);
+  s.s1 = r->at<float4>(C.splat_s1);
+  s.s2 = r->at<float>(C.splat_s2);
+  s.depth = r->at<uint32_t>(C.splat_depth);
+  s.rect = r->at<uint32_t>(C.splat_rect);
+  s.touched = r->at<uint32_t>(C.splat_touched);
+  s.radius = r->at<float>(C.splat_radius);
+  s.tmask = r->at<uint64_t>(C.splat_tmask);
   return s;
 }
 
@@ -318,9 +324,14 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   c.step = p->step0;
   c.last_move = -1000;
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.ctl), &c, sizeof(Ctl), cudaMemcpyHostToDevice, st), "copy", &rc);
+  for (int k = 0; k < kContexts; ++k) {
+    ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.cx[k].ctl), 0, sizeof(Ctl), st), "memset", &rc);
+    ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->ctx_free[k], cudaEventDisableTiming), "event", &rc);
+  }
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->copy_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->res_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_done, cudaEventDisableTiming), "event", &rc);
+  ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_req_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->fb_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->upd_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->proj_done, cudaEventDisableTiming), "event", &rc);
@@ -365,9 +376,12 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   if (r->graph_exec) cudaGraphExecDestroy(r->graph_exec);
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->pf_done) cudaEventDestroy(r->pf_done);
+  if (r->pf_req_done) cudaEventDestroy(r->pf_req_done);
   if (r->fb_done) cudaEventDestroy(r->fb_done);
   if (r->upd_done) cudaEventDestroy(r->upd_done);
   if (r->proj_done) cudaEventDestroy(r->proj_done);
+  for (auto e : r->ctx_free)
+    if (e) cudaEventDestroy(e);
   delete r;
 }
 
@@ -377,9 +391,9 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t NP = r->dims.NP;
-  if (r->pf_pending) {  // a prefetch still reads the previous requests and the page table
-    cudaStreamWaitEvent(st, r->pf_done, 0);
-    r->pf_pending = false;
+  if (r->pf_req_pending) {  // a prefetch still copies the previous request words
+    cudaStreamWaitEvent(st, r->pf_req_done, 0);
+    r->pf_req_pending = false;
   }
   // the last page-table update has read the request words cleared below
   if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
@@ -416,9 +430,9 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
 extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (r->pf_pending) {
-    cudaStreamWaitEvent(st, r->pf_done, 0);
-    r->pf_pending = false;
+  if (r->pf_req_pending) {
+    cudaStreamWaitEvent(st, r->pf_req_done, 0);
+    r->pf_req_pending = false;
   }
   if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
   launch_request_all(r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), r->dims.NP, st);
@@ -575,11 +589,16 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     r->copy_pending = false;
   }
   if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);  // page-table update on another stream
+  // render contexts alternate: this one's last render must be done with it
+  const int k = r->ctx;
+  if (r->ctx_recorded[k]) cudaStreamWaitEvent(st, r->ctx_free[k], 0);
+  const CtxLayout &C = r->lay.cx[k];
   const vm3dgs_scene *s = r->scene;
-  Ctl *ctl = r->at<Ctl>(r->lay.ctl);
-  Splats sp = splats_of(r);
+  Ctl *ctl = r->at<Ctl>(C.ctl);  // the scan, sort and ranges count with the context's control block
+  Splats sp = splats_of(r, k);
   ProjectArgs pa{};
-  pa.ctl = ctl;
+  pa.ctl = r->at<Ctl>(r->lay.ctl);
+  pa.rctl = ctl;
   pa.draw = r->at<int4>(r->lay.draw);
   pa.draw_off = r->at<int64_t>(r->lay.draw_off);
   pa.pool = r->pool;
@@ -591,8 +610,8 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
   pa.ncap = r->dims.ncap;
   pa.sp = sp;
   pa.maps = r->maps_ok ? &r->maps : nullptr;
-  uint64_t *keys[2] = {r->at<uint64_t>(r->lay.keys0), r->at<uint64_t>(r->lay.keys1)};
-  uint32_t *vals[2] = {r->at<uint32_t>(r->lay.vals0), r->at<uint32_t>(r->lay.vals1)};
+  uint64_t *keys[2] = {r->at<uint64_t>(C.keys0), r->at<uint64_t>(C.keys1)};
+  uint32_t *vals[2] = {r->at<uint32_t>(C.vals0), r->at<uint32_t>(C.vals1)};
   for (int v = 0; v < n_cams; ++v) {
     const vm3dgs_camera &c = cams[v];
     if (!images[v]) return fail(VM3DGS_E_INVAL, "null image");
@@ -615,21 +634,21 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     const int64_t max_tiles = (r->dims.pair_cap + kSortTile - 1) / kSortTile;
     if (passes < 1 || passes > kMaxPasses || (int64_t)passes * max_tiles * 256 > r->dims.lookback_words)
       return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
-    const SortHist sh{r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback), max_tiles,
-                      r->at<uint32_t>(r->lay.tile_ctr), lo_bit, passes};
-    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(r->lay.block_sums), r->at<uint32_t>(r->lay.offsets),
+    const SortHist sh{r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback), max_tiles, r->at<uint32_t>(C.tile_ctr),
+                      lo_bit, passes};
+    launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
                      keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, st);
     r->span_end(t, 5, st);
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
     const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
-                                       r->at<uint32_t>(r->lay.hist), r->at<uint32_t>(r->lay.lookback),
-                                       r->at<uint32_t>(r->lay.tile_ctr), st);
+                                       r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback),
+                                       r->at<uint32_t>(C.tile_ctr), st);
     r->span_end(t, passes, st);
     if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
     if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
-    uint2 *ranges = r->at<uint2>(r->lay.ranges);
-    uint32_t *order = r->at<uint32_t>(r->lay.tile_order), *work = r->at<uint32_t>(r->lay.work);
+    uint2 *ranges = r->at<uint2>(C.ranges);
+    uint32_t *order = r->at<uint32_t>(C.tile_order), *work = r->at<uint32_t>(C.work);
     t = r->span_begin(VM3DGS_STAGE_RANGES, st);
     launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, kf.tshift, st);
     launch_tile_order(ranges, ntiles, order, work, st);
@@ -643,20 +662,46 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     r->sorted_buf = cur;
     r->last_ntiles = ntiles;
   }
+  cudaEventRecord(r->ctx_free[k], st);
+  r->ctx_recorded[k] = true;
+  r->last_ctx = k;
+  r->ctx = (k + 1) % kContexts;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("render: ") + cudaGetErrorString(e));
   return VM3DGS_OK;
 }
 
+namespace {
+// orders stream after every outstanding page determination, update and render
+void wait_all(vm3dgs_renderer *r, cudaStream_t st) {
+  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);
+  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
+  for (int k = 0; k < kContexts; ++k)
+    if (r->ctx_recorded[k]) cudaStreamWaitEvent(st, r->ctx_free[k], 0);
+}
+}  // namespace
+
 extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *stream) {
   if (!r || !out) return fail(VM3DGS_E_INVAL, "null argument");
-  Ctl c;
+  Ctl c, cx[kContexts];
   int rc = 0;
-  if (r->upd_recorded) cudaStreamWaitEvent((cudaStream_t)stream, r->upd_done, 0);
-  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
-               "stats", &rc))
+  cudaStream_t st = (cudaStream_t)stream;
+  wait_all(r, st);
+  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "stats", &rc))
     return rc;
-  if (!cuda_ok(cudaStreamSynchronize((cudaStream_t)stream), "stats sync", &rc)) return rc;
+  for (int k = 0; k < kContexts; ++k)
+    if (!cuda_ok(cudaMemcpyAsync(&cx[k], r->at<void>(r->lay.cx[k].ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st),
+                 "stats", &rc))
+      return rc;
+  if (!cuda_ok(cudaStreamSynchronize(st), "stats sync", &rc)) return rc;
+  // the render contexts hold the pair counts and their sums; statuses from any block
+  const Ctl &last = cx[r->last_ctx];
+  c.pairs = last.pairs;
+  for (int k = 0; k < kContexts; ++k) {
+    c.acc_pairs += cx[k].acc_pairs;
+    c.acc_views += cx[k].acc_views;
+    if (c.status == 0) c.status = cx[k].status;
+  }
   std::memset(out, 0, sizeof(*out));
   out->frame = c.frame;
   out->requested = c.n_req;
@@ -691,8 +736,12 @@ extern "C" int vm3dgs_reset_sums(vm3dgs_renderer *r, void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   int rc = 0;
   const size_t off = offsetof(Ctl, acc_frames);
-  if (!cuda_ok(cudaMemsetAsync(r->scratch + r->lay.ctl + off, 0, sizeof(Ctl) - off, (cudaStream_t)stream), "reset", &rc))
-    return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  wait_all(r, st);
+  if (!cuda_ok(cudaMemsetAsync(r->scratch + r->lay.ctl + off, 0, sizeof(Ctl) - off, st), "reset", &rc)) return rc;
+  for (int k = 0; k < kContexts; ++k)
+    if (!cuda_ok(cudaMemsetAsync(r->scratch + r->lay.cx[k].ctl + off, 0, sizeof(Ctl) - off, st), "reset", &rc))
+      return rc;
   return VM3DGS_OK;
 }
 
@@ -700,16 +749,17 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
                                  void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // the visibility buffer may be on another stream
-  if (r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
-  Ctl c;
+  wait_all(r, st);  // the buffers may be written on other streams
+  Ctl c, cr;
   int rc = 0;
-  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(r->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc))
+  const Layout &L = r->lay;
+  const CtxLayout &C = L.cx[r->last_ctx];  // the last render's buffers
+  if (!cuda_ok(cudaMemcpyAsync(&c, r->at<void>(L.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc) ||
+      !cuda_ok(cudaMemcpyAsync(&cr, r->at<void>(C.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, st), "debug", &rc))
     return rc;
   if (!cuda_ok(cudaStreamSynchronize(st), "debug sync", &rc)) return rc;
-  const Layout &L = r->lay;
-  const int64_t NP = r->dims.NP, P = r->P, N = c.r_drawn < r->dims.ncap ? c.r_drawn : r->dims.ncap;
-  const int64_t M = c.pairs < r->dims.pair_cap ? c.pairs : r->dims.pair_cap;
+  const int64_t NP = r->dims.NP, P = r->P, N = cr.r_drawn < r->dims.ncap ? cr.r_drawn : r->dims.ncap;
+  const int64_t M = cr.pairs < r->dims.pair_cap ? cr.pairs : r->dims.pair_cap;
   const void *src = nullptr;
   int64_t n = 0;
   switch (what) {
@@ -730,7 +780,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       if (!dst) return VM3DGS_OK;
       if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
       std::vector<uint32_t> packed(2 * N);
-      if (N && !cuda_ok(cudaMemcpy(packed.data(), r->at<void>(L.splat_rect), 8 * N, cudaMemcpyDeviceToHost), "debug", &rc))
+      if (N && !cuda_ok(cudaMemcpy(packed.data(), r->at<void>(C.splat_rect), 8 * N, cudaMemcpyDeviceToHost), "debug", &rc))
         return rc;
       int32_t *o = (int32_t *)dst;
       for (int64_t i = 0; i < N; ++i) {
@@ -741,9 +791,9 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       }
       return VM3DGS_OK;
     }
-    case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(L.splat_depth); n = 4 * N; break;
-    case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(L.splat_radius); n = 4 * N; break;
-    case VM3DGS_DBG_SPLAT_TMASK: src = r->at<void>(L.splat_tmask); n = 8 * N; break;
+    case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(C.splat_depth); n = 4 * N; break;
+    case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(C.splat_radius); n = 4 * N; break;
+    case VM3DGS_DBG_SPLAT_TMASK: src = r->at<void>(C.splat_tmask); n = 8 * N; break;
     case VM3DGS_DBG_KEYS:
     case VM3DGS_DBG_VALUES: {
       // the sorted pairs as (tile << 32 | bits(depth), splat), whatever the
@@ -754,11 +804,11 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
       const KeyFormat kf = r->kf;
       std::vector<uint64_t> k(M);
-      if (M && !cuda_ok(cudaMemcpy(k.data(), r->at<void>(r->sorted_buf ? L.keys1 : L.keys0), 8 * M,
+      if (M && !cuda_ok(cudaMemcpy(k.data(), r->at<void>(r->sorted_buf ? C.keys1 : C.keys0), 8 * M,
                                    cudaMemcpyDeviceToHost), "debug", &rc))
         return rc;
       if (what == VM3DGS_DBG_VALUES && !kf.packed) {
-        if (M && !cuda_ok(cudaMemcpy(dst, r->at<void>(r->sorted_buf ? L.vals1 : L.vals0), 4 * M,
+        if (M && !cuda_ok(cudaMemcpy(dst, r->at<void>(r->sorted_buf ? C.vals1 : C.vals0), 4 * M,
                                      cudaMemcpyDeviceToHost), "debug", &rc))
           return rc;
         return VM3DGS_OK;
@@ -775,7 +825,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       }
       return VM3DGS_OK;
     }
-    case VM3DGS_DBG_RANGES: src = r->at<void>(L.ranges); n = 8 * (int64_t)r->last_ntiles; break;
+    case VM3DGS_DBG_RANGES: src = r->at<void>(C.ranges); n = 8 * (int64_t)r->last_ntiles; break;
     case VM3DGS_DBG_SPLAT_XY:
     case VM3DGS_DBG_SPLAT_CONIC:
     case VM3DGS_DBG_SPLAT_RGB: {
@@ -786,9 +836,9 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       std::vector<float4> a(N), b(N);
       std::vector<float> cc(N);
       if (N) {
-        bool ok = cuda_ok(cudaMemcpy(a.data(), r->at<void>(L.splat_s0), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
-                  cuda_ok(cudaMemcpy(b.data(), r->at<void>(L.splat_s1), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
-                  cuda_ok(cudaMemcpy(cc.data(), r->at<void>(L.splat_s2), 4 * N, cudaMemcpyDeviceToHost), "debug", &rc);
+        bool ok = cuda_ok(cudaMemcpy(a.data(), r->at<void>(C.splat_s0), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
+                  cuda_ok(cudaMemcpy(b.data(), r->at<void>(C.splat_s1), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
+                  cuda_ok(cudaMemcpy(cc.data(), r->at<void>(C.splat_s2), 4 * N, cudaMemcpyDeviceToHost), "debug", &rc);
         if (!ok) return rc;
       }
       float *o = (float *)dst;

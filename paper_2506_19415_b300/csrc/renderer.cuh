@@ -45,13 +45,24 @@ struct Splats {
   uint64_t *tmask;   // covered tiles of a rectangle of <= 64 tiles, row-major bits
 };
 
+// One render context: the buffers a render writes after its projection
+// (splats, pairs, tile ranges, sort scratch) and its own control block (the
+// drawn count it projected, its pair count, its running pair sums and
+// status).  Two contexts let the projection of frame t+1 run while frame t
+// is still sorted and blended.
+struct CtxLayout {
+  int64_t ctl, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched, splat_radius, splat_tmask,
+      block_sums, offsets, keys0, keys1, vals0, vals1, ranges, work, tile_order, hist, lookback, tile_ctr;
+};
+constexpr int kContexts = 2;
+
 // Layout of the scratch area; offsets in bytes.
 struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
-      clusters, link_ptr, link_col, err, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched,
-      splat_radius, splat_tmask, block_sums, offsets, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, centroid, pf_flag, pf_mask, pf_cand, pf_copies,
-      pf_copy_seg, pf_count, pf_base, views, work, tile_order, keys0, keys1, vals0, vals1, ranges, hist, lookback, tile_ctr, total;
+      clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, centroid,
+      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, total;
+  CtxLayout cx[kContexts];
 };
 
 struct Dims {
@@ -156,7 +167,8 @@ struct ProjMaps {
   CUtensorMap b[kMaxLevels];
 };
 struct ProjectArgs {
-  const Ctl *ctl;
+  const Ctl *ctl;   // the page table's control block (drawn count, draw list length)
+  Ctl *rctl;        // the render context's control block (receives the drawn count as projected)
   const int4 *draw;
   const int64_t *draw_off;
   const uint8_t *pool;
@@ -231,7 +243,8 @@ void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2
 // resets the work counters work[0..2] (the blend uses work[1]).
 void launch_tile_order(const uint2 *ranges, int ntiles, uint32_t *order, uint32_t *work, cudaStream_t st);
 
-void launch_prefetch_features(const vm3dgs_renderer *r, int n_out, const vm3dgs_camera &cam,
+// req: the request words the features count (the live ones or a snapshot)
+void launch_prefetch_features(const vm3dgs_renderer *r, const uint32_t *req, int n_out, const vm3dgs_camera &cam,
                               const vm3dgs_camera &prev, float *x, int32_t *base, cudaStream_t st);
 
 // The splat of pair j is vals[j], or the low bits (idx_mask) of packed[j]
@@ -264,8 +277,9 @@ struct vm3dgs_renderer {
   cudaEvent_t upd_done = nullptr;   // recorded after each page-table update and its in-line copies
   cudaEvent_t proj_done = nullptr;  // recorded after each render's last projection (pool reads done)
   bool res_recorded = false, fb_recorded = false, upd_recorded = false, proj_recorded = false;
-  cudaEvent_t pf_done = nullptr;    // recorded after a prefetch stopped reading this frame's requests
-  bool pf_pending = false;
+  cudaEvent_t pf_done = nullptr;    // recorded after a prefetch's page-table and pool writes
+  cudaEvent_t pf_req_done = nullptr;  // recorded after a prefetch took its copy of the request words
+  bool pf_pending = false, pf_req_pending = false;
   int64_t last_fb_pixels = 0;
   int64_t ncl = 0;  // proxy clusters in use
   double gbox_lo[3] = {0, 0, 0}, gbox_hi[3] = {0, 0, 0};  // holds every Gaussian mean
@@ -280,6 +294,10 @@ struct vm3dgs_renderer {
   vm::ViewTable graph_table{};
   int tuned_shape[4] = {0, 0, 0, 0};
   int sorted_buf = 0;     // pair buffer (0/1) holding the last view's sorted pairs
+  int ctx = 0;            // render context the next single-view render takes
+  int last_ctx = 0;       // render context of the last render
+  cudaEvent_t ctx_free[vm::kContexts] = {nullptr, nullptr};  // recorded after each render's last kernel
+  bool ctx_recorded[vm::kContexts] = {false, false};
   int last_ntiles = 0;
   // per-stage timing
   struct TimedSpan { int stage; int launches; cudaEvent_t a, b; };
@@ -307,3 +325,8 @@ struct vm3dgs_renderer {
   template <class T>
   T *at(int64_t off) const { return reinterpret_cast<T *>(scratch + off); }
 };
+
+namespace vm {
+// the splat arrays of render context k
+Splats splats_of(const vm3dgs_renderer *r, int k);
+}  // namespace vm

@@ -159,12 +159,15 @@ def test_zero_budget_streams_nothing(v):
     assert np.all(img == 0)
 
 
-@pytest.mark.parametrize("fp16,front", [(False, False), (True, False), (False, True), (True, True)])
-def test_feedback_on_own_stream_matches_one_stream(v, fp16, front):
-    """Page determination of frame t+1 (front: and its page-table update) on
-    its own stream, overlapping the rendering of frame t (copies on a third
-    stream), with no host sync between frames: every image, the final page
-    table and the running sums equal the single-stream run bit for bit."""
+@pytest.mark.parametrize("fp16,mode", [(False, "feedback"), (True, "feedback"), (False, "front"), (True, "front"),
+                                       (False, "two_renders"), (True, "two_renders")])
+def test_feedback_on_own_stream_matches_one_stream(v, fp16, mode):
+    """Page determination of frame t+1 on its own stream (front: with its
+    page-table update; two_renders: and consecutive renders on two streams,
+    i.e. the two render contexts in flight), copies on another stream, no host
+    sync between frames: every image, the final page table, the last render's
+    sorted pairs and the running sums equal the single-stream run bit for
+    bit."""
     import torch
     raw, sc = city_scene(levels=3, fanout=4, page_size=1024)
     scene = import_scene(v, raw, sc, fp16=fp16)
@@ -179,19 +182,21 @@ def test_feedback_on_own_stream_matches_one_stream(v, fp16, front):
         a.update_residency()
         ref.append(a.render([c])[0].cpu().numpy())
     b = v.Renderer(scene, cfg, pool_slots=6)
-    st, fst, cst = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    st, fst, cst, st2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     imgs = [torch.empty((3, 120, 200), dtype=torch.float32, device="cuda") for _ in cams]
-    for c, im in zip(cams, imgs):
+    for f, (c, im) in enumerate(zip(cams, imgs)):
         b.render_feedback([c], fst)
-        b.update_residency(fst if front else st, cst)
-        b.render([c], [im], st)
+        b.update_residency(st if mode == "feedback" else fst, cst)
+        b.render([c], [im], st2 if mode == "two_renders" and f % 2 else st)
     torch.cuda.synchronize()
     for f, im in enumerate(imgs):
         assert np.array_equal(im.cpu().numpy(), ref[f]), f"frame {f}"
     for what, dt in ((v.DBG_PT_LOD, np.int32), (v.DBG_PT_LAST, np.int32), (v.DBG_PT_SLOT, np.int32),
-                     (v.DBG_REQ, np.uint32), (v.DBG_FEEDBACK, np.uint64)):
+                     (v.DBG_REQ, np.uint32), (v.DBG_FEEDBACK, np.uint64), (v.DBG_KEYS, np.uint64),
+                     (v.DBG_VALUES, np.uint32), (v.DBG_RANGES, np.uint32), (v.DBG_SPLAT_DEPTH, np.uint32)):
         assert np.array_equal(a.debug(what, dt), b.debug(what, dt, st))
     sa, sb = a.stats(), b.stats(st)
-    for k in ("acc_frames", "acc_pairs", "acc_drawn_gaussians", "acc_streamed_bytes", "acc_missing", "acc_requested"):
+    for k in ("acc_frames", "acc_views", "acc_pairs", "acc_drawn_gaussians", "acc_streamed_bytes", "acc_missing",
+              "acc_requested", "pairs", "drawn_gaussians"):
         assert sa[k] == sb[k], k
     assert sb["status"] == 0
