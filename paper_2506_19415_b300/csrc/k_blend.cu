@@ -143,11 +143,12 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
                                                           float bg2, float *img, const uint32_t *order,
                                                           uint32_t ntiles, uint32_t *work) {
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are made of 8x8 blocks");
-  constexpr int NT = TW * TH / 2, BS = 2 * NT;
+  constexpr int NT = TW * TH / 2, BS = 2 * NT, NW = NT / 32;
   __shared__ float4 s0[BS];
   __shared__ float4 s1[BS];
-  __shared__ float4 s3[BS];
   __shared__ float s2[BS];
+  __shared__ uint8_t s_blocks[BS];      // bit w: the alpha box meets warp w's block
+  __shared__ uint16_t s_list[NW][BS];   // per warp, the staged splats meeting its block, in order
   __shared__ uint32_t s_tile;
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
@@ -165,8 +166,6 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
   const int px = bx + (lane & 7), py0 = by + (lane >> 3), py1 = py0 + 4;
   const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
   const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
-  // pixel centres of the warp's block
-  const float cx0 = (float)bx + 0.5f, cx1 = (float)bx + 7.5f, cy0 = (float)by + 0.5f, cy1 = (float)by + 7.5f;
   const uint2 rg = ranges[tile];
   const int n = (int)(rg.y - rg.x);
   bool done0 = !in0, done1 = !in1;
@@ -186,14 +185,32 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
         s0[k] = a;
         s1[k] = b;
         s2[k] = c;
-        s3[k] = alpha_box(sp, g);
+        // the 8x8 blocks (pixel centres) of the tile that the alpha box meets
+        const float4 bb = alpha_box(sp, g);
+        uint32_t m = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const float x0 = (float)(tx * TW + (w % (TW / 8)) * 8), y0 = (float)(ty * TH + (w / (TW / 8)) * 8);
+          const bool miss = bb.y < x0 + 0.5f || bb.x > x0 + 7.5f || bb.w < y0 + 0.5f || bb.z > y0 + 7.5f;
+          m |= miss ? 0u : 1u << w;
+        }
+        s_blocks[k] = (uint8_t)m;
       }
     }
     __syncthreads();
     const int cnt = min(BS, n - r0);
-    for (int j = 0; j < cnt && !(done0 && done1); ++j) {
-      const float4 bb = s3[j];
-      if (bb.y < cx0 || bb.x > cx1 || bb.w < cy0 || bb.z > cy1) continue;  // same for the whole warp
+    // this warp's list: the staged splats whose alpha box meets its block
+    int nl = 0;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      const int j = c0 + lane;
+      const bool meets = j < cnt && ((s_blocks[j] >> warp) & 1u);
+      const uint32_t bal = __ballot_sync(0xffffffffu, meets);
+      if (meets) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)j;
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    for (int i = 0; i < nl && !(done0 && done1); ++i) {
+      const int j = s_list[warp][i];
       const float4 a = s0[j], b = s1[j];
       // both pixels share x: the exponents of the two in packed FP32 pairs
       const float dx = a.x - fx;
