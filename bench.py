@@ -172,30 +172,32 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     dev = torch.device("cuda")
     st = torch.cuda.current_stream()
     H, W = cams[0].height, cams[0].width
-    # two image buffers: with e2e, frame i's image goes to pinned host memory
-    # on its own stream while frame i+1 renders into the other buffer
-    images = [torch.empty((3, H, W), dtype=torch.float32, device=dev) for _ in range(2)]
-    hosts = [torch.empty((3, H, W), dtype=torch.float32, pin_memory=True) for _ in range(2)] if e2e else None
+    # NB image buffers: with e2e, frame i's image goes to pinned host memory
+    # on its own stream while the next frames render into the other buffers
+    NB = 4
+    images = [torch.empty((3, H, W), dtype=torch.float32, device=dev) for _ in range(NB)]
+    hosts = [torch.empty((3, H, W), dtype=torch.float32, pin_memory=True) for _ in range(NB)] if e2e else None
     d2h = torch.cuda.Stream() if e2e else None
-    # page determination and page-table update of frame i+1 run on their own
-    # stream while frame i renders, and consecutive frames render on two
-    # streams (the renderer's two render contexts): the renderer orders them
-    # with events (update after the previous projection, render after the
-    # update, a context's reuse after its last render)
-    fst = torch.cuda.Stream()
+    # page determination (a frame ahead, on the double-buffered request
+    # words) and the page-table update of frame i+1 run on their own streams
+    # while frame i renders, and consecutive frames render on two streams (the
+    # renderer's two render contexts): the renderer orders them with events
+    # (update after the previous projection, render after the update, a
+    # buffer's or context's reuse after its last reader)
+    fbst, fst = torch.cuda.Stream(), torch.cuda.Stream()
     rst = [st, torch.cuda.Stream()]
-    copied = [torch.cuda.Event() for _ in range(2)] if e2e else None
-    rendered = [torch.cuda.Event() for _ in range(2)] if e2e else None
+    copied = [torch.cuda.Event() for _ in range(NB)] if e2e else None
+    rendered = [torch.cuda.Event() for _ in range(NB)] if e2e else None
     n = len(cams)
 
     def frame(i):
         c = [cams[i % n]]
-        b = i & 1
-        rs = rst[b]
-        r.render_feedback(c, fst)
+        b = i % NB
+        rs = rst[i & 1]
+        r.render_feedback(c, fbst)
         r.update_residency(fst, copy_stream)
         if e2e:
-            rs.wait_event(copied[b])   # the copy of frame i-2 out of this buffer is done
+            rs.wait_event(copied[b])   # the copy of frame i-NB out of this buffer is done
         r.render(c, [images[b]], rs)
         if pf is not None:
             if i % PREFETCH_EVERY == 0:
@@ -226,6 +228,7 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
         st.wait_stream(d2h)   # the last image is on the host before the clock stops
     st.wait_stream(rst[1])
     st.wait_stream(fst)
+    st.wait_stream(fbst)
     e1.record(st)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -472,7 +475,7 @@ def gpu_main(args):
                    "pool_bytes": W["pool_bytes"], "staging_bytes": 40 * 2048 * 236,
                    "l2": "per-frame inputs (2 GiB pool, splat and pair buffers) exceed the 126 MB L2",
                    "arm": "fp16 pool + copy stream + learned prefetch", "parallelism": "replicas, one renderer per GPU",
-                   "streams": "page determination and page-table update on a front stream, consecutive renders on two streams (two render contexts), event-ordered"},
+                   "streams": "page determination and page-table update on their own streams, consecutive renders on two streams (two render contexts), event-ordered"},
         "plain_vm": {"value": round(fps_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain / args.steps, 4),
                      "arm": "fp32 pool, in-line copies",
                      "missing_per_frame": plain["stats"]["acc_missing"] / max(plain["stats"]["acc_frames"], 1)},

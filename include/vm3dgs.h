@@ -19,13 +19,18 @@
  * Gaussians (Sec. 4.2 "Rendering").
  *
  * Frame protocol: vm3dgs_render_feedback -> vm3dgs_update_residency ->
- * vm3dgs_render.  Calls on one renderer are not thread safe.  Page
- * determination and the page-table update may be given a stream of their own
- * (the "front" stream): the renderer orders, with CUDA events, page
- * determination after the previous update, the update after the previous
- * render's projection (its last read of the pool and draw list), and the
- * render after the update, so that frame t+1's front work overlaps the
- * sorting and blending of frame t with results identical to one stream.
+ * vm3dgs_render.  Calls on one renderer are not thread safe.  Each call may
+ * be given a stream of its own; the renderer orders them with CUDA events so
+ * that the results equal those of one stream:
+ *   - page determination writes one of two request buffers, after the update
+ *     that read that buffer (two page determinations ago) and after the
+ *     previous page determination, so it may run a frame ahead;
+ *   - the update reads the latest page determination's buffer, after it and
+ *     after the previous render's projection (its last read of the pool and
+ *     draw list);
+ *   - a render takes one of two render contexts (splat, pair and sort
+ *     buffers), after the update and after the last render that used that
+ *     context, so consecutive renders may overlap.
  */
 #ifndef VM3DGS_H
 #define VM3DGS_H

@@ -245,76 +245,113 @@ __device__ __forceinline__ void box_min(const float *n, float d, const float *lo
   err = 1e-5f * mag + 1e-2f;
 }
 
-// Pass 1: triangles entirely behind the near plane, entirely more than 2
-// pixels beyond one side of the buffer, or in front of it with a screen box
-// that holds no pixel centre, cover no pixel centre; the others in front of
-// it are appended (warp-aggregated) to a dense list so that pass 2 runs
-// without idle lanes, those crossing it to the clipping list.  Whole clusters
-// are dropped first when their box lies, with a margin larger than the
-// rounding of either test, behind the near plane or beyond one of those side
-// planes (planes through the eye, so every triangle inside is beyond it too
-// and covers no pixel centre); lane k < 5 tests plane k.
-__global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int64_t ntri, const Cluster *cl,
-                                                          int64_t ncl, vm3dgs_camera cam, int ds, uint32_t *vis,
-                                                          uint32_t *nvis, uint32_t *clip, uint32_t *nclip) {
+// The five culling planes of a camera as n.p + d > 0 on the culled side:
+// x > kr z, x < kl z, y > kb z, y < kt z (planes through the eye 2 pixels
+// beyond each side of the buffer) and z < zn.
+struct CullPlanes {
+  float n[5][3], d[5];
+  float kr, kl, kb, kt, fxf, fyf, cxf, cyf;
+};
+
+__device__ __forceinline__ CullPlanes cull_planes(const vm3dgs_camera &cam, int ds) {
+  CullPlanes P;
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
-  const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
-  const float zn = 0.2f;
-  const float kr = ((float)Wf + 2.0f - cxf) / fxf, kl = (-2.0f - cxf) / fxf;
-  const float kb = ((float)Hf + 2.0f - cyf) / fyf, kt = (-2.0f - cyf) / fyf;
+  P.fxf = cam.fx / fds; P.fyf = cam.fy / fds; P.cxf = cam.cx / fds; P.cyf = cam.cy / fds;
+  P.kr = ((float)Wf + 2.0f - P.cxf) / P.fxf; P.kl = (-2.0f - P.cxf) / P.fxf;
+  P.kb = ((float)Hf + 2.0f - P.cyf) / P.fyf; P.kt = (-2.0f - P.cyf) / P.fyf;
   const float *V = cam.view;
-  const int lane = threadIdx.x & 31;
-  // this lane's plane as n.p + d > 0 on the culled side (lanes 5.. none)
-  float pn[3], pd;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float v0 = V[a], v1 = V[4 + a], v2 = V[8 + a];
-    pn[a] = lane == 0 ? v0 - kr * v2          // x > kr z
-          : lane == 1 ? kl * v2 - v0          // x < kl z
-          : lane == 2 ? v1 - kb * v2          // y > kb z
-          : lane == 3 ? kt * v2 - v1          // y < kt z
-          : lane == 4 ? -v2 : 0.0f;           // z < zn
+    P.n[0][a] = V[a] - P.kr * V[8 + a];
+    P.n[1][a] = P.kl * V[8 + a] - V[a];
+    P.n[2][a] = V[4 + a] - P.kb * V[8 + a];
+    P.n[3][a] = P.kt * V[8 + a] - V[4 + a];
+    P.n[4][a] = -V[8 + a];
   }
-  pd = lane == 0 ? V[3] - kr * V[11]
-     : lane == 1 ? kl * V[11] - V[3]
-     : lane == 2 ? V[7] - kb * V[11]
-     : lane == 3 ? kt * V[11] - V[7]
-     : lane == 4 ? zn - V[11] : -1.0f;
+  P.d[0] = V[3] - P.kr * V[11];
+  P.d[1] = P.kl * V[11] - V[3];
+  P.d[2] = V[7] - P.kb * V[11];
+  P.d[3] = P.kt * V[11] - V[7];
+  P.d[4] = 0.2f - V[11];
+  return P;
+}
+
+// Pass 1a: a thread per cluster.  A cluster is dropped when its box lies,
+// with a margin larger than the rounding of either test, behind the near
+// plane or beyond one of the side planes (planes through the eye, so every
+// triangle inside is beyond it too and covers no pixel centre); the others
+// are appended (warp-aggregated, in no particular order) to the live list.
+__global__ void __launch_bounds__(256) cluster_cull_kernel(const Cluster *cl, int64_t ncl, vm3dgs_camera cam, int ds,
+                                                           uint32_t *live, uint32_t *nlive) {
+  const CullPlanes P = cull_planes(cam, ds);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < ncl; b += stride) {
+    const int64_t ci = b + lane;
+    bool keep = false;
+    if (ci < ncl) {
+      const float4 *c4 = reinterpret_cast<const float4 *>(cl + ci);
+      const float4 u = __ldg(c4), w = __ldg(c4 + 1);
+      const float lo[3] = {u.x, u.y, u.z}, hi[3] = {w.x, w.y, w.z};
+      keep = true;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        float mn, err;
+        box_min(P.n[k], P.d[k], lo, hi, mn, err);
+        if (mn > err) keep = false;
+      }
+    }
+    const uint32_t km = __ballot_sync(0xffffffffu, keep);
+    uint32_t off = 0;
+    if (lane == 0 && km) off = atomicAdd(nlive, (uint32_t)__popc(km));
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (keep) live[off + __popc(km & ((1u << lane) - 1u))] = (uint32_t)ci;
+  }
+}
+
+// Pass 1b: a warp per live cluster, a triangle per lane.  Triangles entirely
+// behind the near plane, entirely more than 2 pixels beyond one side of the
+// buffer, or in front of it with a screen box that holds no pixel centre,
+// cover no pixel centre; the others in front of it are appended
+// (warp-aggregated) to a dense list so that pass 2 runs without idle lanes,
+// those crossing it to the clipping list.
+__global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int64_t ntri, const Cluster *cl,
+                                                          const uint32_t *live, const uint32_t *nlive,
+                                                          vm3dgs_camera cam, int ds, uint32_t *vis, uint32_t *nvis,
+                                                          uint32_t *clip, uint32_t *nclip) {
+  const CullPlanes P = cull_planes(cam, ds);
+  const float zn = 0.2f;
+  const float *V = cam.view;
+  const int lane = threadIdx.x & 31;
+  const int64_t n = *nlive;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // one cluster per warp (the next one's box already loading), then one
-  // triangle per lane
-  Cluster nx;
-  if (w0 < ncl) nx = cl[w0];
-  for (int64_t ci = w0; ci < ncl; ci += nw) {
-    const Cluster c = nx;
-    if (ci + nw < ncl) nx = cl[ci + nw];
-    float mn, err;
-    box_min(pn, pd, c.lo, c.hi, mn, err);
-    if (__ballot_sync(0xffffffffu, lane < 5 && mn > err)) continue;
-    const int64_t t = (int64_t)c.first + lane;
+  for (int64_t q = w0; q < n; q += nw) {
+    const uint32_t ci = live[q];
+    const uint32_t first = cl[ci].first, count = cl[ci].count;
+    const int64_t t = (int64_t)first + lane;
     bool keep = false;
-    if ((uint32_t)lane < c.count) {
+    if ((uint32_t)lane < count) {
       float4 p[3];
       load_tri(tv, ntri, t, p);
-      V3 q[3];
+      V3 c[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) q[k] = to_cam(V, p[k]);
+      for (int k = 0; k < 3; ++k) c[k] = to_cam(V, p[k]);
       int nin = 0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) nin += q[k].z >= zn;
+      for (int k = 0; k < 3; ++k) nin += c[k].z >= zn;
       if (nin > 0 && nin < 3) clip[atomicAdd(nclip, 1u)] = (uint32_t)t;
       if (nin == 3) {
         bool o1 = true, o2 = true, o3 = true, o4 = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          o1 = o1 && q[k].x > kr * q[k].z;
-          o2 = o2 && q[k].x < kl * q[k].z;
-          o3 = o3 && q[k].y > kb * q[k].z;
-          o4 = o4 && q[k].y < kt * q[k].z;
+          o1 = o1 && c[k].x > P.kr * c[k].z;
+          o2 = o2 && c[k].x < P.kl * c[k].z;
+          o3 = o3 && c[k].y > P.kb * c[k].z;
+          o4 = o4 && c[k].y < P.kt * c[k].z;
         }
-        keep = !(o1 || o2 || o3 || o4) && may_cover(q, fxf, fyf, cxf, cyf);
+        keep = !(o1 || o2 || o3 || o4) && may_cover(c, P.fxf, P.fyf, P.cxf, P.cyf);
       }
     }
     const uint32_t km = __ballot_sync(0xffffffffu, keep);
@@ -487,8 +524,10 @@ __global__ void clear_kernel(uint64_t *fb, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) fb[i] = ~0ull;
 }
 
-__global__ void __launch_bounds__(256) reduce_kernel(const uint64_t *fb, int64_t npix, const int64_t *link_ptr,
-                                                     const int32_t *link_col, int links, uint32_t *req, uint8_t *direct) {
+// Per pixel: the code of its page goes to dst (atomic max, once per page
+// and warp), and the page is marked direct.  With links dst is a separate
+// per-page word, spread to the page and its linked pages afterwards.
+__global__ void __launch_bounds__(256) reduce_kernel(const uint64_t *fb, int64_t npix, uint32_t *dst, uint8_t *direct) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < npix; base += stride) {
@@ -501,10 +540,22 @@ __global__ void __launch_bounds__(256) reduce_kernel(const uint64_t *fb, int64_t
     const uint32_t peers = __match_any_sync(0xffffffffu, page);
     const uint32_t mx = __reduce_max_sync(peers, enc);
     if (!valid || (peers & ((1u << lane) - 1u)) != 0u) continue;
-    atomicMax(req + page, mx);
+    atomicMax(dst + page, mx);
     direct[page] = 1;
-    if (links)
-      for (int64_t k = link_ptr[page]; k < link_ptr[page + 1]; ++k) atomicMax(req + link_col[k], mx);
+  }
+}
+
+// Links (Sec. 3.3): a page seen directly raises its own request word and
+// those of the pages it links to to its code (a thread per page, so each
+// page's links are walked once a frame).
+__global__ void __launch_bounds__(256) link_kernel(const uint32_t *dreq, int64_t NP, const int64_t *link_ptr,
+                                                   const int32_t *link_col, uint32_t *req) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += stride) {
+    const uint32_t v = dreq[p];
+    if (v == 0u) continue;
+    atomicMax(req + p, v);
+    for (int64_t k = link_ptr[p]; k < link_ptr[p + 1]; ++k) atomicMax(req + link_col[k], v);
   }
 }
 
@@ -525,15 +576,17 @@ void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
 void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, int64_t ntri,
                             const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
                             uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
-                            uint32_t *clip, cudaStream_t st) {
+                            uint32_t *clip, uint32_t *live, cudaStream_t st) {
   if (ntri <= 0 || ncl <= 0) return;
   // qcount: [0] queued medium triangles, [1] listed triangles, [2] queued
-  // huge triangles, [3] their bands, [4] triangles to clip
-  cudaMemsetAsync(qcount, 0, 5 * sizeof(uint32_t), st);
+  // huge triangles, [3] their bands, [4] triangles to clip, [5] live clusters
+  cudaMemsetAsync(qcount, 0, 6 * sizeof(uint32_t), st);
   const RasterQueues rq{reinterpret_cast<QTri *>(queue), bands, qcount, qcap, bcap};
+  cluster_cull_kernel<<<wave_grid((const void *)cluster_cull_kernel, 256, 0, ncl, 256), 256, 0, st>>>(
+      cl, ncl, cam, ds, live, qcount + 5);
   // one full wave each: the list lengths are known only on the device
-  raster_cull_kernel<<<wave_grid((const void *)raster_cull_kernel, 256, 0, ncl, 8), 256, 0, st>>>(
-      tv, ntri, cl, ncl, cam, ds, vis, qcount + 1, clip, qcount + 4);
+  raster_cull_kernel<<<full_wave((const void *)raster_cull_kernel, 256, 0), 256, 0, st>>>(
+      tv, ntri, cl, live, qcount + 5, cam, ds, vis, qcount + 1, clip, qcount + 4);
   raster_setup_kernel<<<full_wave((const void *)raster_setup_kernel, 256, 0), 256, 0, st>>>(
       tv, ntri, vis, qcount + 1, cam, ds, fb, rq);
   raster_clip_kernel<<<148, 128, 0, st>>>(tv, ntri, clip, qcount + 4, cam, ds, fb, rq);
@@ -544,10 +597,13 @@ void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, in
                                                                                           bcap, Wf, fb);
 }
 
-void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
-                            int links, uint32_t *req, uint8_t *direct, cudaStream_t st) {
-  reduce_kernel<<<wave_grid((const void *)reduce_kernel, 256, 0, npix, 256), 256, 0, st>>>(fb, npix, link_ptr, link_col,
-                                                                                           links, req, direct);
+void launch_feedback_reduce(const uint64_t *fb, int64_t npix, uint32_t *dst, uint8_t *direct, cudaStream_t st) {
+  reduce_kernel<<<wave_grid((const void *)reduce_kernel, 256, 0, npix, 256), 256, 0, st>>>(fb, npix, dst, direct);
+}
+
+void launch_feedback_links(const uint32_t *dreq, int64_t NP, const int64_t *link_ptr, const int32_t *link_col,
+                           uint32_t *req, cudaStream_t st) {
+  link_kernel<<<wave_grid((const void *)link_kernel, 256, 0, NP, 256), 256, 0, st>>>(dreq, NP, link_ptr, link_col, req);
 }
 
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st) {

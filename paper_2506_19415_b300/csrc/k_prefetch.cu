@@ -363,7 +363,7 @@ extern "C" int vm3dgs_prefetch_features(vm3dgs_renderer *r, int32_t n_out, const
   if (!r || !cam || !prev || !x_dev) return fail(VM3DGS_E_INVAL, "null argument");
   if (n_out <= 0 || n_out % 16) return fail(VM3DGS_E_INVAL, "n_out must be a positive multiple of 16");
   if (r->state < 1) return fail(VM3DGS_E_STATE, "features before render_feedback");
-  launch_prefetch_features(r, r->at<uint32_t>(r->lay.req), n_out, *cam, *prev, x_dev, base_dev, (cudaStream_t)stream);
+  launch_prefetch_features(r, r->req_buf(r->fb_buf), n_out, *cam, *prev, x_dev, base_dev, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, cudaGetErrorString(e));
 }
@@ -372,7 +372,7 @@ extern "C" int vm3dgs_prefetch_labels(vm3dgs_renderer *r, int32_t n_out, const i
                                       float *mask_dev, void *stream) {
   if (!r || !base_dev || !y_dev || !mask_dev) return fail(VM3DGS_E_INVAL, "null argument");
   if (n_out <= 0) return fail(VM3DGS_E_INVAL, "n_out must be positive");
-  labels_kernel<<<(n_out + 255) / 256, 256, 0, (cudaStream_t)stream>>>(r->at<uint32_t>(r->lay.req),
+  labels_kernel<<<(n_out + 255) / 256, 256, 0, (cudaStream_t)stream>>>(r->req_buf(r->fb_buf),
                                                                       (int32_t)r->dims.NP, n_out, base_dev, y_dev,
                                                                       mask_dev);
   cudaError_t e = cudaGetLastError();
@@ -396,9 +396,12 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   cudaStream_t st = cst;
   const int span = r->span_begin(VM3DGS_STAGE_PREFETCH, st);
   uint32_t *req = r->at<uint32_t>(r->lay.pf_req);
-  cudaMemcpyAsync(req, r->at<uint32_t>(r->lay.req), 4 * r->dims.NP, cudaMemcpyDeviceToDevice, st);
+  // the buffer the last update read (page determination of the next frame
+  // writes the other one)
+  cudaMemcpyAsync(req, r->req_buf(r->res_buf), 4 * r->dims.NP, cudaMemcpyDeviceToDevice, st);
   cudaEventRecord(r->pf_req_done, st);
   r->pf_req_pending = true;
+  r->pf_req_buf = r->res_buf;
   const PfLayout &PL = p->lay;
   float *x = p->at<float>(PL.feat);
   int32_t *base = r->at<int32_t>(r->lay.pf_base);

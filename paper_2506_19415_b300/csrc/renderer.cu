@@ -128,8 +128,8 @@ Layout make_layout(const Dims &d) {
   const int64_t NP = d.NP, P = d.P, N = d.ncap * d.nviews;
   L.ctl = take(sizeof(Ctl));
   L.fb = take(8 * d.fb_pixels);
-  L.req = take(4 * NP);
-  L.direct = take(NP);
+  L.req = take(2 * 4 * NP);   // two buffers
+  L.direct = take(2 * NP);
   L.reqlev = take(4 * NP);
   L.matched = take(NP);
   L.draw_info = take(4 * NP);
@@ -159,6 +159,8 @@ Layout make_layout(const Dims &d) {
   L.raster_vis = take(4 * d.ntri);
   L.raster_clip = take(4 * d.ntri);
   L.raster_bands = take(8 * d.raster_cap);
+  L.raster_live = take(4 * d.ncl_cap);
+  L.dreq = take(4 * NP);
   L.centroid = take(16 * NP);
   L.pf_flag = take(P * d.Smax);
   L.pf_mask = take((NP + 3) / 4 * 4);
@@ -332,6 +334,7 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->res_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->pf_req_done, cudaEventDisableTiming), "event", &rc);
+  for (auto &e : r->res_done_buf) ok = ok && cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->fb_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->upd_done, cudaEventDisableTiming), "event", &rc);
   ok = ok && cuda_ok(cudaEventCreateWithFlags(&r->proj_done, cudaEventDisableTiming), "event", &rc);
@@ -377,6 +380,8 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   if (r->graph) cudaGraphDestroy(r->graph);
   if (r->pf_done) cudaEventDestroy(r->pf_done);
   if (r->pf_req_done) cudaEventDestroy(r->pf_req_done);
+  for (auto e : r->res_done_buf)
+    if (e) cudaEventDestroy(e);
   if (r->fb_done) cudaEventDestroy(r->fb_done);
   if (r->upd_done) cudaEventDestroy(r->upd_done);
   if (r->proj_done) cudaEventDestroy(r->proj_done);
@@ -391,14 +396,22 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t NP = r->dims.NP;
-  if (r->pf_req_pending) {  // a prefetch still copies the previous request words
+  const int kb = r->fb_buf ^ 1;  // the request buffer this page determination writes
+  if (r->pf_req_pending && r->pf_req_buf == kb) {  // a prefetch still copies these request words
     cudaStreamWaitEvent(st, r->pf_req_done, 0);
     r->pf_req_pending = false;
   }
-  // the last page-table update has read the request words cleared below
-  if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
-  cudaMemsetAsync(r->at<void>(r->lay.req), 0, 4 * NP, st);
-  cudaMemsetAsync(r->at<void>(r->lay.direct), 0, NP, st);
+  // the update that read this buffer (two page determinations ago) is done;
+  // the visibility buffer and raster scratch are free
+  if (r->res_recorded_buf[kb]) cudaStreamWaitEvent(st, r->res_done_buf[kb], 0);
+  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);
+  uint32_t *req = r->req_buf(kb);
+  uint8_t *direct = r->direct_buf(kb);
+  cudaMemsetAsync(req, 0, 4 * NP, st);
+  cudaMemsetAsync(direct, 0, NP, st);
+  // with links the pixels' codes gather per page first, then spread
+  uint32_t *dreq = r->prm.links ? r->at<uint32_t>(r->lay.dreq) : req;
+  if (r->prm.links) cudaMemsetAsync(dreq, 0, 4 * NP, st);
   const int ds = r->prm.feedback_ds;
   float fpx = 0.0f;
   const int sp_fb = r->span_begin(VM3DGS_STAGE_FEEDBACK, st);
@@ -411,15 +424,18 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
                            r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
                            r->at<uint64_t>(r->lay.raster_bands), (uint32_t)r->dims.raster_cap,
-                           r->at<uint32_t>(r->lay.raster_vis), r->at<uint32_t>(r->lay.raster_clip), st);
-    launch_feedback_reduce(fb, npix, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), r->prm.links,
-                           r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), st);
+                           r->at<uint32_t>(r->lay.raster_vis), r->at<uint32_t>(r->lay.raster_clip),
+                           r->at<uint32_t>(r->lay.raster_live), st);
+    launch_feedback_reduce(fb, npix, dreq, direct, st);
     r->last_fb_pixels = npix;
     if (c.fy > fpx) fpx = c.fy;
   }
-  r->span_end(sp_fb, 6 * n_cams, st);
+  if (r->prm.links)
+    launch_feedback_links(dreq, NP, r->at<int64_t>(r->lay.link_ptr), r->at<int32_t>(r->lay.link_col), req, st);
+  r->span_end(sp_fb, 8 * n_cams + (r->prm.links ? 1 : 0), st);  // kernels: clear, cluster and triangle cull, setup, clip, medium, huge, reduce; links
   cudaEventRecord(r->fb_done, st);
   r->fb_recorded = true;
+  r->fb_buf = kb;
   r->f_px = fpx;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -430,14 +446,17 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
 extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   cudaStream_t st = (cudaStream_t)stream;
-  if (r->pf_req_pending) {
+  const int kb = r->fb_buf ^ 1;
+  if (r->pf_req_pending && r->pf_req_buf == kb) {
     cudaStreamWaitEvent(st, r->pf_req_done, 0);
     r->pf_req_pending = false;
   }
-  if (r->res_recorded) cudaStreamWaitEvent(st, r->res_done, 0);
-  launch_request_all(r->at<uint32_t>(r->lay.req), r->at<uint8_t>(r->lay.direct), r->dims.NP, st);
+  if (r->res_recorded_buf[kb]) cudaStreamWaitEvent(st, r->res_done_buf[kb], 0);
+  if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);
+  launch_request_all(r->req_buf(kb), r->direct_buf(kb), r->dims.NP, st);
   cudaEventRecord(r->fb_done, st);
   r->fb_recorded = true;
+  r->fb_buf = kb;
   r->f_px = 1.0f;
   r->state = 1;
   cudaError_t e = cudaGetLastError();
@@ -463,8 +482,8 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   const vm3dgs_scene *s = r->scene;
   ResidencyArgs a{};
   a.ctl = r->at<Ctl>(r->lay.ctl);
-  a.req = r->at<uint32_t>(r->lay.req);
-  a.direct = r->at<uint8_t>(r->lay.direct);
+  a.req = r->req_buf(r->fb_buf);
+  a.direct = r->direct_buf(r->fb_buf);
   a.reqlev = r->at<int32_t>(r->lay.reqlev);
   a.draw_info = r->at<int32_t>(r->lay.draw_info);
   a.matched = r->at<uint8_t>(r->lay.matched);
@@ -505,6 +524,9 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   r->span_end(sp_res, 1, st);
   cudaEventRecord(r->res_done, st);
   r->res_recorded = true;
+  cudaEventRecord(r->res_done_buf[r->fb_buf], st);
+  r->res_recorded_buf[r->fb_buf] = true;
+  r->res_buf = r->fb_buf;
   StreamArgs sa{};
   sa.count = &a.ctl->n_copies;
   sa.copies = a.copies;
@@ -764,8 +786,8 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
   int64_t n = 0;
   switch (what) {
     case VM3DGS_DBG_FEEDBACK: src = r->at<void>(L.fb); n = 8 * r->last_fb_pixels; break;
-    case VM3DGS_DBG_REQ: src = r->at<void>(L.req); n = 4 * NP; break;
-    case VM3DGS_DBG_DIRECT: src = r->at<void>(L.direct); n = NP; break;
+    case VM3DGS_DBG_REQ: src = r->req_buf(r->fb_buf); n = 4 * NP; break;
+    case VM3DGS_DBG_DIRECT: src = r->direct_buf(r->fb_buf); n = NP; break;
     case VM3DGS_DBG_REQUESTS: src = r->at<void>(L.requests); n = 16 * (int64_t)c.n_req; break;
     case VM3DGS_DBG_PT_LOD: src = r->at<void>(L.pt_lod); n = 4 * P; break;
     case VM3DGS_DBG_PT_LAST: src = r->at<void>(L.pt_last); n = 4 * P; break;

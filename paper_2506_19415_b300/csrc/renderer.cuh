@@ -60,7 +60,7 @@ constexpr int kContexts = 2;
 struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
-      clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, centroid,
+      clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
       pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, total;
   CtxLayout cx[kContexts];
 };
@@ -112,12 +112,16 @@ int64_t build_clusters(const float *verts, const int32_t *tris, const int32_t *f
 // large triangles (more than 16 pixels) are queued: queue holds qcap records of
 // kRasterRecord bytes, qcount is eight device words (32 bytes, 8-aligned)
 constexpr int64_t kRasterRecord = 64;
+// live: ncl words for the clusters that pass the frustum test
 void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, int64_t ntri,
                             const vm3dgs_camera &cam, int ds, uint64_t *fb, void *queue,
                             uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
-                            uint32_t *clip, cudaStream_t st);
-void launch_feedback_reduce(const uint64_t *fb, int64_t npix, const int64_t *link_ptr, const int32_t *link_col,
-                            int links, uint32_t *req, uint8_t *direct, cudaStream_t st);
+                            uint32_t *clip, uint32_t *live, cudaStream_t st);
+// per-page maximum of the pixel codes into dst (atomic max), direct flags
+void launch_feedback_reduce(const uint64_t *fb, int64_t npix, uint32_t *dst, uint8_t *direct, cudaStream_t st);
+// req[p] and req of p's linked pages raised to dreq[p], for every page with dreq[p] != 0
+void launch_feedback_links(const uint32_t *dreq, int64_t NP, const int64_t *link_ptr, const int32_t *link_col,
+                           uint32_t *req, cudaStream_t st);
 void launch_request_all(uint32_t *req, uint8_t *direct, int64_t NP, cudaStream_t st);
 
 struct ResidencyArgs {
@@ -273,6 +277,15 @@ struct vm3dgs_renderer {
   cudaEvent_t copy_done = nullptr;
   bool copy_pending = false;
   cudaEvent_t res_done = nullptr;   // recorded after each page-table update
+  // request words and direct flags are double-buffered: page determination
+  // writes buffer fb_buf ^ 1 while the update may still read buffer fb_buf
+  int fb_buf = 1;                   // buffer of the last page determination
+  cudaEvent_t res_done_buf[2] = {nullptr, nullptr};  // the last update that read buffer k
+  bool res_recorded_buf[2] = {false, false};
+  int pf_req_buf = 0;               // buffer the pending prefetch copies
+  int res_buf = 0;                  // buffer the last update read
+  uint32_t *req_buf(int k) const { return at<uint32_t>(lay.req) + k * dims.NP; }
+  uint8_t *direct_buf(int k) const { return at<uint8_t>(lay.direct) + k * dims.NP; }
   cudaEvent_t fb_done = nullptr;    // recorded after each page determination
   cudaEvent_t upd_done = nullptr;   // recorded after each page-table update and its in-line copies
   cudaEvent_t proj_done = nullptr;  // recorded after each render's last projection (pool reads done)

@@ -160,14 +160,17 @@ def test_zero_budget_streams_nothing(v):
 
 
 @pytest.mark.parametrize("fp16,mode", [(False, "feedback"), (True, "feedback"), (False, "front"), (True, "front"),
-                                       (False, "two_renders"), (True, "two_renders")])
+                                       (False, "two_renders"), (True, "two_renders"), (False, "split"),
+                                       (True, "split")])
 def test_feedback_on_own_stream_matches_one_stream(v, fp16, mode):
     """Page determination of frame t+1 on its own stream (front: with its
     page-table update; two_renders: and consecutive renders on two streams,
-    i.e. the two render contexts in flight), copies on another stream, no host
-    sync between frames: every image, the final page table, the last render's
-    sorted pairs and the running sums equal the single-stream run bit for
-    bit."""
+    i.e. the two render contexts in flight; split: as two_renders with page
+    determination and update on separate streams, so that page determination
+    runs a frame ahead on the double-buffered request words), copies on
+    another stream, no host sync between frames: every image, the final page
+    table, the last render's sorted pairs and the running sums equal the
+    single-stream run bit for bit."""
     import torch
     raw, sc = city_scene(levels=3, fanout=4, page_size=1024)
     scene = import_scene(v, raw, sc, fp16=fp16)
@@ -182,12 +185,12 @@ def test_feedback_on_own_stream_matches_one_stream(v, fp16, mode):
         a.update_residency()
         ref.append(a.render([c])[0].cpu().numpy())
     b = v.Renderer(scene, cfg, pool_slots=6)
-    st, fst, cst, st2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    st, fst, cst, st2, ust = (torch.cuda.Stream() for _ in range(5))
     imgs = [torch.empty((3, 120, 200), dtype=torch.float32, device="cuda") for _ in cams]
     for f, (c, im) in enumerate(zip(cams, imgs)):
         b.render_feedback([c], fst)
-        b.update_residency(st if mode == "feedback" else fst, cst)
-        b.render([c], [im], st2 if mode == "two_renders" and f % 2 else st)
+        b.update_residency({"feedback": st, "split": ust}.get(mode, fst), cst)
+        b.render([c], [im], st2 if mode in ("two_renders", "split") and f % 2 else st)
     torch.cuda.synchronize()
     for f, im in enumerate(imgs):
         assert np.array_equal(im.cpu().numpy(), ref[f]), f"frame {f}"
