@@ -167,7 +167,8 @@ def train_prefetcher(v, scene, W, width, height, n_paths=16, frames=60, steps=60
 PREFETCH_EVERY = 4   # frames between prefetch steps (the network predicts the next 15 frames' pages)
 
 
-def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None, pf=None, pf_thr=0.0):
+def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None, pf=None, pf_thr=0.0,
+            serial=False):
     import torch
     dev = torch.device("cuda")
     st = torch.cuda.current_stream()
@@ -186,6 +187,8 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     # buffer's or context's reuse after its last reader)
     fbst, fst = torch.cuda.Stream(), torch.cuda.Stream()
     rst = [st, torch.cuda.Stream()]
+    if serial:  # every call on one stream: each kernel's time is its own (roofline)
+        fbst = fst = rst[0] = rst[1] = st
     copied = [torch.cuda.Event() for _ in range(NB)] if e2e else None
     rendered = [torch.cuda.Event() for _ in range(NB)] if e2e else None
     n = len(cams)
@@ -435,6 +438,10 @@ def gpu_main(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist, pf=pf)
+    # the same frames with every call on one stream: per-kernel CUDA-event
+    # times without the other streams' kernels sharing the GPU, for the roofline
+    ser = run_arm(v, rh, cams, args.warmup, min(args.steps, 100), copy_stream, timing=True, dist=dist, pf=pf,
+                  serial=True)
     clk = clocks.stop()
     # end to end through the public API: the rendered image returns to pinned host memory every frame
     e2e = run_arm(v, rh, cams, 0, args.steps, copy_stream, e2e=True, dist=dist, pf=pf)
@@ -454,7 +461,12 @@ def gpu_main(args):
         return
     hs = head["stats"]
     frames = max(hs["acc_frames"], 1)
-    rl = roofline(v, head["stage"], hs, peaks, scene.info.record_bytes16, width, height)
+    rl = roofline(v, ser["stage"], ser["stats"], peaks, scene.info.record_bytes16, width, height)
+    rl_pipe = roofline(v, head["stage"], hs, peaks, scene.info.record_bytes16, width, height)
+    rl["timing"] = ("kernels timed by CUDA events in a single-stream pass over %d frames of the same walk "
+                    "(bench.py); in_pipeline: the same kernels as they run overlapped in the timed headline loop"
+                    % min(args.steps, 100))
+    rl["in_pipeline"] = {"kernels": rl_pipe["kernels"], "stage_ms": rl_pipe["stage_ms"]}
     launches_per_frame = sum(head["stage"][1]) / frames
     line = {
         "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
