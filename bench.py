@@ -137,12 +137,52 @@ def build_scene(W):
     return scene, t1 - t0, time.time() - t1
 
 
-def make_renderer(v, scene, W, fp16, width, height):
+def make_renderer(v, scene, W, fp16, width, height, pool_slots=None):
     cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=fp16,
                          max_width=width, max_height=height, tau0=1.0, step0=0.1)
+    if pool_slots is not None:
+        return v.Renderer(scene, cfg, pool_slots=pool_slots)
     if W["pool_bytes"] is None:
         return v.Renderer(scene, cfg, pool_slots=scene.info.n_pages)
     return v.Renderer(scene, cfg, pool_bytes=W["pool_bytes"])
+
+
+def quality_eval(v, scene, W, cams, every=25, frames=150):
+    """PSNR of the fp16 pool's images against the fp32 pool's (equal pool
+    bytes) along the first frames of the walk, both renderers from a cold
+    start on one stream; and the cold first frame's time."""
+    import torch
+    width, height = cams[0].width, cams[0].height
+    rs = [make_renderer(v, scene, W, fp16, width, height) for fp16 in (False, True)]
+    st = torch.cuda.current_stream()
+    imgs = [torch.empty((3, height, width), dtype=torch.float32, device="cuda") for _ in rs]
+    psnr, cold = [], []
+    for k, r in enumerate(rs):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        r.render_feedback([cams[0]], st)
+        r.update_residency(st)
+        r.render([cams[0]], [imgs[k]], st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        cold.append(round(e0.elapsed_time(e1), 3))
+    for f in range(1, frames + 1):
+        for k, r in enumerate(rs):
+            r.render_feedback([cams[f]], st)
+            r.update_residency(st)
+            r.render([cams[f]], [imgs[k]], st)
+        if f % every == 0:
+            a, b = (im.clamp(0.0, 1.0).double() for im in imgs)
+            mse = float(((a - b) ** 2).mean())
+            psnr.append(round(10.0 * math.log10(1.0 / max(mse, 1e-30)), 2))
+    st32, st16 = rs[0].stats(st), rs[1].stats(st)
+    del rs
+    torch.cuda.empty_cache()
+    return {"psnr_fp16_vs_fp32_db": psnr, "min_psnr_db": min(psnr), "frames": [f for f in range(every, frames + 1, every)],
+            "same_draw_list": st32["drawn_gaussians"] == st16["drawn_gaussians"],
+            "cold_first_frame_ms": {"fp32": cold[0], "fp16": cold[1]},
+            "note": "fp16 and fp32 pools of equal bytes, cold start, one stream; images clamped to [0, 1]"}
 
 
 def train_prefetcher(v, scene, W, width, height, n_paths=16, frames=60, steps=600):
@@ -451,6 +491,15 @@ def gpu_main(args):
         rn = make_renderer(v, scene, W, True, width, height)
         nopf = run_arm(v, rn, cams, args.warmup, args.steps, copy_stream, timing=True, dist=dist)
         del rn
+    # fp16 pool with the fp32 arm's slot count (equal pages, half the bytes), no prefetcher
+    eq = None
+    if W["pool_bytes"] is not None:
+        slots32 = W["pool_bytes"] // v.vm3dgs_pool_slot_bytes(scene, fp16_pool=False)
+        rq = make_renderer(v, scene, W, True, width, height, pool_slots=slots32)
+        eq = run_arm(v, rq, cams, args.warmup, args.steps, copy_stream, dist=dist)
+        eq["slots"] = int(slots32)
+        del rq
+    torch.cuda.empty_cache()
 
     (ms_head, ms_plain, ms_e2e), (fps, fps_plain, fps_e2e) = aggregate_ranks(
         [head["ms"], plain["ms"], e2e["ms"]], args.steps, world, dist, "cuda")
@@ -511,6 +560,13 @@ def gpu_main(args):
         "clocks": clk,
         "scene_build_s": {"generate": round(t_gen, 1), "prepare": round(t_build, 1)},
     }
+    if eq is not None:
+        line["fp16_equal_slots"] = {"value": round(1000.0 * args.steps / eq["ms"], 2), "unit": "frames/s",
+                                    "ms_per_step": round(eq["ms"] / args.steps, 4), "pool_slots": eq["slots"],
+                                    "arm": "fp16 pool with the fp32 arm's slot count, copy stream, no prefetcher",
+                                    "missing_per_frame": eq["stats"]["acc_missing"] / max(eq["stats"]["acc_frames"], 1)}
+    if world == 1 and W["pool_bytes"] is not None:
+        line["quality"] = quality_eval(v, scene, W, cams)
     if not args.no_batched and world == 1:
         line["batched_views"] = batched_views_eval(v)
     if not args.no_prefetch and world == 1:

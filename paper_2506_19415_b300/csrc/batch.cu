@@ -95,7 +95,7 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   const int cur = launch_sort(ctl, keys, vals, r->dims.pair_cap, 0, 32 + tbits, r->at<uint32_t>(C.hist),
                               r->at<uint32_t>(C.lookback), r->dims.lookback_words,
                               r->at<uint32_t>(C.tile_ctr), st);
-  r->span_end(span, 2 + (32 + tbits + 7) / 8, st);
+  r->span_end(span, 1 + (32 + tbits + 7) / 8, st);  // histograms, passes
   if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
   if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
   uint2 *ranges = r->at<uint2>(C.ranges);

@@ -313,13 +313,19 @@ __global__ void __launch_bounds__(256) cluster_cull_kernel(const Cluster *cl, in
 // Pass 1b: a warp per live cluster, a triangle per lane.  Triangles entirely
 // behind the near plane, entirely more than 2 pixels beyond one side of the
 // buffer, or in front of it with a screen box that holds no pixel centre,
-// cover no pixel centre; the others in front of it are appended
-// (warp-aggregated) to a dense list so that pass 2 runs without idle lanes,
-// those crossing it to the clipping list.
+// cover no pixel centre; the others in front of it are appended to a dense
+// list so that pass 2 runs without idle lanes (each warp gathers them in
+// shared memory and reserves list space once per kCullBuf entries, not once
+// per cluster: the list counter is a single contended word), those crossing
+// it to the clipping list.
+constexpr int kCullBuf = 256;
 __global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int64_t ntri, const Cluster *cl,
                                                           const uint32_t *live, const uint32_t *nlive,
                                                           vm3dgs_camera cam, int ds, uint32_t *vis, uint32_t *nvis,
                                                           uint32_t *clip, uint32_t *nclip) {
+  __shared__ uint32_t s_buf[8][kCullBuf];
+  uint32_t *buf = s_buf[threadIdx.x >> 5];
+  int nbuf = 0;  // warp-uniform
   const CullPlanes P = cull_planes(cam, ds);
   const float zn = 0.2f;
   const float *V = cam.view;
@@ -355,10 +361,23 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int6
       }
     }
     const uint32_t km = __ballot_sync(0xffffffffu, keep);
+    if (nbuf + __popc(km) > kCullBuf) {  // flush the warp's buffer
+      uint32_t off = 0;
+      if (lane == 0) off = atomicAdd(nvis, (uint32_t)nbuf);
+      off = __shfl_sync(0xffffffffu, off, 0);
+      for (int k = lane; k < nbuf; k += 32) vis[off + k] = buf[k];
+      __syncwarp();
+      nbuf = 0;
+    }
+    if (keep) buf[nbuf + __popc(km & ((1u << lane) - 1u))] = (uint32_t)t;
+    nbuf += __popc(km);
+    __syncwarp();
+  }
+  if (nbuf) {
     uint32_t off = 0;
-    if (lane == 0 && km) off = atomicAdd(nvis, (uint32_t)__popc(km));
+    if (lane == 0) off = atomicAdd(nvis, (uint32_t)nbuf);
     off = __shfl_sync(0xffffffffu, off, 0);
-    if (keep) vis[off + __popc(km & ((1u << lane) - 1u))] = (uint32_t)t;
+    for (int k = lane; k < nbuf; k += 32) vis[off + k] = buf[k];
   }
 }
 

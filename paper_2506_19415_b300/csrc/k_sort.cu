@@ -292,23 +292,6 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const ui
   if (blockIdx.x == 0 && threadIdx.x < kMaxPasses) tile_ctr[threadIdx.x] = 0;
 }
 
-__global__ void __launch_bounds__(256) sort_bases_kernel(uint32_t *hist, int passes) {
-  __shared__ uint32_t tmp[256];
-  for (int d = 0; d < passes; ++d) {
-    tmp[threadIdx.x] = hist[d * 256 + threadIdx.x];
-    __syncthreads();
-    // Hillis-Steele inclusive scan over 256 entries
-    for (int o = 1; o < 256; o <<= 1) {
-      uint32_t v = threadIdx.x >= o ? tmp[threadIdx.x - o] : 0;
-      __syncthreads();
-      tmp[threadIdx.x] += v;
-      __syncthreads();
-    }
-    hist[d * 256 + threadIdx.x] = threadIdx.x == 0 ? 0 : tmp[threadIdx.x - 1];
-    __syncthreads();
-  }
-}
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -318,7 +301,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 template <bool VALS>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
                                                                 uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
-                                                                const uint32_t *bases, uint32_t *status,
+                                                                const uint32_t *counts, uint32_t *status,
                                                                 uint32_t *tile_ctr) {
   constexpr int W = kSortThreads / 32;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -333,6 +316,23 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
   const int64_t ntiles = (M + kSortTile - 1) / kSortTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = lanemask_lt();
+  // global offset of digit tid: exclusive scan of the pass's digit counts
+  uint32_t dbase;
+  {
+    const uint32_t c = counts[tid];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_scan[w];
+    dbase = wpre + x - c;
+    __syncthreads();
+  }
   for (;;) {
     if (tid == 0) s_tile = (int64_t)atomicAdd(tile_ctr, 1u);
     for (int i = tid; i < W * 256; i += kSortThreads) s_wc[i] = 0;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       }
       *st = kFlagInc | ((excl + cnt) & kValMask);
     }
-    s_glob[tid] = bases[tid] + excl;
+    s_glob[tid] = dbase + excl;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
@@ -471,7 +471,6 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
   if (sh.hist) cudaMemsetAsync(sh.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
   emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap,
                                                                             gx, kf, sh);
-  if (sh.hist) sort_bases_kernel<<<1, 256, 0, st>>>(sh.hist, sh.passes);
 }
 
 void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
@@ -496,7 +495,6 @@ int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bi
   sort_hist_kernel<<<full_wave((const void *)sort_hist_kernel, 256, 0), 256, 0, st>>>(ctl, keys, pair_cap, lo_bit,
                                                                                       passes, hist, lookback, max_tiles,
                                                                                       tile_ctr);
-  sort_bases_kernel<<<1, 256, 0, st>>>(hist, passes);
   return 0;
 }
 

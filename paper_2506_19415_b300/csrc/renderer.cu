@@ -660,7 +660,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
                       lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
                      keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, st);
-    r->span_end(t, 5, st);
+    r->span_end(t, 4, st);  // scan reduce, scan blocks, scan offsets, emit
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
     const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,

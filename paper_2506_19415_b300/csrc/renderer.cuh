@@ -217,7 +217,8 @@ struct KeyFormat {
 };
 // The digit histograms of the coming sort (passes of 8 bits from lo_bit),
 // counted by the emission itself, which also clears the sort's look-back
-// words and tile counters; then the digits' bases.  hist null: none.
+// words and tile counters (each sort pass scans its own histogram into digit
+// bases).  hist null: none.
 struct SortHist {
   uint32_t *hist;
   uint32_t *lookback;
@@ -235,7 +236,7 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
 // sorts the keys alone.  Returns the buffer holding the result.
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
                 uint32_t *hist, uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
-// the same in two steps: digit histograms and bases (0 or -1), then the passes
+// the same in two steps: digit histograms (0 or -1), then the passes
 int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bit, int hi_bit, uint32_t *hist,
                      uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
 int launch_sort_passes(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
