@@ -135,16 +135,22 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   const float TW = (float)cam.tile_w, TH = (float)cam.tile_h;
   float x = src.pos(0), y = src.pos(1), z = src.pos(2);
   float o = src.opac();
-  sp.touched[out] = 0;
-  sp.tmask[out] = 0;
-  sp.rect[2 * out] = 0;
-  sp.rect[2 * out + 1] = 0;
-  sp.depth[out] = 0;
-  sp.radius[out] = 0.0f;
+  // a culled splat: no tiles, zero rectangle, depth and radius
+  auto culled = [&]() {
+    sp.touched[out] = 0;
+    sp.tmask[out] = 0;
+    sp.rect[2 * out] = 0;
+    sp.rect[2 * out + 1] = 0;
+    sp.depth[out] = 0;
+    sp.radius[out] = 0.0f;
+  };
   float tx = ((V[0] * x + V[1] * y) + V[2] * z) + V[3];
   float ty = ((V[4] * x + V[5] * y) + V[6] * z) + V[7];
   float tz = ((V[8] * x + V[9] * y) + V[10] * z) + V[11];
-  if (!(o > 0.0f) || !(tz > 0.2f)) return;
+  if (!(o > 0.0f) || !(tz > 0.2f)) {
+    culled();
+    return;
+  }
   float qw = src.rot(0), qx = src.rot(1), qy = src.rot(2), qz = src.rot(3);
   float sc[3] = {src.scale(0), src.scale(1), src.scale(2)};
   float xx = qx * qx, yy = qy * qy, zz = qz * qz;
@@ -201,7 +207,10 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   fx0 = fminf(fmaxf(fx0, 0.0f), (float)gx); fx1 = fminf(fmaxf(fx1, 0.0f), (float)gx);
   fy0 = fminf(fmaxf(fy0, 0.0f), (float)gy); fy1 = fminf(fmaxf(fy1, 0.0f), (float)gy);
   const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-  if (x0 >= x1 || y0 >= y1) return;
+  if (x0 >= x1 || y0 >= y1) {
+    culled();
+    return;
+  }
   float ia = cc / det, ib = -cb / det, ic = ca / det;
   // tiles of the rectangle met by the 3-sigma ellipse (all of a rectangle of
   // more than 64 tiles)
@@ -244,12 +253,13 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
       Y[15] = -SHC3A * dx * (x2 - 3.0f * y2);
     }
   }
+  // (colour is a continuous output: fused multiply-adds are fine here)
   float rgb[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) s += src.sh(k, c) * Y[k];
+    for (int k = 0; k < K; ++k) s = __fmaf_rn(src.sh(k, c), Y[k], s);
     s += 0.5f;
     rgb[c] = s > 0.0f ? s : 0.0f;
   }
