@@ -95,6 +95,86 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int
   }
 }
 
+// Single-pass exclusive scan of the tiles-touched counts into per-splat pair
+// offsets, with the total in ctl->pairs: CTAs take tiles of kScanItems splats
+// in order from a counter, publish their tile's sum, and obtain the sum of
+// all earlier tiles by a decoupled look-back in which warp 0 reads 32
+// predecessors' words per round trip (64-bit words: flag in the top two bits,
+// value below).  Waits are bounded: on expiry the kernel records
+// VM3DGS_E_TIMEOUT in the control block and goes on.  status (one word per
+// tile) and the counter must be zero at launch.
+constexpr uint64_t kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanFlags = 3ull << 62;
+__global__ void __launch_bounds__(kScanThreads) scan_single_kernel(Ctl *ctl, const uint32_t *touched, int64_t ncap,
+                                                                  int views, uint64_t *status, uint32_t *counter,
+                                                                  uint32_t *offsets) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_excl;
+  const int64_t N = n_total(ctl, ncap, views);
+  const int64_t ntiles = N > 0 ? (N + kScanItems - 1) / kScanItems : 1;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (tile >= ntiles) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = tile * kScanItems + (int64_t)threadIdx.x * kScanPer;
+  uint32_t cnt[kScanPer];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    cnt[k] = (i0 + k < N) ? touched[i0 + k] : 0;
+    s += cnt[k];
+  }
+  uint64_t tot;
+  uint64_t pre = block_excl_scan_1024(s, &tot);
+  if (threadIdx.x == 0)
+    *(volatile uint64_t *)(status + tile) = (tile == 0 ? kScanInc : kScanAgg) | tot;
+  if (threadIdx.x < 32) {
+    uint64_t excl = 0;
+    if (tile > 0) {
+      int64_t j = tile - 1;  // the nearest predecessor not yet summed
+      int spins = 0;
+      for (;;) {
+        const uint64_t w = j - lane >= 0 ? *(const volatile uint64_t *)(status + j - lane) : kScanInc;
+        const uint64_t f = w & kScanFlags;
+        const uint32_t inc = __ballot_sync(0xffffffffu, f == kScanInc);
+        const uint32_t ready = __ballot_sync(0xffffffffu, f != 0);
+        // lanes up to the nearest inclusive word (all 32 if none) must be ready
+        const int last = inc ? __ffs(inc) - 1 : 31;
+        const uint32_t need = last == 31 ? 0xffffffffu : (2u << last) - 1u;
+        if ((ready & need) == need) {
+          uint64_t v = lane <= last ? (w & ~kScanFlags) : 0;
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          excl += v;
+          if (inc) break;
+          j -= 32;
+        } else {
+          if (++spins > kSpinLimit) {
+            if (lane == 0) atomicCAS(&ctl->status, 0, VM3DGS_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (lane == 0) *(volatile uint64_t *)(status + tile) = kScanInc | (excl + tot);
+    }
+    if (lane == 0) s_excl = excl;
+  }
+  __syncthreads();
+  uint64_t off = s_excl + pre;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (i0 + k < N) offsets[i0 + k] = off < 0xFFFFFFFFull ? (uint32_t)off : 0xFFFFFFFFu;
+    off += cnt[k];
+  }
+  if (tile == ntiles - 1 && threadIdx.x == 0) {
+    const uint64_t total = s_excl + tot;
+    ctl->pairs = (int64_t)total;
+    ctl->acc_pairs += (int64_t)total;
+    ctl->acc_views += views;
+  }
+}
+
 // Per-splat exclusive pair offsets (saturated to 32 bits: offsets past the
 // pair capacity are never written).
 __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *ctl, const uint32_t *touched,
@@ -146,76 +226,162 @@ __device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t w, uint32_
   return q < c ? __fns(lo, 0, (int)q + 1) : 32u + __fns((uint32_t)(m >> 32), 0, (int)(q - c) + 1);
 }
 
-constexpr int kEmitChunk = 256;  // pairs per warp task
+// adds n to the depth-field digits 0 .. dpass-1 of the shifted key kd
+__device__ __forceinline__ void count_run(uint32_t (*hs)[256], uint64_t kd, int dpass, uint32_t n) {
+  for (int d = 0; d < dpass; ++d) atomicAdd(&hs[d][(kd >> (8 * d)) & 255u], n);
+}
 
-// Pair emission balanced over the whole grid (pairs of a splat: its covered
-// tiles in row-major order): warp task c writes pairs [256 c, 256 c + 256),
-// lane l the pairs 256 c + 32 k + l, so stores are coalesced whatever the
-// splat sizes.  The splat of a pair is the last one whose offset is <= the
-// pair index: for the task's first pair by a warp-wide search, then from the
-// previous pair's splat by a galloping search (runs of culled splats share one
-// offset).  With sh.hist the kernel also counts the sort's digits
+// What the emission writes per pair: the packed key (and value), and the
+// sort's digit counts in the CTA's shared-memory histograms.
+struct PairOut {
+  uint64_t *keys;
+  uint32_t *vals;
+  int64_t M;
+  KeyFormat kf;
+  uint32_t (*hs)[256];
+  bool hist;
+  int lo_bit, passes, dpass;  // digits 0 .. dpass-1 lie in the depth field (counted once per splat)
+  __device__ __forceinline__ void put(int64_t j, uint32_t tile, uint64_t dkey, uint32_t i) const {
+    const uint64_t key = ((uint64_t)tile << kf.tshift) | dkey;
+    if (j < M) {
+      if (kf.packed) {
+        keys[j] = key | (uint64_t)i;
+      } else {
+        keys[j] = key;
+        vals[j] = i;
+      }
+    }
+    if (hist) {
+      const uint64_t kd = key >> lo_bit;
+      for (int d = dpass; d < passes; ++d) atomicAdd(&hs[d][(kd >> (8 * d)) & 255u], 1u);
+    }
+  }
+};
+
+__device__ __forceinline__ PairOut pair_out(const Ctl *ctl, uint64_t *keys, uint32_t *vals, int64_t pair_cap,
+                                            const KeyFormat &kf, const SortHist &sh, uint32_t (*hs)[256]) {
+  PairOut po;
+  po.keys = keys;
+  po.vals = vals;
+  po.M = ctl->pairs < pair_cap ? ctl->pairs : pair_cap;
+  po.kf = kf;
+  po.hs = hs;
+  po.hist = sh.hist != nullptr;
+  po.lo_bit = sh.lo_bit;
+  po.passes = sh.passes;
+  po.dpass = po.hist ? max(0, min(sh.passes, (kf.tshift - sh.lo_bit) / 8)) : 0;
+  return po;
+}
+
+// the depth field of a splat's keys (its view depth's bits above 0.2f, clamped)
+__device__ __forceinline__ uint64_t depth_key(uint32_t db, const KeyFormat &kf) {
+  const uint64_t dmax = (1ull << kf.R) - 1ull;
+  return min((uint64_t)(db >= kf.base ? db - kf.base : 0u), dmax) << kf.ib;
+}
+
+__device__ __forceinline__ void hist_flush(const SortHist &sh, uint32_t (*hs)[256]) {
+  __syncthreads();
+  for (int i2 = threadIdx.x; i2 < sh.passes * 256; i2 += blockDim.x) {
+    const uint32_t v2 = (&hs[0][0])[i2];
+    if (v2) atomicAdd(&sh.hist[i2], v2);
+  }
+}
+
+constexpr uint32_t kSmallSplat = 32;  // pairs a splat may have to be dealt out with others
+constexpr uint32_t kPiece = 256;      // pairs per piece of a larger splat
+
+// Pair emission (pairs of a splat: its covered tiles in row-major order, at
+// its scanned offset), part 1: a warp takes 32 consecutive splats, a lane
+// each, with coalesced loads of their records.  The pairs of the splats with
+// at most 32 of them are dealt out to the lanes together (lane g of a round
+// writes pair g of the concatenation, its splat found by a binary search over
+// the lanes' inclusive counts and its record fetched by shuffles), so stores
+// are contiguous and no lane walks the offsets.  Larger splats are cut into
+// pieces of kPiece pairs, listed for part 2.  Digits that lie in the depth
+// field are the same for all pairs of a splat and are counted once per
+// splat.  With sh.hist the kernel also counts the sort's digits
 // (shared-memory histograms merged into sh.hist) and clears the sort's
 // look-back words and tile counters.
 __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
                                                    uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
-                                                   KeyFormat kf, SortHist sh) {
+                                                   KeyFormat kf, SortHist sh, uint64_t *pieces,
+                                                   uint32_t *piece_ctr, int64_t piece_cap) {
   __shared__ uint32_t hs[kMaxPasses][256];
   if (sh.hist) {
     for (int i = threadIdx.x; i < sh.passes * 256; i += blockDim.x) (&hs[0][0])[i] = 0;
     __syncthreads();
   }
-  const uint64_t dmax = (1ull << kf.R) - 1ull;
+  const PairOut po = pair_out(ctl, keys, vals, pair_cap, kf, sh, hs);
   const int64_t N = n_drawn(ctl, ncap);
-  int64_t M = ctl->pairs;
-  if (M > pair_cap) M = pair_cap;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp0; c * kEmitChunk < M; c += nwarps) {
-    const uint32_t j0 = (uint32_t)(c * kEmitChunk);
-    int64_t i = warp_find(offsets, N, j0, lane);  // last splat with offset <= j0
-    for (int k = 0; k < kEmitChunk / 32; ++k) {
-      const uint32_t j = j0 + 32u * k + lane;
-      if ((int64_t)j >= M) break;
-      if (i + 1 < N && offsets[i + 1] <= j) {
-        // gallop over the splats without pairs, then bisect
-        int64_t lo2 = i + 1, step = 1;
-        while (lo2 + step < N && offsets[lo2 + step] <= j) { lo2 += step; step <<= 1; }
-        int64_t hi2 = lo2 + step < N ? lo2 + step - 1 : N - 1;
-        while (lo2 < hi2) {
-          const int64_t mid = (lo2 + hi2 + 1) >> 1;
-          if (offsets[mid] <= j) lo2 = mid; else hi2 = mid - 1;
-        }
-        i = lo2;
+  for (int64_t b = warp0 * 32; b < N; b += nwarps * 32) {
+    const int64_t i = b + lane;
+    uint32_t cnt = 0, off = 0, rx = 0, ry = 0;
+    uint64_t tm = 0, dkey = 0;
+    if (i < N) cnt = sp.touched[i];
+    const bool big = cnt > kSmallSplat;
+    if (cnt && !big) {
+      off = offsets[i];
+      rx = sp.rect[2 * i];
+      ry = sp.rect[2 * i + 1];
+      tm = sp.tmask[i];
+      dkey = depth_key(sp.depth[i], kf);
+      if (po.hist) count_run(hs, dkey >> po.lo_bit, po.dpass, cnt);
+    }
+    const uint32_t small = big ? 0u : cnt;
+    uint32_t incl = small;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
+      const uint32_t g = g0 + (uint32_t)lane;
+      // owner: the number of lanes whose inclusive count is <= g
+      int L = 0;
+#pragma unroll
+      for (int st = 16; st >= 1; st >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, L + st - 1);
+        if (v <= g) L += st;
       }
-      const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
-      const uint32_t q = covered_tile(sp.tmask[i], w, h, j - offsets[i]);
-      const uint32_t tile = (y0 + q / w) * (uint32_t)gx + x0 + q % w;
-      const uint32_t db = sp.depth[i];
-      const uint64_t doff = min((uint64_t)(db >= kf.base ? db - kf.base : 0u), dmax);
-      const uint64_t key = ((uint64_t)tile << kf.tshift) | (doff << kf.ib);
-      if (kf.packed) {
-        keys[j] = key | (uint64_t)i;
-      } else {
-        keys[j] = key;
-        vals[j] = (uint32_t)i;
+      L = min(L, 31);
+      const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Ln = __shfl_sync(0xffffffffu, small, L);
+      const uint32_t Lrx = __shfl_sync(0xffffffffu, rx, L), Lry = __shfl_sync(0xffffffffu, ry, L);
+      const uint64_t Ltm = __shfl_sync(0xffffffffu, tm, L), Ld = __shfl_sync(0xffffffffu, dkey, L);
+      const uint32_t Loff = __shfl_sync(0xffffffffu, off, L);
+      if (g < total) {
+        const uint32_t q = g - (Li - Ln);
+        const uint32_t x0 = Lrx & 0xFFFFu, w = (Lrx >> 16) - x0, y0 = Lry & 0xFFFFu, h = (Lry >> 16) - y0;
+        const uint32_t qt = covered_tile(Ltm, w, h, q);
+        po.put((int64_t)Loff + q, (y0 + qt / w) * (uint32_t)gx + x0 + qt % w, Ld, (uint32_t)(b + L));
       }
-      if (sh.hist) {
-        const uint64_t kd = key >> sh.lo_bit;
-        for (int d = 0; d < sh.passes; ++d) atomicAdd(&hs[d][(kd >> (8 * d)) & 255u], 1u);
+    }
+    // larger splats: their pieces to the list (one reservation per warp)
+    const uint32_t np = big ? (cnt + kPiece - 1) / kPiece : 0u;
+    uint32_t pincl = np;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, pincl, d);
+      if (lane >= d) pincl += o;
+    }
+    const uint32_t ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+    if (ptotal) {
+      uint32_t pb = 0;
+      if (lane == 0) pb = atomicAdd(piece_ctr, ptotal);
+      pb = __shfl_sync(0xffffffffu, pb, 0);
+      for (uint32_t k = 0; k < np; ++k) {
+        const int64_t slot = (int64_t)pb + (pincl - np) + k;
+        if (slot < piece_cap) pieces[slot] = ((uint64_t)i << 32) | k;
       }
     }
   }
   if (sh.hist) {
-    __syncthreads();
-    for (int i2 = threadIdx.x; i2 < sh.passes * 256; i2 += blockDim.x) {
-      const uint32_t v2 = (&hs[0][0])[i2];
-      if (v2) atomicAdd(&sh.hist[i2], v2);
-    }
+    hist_flush(sh, hs);
     // the look-back words and tile counters of the coming sort
-    const int64_t ntiles = (M + kSortTile - 1) / kSortTile;
+    const int64_t ntiles = (po.M + kSortTile - 1) / kSortTile;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int d = 0; d < sh.passes; ++d) {
       uint32_t *lb = sh.lookback + (int64_t)d * sh.max_tiles * 256;
@@ -224,6 +390,41 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     if (blockIdx.x == 0 && threadIdx.x < kMaxPasses) sh.tile_ctr[threadIdx.x] = 0;
   }
 }
+
+// Pair emission, part 2: a warp per piece of kPiece pairs of a larger splat.
+__global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats sp, const uint32_t *offsets,
+                                                          uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
+                                                          KeyFormat kf, SortHist sh, const uint64_t *pieces,
+                                                          const uint32_t *piece_ctr, int64_t piece_cap) {
+  __shared__ uint32_t hs[kMaxPasses][256];
+  if (sh.hist) {
+    for (int i = threadIdx.x; i < sh.passes * 256; i += blockDim.x) (&hs[0][0])[i] = 0;
+    __syncthreads();
+  }
+  const PairOut po = pair_out(ctl, keys, vals, pair_cap, kf, sh, hs);
+  const int64_t n = min((int64_t)*piece_ctr, piece_cap);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp0; p < n; p += nwarps) {
+    const uint64_t e = pieces[p];
+    const int64_t i = (int64_t)(e >> 32);
+    const uint32_t k = (uint32_t)e;
+    const uint32_t cnt = sp.touched[i], off = offsets[i];
+    const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
+    const uint64_t tm = sp.tmask[i], dkey = depth_key(sp.depth[i], kf);
+    if (po.hist && k == 0 && lane == 0) count_run(hs, dkey >> po.lo_bit, po.dpass, cnt);
+    const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
+    const uint32_t q1 = min(cnt, (k + 1) * kPiece);
+    for (uint32_t q = k * kPiece + lane; q < q1; q += 32) {
+      const uint32_t qt = covered_tile(tm, w, h, q);
+      po.put((int64_t)off + q, (y0 + qt / w) * (uint32_t)gx + x0 + qt % w, dkey, (uint32_t)i);
+    }
+  }
+  if (sh.hist) hist_flush(sh, hs);
+}
+
+constexpr int kEmitChunk = 256;  // pairs per warp task of the batched emission
 
 // Pairs of all views of a batch: splat record v * N + i belongs to view v;
 // the key's tile field is the view's first global tile plus its local tile.
@@ -462,15 +663,19 @@ __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap,
 
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, cudaStream_t st) {
+                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
-  uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
-  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs);
-  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
+  // block_sums: nb status words, then the tile counter
+  uint64_t *status = reinterpret_cast<uint64_t *>(block_sums);
+  cudaMemsetAsync(status, 0, sizeof(uint64_t) * (nb + 1), st);
+  scan_single_kernel<<<(unsigned)(nb > 0 ? nb : 1), kScanThreads, 0, st>>>(
+      ctl_w, sp.touched, ncap, 1, status, reinterpret_cast<uint32_t *>(status + nb), offsets);
   if (sh.hist) cudaMemsetAsync(sh.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
+  cudaMemsetAsync(piece_ctr, 0, sizeof(uint32_t), st);
   emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap,
-                                                                            gx, kf, sh);
+                                                                            gx, kf, sh, pieces, piece_ctr, piece_cap);
+  emit_pieces_kernel<<<full_wave((const void *)emit_pieces_kernel, 256, 0), 256, 0, st>>>(
+      ctl, sp, offsets, keys, vals, pair_cap, gx, kf, sh, pieces, piece_ctr, piece_cap);
 }
 
 void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,

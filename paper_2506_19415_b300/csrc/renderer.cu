@@ -111,6 +111,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.scan_blocks = (d.ncap * d.nviews + kScanItems - 1) / kScanItems;
   d.lookback_words = (int64_t)kMaxPasses * ((d.pair_cap + kSortTile - 1) / kSortTile) * 256;
   d.ncl_cap = (d.ntri + 31) / 32 + d.NP + 1;
+  d.piece_cap = d.pair_cap / 28 + 1;
   d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
@@ -182,7 +183,7 @@ Layout make_layout(const Dims &d) {
     C.splat_touched = take(4 * N);
     C.splat_radius = take(4 * N);
     C.splat_tmask = take(8 * N);
-    C.block_sums = take(8 * d.scan_blocks);
+    C.block_sums = take(8 * (d.scan_blocks + 1));  // scan status words and tile counter
     C.offsets = take(4 * N);
     C.keys0 = take(8 * d.pair_cap);
     C.keys1 = take(8 * d.pair_cap);
@@ -194,6 +195,8 @@ Layout make_layout(const Dims &d) {
     C.hist = take(4 * kMaxPasses * 256);
     C.lookback = take(4 * d.lookback_words);
     C.tile_ctr = take(4 * kMaxPasses);
+    C.pieces = take(8 * d.piece_cap);
+    C.piece_ctr = take(16);
   }
   L.total = o;
   return L;
@@ -659,8 +662,9 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     const SortHist sh{r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback), max_tiles, r->at<uint32_t>(C.tile_ctr),
                       lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
-                     keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, st);
-    r->span_end(t, 4, st);  // scan reduce, scan blocks, scan offsets, emit
+                     keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, r->at<uint64_t>(C.pieces),
+                     r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, st);
+    r->span_end(t, 3, st);  // scan, emit, emit pieces
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
     const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,

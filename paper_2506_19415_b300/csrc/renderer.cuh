@@ -52,7 +52,8 @@ struct Splats {
 // is still sorted and blended.
 struct CtxLayout {
   int64_t ctl, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched, splat_radius, splat_tmask,
-      block_sums, offsets, keys0, keys1, vals0, vals1, ranges, work, tile_order, hist, lookback, tile_ctr;
+      block_sums, offsets, keys0, keys1, vals0, vals1, ranges, work, tile_order, hist, lookback, tile_ctr, pieces,
+      piece_ctr;
 };
 constexpr int kContexts = 2;
 
@@ -70,6 +71,7 @@ struct Dims {
   int ukey_cap, free_cap;
   int64_t raster_cap;
   int64_t ncl_cap;  // proxy clusters (at most 32 triangles of one page each)
+  int64_t piece_cap;  // pieces of 256 pairs of the splats with more than 32 pairs (at most pairs / 28)
   int64_t nviews;  // views a batch may hold (max_views)
 };
 
@@ -226,9 +228,11 @@ struct SortHist {
   uint32_t *tile_ctr;
   int lo_bit, passes;
 };
+// pieces (piece_cap words) and piece_ctr: the list of kPiece-pair pieces of
+// the splats with more than 32 pairs, written by the first emission kernel
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, cudaStream_t st);
+                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, cudaStream_t st);
 
 // sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
 // returns the index (0 or 1) of the buffer holding the result
