@@ -9,12 +9,12 @@
 
 #include "mlp.cuh"
 #include "prefetcher.cuh"
+#include "block_sel.cuh"
 #include "renderer.cuh"
 
 namespace vm {
 namespace {
 
-constexpr int RT = 1024;
 
 struct FeatArgs {
   vm3dgs_camera cam, prev;
@@ -101,65 +101,6 @@ struct PlaceArgs {
   float campos[3];
 };
 
-struct ScanSmem { int64_t warp[32]; };
-
-__device__ int64_t bscan(int64_t v, int64_t *total, ScanSmem &sm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sm.warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int64_t t = sm.warp[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int64_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    sm.warp[lane] = t;
-  }
-  __syncthreads();
-  const int64_t pre = (warp ? sm.warp[warp - 1] : 0) + x - v;
-  *total = sm.warp[31];
-  __syncthreads();
-  return pre;
-}
-
-constexpr int kSmemKeys = 16384;
-// bitonic sort of n (a power of two) keys, in shared memory when they fit
-__device__ void bitonic(uint64_t *g, int n, uint64_t *sh) {
-  uint64_t *a = n <= kSmemKeys ? sh : g;
-  if (a == sh) {
-    for (int i = threadIdx.x; i < n; i += RT) sh[i] = g[i];
-    __syncthreads();
-  }
-  for (int k = 2; k <= n; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n; i += RT) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const uint64_t x = a[i], y = a[ixj];
-          if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ixj] = x; }
-        }
-      }
-      __syncthreads();
-    }
-  if (a == sh) {
-    for (int i = threadIdx.x; i < n; i += RT) g[i] = sh[i];
-    __syncthreads();
-  }
-}
-
-__device__ int pow2_at_least(int n) {
-  int p = 1;
-  while (p < n) p <<= 1;
-  return p;
-}
-
 // order-preserving map of a float to uint32 (larger float -> larger key)
 __device__ __forceinline__ uint32_t ordered(float f) {
   const uint32_t u = __float_as_uint(f);
@@ -221,12 +162,21 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
     if (tid == 0) { a.copy_seg[0] = 0; *a.count = 0; }
     return;
   }
-  const int np2 = pow2_at_least((int)nc);
-  for (int i = (int)nc + tid; i < np2; i += RT) a.cand[i] = ~0ull;
-  __syncthreads();
-  bitonic(a.cand, np2, s_keys);
-  // budget left by this frame
+  // budget left by this frame; no prefix of more than kmax candidates fits it
+  // (each costs at least a page of the coarsest level), so only the kmax
+  // smallest keys need ordering
   const int64_t remaining = a.budget - ctl->streamed_bytes;
+  const int64_t min_cost = (int64_t)m_l[L - 1] * a.rec;
+  const int64_t kfit = remaining >= 0 ? remaining / min_cost + 1 : 1;
+  if (kfit < nc && kfit <= kSmemKeys) {
+    select_smallest(a.cand, (int)nc, (int)kfit, s_keys, sm);
+    nc = kfit;
+  } else {
+    const int np2 = pow2_at_least((int)nc);
+    for (int i = (int)nc + tid; i < np2; i += RT) a.cand[i] = ~0ull;
+    __syncthreads();
+    bitonic(a.cand, np2, s_keys);
+  }
   int64_t nadm = 0, cum = 0;
   for (int c = 0; c < nc; c += RT) {
     const int i = c + tid;
@@ -242,19 +192,6 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
     if (tid == 0) { a.copy_seg[0] = 0; *a.count = 0; }
     return;
   }
-  // free entries: not used this frame, least recently used first
-  int64_t nfree = 0;
-  for (int c = 0; c < a.P; c += RT) {
-    const int e = c + tid;
-    const int f = (e < a.P && a.pt_last[e] < frame_now) ? 1 : 0;
-    const int64_t pos = bscan(f, &tot, sm);
-    if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
-    nfree += tot;
-  }
-  const int fp2 = pow2_at_least((int)nfree);
-  for (int i = (int)nfree + tid; i < fp2; i += RT) a.free_keys[i] = ~0ull;
-  __syncthreads();
-  bitonic(a.free_keys, fp2, s_keys);
   // per-level ranks (stored in the low bits' place: reuse cand's page field order)
   for (int l = 0; l < L; ++l) {
     int64_t b0 = 0;
@@ -273,6 +210,25 @@ __global__ void __launch_bounds__(RT) place_kernel(PlaceArgs a) {
     fresh_start[L] = acc;
   }
   __syncthreads();
+  // free entries: not used this frame, least recently used first (only the
+  // fresh_start[L] least recently used are taken: select them)
+  int64_t nfree = 0;
+  for (int c = 0; c < a.P; c += RT) {
+    const int e = c + tid;
+    const int f = (e < a.P && a.pt_last[e] < frame_now) ? 1 : 0;
+    const int64_t pos = bscan(f, &tot, sm);
+    if (f) a.free_keys[nfree + pos] = ((uint64_t)(uint32_t)(a.pt_last[e] + 1) << 32) | (uint32_t)e;
+    nfree += tot;
+  }
+  __syncthreads();
+  if (fresh_start[L] > 0 && fresh_start[L] < nfree && fresh_start[L] <= kSmemKeys) {
+    select_smallest(a.free_keys, (int)nfree, fresh_start[L], s_keys, sm);
+  } else if (fresh_start[L] > 0) {
+    const int fp2 = pow2_at_least((int)nfree);
+    for (int i = (int)nfree + tid; i < fp2; i += RT) a.free_keys[i] = ~0ull;
+    __syncthreads();
+    bitonic(a.free_keys, fp2, s_keys);
+  }
   const int nf = fresh_start[L] < nfree ? fresh_start[L] : (int)nfree;
   for (int64_t x = tid; x < (int64_t)nf * Smax; x += RT) {
     const int k = (int)(x / Smax), s = (int)(x % Smax);

@@ -95,86 +95,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int
   }
 }
 
-// Single-pass exclusive scan of the tiles-touched counts into per-splat pair
-// offsets, with the total in ctl->pairs: CTAs take tiles of kScanItems splats
-// in order from a counter, publish their tile's sum, and obtain the sum of
-// all earlier tiles by a decoupled look-back in which warp 0 reads 32
-// predecessors' words per round trip (64-bit words: flag in the top two bits,
-// value below).  Waits are bounded: on expiry the kernel records
-// VM3DGS_E_TIMEOUT in the control block and goes on.  status (one word per
-// tile) and the counter must be zero at launch.
-constexpr uint64_t kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanFlags = 3ull << 62;
-__global__ void __launch_bounds__(kScanThreads) scan_single_kernel(Ctl *ctl, const uint32_t *touched, int64_t ncap,
-                                                                  int views, uint64_t *status, uint32_t *counter,
-                                                                  uint32_t *offsets) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_excl;
-  const int64_t N = n_total(ctl, ncap, views);
-  const int64_t ntiles = N > 0 ? (N + kScanItems - 1) / kScanItems : 1;
-  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
-  __syncthreads();
-  const int64_t tile = s_tile;
-  if (tile >= ntiles) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t i0 = tile * kScanItems + (int64_t)threadIdx.x * kScanPer;
-  uint32_t cnt[kScanPer];
-  uint64_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanPer; ++k) {
-    cnt[k] = (i0 + k < N) ? touched[i0 + k] : 0;
-    s += cnt[k];
-  }
-  uint64_t tot;
-  uint64_t pre = block_excl_scan_1024(s, &tot);
-  if (threadIdx.x == 0)
-    *(volatile uint64_t *)(status + tile) = (tile == 0 ? kScanInc : kScanAgg) | tot;
-  if (threadIdx.x < 32) {
-    uint64_t excl = 0;
-    if (tile > 0) {
-      int64_t j = tile - 1;  // the nearest predecessor not yet summed
-      int spins = 0;
-      for (;;) {
-        const uint64_t w = j - lane >= 0 ? *(const volatile uint64_t *)(status + j - lane) : kScanInc;
-        const uint64_t f = w & kScanFlags;
-        const uint32_t inc = __ballot_sync(0xffffffffu, f == kScanInc);
-        const uint32_t ready = __ballot_sync(0xffffffffu, f != 0);
-        // lanes up to the nearest inclusive word (all 32 if none) must be ready
-        const int last = inc ? __ffs(inc) - 1 : 31;
-        const uint32_t need = last == 31 ? 0xffffffffu : (2u << last) - 1u;
-        if ((ready & need) == need) {
-          uint64_t v = lane <= last ? (w & ~kScanFlags) : 0;
-#pragma unroll
-          for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          excl += v;
-          if (inc) break;
-          j -= 32;
-        } else {
-          if (++spins > kSpinLimit) {
-            if (lane == 0) atomicCAS(&ctl->status, 0, VM3DGS_E_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-      if (lane == 0) *(volatile uint64_t *)(status + tile) = kScanInc | (excl + tot);
-    }
-    if (lane == 0) s_excl = excl;
-  }
-  __syncthreads();
-  uint64_t off = s_excl + pre;
-#pragma unroll
-  for (int k = 0; k < kScanPer; ++k) {
-    if (i0 + k < N) offsets[i0 + k] = off < 0xFFFFFFFFull ? (uint32_t)off : 0xFFFFFFFFu;
-    off += cnt[k];
-  }
-  if (tile == ntiles - 1 && threadIdx.x == 0) {
-    const uint64_t total = s_excl + tot;
-    ctl->pairs = (int64_t)total;
-    ctl->acc_pairs += (int64_t)total;
-    ctl->acc_views += views;
-  }
-}
-
 // Per-splat exclusive pair offsets (saturated to 32 bits: offsets past the
 // pair capacity are never written).
 __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *ctl, const uint32_t *touched,
@@ -665,11 +585,10 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
                       const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
-  // block_sums: nb status words, then the tile counter
-  uint64_t *status = reinterpret_cast<uint64_t *>(block_sums);
-  cudaMemsetAsync(status, 0, sizeof(uint64_t) * (nb + 1), st);
-  scan_single_kernel<<<(unsigned)(nb > 0 ? nb : 1), kScanThreads, 0, st>>>(
-      ctl_w, sp.touched, ncap, 1, status, reinterpret_cast<uint32_t *>(status + nb), offsets);
+  uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs);
+  scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
   if (sh.hist) cudaMemsetAsync(sh.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
   cudaMemsetAsync(piece_ctr, 0, sizeof(uint32_t), st);
   emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap,

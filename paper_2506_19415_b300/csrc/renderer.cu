@@ -183,7 +183,7 @@ Layout make_layout(const Dims &d) {
     C.splat_touched = take(4 * N);
     C.splat_radius = take(4 * N);
     C.splat_tmask = take(8 * N);
-    C.block_sums = take(8 * (d.scan_blocks + 1));  // scan status words and tile counter
+    C.block_sums = take(8 * d.scan_blocks);
     C.offsets = take(4 * N);
     C.keys0 = take(8 * d.pair_cap);
     C.keys1 = take(8 * d.pair_cap);
@@ -664,7 +664,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
                      keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, r->at<uint64_t>(C.pieces),
                      r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, st);
-    r->span_end(t, 3, st);  // scan, emit, emit pieces
+    r->span_end(t, 5, st);  // scan reduce, scan blocks, scan offsets, emit, emit pieces
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
     const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
