@@ -102,6 +102,26 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
       }
 }
 
+// Batch-1 inference: y[n] = x . B[:, n] (+ bias, ReLU), a thread per output
+// column n (coalesced rows of B), the input row staged in shared memory.
+constexpr int kGemvThreads = 256, kGemvMaxK = 1024;
+__global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemmArgs g) {
+  __shared__ float xs[kGemvMaxK];
+  for (int k = threadIdx.x; k < g.K; k += kGemvThreads) xs[k] = __bfloat162float(g.A[k]);
+  __syncthreads();
+  const int n = blockIdx.x * kGemvThreads + threadIdx.x;
+  if (n >= g.N) return;
+  const __nv_bfloat16 *b = g.B + n;
+  float acc = 0.0f;
+#pragma unroll 8
+  for (int k = 0; k < g.K; ++k) acc += xs[k] * __bfloat162float(b[(int64_t)k * g.ldb]);
+  float v = acc;
+  if (g.bias) v += g.bias[n];
+  if (g.relu) v = v > 0.0f ? v : 0.0f;
+  if (g.C) g.C[n] = v;
+  if (g.Cb) g.Cb[n] = __float2bfloat16(v);
+}
+
 // dY = (sigmoid(logit) - target) * mask / max(sum(mask), 1); loss (mean BCE) into *loss
 __global__ void bce_grad_kernel(const float *logit, const float *target, const float *mask, int64_t n, float inv_n,
                                 float *dy, __nv_bfloat16 *dyb, float *loss) {
@@ -166,6 +186,14 @@ unsigned blocks_for(int64_t n, int per = 256) {
 void launch_gemm(const GemmArgs &g, cudaStream_t st) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
   gemm_kernel<<<grid, 128, 0, st>>>(g);
+}
+
+void launch_gemv(const GemmArgs &g, cudaStream_t st) {
+  if (g.M != 1 || g.transA || g.transB || g.mask_z || g.K > kGemvMaxK) {
+    launch_gemm(g, st);
+    return;
+  }
+  gemv_kernel<<<(g.N + kGemvThreads - 1) / kGemvThreads, kGemvThreads, 0, st>>>(g);
 }
 
 void launch_bce_grad(const float *logit, const float *target, const float *mask, int64_t n, float inv_n, float *dy,

@@ -22,6 +22,9 @@ struct GemmArgs {
 };
 
 void launch_gemm(const GemmArgs &g, cudaStream_t st);
+// the same product for M = 1, op(A) = A, op(B) = B (a row vector times a
+// K x N matrix): a thread per output, FP32 accumulation in k order
+void launch_gemv(const GemmArgs &g, cudaStream_t st);
 void launch_bce_grad(const float *logit, const float *target, const float *mask, int64_t n, float inv_n, float *dy,
                      __nv_bfloat16 *dyb, float *loss, cudaStream_t st);
 void launch_colsum(const float *x, int rows, int cols, float *out, cudaStream_t st);

@@ -70,15 +70,15 @@ void pf_forward(vm3dgs_prefetcher *p, const float *x, int Bn, float *logits, cud
   // layer 1: h1 = relu(x W1 + b1)
   g = GemmArgs{Bn, H, I, p->at<__nv_bfloat16>(L.xb), I, 0, p->at<__nv_bfloat16>(L.w1b), H, 0, w + L.n_w1, 1, nullptr,
                p->at<float>(L.h1f), p->at<__nv_bfloat16>(L.h1b), H};
-  launch_gemm(g, st);
+  (Bn == 1 ? launch_gemv : launch_gemm)(g, st);
   // layer 2
   g = GemmArgs{Bn, H, H, p->at<__nv_bfloat16>(L.h1b), H, 0, p->at<__nv_bfloat16>(L.w2b), H, 0,
                w + L.n_w1 + L.n_b1 + L.n_w2, 1, nullptr, p->at<float>(L.h2f), p->at<__nv_bfloat16>(L.h2b), H};
-  launch_gemm(g, st);
+  (Bn == 1 ? launch_gemv : launch_gemm)(g, st);
   // output logits
   g = GemmArgs{Bn, O, H, p->at<__nv_bfloat16>(L.h2b), H, 0, p->at<__nv_bfloat16>(L.w3b), O, 0,
                w + L.n_w1 + L.n_b1 + L.n_w2 + L.n_b2 + L.n_w3, 0, nullptr, logits, nullptr, O};
-  launch_gemm(g, st);
+  (Bn == 1 ? launch_gemv : launch_gemm)(g, st);
 }
 
 }  // namespace vm
