@@ -538,9 +538,21 @@ __global__ void __launch_bounds__(256) raster_huge_kernel(const QTri *queue, con
   }
 }
 
-__global__ void clear_kernel(uint64_t *fb, int64_t n) {
+// The visibility buffer to "empty", the raster counters to 0, and (when req
+// is given: the first view of a page determination) the request words,
+// direct flags and per-page gathering words to 0.
+__global__ void clear_kernel(uint64_t *fb, int64_t n, uint32_t *qcount, uint32_t *req, uint8_t *direct, uint32_t *dreq,
+                             int64_t NP) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) fb[i] = ~0ull;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t; i < n; i += stride) fb[i] = ~0ull;
+  if (t < 8) qcount[t] = 0;
+  if (req)
+    for (int64_t i = t; i < NP; i += stride) {
+      req[i] = 0;
+      direct[i] = 0;
+      if (dreq) dreq[i] = 0;
+    }
 }
 
 // Per pixel: the code of its page goes to dst (atomic max, once per page
@@ -588,8 +600,11 @@ __global__ void request_all_kernel(uint32_t *req, uint8_t *direct, int64_t NP) {
 
 }  // namespace
 
-void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st) {
-  clear_kernel<<<wave_grid((const void *)clear_kernel, 256, 0, n, 256), 256, 0, st>>>(fb, n);
+void launch_feedback_clear(uint64_t *fb, int64_t n, uint32_t *qcount, uint32_t *req, uint8_t *direct, uint32_t *dreq,
+                           int64_t NP, cudaStream_t st) {
+  const int64_t m = n > NP ? n : NP;
+  clear_kernel<<<wave_grid((const void *)clear_kernel, 256, 0, m, 256), 256, 0, st>>>(fb, n, qcount, req, direct, dreq,
+                                                                                     NP);
 }
 
 void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, int64_t ntri,
@@ -597,9 +612,9 @@ void launch_feedback_raster(const float4 *tv, const Cluster *cl, int64_t ncl, in
                             uint32_t *qcount, uint32_t qcap, uint64_t *bands, uint32_t bcap, uint32_t *vis,
                             uint32_t *clip, uint32_t *live, cudaStream_t st) {
   if (ntri <= 0 || ncl <= 0) return;
-  // qcount: [0] queued medium triangles, [1] listed triangles, [2] queued
-  // huge triangles, [3] their bands, [4] triangles to clip, [5] live clusters
-  cudaMemsetAsync(qcount, 0, 6 * sizeof(uint32_t), st);
+  // qcount (zeroed by the clear): [0] queued medium triangles, [1] listed
+  // triangles, [2] queued huge triangles, [3] their bands, [4] triangles to
+  // clip, [5] live clusters
   const RasterQueues rq{reinterpret_cast<QTri *>(queue), bands, qcount, qcap, bcap};
   cluster_cull_kernel<<<wave_grid((const void *)cluster_cull_kernel, 256, 0, ncl, 256), 256, 0, st>>>(
       cl, ncl, cam, ds, live, qcount + 5);

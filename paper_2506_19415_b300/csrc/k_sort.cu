@@ -76,8 +76,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Ctl *ct
   if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
+// (also zeroes the n0 words at z0 and the n1 at z1: the emission's counters)
 __global__ void __launch_bounds__(kScanThreads) scan_blocks_kernel(Ctl *ctl, int64_t ncap, int views,
-                                                                  uint64_t *block_sums) {
+                                                                  uint64_t *block_sums, uint32_t *z0, int n0,
+                                                                  uint32_t *z1, int n1) {
+  for (int i = threadIdx.x; i < n0; i += kScanThreads) z0[i] = 0;
+  for (int i = threadIdx.x; i < n1; i += kScanThreads) z1[i] = 0;
   const int64_t N = n_total(ctl, ncap, views);
   const int64_t nb = (N + kScanItems - 1) / kScanItems;
   uint64_t carry = 0;
@@ -225,7 +229,7 @@ constexpr uint32_t kPiece = 256;      // pairs per piece of a larger splat
 __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
                                                    uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
                                                    KeyFormat kf, SortHist sh, uint64_t *pieces,
-                                                   uint32_t *piece_ctr, int64_t piece_cap) {
+                                                   uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges, int ntiles) {
   __shared__ uint32_t hs[kMaxPasses][256];
   if (sh.hist) {
     for (int i = threadIdx.x; i < sh.passes * 256; i += blockDim.x) (&hs[0][0])[i] = 0;
@@ -309,6 +313,9 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     }
     if (blockIdx.x == 0 && threadIdx.x < kMaxPasses) sh.tile_ctr[threadIdx.x] = 0;
   }
+  // the tile ranges, written only for tiles with pairs, start empty
+  for (int64_t q2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q2 < ntiles; q2 += (int64_t)gridDim.x * blockDim.x)
+    ranges[q2] = make_uint2(0u, 0u);
 }
 
 // Pair emission, part 2: a warp per piece of kPiece pairs of a larger splat.
@@ -583,16 +590,18 @@ __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap,
 
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, cudaStream_t st) {
+                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges,
+                      int ntiles, cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
-  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs);
+  // the scan of the block sums also zeroes the digit histograms and the piece counter
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs, sh.hist, sh.hist ? kMaxPasses * 256 : 0, piece_ctr,
+                                                 1);
   scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
-  if (sh.hist) cudaMemsetAsync(sh.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
-  cudaMemsetAsync(piece_ctr, 0, sizeof(uint32_t), st);
   emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap,
-                                                                            gx, kf, sh, pieces, piece_ctr, piece_cap);
+                                                                            gx, kf, sh, pieces, piece_ctr, piece_cap,
+                                                                            ranges, ntiles);
   emit_pieces_kernel<<<full_wave((const void *)emit_pieces_kernel, 256, 0), 256, 0, st>>>(
       ctl, sp, offsets, keys, vals, pair_cap, gx, kf, sh, pieces, piece_ctr, piece_cap);
 }
@@ -603,7 +612,7 @@ void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int view
   const int64_t nb = (ncap * views + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs);
-  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl, ncap, views, bs);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl, ncap, views, bs, nullptr, 0, nullptr, 0);
   scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs, offsets);
   emit_batched_kernel<<<full_wave((const void *)emit_batched_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, views, vt,
                                                                                             offsets, keys, vals, pair_cap);
@@ -663,8 +672,8 @@ int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap
 }
 
 void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, int tshift,
-                   cudaStream_t st) {
-  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
+                   cudaStream_t st, bool zeroed) {
+  if (!zeroed) cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
   ranges_kernel<<<full_wave((const void *)ranges_kernel, 256, 0), 256, 0, st>>>(ctl, keys, pair_cap, ranges,
                                                                                 (uint32_t)ntiles, tshift);
 }

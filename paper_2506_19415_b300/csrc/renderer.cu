@@ -410,11 +410,8 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
   if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);
   uint32_t *req = r->req_buf(kb);
   uint8_t *direct = r->direct_buf(kb);
-  cudaMemsetAsync(req, 0, 4 * NP, st);
-  cudaMemsetAsync(direct, 0, NP, st);
   // with links the pixels' codes gather per page first, then spread
   uint32_t *dreq = r->prm.links ? r->at<uint32_t>(r->lay.dreq) : req;
-  if (r->prm.links) cudaMemsetAsync(dreq, 0, 4 * NP, st);
   const int ds = r->prm.feedback_ds;
   float fpx = 0.0f;
   const int sp_fb = r->span_begin(VM3DGS_STAGE_FEEDBACK, st);
@@ -422,7 +419,8 @@ extern "C" int vm3dgs_render_feedback(vm3dgs_renderer *r, const vm3dgs_camera *c
     const vm3dgs_camera &c = cams[v];
     const int64_t npix = (int64_t)((c.width + ds - 1) / ds) * ((c.height + ds - 1) / ds);
     uint64_t *fb = r->at<uint64_t>(r->lay.fb);
-    launch_feedback_clear(fb, npix, st);
+    launch_feedback_clear(fb, npix, r->at<uint32_t>(r->lay.raster_count), v == 0 ? req : nullptr, direct,
+                          r->prm.links ? dreq : nullptr, NP, st);
     launch_feedback_raster(r->at<float4>(r->lay.tri_v), r->at<Cluster>(r->lay.clusters), r->ncl, r->dims.ntri, c, ds, fb,
                            r->at<void>(r->lay.raster_queue),
                            r->at<uint32_t>(r->lay.raster_count), (uint32_t)r->dims.raster_cap,
@@ -663,7 +661,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
                       lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
                      keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, r->at<uint64_t>(C.pieces),
-                     r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, st);
+                     r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, r->at<uint2>(C.ranges), ntiles, st);
     r->span_end(t, 5, st);  // scan reduce, scan blocks, scan offsets, emit, emit pieces
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
@@ -676,7 +674,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     uint2 *ranges = r->at<uint2>(C.ranges);
     uint32_t *order = r->at<uint32_t>(C.tile_order), *work = r->at<uint32_t>(C.work);
     t = r->span_begin(VM3DGS_STAGE_RANGES, st);
-    launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, kf.tshift, st);
+    launch_ranges(ctl, keys[cur], r->dims.pair_cap, ranges, ntiles, kf.tshift, st, true);
     launch_tile_order(ranges, ntiles, order, work, st);
     r->span_end(t, 2, st);
     t = r->span_begin(VM3DGS_STAGE_BLEND, st);

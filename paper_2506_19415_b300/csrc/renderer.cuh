@@ -96,7 +96,10 @@ void prefer_shared(const void *kernel);
 int wave_grid(const void *kernel, int threads, size_t smem, int64_t n, int64_t per_block);
 
 // ----- launchers (one per kernel family)
-void launch_feedback_clear(uint64_t *fb, int64_t n, cudaStream_t st);
+// fb (n pixels) to empty and qcount (8 words) to 0; with req also req,
+// direct and dreq (NP each; dreq may be null) to 0
+void launch_feedback_clear(uint64_t *fb, int64_t n, uint32_t *qcount, uint32_t *req, uint8_t *direct, uint32_t *dreq,
+                           int64_t NP, cudaStream_t st);
 // A run of at most 32 consecutive proxy triangles of one page with the
 // axis-aligned box of their vertices (world units).
 struct Cluster {
@@ -230,9 +233,11 @@ struct SortHist {
 };
 // pieces (piece_cap words) and piece_ctr: the list of kPiece-pair pieces of
 // the splats with more than 32 pairs, written by the first emission kernel
+// (also zeroes ranges[0 .. ntiles) for the ranges of the coming sort)
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
                       uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, cudaStream_t st);
+                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges,
+                      int ntiles, cudaStream_t st);
 
 // sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
 // returns the index (0 or 1) of the buffer holding the result
@@ -246,8 +251,9 @@ int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bi
 int launch_sort_passes(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
                        uint32_t *hist, uint32_t *lookback, uint32_t *tile_ctr, cudaStream_t st);
 
+// zeroed: ranges[0 .. ntiles) are already zero (else they are cleared first)
 void launch_ranges(const Ctl *ctl, const uint64_t *keys, int64_t pair_cap, uint2 *ranges, int ntiles, int tshift,
-                   cudaStream_t st);
+                   cudaStream_t st, bool zeroed = false);
 // Tile processing order by descending pair count (empty tiles last); also
 // resets the work counters work[0..2] (the blend uses work[1]).
 void launch_tile_order(const uint2 *ranges, int ntiles, uint32_t *order, uint32_t *work, cudaStream_t st);
