@@ -240,18 +240,39 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // a task's records are loaded together (one round trip, culled splats
+  // included) and the next task's while this one is dealt out
+  struct Rec {
+    uint32_t cnt, off, rx, ry, db;
+    uint64_t tm;
+  };
+  auto load = [&](int64_t i) {
+    Rec q{0u, 0u, 0u, 0u, 0u, 0ull};
+    if (i < N) {
+      q.cnt = sp.touched[i];
+      q.off = offsets[i];
+      q.rx = sp.rect[2 * i];
+      q.ry = sp.rect[2 * i + 1];
+      q.tm = sp.tmask[i];
+      q.db = sp.depth[i];
+    }
+    return q;
+  };
+  Rec nx = load(warp0 * 32 + lane);
   for (int64_t b = warp0 * 32; b < N; b += nwarps * 32) {
     const int64_t i = b + lane;
-    uint32_t cnt = 0, off = 0, rx = 0, ry = 0;
+    const Rec cur = nx;
+    nx = load(b + nwarps * 32 + lane);
+    const uint32_t cnt = cur.cnt;
+    uint32_t off = 0, rx = 0, ry = 0;
     uint64_t tm = 0, dkey = 0;
-    if (i < N) cnt = sp.touched[i];
     const bool big = cnt > kSmallSplat;
     if (cnt && !big) {
-      off = offsets[i];
-      rx = sp.rect[2 * i];
-      ry = sp.rect[2 * i + 1];
-      tm = sp.tmask[i];
-      dkey = depth_key(sp.depth[i], kf);
+      off = cur.off;
+      rx = cur.rx;
+      ry = cur.ry;
+      tm = cur.tm;
+      dkey = depth_key(cur.db, kf);
       if (po.hist) count_run(hs, dkey >> po.lo_bit, po.dpass, cnt);
     }
     const uint32_t small = big ? 0u : cnt;
