@@ -4,10 +4,11 @@
 // prioritised and asynchronous copies, which the prefetcher provides.
 //
 // GEMM: C[M,N] = op(A)[M,K] * op(B)[K,N], A and B bf16 in row-major memory
-// (op = optional transpose), FP32 accumulation on the tensor cores with
-// mma.sync m16n8k16 (bf16 x bf16 -> f32).  Block tile 64 x 64 x 32, 4 warps
-// of 32 x 32.  Epilogue: + bias[n], optional ReLU, optional multiply by
-// (mask_z[m,n] > 0) (the ReLU derivative), stores fp32 and/or bf16.
+// (op = optional transpose), FP32 accumulation on the tensor cores
+// (tcgen05.mma, accumulator in tensor memory; batch-1 inference instead
+// takes a GEMV on the CUDA cores).  Epilogue: + bias[n], optional ReLU,
+// optional multiply by (mask_z[m,n] > 0) (the ReLU derivative), stores fp32
+// and/or bf16.
 #include <cuda_bf16.h>
 
 #include "mlp.cuh"
@@ -15,91 +16,136 @@
 namespace vm {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+// GEMM on the 5th-generation tensor cores: a CTA of 4 warps computes a
+// 128 x 64 tile of C with tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128,
+// N = 64, K = 16 per instruction) into a 64-column accumulator in tensor
+// memory.  Per K-step of 64 the threads stage op(A) and op(B) tiles (zero
+// padded) in shared memory in the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, adjacent along K 128 B apart (leading byte
+// offset), adjacent 8-row groups 1024 B apart (stride byte offset).  One
+// thread issues the four MMAs and commits them to an mbarrier the CTA waits
+// on (bounded); the epilogue reads the accumulator rows of each warp's lane
+// quarter with tcgen05.ld.
+constexpr int TM = 128, TN = 64, TK = 64;
+constexpr uint32_t kLbo = 128, kSbo = (TK / 8) * 128;
 
-__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t core_off(int r, int k) {  // byte offset of (r, k) in a staged tile
+  return (uint32_t)((r >> 3) * kSbo + (k >> 3) * kLbo + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];   // [m][k]
-  __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];   // [n][k]
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((kSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__global__ void __launch_bounds__(128) gemm_tc_kernel(GemmArgs g) {
+  __shared__ __align__(1024) uint8_t As[TM * TK * 2];
+  __shared__ __align__(1024) uint8_t Bs[TN * TK * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gq = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"((uint32_t)TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar)), "r"(1u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    // A tile: element (m, k) of op(A)
-    for (int e = tid; e < BM * BK; e += 128) {
-      const int r = e / BK, c = e % BK;
-      const int m = m0 + r, k = k0 + c;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < g.K; k0 += TK) {
+    for (int e = tid; e < TM * TK; e += 128) {
+      const int r = e / TK, c = e % TK, m = m0 + r, k = k0 + c;
       __nv_bfloat16 v = zero;
       if (m < g.M && k < g.K) v = g.transA ? g.A[(int64_t)k * g.lda + m] : g.A[(int64_t)m * g.lda + k];
-      As[r][c] = v;
+      *reinterpret_cast<__nv_bfloat16 *>(As + core_off(r, c)) = v;
     }
-    // B tile: element (k, n) of op(B), stored [n][k]
-    for (int e = tid; e < BN * BK; e += 128) {
-      const int r = e / BK, c = e % BK;   // r = n offset, c = k offset
-      const int n = n0 + r, k = k0 + c;
+    for (int e = tid; e < TN * TK; e += 128) {
+      const int r = e / TK, c = e % TK, n = n0 + r, k = k0 + c;
       __nv_bfloat16 v = zero;
       if (n < g.N && k < g.K) v = g.transB ? g.B[(int64_t)n * g.ldb + k] : g.B[(int64_t)k * g.ldb + n];
-      Bs[r][c] = v;
+      *reinterpret_cast<__nv_bfloat16 *>(Bs + core_off(r, c)) = v;
     }
+    // the staged tiles become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t af[2][4], bf[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gq;
-        af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq]);
-        af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq]);
-        af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * tq + 8]);
-        af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * tq + 8]);
+      for (int s = 0; s < TK / 16; ++s) {
+        const uint64_t ad = smem_desc(smem_addr(As) + s * 2 * kLbo), bd = smem_desc(smem_addr(Bs) + s * 2 * kLbo);
+        const uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gq;
-        bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq]);
-        bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(&bar))
+                   : "memory");
     }
+    // wait (bounded) for the MMAs: they read the staged tiles
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it)
+      asm volatile(
+          "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+          : "=r"(done)
+          : "r"(smem_addr(&bar)), "r"(phase)
+          : "memory");
+    ok = ok && done;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
   }
-  // epilogue: accumulator element (row gq or gq+8, col 2tq or 2tq+1) of each 16x8 tile
+  if (!ok && tid == 0 && g.err) atomicExch(g.err, 1);
+  // epilogue: warp w holds rows 32 w .. 32 w + 31 of the tile in its lane quarter
+  const int m = m0 + 32 * warp + lane;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int c = 0; c < TN / 16; ++c) {
+    uint32_t v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * c);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (m < g.M && g.K > 0) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int m = m0 + wm + i * 16 + gq + (h >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * tq + (h & 1);
-        if (m >= g.M || n >= g.N) continue;
-        float v = acc[i][j][h];
-        if (g.bias) v += g.bias[n];
-        if (g.relu) v = v > 0.0f ? v : 0.0f;
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + 16 * c + j;
+        if (n >= g.N) continue;
+        float x = __uint_as_float(v[j]);
+        if (g.bias) x += g.bias[n];
+        if (g.relu) x = x > 0.0f ? x : 0.0f;
         const int64_t o = (int64_t)m * g.ldc + n;
-        if (g.mask_z && !(g.mask_z[o] > 0.0f)) v = 0.0f;
-        if (g.C) g.C[o] = v;
-        if (g.Cb) g.Cb[o] = __float2bfloat16(v);
+        if (g.mask_z && !(g.mask_z[o] > 0.0f)) x = 0.0f;
+        if (g.C) g.C[o] = x;
+        if (g.Cb) g.Cb[o] = __float2bfloat16(x);
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TN) : "memory");
+  }
 }
 
 // Batch-1 inference: y[n] = x . B[:, n] (+ bias, ReLU), a thread per output
@@ -184,8 +230,8 @@ unsigned blocks_for(int64_t n, int per = 256) {
 }  // namespace
 
 void launch_gemm(const GemmArgs &g, cudaStream_t st) {
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  gemm_kernel<<<grid, 128, 0, st>>>(g);
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM);
+  gemm_tc_kernel<<<grid, 128, 0, st>>>(g);
 }
 
 void launch_gemv(const GemmArgs &g, cudaStream_t st) {

@@ -19,6 +19,7 @@ struct GemmArgs {
   float *C;                // fp32 out [M, ldc] or null
   __nv_bfloat16 *Cb;       // bf16 out [M, ldc] or null
   int ldc;
+  int *err;                // set to 1 if a bounded wait for the tensor cores gave up (or null)
 };
 
 void launch_gemm(const GemmArgs &g, cudaStream_t st);
