@@ -476,7 +476,9 @@ __global__ void __launch_bounds__(256) raster_clip_kernel(const float4 *tv, int6
   }
 }
 
-// medium triangles: one warp each, lanes over the pixel box
+// medium triangles: one warp each, lanes over the pixel box (a static split:
+// taking them from a shared counter cost more in contended atomics than the
+// tail it removed)
 __global__ void __launch_bounds__(256) raster_medium_kernel(const QTri *queue, const uint32_t *qcount, uint32_t qcap,
                                                             int Wf, uint64_t *fb) {
   const uint32_t n = min(qcount[0], qcap / 2);

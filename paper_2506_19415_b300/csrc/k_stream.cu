@@ -4,13 +4,17 @@
 // buffer with the graphics driver; here the GPU pulls the bytes itself over
 // the host link with 16-byte loads, so the copy list never returns to the
 // CPU.  Work is cut into 64 KiB segments spread over a persistent grid;
-// every copied page is one contiguous block on both sides.
+// every copied page is one contiguous block on both sides.  A thread issues
+// kInFlight loads before its stores, so a segment crosses the host link in
+// one round trip.
 #include "renderer.cuh"
 
 namespace vm {
 namespace {
 
-__global__ void __launch_bounds__(512) stream_kernel(StreamArgs a) {
+constexpr int kStreamThreads = 512, kInFlight = 8;  // 512 x 8 x 16 B = one 64 KiB segment
+
+__global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
   const int n = *a.count;
   const int64_t nseg = a.copy_seg[n];
   for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
@@ -29,12 +33,24 @@ __global__ void __launch_bounds__(512) stream_kernel(StreamArgs a) {
     const uint4 *src = reinterpret_cast<const uint4 *>(a.host + a.level_off[c.y] + (int64_t)c.x * bytes + off);
     uint4 *dst = reinterpret_cast<uint4 *>(a.pool + (int64_t)c.z * a.slot_bytes + (int64_t)c.w * bytes + off);
     const int64_t n16 = len / 16;
-    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    for (int64_t i0 = threadIdx.x; i0 < n16; i0 += (int64_t)kInFlight * kStreamThreads) {
+      uint4 v[kInFlight];
+#pragma unroll
+      for (int u = 0; u < kInFlight; ++u) {
+        const int64_t i = i0 + (int64_t)u * kStreamThreads;
+        if (i < n16) v[u] = src[i];
+      }
+#pragma unroll
+      for (int u = 0; u < kInFlight; ++u) {
+        const int64_t i = i0 + (int64_t)u * kStreamThreads;
+        if (i < n16) dst[i] = v[u];
+      }
+    }
   }
 }
 
 }  // namespace
 
-void launch_stream(const StreamArgs &a, cudaStream_t st) { stream_kernel<<<148 * 2, 512, 0, st>>>(a); }
+void launch_stream(const StreamArgs &a, cudaStream_t st) { stream_kernel<<<148 * 2, kStreamThreads, 0, st>>>(a); }
 
 }  // namespace vm
