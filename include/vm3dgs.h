@@ -303,7 +303,7 @@ enum {
   VM3DGS_STAGE_RANGES = 6,    /* tile ranges and the tiles' processing order */
   VM3DGS_STAGE_BLEND = 7,     /* per-tile blending */
   VM3DGS_STAGE_PREFETCH = 8,  /* prefetch input, network, placement and copies */
-  VM3DGS_STAGE_SORT_PREP = 9, /* digit histograms of the sort and their bases (STAGE_SORT: the passes alone) */
+  VM3DGS_STAGE_SORT_PREP = 9, /* reserved (the single-view sort's histograms are counted by the emission) */
   VM3DGS_N_STAGES = 10
 };
 int vm3dgs_timing_enable(vm3dgs_renderer *r, int32_t on);

@@ -152,11 +152,13 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
   __shared__ uint32_t s_tile;
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
+  bool first = true;  // a CTA's first tile is its index in the order; later ones come from the counter
   for (;;) {
   if (threadIdx.x == 0) {
-    const uint32_t w = atomicAdd(work, 1u);
+    const uint32_t w = first ? blockIdx.x : gridDim.x + atomicAdd(work, 1u);
     s_tile = w < ntiles ? order[w] : 0xFFFFFFFFu;
   }
+  first = false;
   __syncthreads();
   const uint32_t tile = s_tile;
   if (tile == 0xFFFFFFFFu) break;

@@ -284,11 +284,13 @@ __device__ __forceinline__ CullPlanes cull_planes(const vm3dgs_camera &cam, int 
 // are appended (warp-aggregated, in no particular order) to the live list.
 __global__ void __launch_bounds__(256) cluster_cull_kernel(const Cluster *cl, int64_t ncl, vm3dgs_camera cam, int ds,
                                                            uint32_t *live, uint32_t *nlive) {
+  __shared__ uint32_t s_cnt[8], s_base;
   const CullPlanes P = cull_planes(cam, ds);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < ncl; b += stride) {
-    const int64_t ci = b + lane;
+  // CTA-uniform rounds: one list reservation per CTA and round
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < ncl; b0 += stride) {
+    const int64_t ci = b0 + threadIdx.x;
     bool keep = false;
     if (ci < ncl) {
       const float4 *c4 = reinterpret_cast<const float4 *>(cl + ci);
@@ -303,10 +305,16 @@ __global__ void __launch_bounds__(256) cluster_cull_kernel(const Cluster *cl, in
       }
     }
     const uint32_t km = __ballot_sync(0xffffffffu, keep);
-    uint32_t off = 0;
-    if (lane == 0 && km) off = atomicAdd(nlive, (uint32_t)__popc(km));
-    off = __shfl_sync(0xffffffffu, off, 0);
-    if (keep) live[off + __popc(km & ((1u << lane) - 1u))] = (uint32_t)ci;
+    if (lane == 0) s_cnt[warp] = (uint32_t)__popc(km);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < 8; ++w) { const uint32_t c = s_cnt[w]; s_cnt[w] = tot; tot += c; }
+      s_base = tot ? atomicAdd(nlive, tot) : 0u;
+    }
+    __syncthreads();
+    if (keep) live[s_base + s_cnt[warp] + __popc(km & ((1u << lane) - 1u))] = (uint32_t)ci;
+    __syncthreads();  // s_cnt and s_base are rewritten next round
   }
 }
 
@@ -324,7 +332,9 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int6
                                                           vm3dgs_camera cam, int ds, uint32_t *vis, uint32_t *nvis,
                                                           uint32_t *clip, uint32_t *nclip) {
   __shared__ uint32_t s_buf[8][kCullBuf];
-  uint32_t *buf = s_buf[threadIdx.x >> 5];
+  __shared__ uint32_t s_cnt[8], s_base;
+  const int warp = threadIdx.x >> 5;
+  uint32_t *buf = s_buf[warp];
   int nbuf = 0;  // warp-uniform
   const CullPlanes P = cull_planes(cam, ds);
   const float zn = 0.2f;
@@ -373,23 +383,44 @@ __global__ void __launch_bounds__(256) raster_cull_kernel(const float4 *tv, int6
     nbuf += __popc(km);
     __syncwarp();
   }
-  if (nbuf) {
-    uint32_t off = 0;
-    if (lane == 0) off = atomicAdd(nvis, (uint32_t)nbuf);
-    off = __shfl_sync(0xffffffffu, off, 0);
-    for (int k = lane; k < nbuf; k += 32) vis[off + k] = buf[k];
+  // one reservation for the rest of the CTA's buffers
+  if (lane == 0) s_cnt[warp] = (uint32_t)nbuf;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < 8; ++w) { const uint32_t c = s_cnt[w]; s_cnt[w] = tot; tot += c; }
+    s_base = tot ? atomicAdd(nvis, tot) : 0u;
   }
+  __syncthreads();
+  for (int k = lane; k < nbuf; k += 32) vis[s_base + s_cnt[warp] + k] = buf[k];
 }
 
 // Pass 2: snap and rasterise the listed triangles (small ones by the warp
 // together, medium ones queued with one counter update per warp, huge ones
 // in bands); each lane's triangle is set up directly in the warp's shared
 // slots.
+// Medium triangles gather per warp in shared memory (kMedBuf records) and
+// reach the queue through one reservation per CTA at the end (the queue
+// counter is a single contended word); a full buffer is flushed at once.
+constexpr int kMedBuf = 32;
+__device__ __forceinline__ void copy_tris(Tri *dst, const Tri *src, int n, int lane) {
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+  constexpr int W = sizeof(Tri) / 4;
+  for (int k = lane; k < n * W; k += 32) d[k] = s[k];
+}
+
 __global__ void __launch_bounds__(256, 4) raster_setup_kernel(const float4 *tv, int64_t ntri, const uint32_t *vis,
                                                            const uint32_t *nvis, vm3dgs_camera cam, int ds,
                                                            uint64_t *fb, RasterQueues rq) {
+  static_assert(sizeof(Tri) % 4 == 0, "Tri is copied as words");
   __shared__ Tri s_tri[8][32];
-  Tri *wtri = s_tri[threadIdx.x >> 5];
+  __shared__ Tri s_med[8][kMedBuf];
+  __shared__ uint32_t s_cnt[8], s_base;
+  const int warp = threadIdx.x >> 5;
+  Tri *wtri = s_tri[warp];
+  Tri *mbuf = s_med[warp];
+  int nmed = 0;  // warp-uniform
   const int Wf = (cam.width + ds - 1) / ds, Hf = (cam.height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam.fx / fds, fyf = cam.fy / fds, cxf = cam.cx / fds, cyf = cam.cy / fds;
@@ -415,14 +446,37 @@ __global__ void __launch_bounds__(256, 4) raster_setup_kernel(const float4 *tv, 
     const bool med = npx > kSmallPx;
     const uint32_t mm = __ballot_sync(0xffffffffu, med);
     if (mm) {
-      const int leader = __ffs(mm) - 1;
-      uint32_t q0 = 0;
-      if (lane == leader) q0 = atomicAdd(rq.count, (uint32_t)__popc(mm));
-      q0 = __shfl_sync(0xffffffffu, q0, leader);
-      if (med) queue_medium(wtri[lane], q0 + __popc(mm & ((1u << lane) - 1u)), rq, Wf, fb);
+      if (nmed + __popc(mm) > kMedBuf) {  // flush the warp's buffer now
+        uint32_t q0 = 0;
+        if (lane == 0) q0 = atomicAdd(rq.count, (uint32_t)nmed);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        const int fit = q0 < rq.qcap / 2 ? (int)min((uint32_t)nmed, rq.qcap / 2 - q0) : 0;
+        copy_tris(rq.queue + q0, mbuf, fit, lane);
+        __syncwarp();
+        for (int k = fit + lane; k < nmed; k += 32) raster_serial(mbuf[k], Wf, fb);  // queue full
+        __syncwarp();
+        nmed = 0;
+      }
+      if (med) mbuf[nmed + __popc(mm & ((1u << lane) - 1u))] = wtri[lane];
+      nmed += __popc(mm);
     }
     __syncwarp();
     raster_warp(med ? 0 : (int)npx, wtri, Wf, fb);
+  }
+  // one reservation for the CTA's buffered medium triangles
+  if (lane == 0) s_cnt[warp] = (uint32_t)nmed;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < 8; ++w) { const uint32_t c = s_cnt[w]; s_cnt[w] = tot; tot += c; }
+    s_base = tot ? atomicAdd(rq.count, tot) : 0u;
+  }
+  __syncthreads();
+  if (nmed) {
+    const uint32_t q0 = s_base + s_cnt[warp];
+    const int fit = q0 < rq.qcap / 2 ? (int)min((uint32_t)nmed, rq.qcap / 2 - q0) : 0;
+    copy_tris(rq.queue + q0, mbuf, fit, lane);
+    for (int k = fit + lane; k < nmed; k += 32) raster_serial(mbuf[k], Wf, fb);  // queue full
   }
 }
 
