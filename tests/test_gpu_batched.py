@@ -105,3 +105,40 @@ def test_autotuner_picks_valid_shapes(v):
     assert all((c.tile_w, c.tile_h) in ((16, 16), (8, 8), (32, 8)) for c in tuned)
     imgs = r.render_batched(tuned)
     assert r.stats()["status"] == 0 and all(np.isfinite(im.cpu().numpy()).all() for im in imgs)
+
+
+def test_interleaved_streams_equal_one_stream(v):
+    """Single-view renders on two streams (the two render contexts) and
+    batched renders (context 0) interleaved with no host sync: every image
+    equals the same sequence rendered on one stream."""
+    import torch
+    sc, scene = _scene(v)
+    cams = _views(6, [(16, 16), (8, 8), (32, 8)])
+    cfg = v.RenderConfig(max_width=640, max_height=400, lod=False, fp16_pool=True, max_views=8,
+                         staging_bytes=1 << 40)
+    r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    r.request_all()
+    r.update_residency()
+    plan = [("one", 0), ("one", 1), ("batch", None), ("one", 2), ("one", 3), ("batch", None), ("one", 4)]
+
+    def run(streams):
+        out = []
+        for k, (what, i) in enumerate(plan):
+            s = streams[k % len(streams)]
+            if what == "one":
+                img = torch.empty((3, cams[i].height, cams[i].width), dtype=torch.float32, device="cuda")
+                r.render([cams[i]], [img], s)
+                out.append([img])
+            else:
+                imgs = [torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda") for c in cams]
+                r.render_batched(cams, imgs, s)
+                out.append(imgs)
+        torch.cuda.synchronize()
+        return [[im.cpu().numpy() for im in group] for group in out]
+
+    ref = run([torch.cuda.current_stream()])
+    got = run([torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()])
+    for a, b in zip(ref, got):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert r.stats()["status"] == 0
