@@ -447,6 +447,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// one radix digit per thread: the digit scans and count loads index by tid
+static_assert(kSortThreads == 256, "onesweep assumes one thread per 8-bit digit");
+
 template <bool VALS>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
                                                                 uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
