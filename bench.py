@@ -15,6 +15,7 @@ Synthetic, seeded inputs (scenegen); no dataset.
 
   python bench.py [--gpus N --steps K --warmup W] [--config city50m|blobs1m|tiny]
   python bench.py --impl reference ...   (the CPU oracle, bounded sample)
+  python bench.py --table pagesize|buffer (the page-size / buffer-size tables of Sec. 5)
 """
 from __future__ import annotations
 
@@ -137,9 +138,9 @@ def build_scene(W):
     return scene, t1 - t0, time.time() - t1
 
 
-def make_renderer(v, scene, W, fp16, width, height, pool_slots=None):
+def make_renderer(v, scene, W, fp16, width, height, pool_slots=None, max_pairs=0):
     cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=fp16,
-                         max_width=width, max_height=height, tau0=1.0, step0=0.1)
+                         max_width=width, max_height=height, tau0=1.0, step0=0.1, max_pairs=max_pairs)
     if pool_slots is not None:
         return v.Renderer(scene, cfg, pool_slots=pool_slots)
     if W["pool_bytes"] is None:
@@ -641,6 +642,102 @@ def reference_main(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- paging tables
+def frame_medians(v, r, cams, warmup, frames):
+    """Frames on one stream with a CUDA-event time per stage and the counters
+    of each frame; medians over the frames (the statistic of the page-size and
+    buffer-size tables of Sec. 5)."""
+    import torch
+    st = torch.cuda.current_stream()
+    img = torch.empty((3, cams[0].height, cams[0].width), dtype=torch.float32, device="cuda")
+    n = len(cams)
+
+    def frame(i):
+        c = [cams[i % n]]
+        r.render_feedback(c, st)
+        r.update_residency(st)
+        r.render(c, [img], st)
+
+    for i in range(warmup):
+        frame(i)
+    torch.cuda.synchronize()
+    r.timing(True)
+    r.timing_read()
+    per = []
+    for i in range(warmup, warmup + frames):
+        frame(i)
+        ms, _ = r.timing_read()
+        s = r.stats(st)
+        if s["status"] != 0:
+            raise RuntimeError("renderer status %d" % s["status"])
+        d = dict(zip(v.STAGES, ms))
+        per.append(dict(
+            page_table_update_ms=d["residency"], stream_ms=d["stream"],
+            depth_sort_ms=d["scan_emit"] + d["sort"] + d["ranges"], render_ms=d["project"] + d["blend"],
+            feedback_ms=d["feedback"], frame_ms=sum(ms), missing_pages=s["missing"],
+            requested_pages=s["requested"], drawn_pages=s["drawn_pages"], drawn_gaussians=s["drawn_gaussians"],
+            pairs=s["pairs"], tau=s["tau"], usage=s["usage"], staged_projection=s["staged_projection"]))
+    r.timing(False)
+    out = {k: float(np.median([p[k] for p in per])) for k in per[0]}
+    out["missing_pages_mean"] = float(np.mean([p["missing_pages"] for p in per]))
+    # the LOD controller's approach: mean missing pages per block of 50 frames, and tau at the end
+    out["missing_pages_per_50_frames"] = [round(float(np.mean([p["missing_pages"] for p in per[b:b + 50]])), 1)
+                                          for b in range(0, frames, 50)]
+    out["tau_last"] = float(per[-1]["tau"])
+    out["frames"] = frames
+    return {k: (round(x, 4) if isinstance(x, float) else x) for k, x in out.items()}
+
+
+def paging_tables(args):
+    """The page-size and buffer-size tables of Sec. 5 on a city walk (by
+    default the 50M-Gaussian city): per-stage medians over the frames for page sizes 2048/4096/8192 at a
+    fixed pool of bytes, and for pools of 250/500/1000 pages of 2048 Gaussians
+    with and without LOD.  Column mapping: page-table update = the residency
+    kernel; depth sort = key emission + radix sort + tile ranges; render =
+    projection + blend."""
+    import torch
+    import paper_2506_19415_b300 as v
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    base = workload(args.config)
+    frames = min(args.steps, 300)
+    cams = base["path"](base["frames"])
+    width, height = cams[0].width, cams[0].height
+    rows = []
+
+    def scene_at(ps):
+        W = dict(base, build=dict(base["build"], page_size=ps))
+        scene, _, t_build = build_scene(W)
+        return W, scene, t_build
+
+    if args.table == "pagesize":
+        for ps in (2048, 4096, 8192):
+            W, scene, t_build = scene_at(ps)
+            r = make_renderer(v, scene, W, True, width, height)
+            row = dict(page_size=ps, pages=scene.info.n_pages, pool_slots=r.n_slots, build_s=round(t_build, 1))
+            row.update(frame_medians(v, r, cams, args.warmup, frames))
+            rows.append(row)
+            del r, scene
+            torch.cuda.empty_cache()
+        what = "page size (2 GiB fp16 pool, LOD on)"
+    else:
+        W, scene, t_build = scene_at(2048)
+        for lod in (False, True):
+            for slots in (250, 500, 1000):
+                # small pools at close range put many more pairs on each resident Gaussian
+                # than the default capacity (8 per pool Gaussian) allows
+                r = make_renderer(v, scene, dict(W, lod=lod), True, width, height, pool_slots=slots,
+                                  max_pairs=32 << 20)
+                row = dict(page_size=2048, pool_slots=slots, lod=lod)
+                row.update(frame_medians(v, r, cams, args.warmup, frames))
+                rows.append(row)
+                del r
+                torch.cuda.empty_cache()
+        what = "pool size in pages of 2048 Gaussians (fp16 pool), without and with LOD"
+    print(json.dumps({"table": args.table, "varies": what, "workload": base["name"], "frames": frames,
+                      "warmup": args.warmup, "statistic": "median over frames (missing pages also as a mean)",
+                      "timing": "CUDA events per stage, every call on one stream", "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -651,11 +748,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefetch", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--table", choices=("pagesize", "buffer"), default=None,
+                    help="print the page-size or buffer-size table of Sec. 5 instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_main(args)
+    elif args.table is not None:
+        paging_tables(args)
     else:
         gpu_main(args)
 
