@@ -16,6 +16,10 @@ Steps, each following the paper (Sec. 3 "Preprocessing"):
   lod_build       Sec. 3.4 "Level of Detail": only Gaussians of one page merge;
                   each parent merges `fanout` consecutive children by moment
                   matching (mean, covariance), opacity averaged, SH weighted.
+  lod_build_kmeans  the paper's own LOD of Sec. 3.4: k-means clusters of a
+                  page's Gaussians in a scaled attribute space (position
+                  first), each cluster averaged into one parent, the scale
+                  enlarged by a fixed factor; `fanout` 2 halves per level.
   voxel_proxy     Sec. 3.1 "Mesh Extraction" stand-in: occupancy grid, one
                   closing, exposed voxel faces merged into rectangles, each
                   face marked with one page.
@@ -264,6 +268,144 @@ def lod_build(pages, levels, fanout):
         out.append({k: v.reshape((n_pages, m_new) + v.shape[1:]) for k, v in par.items()})
         err[:, l] = smax.reshape(n_pages, m_new).max(1).astype(np.float32)
     return out, err
+
+
+# --------------------------------------------------------------------------- k-means LOD
+def kmeans_features(pos, rot, opac, sh, attr_weight):
+    """Clustering features [n, 11] (fp64) of one page's real Gaussians
+    (Sec. 3.4, "Level of Detail": Gaussians are points in attribute space,
+    attributes scaled to set their influence, position prioritised).
+    Position is centred on the page mean and divided by the page's RMS
+    radius (1 where that is 0); then the quaternion with w >= 0, the
+    degree-0 SH colour and the opacity, each times attr_weight."""
+    p = pos.astype(np.float64)
+    n = len(p)
+    mu = np.zeros(3)
+    for i in range(n):
+        mu += p[i]
+    mu /= n
+    r2 = 0.0
+    for i in range(n):
+        d = p[i] - mu
+        r2 += d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+    rad = np.sqrt(r2 / n)
+    if not rad > 0:
+        rad = 1.0
+    q = rot.astype(np.float64)
+    q = np.where(q[:, :1] < 0, -q, q)
+    return np.concatenate([(p - mu) / rad, attr_weight * q, attr_weight * sh[:, 0, :].astype(np.float64),
+                           attr_weight * opac.astype(np.float64)[:, None]], 1)
+
+
+def kmeans_lloyd(X, C0, iters):
+    """Lloyd's iterations from the given centroids: assign every point to the
+    nearest centroid (squared Euclidean distance, lowest index on a tie),
+    then move each centroid to the mean of its points (a centroid without
+    points stays).  Stops after `iters` rounds or when an assignment repeats
+    the previous one (later rounds would change nothing).  Returns the last
+    assignment and the centroids after it."""
+    C = np.array(C0, np.float64)
+    lab, prev = None, None
+    for _ in range(iters):
+        d = np.zeros((len(X), len(C)))
+        for a in range(X.shape[1]):      # features summed in order
+            t = X[:, None, a] - C[None, :, a]
+            d += t * t
+        lab = d.argmin(1)
+        if prev is not None and np.array_equal(lab, prev):
+            break
+        for i in range(len(C)):
+            mem = np.nonzero(lab == i)[0]
+            if len(mem):
+                acc = np.zeros(X.shape[1])
+                for j in mem:
+                    acc += X[j]
+                C[i] = acc / len(mem)
+        prev = lab
+    return lab, C
+
+
+def merge_cluster(pos, scale, rot, opac, sh, scale_factor):
+    """One merged Gaussian from its members (Sec. 3.4): arithmetic means of
+    position, opacity and SH; the quaternions averaged after each is turned
+    to the first member's hemisphere, then normalised with w >= 0; the mean
+    scale enlarged by the fixed factor when two or more members merge.
+    Returns the fp64 attributes."""
+    n = len(opac)
+    q0 = rot[0].astype(np.float64)
+    qs = np.zeros(4)
+    for i in range(n):
+        q = rot[i].astype(np.float64)
+        qs += q if float(q @ q0) >= 0 else -q
+    nq = np.sqrt(qs @ qs)
+    q = qs / nq if nq > 0 else q0 / np.sqrt(q0 @ q0)
+    if q[0] < 0:
+        q = -q
+    ps, sc, op, shs = np.zeros(3), np.zeros(3), 0.0, np.zeros(sh.shape[1:])
+    for i in range(n):                   # members summed in order
+        ps += pos[i].astype(np.float64)
+        sc += scale[i].astype(np.float64)
+        op += float(opac[i])
+        shs += sh[i].astype(np.float64)
+    sc = sc / n
+    if n >= 2:
+        sc = sc * scale_factor
+    return dict(pos=ps / n, scale=sc, rot=q, opacity=op / n, sh=shs / n)
+
+
+def lod_build_kmeans(pages, levels, fanout, iters=10, scale_factor=0.0, attr_weight=0.1):
+    """Levels 1..levels-1 by k-means clustering inside each page (Sec. 3.4,
+    Fig. "LOD generation": the Gaussians per page shrink by `fanout` per
+    level, 2 in the paper).  Level l clusters the n real Gaussians of level
+    l-1 into k = ceil(n / fanout) clusters seeded at children floor(i*n/k)
+    (the page's Morton order), then merges each non-empty cluster into one
+    parent; parents fill slots in cluster order, the rest is padding.
+    scale_factor 0 means fanout^(1/3) (the volume of `fanout` equal
+    Gaussians).  e_l(p) = max over parents and their members of
+    |member mean - parent mean| + the member's largest scale.
+    Returns the per-level dicts, err[n_pages, levels] (fp32) and the
+    assignments labels[l][p] (cluster index per real child, in slot order)."""
+    f = scale_factor if scale_factor > 0 else float(fanout) ** (1.0 / 3.0)
+    out = [{k: pages[k] for k in ("pos", "scale", "rot", "opacity", "sh")}]
+    n_pages, m = pages["opacity"].shape
+    err = np.zeros((n_pages, levels), np.float32)
+    labels = [None]
+    for l in range(1, levels):
+        prev = out[-1]
+        m_new = prev["opacity"].shape[1] // fanout
+        K = prev["sh"].shape[2]
+        cur = dict(pos=np.zeros((n_pages, m_new, 3), np.float32), scale=np.zeros((n_pages, m_new, 3), np.float32),
+                   rot=np.zeros((n_pages, m_new, 4), np.float32), opacity=np.zeros((n_pages, m_new), np.float32),
+                   sh=np.zeros((n_pages, m_new, K, 3), np.float32))
+        lab_l = []
+        for p in range(n_pages):
+            real = np.nonzero(prev["opacity"][p] > 0)[0]
+            n = len(real)
+            if n == 0:
+                lab_l.append(np.zeros(0, np.int64))
+                continue
+            g = {k: prev[k][p][real] for k in ("pos", "scale", "rot", "opacity", "sh")}
+            X = kmeans_features(g["pos"], g["rot"], g["opacity"], g["sh"], attr_weight)
+            k = -(-n // fanout)
+            C0 = X[[i * n // k for i in range(k)]]
+            lab, _ = kmeans_lloyd(X, C0, iters)
+            lab_l.append(lab)
+            slot, emax = 0, 0.0
+            for c in range(k):
+                mem = np.nonzero(lab == c)[0]
+                if len(mem) == 0:
+                    continue
+                par = merge_cluster(g["pos"][mem], g["scale"][mem], g["rot"][mem], g["opacity"][mem], g["sh"][mem], f)
+                for k2 in cur:
+                    cur[k2][p, slot] = par[k2]
+                for j in mem:
+                    d = g["pos"][j].astype(np.float64) - par["pos"]
+                    emax = max(emax, float(np.sqrt(d @ d)) + float(g["scale"][j].astype(np.float64).max()))
+                slot += 1
+            err[p, l] = np.float32(emax)
+        out.append(cur)
+        labels.append(lab_l)
+    return out, err, labels
 
 
 # --------------------------------------------------------------------------- splitmix
@@ -524,6 +666,10 @@ class BuildParams:
     link_sigma: float = 2.0
     seed: int = 77
     links: bool = True
+    lod_method: str = "moment"      # or "kmeans"
+    kmeans_iters: int = 10
+    kmeans_scale: float = 0.0       # 0: fanout^(1/3)
+    kmeans_attr_weight: float = 0.1
 
 
 @dataclass
@@ -554,7 +700,11 @@ def build_scene(raw, bp: BuildParams) -> Scene:
     else:
         order, starts, counts = octree_pages(codes, bp.page_size)
     pages = paged_arrays(dec, order, starts, counts, bp.page_size)
-    levels, err = lod_build(pages, bp.lod_levels, bp.lod_fanout)
+    if bp.lod_method == "kmeans":
+        levels, err, _ = lod_build_kmeans(pages, bp.lod_levels, bp.lod_fanout, bp.kmeans_iters, bp.kmeans_scale,
+                                          bp.kmeans_attr_weight)
+    else:
+        levels, err = lod_build(pages, bp.lod_levels, bp.lod_fanout)
     px = voxel_proxy_and_links(pages["pos"], pages["rot"], pages["scale"], pages["opacity"], counts, bp.page_size,
                                bp.lo, bp.hi, bp.voxel, bp.kappa, bp.closing, bp.link_samples, bp.link_sigma,
                                bp.seed, bp.links)
