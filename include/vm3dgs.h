@@ -82,6 +82,22 @@ typedef struct {
   int32_t links;           /* 0: build no links */
   int32_t fp16;            /* 1: also build the fp16 page records */
   int32_t n_threads;       /* host threads, 0 = all */
+  /* LOD construction (Sec. 3.4).  0: moment matching of `lod_fanout`
+   * consecutive children.  1: the paper's k-means -- per page, the real
+   * Gaussians of level l-1 are clustered into ceil(n / lod_fanout) clusters
+   * (Lloyd's iterations from evenly spaced seeds, at most kmeans_iters) on
+   * features: position centred and divided by the page's RMS radius, then
+   * kmeans_attr_weight x (quaternion with w >= 0, degree-0 SH colour,
+   * opacity); each non-empty cluster becomes one parent with the mean
+   * position, quaternion, opacity and SH and the mean scale times
+   * kmeans_scale (0: lod_fanout^(1/3)) when it merges two or more.  The
+   * page's error at a level is the largest member distance from its parent
+   * plus that member's largest scale.  E_INVAL for another method,
+   * kmeans_iters < 1 or a negative scale or weight. */
+  int32_t lod_method;
+  int32_t kmeans_iters;
+  double kmeans_scale;
+  double kmeans_attr_weight;
 } vm3dgs_build_params;
 
 /* Pinhole camera, OpenCV axes (+x right, +y down, +z forward). */

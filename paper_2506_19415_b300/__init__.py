@@ -43,7 +43,8 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("page_size", c_i32), ("paging", c_i32), ("lod_levels", c_i32), ("lod_fanout", c_i32),
                 ("lo", c_d * 3), ("hi", c_d * 3), ("voxel", c_d), ("kappa", c_d), ("closing", c_i32),
                 ("link_samples", c_i32), ("link_sigma", c_d), ("seed", c_u64), ("links", c_i32), ("fp16", c_i32),
-                ("n_threads", c_i32)]
+                ("n_threads", c_i32), ("lod_method", c_i32), ("kmeans_iters", c_i32), ("kmeans_scale", c_d),
+                ("kmeans_attr_weight", c_d)]
 
 
 class Camera(ctypes.Structure):
@@ -200,6 +201,10 @@ class BuildConfig:
     links: bool = True
     fp16: bool = False
     n_threads: int = 0
+    lod_method: str = "moment"   # or "kmeans" (Sec. 3.4)
+    kmeans_iters: int = 10
+    kmeans_scale: float = 0.0    # 0: lod_fanout^(1/3)
+    kmeans_attr_weight: float = 0.1
 
     def struct(self) -> BuildParams:
         b = BuildParams()
@@ -210,6 +215,11 @@ class BuildConfig:
         b.voxel, b.kappa, b.closing = self.voxel, self.kappa, int(self.closing)
         b.link_samples, b.link_sigma, b.seed = self.link_samples, self.link_sigma, self.seed
         b.links, b.fp16, b.n_threads = int(self.links), int(self.fp16), self.n_threads
+        if self.lod_method not in ("moment", "kmeans"):
+            raise ValueError("lod_method is 'moment' or 'kmeans'")
+        b.lod_method = 1 if self.lod_method == "kmeans" else 0
+        b.kmeans_iters, b.kmeans_scale, b.kmeans_attr_weight = self.kmeans_iters, self.kmeans_scale, \
+            self.kmeans_attr_weight
         return b
 
 

@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, f + ".o")
         objs.append(obj)
         if force or _newer([src] + hdrs + [__file__], obj):
-            _run(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+            _run(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
                   "-I" + os.path.join(CUDA, "include"), "-c", "-o", obj, src])
     if force or _newer(objs, OUT):
         tmp = OUT + ".tmp%d" % os.getpid()

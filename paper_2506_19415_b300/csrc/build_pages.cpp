@@ -10,11 +10,13 @@
 //               zero-opacity Gaussians.  Mode 0: Morton order in chunks.
 //               Mode 1: octree leaves (split while > page_size) in Morton
 //               order, merged greedily up to, never over, the page size.
-//   LOD         Sec. 3.4: only Gaussians of one page merge; parent j of level
-//               l+1 merges children fanout*j.. of level l by moment matching
-//               (weights opacity x volume); opacity is the mean of the real
-//               children; the page's error at level l is its largest parent
-//               standard deviation.
+//   LOD         Sec. 3.4: only Gaussians of one page merge.  Method 0: parent
+//               j of level l+1 merges children fanout*j.. of level l by moment
+//               matching (weights opacity x volume); opacity is the mean of
+//               the real children; the page's error at level l is its largest
+//               parent standard deviation.  Method 1, the paper's own: k-means
+//               clusters of the page's Gaussians in a scaled attribute space,
+//               each averaged into one parent (kmeans_level).
 //   proxy       Sec. 3.1 stand-in: voxels whose means' opacities sum to
 //               kappa, one 3x3x3 closing, exposed faces marked with the
 //               majority page of the voxel and merged into rectangles.
@@ -239,6 +241,164 @@ void majority(std::vector<std::pair<int64_t, int64_t>> &kv, std::vector<int64_t>
   }
 }
 
+
+// One LOD level of one page by k-means (Sec. 3.4): the real children of the
+// level above (opacity > 0, slot order) are clustered into ceil(n / F)
+// clusters in a position-first attribute space and every non-empty cluster
+// becomes one parent.  Every sum runs in member order and every distance in
+// feature order, in double, so the result is a fixed sequence of IEEE
+// operations.
+//   features  (pos - page mean) / page RMS radius (1 if 0); then aw times
+//             the quaternion with w >= 0, the degree-0 SH colour, opacity
+//   seeds     children floor(i * n / k), i < k
+//   Lloyd     nearest centroid (lowest index on a tie), then each centroid
+//             to its points' mean (one without points stays); at most
+//             `iters` rounds, ending early when an assignment repeats
+//   merge     means of position, opacity and SH; quaternions turned to the
+//             first member's hemisphere, summed, normalised, w >= 0; mean
+//             scale times sfac for two or more members
+//   error     max over members of |member - parent position| + the
+//             member's largest scale
+// pb/cb are the SoA blocks (attribute row a at [a * m + g]); cb is zeroed by
+// the caller.  Returns the page's error at this level.
+// Nearest centroid of every point (lowest index on a tie).  X is [n][D],
+// C is feature-major [D][k]; each distance sums its D squared differences in
+// feature order, so vectorising across centroids leaves every value as is.
+template <int D>
+__attribute__((target_clones("avx2", "default"))) void assign_nearest(const double *__restrict X, int n,
+                                                                      const double *__restrict C, int k,
+                                                                      double *__restrict dist, int *__restrict lab) {
+  for (int i = 0; i < n; ++i) {
+    const double *x = X + (size_t)i * D;
+    for (int j = 0; j < k; ++j) dist[j] = 0.0;
+    for (int a = 0; a < D; ++a) {
+      const double xa = x[a];
+      const double *__restrict ca = C + (size_t)a * k;
+      for (int j = 0; j < k; ++j) {
+        const double t = xa - ca[j];
+        dist[j] += t * t;
+      }
+    }
+    int best = 0;
+    for (int j = 1; j < k; ++j)
+      if (dist[j] < dist[best]) best = j;
+    lab[i] = best;
+  }
+}
+
+double kmeans_level(const float *pb, int64_t mp, float *cb, int64_t mn, int K, int F, int iters, double sfac,
+                    double aw) {
+  constexpr int D = 11;
+  std::vector<int> real;
+  for (int64_t g = 0; g < mp; ++g)
+    if (pb[10 * mp + g] > 0) real.push_back((int)g);
+  const int n = (int)real.size();
+  if (n == 0) return 0.0;
+  auto at = [&](int row, int i) { return (double)pb[row * mp + real[i]]; };
+  double mu[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) mu[a] += at(a, i);
+  for (int a = 0; a < 3; ++a) mu[a] /= n;
+  double r2 = 0;
+  for (int i = 0; i < n; ++i) {
+    const double d0 = at(0, i) - mu[0], d1 = at(1, i) - mu[1], d2 = at(2, i) - mu[2];
+    const double t = d0 * d0 + d1 * d1 + d2 * d2;
+    r2 += t;
+  }
+  double rad = std::sqrt(r2 / n);
+  if (!(rad > 0)) rad = 1.0;
+  std::vector<double> X((size_t)n * D);
+  for (int i = 0; i < n; ++i) {
+    double *x = &X[(size_t)i * D];
+    for (int a = 0; a < 3; ++a) x[a] = (at(a, i) - mu[a]) / rad;
+    const bool flip = at(6, i) < 0;
+    for (int a = 0; a < 4; ++a) x[3 + a] = aw * (flip ? -at(6 + a, i) : at(6 + a, i));
+    for (int c = 0; c < 3; ++c) x[7 + c] = aw * at(11 + c, i);
+    x[10] = aw * at(10, i);
+  }
+  const int k = (n + F - 1) / F;
+  // centroids feature-major [D][k] so the distance loop runs along centroids
+  std::vector<double> C((size_t)D * k), acc((size_t)D * k), dist(k);
+  for (int j = 0; j < k; ++j) {
+    const double *x = &X[(size_t)((int64_t)j * n / k) * D];
+    for (int a = 0; a < D; ++a) C[(size_t)a * k + j] = x[a];
+  }
+  std::vector<int> lab(n), prev(n), cnt(k);
+  for (int it = 0; it < iters; ++it) {
+    assign_nearest<D>(X.data(), n, C.data(), k, dist.data(), lab.data());
+    if (it > 0 && lab == prev) break;
+    std::fill(acc.begin(), acc.end(), 0.0);
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int i = 0; i < n; ++i) {
+      const int j = lab[i];
+      ++cnt[j];
+      for (int a = 0; a < D; ++a) acc[(size_t)a * k + j] += X[(size_t)i * D + a];
+    }
+    for (int j = 0; j < k; ++j)
+      if (cnt[j] > 0)
+        for (int a = 0; a < D; ++a) C[(size_t)a * k + j] = acc[(size_t)a * k + j] / cnt[j];
+    prev = lab;
+  }
+  // members of each cluster in slot order
+  std::vector<int> head(k + 1, 0), mem(n);
+  for (int i = 0; i < n; ++i) ++head[lab[i] + 1];
+  for (int j = 0; j < k; ++j) head[j + 1] += head[j];
+  {
+    std::vector<int> fill(head.begin(), head.end() - 1);
+    for (int i = 0; i < n; ++i) mem[fill[lab[i]]++] = i;
+  }
+  std::vector<double> shs(3 * K);
+  double emax = 0.0;
+  int64_t slot = 0;
+  for (int j = 0; j < k; ++j) {
+    const int b = head[j], e = head[j + 1], cn = e - b;
+    if (cn == 0) continue;
+    double q0[4], qs[4] = {0, 0, 0, 0}, ps[3] = {0, 0, 0}, sc[3] = {0, 0, 0}, op = 0;
+    for (int a = 0; a < 4; ++a) q0[a] = at(6 + a, mem[b]);
+    std::fill(shs.begin(), shs.end(), 0.0);
+    for (int t = b; t < e; ++t) {
+      const int i = mem[t];
+      double q[4];
+      for (int a = 0; a < 4; ++a) q[a] = at(6 + a, i);
+      const double dq = q[0] * q0[0] + q[1] * q0[1] + q[2] * q0[2] + q[3] * q0[3];
+      for (int a = 0; a < 4; ++a) qs[a] += dq >= 0 ? q[a] : -q[a];
+      for (int a = 0; a < 3; ++a) ps[a] += at(a, i);
+      for (int a = 0; a < 3; ++a) sc[a] += at(3 + a, i);
+      op += at(10, i);
+      for (int c = 0; c < 3 * K; ++c) shs[c] += at(11 + c, i);
+    }
+    const double nq = std::sqrt(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
+    double q[4];
+    if (nq > 0) {
+      for (int a = 0; a < 4; ++a) q[a] = qs[a] / nq;
+    } else {
+      const double n0 = std::sqrt(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] + q0[3] * q0[3]);
+      for (int a = 0; a < 4; ++a) q[a] = q0[a] / n0;
+    }
+    if (q[0] < 0)
+      for (int a = 0; a < 4; ++a) q[a] = -q[a];
+    double pos[3];
+    for (int a = 0; a < 3; ++a) pos[a] = ps[a] / cn;
+    for (int a = 0; a < 3; ++a) {
+      double s = sc[a] / cn;
+      if (cn >= 2) s = s * sfac;
+      cb[(3 + a) * mn + slot] = (float)s;
+      cb[a * mn + slot] = (float)pos[a];
+    }
+    for (int a = 0; a < 4; ++a) cb[(6 + a) * mn + slot] = (float)q[a];
+    cb[10 * mn + slot] = (float)(op / cn);
+    for (int c = 0; c < 3 * K; ++c) cb[(11 + c) * mn + slot] = (float)(shs[c] / cn);
+    for (int t = b; t < e; ++t) {
+      const int i = mem[t];
+      const double d0 = at(0, i) - pos[0], d1 = at(1, i) - pos[1], d2 = at(2, i) - pos[2];
+      const double smax = std::max(std::max(at(3, i), at(4, i)), at(5, i));
+      emax = std::max(emax, std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) + smax);
+    }
+    ++slot;
+  }
+  return emax;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -252,6 +412,9 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
   if (bp->page_size <= 0 || bp->lod_levels < 1 || bp->lod_levels > kMaxLevels || bp->lod_fanout < 2 ||
       bp->voxel <= 0 || bp->link_samples < 0)
     return fail(VM3DGS_E_INVAL, "bad build parameters");
+  if (bp->lod_method < 0 || bp->lod_method > 1 ||
+      (bp->lod_method == 1 && (bp->kmeans_iters < 1 || !(bp->kmeans_scale >= 0) || !(bp->kmeans_attr_weight >= 0))))
+    return fail(VM3DGS_E_INVAL, "bad LOD method parameters");
   {
     int64_t m = bp->page_size;
     for (int l = 1; l < bp->lod_levels; ++l) {
@@ -343,7 +506,22 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
   }
   // LOD levels and errors
   S->err.assign(NP * S->levels, 0.0f);
-  for (int l = 1; l < S->levels; ++l) {
+  if (bp->lod_method == 1) {
+    const double sfac = bp->kmeans_scale > 0 ? bp->kmeans_scale : std::pow((double)S->fanout, 1.0 / 3.0);
+    for (int l = 1; l < S->levels; ++l) {
+      const int64_t mp = S->m(l - 1), mn = S->m(l);
+      const float *prev = (const float *)(S->data32 + S->off32[l - 1]);
+      float *cur = (float *)(S->data32 + S->off32[l]);
+#pragma omp parallel for schedule(dynamic, 1)
+      for (int64_t p = 0; p < NP; ++p) {
+        float *cb = cur + p * mn * NA;
+        std::memset(cb, 0, sizeof(float) * mn * NA);
+        S->err[p * S->levels + l] = (float)kmeans_level(prev + p * mp * NA, mp, cb, mn, K, S->fanout,
+                                                        bp->kmeans_iters, sfac, bp->kmeans_attr_weight);
+      }
+    }
+  }
+  for (int l = 1; l < S->levels && bp->lod_method != 1; ++l) {
     const int64_t mp = S->m(l - 1), mn = S->m(l), F = S->fanout;
     const float *prev = (const float *)(S->data32 + S->off32[l - 1]);
     float *cur = (float *)(S->data32 + S->off32[l]);

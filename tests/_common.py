@@ -17,10 +17,11 @@ def tiny_scene(links=True):
     return raw, ob.build_scene(raw, bp)
 
 
-def city_scene(n=60000, n_boxes=20, extent=160.0, levels=3, fanout=8, page_size=512, sh=3):
+def city_scene(n=60000, n_boxes=20, extent=160.0, levels=3, fanout=8, page_size=512, sh=3, lod_method="moment"):
     raw = scenegen.city_scene(n=n, n_boxes=n_boxes, extent=extent, sh_degree=sh)
     bp = ob.BuildParams(page_size=page_size, paging="octree", lod_levels=levels, lod_fanout=fanout, lo=(-4, -4, -4),
-                        hi=(extent + 4, extent + 4, 84), voxel=4.0, kappa=0.5, link_samples=4)
+                        hi=(extent + 4, extent + 4, 84), voxel=4.0, kappa=0.5, link_samples=4, lod_method=lod_method,
+                        kmeans_iters=6)
     return raw, ob.build_scene(raw, bp)
 
 

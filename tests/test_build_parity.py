@@ -22,6 +22,14 @@ CASES = {
     "halving_lod": (lambda: scenegen.uniform_scene(n=5000, seed=8, sh_degree=1),
                     dict(page_size=256, paging="octree", lod_levels=4, lod_fanout=2, lo=(-5, -5, -5), hi=(5, 5, 5),
                          voxel=0.5, kappa=0.3, link_samples=2)),
+    # the paper's own LOD: k-means per page, halving per level (Sec. 3.4)
+    "kmeans_halving": (lambda: scenegen.uniform_scene(n=5000, seed=9, sh_degree=1),
+                       dict(page_size=256, paging="octree", lod_levels=4, lod_fanout=2, lo=(-5, -5, -5),
+                            hi=(5, 5, 5), voxel=0.5, kappa=0.3, link_samples=2, lod_method="kmeans", kmeans_iters=8)),
+    "kmeans_city": (lambda: scenegen.city_scene(n=20000, n_boxes=8, extent=100.0),
+                    dict(page_size=512, paging="octree", lod_levels=3, lod_fanout=2, lo=(-4, -4, -4),
+                         hi=(104, 104, 84), voxel=4.0, kappa=0.5, link_samples=2, lod_method="kmeans",
+                         kmeans_iters=10, kmeans_attr_weight=0.2)),
 }
 
 
@@ -99,3 +107,44 @@ def test_import_roundtrip():
         for k in U:
             np.testing.assert_array_equal(U[k], osc.levels[l][k])
     np.testing.assert_array_equal(imp.pages(0, fp16=True), psc.pages(0, fp16=True))
+
+
+def _ulps(a, b):
+    """Distance in units in the last place between fp32 arrays."""
+    ia = a.astype(np.float32).view(np.int32).astype(np.int64)
+    ib = b.astype(np.float32).view(np.int32).astype(np.int64)
+    ia = np.where(ia < 0, -(ia & 0x7FFFFFFF), ia)
+    ib = np.where(ib < 0, -(ib & 0x7FFFFFFF), ib)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("name", ["kmeans_halving", "kmeans_city"])
+def test_kmeans_levels_match_oracle(name):
+    """k-means LOD: the same clusters (hence the same parents in the same
+    slots) and every merged attribute within one fp32 ulp of the oracle's;
+    both sides run the same sequence of FP64 operations except the
+    quaternion norms and the error's distance, which may round differently."""
+    raw, osc, psc = _both(name)
+    for l in range(1, len(osc.levels)):
+        Pl, O = psc.unpack(l), osc.levels[l]
+        np.testing.assert_array_equal(Pl["opacity"] > 0, O["opacity"] > 0)
+        for k in ("pos", "scale", "rot", "opacity", "sh"):
+            assert int(_ulps(Pl[k], O[k]).max()) <= 1, (l, k)
+    e = psc.export(v.SCENE_ERR, dtype=np.float32).reshape(osc.n_pages, -1)
+    assert int(_ulps(e, osc.err).max()) <= 1
+    # the paper's halving: real parents per page at most ceil(children / fanout)
+    F = osc.params.lod_fanout
+    for l in range(1, len(osc.levels)):
+        a = (osc.levels[l - 1]["opacity"] > 0).sum(1)
+        b = (osc.levels[l]["opacity"] > 0).sum(1)
+        assert np.all(b <= -(-a // F)) and np.all(b >= 1)
+
+
+def test_kmeans_parameters_rejected():
+    raw = scenegen.uniform_scene(n=500, seed=2)
+    for bad in (dict(kmeans_iters=0), dict(kmeans_scale=-1.0), dict(kmeans_attr_weight=-0.5)):
+        with pytest.raises(v.Vm3dgsError):
+            v.vm3dgs_build_pages(raw, v.BuildConfig(page_size=64, lod_levels=2, lod_fanout=2, lod_method="kmeans",
+                                                    **bad))
+    with pytest.raises(ValueError):
+        v.BuildConfig(lod_method="median").struct()

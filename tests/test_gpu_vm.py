@@ -117,6 +117,17 @@ def test_halving_lod_four_levels(v):
     assert r.stats()["staged_projection"] == 0
 
 
+@pytest.mark.parametrize("fp16", [False, True])
+def test_kmeans_lod_trajectory(v, fp16):
+    """The paper's k-means LOD (four levels, halving per level): LOD choice,
+    residency, streaming and images along a trajectory equal the oracle's
+    on the k-means levels."""
+    raw, sc = city_scene(levels=4, fanout=2, page_size=256, n=30000, lod_method="kmeans")
+    cams = [city_cam(160.0, k, width=160, height=96) for k in range(8)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=10, budget_pages=4, lod=True, tau0=4.0, fp16=fp16,
+                    check_images=(0, 7))
+
+
 def test_fully_resident_vm_render_equals_full_scene(v):
     """Pool holding the whole scene, LOD off: after feedback-driven streaming
     frames (pages land in arbitrary slots), requesting every page renders the
