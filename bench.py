@@ -16,6 +16,7 @@ Synthetic, seeded inputs (scenegen); no dataset.
   python bench.py [--gpus N --steps K --warmup W] [--config city50m|blobs1m|tiny]
   python bench.py --impl reference ...   (the CPU oracle, bounded sample)
   python bench.py --table pagesize|buffer (the page-size / buffer-size tables of Sec. 5)
+  python bench.py --table lod            (k-means LOD against moment matching: time and PSNR)
 """
 from __future__ import annotations
 
@@ -738,6 +739,93 @@ def paging_tables(args):
                       "timing": "CUDA events per stage, every call on one stream", "rows": rows}))
 
 
+def lod_table(args, every=25):
+    """The paper's LOD (Sec. 3.4: k-means inside each page, the page halving
+    per level, four levels) beside the moment-matching LOD (fanout 8, three
+    levels), pages of 2048, on pools of 125, 250 and 500 pages where LOD has
+    to cut detail.  All renderers step through the same walk in lockstep on one
+    stream; per-frame medians of the stage times, drawn Gaussians and missing
+    pages, and the PSNR of every `every`-th frame against the full-detail
+    render (LOD off, the whole 2 GiB pool)."""
+    import torch
+    import paper_2506_19415_b300 as v
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    base = workload(args.config)
+    frames, warm = min(args.steps, 300), args.warmup
+    cams = base["path"](base["frames"])
+    width, height = cams[0].width, cams[0].height
+    st = torch.cuda.current_stream()
+    Wm = dict(base, build=dict(base["build"], page_size=2048))
+    Wk = dict(base, build=dict(base["build"], page_size=2048, lod_levels=4, lod_fanout=2, lod_method="kmeans"))
+    sm, _, tbm = build_scene(Wm)
+    sk, _, tbk = build_scene(Wk)
+    ref = make_renderer(v, sm, dict(Wm, lod=False), True, width, height)
+    arms = []
+    for label, sc, W, tb in (("moment matching, fanout 8, 3 levels", sm, Wm, tbm),
+                             ("k-means, halving, 4 levels", sk, Wk, tbk)):
+        for slots in (125, 250, 500):
+            arms.append(dict(lod=label, pool_slots=slots, build_s=round(tb, 1), host_bytes=int(sc.info.host_bytes),
+                             r=make_renderer(v, sc, W, True, width, height, pool_slots=slots, max_pairs=32 << 20),
+                             per=[], mse=[]))
+    img_ref = torch.empty((3, height, width), dtype=torch.float32, device="cuda")
+    img = torch.empty_like(img_ref)
+    ref_missing = 0
+
+    def frame(r, i, out):
+        c = [cams[i % len(cams)]]
+        r.render_feedback(c, st)
+        r.update_residency(st)
+        r.render(c, [out], st)
+
+    for i in range(warm + frames):
+        if i == warm:
+            torch.cuda.synchronize()
+            for a in arms:
+                a["r"].timing(True)
+                a["r"].timing_read()
+        frame(ref, i, img_ref)
+        sample = i >= warm and (i - warm) % every == 0
+        if sample:
+            ref_missing = max(ref_missing, ref.stats(st)["missing"])
+        for a in arms:
+            frame(a["r"], i, img)
+            if i < warm:
+                continue
+            ms, _ = a["r"].timing_read()
+            s = a["r"].stats(st)
+            if s["status"] != 0:
+                raise RuntimeError("renderer status %d" % s["status"])
+            d = dict(zip(v.STAGES, ms))
+            a["per"].append(dict(frame_ms=sum(ms), render_ms=d["project"] + d["blend"],
+                                 depth_sort_ms=d["scan_emit"] + d["sort"] + d["ranges"],
+                                 page_table_update_ms=d["residency"], drawn_gaussians=s["drawn_gaussians"],
+                                 missing_pages=s["missing"], tau=s["tau"]))
+            if sample:
+                x, y = img.clamp(0.0, 1.0).double(), img_ref.clamp(0.0, 1.0).double()
+                a["mse"].append(float(((x - y) ** 2).mean()))
+    rows = []
+    for a in arms:
+        a["r"].timing(False)
+        per = a.pop("per")
+        row = {k: a[k] for k in ("lod", "pool_slots", "build_s", "host_bytes")}
+        for k in per[0]:
+            row[k] = round(float(np.median([p[k] for p in per])), 4)
+        row["missing_pages_mean"] = round(float(np.mean([p["missing_pages"] for p in per])), 2)
+        row["tau_last"] = round(float(per[-1]["tau"]), 3)
+        mse = np.asarray(a["mse"])
+        psnr = lambda e: round(10.0 * math.log10(1.0 / e), 2) if e > 0 else None  # None: identical images
+        row["psnr_db_pooled"] = psnr(float(mse.mean()))
+        row["psnr_db_worst_frame"] = psnr(float(mse.max()))
+        row["frames_identical"] = "%d of %d" % (int((mse == 0).sum()), len(mse))
+        rows.append(row)
+    print(json.dumps({"table": "lod", "workload": base["name"] + "; pages of 2048", "frames": frames, "warmup": warm,
+                      "psnr": "every %dth frame against the LOD-off render with every page resident (images clamped "
+                              "to [0, 1]): over the pooled squared error of those frames and on the worst one; "
+                              "the reference missed at most %d pages on them" % (every, ref_missing),
+                      "statistic": "median over frames (missing pages also as a mean)",
+                      "timing": "CUDA events per stage, every call on one stream", "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,13 +836,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefetch", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--table", choices=("pagesize", "buffer"), default=None,
-                    help="print the page-size or buffer-size table of Sec. 5 instead of the benchmark line")
+    ap.add_argument("--table", choices=("pagesize", "buffer", "lod"), default=None,
+                    help="print the page-size or buffer-size table of Sec. 5, or the LOD comparison, instead of the "
+                         "benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_main(args)
+    elif args.table == "lod":
+        lod_table(args)
     elif args.table is not None:
         paging_tables(args)
     else:

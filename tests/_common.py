@@ -25,6 +25,19 @@ def city_scene(n=60000, n_boxes=20, extent=160.0, levels=3, fanout=8, page_size=
     return raw, ob.build_scene(raw, bp)
 
 
+def round16_scene(sc):
+    """The scene as an fp16 pool stores it: scale, rotation and SH rounded to
+    half precision (round to nearest even), position and opacity kept fp32."""
+    import dataclasses
+    levels = []
+    for L in sc.levels:
+        L = dict(L)
+        for k in ("scale", "rot", "sh"):
+            L[k] = L[k].astype(np.float16).astype(np.float32)
+        levels.append(L)
+    return dataclasses.replace(sc, levels=levels)
+
+
 def import_scene(v, raw, sc, fp16=False):
     return v.vm3dgs_scene_import(sc.levels, sc.err, sc.count, sc.verts, sc.tris, sc.face_page, sc.link_ptr,
                                  sc.link_col, sc.params.page_size, sc.params.lod_fanout, raw.sh_degree, fp16=fp16)
