@@ -17,6 +17,7 @@ Synthetic, seeded inputs (scenegen); no dataset.
   python bench.py --impl reference ...   (the CPU oracle, bounded sample)
   python bench.py --table pagesize|buffer (the page-size / buffer-size tables of Sec. 5)
   python bench.py --table lod            (k-means LOD against moment matching: time and PSNR)
+  python bench.py --table disk           (the scene from a memory-mapped file through a staging buffer)
 """
 from __future__ import annotations
 
@@ -826,6 +827,61 @@ def lod_table(args, every=25):
                       "timing": "CUDA events per stage, every call on one stream", "rows": rows}))
 
 
+def disk_table(args):
+    """Sec. 3.5 / Sec. 4.1 "Transfer": the scene saved to a file and opened
+    as a read-only mapping, its pages gathered by host threads into a
+    page-locked staging buffer each frame, against the same scene held in
+    page-locked memory and pulled by the GPU.  The walk runs through the
+    public calls (fp16 pool, the overlapped streams of the headline loop);
+    "cold" first drops the file's pages from the OS cache, so the first
+    touches read the disk."""
+    import tempfile
+    import torch
+    import paper_2506_19415_b300 as v
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    W = workload(args.config)
+    cams = W["path"](W["frames"])
+    width, height = cams[0].width, cams[0].height
+    scene, _, _ = build_scene(W)
+    d = args.scene_dir or tempfile.gettempdir()
+    path = os.path.join(d, "vm3dgs_%s_%d.scene" % (args.config, os.getpid()))
+    t0 = time.time()
+    scene.save(path)
+    t_save = time.time() - t0
+    rows, img = [], {}
+    try:
+        for label in ("in memory (page-locked, GPU pulls)", "file, warm OS cache", "file, cold OS cache"):
+            if label.startswith("file"):
+                if "cold" in label:
+                    fd = os.open(path, os.O_RDONLY)
+                    os.fsync(fd)
+                    os.posix_fadvise(fd, 0, 0, os.POSIX_FADV_DONTNEED)
+                    os.close(fd)
+                sc = v.vm3dgs_scene_open(path)
+            else:
+                sc = scene
+            r = make_renderer(v, sc, W, True, width, height)
+            warm = 0 if "cold" in label else args.warmup
+            res = run_arm(v, r, cams, warm, args.steps, torch.cuda.Stream())
+            st = res["stats"]
+            frames = max(st["acc_frames"], 1)
+            out = torch.empty((3, height, width), dtype=torch.float32, device="cuda")
+            r.render([cams[(warm + args.steps - 1) % len(cams)]], [out])
+            img[label] = out.cpu()
+            rows.append(dict(scene=label, ms_per_frame=round(res["ms"] / args.steps, 4),
+                             frames_per_s=round(1e3 * args.steps / res["ms"], 1),
+                             streamed_mb_per_frame=round(st["acc_streamed_bytes"] / frames / 1e6, 3),
+                             missing_per_frame=round(st["acc_missing"] / frames, 2), warmup=warm))
+            del r, sc
+            torch.cuda.empty_cache()
+    finally:
+        os.remove(path)
+    same = all(torch.equal(img[k], img[rows[0]["scene"]]) for k in img)
+    print(json.dumps({"table": "disk", "workload": W["name"], "steps": args.steps,
+                      "file_bytes": int(scene.info.host_bytes), "save_s": round(t_save, 1),
+                      "last_image_equal_across_rows": same, "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -836,9 +892,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefetch", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--table", choices=("pagesize", "buffer", "lod"), default=None,
-                    help="print the page-size or buffer-size table of Sec. 5, or the LOD comparison, instead of the "
-                         "benchmark line")
+    ap.add_argument("--table", choices=("pagesize", "buffer", "lod", "disk"), default=None,
+                    help="print the page-size or buffer-size table of Sec. 5, the LOD comparison or the "
+                         "file-backed scene measurement instead of the benchmark line")
+    ap.add_argument("--scene-dir", default=None, help="directory for the scene file of --table disk")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -846,6 +903,8 @@ def main():
         reference_main(args)
     elif args.table == "lod":
         lod_table(args)
+    elif args.table == "disk":
+        disk_table(args)
     elif args.table is not None:
         paging_tables(args)
     else:

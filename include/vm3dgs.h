@@ -211,6 +211,28 @@ int vm3dgs_scene_export(const vm3dgs_scene *s, int32_t what, int32_t level, void
                         int64_t *needed);
 void vm3dgs_scene_destroy(vm3dgs_scene *s);
 
+/* Scene files (Sec. 3.5, "Scene Storage": the proxy loads at once, the
+ * Gaussians stay in a memory-mapped file that the OS reads on demand, so a
+ * scene may exceed host memory).
+ *
+ * vm3dgs_scene_save writes everything a scene holds to `path` (a
+ * little-endian binary of this library's own layout: a header, the per-page
+ * counts, sources, errors, proxy mesh, links and centroids, then the fp32 and,
+ * if built, fp16 page data, each at a 4096-byte aligned offset).  E_INVAL if
+ * the file cannot be written.
+ *
+ * vm3dgs_scene_open reads the header and the small arrays and maps the page
+ * data read-only; *out owns the mapping.  E_INVAL for a missing, truncated or
+ * inconsistent file, E_NOMEM if the mapping fails.  A renderer on an opened
+ * scene moves pages as the paper does: vm3dgs_update_residency reads the copy
+ * list back (a stream synchronisation), copies the pages from the mapping
+ * into a page-locked staging buffer of staging_bytes with host threads, and
+ * streams from there on `stream` (its copy_stream is not used); the frame's
+ * results equal those of the in-memory scene.  vm3dgs_prefetch returns
+ * E_STATE on such a renderer. */
+int vm3dgs_scene_save(const vm3dgs_scene *s, const char *path);
+int vm3dgs_scene_open(const char *path, vm3dgs_scene **out);
+
 /* Device memory the caller must provide for a renderer. */
 int vm3dgs_pool_slot_bytes(const vm3dgs_scene *s, int32_t fp16_pool, int64_t *out);
 int vm3dgs_scratch_bytes(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t pool_bytes, int64_t *out);

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvm3dgs.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libvm3dgs.so is not built; run `python -m paper_2506_19415_b300._build` "
+    raise ImportError("libvm3dgs.so is not built; run `python paper_2506_19415_b300/_build.py` "
                       "(or __graft_entry__.build()) first")
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -97,6 +97,8 @@ _SIGS = {
     "vm3dgs_scene_info_get": [c_p, ctypes.POINTER(SceneInfo)],
     "vm3dgs_scene_export": [c_p, c_i32, c_i32, c_p, c_i64, ctypes.POINTER(c_i64)],
     "vm3dgs_scene_destroy": [c_p],
+    "vm3dgs_scene_save": [c_p, ctypes.c_char_p],
+    "vm3dgs_scene_open": [ctypes.c_char_p, ctypes.POINTER(c_p)],
     "vm3dgs_pool_slot_bytes": [c_p, c_i32, ctypes.POINTER(c_i64)],
     "vm3dgs_scratch_bytes": [c_p, ctypes.POINTER(Params), c_i64, ctypes.POINTER(c_i64)],
     "vm3dgs_renderer_create": [c_p, ctypes.POINTER(Params), c_p, c_i64, c_p, c_i64, c_p, ctypes.POINTER(c_p)],
@@ -237,6 +239,10 @@ class Scene:
             _lib.vm3dgs_scene_destroy(self.h)
             self.h = None
 
+    def save(self, path):
+        """Writes the scene to a file that vm3dgs_scene_open maps (Sec. 3.5)."""
+        _check(_lib.vm3dgs_scene_save(self.h, os.fsencode(path)))
+
     def export(self, what, level=0, dtype=np.uint8):
         need = c_i64()
         _check(_lib.vm3dgs_scene_export(self.h, what, level, None, 0, ctypes.byref(need)))
@@ -270,6 +276,17 @@ def vm3dgs_build_pages(raw, cfg: BuildConfig) -> Scene:
     h = c_p()
     b = cfg.struct()
     _check(_lib.vm3dgs_build_pages(ctypes.byref(g), ctypes.byref(b), ctypes.byref(h)))
+    return Scene(h)
+
+
+def vm3dgs_scene_save(scene, path):
+    scene.save(path)
+
+
+def vm3dgs_scene_open(path) -> Scene:
+    """A scene whose page data stays in a read-only mapping of the file."""
+    h = c_p()
+    _check(_lib.vm3dgs_scene_open(os.fsencode(path), ctypes.byref(h)))
     return Scene(h)
 
 

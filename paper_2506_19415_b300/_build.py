@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, f + ".o")
         objs.append(obj)
         if force or _newer([src] + hdrs + [__file__], obj):
-            flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+            flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "--expt-relaxed-constexpr"]
             if f in EXACT:
                 flags += ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
             if verbose:

@@ -339,6 +339,8 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
                                const vm3dgs_camera *prev, float threshold, void *stream, void *copy_stream) {
   if (!r || !p || !cam || !prev) return fail(VM3DGS_E_INVAL, "null argument");
   if (r->state < 2) return fail(VM3DGS_E_STATE, "prefetch before update_residency");
+  if (r->staged)
+    return fail(VM3DGS_E_STATE, "prefetch streams from page-locked scene memory; a scene opened from a file has none");
   const int n_out = p->cfg.n_out;
   if (n_out % 16 || p->cfg.n_in != 12 + n_out / 16)
     return fail(VM3DGS_E_INVAL, "network must have n_in = 12 + n_out / 16 and n_out a multiple of 16");

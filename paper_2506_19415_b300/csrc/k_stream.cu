@@ -6,7 +6,9 @@
 // CPU.  Work is cut into 64 KiB segments spread over a persistent grid;
 // every copied page is one contiguous block on both sides.  A thread issues
 // kInFlight loads before its stores, so a segment crosses the host link in
-// one round trip.
+// one round trip.  For a scene opened from a file the host first gathers the
+// frame's pages into a page-locked staging buffer, and the kernel reads each
+// copy at its staging offset instead.
 #include "renderer.cuh"
 
 namespace vm {
@@ -30,7 +32,8 @@ __global__ void __launch_bounds__(kStreamThreads) stream_kernel(StreamArgs a) {
     const int64_t bytes = (int64_t)m * a.rec;
     const int64_t off = (sg - a.copy_seg[lo]) * kCopySeg;
     const int64_t len = bytes - off < kCopySeg ? bytes - off : kCopySeg;
-    const uint4 *src = reinterpret_cast<const uint4 *>(a.host + a.level_off[c.y] + (int64_t)c.x * bytes + off);
+    const uint4 *src = reinterpret_cast<const uint4 *>(
+        a.host + (a.staged_off ? a.staged_off[lo] : a.level_off[c.y] + (int64_t)c.x * bytes) + off);
     uint4 *dst = reinterpret_cast<uint4 *>(a.pool + (int64_t)c.z * a.slot_bytes + (int64_t)c.w * bytes + off);
     const int64_t n16 = len / 16;
     for (int64_t i0 = threadIdx.x; i0 < n16; i0 += (int64_t)kInFlight * kStreamThreads) {

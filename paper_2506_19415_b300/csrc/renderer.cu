@@ -142,6 +142,7 @@ Layout make_layout(const Dims &d) {
   L.admitted_pos = take(4 * NP);
   L.copies = take(16 * NP);
   L.copy_seg = take(8 * (NP + 1));
+  L.staged_off = take(8 * (NP + 1));
   L.draw = take(16 * NP);
   L.draw_off = take(8 * (NP + 1));
   L.missing = take(4 * NP);
@@ -273,12 +274,27 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   r->dims = d;
   r->lay = L;
   cudaStream_t st = (cudaStream_t)stream;
-  // page-lock the pages the GPU will pull, once per scene
+  // page-lock the pages the GPU will pull, once per scene; a scene mapped
+  // from a file is read by the host into a page-locked staging buffer instead
   auto *ms = const_cast<vm3dgs_scene *>(s);
   uint8_t *data = r->fp16 ? ms->data16 : ms->data32;
   const int64_t bytes = r->fp16 ? ms->bytes16 : ms->bytes32;
   bool &reg = r->fp16 ? ms->registered16 : ms->registered32;
-  if (!reg) {
+  if (ms->mapped) {
+    r->staged = true;
+    const size_t sbytes = (size_t)((p->staging_bytes + 4095) / 4096 * 4096);
+    if (!cuda_ok(cudaHostAlloc((void **)&r->staging, sbytes > 0 ? sbytes : 4096, cudaHostAllocMapped), "cudaHostAlloc",
+                 &rc) ||
+        !cuda_ok(cudaHostAlloc((void **)&r->h_copies, 16 * (size_t)d.NP + 16, cudaHostAllocDefault), "cudaHostAlloc",
+                 &rc) ||
+        !cuda_ok(cudaHostAlloc((void **)&r->h_off, 8 * (size_t)(d.NP + 1), cudaHostAllocDefault), "cudaHostAlloc",
+                 &rc) ||
+        !cuda_ok(cudaHostAlloc((void **)&r->h_count, 64, cudaHostAllocDefault), "cudaHostAlloc", &rc)) {
+      vm3dgs_renderer_destroy(r);
+      return rc;
+    }
+    data = r->staging;
+  } else if (!reg) {
     if (!cuda_ok(cudaHostRegister(data, (size_t)((bytes + 4095) / 4096 * 4096),
                                   cudaHostRegisterMapped | cudaHostRegisterPortable),
                  "cudaHostRegister", &rc)) {
@@ -390,6 +406,10 @@ extern "C" void vm3dgs_renderer_destroy(vm3dgs_renderer *r) {
   if (r->proj_done) cudaEventDestroy(r->proj_done);
   for (auto e : r->ctx_free)
     if (e) cudaEventDestroy(e);
+  if (r->staging) cudaFreeHost(r->staging);
+  if (r->h_copies) cudaFreeHost(r->h_copies);
+  if (r->h_off) cudaFreeHost(r->h_off);
+  if (r->h_count) cudaFreeHost(r->h_count);
   delete r;
 }
 
@@ -539,6 +559,39 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   sa.rec = r->rec;
   sa.pool = r->pool;
   sa.slot_bytes = r->slot_bytes;
+  if (r->staged) {
+    // the paper's transfer: the copy list returns to the host, which copies
+    // the pages from the file mapping (the OS reads what is not cached) into
+    // the staging buffer; the update completes its copies before returning
+    int rc = VM3DGS_OK;
+    const int NPc = (int)r->dims.NP;
+    const bool ok =
+        cuda_ok(cudaMemcpyAsync(r->h_count, &a.ctl->n_copies, 4, cudaMemcpyDeviceToHost, st), "copy", &rc) &&
+        cuda_ok(cudaMemcpyAsync(r->h_copies, a.copies, 16 * (size_t)NPc, cudaMemcpyDeviceToHost, st), "copy", &rc) &&
+        cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize", &rc);
+    if (!ok) return rc;
+    const int n = std::min(std::max(*r->h_count, 0), NPc);
+    const uint8_t *base = r->fp16 ? s->data16 : s->data32;
+    int64_t cum = 0;
+    for (int i = 0; i < n; ++i) {
+      r->h_off[i] = cum;
+      cum += (int64_t)s->m(r->h_copies[i].y) * r->rec;
+    }
+    r->h_off[n] = cum;
+    if (cum > r->prm.staging_bytes) return fail(VM3DGS_E_CAPACITY, "copies exceed the staging buffer");
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; ++i) {
+      const int4 c = r->h_copies[i];
+      const int64_t pb = (int64_t)s->m(c.y) * r->rec;
+      const int64_t lo = r->fp16 ? s->off16[c.y] : s->off32[c.y];
+      std::memcpy(r->staging + r->h_off[i], base + lo + (int64_t)c.x * pb, (size_t)pb);
+    }
+    int64_t *d_off = r->at<int64_t>(r->lay.staged_off);
+    if (!cuda_ok(cudaMemcpyAsync(d_off, r->h_off, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st), "copy", &rc))
+      return rc;
+    sa.staged_off = d_off;
+    cst = st;  // the staging buffer is refilled by the next update, after this stream's copies
+  }
   if (cst == st) {
     const int sp = r->span_begin(VM3DGS_STAGE_STREAM, st);
     launch_stream(sa, st);

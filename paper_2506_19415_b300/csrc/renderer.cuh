@@ -62,7 +62,7 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
       clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
-      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, total;
+      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, staged_off, total;
   CtxLayout cx[kContexts];
 };
 
@@ -161,6 +161,7 @@ struct StreamArgs {
   const int4 *copies;
   const int64_t *copy_seg;
   const uint8_t *host;          // device-visible pointer to the scene's page data (fp32 or fp16)
+  const int64_t *staged_off;    // null, or the byte offset in `host` of each copy (a staging buffer)
   int64_t level_off[kMaxLevels];
   int32_t page_size, fanout, rec;
   uint8_t *pool;
@@ -283,6 +284,13 @@ struct vm3dgs_renderer {
   vm::Dims dims{};
   vm::Layout lay{};
   const uint8_t *host_dev = nullptr;   // device-visible pointer to the pages streamed
+  // scene opened from a file: the frame's pages pass through a page-locked
+  // staging buffer the host fills from the file mapping (Sec. 4.1, Transfer)
+  bool staged = false;
+  uint8_t *staging = nullptr;           // page-locked, staging_bytes
+  int32_t *h_count = nullptr;           // page-locked copy-list readback
+  int4 *h_copies = nullptr;
+  int64_t *h_off = nullptr;             // page-locked byte offsets of the copies in staging
   int state = 0;                        // 0 idle, 1 feedback done, 2 residency done
   float f_px = 0.0f;
   cudaEvent_t copy_done = nullptr;

@@ -1,8 +1,13 @@
 // Scene object: error reporting, import of prepared pages, inspection.
 #include <cuda_runtime.h>
+#include <fcntl.h>
+#include <sys/mman.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -58,10 +63,135 @@ void finish_scene(vm3dgs_scene *S) {
 }  // namespace vm
 
 vm3dgs_scene::~vm3dgs_scene() {
+  if (mapped) {
+    if (map_base) munmap(map_base, map_len);
+    return;
+  }
   if (registered32 && data32) cudaHostUnregister(data32);
   if (registered16 && data16) cudaHostUnregister(data16);
   std::free(data32);
   std::free(data16);
+}
+
+// ---------------------------------------------------------------- scene files
+// Layout: FileHeader, then the arrays count, src, err, verts, tris, face_page,
+// link_ptr, link_col, centroid in that order; the fp32 page data at a
+// 4096-aligned offset, then the fp16 page data (if built) at the next one.
+namespace {
+constexpr char kMagic[8] = {'V', 'M', '3', 'D', 'G', 'S', 'f', '1'};
+struct FileHeader {
+  char magic[8];
+  int32_t n_pages, page_size, levels, fanout, sh_degree, K, rec32, rec16;
+  int64_t n_gauss, bytes32, bytes16;
+  int64_t off32[vm::kMaxLevels], off16[vm::kMaxLevels];
+  int64_t n_count, n_src, n_err, n_verts, n_tris, n_face, n_lptr, n_lcol, n_centroid;
+  float box_center[3], box_half;
+  int64_t data32_at, data16_at, file_bytes;
+};
+int64_t align4k(int64_t x) { return (x + 4095) / 4096 * 4096; }
+}  // namespace
+
+extern "C" int vm3dgs_scene_save(const vm3dgs_scene *s, const char *path) {
+  if (!s || !path) return vm::fail(VM3DGS_E_INVAL, "null argument");
+  FileHeader h{};
+  std::memcpy(h.magic, kMagic, 8);
+  h.n_pages = s->n_pages; h.page_size = s->page_size; h.levels = s->levels; h.fanout = s->fanout;
+  h.sh_degree = s->sh_degree; h.K = s->K; h.rec32 = s->rec32; h.rec16 = s->rec16;
+  h.n_gauss = s->n_gauss; h.bytes32 = s->bytes32; h.bytes16 = s->data16 ? s->bytes16 : 0;
+  for (int l = 0; l < vm::kMaxLevels; ++l) { h.off32[l] = s->off32[l]; h.off16[l] = s->off16[l]; }
+  h.n_count = (int64_t)s->count.size(); h.n_src = (int64_t)s->src.size(); h.n_err = (int64_t)s->err.size();
+  h.n_verts = (int64_t)s->verts.size(); h.n_tris = (int64_t)s->tris.size(); h.n_face = (int64_t)s->face_page.size();
+  h.n_lptr = (int64_t)s->link_ptr.size(); h.n_lcol = (int64_t)s->link_col.size();
+  h.n_centroid = (int64_t)s->centroid.size();
+  for (int a = 0; a < 3; ++a) h.box_center[a] = s->box_center[a];
+  h.box_half = s->box_half;
+  const int64_t arrays = 8 * (h.n_count + h.n_src) + 4 * (h.n_err + h.n_verts + h.n_tris + h.n_face) + 8 * h.n_lptr +
+                         4 * (h.n_lcol + h.n_centroid);
+  h.data32_at = align4k((int64_t)sizeof(FileHeader) + arrays);
+  h.data16_at = align4k(h.data32_at + h.bytes32);
+  h.file_bytes = h.bytes16 > 0 ? h.data16_at + h.bytes16 : h.data32_at + h.bytes32;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return vm::fail(VM3DGS_E_INVAL, std::string("cannot create ") + path);
+  bool ok = std::fwrite(&h, sizeof h, 1, f) == 1;
+  auto put = [&](const void *p, int64_t n) { if (ok && n > 0) ok = std::fwrite(p, 1, (size_t)n, f) == (size_t)n; };
+  put(s->count.data(), 8 * h.n_count);
+  put(s->src.data(), 8 * h.n_src);
+  put(s->err.data(), 4 * h.n_err);
+  put(s->verts.data(), 4 * h.n_verts);
+  put(s->tris.data(), 4 * h.n_tris);
+  put(s->face_page.data(), 4 * h.n_face);
+  put(s->link_ptr.data(), 8 * h.n_lptr);
+  put(s->link_col.data(), 4 * h.n_lcol);
+  put(s->centroid.data(), 4 * h.n_centroid);
+  ok = ok && std::fseek(f, (long)h.data32_at, SEEK_SET) == 0;
+  put(s->data32, h.bytes32);
+  if (h.bytes16 > 0) {
+    ok = ok && std::fseek(f, (long)h.data16_at, SEEK_SET) == 0;
+    put(s->data16, h.bytes16);
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return vm::fail(VM3DGS_E_INVAL, std::string("write failed: ") + path);
+  return VM3DGS_OK;
+}
+
+extern "C" int vm3dgs_scene_open(const char *path, vm3dgs_scene **out) {
+  if (!path || !out) return vm::fail(VM3DGS_E_INVAL, "null argument");
+  *out = nullptr;
+  const int fd = ::open(path, O_RDONLY);
+  if (fd < 0) return vm::fail(VM3DGS_E_INVAL, std::string("cannot open ") + path);
+  struct stat sb{};
+  FileHeader h{};
+  const bool head = fstat(fd, &sb) == 0 && pread(fd, &h, sizeof h, 0) == (ssize_t)sizeof h;
+  auto bad = [&](const char *why) {
+    ::close(fd);
+    return vm::fail(VM3DGS_E_INVAL, std::string("not a scene file (") + why + "): " + path);
+  };
+  if (!head || std::memcmp(h.magic, kMagic, 8) != 0) return bad("header");
+  if (h.n_pages <= 0 || h.page_size <= 0 || h.levels < 1 || h.levels > vm::kMaxLevels || h.fanout < 2 ||
+      h.sh_degree < 0 || h.sh_degree > 3 || h.K != (h.sh_degree + 1) * (h.sh_degree + 1) ||
+      h.rec32 != vm::rec_bytes32(h.K) || (h.bytes16 > 0 && h.rec16 != vm::rec_bytes16(h.K)) ||
+      h.n_count != h.n_pages || h.n_src != (int64_t)h.n_pages * h.page_size ||
+      h.n_err != (int64_t)h.n_pages * h.levels || h.n_lptr != h.n_pages + 1 || h.n_tris != 3 * h.n_face ||
+      h.n_verts % 3 || h.n_centroid != 4 * (int64_t)h.n_pages || h.bytes32 <= 0 || h.bytes16 < 0 ||
+      h.data32_at % 4096 || h.data16_at % 4096 || h.file_bytes != (int64_t)sb.st_size ||
+      h.data32_at + h.bytes32 > h.file_bytes || (h.bytes16 > 0 && h.data16_at + h.bytes16 > h.file_bytes))
+    return bad("fields");
+  auto *S = new (std::nothrow) vm3dgs_scene;
+  if (!S) { ::close(fd); return vm::fail(VM3DGS_E_NOMEM, "scene"); }
+  S->n_pages = h.n_pages; S->page_size = h.page_size; S->levels = h.levels; S->fanout = h.fanout;
+  S->sh_degree = h.sh_degree; S->K = h.K; S->rec32 = h.rec32; S->rec16 = h.bytes16 > 0 ? h.rec16 : 0;
+  S->n_gauss = h.n_gauss; S->bytes32 = h.bytes32; S->bytes16 = h.bytes16;
+  for (int l = 0; l < vm::kMaxLevels; ++l) { S->off32[l] = h.off32[l]; S->off16[l] = h.off16[l]; }
+  for (int a = 0; a < 3; ++a) S->box_center[a] = h.box_center[a];
+  S->box_half = h.box_half;
+  int64_t at = (int64_t)sizeof h;
+  bool ok = true;
+  auto get = [&](auto &vec, int64_t n) {
+    vec.resize((size_t)n);
+    const int64_t bytes = n * (int64_t)sizeof(vec[0]);
+    if (ok && bytes > 0) ok = pread(fd, vec.data(), (size_t)bytes, at) == (ssize_t)bytes;
+    at += bytes;
+  };
+  get(S->count, h.n_count);
+  get(S->src, h.n_src);
+  get(S->err, h.n_err);
+  get(S->verts, h.n_verts);
+  get(S->tris, h.n_tris);
+  get(S->face_page, h.n_face);
+  get(S->link_ptr, h.n_lptr);
+  get(S->link_col, h.n_lcol);
+  get(S->centroid, h.n_centroid);
+  if (!ok || at > h.data32_at) { delete S; ::close(fd); return vm::fail(VM3DGS_E_INVAL, "short scene file"); }
+  void *base = mmap(nullptr, (size_t)h.file_bytes, PROT_READ, MAP_SHARED, fd, 0);
+  ::close(fd);
+  if (base == MAP_FAILED) { delete S; return vm::fail(VM3DGS_E_NOMEM, "mmap of the scene file failed"); }
+  S->mapped = true;
+  S->map_base = base;
+  S->map_len = (size_t)h.file_bytes;
+  S->data32 = (uint8_t *)base + h.data32_at;
+  S->data16 = h.bytes16 > 0 ? (uint8_t *)base + h.data16_at : nullptr;
+  *out = S;
+  return VM3DGS_OK;
 }
 
 extern "C" const char *vm3dgs_last_error(void) { return vm::g_last_error.c_str(); }

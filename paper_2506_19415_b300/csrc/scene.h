@@ -58,6 +58,11 @@ struct vm3dgs_scene {
   std::vector<float> centroid;   // [n_pages * 4]: mean of the level-0 means, radius incl. 3 sigma
   float box_center[3] = {0, 0, 0}, box_half = 1.0f;
   bool registered32 = false, registered16 = false;
+  // opened from a scene file: data32/data16 point into a read-only mapping of
+  // the file, read by the OS on first touch (Sec. 3.5, memory-mapped scene)
+  bool mapped = false;
+  void *map_base = nullptr;
+  size_t map_len = 0;
 
   int32_t m(int l) const {
     int32_t v = page_size;
