@@ -37,6 +37,7 @@ def test_mapped_scene_frames_equal_in_memory(v, tmp_path, fp16):
                          fp16_pool=fp16)
     ra, rb = v.Renderer(sc, cfg, pool_slots=8), v.Renderer(op, cfg, pool_slots=8)
     copy_stream = torch.cuda.Stream()
+    host = [sc.pages(l, fp16=fp16) for l in range(3)]
     streamed = 0
     for cam in cams:
         ra.render_feedback([cam])
@@ -50,6 +51,14 @@ def test_mapped_scene_frames_equal_in_memory(v, tmp_path, fp16):
         assert sa["status"] == 0 and sa == sb
         streamed += sb["streamed_pages"]
         for what, dt in ((v.DBG_COPIES, np.int32), (v.DBG_DRAW, np.int32), (v.DBG_PT_SLOT, np.int32),
-                         (v.DBG_PT_LOD, np.int32), (v.DBG_POOL, np.uint8)):
+                         (v.DBG_PT_LOD, np.int32)):
             np.testing.assert_array_equal(ra.debug(what, dt), rb.debug(what, dt))
+        # every drawn sub-slot holds the scene's bytes in both pools (the rest
+        # of a pool is whatever its memory held before)
+        pa = ra.debug(v.DBG_POOL, np.uint8).reshape(8, -1)
+        pb = rb.debug(v.DBG_POOL, np.uint8).reshape(8, -1)
+        for (p, l, e, s_) in ra.debug(v.DBG_DRAW, np.int32).reshape(-1, 4):
+            blk = host[l][p]
+            np.testing.assert_array_equal(pa[e, s_ * len(blk):(s_ + 1) * len(blk)], blk)
+            np.testing.assert_array_equal(pb[e, s_ * len(blk):(s_ + 1) * len(blk)], blk)
     assert streamed > 8   # pages were replaced, not only loaded once
