@@ -225,11 +225,11 @@ void vm3dgs_scene_destroy(vm3dgs_scene *s);
  * data read-only; *out owns the mapping.  E_INVAL for a missing, truncated or
  * inconsistent file, E_NOMEM if the mapping fails.  A renderer on an opened
  * scene moves pages as the paper does: vm3dgs_update_residency reads the copy
- * list back (a stream synchronisation), copies the pages from the mapping
- * into a page-locked staging buffer of staging_bytes with host threads, and
- * streams from there on `stream` (its copy_stream is not used); the frame's
- * results equal those of the in-memory scene.  vm3dgs_prefetch returns
- * E_STATE on such a renderer. */
+ * list back, copies the pages from the mapping into a page-locked staging
+ * buffer of staging_bytes with host threads, and streams from there, all on
+ * `stream` (the gather is a host function in stream order, so the call does
+ * not wait; its copy_stream is not used); the frame's results equal those of
+ * the in-memory scene.  vm3dgs_prefetch returns E_STATE on such a renderer. */
 int vm3dgs_scene_save(const vm3dgs_scene *s, const char *path);
 int vm3dgs_scene_open(const char *path, vm3dgs_scene **out);
 

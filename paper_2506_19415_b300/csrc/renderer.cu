@@ -142,7 +142,6 @@ Layout make_layout(const Dims &d) {
   L.admitted_pos = take(4 * NP);
   L.copies = take(16 * NP);
   L.copy_seg = take(8 * (NP + 1));
-  L.staged_off = take(8 * (NP + 1));
   L.draw = take(16 * NP);
   L.draw_off = take(8 * (NP + 1));
   L.missing = take(4 * NP);
@@ -287,8 +286,9 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
                  &rc) ||
         !cuda_ok(cudaHostAlloc((void **)&r->h_copies, 16 * (size_t)d.NP + 16, cudaHostAllocDefault), "cudaHostAlloc",
                  &rc) ||
-        !cuda_ok(cudaHostAlloc((void **)&r->h_off, 8 * (size_t)(d.NP + 1), cudaHostAllocDefault), "cudaHostAlloc",
+        !cuda_ok(cudaHostAlloc((void **)&r->h_off, 8 * (size_t)(d.NP + 1), cudaHostAllocMapped), "cudaHostAlloc",
                  &rc) ||
+        !cuda_ok(cudaHostGetDevicePointer((void **)&r->h_off_dev, r->h_off, 0), "cudaHostGetDevicePointer", &rc) ||
         !cuda_ok(cudaHostAlloc((void **)&r->h_count, 64, cudaHostAllocDefault), "cudaHostAlloc", &rc)) {
       vm3dgs_renderer_destroy(r);
       return rc;
@@ -485,6 +485,36 @@ extern "C" int vm3dgs_request_all(vm3dgs_renderer *r, void *stream) {
   return VM3DGS_OK;
 }
 
+namespace {
+// Host function of a file-backed update: staging offsets of the copy list
+// just read back, then the pages from the scene mapping into the staging
+// buffer (host threads).  Makes no CUDA call.
+void CUDART_CB gather_staged(void *user) {
+  auto *r = static_cast<vm3dgs_renderer *>(user);
+  const vm3dgs_scene *s = r->scene;
+  const int n = std::min(std::max(*r->h_count, 0), (int)r->dims.NP);
+  int64_t cum = 0;
+  for (int i = 0; i < n; ++i) {
+    r->h_off[i] = cum;
+    cum += (int64_t)s->m(r->h_copies[i].y) * r->rec;
+  }
+  r->h_off[n] = cum;
+  if (cum > r->prm.staging_bytes) {  // cannot happen: admission keeps the copies within the budget;
+    r->staged_err = 1;               // every copy then reads the buffer's start (each page fits in it)
+    for (int i = 0; i <= n; ++i) r->h_off[i] = 0;
+    return;
+  }
+  const uint8_t *base = r->fp16 ? s->data16 : s->data32;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < n; ++i) {
+    const int4 c = r->h_copies[i];
+    const int64_t pb = (int64_t)s->m(c.y) * r->rec;
+    const int64_t lo = r->fp16 ? s->off16[c.y] : s->off32[c.y];
+    std::memcpy(r->staging + r->h_off[i], base + lo + (int64_t)c.x * pb, (size_t)pb);
+  }
+}
+}  // namespace
+
 extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *copy_stream) {
   if (!r) return fail(VM3DGS_E_INVAL, "null renderer");
   if (r->state < 1) return fail(VM3DGS_E_STATE, "update_residency before render_feedback");
@@ -498,6 +528,8 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
     r->copy_pending = false;
   }
   if (r->fb_recorded) cudaStreamWaitEvent(st, r->fb_done, 0);  // page determination on another stream
+  // a file-backed update reuses the read-back and staging buffers of the last one
+  if (r->staged && r->upd_recorded) cudaStreamWaitEvent(st, r->upd_done, 0);
   // the last render's projection has read the pool and the draw list
   if (r->proj_recorded) cudaStreamWaitEvent(st, r->proj_done, 0);
   const vm3dgs_scene *s = r->scene;
@@ -562,35 +594,23 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   if (r->staged) {
     // the paper's transfer: the copy list returns to the host, which copies
     // the pages from the file mapping (the OS reads what is not cached) into
-    // the staging buffer; the update completes its copies before returning
+    // the staging buffer, then the GPU streams them.  The host gather is a
+    // host function in stream order (between the list's read-back and the
+    // stream kernel), so the calling thread does not wait; the next update's
+    // gather follows this update's copies on the same stream.
+    if (r->staged_err) {
+      r->staged_err = 0;
+      return fail(VM3DGS_E_CAPACITY, "an earlier update's copies exceeded the staging buffer");
+    }
     int rc = VM3DGS_OK;
     const int NPc = (int)r->dims.NP;
     const bool ok =
         cuda_ok(cudaMemcpyAsync(r->h_count, &a.ctl->n_copies, 4, cudaMemcpyDeviceToHost, st), "copy", &rc) &&
         cuda_ok(cudaMemcpyAsync(r->h_copies, a.copies, 16 * (size_t)NPc, cudaMemcpyDeviceToHost, st), "copy", &rc) &&
-        cuda_ok(cudaStreamSynchronize(st), "cudaStreamSynchronize", &rc);
+        cuda_ok(cudaLaunchHostFunc(st, gather_staged, r), "cudaLaunchHostFunc", &rc);
     if (!ok) return rc;
-    const int n = std::min(std::max(*r->h_count, 0), NPc);
-    const uint8_t *base = r->fp16 ? s->data16 : s->data32;
-    int64_t cum = 0;
-    for (int i = 0; i < n; ++i) {
-      r->h_off[i] = cum;
-      cum += (int64_t)s->m(r->h_copies[i].y) * r->rec;
-    }
-    r->h_off[n] = cum;
-    if (cum > r->prm.staging_bytes) return fail(VM3DGS_E_CAPACITY, "copies exceed the staging buffer");
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int i = 0; i < n; ++i) {
-      const int4 c = r->h_copies[i];
-      const int64_t pb = (int64_t)s->m(c.y) * r->rec;
-      const int64_t lo = r->fp16 ? s->off16[c.y] : s->off32[c.y];
-      std::memcpy(r->staging + r->h_off[i], base + lo + (int64_t)c.x * pb, (size_t)pb);
-    }
-    int64_t *d_off = r->at<int64_t>(r->lay.staged_off);
-    if (!cuda_ok(cudaMemcpyAsync(d_off, r->h_off, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st), "copy", &rc))
-      return rc;
-    sa.staged_off = d_off;
-    cst = st;  // the staging buffer is refilled by the next update, after this stream's copies
+    sa.staged_off = r->h_off_dev;
+    cst = st;
   }
   if (cst == st) {
     const int sp = r->span_begin(VM3DGS_STAGE_STREAM, st);

@@ -62,7 +62,7 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
       clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
-      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, staged_off, total;
+      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, total;
   CtxLayout cx[kContexts];
 };
 
@@ -290,7 +290,9 @@ struct vm3dgs_renderer {
   uint8_t *staging = nullptr;           // page-locked, staging_bytes
   int32_t *h_count = nullptr;           // page-locked copy-list readback
   int4 *h_copies = nullptr;
-  int64_t *h_off = nullptr;             // page-locked byte offsets of the copies in staging
+  int64_t *h_off = nullptr;             // mapped page-locked byte offsets of the copies in staging
+  const int64_t *h_off_dev = nullptr;   // its device-visible pointer
+  int staged_err = 0;                   // set by the host gather, reported by the next update
   int state = 0;                        // 0 idle, 1 feedback done, 2 residency done
   float f_px = 0.0f;
   cudaEvent_t copy_done = nullptr;
