@@ -147,7 +147,7 @@ typedef struct {
   int64_t acc_prefetched_pages, acc_prefetched_bytes, acc_prefetch_hits;  /* hits: requested pages found resident
                                                                             because a prefetch brought them */
   int32_t staged_projection; /* 1: the projection stages records with tensor-map tile loads (every level block a
-                                multiple of 64 Gaussians); 0: it gathers them with plain loads */
+                                multiple of 32 Gaussians); 0: it gathers them with plain loads */
 } vm3dgs_stats;
 
 typedef struct {

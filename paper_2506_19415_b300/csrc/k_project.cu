@@ -111,19 +111,18 @@ struct GlobalSrc {
 };
 
 // The same attributes staged in shared memory: the record's float rows (A)
-// and half rows (B) of a chunk of kChunk Gaussians, row after row.
-constexpr int kChunk = 64;
-template <int K, bool F16>
+// and half rows (B) of a chunk of CH Gaussians, row after row.
+template <int K, bool F16, int CH>
 struct SharedSrc {
   const float *A;
   const __half *B;
   int g;
-  __device__ float half_at(int h) const { return __half2float(B[h * kChunk + g]); }
-  __device__ float pos(int a) const { return A[a * kChunk + g]; }
-  __device__ float opac() const { return A[(F16 ? 3 : 10) * kChunk + g]; }
-  __device__ float scale(int a) const { return F16 ? half_at(a) : A[(3 + a) * kChunk + g]; }
-  __device__ float rot(int a) const { return F16 ? half_at(3 + a) : A[(6 + a) * kChunk + g]; }
-  __device__ float sh(int k, int c) const { return F16 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * kChunk + g]; }
+  __device__ float half_at(int h) const { return __half2float(B[h * CH + g]); }
+  __device__ float pos(int a) const { return A[a * CH + g]; }
+  __device__ float opac() const { return A[(F16 ? 3 : 10) * CH + g]; }
+  __device__ float scale(int a) const { return F16 ? half_at(a) : A[(3 + a) * CH + g]; }
+  __device__ float rot(int a) const { return F16 ? half_at(3 + a) : A[(6 + a) * CH + g]; }
+  __device__ float sh(int k, int c) const { return F16 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * CH + g]; }
 };
 
 // Projects one Gaussian for one camera and writes splat record out.
@@ -348,23 +347,25 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
 // next item while the CTA projects the current one from shared memory (two
 // stages).  A wait that expires records VM3DGS_E_TIMEOUT and ends the CTA
 // after its copies in flight have landed.
-constexpr int kChunksPerCta = 2;
 constexpr int kMbarPolls = 1 << 20;
 
-template <int K, bool F16>
+// CH Gaussians per chunk (64 or 32), 128 / CH chunks per CTA of 128 threads
+template <int K, bool F16, int CH>
 struct TmaShape {
   static constexpr int NA = F16 ? 4 : 11 + 3 * K;                // float rows
   static constexpr int NH = F16 ? ((7 + 3 * K + 1) & ~1) : 0;    // half rows
-  static constexpr int ABYTES = NA * kChunk * 4, BBYTES = NH * kChunk * 2;
+  static constexpr int ABYTES = NA * CH * 4, BBYTES = NH * CH * 2;
   static constexpr int CHUNK = ABYTES + BBYTES;
-  static constexpr int STAGE = kChunksPerCta * CHUNK;
+  static constexpr int PER = 128 / CH;                            // chunks per CTA item
+  static constexpr int STAGE = PER * CHUNK;
   static constexpr int SMEM = 2 * STAGE + 64;                     // + barriers
 };
 
-template <int K, bool F16>
+template <int K, bool F16, int CH>
 __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_camera cam,
                                                           const __grid_constant__ ProjMaps maps) {
-  using S = TmaShape<K, F16>;
+  using S = TmaShape<K, F16, CH>;
+  constexpr int kChunk = CH, kChunksPerCta = S::PER;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
     const int64_t c = item * kChunksPerCta + ch;
     if (c < nchunks) {
       const uint8_t *buf = smem + stg * S::STAGE + ch * S::CHUNK;
-      const SharedSrc<K, F16> src{reinterpret_cast<const float *>(buf),
+      const SharedSrc<K, F16, CH> src{reinterpret_cast<const float *>(buf),
                                   reinterpret_cast<const __half *>(buf + S::ABYTES), g};
       project_one<K, F16>(a.sp, cam, src, c * kChunk + g);
     }
@@ -478,29 +479,26 @@ void launch_kb(const ProjectArgs &a, const ViewTable *views, int n_views, cudaSt
     project_batched_kernel<K, false><<<grid, 256, 0, st>>>(a, views);
 }
 
+template <int K, bool F16, int CH>
+void launch_tma(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
+  using S = TmaShape<K, F16, CH>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(project_tma_kernel<K, F16, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    prefer_shared((const void *)project_tma_kernel<K, F16, CH>);
+    attr = true;
+  }
+  project_tma_kernel<K, F16, CH>
+      <<<full_wave((const void *)project_tma_kernel<K, F16, CH>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
+}
+
 template <int K>
 void launch_k(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
   if (a.maps) {
-    static bool attr[2] = {false, false};
-    if (a.fp16) {
-      using S = TmaShape<K, true>;
-      if (!attr[1]) {
-        cudaFuncSetAttribute(project_tma_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-        prefer_shared((const void *)project_tma_kernel<K, true>);
-        attr[1] = true;
-      }
-      project_tma_kernel<K, true>
-          <<<full_wave((const void *)project_tma_kernel<K, true>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
-    } else {
-      using S = TmaShape<K, false>;
-      if (!attr[0]) {
-        cudaFuncSetAttribute(project_tma_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-        prefer_shared((const void *)project_tma_kernel<K, false>);
-        attr[0] = true;
-      }
-      project_tma_kernel<K, false>
-          <<<full_wave((const void *)project_tma_kernel<K, false>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
-    }
+    if (a.maps->chunk == 64)
+      a.fp16 ? launch_tma<K, true, 64>(a, cam, st) : launch_tma<K, false, 64>(a, cam, st);
+    else
+      a.fp16 ? launch_tma<K, true, 32>(a, cam, st) : launch_tma<K, false, 32>(a, cam, st);
     return;
   }
   int64_t blocks = (a.ncap + 255) / 256;
@@ -543,6 +541,15 @@ bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, boo
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   if (s->levels > kMaxLevels) return false;
+  // the widest chunk that divides every level block
+  int chunk = 64;
+  {
+    int64_t sub = 1;
+    for (int l = 0; l < s->levels; ++l, sub *= s->fanout)
+      if ((s->page_size / sub) % 64 != 0) chunk = 32;
+  }
+  const int kChunk = chunk;
+  out->chunk = chunk;
   const int K = s->K;
   const cuuint32_t NA = fp16 ? 4u : (cuuint32_t)(11 + 3 * K);
   const cuuint32_t NH = fp16 ? (cuuint32_t)((7 + 3 * K + 1) & ~1) : 0u;

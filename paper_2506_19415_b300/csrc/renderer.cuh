@@ -171,10 +171,12 @@ void launch_stream(const StreamArgs &a, cudaStream_t st);
 
 // Tensor maps of the pool, one per level: the record's float rows (a) and,
 // for fp16 pools, its half rows (b), each as (Gaussian of the level block,
-// row, level block of the whole pool), loaded 64 Gaussians at a time.
+// row, level block of the whole pool), loaded `chunk` Gaussians at a time
+// (64, or 32 when a level block holds 32 Gaussians).
 struct ProjMaps {
   CUtensorMap a[kMaxLevels];
   CUtensorMap b[kMaxLevels];
+  int32_t chunk;
 };
 struct ProjectArgs {
   const Ctl *ctl;   // the page table's control block (drawn count, draw list length)
@@ -189,7 +191,7 @@ struct ProjectArgs {
   const ProjMaps *maps;  // host copy; null: gather from the pool with plain loads
 };
 // Encodes the pool's tensor maps; false when a level block is not a multiple
-// of 64 Gaussians or the driver refuses (the projection then gathers).
+// of 32 Gaussians or the driver refuses (the projection then gathers).
 bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, bool fp16, ProjMaps *out);
 void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st);
 

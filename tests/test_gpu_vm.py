@@ -102,8 +102,8 @@ def test_city_lod_trajectory_fp16(v):
 @pytest.mark.parametrize("fp16", [False, True])
 def test_city_lod_trajectory_staged_projection(v, fp16):
     """Level blocks of 1024, 256 and 64 Gaussians: the projection stages the
-    records with tensor-map tile loads (fp32 and fp16 pools); the other
-    trajectories (blocks of 8 or 32) gather them with plain loads."""
+    records with tensor-map tile loads of 64 Gaussians (fp32 and fp16 pools);
+    scenes with a block of 8 gather them with plain loads."""
     raw, sc = city_scene(levels=3, fanout=4, page_size=1024)
     cams = [city_cam(160.0, k, width=200, height=120) for k in range(6)]
     r = _run_trajectory(v, raw, sc, cams, pool_slots=6, budget_pages=3, lod=True, tau0=1.0, fp16=fp16,
@@ -112,10 +112,20 @@ def test_city_lod_trajectory_staged_projection(v, fp16):
 
 
 def test_halving_lod_four_levels(v):
-    """The paper's own LOD shape: four levels, each halving the page."""
+    """The paper's own LOD shape: four levels, each halving the page (blocks
+    of 256, 128, 64 and 32 Gaussians: staged in tile loads of 32)."""
     raw, sc = city_scene(levels=4, fanout=2, page_size=256, n=30000)
     cams = [city_cam(160.0, k, width=160, height=96) for k in range(8)]
-    r = _run_trajectory(v, raw, sc, cams, pool_slots=10, budget_pages=4, lod=True, tau0=4.0)
+    r = _run_trajectory(v, raw, sc, cams, pool_slots=10, budget_pages=4, lod=True, tau0=4.0, check_images=(0, 7))
+    assert r.stats()["staged_projection"] == 1
+
+
+def test_gather_projection_for_blocks_of_eight(v):
+    """Level blocks of 512, 64 and 8 Gaussians: no tile width divides them
+    all, so the projection gathers with plain loads."""
+    raw, sc = city_scene(levels=3, fanout=8, page_size=512)
+    cams = [city_cam(160.0, k, width=160, height=96) for k in range(4)]
+    r = _run_trajectory(v, raw, sc, cams, pool_slots=8, budget_pages=4, lod=True, tau0=2.0, check_images=(3,))
     assert r.stats()["staged_projection"] == 0
 
 
