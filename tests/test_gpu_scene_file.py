@@ -62,3 +62,24 @@ def test_mapped_scene_frames_equal_in_memory(v, tmp_path, fp16):
             np.testing.assert_array_equal(pa[e, s_ * len(blk):(s_ + 1) * len(blk)], blk)
             np.testing.assert_array_equal(pb[e, s_ * len(blk):(s_ + 1) * len(blk)], blk)
     assert streamed > 8   # pages were replaced, not only loaded once
+
+
+def test_prefetch_refused_on_a_file_backed_renderer(v, tmp_path):
+    """The prefetcher pulls pages from page-locked scene memory, which a
+    scene opened from a file does not have: the call returns E_STATE."""
+    raw = scenegen.city_scene(n=20000, n_boxes=8, extent=100.0)
+    sc = v.vm3dgs_build_pages(raw, v.BuildConfig(page_size=512, paging="octree", lod_levels=1, lo=(-4, -4, -4),
+                                                   hi=(104, 104, 84), voxel=4.0, kappa=0.5, link_samples=2))
+    path = tmp_path / "city.vm3dgs"
+    sc.save(path)
+    op = v.vm3dgs_scene_open(path)
+    cam = city_cam(100.0, 0, width=160, height=96)
+    r = v.Renderer(op, v.RenderConfig(max_width=160, max_height=96, staging_bytes=4 * 512 * sc.info.record_bytes),
+                   pool_slots=8)
+    r.render_feedback([cam])
+    r.update_residency()
+    O = 256
+    p = v.Prefetcher(v.MlpShape(n_in=12 + O // 16, n_hidden=64, n_out=O, max_batch=8, seed=1, lr=0.0))
+    with pytest.raises(v.Vm3dgsError) as e:
+        v.vm3dgs_prefetch(r, p, cam, cam, 0.0)
+    assert e.value.code == v.E_STATE
