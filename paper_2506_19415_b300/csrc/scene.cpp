@@ -89,6 +89,18 @@ struct FileHeader {
   int64_t data32_at, data16_at, file_bytes;
 };
 int64_t align4k(int64_t x) { return (x + 4095) / 4096 * 4096; }
+// pread until `bytes` have arrived (one call returns at most about 2 GB)
+bool pread_all(int fd, void *dst, int64_t bytes, int64_t at) {
+  auto *p = static_cast<uint8_t *>(dst);
+  while (bytes > 0) {
+    const ssize_t got = pread(fd, p, (size_t)std::min<int64_t>(bytes, int64_t(1) << 30), (off_t)at);
+    if (got <= 0) return false;
+    p += got;
+    at += got;
+    bytes -= got;
+  }
+  return true;
+}
 }  // namespace
 
 extern "C" int vm3dgs_scene_save(const vm3dgs_scene *s, const char *path) {
@@ -141,7 +153,7 @@ extern "C" int vm3dgs_scene_open(const char *path, vm3dgs_scene **out) {
   if (fd < 0) return vm::fail(VM3DGS_E_INVAL, std::string("cannot open ") + path);
   struct stat sb{};
   FileHeader h{};
-  const bool head = fstat(fd, &sb) == 0 && pread(fd, &h, sizeof h, 0) == (ssize_t)sizeof h;
+  const bool head = fstat(fd, &sb) == 0 && pread_all(fd, &h, (int64_t)sizeof h, 0);
   auto bad = [&](const char *why) {
     ::close(fd);
     return vm::fail(VM3DGS_E_INVAL, std::string("not a scene file (") + why + "): " + path);
@@ -169,7 +181,7 @@ extern "C" int vm3dgs_scene_open(const char *path, vm3dgs_scene **out) {
   auto get = [&](auto &vec, int64_t n) {
     vec.resize((size_t)n);
     const int64_t bytes = n * (int64_t)sizeof(vec[0]);
-    if (ok && bytes > 0) ok = pread(fd, vec.data(), (size_t)bytes, at) == (ssize_t)bytes;
+    if (ok && bytes > 0) ok = pread_all(fd, vec.data(), bytes, at);
     at += bytes;
   };
   get(S->count, h.n_count);
