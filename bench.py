@@ -85,48 +85,55 @@ def workload(name):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons sampled through NVML every `period` s
+    in a background thread while it runs, plus one sample at start and one
+    at stop, so even a timed region of a few milliseconds has samples."""
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4), ("hw_power_brake_slowdown", 0x80))
 
-    def __init__(self, index):
-        self.index, self.rows, self.proc = index, [], None
+    def __init__(self, index, period=0.002):
+        self.index, self.period, self.rows, self.h, self.t = index, period, [], None, None
+        self.stop_flag = threading.Event()
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+        except Exception as e:  # noqa: BLE001 (no NVML: reported in the line)
+            self.err = str(e)
+
+    def _sample(self):
+        nv = self.nv
+        sm = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
+        mx = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+        get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self.rows.append((sm, mx, int(get(self.h))))
+
+    def _loop(self):
+        while not self.stop_flag.wait(self.period):
+            self._sample()
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+        if self.h is None:
+            return
+        self.rows = []
+        self.stop_flag.clear()
+        self._sample()
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        rows = [r for r in self.rows if len(r) >= 8]
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return None
-        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
-        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        if self.h is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["NVML unavailable: " + self.err], "samples": 0}
+        self.stop_flag.set()
+        self.t.join()
+        self._sample()
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({name for r in self.rows for name, bit in self.REASONS if r[2] & bit})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
+                "sm_mhz_min": min(sm), "reasons": reasons, "samples": len(self.rows),
+                "how": "NVML every %.0f ms during the timed frames" % (1e3 * self.period)}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -210,8 +217,14 @@ def train_prefetcher(v, scene, W, width, height, n_paths=16, frames=60, steps=60
 PREFETCH_EVERY = 4   # frames between prefetch steps (the network predicts the next 15 frames' pages)
 
 
+# Frames of the walk rendered untimed before an arm's warm-up frames, so that
+# the timed frames see the warm pool of a running walk (the cold fill of the
+# first frame is reported separately under "quality").
+PREROLL = 60
+
+
 def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False, dist=None, pf=None, pf_thr=0.0,
-            serial=False):
+            serial=False, clocks=None, preroll=0):
     import torch
     dev = torch.device("cuda")
     st = torch.cuda.current_stream()
@@ -255,7 +268,7 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
                 hosts[b].copy_(images[b], non_blocking=True)
             copied[b].record(d2h)
 
-    for i in range(warmup):
+    for i in range(preroll + warmup):
         frame(i)
     torch.cuda.synchronize()
     r.reset_sums(st)
@@ -266,9 +279,11 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks is not None:
+        clocks.start()
     t_wall = time.perf_counter()
     e0.record(st)
-    for i in range(warmup, warmup + steps):
+    for i in range(preroll + warmup, preroll + warmup + steps):
         frame(i)
     issue = time.perf_counter() - t_wall  # host time to enqueue the frames
     if e2e:
@@ -279,6 +294,7 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     e1.record(st)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    clk = clocks.stop() if clocks is not None else None
     if dist is not None:
         dist.barrier()
     ms = e0.elapsed_time(e1)
@@ -286,7 +302,7 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     if timing:
         r.timing(False)
     stats = r.stats(st)
-    return dict(ms=ms, wall=wall, issue=issue, stage=stage, stats=stats)
+    return dict(ms=ms, wall=wall, issue=issue, stage=stage, stats=stats, clocks=clk)
 
 
 # DRAM bytes per onesweep pass per sorted pair, from the ncu capture summarised
@@ -470,7 +486,8 @@ def gpu_main(args):
     K = (scene.info.sh_degree + 1) ** 2
     # plain arm
     rp = make_renderer(v, scene, W, False, width, height)
-    plain = run_arm(v, rp, cams, args.warmup, args.steps, None, dist=dist)
+    plain = run_arm(v, rp, cams, args.warmup, args.steps, None, dist=dist, preroll=PREROLL,
+                    clocks=ClockSampler(torch.cuda.current_device()))
     del rp
     torch.cuda.empty_cache()
     # headline arm: fp16 pool, copies on a copy stream, learned prefetch
@@ -479,29 +496,28 @@ def gpu_main(args):
         pf, pf_info = train_prefetcher(v, scene, W, width, height)
     rh = make_renderer(v, scene, W, True, width, height)
     copy_stream = torch.cuda.Stream()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, dist=dist, pf=pf)
+    head = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, dist=dist, pf=pf, preroll=PREROLL,
+                   clocks=ClockSampler(torch.cuda.current_device()))
     # the same frames with every call on one stream: per-kernel CUDA-event
     # times without the other streams' kernels sharing the GPU, for the roofline
     ser = run_arm(v, rh, cams, args.warmup, min(args.steps, 100), copy_stream, timing=True, dist=dist, pf=pf,
-                  serial=True)
-    clk = clocks.stop()
+                  serial=True, preroll=PREROLL)
+    clk = head["clocks"]
     # end to end through the public API: the rendered image returns to pinned host memory every frame
-    e2e = run_arm(v, rh, cams, 0, args.steps, copy_stream, e2e=True, dist=dist, pf=pf)
+    e2e = run_arm(v, rh, cams, args.warmup, args.steps, copy_stream, e2e=True, dist=dist, pf=pf, preroll=PREROLL)
     # same fp16 arm without the prefetcher, for its misses and copy stall
     nopf = None
     if pf is not None:
         rn = make_renderer(v, scene, W, True, width, height)
         nopf = run_arm(v, rn, cams, args.warmup, min(args.steps, 100), copy_stream, timing=True, dist=dist,
-                       serial=True)
+                       serial=True, preroll=PREROLL)
         del rn
     # fp16 pool with the fp32 arm's slot count (equal pages, half the bytes), no prefetcher
     eq = None
     if W["pool_bytes"] is not None:
         slots32 = W["pool_bytes"] // v.vm3dgs_pool_slot_bytes(scene, fp16_pool=False)
         rq = make_renderer(v, scene, W, True, width, height, pool_slots=slots32)
-        eq = run_arm(v, rq, cams, args.warmup, args.steps, copy_stream, dist=dist)
+        eq = run_arm(v, rq, cams, args.warmup, args.steps, copy_stream, dist=dist, preroll=PREROLL)
         eq["slots"] = int(slots32)
         del rq
     torch.cuda.empty_cache()
@@ -523,6 +539,8 @@ def gpu_main(args):
         "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
         "value": round(fps, 2),
         "unit": "frames/s",
+        "plain_vm_value": round(fps_plain, 2),
+        "speedup_vs_plain_vm": round(fps / fps_plain, 4),
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -538,9 +556,12 @@ def gpu_main(args):
                    "pool_bytes": W["pool_bytes"], "staging_bytes": 40 * 2048 * 236,
                    "l2": "per-frame inputs (2 GiB pool, splat and pair buffers) exceed the 126 MB L2",
                    "arm": "fp16 pool + copy stream + learned prefetch", "parallelism": "replicas, one renderer per GPU",
+                   "timed_frames": [PREROLL + args.warmup, PREROLL + args.warmup + args.steps],
+                   "preroll": "frames 0..%d of the walk rendered untimed before the warm-up frames (warm pool)"
+                              % (PREROLL - 1),
                    "streams": "page determination and page-table update on their own streams, consecutive renders on two streams (two render contexts), event-ordered"},
         "plain_vm": {"value": round(fps_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain / args.steps, 4),
-                     "arm": "fp32 pool, in-line copies",
+                     "arm": "fp32 pool, in-line copies", "clocks": plain["clocks"],
                      "missing_per_frame": plain["stats"]["acc_missing"] / max(plain["stats"]["acc_frames"], 1)},
         "per_frame": {"missing": hs["acc_missing"] / frames, "requested": hs["acc_requested"] / frames,
                       "drawn_gaussians": hs["acc_drawn_gaussians"] / frames, "pairs": hs["acc_pairs"] / frames,
@@ -577,7 +598,8 @@ def gpu_main(args):
     if not args.no_prefetch and world == 1:
         line["prefetch_c4"] = prefetch_eval(v)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, W, quick=True)
+        line["cpu_baseline"], sample = cpu_baseline(args, W, keep=True)
+        line.setdefault("quality", {})["vs_fp64_oracle"] = quality_vs_oracle(v, W, sample)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -585,10 +607,21 @@ def gpu_main(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm
+STAGING = 40 * 2048 * 236   # the paper's staging buffer (about 18.4 MiB)
+
+
+def rec_bytes16(K):
+    """Bytes per Gaussian of the fp16 pool record (position and opacity in
+    float, scale, rotation and SH in half, padded to an even half count)."""
+    return 16 + 2 * (((7 + 3 * K) + 1) & ~1)
+
+
 def cpu_sample(W, n_frames):
     """Bounded sample of the workload for the oracle: the same generator and
     density on a small patch (city) or the same scene (others), same camera
-    model and resolution; returns (oracle scene, page table, cameras)."""
+    model and resolution, and a page table kept as the headline arm keeps it
+    (fp16 records, the pool scaled to the patch, the paper's staging budget).
+    Returns (raw, build params, oracle scene, page table, cameras, slots)."""
     import scenegen
     from oracle import build as ob
     from oracle import residency as rs
@@ -605,28 +638,82 @@ def cpu_sample(W, n_frames):
         cams = W["path"](max(n_frames, 1))[:n_frames]
         pool_bytes = W["pool_bytes"]
     sc = ob.build_scene(raw, ob.BuildParams(**b, seed=77))
-    rec = 4 * (11 + 3 * (raw.sh_degree + 1) ** 2)
+    rec = rec_bytes16((raw.sh_degree + 1) ** 2)
     P = sc.n_pages if pool_bytes is None else max(1, pool_bytes // (sc.params.page_size * rec))
     pt = rs.PageTable(rs.ResidencyParams(n_entries=P, page_size=sc.params.page_size, levels=len(sc.levels),
-                                         fanout=sc.params.lod_fanout, record_bytes=rec,
-                                         budget_bytes=40 * 2048 * 236, lod=W["lod"]))
-    return sc, pt, cams
+                                         fanout=sc.params.lod_fanout, record_bytes=rec, budget_bytes=STAGING,
+                                         lod=W["lod"]))
+    return raw, b, sc, pt, cams, P
 
 
-def cpu_baseline(args, W, quick=False, steps=None):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(args, W, n_frames=20, keep=False):
+    """The oracle, as it stands, timed on all host cores (OpenMP over the
+    Gaussians of the projection, the tiles of the blend and the triangles of
+    the feedback raster; the page table and the rest in single-threaded
+    Python) over n_frames consecutive frames of the bounded sample.  With
+    keep, also returns what the GPU quality check needs."""
     import oracle
-    n = 2 if quick else max(1, steps or 1)
-    sc, pt, cams = cpu_sample(W, n)
-    t0 = time.perf_counter()
-    for c in cams[:n]:
-        oracle.frame(sc, pt, c, ds=4, links=True)
-    dt = time.perf_counter() - t0
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    raw, b, sc, pt, cams, P = cpu_sample(W, n_frames)
+    outs = []
+    try:
+        t0 = time.perf_counter()
+        for c in cams[:n_frames]:
+            o = oracle.frame(sc, pt, c, ds=4, links=True)
+            if keep:
+                outs.append({"image": o["render"]["image"], "draw": o["update"]["draw"]})
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
     s = W["sample"]
-    desc = ("%d oracle frames of the full per-frame path at %dx%d on %s" %
-            (n, cams[0].width, cams[0].height,
+    desc = ("%d consecutive oracle frames of the full per-frame path at %dx%d on %s, page table of %d fp16 slots" %
+            (n_frames, cams[0].width, cams[0].height,
              ("a %.0f m x %.0f m patch of the city at the same density (%d Gaussians, %d boxes)" %
-              (s["extent"], s["extent"], s["n"], s["n_boxes"])) if s else "the same scene"))
-    return {"value": round(n / dt, 5), "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": desc}
+              (s["extent"], s["extent"], s["n"], s["n_boxes"])) if s else "the same scene", P))
+    res = {"value": round(n_frames / dt, 5), "unit": "frames/s", "cores": threads, "kind": "oracle",
+           "sample": desc, "nproc": os.cpu_count(), "cpu": cpu_model(), "seconds": round(dt, 2)}
+    return (res, (raw, b, cams[:n_frames], P, outs)) if keep else res
+
+
+def quality_vs_oracle(v, W, sample):
+    """PSNR of the GPU fp16 pool's images against the FP64 oracle's renders
+    of the fp32 scene, on the frames of the CPU-baseline sample (same scene,
+    built by the library from the same raw input; same page-table size and
+    budget, so the same pages are drawn, which is checked too)."""
+    import torch
+    raw, b, cams, P, outs = sample
+    scene = v.vm3dgs_build_pages(raw, v.BuildConfig(**b, fp16=True, seed=77))
+    cfg = v.RenderConfig(staging_bytes=STAGING, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=True,
+                         max_width=cams[0].width, max_height=cams[0].height, tau0=1.0, step0=0.1)
+    r = v.Renderer(scene, cfg, pool_slots=P)
+    img = torch.empty((3, cams[0].height, cams[0].width), dtype=torch.float32, device="cuda")
+    psnr, same = [], 0
+    for c, o in zip(cams, outs):
+        r.render_feedback([c])
+        r.update_residency()
+        r.render([c], [img])
+        g = img.clamp(0.0, 1.0).double().cpu().numpy()
+        mse = float(np.mean((g - np.clip(o["image"], 0.0, 1.0)) ** 2))
+        psnr.append(round(10.0 * math.log10(1.0 / max(mse, 1e-30)), 2))
+        draw = r.debug(v.DBG_DRAW, np.int32).reshape(-1, 4)
+        same += int(np.array_equal(draw, np.asarray(o["draw"], np.int32).reshape(-1, 4)))
+    st = r.stats()
+    del r, scene
+    torch.cuda.empty_cache()
+    return {"psnr_fp16_vs_fp64_oracle_db": psnr, "min_psnr_db": min(psnr), "frames": len(psnr),
+            "draw_lists_equal": "%d of %d" % (same, len(psnr)), "status": st["status"],
+            "note": "GPU fp16 pool (FP32 math) against the oracle's FP64 render of the fp32 attributes of the same "
+                    "drawn pages; images clamped to [0, 1]; the frames of cpu_baseline.sample"}
 
 
 def reference_main(args):
@@ -634,7 +721,7 @@ def reference_main(args):
     if rank != 0:
         return
     W = workload(args.config)
-    cb = cpu_baseline(args, W, steps=args.steps)
+    cb = cpu_baseline(args, W, n_frames=max(1, args.steps))
     line = {"impl": "reference", "metric": "1080p frames/s on 50M-Gaussian scene, plain VM vs FP16+prefetch, PSNR>=45dB",
             "value": cb["value"], "unit": "frames/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",

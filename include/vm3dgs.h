@@ -320,8 +320,11 @@ enum {
   VM3DGS_DBG_RASTER = 20,    /* uint32 [5] of the last feedback view: triangles queued for a warp, triangles left
                                 in front of the near plane by the frustum test, huge triangles queued, their bands
                                 of 4 rows, triangles crossing the near plane */
-  VM3DGS_DBG_SPLAT_TMASK = 21 /* uint64 [N] tiles of the rectangle (row-major bits) met by the 3-sigma ellipse,
-                                all ones when the rectangle has more than 64 tiles, 0 if culled */
+  VM3DGS_DBG_SPLAT_TMASK = 21, /* uint64 [N] the splat's tiles (those of its rectangle whose box of pixel centres
+                                meets its 3-sigma ellipse, by the row rule of Sec. 4.2's tiled rendering reading) as
+                                row-major bits of a rectangle of at most 64 tiles; 0 for larger rectangles and culled
+                                splats */
+  VM3DGS_DBG_SPLAT_TOUCHED = 22 /* uint32 [N] number of the splat's tiles (0 if culled) */
 };
 int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *host_dst, int64_t bytes, int64_t *needed, void *stream);
 
@@ -411,17 +414,22 @@ int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const vm3dgs_camer
  *
  * Sorts n (key, value) pairs in place, stably, by the low key_bits bits of the
  * keys (the renderer's onesweep radix sort), enqueued on stream.  keys_dev and
- * vals_dev are the caller's device arrays (input and output).  All scratch is
+ * vals_dev are the caller's device arrays (input and output; they may be null
+ * when n is 0).  Bits above key_bits are kept but do not order.  All scratch is
  * a fixed array inside the library (about 8.4 MB, held on every device that
  * loads the library until the process exits); n above
  * VM3DGS_NOALLOC_MAX_PAIRS is rejected with VM3DGS_E_CAPACITY before any
- * work.  The first call on a device looks up the array's device address (do
- * it once before time-critical use).  Every call shares the array and the
+ * work.  Every call looks up the array's device address in the current
+ * context (a host-side lookup once the library's module is loaded there; the
+ * first call on a device loads it, so make that first call before any stream
+ * capture and before time-critical use).  Every call shares the array and the
  * array keeps the last call's contents (each call clears what must start at
- * zero); calls that overlap on one device race.  If status_dev is not null it
- * receives 0, or VM3DGS_E_TIMEOUT if a bounded wait of the sort gave up (the
- * output is then not sorted).  Calls no cudaMalloc, cudaFree or allocating
- * library routine. */
+ * zero); calls that overlap on one device race.  A CUDA error left pending by
+ * earlier work is reported as VM3DGS_E_CUDA before anything is enqueued (and
+ * is not cleared).  If status_dev is not null it receives 0, VM3DGS_E_TIMEOUT
+ * if a bounded wait of the sort gave up (the output is then not sorted), or
+ * VM3DGS_E_CUDA if the call failed after enqueueing its first kernel.  Calls
+ * no cudaMalloc, cudaFree or allocating library routine. */
 #define VM3DGS_NOALLOC_MAX_PAIRS (1 << 19)
 int vm3dgs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, int64_t n, int32_t key_bits,
                               int32_t *status_dev, void *stream);

@@ -14,7 +14,9 @@ Layout
 
 The C files are compiled with gcc -O2 -ffp-contract=off -fno-fast-math, so
 every float32 operation of a discrete decision is a single correctly rounded
-IEEE operation, in the written order.
+IEEE operation, in the written order.  Their per-Gaussian, per-tile and
+per-triangle loops may run on several OpenMP threads (set_threads; one by
+default): the iterations are independent, so the results are the same.
 
 Parity pins (tests/test_oracle_*.py) tie every function to something other
 than itself: closed-form images, finite differences, quadrature, brute force,
@@ -41,8 +43,8 @@ def compile_oracle(force=False):
     newest = max(os.path.getmtime(s) for s in _SRCS)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", *_SRCS,
-                               "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+                               *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -56,6 +58,8 @@ def lib():
         _lib.vo_compact.restype = ctypes.c_int
         _lib.vo_float_bits.restype = ctypes.c_uint32
         _lib.vo_float_bits.argtypes = [ctypes.c_float]
+        _lib.vo_tile_kept.restype = ctypes.c_int
+        _lib.vo_set_threads(1)
     return _lib
 
 
@@ -83,20 +87,50 @@ def _c(a, dt):
 
 
 # --------------------------------------------------------------------------- render
-def project(g, cam):
-    """g: dict pos[n,3] scale[n,3] rot[n,4] opacity[n] sh[n,K,3] (fp32)."""
+def project(g, cam, rect_binning=False):
+    """g: dict pos[n,3] scale[n,3] rot[n,4] opacity[n] sh[n,K,3] (fp32).
+    ctr32/con32 are the FP32 centre and conic the tile rule reads;
+    rect_binning keeps every tile of a splat's rectangle instead."""
     n = len(g["opacity"])
     K = g["sh"].shape[1]
     pos, scale, rot = _c(g["pos"], np.float32), _c(g["scale"], np.float32), _c(g["rot"], np.float32)
     op, sh = _c(g["opacity"], np.float32), _c(g["sh"], np.float32)
     out = dict(vis=np.zeros(n, np.uint8), radius=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
-               depth=np.zeros(n, np.float32), touched=np.zeros(n, np.int32), tmask=np.zeros(n, np.uint64),
-               centre=np.zeros((n, 2)), conic=np.zeros((n, 3)), rgb=np.zeros((n, 3)))
+               depth=np.zeros(n, np.float32), touched=np.zeros(n, np.int32), ctr32=np.zeros((n, 2), np.float32),
+               con32=np.zeros((n, 3), np.float32), centre=np.zeros((n, 2)), conic=np.zeros((n, 3)),
+               rgb=np.zeros((n, 3)), rect_binning=bool(rect_binning))
     c = vo_camera(cam)
     lib().vo_project(ctypes.c_int64(n), _p(pos), _p(scale), _p(rot), _p(op), _p(sh), ctypes.c_int(K), ctypes.byref(c),
                      _p(out["vis"]), _p(out["radius"]), _p(out["rect"]), _p(out["depth"]), _p(out["touched"]),
-                     _p(out["tmask"]), _p(out["centre"]), _p(out["conic"]), _p(out["rgb"]))
+                     _p(out["ctr32"]), _p(out["con32"]), ctypes.c_int(1 if rect_binning else 0), _p(out["centre"]),
+                     _p(out["conic"]), _p(out["rgb"]))
     return out
+
+
+def tile_kept(pr, i, cam, tx, ty):
+    """Is tile (tx, ty) of its rectangle one of splat i's tiles (the row rule
+    of the tile binning, FP32 spec)?"""
+    c = vo_camera(cam)
+    u, w = pr["ctr32"][i], pr["con32"][i]
+    return bool(lib().vo_tile_kept(ctypes.c_float(u[0]), ctypes.c_float(u[1]), ctypes.c_float(w[0]),
+                                   ctypes.c_float(w[1]), ctypes.c_float(w[2]), ctypes.byref(c), ctypes.c_int(int(tx)),
+                                   ctypes.c_int(int(ty))))
+
+
+def splat_tiles(pr, i, cam):
+    """Tiles (tx, ty) of splat i in row-major order."""
+    if not pr["vis"][i]:
+        return []
+    x0, y0, x1, y1 = (int(t) for t in pr["rect"][i])
+    return [(tx, ty) for ty in range(y0, y1) for tx in range(x0, x1)
+            if pr["rect_binning"] or tile_kept(pr, i, cam, tx, ty)]
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's C loops (results do not depend on it);
+    returns the count now in effect."""
+    lib().vo_set_threads(int(n))
+    return int(lib().vo_max_threads())
 
 
 def grid_dims(cam):
@@ -104,15 +138,15 @@ def grid_dims(cam):
 
 
 def bin_sort(pr, vid, cam):
-    gx, gy = grid_dims(cam)
     M = int(pr["touched"][pr["vis"] != 0].astype(np.int64).sum())
     keys = np.zeros(max(M, 1), np.uint64)
     idx = np.zeros(max(M, 1), np.int64)
     vid = _c(vid, np.int64)
-    m = lib().vo_bin_sort(ctypes.c_int64(len(vid)), _p(pr["vis"]), _p(pr["rect"]), _p(pr["touched"]),
-                          _p(pr["tmask"]), _p(pr["depth"]), _p(vid), ctypes.c_int(gx), _p(keys), _p(idx),
-                          ctypes.c_int64(len(keys)))
-    assert m == M
+    c = vo_camera(cam)
+    m = lib().vo_bin_sort(ctypes.c_int64(len(vid)), _p(pr["vis"]), _p(pr["rect"]), _p(pr["touched"]), _p(pr["ctr32"]),
+                          _p(pr["con32"]), ctypes.c_int(1 if pr["rect_binning"] else 0), _p(pr["depth"]), _p(vid),
+                          ctypes.byref(c), _p(keys), _p(idx), ctypes.c_int64(len(keys)))
+    assert m == M, (m, M)
     return keys[:M], idx[:M]
 
 
@@ -134,9 +168,9 @@ def blend(cam, rng, idx, pr, opacity, bg=(0.0, 0.0, 0.0)):
     return img, flag, nc
 
 
-def render(g, vid, cam, bg=(0.0, 0.0, 0.0)):
+def render(g, vid, cam, bg=(0.0, 0.0, 0.0), rect_binning=False):
     """Full splat pipeline over the given Gaussians (vid = virtual ids for ties)."""
-    pr = project(g, cam)
+    pr = project(g, cam, rect_binning)
     keys, idx = bin_sort(pr, vid, cam)
     rng = ranges(keys, cam)
     img, flag, nc = blend(cam, rng, idx, pr, g["opacity"], bg)

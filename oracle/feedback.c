@@ -62,6 +62,14 @@ static v3 to_cam(const float *V, const float *p) {
   return r;
 }
 
+/* *dst = min(*dst, key), atomically: triangles may be rasterised by several
+ * threads at once, and a minimum does not depend on their order */
+static void min_store(uint64_t *dst, uint64_t key) {
+  uint64_t cur = __atomic_load_n(dst, __ATOMIC_RELAXED);
+  while (key < cur && !__atomic_compare_exchange_n(dst, &cur, key, 1, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+  }
+}
+
 /* edge a->b owns pixels exactly on it when it points up, or right when flat */
 static int owns(int64_t dx, int64_t dy) { return dy < 0 || (dy == 0 && dx > 0); }
 
@@ -120,21 +128,23 @@ static void raster_tri(const v3 *c, uint32_t page1, float fxf, float fyf, float 
       float s = ((float)E[0] * w0 + (float)E[1] * w1) + (float)E[2] * w2;
       float zp = farea / s;
       uint64_t key = ((uint64_t)fbits(zp) << 32) | page1;
-      uint64_t *dst = buf + j * Wf + i;
-      if (key < *dst) *dst = key;
+      min_store(buf + j * Wf + i, key);
     }
 }
 
 /*
  * Rasterises n_tris proxy triangles (vertex indices tris[3t..3t+2] into
  * verts[3v..3v+2], page face_page[t], -1 = none) into buf[Hf][Wf], which the
- * caller fills with all ones beforehand.
+ * caller fills with all ones beforehand.  Triangles are independent (the
+ * per-pixel minimum is order-free), so they may run on several OpenMP threads
+ * (vo_set_threads); one thread by default.
  */
 void vo_feedback_raster(int64_t n_tris, const float *verts, const int32_t *tris, const int32_t *face_page,
                         const vo_camera *cam, int ds, uint64_t *buf) {
   const int Wf = (cam->width + ds - 1) / ds, Hf = (cam->height + ds - 1) / ds;
   const float fds = (float)ds;
   const float fxf = cam->fx / fds, fyf = cam->fy / fds, cxf = cam->cx / fds, cyf = cam->cy / fds;
+#pragma omp parallel for schedule(dynamic, 4096)
   for (int64_t t = 0; t < n_tris; ++t) {
     v3 c[3];
     for (int k = 0; k < 3; ++k) c[k] = to_cam(cam->view, verts + 3 * (int64_t)tris[3 * t + k]);

@@ -22,15 +22,31 @@
  * Tie order of the sort: (tile, depth bits, virtual Gaussian id), the id
  * being page * page_size + slot of the level the page is drawn at.
  *
- * Tiles of a splat.  The 3-sigma rectangle bounds the circle of radius r
- * around the centre; of a rectangle of at most 64 tiles, a splat covers only
- * the tiles whose pixel centres' bounding box meets its 3-sigma ellipse
- * d^T conic d <= 9 (conic in FP32 as above; the minimum of the quadratic over
- * the box is taken on its edges, each a clamped one-dimensional minimum, in
- * the order written in meets()).  Larger rectangles keep all their tiles.
- * The kept tiles are a 64-bit mask over the rectangle in row-major order.
+ * Tiles of a splat (binning is left to the 3DGS renderer; this is a reading).
+ * A splat is binned to the tiles of its rectangle whose box of pixel centres
+ * meets its 3-sigma ellipse E = {d : ia dx^2 + 2 ib dx dy + ic dy^2 <= 9}
+ * (d = pixel - centre, the FP32 conic), for rectangles of any size.  The test
+ * is taken one tile row at a time, since a convex region cut by the row's
+ * band of pixel-centre y values is an x-interval:
+ *   D   = ia ic - ib^2 (the conic's determinant; if it is not positive the
+ *         splat keeps every tile of its rectangle)
+ *   ey  = sqrt(9 ia / D)           half the y-extent of E
+ *   dys = -3 ib / sqrt(ic D)       dy of E's rightmost point (-dys: leftmost)
+ *   band [l, h] = [yl - pv, yh - pv] clipped to [-ey, ey]; empty: no tile
+ *   X1 = x_hi(clamp(dys, l, h)),  X0 = x_lo(clamp(-dys, l, h)), where
+ *   x_hi/lo(t) = (-ib t +/- sqrt(max(0, 9 ia - D t^2))) / ia
+ *         are E's right and left boundary at height t (x_hi is concave and
+ *         peaks at dys, x_lo convex with its minimum at -dys, so X0 and X1
+ *         bound E within the band)
+ *   a tile column is kept when xl - pu <= X1 and xh - pu >= X0
+ * ([xl, xh] x [yl, yh] is the tile's box of pixel centres).  Every operation
+ * is one FP32 operation in the order written in tile_kept().  The kept tiles
+ * of a row are contiguous.  With rect_binning the splat keeps every tile of
+ * its rectangle instead (the 3DGS reference renderer's binning), for
+ * measuring what the ellipse test changes.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -46,30 +62,35 @@ typedef struct {
 
 static uint32_t fbits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 
-/* Does the box [xl, xh] x [yl, yh] (pixel centres) meet the ellipse
- * q(d) = ia dx^2 + 2 ib dx dy + ic dy^2 <= 9 around (pu, pv)?  FP32 spec;
- * ria = 1/ia and ric = 1/ic give the stationary points of the edges. */
-static int meets(float pu, float pv, float ia, float ib, float ic, float ria, float ric, float xl, float xh, float yl,
-                 float yh) {
-  const float dxl = xl - pu, dxh = xh - pu, dyl = yl - pv, dyh = yh - pv;
-  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return 1;
-  const float b2 = 2.0f * ib;
-  float best = 3.0e38f;
-  for (int k = 0; k < 2; ++k) { /* edges dx = e, dy in [dyl, dyh] */
-    const float e = k ? dxh : dxl;
-    float t = -(ib * e) * ric;
-    t = t < dyl ? dyl : (t > dyh ? dyh : t);
-    const float f = ((ia * e) * e + (b2 * e) * t) + (ic * t) * t;
-    if (f < best) best = f;
-  }
-  for (int k = 0; k < 2; ++k) { /* edges dy = e, dx in [dxl, dxh] */
-    const float e = k ? dyh : dyl;
-    float t = -(ib * e) * ria;
-    t = t < dxl ? dxl : (t > dxh ? dxh : t);
-    const float f = ((ia * t) * t + (b2 * t) * e) + (ic * e) * e;
-    if (f < best) best = f;
-  }
-  return best <= 9.0f;
+/* Is tile (tx, ty) one of the splat's?  The row rule stated above, FP32
+ * spec; (pu, pv) is the FP32 centre and (ia, ib, ic) the FP32 conic. */
+static int tile_kept(float pu, float pv, float ia, float ib, float ic, const vo_camera *cam, int tx, int ty) {
+  const float D = ia * ic - ib * ib;
+  if (!(D > 0.0f)) return 1;
+  const float ey = sqrtf((9.0f * ia) / D);
+  const float dys = -(3.0f * ib) / sqrtf(ic * D);
+  const int py1 = (ty + 1) * cam->tile_h < cam->height ? (ty + 1) * cam->tile_h : cam->height;
+  const int px1 = (tx + 1) * cam->tile_w < cam->width ? (tx + 1) * cam->tile_w : cam->width;
+  const float yl = (float)(ty * cam->tile_h) + 0.5f, yh = (float)py1 - 0.5f;
+  const float xl = (float)(tx * cam->tile_w) + 0.5f, xh = (float)px1 - 0.5f;
+  const float l = fmaxf(yl - pv, -ey), h = fminf(yh - pv, ey);
+  if (l > h) return 0;
+  const float t1 = fminf(fmaxf(dys, l), h), t0 = fminf(fmaxf(-dys, l), h);
+  const float s1 = sqrtf(fmaxf(0.0f, 9.0f * ia - D * (t1 * t1)));
+  const float s0 = sqrtf(fmaxf(0.0f, 9.0f * ia - D * (t0 * t0)));
+  const float X1 = (-(ib * t1) + s1) / ia;
+  const float X0 = (-(ib * t0) - s0) / ia;
+  return (xl - pu) <= X1 && (xh - pu) >= X0;
+}
+
+/* Threads of the OpenMP loops of the oracle (projection per Gaussian, blend
+ * per tile, feedback raster per triangle: independent iterations, so the
+ * results do not depend on the count).  One thread unless set. */
+void vo_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int vo_max_threads(void) { return omp_get_max_threads(); }
+
+int vo_tile_kept(float pu, float pv, float ia, float ib, float ic, const vo_camera *cam, int tx, int ty) {
+  return tile_kept(pu, pv, ia, ib, ic, cam, tx, ty);
 }
 
 /* real spherical harmonics up to degree 3, constants from their definition
@@ -113,13 +134,16 @@ void vo_sh_basis(int64_t n, const double *dirs, double *out) {
  */
 void vo_project(int64_t n, const float *pos, const float *scale, const float *rot, const float *opac,
                 const float *sh, int K, const vo_camera *cam, uint8_t *vis, float *radius, int32_t *rect,
-                float *depth, int32_t *touched, uint64_t *tmask, double *centre, double *conic, double *rgb) {
+                float *depth, int32_t *touched, float *ctr32, float *con32, int rect_binning, double *centre,
+                double *conic, double *rgb) {
   const float *V = cam->view;
   const int gx = (cam->width + cam->tile_w - 1) / cam->tile_w;
   const int gy = (cam->height + cam->tile_h - 1) / cam->tile_h;
   const float TW = (float)cam->tile_w, TH = (float)cam->tile_h;
+#pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t i = 0; i < n; ++i) {
-    vis[i] = 0; radius[i] = 0; touched[i] = 0; depth[i] = 0; tmask[i] = 0;
+    vis[i] = 0; radius[i] = 0; touched[i] = 0; depth[i] = 0;
+    ctr32[2 * i] = ctr32[2 * i + 1] = 0; con32[3 * i] = con32[3 * i + 1] = con32[3 * i + 2] = 0;
     rect[4 * i + 0] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
     const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     const float o = opac[i];
@@ -188,25 +212,12 @@ void vo_project(int64_t n, const float *pos, const float *scale, const float *ro
     /* ---- fp32 spec: conic and the tiles the 3-sigma ellipse meets */
     {
       const float ia = c / det, ib = -b / det, ic = a / det;
-      const float ria = 1.0f / ia, ric = 1.0f / ic;
-      const int area = (x1 - x0) * (y1 - y0);
-      if (area <= 64) {
-        uint64_t mask = 0;
-        int bit = 0, cnt = 0;
-        for (int ty = y0; ty < y1; ++ty)
-          for (int tx = x0; tx < x1; ++tx, ++bit) {
-            const int px1 = (tx + 1) * cam->tile_w < cam->width ? (tx + 1) * cam->tile_w : cam->width;
-            const int py1 = (ty + 1) * cam->tile_h < cam->height ? (ty + 1) * cam->tile_h : cam->height;
-            const float xl = (float)(tx * cam->tile_w) + 0.5f, xh = (float)px1 - 0.5f;
-            const float yl = (float)(ty * cam->tile_h) + 0.5f, yh = (float)py1 - 0.5f;
-            if (meets(pu, pv, ia, ib, ic, ria, ric, xl, xh, yl, yh)) { mask |= 1ull << bit; ++cnt; }
-          }
-        tmask[i] = mask;
-        touched[i] = cnt;
-      } else {
-        tmask[i] = ~0ull;
-        touched[i] = area;
-      }
+      ctr32[2 * i] = pu; ctr32[2 * i + 1] = pv;
+      con32[3 * i] = ia; con32[3 * i + 1] = ib; con32[3 * i + 2] = ic;
+      int cnt = 0;
+      for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx) cnt += rect_binning || tile_kept(pu, pv, ia, ib, ic, cam, tx, ty);
+      touched[i] = cnt;
     }
 
     /* ---- fp64: continuous outputs */
@@ -271,12 +282,13 @@ static int cmp_pair(const void *pa, const void *pb) {
   return 0;
 }
 
-/* Emits one (tile << 32 | depth bits) key per (visible splat, covered tile
- * of its rectangle) and sorts by (key, virtual id).  Returns the number of pairs, or
- * -needed when cap is too small. */
-int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const int32_t *touched,
-                    const uint64_t *tmask, const float *depth, const int64_t *vid, int gx, uint64_t *keys_out,
-                    int64_t *idx_out, int64_t cap) {
+/* Emits one (tile << 32 | depth bits) key per (visible splat, kept tile of
+ * its rectangle, row-major) and sorts by (key, virtual id).  Returns the number
+ * of pairs, or -needed when cap is too small. */
+int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const int32_t *touched, const float *ctr32,
+                    const float *con32, int rect_binning, const float *depth, const int64_t *vid,
+                    const vo_camera *cam, uint64_t *keys_out, int64_t *idx_out, int64_t cap) {
+  const int gx = (cam->width + cam->tile_w - 1) / cam->tile_w;
   int64_t M = 0;
   for (int64_t i = 0; i < n; ++i)
     if (vis[i]) M += touched[i];
@@ -285,11 +297,12 @@ int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const in
   int64_t k = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (!vis[i]) continue;
-    const int w = rect[4 * i + 2] - rect[4 * i], h = rect[4 * i + 3] - rect[4 * i + 1];
-    int bit = 0;
     for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ++ty)
-      for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx, ++bit) {
-        if (w * h <= 64 && !((tmask[i] >> bit) & 1u)) continue;
+      for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; ++tx) {
+        if (!rect_binning && !tile_kept(ctr32[2 * i], ctr32[2 * i + 1], con32[3 * i], con32[3 * i + 1],
+                                        con32[3 * i + 2], cam, tx, ty))
+          continue;
+        if (k == M) { free(p); return -(M + 1); } /* touched disagrees with the rule */
         uint64_t tile = (uint64_t)ty * gx + tx;
         p[k].key = (tile << 32) | fbits(depth[i]);
         p[k].vid = vid[i];
@@ -300,7 +313,7 @@ int64_t vo_bin_sort(int64_t n, const uint8_t *vis, const int32_t *rect, const in
   qsort(p, M, sizeof(vo_pair), cmp_pair);
   for (int64_t j = 0; j < M; ++j) { keys_out[j] = p[j].key; idx_out[j] = p[j].idx; }
   free(p);
-  return M;
+  return k == M ? M : -(M + 1);
 }
 
 /* [start, end) of every tile in the sorted key list */
@@ -327,6 +340,7 @@ void vo_blend(const vo_camera *cam, const int64_t *ranges, const int64_t *idx, c
               uint8_t *flag, int32_t *n_contrib) {
   const int W = cam->width, H = cam->height, TW = cam->tile_w, TH = cam->tile_h;
   const int gx = (W + TW - 1) / TW, gy = (H + TH - 1) / TH;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
   for (int ty = 0; ty < gy; ++ty)
     for (int tx = 0; tx < gx; ++tx) {
       const int64_t s = ranges[2 * (ty * gx + tx)], e = ranges[2 * (ty * gx + tx) + 1];

@@ -142,7 +142,7 @@ SCENE_PAGE_COUNT, SCENE_PAGE_SRC, SCENE_PAGES, SCENE_PAGES16, SCENE_ERR, SCENE_V
     SCENE_FACE_PAGE, SCENE_LINK_PTR, SCENE_LINK_COL = range(10)
 (DBG_FEEDBACK, DBG_REQ, DBG_DIRECT, DBG_REQUESTS, DBG_PT_LOD, DBG_PT_LAST, DBG_PT_SLOT, DBG_COPIES, DBG_DRAW,
  DBG_MISSING, DBG_SPLAT_RECT, DBG_SPLAT_DEPTH, DBG_SPLAT_RADIUS, DBG_KEYS, DBG_VALUES, DBG_RANGES, DBG_SPLAT_XY,
- DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK) = range(22)
+ DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK, DBG_SPLAT_TOUCHED) = range(23)
 
 
 STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend", "prefetch", "sort_prep")
@@ -596,7 +596,23 @@ NOALLOC_MAX_PAIRS = 1 << 19
 def vm3dgs_sort_pairs_noalloc(keys, vals, n, key_bits, status=None, stream=None):
     """Stable in-place sort of device tensors keys (uint64 as int64) / vals
     (int32) by the low key_bits bits, with the library's fixed scratch (no
-    allocation).  status: optional 1-element int32 device tensor."""
+    allocation).  status: optional 1-element int32 device tensor.  The
+    tensors are checked here (device, layout, dtype, size), since the C ABI
+    sees only their addresses."""
+    import torch
+
+    def _dev(t, dts, need, what):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype in dts):
+            raise Vm3dgsError(E_INVAL, "%s must be a contiguous CUDA tensor of dtype %s" % (what, dts))
+        if t.numel() < need:
+            raise Vm3dgsError(E_INVAL, "%s holds %d elements, fewer than %d" % (what, t.numel(), need))
+
+    n = int(n)
+    if 0 <= n <= NOALLOC_MAX_PAIRS:
+        _dev(keys, (torch.int64, torch.uint64), n, "keys")
+        _dev(vals, (torch.int32, torch.uint32), n, "vals")
+    if status is not None:
+        _dev(status, (torch.int32,), 1, "status")
     _check(_lib.vm3dgs_sort_pairs_noalloc(c_p(keys.data_ptr()), c_p(vals.data_ptr()), int(n), int(key_bits),
                                           c_p(status.data_ptr()) if status is not None else None,
                                           _stream_ptr(stream)))

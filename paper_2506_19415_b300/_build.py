@@ -20,7 +20,7 @@ CU = ["k_project.cu", "k_feedback.cu", "k_residency.cu", "k_stream.cu", "k_sort.
       "k_mlp.cu", "prefetcher.cu", "k_prefetch.cu",
       "sort_noalloc.cu", "batch.cu"]
 CPP = ["build_pages.cpp", "scene.cpp"]
-HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh", "block_sel.cuh", "tma.cuh"]
+HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh", "block_sel.cuh", "tma.cuh", "coverage.cuh"]
 
 
 def _newer(src_list, target):

@@ -86,7 +86,8 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   uint32_t *vals[2] = {r->at<uint32_t>(C.vals0), r->at<uint32_t>(C.vals1)};
   span = timed ? r->span_begin(VM3DGS_STAGE_SCAN_EMIT, st) : -1;
   launch_scan_emit_batched(ctl, sp, r->dims.ncap, n, dvt, r->at<uint32_t>(C.block_sums),
-                           r->at<uint32_t>(C.offsets), keys[0], vals[0], r->dims.pair_cap, st);
+                           r->at<uint32_t>(C.offsets), keys[0], vals[0], r->dims.pair_cap,
+                           r->at<uint64_t>(C.pieces), r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, st);
   r->span_end(span, 4, st);
   const int ntiles = t.tile_off[n];
   int tbits = 0;

@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include "coverage.cuh"
 #include "renderer.cuh"
 #include "tma.cuh"
 
@@ -66,36 +67,6 @@ struct Rec {
 #define SHC3C 0.4570457994644658f
 #define SHC3D 0.3731763325901154f
 #define SHC3E 1.445305721320277f
-
-// Does the box [xl, xh] x [yl, yh] (a tile's pixel centres) meet the ellipse
-// ia dx^2 + 2 ib dx dy + ic dy^2 <= 9 around (pu, pv)?  Inside the box the
-// answer is yes; otherwise the quadratic's minimum over the box lies on an
-// edge, where it is a clamped one-dimensional minimum (ria = 1/ia and
-// ric = 1/ic give the stationary points).
-__device__ __forceinline__ bool meets_ellipse(float pu, float pv, float ia, float ib, float ic, float ria, float ric,
-                                              float xl, float xh, float yl, float yh) {
-  const float dxl = xl - pu, dxh = xh - pu, dyl = yl - pv, dyh = yh - pv;
-  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return true;
-  const float b2 = 2.0f * ib;
-  float best = 3.0e38f;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {  // edges dx = e
-    const float e = k ? dxh : dxl;
-    float t = -(ib * e) * ric;
-    t = t < dyl ? dyl : (t > dyh ? dyh : t);
-    const float f = ((ia * e) * e + (b2 * e) * t) + (ic * t) * t;
-    if (f < best) best = f;
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {  // edges dy = e
-    const float e = k ? dyh : dyl;
-    float t = -(ib * e) * ria;
-    t = t < dxl ? dxl : (t > dxh ? dxh : t);
-    const float f = ((ia * t) * t + (b2 * t) * e) + (ic * e) * e;
-    if (f < best) best = f;
-  }
-  return best <= 9.0f;
-}
 
 // Attributes of Gaussian g of a level block of m Gaussians in the pool.
 template <int K, bool F16>
@@ -211,26 +182,20 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
     return;
   }
   float ia = cc / det, ib = -cb / det, ic = ca / det;
-  // tiles of the rectangle met by the 3-sigma ellipse (all of a rectangle of
-  // more than 64 tiles)
-  const int area = (x1 - x0) * (y1 - y0);
-  uint64_t tmask = ~0ull;
-  int covered = area;
-  if (area <= 64) {
-    const float ria = 1.0f / ia, ric = 1.0f / ic;
-    tmask = 0;
-    covered = 0;
-    int bit = 0;
-    for (int ty = y0; ty < y1; ++ty)
-      for (int tx = x0; tx < x1; ++tx, ++bit) {
-        const int px1 = min((tx + 1) * cam.tile_w, cam.width), py1 = min((ty + 1) * cam.tile_h, cam.height);
-        const float xl = (float)(tx * cam.tile_w) + 0.5f, xh = (float)px1 - 0.5f;
-        const float yl = (float)(ty * cam.tile_h) + 0.5f, yh = (float)py1 - 0.5f;
-        if (meets_ellipse(pu, pv, ia, ib, ic, ria, ric, xl, xh, yl, yh)) {
-          tmask |= 1ull << bit;
-          ++covered;
-        }
-      }
+  // tiles of the rectangle met by the 3-sigma ellipse, counted row by row;
+  // a rectangle of at most 64 tiles also keeps them as a row-major mask
+  const SplatEllipse el = splat_ellipse(pu, pv, ia, ib, ic);
+  const TileGeom tg{cam.width, cam.height, cam.tile_w, cam.tile_h};
+  const int rw = x1 - x0;
+  const bool small_rect = rw * (y1 - y0) <= 64;
+  uint64_t tmask = 0;
+  int covered = 0;
+  for (int ty = y0; ty < y1; ++ty) {
+    const int2 sp2 = row_span(el, ty, x0, x1, tg);
+    const int n = sp2.y - sp2.x;
+    if (n <= 0) continue;
+    covered += n;
+    if (small_rect) tmask |= (n >= 64 ? ~0ull : ((1ull << n) - 1ull)) << ((ty - y0) * rw + (sp2.x - x0));
   }
   // continuous outputs
   float dx = x - cam.campos[0], dy = y - cam.campos[1], dz = z - cam.campos[2];

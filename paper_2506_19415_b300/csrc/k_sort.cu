@@ -17,6 +17,10 @@
 //   ranges        [first, last+1) of every tile in the sorted keys.
 // Stability plus ascending emission order gives the order (tile, depth,
 // drawn index), and the drawn index ascends with the virtual Gaussian id.
+#include <mutex>
+#include <unordered_set>
+
+#include "coverage.cuh"
 #include "renderer.cuh"
 
 namespace vm {
@@ -124,30 +128,46 @@ __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *c
   }
 }
 
-// Last index i in [0, N) with offsets[i] <= j (offsets ascending from 0),
-// found by the whole warp: each round probes 32 evenly spaced entries and
-// keeps the span between the last probe at or below j and the next one.
-__device__ __forceinline__ int64_t warp_find(const uint32_t *offsets, int64_t N, uint32_t j, int lane) {
-  int64_t lo = 0, hi = N;
-  while (hi - lo > 32) {
-    const int64_t step = (hi - lo + 31) / 32;
-    const int64_t p = lo + lane * step;
-    const bool ok = p < hi && offsets[p] <= j;
-    const uint32_t b = __ballot_sync(0xffffffffu, ok);
-    const int last = 31 - __clz(b);
-    lo += last * step;
-    hi = min(hi, lo + step);
-  }
-  const int64_t p = lo + lane;
-  const uint32_t b = __ballot_sync(0xffffffffu, p < hi && offsets[p] <= j);
-  return lo + (31 - __clz(b));
-}
-
-// Rectangle position (row-major) of the q-th covered tile of a splat.
-__device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t w, uint32_t h, uint32_t q) {
-  if (w * h > 64) return q;
+// Rectangle position (row-major) of the q-th covered tile of a splat whose
+// rectangle has at most 64 tiles (m: its tile mask).
+__device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t q) {
   const uint32_t lo = (uint32_t)m, c = __popc(lo);
   return q < c ? __fns(lo, 0, (int)q + 1) : 32u + __fns((uint32_t)(m >> 32), 0, (int)(q - c) + 1);
+}
+
+// Where a splat's pairs go: its view's image and tile size, the view's first
+// global tile and its tiles per row.  One view (vt null): g and gx; a batch:
+// splat record i belongs to view i / nv of the device table.
+struct EmitViews {
+  const ViewTable *vt;
+  TileGeom g;
+  int gx;
+  __device__ __forceinline__ void of(int64_t i, int64_t nv, TileGeom &tg, int &tgx, int &toff) const {
+    if (!vt) {
+      tg = g;
+      tgx = gx;
+      toff = 0;
+      return;
+    }
+    const int v = (int)(i / nv);
+    const vm3dgs_camera &c = vt->cam[v];
+    tg = TileGeom{c.width, c.height, c.tile_w, c.tile_h};
+    tgx = vt->gx[v];
+    toff = vt->tile_off[v];
+  }
+};
+
+// (tx, ty) of the q-th pair of a splat whose rectangle has more than 64
+// tiles, walking its rows with the tile rule (one lane)
+__device__ __forceinline__ int2 nth_tile_by_rows(const SplatEllipse &el, uint32_t q, int x0, int x1, int y0, int y1,
+                                                 const TileGeom &tg) {
+  for (int ty = y0; ty < y1; ++ty) {
+    const int2 sp2 = row_span(el, ty, x0, x1, tg);
+    const uint32_t n = sp2.y > sp2.x ? (uint32_t)(sp2.y - sp2.x) : 0u;
+    if (q < n) return make_int2(sp2.x + (int)q, ty);
+    q -= n;
+  }
+  return make_int2(x0, y0);  // not reached while the count agrees with the rule
 }
 
 // adds n to the depth-field digits 0 .. dpass-1 of the shifted key kd
@@ -214,21 +234,23 @@ __device__ __forceinline__ void hist_flush(const SortHist &sh, uint32_t (*hs)[25
 constexpr uint32_t kSmallSplat = 32;  // pairs a splat may have to be dealt out with others
 constexpr uint32_t kPiece = 256;      // pairs per piece of a larger splat
 
-// Pair emission (pairs of a splat: its covered tiles in row-major order, at
-// its scanned offset), part 1: a warp takes 32 consecutive splats, a lane
-// each, with coalesced loads of their records.  The pairs of the splats with
-// at most 32 of them are dealt out to the lanes together (lane g of a round
+// Pair emission (pairs of a splat: its kept tiles in row-major order, at its
+// scanned offset), part 1: a warp takes 32 consecutive splats, a lane each,
+// with coalesced loads of their records.  The pairs of the splats with at
+// most 32 of them are dealt out to the lanes together (lane g of a round
 // writes pair g of the concatenation, its splat found by a binary search over
 // the lanes' inclusive counts and its record fetched by shuffles), so stores
-// are contiguous and no lane walks the offsets.  Larger splats are cut into
-// pieces of kPiece pairs, listed for part 2.  Digits that lie in the depth
-// field are the same for all pairs of a splat and are counted once per
-// splat.  With sh.hist the kernel also counts the sort's digits
-// (shared-memory histograms merged into sh.hist) and clears the sort's
-// look-back words and tile counters.
-__global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, const uint32_t *offsets,
-                                                   uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
-                                                   KeyFormat kf, SortHist sh, uint64_t *pieces,
+// are contiguous and no lane walks the offsets; a pair's tile comes from the
+// splat's tile mask, or, for a rectangle of more than 64 tiles, from a walk
+// over its rows with the tile rule.  Larger splats are cut into pieces of
+// kPiece pairs, listed for part 2.  Digits that lie in the depth field are
+// the same for all pairs of a splat and are counted once per splat.  With
+// sh.hist the kernel also counts the sort's digits (shared-memory histograms
+// merged into sh.hist) and clears the sort's look-back words and tile
+// counters.  A batch (ev.vt) emits the records of all its views.
+__global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, int views, EmitViews ev,
+                                                   const uint32_t *offsets, uint64_t *keys, uint32_t *vals,
+                                                   int64_t pair_cap, KeyFormat kf, SortHist sh, uint64_t *pieces,
                                                    uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges, int ntiles) {
   __shared__ uint32_t hs[kMaxPasses][256];
   if (sh.hist) {
@@ -236,7 +258,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     __syncthreads();
   }
   const PairOut po = pair_out(ctl, keys, vals, pair_cap, kf, sh, hs);
-  const int64_t N = n_drawn(ctl, ncap);
+  const int64_t Nv = n_drawn(ctl, ncap);
+  const int64_t N = Nv * views;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -298,10 +321,26 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
       const uint64_t Ltm = __shfl_sync(0xffffffffu, tm, L), Ld = __shfl_sync(0xffffffffu, dkey, L);
       const uint32_t Loff = __shfl_sync(0xffffffffu, off, L);
       if (g < total) {
+        const int64_t si = b + L;
         const uint32_t q = g - (Li - Ln);
-        const uint32_t x0 = Lrx & 0xFFFFu, w = (Lrx >> 16) - x0, y0 = Lry & 0xFFFFu, h = (Lry >> 16) - y0;
-        const uint32_t qt = covered_tile(Ltm, w, h, q);
-        po.put((int64_t)Loff + q, (y0 + qt / w) * (uint32_t)gx + x0 + qt % w, Ld, (uint32_t)(b + L));
+        const int x0 = (int)(Lrx & 0xFFFFu), x1 = (int)(Lrx >> 16), y0 = (int)(Lry & 0xFFFFu), y1 = (int)(Lry >> 16);
+        const int w = x1 - x0;
+        TileGeom tg;
+        int tgx, toff;
+        ev.of(si, Nv, tg, tgx, toff);
+        int tx, ty;
+        if (w * (y1 - y0) <= 64) {
+          const uint32_t qt = covered_tile(Ltm, q);
+          tx = x0 + (int)(qt % (uint32_t)w);
+          ty = y0 + (int)(qt / (uint32_t)w);
+        } else {
+          const float4 s0 = sp.s0[si];
+          const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.s1[si].x);
+          const int2 t = nth_tile_by_rows(el, q, x0, x1, y0, y1, tg);
+          tx = t.x;
+          ty = t.y;
+        }
+        po.put((int64_t)Loff + q, (uint32_t)(toff + ty * tgx + tx), Ld, (uint32_t)si);
       }
     }
     // larger splats: their pieces to the list (one reservation per warp)
@@ -340,16 +379,22 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
 }
 
 // Pair emission, part 2: a warp per piece of kPiece pairs of a larger splat.
-__global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats sp, const uint32_t *offsets,
-                                                          uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx,
-                                                          KeyFormat kf, SortHist sh, const uint64_t *pieces,
-                                                          const uint32_t *piece_ctr, int64_t piece_cap) {
+// A rectangle of at most 64 tiles reads its tile mask; a larger one is walked
+// 32 rows at a time (a lane per row computes the row's run of kept columns,
+// a warp scan gives the rows' first pairs, and each pair of the piece in
+// those rows finds its row by a binary search over the scan).
+__global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats sp, int64_t ncap, EmitViews ev,
+                                                          const uint32_t *offsets, uint64_t *keys, uint32_t *vals,
+                                                          int64_t pair_cap, KeyFormat kf, SortHist sh,
+                                                          const uint64_t *pieces, const uint32_t *piece_ctr,
+                                                          int64_t piece_cap) {
   __shared__ uint32_t hs[kMaxPasses][256];
   if (sh.hist) {
     for (int i = threadIdx.x; i < sh.passes * 256; i += blockDim.x) (&hs[0][0])[i] = 0;
     __syncthreads();
   }
   const PairOut po = pair_out(ctl, keys, vals, pair_cap, kf, sh, hs);
+  const int64_t Nv = n_drawn(ctl, ncap);
   const int64_t n = min((int64_t)*piece_ctr, piece_cap);
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -360,63 +405,64 @@ __global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats
     const uint32_t k = (uint32_t)e;
     const uint32_t cnt = sp.touched[i], off = offsets[i];
     const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-    const uint64_t tm = sp.tmask[i], dkey = depth_key(sp.depth[i], kf);
+    const uint64_t dkey = depth_key(sp.depth[i], kf);
     if (po.hist && k == 0 && lane == 0) count_run(hs, dkey >> po.lo_bit, po.dpass, cnt);
-    const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
-    const uint32_t q1 = min(cnt, (k + 1) * kPiece);
-    for (uint32_t q = k * kPiece + lane; q < q1; q += 32) {
-      const uint32_t qt = covered_tile(tm, w, h, q);
-      po.put((int64_t)off + q, (y0 + qt / w) * (uint32_t)gx + x0 + qt % w, dkey, (uint32_t)i);
+    const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16), y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+    const int w = x1 - x0;
+    TileGeom tg;
+    int tgx, toff;
+    ev.of(i, Nv, tg, tgx, toff);
+    const uint32_t qa = k * kPiece, qb = min(cnt, qa + kPiece);
+    if (w * (y1 - y0) <= 64) {
+      const uint64_t tm = sp.tmask[i];
+      for (uint32_t q = qa + lane; q < qb; q += 32) {
+        const uint32_t qt = covered_tile(tm, q);
+        po.put((int64_t)off + q, (uint32_t)(toff + (y0 + (int)(qt / (uint32_t)w)) * tgx + x0 + (int)(qt % (uint32_t)w)),
+               dkey, (uint32_t)i);
+      }
+      continue;
+    }
+    const float4 s0 = sp.s0[i];
+    const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.s1[i].x);
+    uint32_t base = 0;  // pairs in the rows before this group of 32
+    for (int r0 = y0; r0 < y1 && base < qb; r0 += 32) {
+      const int ty = r0 + lane;
+      const int2 sp2 = ty < y1 ? row_span(el, ty, x0, x1, tg) : make_int2(0, 0);
+      const uint32_t nr = sp2.y > sp2.x ? (uint32_t)(sp2.y - sp2.x) : 0u;
+      uint32_t incl = nr;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+      }
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t lo = max(qa, base), hi = min(qb, base + tot);
+      for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
+        const uint32_t q = g0 + (uint32_t)lane, rel = q - base;
+        // row: the number of rows whose inclusive count is <= rel
+        int L = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1) {
+          const uint32_t v = __shfl_sync(0xffffffffu, incl, L + st - 1);
+          if (v <= rel) L += st;
+        }
+        L = min(L, 31);
+        const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Ln = __shfl_sync(0xffffffffu, nr, L);
+        const int Lc0 = __shfl_sync(0xffffffffu, sp2.x, L);
+        if (q < hi) po.put((int64_t)off + q, (uint32_t)(toff + (r0 + L) * tgx + Lc0 + (int)(rel - (Li - Ln))), dkey,
+                           (uint32_t)i);
+      }
+      base += tot;
     }
   }
   if (sh.hist) hist_flush(sh, hs);
 }
 
-constexpr int kEmitChunk = 256;  // pairs per warp task of the batched emission
-
-// Pairs of all views of a batch: splat record v * N + i belongs to view v;
-// the key's tile field is the view's first global tile plus its local tile.
-__global__ void __launch_bounds__(256) emit_batched_kernel(const Ctl *ctl, Splats sp, int64_t ncap, int views,
-                                                           const ViewTable *vt, const uint32_t *offsets,
-                                                           uint64_t *keys, uint32_t *vals, int64_t pair_cap) {
-  const int64_t Nv = n_drawn(ctl, ncap);
-  const int64_t N = Nv * views;
-  int64_t M = ctl->pairs;
-  if (M > pair_cap) M = pair_cap;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp0; c * kEmitChunk < M; c += nwarps) {
-    const uint32_t j0 = (uint32_t)(c * kEmitChunk);
-    int64_t i = warp_find(offsets, N, j0, lane);  // last splat with offset <= j0
-    for (int k = 0; k < kEmitChunk / 32; ++k) {
-      const uint32_t j = j0 + 32u * k + lane;
-      if ((int64_t)j >= M) break;
-      if (i + 1 < N && offsets[i + 1] <= j) {
-        int64_t lo2 = i + 1, step = 1;
-        while (lo2 + step < N && offsets[lo2 + step] <= j) { lo2 += step; step <<= 1; }
-        int64_t hi2 = lo2 + step < N ? lo2 + step - 1 : N - 1;
-        while (lo2 < hi2) {
-          const int64_t mid = (lo2 + hi2 + 1) >> 1;
-          if (offsets[mid] <= j) lo2 = mid; else hi2 = mid - 1;
-        }
-        i = lo2;
-      }
-      const int v = (int)(i / Nv);
-      const uint32_t rx = sp.rect[2 * i], ry = sp.rect[2 * i + 1];
-      const uint32_t x0 = rx & 0xFFFFu, w = (rx >> 16) - x0, y0 = ry & 0xFFFFu, h = (ry >> 16) - y0;
-      const uint32_t q = covered_tile(sp.tmask[i], w, h, j - offsets[i]);
-      const uint32_t tile = (uint32_t)vt->tile_off[v] + (y0 + q / w) * (uint32_t)vt->gx[v] + x0 + q % w;
-      keys[j] = ((uint64_t)tile << 32) | sp.depth[i];
-      vals[j] = (uint32_t)i;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ onesweep
+// (the last pass's digit holds the bits left below hi_bit: last_mask)
 __global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, int lo_bit,
-                                                        int passes, uint32_t *hist, uint32_t *lookback,
-                                                        int64_t max_tiles, uint32_t *tile_ctr) {
+                                                        int passes, uint32_t last_mask, uint32_t *hist,
+                                                        uint32_t *lookback, int64_t max_tiles, uint32_t *tile_ctr) {
   __shared__ uint32_t h[kMaxPasses][256];
   const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -424,7 +470,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const ui
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
     const uint64_t k = keys[j] >> lo_bit;
-    for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(k >> (8 * d)) & 255u], 1u);
+    for (int d = 0; d < passes; ++d) atomicAdd(&h[d][(k >> (8 * d)) & (d == passes - 1 ? last_mask : 255u)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
@@ -453,8 +499,8 @@ static_assert(kSortThreads == 256, "onesweep assumes one thread per 8-bit digit"
 template <bool VALS>
 __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, const uint64_t *kin, const uint32_t *vin,
                                                                 uint64_t *kout, uint32_t *vout, int64_t cap, int shift,
-                                                                const uint32_t *counts, uint32_t *status,
-                                                                uint32_t *tile_ctr) {
+                                                                uint32_t dmask, const uint32_t *counts,
+                                                                uint32_t *status, uint32_t *tile_ctr) {
   constexpr int W = kSortThreads / 32;
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
@@ -501,7 +547,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       const bool valid = idx < M;
       k[it] = valid ? kin[idx] : 0ull;
       v[it] = (VALS && valid) ? vin[idx] : 0u;
-      dg[it] = valid ? (int)((k[it] >> shift) & 255u) : -1;
+      dg[it] = valid ? (int)((k[it] >> shift) & dmask) : -1;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
@@ -586,7 +632,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
     const int nvalid = (int)((M - t0) < kSortTile ? (M - t0) : kSortTile);
     for (int i = tid; i < nvalid; i += kSortThreads) {
       const uint64_t key = s_keys[i];
-      const int d = (int)((key >> shift) & 255u);
+      const int d = (int)((key >> shift) & dmask);
       const uint32_t o = s_glob[d] + (uint32_t)i - s_doff[d];
       if ((int64_t)o < M) {  // always true unless a look-back wait timed out
         kout[o] = key;
@@ -613,9 +659,9 @@ __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap,
 }  // namespace
 
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
-                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges,
-                      int ntiles, cudaStream_t st) {
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, const TileGeom &tg, int gx,
+                      const KeyFormat &kf, const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr,
+                      int64_t piece_cap, uint2 *ranges, int ntiles, cudaStream_t st) {
   const int64_t nb = (ncap + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs);
@@ -623,23 +669,32 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
   scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl_w, ncap, 1, bs, sh.hist, sh.hist ? kMaxPasses * 256 : 0, piece_ctr,
                                                  1);
   scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, 1, bs, offsets);
-  emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, offsets, keys, vals, pair_cap,
-                                                                            gx, kf, sh, pieces, piece_ctr, piece_cap,
-                                                                            ranges, ntiles);
+  const EmitViews ev{nullptr, tg, gx};
+  emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, 1, ev, offsets, keys, vals,
+                                                                            pair_cap, kf, sh, pieces, piece_ctr,
+                                                                            piece_cap, ranges, ntiles);
   emit_pieces_kernel<<<full_wave((const void *)emit_pieces_kernel, 256, 0), 256, 0, st>>>(
-      ctl, sp, offsets, keys, vals, pair_cap, gx, kf, sh, pieces, piece_ctr, piece_cap);
+      ctl, sp, ncap, ev, offsets, keys, vals, pair_cap, kf, sh, pieces, piece_ctr, piece_cap);
 }
 
 void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
                               uint32_t *block_sums, uint32_t *offsets, uint64_t *keys, uint32_t *vals,
-                              int64_t pair_cap, cudaStream_t st) {
+                              int64_t pair_cap, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap,
+                              cudaStream_t st) {
   const int64_t nb = (ncap * views + kScanItems - 1) / kScanItems;
   uint64_t *bs = reinterpret_cast<uint64_t *>(block_sums);
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs);
-  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl, ncap, views, bs, nullptr, 0, nullptr, 0);
+  scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(ctl, ncap, views, bs, nullptr, 0, piece_ctr, 1);
   scan_offsets_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(ctl, sp.touched, ncap, views, bs, offsets);
-  emit_batched_kernel<<<full_wave((const void *)emit_batched_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, views, vt,
-                                                                                            offsets, keys, vals, pair_cap);
+  // keys (global tile << 32 | depth bits) with the record index as value
+  const KeyFormat kf{32, 0, 32, 0u, false};
+  const SortHist none{};
+  const EmitViews ev{vt, TileGeom{0, 0, 1, 1}, 0};
+  emit_kernel<<<full_wave((const void *)emit_kernel, 256, 0), 256, 0, st>>>(ctl, sp, ncap, views, ev, offsets, keys,
+                                                                            vals, pair_cap, kf, none, pieces, piece_ctr,
+                                                                            piece_cap, nullptr, 0);
+  emit_pieces_kernel<<<full_wave((const void *)emit_pieces_kernel, 256, 0), 256, 0, st>>>(
+      ctl, sp, ncap, ev, offsets, keys, vals, pair_cap, kf, none, pieces, piece_ctr, piece_cap);
 }
 
 int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bit, int hi_bit, uint32_t *hist,
@@ -649,9 +704,9 @@ int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bi
   const int64_t max_tiles = (pair_cap + kSortTile - 1) / kSortTile;
   if ((int64_t)passes * max_tiles * 256 > lookback_words) return -1;
   cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kMaxPasses * 256, st);
-  sort_hist_kernel<<<full_wave((const void *)sort_hist_kernel, 256, 0), 256, 0, st>>>(ctl, keys, pair_cap, lo_bit,
-                                                                                      passes, hist, lookback, max_tiles,
-                                                                                      tile_ctr);
+  const int last_bits = hi_bit - lo_bit - 8 * (passes - 1);
+  sort_hist_kernel<<<full_wave((const void *)sort_hist_kernel, 256, 0), 256, 0, st>>>(
+      ctl, keys, pair_cap, lo_bit, passes, (1u << last_bits) - 1u, hist, lookback, max_tiles, tile_ctr);
   return 0;
 }
 
@@ -659,29 +714,39 @@ int launch_sort_passes(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t p
                        uint32_t *hist, uint32_t *lookback, uint32_t *tile_ctr, cudaStream_t st) {
   const int passes = (hi_bit - lo_bit + 7) / 8;
   if (passes < 1 || passes > kMaxPasses || lo_bit < 0) return -1;
-  static bool attr_set = false;
   const int smem = kSortTile * 12 + (kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return -2;
-    prefer_shared((const void *)onesweep_kernel<true>);
-    prefer_shared((const void *)onesweep_kernel<false>);
-    attr_set = true;
+  {
+    // kernel attributes belong to a device: set them once on each
+    static std::mutex mu;
+    static std::unordered_set<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.count(dev)) {
+      if (cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+          cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -2;
+      prefer_shared((const void *)onesweep_kernel<true>);
+      prefer_shared((const void *)onesweep_kernel<false>);
+      done.insert(dev);
+    }
   }
   const int64_t max_tiles = (pair_cap + kSortTile - 1) / kSortTile;
   int grid = 148 * 4;
   if (grid > max_tiles) grid = (int)(max_tiles > 0 ? max_tiles : 1);
   int cur = 0;
+  const int last_bits = hi_bit - lo_bit - 8 * (passes - 1);
   for (int d = 0; d < passes; ++d) {
     const int64_t lb_off = (int64_t)d * max_tiles * 256;
+    // the digit of the last pass holds only the bits left below hi_bit
+    const uint32_t dmask = d == passes - 1 ? (1u << last_bits) - 1u : 255u;
     if (vals[0])
       onesweep_kernel<true><<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
-                                                              pair_cap, lo_bit + 8 * d, hist + d * 256,
+                                                              pair_cap, lo_bit + 8 * d, dmask, hist + d * 256,
                                                               lookback + lb_off, tile_ctr + d);
     else
       onesweep_kernel<false><<<grid, kSortThreads, smem, st>>>(ctl, keys[cur], nullptr, keys[cur ^ 1], nullptr,
-                                                               pair_cap, lo_bit + 8 * d, hist + d * 256,
+                                                               pair_cap, lo_bit + 8 * d, dmask, hist + d * 256,
                                                                lookback + lb_off, tile_ctr + d);
     cur ^= 1;
   }

@@ -733,7 +733,8 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     const SortHist sh{r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback), max_tiles, r->at<uint32_t>(C.tile_ctr),
                       lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
-                     keys[0], vals[0], r->dims.pair_cap, gx, kf, sh, r->at<uint64_t>(C.pieces),
+                     keys[0], vals[0], r->dims.pair_cap, TileGeom{c.width, c.height, c.tile_w, c.tile_h}, gx, kf,
+                     sh, r->at<uint64_t>(C.pieces),
                      r->at<uint32_t>(C.piece_ctr), r->dims.piece_cap, r->at<uint2>(C.ranges), ntiles, st);
     r->span_end(t, 5, st);  // scan reduce, scan blocks, scan offsets, emit, emit pieces
     uint32_t *no_vals[2] = {nullptr, nullptr};
@@ -891,6 +892,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
     case VM3DGS_DBG_SPLAT_DEPTH: src = r->at<void>(C.splat_depth); n = 4 * N; break;
     case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(C.splat_radius); n = 4 * N; break;
     case VM3DGS_DBG_SPLAT_TMASK: src = r->at<void>(C.splat_tmask); n = 8 * N; break;
+    case VM3DGS_DBG_SPLAT_TOUCHED: src = r->at<void>(C.splat_touched); n = 4 * N; break;
     case VM3DGS_DBG_KEYS:
     case VM3DGS_DBG_VALUES: {
       // the sorted pairs as (tile << 32 | bits(depth), splat), whatever the

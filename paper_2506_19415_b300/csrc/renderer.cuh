@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "coverage.cuh"
 #include "scene.h"
 
 struct vm3dgs_renderer;
@@ -42,7 +43,7 @@ struct Splats {
   uint32_t *rect;    // [2] per splat: x0 | x1 << 16, y0 | y1 << 16
   uint32_t *touched; // tiles covered (0 = culled)
   float *radius;     // pixels
-  uint64_t *tmask;   // covered tiles of a rectangle of <= 64 tiles, row-major bits
+  uint64_t *tmask;   // kept tiles of a rectangle of <= 64 tiles, row-major bits (0 for larger ones)
 };
 
 // One render context: the buffers a render writes after its projection
@@ -207,7 +208,8 @@ struct ViewTable {
 void launch_project_batched(const ProjectArgs &a, const ViewTable *views, int n_views, cudaStream_t st);
 void launch_scan_emit_batched(Ctl *ctl, const Splats &sp, int64_t ncap, int views, const ViewTable *vt,
                               uint32_t *block_sums, uint32_t *offsets, uint64_t *keys, uint32_t *vals,
-                              int64_t pair_cap, cudaStream_t st);
+                              int64_t pair_cap, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap,
+                              cudaStream_t st);
 void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splats &sp, int64_t ncap_total,
                           const ViewTable *vt, int ntiles, const float bg[3], uint32_t *order, uint32_t *work,
                           cudaStream_t st);
@@ -238,9 +240,9 @@ struct SortHist {
 // the splats with more than 32 pairs, written by the first emission kernel
 // (also zeroes ranges[0 .. ntiles) for the ranges of the coming sort)
 void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap, uint32_t *block_sums,
-                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, int gx, const KeyFormat &kf,
-                      const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges,
-                      int ntiles, cudaStream_t st);
+                      uint32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t pair_cap, const TileGeom &tg, int gx,
+                      const KeyFormat &kf, const SortHist &sh, uint64_t *pieces, uint32_t *piece_ctr,
+                      int64_t piece_cap, uint2 *ranges, int ntiles, cudaStream_t st);
 
 // sorts keys/vals (pairs = ctl->pairs, capped at pair_cap) on the low `bits` bits;
 // returns the index (0 or 1) of the buffer holding the result

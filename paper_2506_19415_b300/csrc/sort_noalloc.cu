@@ -17,7 +17,6 @@
 // different streams, or from different threads) race on the array.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "renderer.cuh"
@@ -40,17 +39,15 @@ constexpr int64_t kScratchBytes = align256(kOffVals + 4 * kMaxPairs);
 // the scratch of every call on this device
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {nullptr};
-
 __global__ void begin_kernel(Ctl *ctl, int64_t n) {
   ctl->pairs = n;
   ctl->status = 0;
 }
 
-__global__ void end_kernel(Ctl *ctl, int32_t *status_out) {
-  if (status_out) *status_out = ctl->status;
+// copies the call's status out (forced, when non-zero, replaces it) and
+// clears it for the next call
+__global__ void end_kernel(Ctl *ctl, int32_t *status_out, int32_t forced) {
+  if (status_out) *status_out = forced ? forced : ctl->status;
   ctl->status = 0;
 }
 
@@ -61,41 +58,56 @@ using namespace vm;
 
 extern "C" int vm3dgs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, int64_t n, int32_t key_bits,
                                          int32_t *status_dev, void *stream) {
-  if (!keys_dev || !vals_dev) return fail(VM3DGS_E_INVAL, "null keys or values");
+  if ((!keys_dev || !vals_dev) && n > 0) return fail(VM3DGS_E_INVAL, "null keys or values");
   if (n < 0 || n > kMaxPairs)
     return fail(VM3DGS_E_CAPACITY, "at most " + std::to_string(kMaxPairs) + " pairs per call, got " + std::to_string(n));
   if (key_bits < 1 || key_bits > 64) return fail(VM3DGS_E_INVAL, "key_bits must be 1..64");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fail(VM3DGS_E_CUDA, "no usable current device");
-  unsigned char *base = nullptr;
-  {
-    // first call on this device: look up the device address of the array
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void *p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
-      if (e != cudaSuccess || !p) return fail(VM3DGS_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    base = g_addr[dev];
-  }
+  // an error left by the caller's earlier work is not this call's to report
+  // (or to clear): refuse to start on top of it
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return fail(VM3DGS_E_CUDA, std::string("a CUDA error from earlier work is pending: ") + cudaGetErrorString(pending));
+  // the array's address in the current context, looked up on every call: a
+  // host-side lookup once the library's module is loaded there (the first
+  // call on a device loads it), and never stale after a device reset or in
+  // another context of the same device
+  void *p = nullptr;
+  const cudaError_t ea = cudaGetSymbolAddress(&p, g_sort_scratch);
+  if (ea != cudaSuccess || !p) return fail(VM3DGS_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ea));
+  unsigned char *base = static_cast<unsigned char *>(p);
   cudaStream_t st = (cudaStream_t)stream;
   Ctl *ctl = reinterpret_cast<Ctl *>(base + kOffCtl);
   begin_kernel<<<1, 1, 0, st>>>(ctl, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(VM3DGS_E_CUDA, std::string("sort: ") + cudaGetErrorString(e));
+  int32_t forced = 0;
+  std::string why;
   if (n > 1) {
     uint64_t *keys[2] = {keys_dev, reinterpret_cast<uint64_t *>(base + kOffKeys)};
     uint32_t *vals[2] = {vals_dev, reinterpret_cast<uint32_t *>(base + kOffVals)};
     const int cur = launch_sort(ctl, keys, vals, n, 0, key_bits, reinterpret_cast<uint32_t *>(base + kOffHist),
                                 reinterpret_cast<uint32_t *>(base + kOffLook), kLookbackWords,
                                 reinterpret_cast<uint32_t *>(base + kOffTiles), st);
-    if (cur < 0) return fail(VM3DGS_E_CUDA, "sort launch refused");
-    if (cur == 1) {
-      cudaMemcpyAsync(keys_dev, keys[1], 8 * (size_t)n, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(vals_dev, vals[1], 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (cur < 0) {
+      forced = VM3DGS_E_CUDA;
+      why = "sort launch refused";
+    } else if ((e = cudaGetLastError()) != cudaSuccess) {
+      forced = VM3DGS_E_CUDA;
+      why = std::string("sort: ") + cudaGetErrorString(e);
+    } else if (cur == 1) {
+      cudaError_t c1 = cudaMemcpyAsync(keys_dev, keys[1], 8 * (size_t)n, cudaMemcpyDeviceToDevice, st);
+      cudaError_t c2 = c1 == cudaSuccess ? cudaMemcpyAsync(vals_dev, vals[1], 4 * (size_t)n, cudaMemcpyDeviceToDevice, st)
+                                         : c1;
+      if (c2 != cudaSuccess) {
+        forced = VM3DGS_E_CUDA;
+        why = std::string("copy back: ") + cudaGetErrorString(c2);
+      }
     }
   }
-  end_kernel<<<1, 1, 0, st>>>(ctl, status_dev);
-  const cudaError_t e = cudaGetLastError();
+  // the status word is written on the failure path too, so a stream-ordered
+  // reader of it sees the failure
+  end_kernel<<<1, 1, 0, st>>>(ctl, status_dev, forced);
+  e = cudaGetLastError();
+  if (forced) return fail(VM3DGS_E_CUDA, why);
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, std::string("sort: ") + cudaGetErrorString(e));
 }

@@ -55,6 +55,23 @@ def compare_image(gpu_img, ref):
     return e0, int(flag.sum())
 
 
+def expected_tmask(pr, cam):
+    """The kernel's per-splat tile mask as the oracle's tile rule gives it:
+    the kept tiles of a rectangle of at most 64 tiles as row-major bits of
+    the rectangle, 0 for culled splats and larger rectangles."""
+    out = np.zeros(len(pr["vis"]), np.uint64)
+    for i in np.nonzero(pr["vis"])[0]:
+        x0, y0, x1, y1 = (int(t) for t in pr["rect"][i])
+        w = x1 - x0
+        if w * (y1 - y0) > 64:
+            continue
+        m = 0
+        for tx, ty in oracle.splat_tiles(pr, i, cam):
+            m |= 1 << ((ty - y0) * w + (tx - x0))
+        out[i] = m
+    return out
+
+
 def city_cam(extent, k=0, width=320, height=180, tile=(16, 16)):
     """Street-level camera looking along the city from one corner."""
     eye = np.array([0.35 * extent + 3.0 * k, 0.2 * extent, 1.7 + 0.3 * k])

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import scenegen
-from _common import compare_image, import_scene, tiny_scene
+from _common import compare_image, expected_tmask, import_scene, tiny_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,8 @@ def test_full_scene_render_parity(v, name, kw, sep):
     np.testing.assert_array_equal(depth.view(np.uint32), np.where(vis, pr["depth"], 0).view(np.uint32))
     np.testing.assert_array_equal(rad, np.where(vis, pr["radius"], 0))
     tmask = r.debug(v.DBG_SPLAT_TMASK, np.uint64)
-    np.testing.assert_array_equal(tmask, np.where(vis, pr["tmask"], 0))
+    np.testing.assert_array_equal(tmask, expected_tmask(pr, cam))
+    np.testing.assert_array_equal(r.debug(v.DBG_SPLAT_TOUCHED, np.uint32), np.where(vis, pr["touched"], 0))
     keys = r.debug(v.DBG_KEYS, np.uint64)
     vals = r.debug(v.DBG_VALUES, np.uint32)
     assert st["pairs"] == len(ref["keys"])
@@ -95,6 +96,36 @@ def test_crowded_tiles(v):
     np.testing.assert_array_equal(r.debug(v.DBG_KEYS, np.uint64), ref["keys"])
     np.testing.assert_array_equal(r.debug(v.DBG_VALUES, np.uint32).astype(np.int64), ref["idx"])
     np.testing.assert_array_equal(r.debug(v.DBG_RANGES, np.uint32).reshape(-1, 2).astype(np.int64), rng)
+    compare_image(img, ref)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (32, 8)])
+def test_large_splat_binning(v, tile):
+    """Gaussians close to a ragged 250x131 view, half of them stretched along
+    one axis: many rectangles hold more than 64 tiles, some with at most 32
+    kept tiles (dealt out by lanes walking their rows) and some with hundreds
+    (cut into pieces whose rows a warp walks).  Tile counts, keys, values and
+    ranges equal the oracle's bit for bit; the image is within tolerance."""
+    raw = scenegen.uniform_scene(n=6000, seed=41, lo=-1.6, hi=1.6, ls_mu=-3.2, ls_sd=0.6, sh_degree=1)
+    raw.log_scale[::2, 0] += np.float32(2.0)
+    from oracle import build as ob
+    bp = ob.BuildParams(page_size=256, paging="morton", lo=(-2, -2, -2), hi=(2, 2, 2), voxel=0.25, kappa=0.5,
+                        link_samples=0)
+    sc = ob.build_scene(raw, bp)
+    cam = scenegen.look_at((0.3, -0.2, -2.6), (0, 0, 0), (0, -1, 0), 250, 131, 70.0, tile)
+    r, img, st = _full_render(v, raw, sc, cam)
+    g, vid = oracle.full_scene(sc)
+    ref = oracle.render(g, vid, cam)
+    pr = ref["proj"]
+    vis = pr["vis"] != 0
+    rc = pr["rect"]
+    area = (rc[:, 2] - rc[:, 0]) * (rc[:, 3] - rc[:, 1])
+    wide = vis & (area > 64)
+    assert (wide & (pr["touched"] <= 32)).sum() > 20 and (wide & (pr["touched"] > 256)).sum() > 5
+    np.testing.assert_array_equal(r.debug(v.DBG_SPLAT_TOUCHED, np.uint32), np.where(vis, pr["touched"], 0))
+    np.testing.assert_array_equal(r.debug(v.DBG_KEYS, np.uint64), ref["keys"])
+    np.testing.assert_array_equal(r.debug(v.DBG_VALUES, np.uint32).astype(np.int64), ref["idx"])
+    np.testing.assert_array_equal(r.debug(v.DBG_RANGES, np.uint32).reshape(-1, 2).astype(np.int64), ref["ranges"])
     compare_image(img, ref)
 
 
