@@ -128,3 +128,160 @@ def test_controller_keeps_usage_in_band():
     # and shrinks on a quick reversal
     rs.control(pt2, np.float32(0.1), [(0, 1, 0, 0)])
     assert abs(float(pt2.step) - 0.1 * 1.01 ** 4 * 0.99) < 1e-6
+
+
+# --------------------------------------------------------------------------- prefetch placement
+def _resident_pairs(pt):
+    out = []
+    for e in range(pt.rp.n_entries):
+        if pt.lod[e] < 0:
+            continue
+        for s in range(pt.rp.fanout ** int(pt.lod[e])):
+            if pt.slot[e, s] >= 0:
+                out.append((int(pt.slot[e, s]), int(pt.lod[e])))
+    return out
+
+
+def _sse_level_fp64(f_px, err_p, centre, campos, tau, levels):
+    """The screen-space-error level recomputed in FP64 (d = the distance from
+    the camera to the page sphere, at least 0.2); None near a threshold."""
+    d = max(float(np.linalg.norm(np.asarray(centre[:3], np.float64) - np.asarray(campos, np.float64)))
+            - float(centre[3]), 0.2)
+    for l in range(levels - 1, 0, -1):
+        sse = f_px * float(err_p[l]) / d
+        if abs(sse - float(tau)) < 1e-4 * max(1.0, float(tau)):
+            return None
+        if sse <= float(tau):
+            return l
+    return 0
+
+
+@pytest.mark.parametrize("levels,fanout,P,budget_pages,lod", [(1, 8, 12, 5, False), (3, 8, 10, 4, True),
+                                                              (4, 2, 14, 7, True), (2, 4, 6, 50, True)])
+def test_prefetch_placement_invariants(levels, fanout, P, budget_pages, lod):
+    """Random tables, logits, requests and cameras; every placement checked
+    against what the sequential definition promises, each property computed
+    here independently: the candidates are the window pages with logit above
+    the threshold, not requested, not resident at their (FP64-recomputed)
+    level; the copies are the longest prefix of (logit desc, level asc, page
+    asc) that fits the budget; fresh entries are the least recently used of
+    those not used this frame; entries used this frame are untouched; every
+    copied page sits at its level in a slot of its entry; no (page, level) is
+    resident twice."""
+    rng = np.random.default_rng(1000 * levels + P)
+    ps = 64
+    rp = rs.ResidencyParams(n_entries=P, page_size=ps, levels=levels, fanout=fanout, record_bytes=56,
+                            budget_bytes=budget_pages * ps * 56, lod=lod, tau0=1.5)
+    n_vp = 48
+    err = np.zeros((n_vp, levels), np.float32)
+    for l in range(1, levels):
+        err[:, l] = (err[:, l - 1] if l > 1 else 0) + rng.uniform(0.02, 0.3, n_vp).astype(np.float32)
+    centroid = np.concatenate([rng.uniform(-20, 20, (n_vp, 3)), rng.uniform(0.5, 3, (n_vp, 1))], 1).astype(np.float32)
+    checked = admitted_total = 0
+    for it in range(40):
+        pt = rs.PageTable(rp)
+        # a random earlier history: entries at random levels and ages
+        for e in range(P):
+            if rng.random() < 0.7:
+                l = int(rng.integers(0, levels))
+                pt.lod[e] = l
+                pt.last_used[e] = int(rng.integers(0, 10))
+                for s in range(fanout ** l):
+                    if rng.random() < 0.8:
+                        pt.slot[e, s] = int(rng.integers(0, n_vp))
+        # de-duplicate (page, level) as a real table never holds twice
+        seen = set()
+        for e in range(P):
+            for s in range(fanout ** max(int(pt.lod[e]), 0)):
+                k = (int(pt.slot[e, s]), int(pt.lod[e]))
+                if pt.slot[e, s] >= 0 and k in seen:
+                    pt.slot[e, s] = -1
+                seen.add(k)
+        frame_now = 10
+        pt.tau = np.float32(rng.uniform(0.5, 4.0))
+        req = (rng.random(n_vp) < 0.3).astype(np.uint32) * np.uint32(0x90000000)
+        base = int(rng.integers(0, 8))
+        logits = (rng.integers(-2, 5, size=32) * 0.5).astype(np.float32)  # ties: the tie order matters
+        campos = rng.uniform(-25, 25, 3).astype(np.float32)
+        f_px = 500.0
+        budget_left = int(rng.integers(0, budget_pages + 1)) * ps * 56
+        before_lod, before_slot, before_last = pt.lod.copy(), pt.slot.copy(), pt.last_used.copy()
+        resident_before = set(_resident_pairs(pt))
+        copies = rs.prefetch(pt, logits, base, 0.0, req, err, centroid, campos, f_px, budget_left, frame_now)
+        # candidates, recomputed
+        cands, ambiguous = [], False
+        for j in range(len(logits)):
+            p = base + j
+            if p >= n_vp or not logits[j] > 0.0 or req[p] != 0:
+                continue
+            lev = _sse_level_fp64(f_px, err[p], centroid[p], campos, pt.tau, levels) if lod and levels > 1 else 0
+            if lev is None:
+                ambiguous = True
+                continue
+            if (p, lev) not in resident_before:
+                cands.append((-float(logits[j]), lev, p))
+        if ambiguous:
+            continue
+        checked += 1
+        cands.sort()
+        adm, cum = [], 0
+        for c in cands:
+            cost = ps // fanout ** c[1] * 56
+            if cum + cost > budget_left:
+                break
+            cum += cost
+            adm.append(c)
+        free = sorted([e for e in range(P) if before_last[e] < frame_now], key=lambda e: (before_last[e], e))
+        need = sum((sum(1 for c in adm if c[1] == l) + fanout ** l - 1) // fanout ** l for l in range(levels))
+        # copies: the admitted prefix in order, as far as fresh entries last
+        got = [(p, l) for (p, l, e, s) in copies]
+        want = [(c[2], c[1]) for c in adm]
+        if need <= len(free):
+            assert got == want
+        else:
+            assert got == [w for w in want if w in set(got)] and len(got) < len(want)
+        admitted_total += len(got)
+        assert sum(ps // fanout ** l * 56 for (p, l) in got) <= budget_left
+        used = {e for (p, l, e, s) in copies}
+        assert used <= set(free[:need])
+        assert used == set(free[:len(used)]) or need > len(free)
+        for e in range(P):
+            if before_last[e] >= frame_now:
+                assert pt.lod[e] == before_lod[e] and np.array_equal(pt.slot[e], before_slot[e])
+        for (p, l, e, s) in copies:
+            assert pt.lod[e] == l and pt.slot[e, s] == p and s < fanout ** l and pt.last_used[e] == frame_now
+        pairs = _resident_pairs(pt)
+        assert len(pairs) == len(set(pairs))
+    assert checked >= 30 and admitted_total > 20
+
+
+def test_page_centroids_closed_form_and_containment():
+    """Closed form: a page of eight Gaussians at the corners of a cube of
+    half-side h around c with scale s has centroid c and radius
+    h sqrt(3) + 3 s.  On a built scene: every Gaussian's 3-sigma ball (its
+    mean, 3 x its largest scale) lies inside its page's sphere and touches it
+    for at least one Gaussian; the centre is the mean (zero sum of offsets)."""
+    import dataclasses
+    from _common import tiny_scene
+    raw, sc = tiny_scene(links=False)
+    h, s, c = 1.25, 0.03, np.array([2.0, -1.0, 0.5])
+    corners = np.array([[x, y, z] for x in (-h, h) for y in (-h, h) for z in (-h, h)]) + c
+    L0 = dict(sc.levels[0])
+    L0["pos"] = L0["pos"].copy()
+    L0["scale"] = L0["scale"].copy()
+    L0["pos"][0, :8] = corners
+    L0["scale"][0, :8] = s
+    count = sc.count.copy()
+    count[0] = 8
+    sc2 = dataclasses.replace(sc, levels=[L0] + list(sc.levels[1:]), count=count)
+    cen = rs.page_centroids(sc2)
+    np.testing.assert_allclose(cen[0, :3], c, atol=1e-6)
+    np.testing.assert_allclose(cen[0, 3], h * np.sqrt(3) + 3 * s, rtol=1e-6)
+    cen = rs.page_centroids(sc)
+    for p in range(sc.n_pages):
+        n = int(sc.count[p])
+        pos = sc.levels[0]["pos"][p, :n].astype(np.float64)
+        reach = np.linalg.norm(pos - cen[p, :3], axis=1) + 3 * sc.levels[0]["scale"][p, :n].max(1)
+        assert reach.max() <= cen[p, 3] * (1 + 1e-6) + 1e-6
+        assert reach.max() >= cen[p, 3] * (1 - 1e-6) - 1e-6
+        np.testing.assert_allclose((pos - cen[p, :3]).sum(0) / n, 0, atol=1e-5)
