@@ -94,46 +94,72 @@ class ClockSampler:
     def __init__(self, index, period=0.002):
         self.index, self.period, self.rows, self.h, self.t = index, period, [], None, None
         self.stop_flag = threading.Event()
+        self.err = ""
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self._open_ctypes(index)
         except Exception as e:  # noqa: BLE001 (no NVML: reported in the line)
             self.err = str(e)
+            self.h = None
+
+    def _open_ctypes(self, index):
+        """NVML's C library (read-only queries: clocks and their reasons)."""
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle for device %d" % index)
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.nv, self.h, self.reasons_fn, self.ct = nv, h, reasons, ctypes
+
+    def _smi_sample(self):
+        """One nvidia-smi query (when NVML's library cannot be opened)."""
+        q = "clocks.sm,clocks.max.sm,clocks_event_reasons.active"
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10).stdout
+            sm, mx, act = [x.strip() for x in out.strip().split(",")[:3]]
+            self.rows.append((int(float(sm)), int(float(mx)), int(act, 16)))
+        except (OSError, ValueError, subprocess.SubprocessError):
+            pass
 
     def _sample(self):
-        nv = self.nv
-        sm = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
-        mx = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
-        get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
-        self.rows.append((sm, mx, int(get(self.h))))
+        if self.h is None:
+            return self._smi_sample()
+        ct, nv, h = self.ct, self.nv, self.h
+        sm, mx, rs_ = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        nv.nvmlDeviceGetClockInfo(h, ct.c_int(1), ct.byref(sm))      # NVML_CLOCK_SM = 1
+        nv.nvmlDeviceGetMaxClockInfo(h, ct.c_int(1), ct.byref(mx))
+        self.reasons_fn(h, ct.byref(rs_))
+        self.rows.append((int(sm.value), int(mx.value), int(rs_.value)))
 
     def _loop(self):
         while not self.stop_flag.wait(self.period):
             self._sample()
 
     def start(self):
-        if self.h is None:
-            return
         self.rows = []
         self.stop_flag.clear()
         self._sample()
-        self.t = threading.Thread(target=self._loop, daemon=True)
-        self.t.start()
+        if self.h is not None:
+            self.t = threading.Thread(target=self._loop, daemon=True)
+            self.t.start()
 
     def stop(self):
-        if self.h is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["NVML unavailable: " + self.err], "samples": 0}
-        self.stop_flag.set()
-        self.t.join()
+        if self.h is not None:
+            self.stop_flag.set()
+            self.t.join()
         self._sample()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source: " + self.err], "samples": 0}
         sm = [r[0] for r in self.rows]
         reasons = sorted({name for r in self.rows for name, bit in self.REASONS if r[2] & bit})
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in self.rows),
                 "sm_mhz_min": min(sm), "reasons": reasons, "samples": len(self.rows),
-                "how": "NVML every %.0f ms during the timed frames" % (1e3 * self.period)}
+                "how": ("NVML every %.0f ms during the timed frames" % (1e3 * self.period)) if self.h is not None
+                else "nvidia-smi at the start and end of the timed frames (NVML library unavailable)"}
 
 
 # ----------------------------------------------------------------------------- GPU arm

@@ -148,6 +148,10 @@ typedef struct {
                                                                             because a prefetch brought them */
   int32_t staged_projection; /* 1: the projection stages records with tensor-map tile loads (every level block a
                                 multiple of 32 Gaussians); 0: it gathers them with plain loads */
+  /* sort key of the last rendered view: tile, depth and splat-index field
+   * widths in bits (index 0 when the index travels in a value array, i.e.
+   * key_packed = 0); the sort orders the key's tile and depth fields */
+  int32_t key_tile_bits, key_depth_bits, key_index_bits, key_packed;
 } vm3dgs_stats;
 
 typedef struct {

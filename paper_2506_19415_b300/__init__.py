@@ -66,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("acc_frames", c_i64), ("acc_views", c_i64), ("acc_pairs", c_i64), ("acc_drawn_gaussians", c_i64),
                 ("acc_streamed_bytes", c_i64), ("acc_streamed_pages", c_i64), ("acc_missing", c_i64),
                 ("acc_requested", c_i64), ("acc_prefetched_pages", c_i64), ("acc_prefetched_bytes", c_i64),
-                ("acc_prefetch_hits", c_i64), ("staged_projection", c_i32)]
+                ("acc_prefetch_hits", c_i64), ("staged_projection", c_i32), ("key_tile_bits", c_i32),
+                ("key_depth_bits", c_i32), ("key_index_bits", c_i32), ("key_packed", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

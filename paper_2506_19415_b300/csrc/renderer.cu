@@ -827,6 +827,12 @@ extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *str
   out->acc_prefetched_bytes = c.acc_prefetched_bytes;
   out->acc_prefetch_hits = c.acc_prefetch_hits;
   out->staged_projection = r->maps_ok ? 1 : 0;
+  int tbits = 0;
+  while ((1 << tbits) < r->last_ntiles) ++tbits;
+  out->key_tile_bits = tbits;
+  out->key_depth_bits = r->kf.R;
+  out->key_index_bits = r->kf.packed ? r->kf.ib : 0;
+  out->key_packed = r->kf.packed ? 1 : 0;
   return VM3DGS_OK;
 }
 

@@ -142,3 +142,73 @@ def test_interleaved_streams_equal_one_stream(v):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
     assert r.stats()["status"] == 0
+
+
+def test_batched_views_against_oracle(v):
+    """Every view of a batch (uneven sizes, 16x16 / 8x8 / 32x8 tiles, fp16
+    pool, SH2) against the oracle run on the fp16-rounded attributes of the
+    drawn Gaussians: the view's share of the batch's sorted keys (global tile
+    mapped back to the view's tile) and values (record index mapped back to
+    the view's splat) and its tile ranges bit-exact, its image within the
+    FP32 tolerance."""
+    import oracle
+    from _common import compare_image, round16_scene
+    sc, scene = _scene(v)
+    cams = _views(6, [(16, 16), (8, 8), (32, 8)])
+    cfg = v.RenderConfig(max_width=640, max_height=400, lod=False, fp16_pool=True, max_views=8,
+                         staging_bytes=1 << 40)
+    r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    r.request_all()
+    r.update_residency()
+    imgs = [im.cpu().numpy() for im in r.render_batched(cams)]
+    st = r.stats()
+    assert st["status"] == 0
+    bk = r.debug(v.DBG_KEYS, np.uint64)
+    bv = r.debug(v.DBG_VALUES, np.uint32).astype(np.int64)
+    brng = r.debug(v.DBG_RANGES, np.uint32).reshape(-1, 2).astype(np.int64)
+    g, vid = oracle.full_scene(round16_scene(sc))
+    N = len(vid)
+    assert st["drawn_gaussians"] == N
+    off = [0]
+    for c in cams:
+        off.append(off[-1] + ((c.width + c.tile_w - 1) // c.tile_w) * ((c.height + c.tile_h - 1) // c.tile_h))
+    tile = (bk >> np.uint64(32)).astype(np.int64)
+    for k, c in enumerate(cams):
+        ref = oracle.render(g, vid, c)
+        sel = (tile >= off[k]) & (tile < off[k + 1])
+        local = ((tile[sel] - off[k]).astype(np.uint64) << np.uint64(32)) | (bk[sel] & np.uint64(0xFFFFFFFF))
+        np.testing.assert_array_equal(local, ref["keys"])
+        np.testing.assert_array_equal(bv[sel] - k * N, ref["idx"])
+        first = np.flatnonzero(sel)[0] if sel.any() else 0
+        rk = brng[off[k]:off[k + 1]]
+        rk = np.where(rk[:, 1:] > rk[:, :1], rk - first, 0)
+        np.testing.assert_array_equal(rk, ref["ranges"])
+        compare_image(imgs[k], ref)
+
+
+def test_multi_camera_feedback_against_oracle(v):
+    """Page determination over several cameras in one call: the request words
+    are the maximum over the cameras of each camera's oracle request words
+    (links included), the direct flags their union, and the request list the
+    pages with a non-zero word."""
+    import oracle
+    sc, scene = _scene(v)
+    cams = _views(4, [(16, 16)])
+    cfg = v.RenderConfig(max_width=640, max_height=400, lod=False, fp16_pool=True, max_views=8,
+                         staging_bytes=1 << 40)
+    r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    r.render_feedback(cams)
+    req = np.zeros(sc.n_pages, np.uint32)
+    direct = np.zeros(sc.n_pages, np.uint8)
+    for c in cams:
+        buf = oracle.feedback_raster(sc.verts, sc.tris, sc.face_page, c, 4)
+        q, d = oracle.feedback_reduce(buf, sc.n_pages, sc.link_ptr, sc.link_col, True)
+        req = np.maximum(req, q)
+        direct |= d
+    assert (req != 0).sum() > 10
+    np.testing.assert_array_equal(r.debug(v.DBG_REQ, np.uint32), req)
+    np.testing.assert_array_equal(r.debug(v.DBG_DIRECT, np.uint8), direct)
+    r.update_residency()
+    reqs = r.debug(v.DBG_REQUESTS, np.int32).reshape(-1, 4)
+    np.testing.assert_array_equal(reqs[:, 0], np.flatnonzero(req))
+    np.testing.assert_array_equal(reqs[:, 1].view(np.uint32), req[req != 0])
