@@ -173,9 +173,10 @@ def build_scene(W):
     return scene, t1 - t0, time.time() - t1
 
 
-def make_renderer(v, scene, W, fp16, width, height, pool_slots=None, max_pairs=0):
+def make_renderer(v, scene, W, fp16, width, height, pool_slots=None, max_pairs=0, sort_mode=0):
     cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=fp16,
-                         max_width=width, max_height=height, tau0=1.0, step0=0.1, max_pairs=max_pairs)
+                         max_width=width, max_height=height, tau0=1.0, step0=0.1, max_pairs=max_pairs,
+                         sort_mode=sort_mode)
     if pool_slots is not None:
         return v.Renderer(scene, cfg, pool_slots=pool_slots)
     if W["pool_bytes"] is None:
@@ -331,17 +332,19 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
     return dict(ms=ms, wall=wall, issue=issue, stage=stage, stats=stats, clocks=clk)
 
 
-# DRAM bytes per onesweep pass per sorted pair, from the ncu capture summarised
-# in profiles/onesweep_kernel_citypatch.md (dram__bytes_read.sum +
-# dram__bytes_write.sum of one pass over the profiling workload divided by its
-# pairs); None until a capture of the current kernel exists.
-ONESWEEP_DRAM_BYTES_PER_PAIR = 7.0
+# DRAM bytes per sort pass per sorted pair, from an ncu capture of the
+# current sort kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch over the profiling workload divided by its pairs and passes); None
+# until a capture of the current kernel exists.
+SORT_DRAM_BYTES_PER_PAIR_PASS = None
 
 
-def roofline(v, stage, stats, peaks, rec16, width, height):
-    """Roofline of the dominant kernel (the onesweep sort pass) and of the
-    gather (projection) and blend kernels, from the CUDA-event spans of the
-    timed frames: algorithmic bytes per launch / mean launch time."""
+def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
+    """Roofline of the dominant kernel (the radix sort) and of the gather
+    (projection) and blend kernels, from the CUDA-event spans of the timed
+    frames: algorithmic bytes per launch / mean launch time.  The sort moves
+    every 8-byte packed key in and out once per pass (16 B per pair per pass);
+    one cooperative launch runs all of a view's passes."""
     ms, launches = stage
     names = v.STAGES
     frames = max(stats["acc_frames"], 1)
@@ -349,15 +352,17 @@ def roofline(v, stage, stats, peaks, rec16, width, height):
     pairs = stats["acc_pairs"] / views              # per view
     gauss = stats["acc_drawn_gaussians"] / frames   # per frame
     peak = peaks.get("hbm_gbs", 6400.0)
+    passes = -(-(stats["key_tile_bits"] + stats["key_depth_bits"]) // 8)
 
     def per_launch_s(stage_name, n):
         return ms[names.index(stage_name)] / max(n, 1) / 1e3
 
-    passes = launches[names.index("sort")] / views
+    sort_launches = launches[names.index("sort")]
+    per_view = sort_launches / views
     kern = {
-        # one pass reads and writes every 8-byte packed key once
-        "onesweep": (pairs * 16, per_launch_s("sort", launches[names.index("sort")]),
-                     "16 B per pair per pass (8 B key read + written)"),
+        "sort": (pairs * 16 * passes / max(per_view, 1), per_launch_s("sort", sort_launches),
+                 "16 B per pair per pass (8 B key read + written) x %d passes / %g launches per view" %
+                 (passes, per_view)),
         # pool record (fp16) read + 64 B of splat outputs written per drawn Gaussian
         "project": (gauss * (rec16 + 64), per_launch_s("project", frames),
                     "%d B record read + 64 B splat record written per drawn Gaussian" % rec16),
@@ -370,16 +375,42 @@ def roofline(v, stage, stats, peaks, rec16, width, height):
         a = b / t / 1e9 if t > 0 else 0.0
         detail[k] = {"achieved": round(a, 1), "frac": round(a / peak, 4), "us_per_launch": round(t * 1e6, 2),
                      "algorithmic_bytes_per_launch": int(b), "per_unit": note}
-    traffic = None if ONESWEEP_DRAM_BYTES_PER_PAIR is None else int(ONESWEEP_DRAM_BYTES_PER_PAIR * pairs)
-    out = {"bound": "hbm", "kernel": "onesweep_kernel (one sort pass)", "achieved": detail["onesweep"]["achieved"],
-           "peak": peak, "unit": "GB/s", "frac": detail["onesweep"]["frac"], "traffic": traffic,
+    if alt_sort is not None:
+        detail["sort_onesweep_per_pass"] = alt_sort
+    coop = per_view < passes
+    traffic = None if SORT_DRAM_BYTES_PER_PAIR_PASS is None else \
+        int(SORT_DRAM_BYTES_PER_PAIR_PASS * pairs * passes / max(per_view, 1))
+    out = {"bound": "hbm",
+           "kernel": ("coop_sort_kernel (all %d passes in one cooperative launch)" % passes) if coop
+           else "onesweep_kernel (one sort pass)",
+           "achieved": detail["sort"]["achieved"], "peak": peak, "unit": "GB/s", "frac": detail["sort"]["frac"],
+           "traffic": traffic,
            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
-           "passes_per_view": passes, "kernels": detail,
+           "passes_per_view": passes, "sort_launches_per_view": per_view, "kernels": detail,
            "stage_ms": {names[i]: round(ms[i], 3) for i in range(len(ms))},
            "stage_launches": {names[i]: int(launches[i]) for i in range(len(ms))},
            "note": ("blend's inputs (sorted keys and splats, < 126 MB) stay in L2 and it is bound by FP32/ALU issue, "
                     "so its HBM fraction is low by construction")}
     return out
+
+
+def onesweep_reference(v, scene, W, cams, warmup, steps, copy_stream, dist, pf, width, height, peaks):
+    """The same single-stream frames with the onesweep sort (a launch per
+    pass): its per-pass time and HBM fraction beside the cooperative sort's."""
+    rn = make_renderer(v, scene, W, True, width, height, sort_mode=1)
+    res = run_arm(v, rn, cams, warmup, steps, copy_stream, timing=True, dist=dist, pf=pf, serial=True,
+                  preroll=PREROLL)
+    ms, launches = res["stage"]
+    st = res["stats"]
+    views = max(st["acc_views"], 1)
+    i = v.STAGES.index("sort")
+    t = ms[i] / max(launches[i], 1) / 1e3
+    b = st["acc_pairs"] / views * 16
+    a = b / t / 1e9 if t > 0 else 0.0
+    del rn
+    return {"us_per_pass": round(t * 1e6, 2), "passes_per_view": launches[i] / views,
+            "sort_ms_per_view": round(ms[i] / views, 4), "achieved": round(a, 1),
+            "frac": round(a / peaks.get("hbm_gbs", 6400.0), 4), "ms_per_step_one_stream": round(res["ms"] / steps, 4)}
 
 
 def prefetch_eval(v):
@@ -557,7 +588,10 @@ def gpu_main(args):
         return
     hs = head["stats"]
     frames = max(hs["acc_frames"], 1)
-    rl = roofline(v, ser["stage"], ser["stats"], peaks, scene.info.record_bytes16, width, height)
+    # (rank 0 only: the other ranks have returned, so no barrier here)
+    alt = onesweep_reference(v, scene, W, cams, args.warmup, min(args.steps, 100), copy_stream, None, pf, width,
+                             height, peaks)
+    rl = roofline(v, ser["stage"], ser["stats"], peaks, scene.info.record_bytes16, width, height, alt)
     rl["timing"] = ("kernels timed by CUDA events in a single-stream pass over %d frames of the same walk "
                     "(bench.py); the timed headline loop itself records no per-stage events" % min(args.steps, 100))
     launches_per_frame = sum(ser["stage"][1]) / max(ser["stats"]["acc_frames"], 1)

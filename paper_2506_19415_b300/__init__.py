@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
     _fields_ = [("staging_bytes", c_i64), ("feedback_ds", c_i32), ("links", c_i32), ("lod", c_i32),
                 ("fp16_pool", c_i32), ("usage_lo", c_f), ("usage_hi", c_f), ("tau0", c_f), ("step0", c_f),
                 ("max_width", c_i32), ("max_height", c_i32), ("max_views", c_i32), ("max_pairs", c_i64),
-                ("bg", c_f * 3), ("separate_values", c_i32)]
+                ("bg", c_f * 3), ("separate_values", c_i32), ("sort_mode", c_i32)]
 
 
 class Stats(ctypes.Structure):
@@ -338,6 +338,7 @@ class RenderConfig:
     max_pairs: int = 0
     bg: tuple = (0.0, 0.0, 0.0)
     separate_values: bool = False   # True: always sort (key, splat) pairs instead of packed keys
+    sort_mode: int = 0              # 0: one cooperative launch for all passes; 1: a onesweep launch per pass
 
     def struct(self) -> Params:
         p = Params()
@@ -346,6 +347,7 @@ class RenderConfig:
         p.max_width, p.max_height, p.max_views, p.max_pairs = self.max_width, self.max_height, self.max_views, self.max_pairs
         p.bg[:] = [float(v) for v in self.bg]
         p.separate_values = int(self.separate_values)
+        p.sort_mode = int(self.sort_mode)
         return p
 
 

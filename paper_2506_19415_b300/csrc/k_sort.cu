@@ -17,7 +17,9 @@
 //   ranges        [first, last+1) of every tile in the sorted keys.
 // Stability plus ascending emission order gives the order (tile, depth,
 // drawn index), and the drawn index ascends with the virtual Gaussian id.
+#include <algorithm>
 #include <mutex>
+#include <unordered_map>
 #include <unordered_set>
 
 #include "coverage.cuh"
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     // the look-back words and tile counters of the coming sort
     const int64_t ntiles = (po.M + kSortTile - 1) / kSortTile;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int d = 0; d < sh.passes; ++d) {
+    for (int d = 0; d < sh.passes && sh.lookback; ++d) {
       uint32_t *lb = sh.lookback + (int64_t)d * sh.max_tiles * 256;
       for (int64_t q2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q2 < ntiles * 256; q2 += stride) lb[q2] = 0;
     }
@@ -644,6 +646,213 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
 }
 
 
+// ------------------------------------------------------------ cooperative sort
+// All passes of the LSD radix sort in one cooperative launch: CTA b owns the
+// fixed chunk [b c, (b + 1) c) of the pairs (c = ceil(M / G)), and each pass
+// runs in three phases separated by grid barriers:
+//   count   the chunk's digit histogram -> column b of colhist[256][G]
+//   scan    CTA d (d < 256) scans digit d's column over the CTAs into the
+//           global output offsets offs[d][b] = (pairs with a smaller digit,
+//           from the pass's digit histogram counted by the emission) + (pairs
+//           of digit d in earlier chunks)
+//   scatter the chunk, in sub-tiles of kCoopTile pairs in order, ranked
+//           stably (warp match + per-warp digit counters, as in the onesweep
+//           pass) and written through shared memory to offs + the digit's
+//           running count in the chunk.
+// No look-back chain and one launch for all passes: the pass costs two reads
+// and one write of the keys (in L2 at these sizes) and three barriers.  Each
+// barrier wait is bounded: on expiry the kernel sets an error word that every
+// CTA checks, records VM3DGS_E_TIMEOUT and returns (writes stay in bounds:
+// every scatter checks its position against the pair count).
+constexpr int kCoopThreads = 512;
+constexpr int kCoopWarps = kCoopThreads / 32;
+constexpr int kCoopItems = 8;
+constexpr int kCoopTile = kCoopThreads * kCoopItems;
+constexpr int kCoopMaxGrid = kCoopThreads;  // the column scan holds one CTA per thread
+constexpr uint32_t kBarrierSpins = 1u << 22;
+
+struct CoopSortArgs {
+  Ctl *ctl;
+  uint64_t *keys[2];
+  uint32_t *vals[2];
+  int64_t cap;
+  int lo_bit, passes;
+  uint32_t last_mask;
+  const uint32_t *hist;  // [passes][256] digit counts of all pairs
+  uint32_t *colhist;     // [256][G]
+  uint32_t *offs;        // [256][G]
+  uint32_t *bar;         // [0] barrier arrivals, [1] error word (both zero at launch)
+};
+
+// exclusive scan of one value per thread over the 512-thread block; *total
+// gets the block's sum
+__device__ __forceinline__ uint32_t coop_block_scan(uint32_t v, uint32_t *total, uint32_t *s_scan) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_scan[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kCoopWarps; ++w) {
+    const uint32_t t = s_scan[w];
+    if (w < warp) wpre += t;
+    tot += t;
+  }
+  __syncthreads();
+  *total = tot;
+  return wpre + x - v;
+}
+
+// Grid barrier: every CTA arrives once per call; returns false (in every
+// thread) when the bounded wait expired or another CTA reported an error.
+__device__ __forceinline__ bool coop_grid_sync(uint32_t *bar, uint32_t target, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&bar[0], 1u);
+    uint32_t spins = 0;
+    for (;;) {
+      if (*(volatile uint32_t *)&bar[1]) {
+        ok = 0;
+        break;
+      }
+      if (*(volatile uint32_t *)&bar[0] >= target) break;
+      if (++spins > kBarrierSpins) {
+        atomicExch(&bar[1], 1u);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(kCoopThreads, 2) coop_sort_kernel(CoopSortArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kCoopTile);
+  uint32_t *s_wc = s_vals + (VALS ? kCoopTile : 0);  // [kCoopWarps][256]
+  __shared__ uint32_t s_hist[256], s_base[256], s_run[256], s_doff[256], s_cnt[256], s_scan[kCoopWarps];
+  __shared__ int s_ok;
+  const int64_t M = a.ctl->pairs < a.cap ? a.ctl->pairs : a.cap;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  const int64_t c = (M + G - 1) / G;
+  const int64_t lo = min(M, (int64_t)b * c), hi = min(M, lo + c);
+  uint32_t nbar = 0;
+  bool ok = true;
+  for (int p = 0; p < a.passes && ok; ++p) {
+    const bool odd = p & 1;  // (selects, not indexing: the parameter arrays stay in registers)
+    const uint64_t *kin = odd ? a.keys[1] : a.keys[0];
+    uint64_t *kout = odd ? a.keys[0] : a.keys[1];
+    const uint32_t *vin = odd ? a.vals[1] : a.vals[0];
+    uint32_t *vout = odd ? a.vals[0] : a.vals[1];
+    const int shift = a.lo_bit + 8 * p;
+    const uint32_t dmask = p == a.passes - 1 ? a.last_mask : 255u;
+    // ---- count
+    for (int d = tid; d < 256; d += kCoopThreads) s_hist[d] = 0;
+    __syncthreads();
+    for (int64_t i = lo + tid; i < hi; i += kCoopThreads) atomicAdd(&s_hist[(kin[i] >> shift) & dmask], 1u);
+    __syncthreads();
+    for (int d = tid; d < 256; d += kCoopThreads) a.colhist[(int64_t)d * G + b] = s_hist[d];
+    if (!(ok = coop_grid_sync(a.bar, ++nbar * (uint32_t)G, &s_ok))) break;
+    // ---- scan: digit d's column, by CTA d (and d + G, ... when G < 256)
+    for (int d = b; d < 256; d += G) {
+      uint32_t tot;
+      const uint32_t below = coop_block_scan(tid < 256 && tid < d ? a.hist[p * 256 + tid] : 0u, &tot, s_scan);
+      (void)below;
+      const uint32_t base = tot;  // pairs with a digit below d
+      const uint32_t x = tid < G ? a.colhist[(int64_t)d * G + tid] : 0u;
+      const uint32_t ex = coop_block_scan(x, &tot, s_scan);
+      if (tid < G) a.offs[(int64_t)d * G + tid] = base + ex;
+    }
+    if (!(ok = coop_grid_sync(a.bar, ++nbar * (uint32_t)G, &s_ok))) break;
+    // ---- scatter
+    for (int d = tid; d < 256; d += kCoopThreads) {
+      s_base[d] = a.offs[(int64_t)d * G + b];
+      s_run[d] = 0;
+    }
+    for (int64_t t0 = lo; t0 < hi; t0 += kCoopTile) {
+      for (int i = tid; i < kCoopWarps * 256; i += kCoopThreads) s_wc[i] = 0;
+      __syncthreads();
+      uint64_t k[kCoopItems];
+      uint32_t v[kCoopItems], rk[kCoopItems];
+      int dg[kCoopItems];
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        const int64_t idx = t0 + (int64_t)warp * 32 * kCoopItems + it * 32 + lane;
+        const bool valid = idx < hi;
+        k[it] = valid ? kin[idx] : 0ull;
+        v[it] = (VALS && valid) ? vin[idx] : 0u;
+        dg[it] = valid ? (int)((k[it] >> shift) & dmask) : -1;
+      }
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        const int d = dg[it];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (d >= 0) before = s_wc[warp * 256 + d];
+        rk[it] = before + __popc(peers & lt);
+        __syncwarp();
+        if (d >= 0 && (peers & lt) == 0) s_wc[warp * 256 + d] = before + __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      // per digit: exclusive prefix over the warps, and the sub-tile's count
+      uint32_t cnt = 0;
+      if (tid < 256) {
+        for (int w = 0; w < kCoopWarps; ++w) {
+          const uint32_t cw = s_wc[w * 256 + tid];
+          s_wc[w * 256 + tid] = cnt;
+          cnt += cw;
+        }
+      }
+      uint32_t tot;
+      const uint32_t dofs = coop_block_scan(tid < 256 ? cnt : 0u, &tot, s_scan);
+      if (tid < 256) {
+        s_doff[tid] = dofs;
+        s_cnt[tid] = cnt;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        const int d = dg[it];
+        if (d < 0) continue;
+        const uint32_t pos = s_doff[d] + s_wc[warp * 256 + d] + rk[it];
+        s_keys[pos] = k[it];
+        if (VALS) s_vals[pos] = v[it];
+      }
+      __syncthreads();
+      const int nvalid = (int)((hi - t0) < kCoopTile ? (hi - t0) : kCoopTile);
+      for (int i = tid; i < nvalid; i += kCoopThreads) {
+        const uint64_t key = s_keys[i];
+        const int d = (int)((key >> shift) & dmask);
+        const int64_t o = (int64_t)s_base[d] + s_run[d] + (i - (int)s_doff[d]);
+        if (o < M) {
+          kout[o] = key;
+          if (VALS) vout[o] = s_vals[i];
+        }
+      }
+      __syncthreads();
+      if (tid < 256) s_run[tid] += s_cnt[tid];
+      __syncthreads();
+    }
+    if (p + 1 < a.passes && !(ok = coop_grid_sync(a.bar, ++nbar * (uint32_t)G, &s_ok))) break;
+  }
+  if (!ok && tid == 0) atomicCAS(&a.ctl->status, 0, VM3DGS_E_TIMEOUT);
+}
+
 __global__ void ranges_kernel(const Ctl *ctl, const uint64_t *keys, int64_t cap, uint2 *ranges, uint32_t ntiles,
                               int tshift) {
   const int64_t M = ctl->pairs < cap ? ctl->pairs : cap;
@@ -751,6 +960,68 @@ int launch_sort_passes(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t p
     cur ^= 1;
   }
   return cur;
+}
+
+int coop_sort_grid() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> grid;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = grid.find(dev);
+  if (it != grid.end()) return it->second;
+  int g = 0, coop = 0, sms = 0, per_sm = 0;
+  const int smem = kCoopTile * 12 + kCoopWarps * 256 * 4;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaFuncSetAttribute(coop_sort_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+      cudaFuncSetAttribute(coop_sort_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_sort_kernel<true>, kCoopThreads, smem) == cudaSuccess) {
+    int per_sm2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, coop_sort_kernel<false>, kCoopThreads, smem) ==
+        cudaSuccess)
+      per_sm = std::min(per_sm, per_sm2);
+    g = std::min(per_sm * sms, kCoopMaxGrid);
+  }
+  cudaGetLastError();  // a refused attribute only means: no cooperative sort
+  grid[dev] = g;
+  return g;
+}
+
+int launch_sort_coop(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
+                     const uint32_t *hist, uint32_t *scratch, int64_t scratch_words, uint32_t *bar, cudaStream_t st) {
+  const int passes = (hi_bit - lo_bit + 7) / 8;
+  if (passes < 1 || passes > kMaxPasses || lo_bit < 0) return -1;
+  const int G = coop_sort_grid();
+  if (G < 1 || (int64_t)2 * 256 * G > scratch_words) return -2;
+  CoopSortArgs a;
+  a.ctl = ctl;
+  a.keys[0] = keys[0];
+  a.keys[1] = keys[1];
+  a.vals[0] = vals[0];
+  a.vals[1] = vals[1];
+  a.cap = pair_cap;
+  a.lo_bit = lo_bit;
+  a.passes = passes;
+  a.last_mask = (1u << (hi_bit - lo_bit - 8 * (passes - 1))) - 1u;
+  a.hist = hist;
+  a.colhist = scratch;
+  a.offs = scratch + (int64_t)256 * G;
+  a.bar = bar;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(kCoopThreads);
+  cfg.dynamicSmemBytes = (size_t)(kCoopTile * (vals[0] ? 12 : 8) + kCoopWarps * 256 * 4);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = vals[0] ? cudaLaunchKernelEx(&cfg, coop_sort_kernel<true>, a)
+                                : cudaLaunchKernelEx(&cfg, coop_sort_kernel<false>, a);
+  if (e != cudaSuccess) return -3;
+  return passes & 1;
 }
 
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,

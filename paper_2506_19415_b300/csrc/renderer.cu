@@ -730,8 +730,10 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     const int64_t max_tiles = (r->dims.pair_cap + kSortTile - 1) / kSortTile;
     if (passes < 1 || passes > kMaxPasses || (int64_t)passes * max_tiles * 256 > r->dims.lookback_words)
       return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
-    const SortHist sh{r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback), max_tiles, r->at<uint32_t>(C.tile_ctr),
-                      lo_bit, passes};
+    // the cooperative sort needs no look-back words (the emission clears them otherwise)
+    const bool coop = r->prm.sort_mode == 0 && coop_sort_grid() > 0;
+    const SortHist sh{r->at<uint32_t>(C.hist), coop ? nullptr : r->at<uint32_t>(C.lookback), max_tiles,
+                      r->at<uint32_t>(C.tile_ctr), lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
                      keys[0], vals[0], r->dims.pair_cap, TileGeom{c.width, c.height, c.tile_w, c.tile_h}, gx, kf,
                      sh, r->at<uint64_t>(C.pieces),
@@ -739,11 +741,15 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     r->span_end(t, 5, st);  // scan reduce, scan blocks, scan offsets, emit, emit pieces
     uint32_t *no_vals[2] = {nullptr, nullptr};
     t = r->span_begin(VM3DGS_STAGE_SORT, st);
-    const int cur = launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
-                                       r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback),
-                                       r->at<uint32_t>(C.tile_ctr), st);
-    r->span_end(t, passes, st);
-    if (cur == -2) return fail(VM3DGS_E_CUDA, "sort shared-memory attribute refused");
+    const int cur = coop ? launch_sort_coop(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
+                                            r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback),
+                                            r->dims.lookback_words, r->at<uint32_t>(C.tile_ctr), st)
+                         : launch_sort_passes(ctl, keys, kf.packed ? no_vals : vals, r->dims.pair_cap, lo_bit, hi_bit,
+                                              r->at<uint32_t>(C.hist), r->at<uint32_t>(C.lookback),
+                                              r->at<uint32_t>(C.tile_ctr), st);
+    r->span_end(t, coop ? 1 : passes, st);
+    if (cur == -3) return fail(VM3DGS_E_CUDA, "cooperative sort launch refused");
+    if (cur == -2) return fail(VM3DGS_E_CUDA, coop ? "cooperative sort scratch too small" : "sort shared-memory attribute refused");
     if (cur < 0) return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
     uint2 *ranges = r->at<uint2>(C.ranges);
     uint32_t *order = r->at<uint32_t>(C.tile_order), *work = r->at<uint32_t>(C.work);

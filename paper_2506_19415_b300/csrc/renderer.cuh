@@ -250,6 +250,15 @@ void launch_scan_emit(const Ctl *ctl, Ctl *ctl_w, const Splats &sp, int64_t ncap
 // sorts the keys alone.  Returns the buffer holding the result.
 int launch_sort(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
                 uint32_t *hist, uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
+// All passes in one cooperative launch (the chunk-per-CTA sort with grid
+// barriers): hist holds the passes' digit counts of all pairs (counted by the
+// emission), scratch 2 x 256 x grid words, bar two zeroed words.  Returns the
+// buffer holding the result, -1 bad bits, -2 no cooperative launch or too
+// little scratch, -3 launch refused.
+int launch_sort_coop(Ctl *ctl, uint64_t *keys[2], uint32_t *vals[2], int64_t pair_cap, int lo_bit, int hi_bit,
+                     const uint32_t *hist, uint32_t *scratch, int64_t scratch_words, uint32_t *bar, cudaStream_t st);
+// CTAs of the cooperative sort on the current device (0: not available)
+int coop_sort_grid();
 // the same in two steps: digit histograms (0 or -1), then the passes
 int launch_sort_prep(Ctl *ctl, const uint64_t *keys, int64_t pair_cap, int lo_bit, int hi_bit, uint32_t *hist,
                      uint32_t *lookback, int64_t lookback_words, uint32_t *tile_ctr, cudaStream_t st);
