@@ -376,7 +376,7 @@ def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
         detail[k] = {"achieved": round(a, 1), "frac": round(a / peak, 4), "us_per_launch": round(t * 1e6, 2),
                      "algorithmic_bytes_per_launch": int(b), "per_unit": note}
     if alt_sort is not None:
-        detail["sort_onesweep_per_pass"] = alt_sort
+        detail["sort_cooperative"] = alt_sort
     coop = per_view < passes
     traffic = None if SORT_DRAM_BYTES_PER_PAIR_PASS is None else \
         int(SORT_DRAM_BYTES_PER_PAIR_PASS * pairs * passes / max(per_view, 1))
@@ -394,9 +394,10 @@ def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
     return out
 
 
-def onesweep_reference(v, scene, W, cams, warmup, steps, copy_stream, dist, pf, width, height, peaks):
-    """The same single-stream frames with the onesweep sort (a launch per
-    pass): its per-pass time and HBM fraction beside the cooperative sort's."""
+def coop_sort_reference(v, scene, W, cams, warmup, steps, copy_stream, dist, pf, width, height, peaks):
+    """The same single-stream frames with the cooperative sort (all passes
+    in one launch): its time per view and HBM fraction beside the onesweep
+    sort's (the default)."""
     rn = make_renderer(v, scene, W, True, width, height, sort_mode=1)
     res = run_arm(v, rn, cams, warmup, steps, copy_stream, timing=True, dist=dist, pf=pf, serial=True,
                   preroll=PREROLL)
@@ -404,13 +405,15 @@ def onesweep_reference(v, scene, W, cams, warmup, steps, copy_stream, dist, pf, 
     st = res["stats"]
     views = max(st["acc_views"], 1)
     i = v.STAGES.index("sort")
+    passes = -(-(st["key_tile_bits"] + st["key_depth_bits"]) // 8)
     t = ms[i] / max(launches[i], 1) / 1e3
-    b = st["acc_pairs"] / views * 16
+    b = st["acc_pairs"] / views * 16 * passes * views / max(launches[i], 1)
     a = b / t / 1e9 if t > 0 else 0.0
     del rn
-    return {"us_per_pass": round(t * 1e6, 2), "passes_per_view": launches[i] / views,
+    return {"us_per_launch": round(t * 1e6, 2), "launches_per_view": launches[i] / views,
             "sort_ms_per_view": round(ms[i] / views, 4), "achieved": round(a, 1),
-            "frac": round(a / peaks.get("hbm_gbs", 6400.0), 4), "ms_per_step_one_stream": round(res["ms"] / steps, 4)}
+            "frac": round(a / peaks.get("hbm_gbs", 6400.0), 4), "ms_per_step_one_stream": round(res["ms"] / steps, 4),
+            "kernel": "coop_sort_kernel (sort_mode 1)"}
 
 
 def prefetch_eval(v):
@@ -589,8 +592,8 @@ def gpu_main(args):
     hs = head["stats"]
     frames = max(hs["acc_frames"], 1)
     # (rank 0 only: the other ranks have returned, so no barrier here)
-    alt = onesweep_reference(v, scene, W, cams, args.warmup, min(args.steps, 100), copy_stream, None, pf, width,
-                             height, peaks)
+    alt = coop_sort_reference(v, scene, W, cams, args.warmup, min(args.steps, 100), copy_stream, None, pf, width,
+                              height, peaks)
     rl = roofline(v, ser["stage"], ser["stats"], peaks, scene.info.record_bytes16, width, height, alt)
     rl["timing"] = ("kernels timed by CUDA events in a single-stream pass over %d frames of the same walk "
                     "(bench.py); the timed headline loop itself records no per-stage events" % min(args.steps, 100))

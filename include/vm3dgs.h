@@ -125,9 +125,10 @@ typedef struct {
   int32_t separate_values; /* 0: the splat index rides in the low bits of the sort key whenever tile, depth and
                               index bits fit in 64 (a keys-only sort); 1: always sort (key, splat) pairs.  The
                               rendered image and the pairs read back are the same either way. */
-  int32_t sort_mode;       /* radix sort of a single-view render: 0 = all passes in one cooperative launch (chunk
-                              per CTA, grid barriers; the default where the device supports cooperative launches),
-                              1 = one onesweep launch per pass (decoupled look-back).  Same sorted pairs either way. */
+  int32_t sort_mode;       /* radix sort of a single-view render: 0 = one onesweep launch per pass (decoupled
+                              look-back; the default), 1 = all passes in one cooperative launch (a chunk per CTA,
+                              bounded grid barriers; where the device supports cooperative launches, else as 0).
+                              Same sorted pairs either way. */
 } vm3dgs_params;
 
 typedef struct {

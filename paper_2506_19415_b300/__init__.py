@@ -338,7 +338,7 @@ class RenderConfig:
     max_pairs: int = 0
     bg: tuple = (0.0, 0.0, 0.0)
     separate_values: bool = False   # True: always sort (key, splat) pairs instead of packed keys
-    sort_mode: int = 0              # 0: one cooperative launch for all passes; 1: a onesweep launch per pass
+    sort_mode: int = 0              # 0: a onesweep launch per pass; 1: one cooperative launch for all passes
 
     def struct(self) -> Params:
         p = Params()

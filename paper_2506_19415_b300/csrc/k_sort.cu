@@ -495,6 +495,20 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Lanes of the warp holding the same digit as this lane (d < 0: an empty
+// slot, in no lane's set): the AND of the eight ballots on the digit's bits
+// (a warp multisplit, cheaper here than the match instruction).
+__device__ __forceinline__ uint32_t digit_peers(int d) {
+  uint32_t peers = __ballot_sync(0xffffffffu, d >= 0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool bit = (d >> j) & 1;
+    const uint32_t bj = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bj : ~bj;
+  }
+  return peers;
+}
+
 // one radix digit per thread: the digit scans and count loads index by tid
 static_assert(kSortThreads == 256, "onesweep assumes one thread per 8-bit digit");
 
@@ -553,6 +567,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
+      // (the match instruction: the pairs of a splat share their depth
+      // digits, so groups are large and it is cheaper here than ballots)
       const int d = dg[it];
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
@@ -656,7 +672,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
 //           from the pass's digit histogram counted by the emission) + (pairs
 //           of digit d in earlier chunks)
 //   scatter the chunk, in sub-tiles of kCoopTile pairs in order, ranked
-//           stably (warp match + per-warp digit counters, as in the onesweep
+//           stably (warp multisplit by ballots + per-warp digit counters taken
+//           by one shared atomic per digit group; otherwise as in the onesweep
 //           pass) and written through shared memory to offs + the digit's
 //           running count in the chunk.
 // No look-back chain and one launch for all passes: the pass costs two reads
@@ -760,10 +777,35 @@ __global__ void __launch_bounds__(kCoopThreads, 2) coop_sort_kernel(CoopSortArgs
     uint32_t *vout = odd ? a.vals[0] : a.vals[1];
     const int shift = a.lo_bit + 8 * p;
     const uint32_t dmask = p == a.passes - 1 ? a.last_mask : 255u;
-    // ---- count
+    // ---- count (eight independent loads per thread in flight; the first
+    // sub-tile is loaded as the scatter reads it and kept in registers)
     for (int d = tid; d < 256; d += kCoopThreads) s_hist[d] = 0;
     __syncthreads();
-    for (int64_t i = lo + tid; i < hi; i += kCoopThreads) atomicAdd(&s_hist[(kin[i] >> shift) & dmask], 1u);
+    {
+      uint64_t k0[kCoopItems];
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        const int64_t idx = lo + (int64_t)warp * 32 * kCoopItems + it * 32 + lane;
+        k0[it] = idx < hi ? kin[idx] : 0ull;
+      }
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        // parked where the scatter's first sub-tile reads it (s_keys is free until then)
+        s_keys[warp * 32 * kCoopItems + it * 32 + lane] = k0[it];
+        if (lo + (int64_t)warp * 32 * kCoopItems + it * 32 + lane < hi) atomicAdd(&s_hist[(k0[it] >> shift) & dmask], 1u);
+      }
+    }
+    for (int64_t t0 = lo + kCoopTile; t0 < hi; t0 += kCoopTile) {
+      uint32_t dd[kCoopItems];
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it) {
+        const int64_t idx = t0 + (int64_t)it * kCoopThreads + tid;
+        dd[it] = idx < hi ? (uint32_t)((kin[idx] >> shift) & dmask) : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int it = 0; it < kCoopItems; ++it)
+        if (dd[it] != 0xFFFFFFFFu) atomicAdd(&s_hist[dd[it]], 1u);
+    }
     __syncthreads();
     for (int d = tid; d < 256; d += kCoopThreads) a.colhist[(int64_t)d * G + b] = s_hist[d];
     if (!(ok = coop_grid_sync(a.bar, ++nbar * (uint32_t)G, &s_ok))) break;
@@ -793,20 +835,20 @@ __global__ void __launch_bounds__(kCoopThreads, 2) coop_sort_kernel(CoopSortArgs
       for (int it = 0; it < kCoopItems; ++it) {
         const int64_t idx = t0 + (int64_t)warp * 32 * kCoopItems + it * 32 + lane;
         const bool valid = idx < hi;
-        k[it] = valid ? kin[idx] : 0ull;
+        k[it] = t0 == lo ? s_keys[warp * 32 * kCoopItems + it * 32 + lane] : (valid ? kin[idx] : 0ull);
         v[it] = (VALS && valid) ? vin[idx] : 0u;
         dg[it] = valid ? (int)((k[it] >> shift) & dmask) : -1;
       }
 #pragma unroll
       for (int it = 0; it < kCoopItems; ++it) {
         const int d = dg[it];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d >= 0) before = s_wc[warp * 256 + d];
-        rk[it] = before + __popc(peers & lt);
-        __syncwarp();
-        if (d >= 0 && (peers & lt) == 0) s_wc[warp * 256 + d] = before + __popc(peers);
-        __syncwarp();
+        // the lowest lane of each digit group takes the group's places from the
+        // warp's counter (a shared atomic returns the places taken before it)
+        const uint32_t peers = digit_peers(d);
+        const int leader = peers ? __ffs(peers) - 1 : lane;
+        uint32_t old = 0;
+        if (d >= 0 && leader == lane) old = atomicAdd(&s_wc[warp * 256 + d], (uint32_t)__popc(peers));
+        rk[it] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
       }
       __syncthreads();
       // per digit: exclusive prefix over the warps, and the sub-tile's count

@@ -731,7 +731,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     if (passes < 1 || passes > kMaxPasses || (int64_t)passes * max_tiles * 256 > r->dims.lookback_words)
       return fail(VM3DGS_E_CAPACITY, "sort look-back area too small");
     // the cooperative sort needs no look-back words (the emission clears them otherwise)
-    const bool coop = r->prm.sort_mode == 0 && coop_sort_grid() > 0;
+    const bool coop = r->prm.sort_mode == 1 && coop_sort_grid() > 0;
     const SortHist sh{r->at<uint32_t>(C.hist), coop ? nullptr : r->at<uint32_t>(C.lookback), max_tiles,
                       r->at<uint32_t>(C.tile_ctr), lo_bit, passes};
     launch_scan_emit(ctl, ctl, sp, r->dims.ncap, r->at<uint32_t>(C.block_sums), r->at<uint32_t>(C.offsets),
