@@ -401,9 +401,12 @@ int vm3dgs_prefetch_features(vm3dgs_renderer *r, int32_t n_out, const vm3dgs_cam
                              float *x_dev, int32_t *base_dev, void *stream);
 /* Training targets from the last vm3dgs_render_feedback for a window:
  * y_dev[j] = 1 if page base + j was requested, else 0; mask_dev[j] = 1 if
- * base + j is a page of the scene, else 0 (base read from base_dev). */
+ * base + j is a page of the scene, else 0 (base read from base_dev).  With
+ * accumulate != 0, y_dev[j] becomes the OR (maximum) of its value and that
+ * label, so calls over the frames of a horizon leave the pages requested in
+ * any of them. */
 int vm3dgs_prefetch_labels(vm3dgs_renderer *r, int32_t n_out, const int32_t *base_dev, float *y_dev, float *mask_dev,
-                           void *stream);
+                           int32_t accumulate, void *stream);
 /* Prefetch for the next frame, after vm3dgs_render of this one: builds the
  * input as vm3dgs_prefetch_features does, runs the network, and spends the
  * staging budget this frame left unused on the window pages whose logit

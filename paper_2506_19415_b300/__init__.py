@@ -120,7 +120,7 @@ _SIGS = {
     "vm3dgs_prefetcher_train_step": [c_p, c_p, c_p, c_p, c_i32, c_f, c_p, c_p],
     "vm3dgs_prefetcher_params": [c_p, c_i32, c_p, c_i64, c_p],
     "vm3dgs_prefetch_features": [c_p, c_i32, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_p, c_p, c_p],
-    "vm3dgs_prefetch_labels": [c_p, c_i32, c_p, c_p, c_p, c_p],
+    "vm3dgs_prefetch_labels": [c_p, c_i32, c_p, c_p, c_p, c_i32, c_p],
     "vm3dgs_prefetch": [c_p, c_p, ctypes.POINTER(Camera), ctypes.POINTER(Camera), c_f, c_p, c_p],
     "vm3dgs_sort_pairs_noalloc": [c_p, c_p, c_i64, c_i32, c_p, c_p],
     "vm3dgs_render_batched": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_p],
@@ -582,9 +582,9 @@ def vm3dgs_prefetch_features(r: "Renderer", n_out, cam, prev, x_out, base_out=No
                                          _stream_ptr(stream)))
 
 
-def vm3dgs_prefetch_labels(r: "Renderer", n_out, base_dev, y_out, mask_out, stream=None):
+def vm3dgs_prefetch_labels(r: "Renderer", n_out, base_dev, y_out, mask_out, accumulate=False, stream=None):
     _check(_lib.vm3dgs_prefetch_labels(r.h, n_out, c_p(base_dev.data_ptr()), c_p(y_out.data_ptr()),
-                                       c_p(mask_out.data_ptr()), _stream_ptr(stream)))
+                                       c_p(mask_out.data_ptr()), 1 if accumulate else 0, _stream_ptr(stream)))
 
 
 def vm3dgs_prefetch(r: "Renderer", p: Prefetcher, cam, prev, threshold=0.0, stream=None, copy_stream=None):

@@ -71,13 +71,16 @@ __global__ void __launch_bounds__(RT) features_kernel(FeatArgs a) {
   }
 }
 
+// labels of the window's pages; with accumulate, OR-ed into what y holds
+// (the pages requested in any frame of a horizon)
 __global__ void labels_kernel(const uint32_t *req, int32_t NP, int32_t n_out, const int32_t *base_p, float *y,
-                              float *mask) {
+                              float *mask, int accumulate) {
   const int base = *base_p;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_out; j += gridDim.x * blockDim.x) {
     const int p = base + j;
     const bool in = p < NP;
-    y[j] = (in && req[p] != 0u) ? 1.0f : 0.0f;
+    const float l = (in && req[p] != 0u) ? 1.0f : 0.0f;
+    y[j] = accumulate ? fmaxf(y[j], l) : l;
     mask[j] = in ? 1.0f : 0.0f;
   }
 }
@@ -325,12 +328,12 @@ extern "C" int vm3dgs_prefetch_features(vm3dgs_renderer *r, int32_t n_out, const
 }
 
 extern "C" int vm3dgs_prefetch_labels(vm3dgs_renderer *r, int32_t n_out, const int32_t *base_dev, float *y_dev,
-                                      float *mask_dev, void *stream) {
+                                      float *mask_dev, int32_t accumulate, void *stream) {
   if (!r || !base_dev || !y_dev || !mask_dev) return fail(VM3DGS_E_INVAL, "null argument");
   if (n_out <= 0) return fail(VM3DGS_E_INVAL, "n_out must be positive");
   labels_kernel<<<(n_out + 255) / 256, 256, 0, (cudaStream_t)stream>>>(r->req_buf(r->fb_buf),
                                                                       (int32_t)r->dims.NP, n_out, base_dev, y_dev,
-                                                                      mask_dev);
+                                                                      mask_dev, accumulate ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VM3DGS_OK : fail(VM3DGS_E_CUDA, cudaGetErrorString(e));
 }

@@ -27,16 +27,15 @@ def make_dataset(v, r, paths, n_out, n_in, horizon=1):
     M = torch.empty((n, n_out), dtype=torch.float32, device=dev)
     T = max(len(p) for p in paths)
     base = torch.empty((T, 1), dtype=torch.int32, device=dev)
-    ytmp = torch.empty((n_out,), dtype=torch.float32, device=dev)
     k0 = 0
     for path in paths:
         for t, cam in enumerate(path):
             r.render_feedback([cam])
-            # frame t is within the horizon of the samples of frames t-horizon .. t-1
+            # frame t is within the horizon of the samples of frames t-horizon .. t-1:
+            # the labels kernel ORs this frame's requests into theirs
             for s_ in range(max(0, t - horizon), t):
                 k = k0 + s_
-                v.vm3dgs_prefetch_labels(r, n_out, base[s_], ytmp, M[k])
-                torch.maximum(Y[k], ytmp, out=Y[k])
+                v.vm3dgs_prefetch_labels(r, n_out, base[s_], Y[k], M[k], accumulate=True)
             if t + 1 < len(path):
                 v.vm3dgs_prefetch_features(r, n_out, cam, path[t - 1] if t > 0 else cam, X[k0 + t], base[t])
         k0 += len(path) - 1

@@ -118,6 +118,10 @@ def test_features_and_labels(v):
     m = torch.empty(n_out, device="cuda")
     v.vm3dgs_prefetch_labels(r, n_out, base, y, m)
     req = r.debug(v.DBG_REQ, np.uint32)
+    # accumulated labels: the OR with what y already holds
+    y2 = torch.zeros(n_out, device="cuda")
+    y2[::3] = 1.0
+    v.vm3dgs_prefetch_labels(r, n_out, base, y2, m, accumulate=True)
     cen = rs.page_centroids(sc)
     pos = cams[1].campos.astype(np.float32)
     d2 = ((cen[:, :3] - pos) ** 2).sum(1)
@@ -133,6 +137,9 @@ def test_features_and_labels(v):
     np.testing.assert_array_equal(x.cpu().numpy()[12:], np.float32(hist))
     yy = np.array([1.0 if b + j < sc.n_pages and req[b + j] else 0.0 for j in range(n_out)], np.float32)
     np.testing.assert_array_equal(y.cpu().numpy(), yy)
+    want2 = yy.copy()
+    want2[::3] = 1.0
+    np.testing.assert_array_equal(y2.cpu().numpy(), want2)
     np.testing.assert_array_equal(m.cpu().numpy(), (b + np.arange(n_out) < sc.n_pages).astype(np.float32))
 
 
@@ -179,6 +186,60 @@ def test_prefetch_placement_parity(v):
         for (pg, l, e, s) in copies:
             np.testing.assert_array_equal(pool[e], host[pg])
     assert r.stats()["acc_prefetched_pages"] > 0
+
+
+def test_prefetch_placement_parity_lod(v):
+    """As above on a city scene with three LOD levels (pages of 512, fanout 8)
+    and LOD on: the level of each prefetch candidate comes from the
+    screen-space-error rule on the page's sphere, so levels 1 and 2 are
+    prefetched too (packed eight or 64 to an entry); the page table and the
+    pool's sub-slots equal the oracle's after every frame."""
+    from _common import city_cam, city_scene
+    raw, sc = city_scene(levels=3, fanout=8, page_size=512)
+    scene = import_scene(v, raw, sc)
+    # a pool larger than the view's demand and a budget that catches up with
+    # it after a few frames, so budget and unused entries are left to prefetch
+    n_out = 128
+    W, H = 320, 180
+    P = 200
+    rec = scene.info.record_bytes
+    budget = 60 * 512 * rec
+    r = v.Renderer(scene, v.RenderConfig(max_width=W, max_height=H, lod=True, staging_bytes=budget, tau0=16.0),
+                   pool_slots=P)
+    p = v.Prefetcher(v.MlpShape(n_in=12 + n_out // 16, n_hidden=32, n_out=n_out, max_batch=1, seed=1, lr=0.0))
+    rng = np.random.default_rng(9)
+    b3 = rng.permutation(n_out).astype(np.float32) / n_out - 0.3
+    Pp = p.params()
+    Pp["W3"][:] = 0
+    Pp["b3"][:] = b3
+    p.set_params(Pp)
+    rp = rs.ResidencyParams(n_entries=P, page_size=512, levels=3, fanout=8, record_bytes=rec, budget_bytes=budget,
+                            lod=True, tau0=16.0)
+    pt = rs.PageTable(rp)
+    cen = rs.page_centroids(sc)
+    cams = [city_cam(160.0, k, width=W, height=H) for k in range(8)]
+    host = [scene.pages(l) for l in range(3)]
+    levels_seen = set()
+    for t, cam in enumerate(cams):
+        prev = cams[t - 1] if t else cam
+        r.render_feedback([cam])
+        r.update_residency()
+        v.vm3dgs_prefetch(r, p, cam, prev, 0.0)
+        ref = oracle.frame(sc, pt, cam, ds=4, render_image=False)
+        d2 = ((cen[:, :3] - cam.campos.astype(np.float32)) ** 2).sum(1)
+        base = min(max(int(np.argmin(d2)) - n_out // 2, 0), max(sc.n_pages - n_out, 0))
+        copies = rs.prefetch(pt, b3, base, 0.0, ref["req"], sc.err, cen, cam.campos, cam.fy,
+                             budget - ref["update"]["streamed_bytes"], pt.frame - 1)
+        levels_seen |= {l for (_, l, _, _) in copies}
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_SLOT, np.int32).reshape(P, 64), pt.slot)
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_LAST, np.int32), pt.last_used)
+        np.testing.assert_array_equal(r.debug(v.DBG_PT_LOD, np.int32), pt.lod)
+        pool = r.debug(v.DBG_POOL, np.uint8).reshape(P, -1)
+        for (pg, l, e, s_) in copies:
+            blk = host[l][pg]
+            np.testing.assert_array_equal(pool[e, s_ * len(blk):(s_ + 1) * len(blk)], blk)
+    assert r.stats()["acc_prefetched_pages"] > 0
+    assert levels_seen & {1, 2}, levels_seen
 
 
 def test_prefetcher_reduces_misses(v):
