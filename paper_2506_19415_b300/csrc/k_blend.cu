@@ -4,7 +4,12 @@
 // in shared memory in batches; a pixel stops when its transmittance would
 // fall below 1e-4, the CTA stops when every pixel has.  alpha = min(0.99, o exp(power)); splats
 // with alpha < 1/255 are skipped; the image is C + T * background, CHW.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "renderer.cuh"
+#include "tma.cuh"
 
 namespace vm {
 namespace {
@@ -18,10 +23,10 @@ namespace {
 #define LOG2_SKIP (-7.99435343685886f)  /* log2(1/255) */
 
 __device__ __forceinline__ void stage(const Splats &sp, uint32_t g, float4 &a, float4 &b, float &c) {
-  const float4 s0 = sp.s0[g], s1 = sp.s1[g];
+  const float4 s0 = sp.rec[3 * g], s1 = sp.rec[3 * g + 1];
   a = make_float4(s0.x, s0.y, -0.5f * LOG2E * s0.z, -LOG2E * s0.w);
   b = make_float4(-0.5f * LOG2E * s1.x, __log2f(s1.y), s1.z, s1.w);
-  c = sp.s2[g];
+  c = sp.rec[3 * g + 2].x;
 }
 
 // Box (x0, x1, y0, y1) outside which a splat has alpha < 1/255 with a margin
@@ -31,9 +36,9 @@ __device__ __forceinline__ void stage(const Splats &sp, uint32_t g, float4 &a, f
 // |dx| <= sqrt(tau C / det M), |dy| <= sqrt(tau A / det M), taken here for
 // 1.01 tau + 0.05 and widened by 1% + 0.1 px.  Splats whose conic is too
 // ill-conditioned for that margin (eigenvalue ratio above 1e4) get an
-// unbounded box; those with o < 0.999 / 255 an empty one.
-__device__ __forceinline__ float4 alpha_box(const Splats &sp, uint32_t g) {
-  const float4 s0 = sp.s0[g], s1 = sp.s1[g];
+// unbounded box; those with o < 0.999 / 255 an empty one.  s0, s1: the
+// first two float4 of the splat's record.
+__device__ __forceinline__ float4 alpha_box(const float4 &s0, const float4 &s1) {
   const float A = s0.z, B = s0.w, C = s1.x, o = s1.y;
   if (!(o * 255.0f >= 0.999f)) return make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
   const float det = A * C - B * B, m = 0.5f * (A + C);
@@ -136,22 +141,40 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2 *ranges, i
   }
 }
 
+constexpr int kBlendPolls = 1 << 20;  // bound of each staging wait (try_wait polls)
+
+// Staged splat j of a batch: float4 index of its record in the staging
+// area, where records come in groups of four, 256 bytes apart (the 128-byte
+// aligned destinations of the gather loads), 48 bytes each within a group.
+__device__ __forceinline__ int rec_slot(int j) { return (j >> 2) * 16 + (j & 3) * 3; }
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, const uint32_t *vals,
                                                           const uint64_t *packed, uint32_t idx_mask, Splats sp,
                                                           uint32_t ncap, vm3dgs_camera cam, float bg0, float bg1,
                                                           float bg2, float *img, const uint32_t *order,
-                                                          uint32_t ntiles, uint32_t *work) {
+                                                          uint32_t ntiles, uint32_t *work,
+                                                          const __grid_constant__ CUtensorMap rec_map, int use_tma,
+                                                          Ctl *ctl) {
   static_assert(TW % 8 == 0 && TH % 8 == 0, "tiles are made of 8x8 blocks");
   constexpr int NT = TW * TH / 2, BS = 2 * NT, NW = NT / 32;
-  __shared__ float4 s0[BS];
-  __shared__ float4 s1[BS];
-  __shared__ float s2[BS];
+  // the batch's records: raw as loaded, then rewritten in place for the
+  // blend (log2-domain conic and opacity)
+  __shared__ __align__(128) float4 s_rec[BS / 4 * 16];
+  __shared__ __align__(16) uint64_t s_key[BS + 2];  // the batch's sorted keys (or values), bulk-copied
+  __shared__ __align__(8) uint64_t s_bar[2];        // [0] keys, [1] records
   __shared__ uint8_t s_blocks[BS];      // bit w: the alpha box meets warp w's block
   __shared__ uint16_t s_list[NW][BS];   // per warp, the staged splats meeting its block, in order
   __shared__ uint32_t s_tile;
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
+  if (use_tma && threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t ph = 0;    // parity of the staging barriers' current phase (each completes once per batch)
   bool first = true;  // a CTA's first tile is its index in the order; later ones come from the counter
   for (;;) {
   if (threadIdx.x == 0) {
@@ -175,20 +198,67 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
   float T1 = 1.0f, A1 = 0.0f, B1 = 0.0f, D1 = 0.0f;
   for (int r0 = 0; r0 < n; r0 += BS) {
     if (__syncthreads_count(done0 && done1) == NT) break;
+    const int cnt = min(BS, n - r0);
+    const int64_t first_pair = (int64_t)rg.x + r0;
+    if (use_tma) {
+      // the batch's keys: one bulk copy of the 16-byte-aligned span around them
+      const int esz = packed ? 8 : 4, per16 = 16 / esz;
+      const int64_t a0 = first_pair & ~(int64_t)(per16 - 1);
+      const int lead = (int)(first_pair - a0);
+      const uint32_t bytes = (uint32_t)(((lead + cnt) * esz + 15) & ~15);
+      if (threadIdx.x == 0) {
+        proxy_fence_shared();
+        mbar_arrive_expect(&s_bar[0], bytes);
+        bulk_load(s_key, packed ? (const void *)(packed + a0) : (const void *)(vals + a0), bytes, &s_bar[0]);
+      }
+      bool ok = mbar_wait(&s_bar[0], ph, kBlendPolls);
+      // the records: thread t gathers those of staged splats 4t .. 4t+3
+      const int ng = (cnt + 3) / 4;
+      if (threadIdx.x == 0) mbar_arrive_expect(&s_bar[1], (uint32_t)(ng * 4 * 48));
+      const uint32_t *k32 = reinterpret_cast<const uint32_t *>(s_key);
+      for (int t = threadIdx.x; t < ng; t += NT) {
+        int rows[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = lead + min(4 * t + q, cnt - 1);
+          uint32_t g = packed ? (uint32_t)s_key[j] & idx_mask : k32[j];
+          rows[q] = (int)(g < ncap ? g : 0u);  // (only after a timed-out sort or wait)
+        }
+        proxy_fence_shared();
+        tma_gather4(&s_rec[t * 16], &rec_map, 0, rows[0], rows[1], rows[2], rows[3], &s_bar[1]);
+      }
+      ok = mbar_wait(&s_bar[1], ph, kBlendPolls) && ok;
+      if (!ok) {
+        atomicCAS(&ctl->status, 0, VM3DGS_E_TIMEOUT);
+        mbar_wait(&s_bar[1], ph, kBlendPolls);  // the gathers still in flight land before the area is reused
+      }
+      ph ^= 1u;
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = (int)threadIdx.x + h * NT;
+        if (k < cnt) {
+          uint32_t g = packed ? (uint32_t)packed[first_pair + k] & idx_mask : vals[first_pair + k];
+          if (g >= ncap) g = 0;  // only after a timed-out sort
+          const int o = rec_slot(k);
+          s_rec[o] = sp.rec[3 * g];
+          s_rec[o + 1] = sp.rec[3 * g + 1];
+          s_rec[o + 2] = sp.rec[3 * g + 2];
+        }
+      }
+      __syncthreads();
+    }
+    // rewrite each staged record for the blend, and mark the 8x8 blocks
+    // (pixel centres) of the tile that its alpha box meets
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int k = (int)threadIdx.x + h * NT, idx = r0 + k;
-      if (idx < n) {
-        uint32_t g = packed ? (uint32_t)packed[rg.x + idx] & idx_mask : vals[rg.x + idx];
-        if (g >= ncap) g = 0;  // only after a timed-out sort
-        float4 a, b;
-        float c;
-        stage(sp, g, a, b, c);
-        s0[k] = a;
-        s1[k] = b;
-        s2[k] = c;
-        // the 8x8 blocks (pixel centres) of the tile that the alpha box meets
-        const float4 bb = alpha_box(sp, g);
+      const int k = (int)threadIdx.x + h * NT;
+      if (k < cnt) {
+        const int o = rec_slot(k);
+        const float4 r0v = s_rec[o], r1v = s_rec[o + 1];
+        const float4 bb = alpha_box(r0v, r1v);
+        s_rec[o] = make_float4(r0v.x, r0v.y, -0.5f * LOG2E * r0v.z, -LOG2E * r0v.w);
+        s_rec[o + 1] = make_float4(-0.5f * LOG2E * r1v.x, __log2f(r1v.y), r1v.z, r1v.w);
         uint32_t m = 0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
@@ -200,7 +270,6 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
       }
     }
     __syncthreads();
-    const int cnt = min(BS, n - r0);
     // this warp's list: the staged splats whose alpha box meets its block
     int nl = 0;
     for (int c0 = 0; c0 < cnt; c0 += 32) {
@@ -212,8 +281,8 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
     }
     __syncwarp();
     for (int i = 0; i < nl && !(done0 && done1); ++i) {
-      const int j = s_list[warp][i];
-      const float4 a = s0[j], b = s1[j];
+      const int o = rec_slot(s_list[warp][i]);
+      const float4 a = s_rec[o], b = s_rec[o + 1];
       // both pixels share x: the exponents of the two in packed FP32 pairs
       const float dx = a.x - fx;
       const float2 dy = __fadd2_rn(make_float2(a.y, a.y), make_float2(-fy0, -fy1));
@@ -225,7 +294,7 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
       const bool go0 = !done0 && q.x <= 0.0f && t.x >= LOG2_SKIP;
       const bool go1 = !done1 && q.y <= 0.0f && t.y >= LOG2_SKIP;
       if (!(go0 || go1)) continue;
-      const float c = s2[j];
+      const float c = s_rec[o + 2].x;
       if (go0) accumulate(t.x, b, c, T0, A0, B0, D0, done0);
       if (go1) accumulate(t.y, b, c, T1, A1, B1, D1, done1);
     }
@@ -328,24 +397,50 @@ void launch_blend_batched(const uint2 *ranges, const uint32_t *vals, const Splat
       ranges, vals, sp, (uint32_t)ncap_total, vt, bg[0], bg[1], bg[2], order, work);
 }
 
+bool encode_rec_map(const float4 *rec, int64_t n, CUtensorMap *out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // rows of 12 floats (the 48-byte record), one row per box (gather loads)
+  const cuuint64_t dim[2] = {12, (cuuint64_t)(n > 0 ? n : 1)};
+  const cuuint64_t str[1] = {48};
+  const cuuint32_t box[2] = {12, 1}, estr[2] = {1, 1};
+  return enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float4 *>(rec), dim, str, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
                   const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
-                  uint32_t *order, uint32_t *work, cudaStream_t st) {
+                  uint32_t *order, uint32_t *work, const CUtensorMap *rec_map, Ctl *ctl, cudaStream_t st) {
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w, gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
   const int nt = gx * gy;
   const uint32_t nc = (uint32_t)ncap;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  const CUtensorMap &map = rec_map ? *rec_map : none;
+  const int tma = rec_map ? 1 : 0;
   prefer_shared((const void *)blend_kernel<16, 16>);
   prefer_shared((const void *)blend_kernel<8, 8>);
   prefer_shared((const void *)blend_kernel<32, 8>);
   if (cam.tile_w == 16 && cam.tile_h == 16)
     blend_kernel<16, 16><<<wave_grid((const void *)blend_kernel<16, 16>, 128, 0, nt, 1), 128, 0, st>>>(
-        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work, map, tma,
+        ctl);
   else if (cam.tile_w == 8 && cam.tile_h == 8)
     blend_kernel<8, 8><<<wave_grid((const void *)blend_kernel<8, 8>, 32, 0, nt, 1), 32, 0, st>>>(
-        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work, map, tma,
+        ctl);
   else
     blend_kernel<32, 8><<<wave_grid((const void *)blend_kernel<32, 8>, 128, 0, nt, 1), 128, 0, st>>>(
-        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work);
+        ranges, vals, packed, idx_mask, sp, nc, cam, bg[0], bg[1], bg[2], image, order, (uint32_t)nt, work, map, tma,
+        ctl);
 }
 
 }  // namespace vm

@@ -227,9 +227,9 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
     s += 0.5f;
     rgb[c] = s > 0.0f ? s : 0.0f;
   }
-  sp.s0[out] = make_float4(pu, pv, ia, ib);
-  sp.s1[out] = make_float4(ic, o, rgb[0], rgb[1]);
-  sp.s2[out] = rgb[2];
+  sp.rec[3 * out] = make_float4(pu, pv, ia, ib);
+  sp.rec[3 * out + 1] = make_float4(ic, o, rgb[0], rgb[1]);
+  sp.rec[3 * out + 2] = make_float4(rgb[2], 0.0f, 0.0f, 0.0f);
   sp.depth[out] = __float_as_uint(tz);
   sp.radius[out] = r;
   sp.rect[2 * out] = (uint32_t)x0 | ((uint32_t)x1 << 16);

@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
           tx = x0 + (int)(qt % (uint32_t)w);
           ty = y0 + (int)(qt / (uint32_t)w);
         } else {
-          const float4 s0 = sp.s0[si];
-          const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.s1[si].x);
+          const float4 s0 = sp.rec[3 * si];
+          const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.rec[3 * si + 1].x);
           const int2 t = nth_tile_by_rows(el, q, x0, x1, y0, y1, tg);
           tx = t.x;
           ty = t.y;
@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats
       }
       continue;
     }
-    const float4 s0 = sp.s0[i];
-    const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.s1[i].x);
+    const float4 s0 = sp.rec[3 * i];
+    const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.rec[3 * i + 1].x);
     uint32_t base = 0;  // pairs in the rows before this group of 32
     for (int r0 = y0; r0 < y1 && base < qb; r0 += 32) {
       const int ty = r0 + lane;

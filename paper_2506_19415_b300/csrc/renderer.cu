@@ -175,9 +175,7 @@ Layout make_layout(const Dims &d) {
   for (int k = 0; k < kContexts; ++k) {
     CtxLayout &C = L.cx[k];
     C.ctl = take(sizeof(Ctl));
-    C.splat_s0 = take(16 * N);
-    C.splat_s1 = take(16 * N);
-    C.splat_s2 = take(4 * N);
+    C.splat_rec = take(48 * N);
     C.splat_depth = take(4 * N);
     C.splat_rect = take(8 * N);
     C.splat_touched = take(4 * N);
@@ -205,9 +203,7 @@ Layout make_layout(const Dims &d) {
 Splats splats_of(const vm3dgs_renderer *r, int k) {
   const CtxLayout &C = r->lay.cx[k];
   Splats s;
-  s.s0 = r->at<float4>(C.splat_s0);
-  s.s1 = r->at<float4>(C.splat_s1);
-  s.s2 = r->at<float>(C.splat_s2);
+  s.rec = r->at<float4>(C.splat_rec);
   s.depth = r->at<uint32_t>(C.splat_depth);
   s.rect = r->at<uint32_t>(C.splat_rect);
   s.touched = r->at<uint32_t>(C.splat_touched);
@@ -318,6 +314,9 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
                                   cudaMemcpyHostToDevice), "copy", &rc);
   }
   r->maps_ok = encode_proj_maps(s, r->pool, P, r->fp16, &r->maps);
+  r->rec_maps_ok = true;
+  for (int k = 0; k < kContexts; ++k)
+    r->rec_maps_ok = r->rec_maps_ok && encode_rec_map(r->at<float4>(L.cx[k].splat_rec), d.ncap, &r->rec_map[k]);
   // a box around every page's sphere (centroid, radius), hence around every
   // Gaussian mean of every level: it bounds the depth of any splat
   for (int a = 0; a < 3; ++a) { r->gbox_lo[a] = 0.0; r->gbox_hi[a] = 0.0; }
@@ -760,7 +759,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
     t = r->span_begin(VM3DGS_STAGE_BLEND, st);
     const uint32_t idx_mask = kf.ib >= 32 ? 0xFFFFFFFFu : (uint32_t)((1ull << kf.ib) - 1ull);
     launch_blend(ranges, vals[cur], kf.packed ? keys[cur] : nullptr, idx_mask, sp, r->dims.ncap, c, r->prm.bg,
-                 images[v], order, work + 1, st);
+                 images[v], order, work + 1, r->rec_maps_ok ? &r->rec_map[k] : nullptr, ctl, st);
     r->span_end(t, 1, st);
     r->kf = kf;
     r->sorted_buf = cur;
@@ -944,19 +943,15 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
       if (needed) *needed = n;
       if (!dst) return VM3DGS_OK;
       if (bytes < n) return fail(VM3DGS_E_CAPACITY, "destination too small");
-      std::vector<float4> a(N), b(N);
-      std::vector<float> cc(N);
-      if (N) {
-        bool ok = cuda_ok(cudaMemcpy(a.data(), r->at<void>(C.splat_s0), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
-                  cuda_ok(cudaMemcpy(b.data(), r->at<void>(C.splat_s1), 16 * N, cudaMemcpyDeviceToHost), "debug", &rc) &&
-                  cuda_ok(cudaMemcpy(cc.data(), r->at<void>(C.splat_s2), 4 * N, cudaMemcpyDeviceToHost), "debug", &rc);
-        if (!ok) return rc;
-      }
+      std::vector<float4> rec(3 * N);
+      if (N && !cuda_ok(cudaMemcpy(rec.data(), r->at<void>(C.splat_rec), 48 * N, cudaMemcpyDeviceToHost), "debug", &rc))
+        return rc;
       float *o = (float *)dst;
       for (int64_t i = 0; i < N; ++i) {
-        if (what == VM3DGS_DBG_SPLAT_XY) { o[2 * i] = a[i].x; o[2 * i + 1] = a[i].y; }
-        else if (what == VM3DGS_DBG_SPLAT_CONIC) { o[4 * i] = a[i].z; o[4 * i + 1] = a[i].w; o[4 * i + 2] = b[i].x; o[4 * i + 3] = b[i].y; }
-        else { o[3 * i] = b[i].z; o[3 * i + 1] = b[i].w; o[3 * i + 2] = cc[i]; }
+        const float4 &a = rec[3 * i], &b = rec[3 * i + 1], &c3 = rec[3 * i + 2];
+        if (what == VM3DGS_DBG_SPLAT_XY) { o[2 * i] = a.x; o[2 * i + 1] = a.y; }
+        else if (what == VM3DGS_DBG_SPLAT_CONIC) { o[4 * i] = a.z; o[4 * i + 1] = a.w; o[4 * i + 2] = b.x; o[4 * i + 3] = b.y; }
+        else { o[3 * i] = b.z; o[3 * i + 1] = b.w; o[3 * i + 2] = c3.x; }
       }
       return VM3DGS_OK;
     }

@@ -36,9 +36,7 @@ struct Ctl {
 };
 
 struct Splats {
-  float4 *s0;        // (x, y, A, B)
-  float4 *s1;        // (C, opacity, r, g)
-  float *s2;         // b
+  float4 *rec;       // [3] per splat, one 48-byte record: (x, y, A, B), (C, opacity, r, g), (b, 0, 0, 0)
   uint32_t *depth;   // float bits of view z
   uint32_t *rect;    // [2] per splat: x0 | x1 << 16, y0 | y1 << 16
   uint32_t *touched; // tiles covered (0 = culled)
@@ -52,7 +50,7 @@ struct Splats {
 // status).  Two contexts let the projection of frame t+1 run while frame t
 // is still sorted and blended.
 struct CtxLayout {
-  int64_t ctl, splat_s0, splat_s1, splat_s2, splat_depth, splat_rect, splat_touched, splat_radius, splat_tmask,
+  int64_t ctl, splat_rec, splat_depth, splat_rect, splat_touched, splat_radius, splat_tmask,
       block_sums, offsets, keys0, keys1, vals0, vals1, ranges, work, tile_order, hist, lookback, tile_ctr, pieces,
       piece_ctr;
 };
@@ -279,9 +277,16 @@ void launch_prefetch_features(const vm3dgs_renderer *r, const uint32_t *req, int
 // The splat of pair j is vals[j], or the low bits (idx_mask) of packed[j]
 // when packed is not null; tiles are taken in `order` from the counter *work
 // (reset by launch_tile_order).
+// With rec_map (the tensor map of the context's splat records, rows of 48
+// bytes) each batch of the tile's splats is staged by TMA: one bulk copy of
+// its sorted keys, then gather loads of four records each; without, by plain
+// loads.  A staging wait that expires records VM3DGS_E_TIMEOUT in ctl.
 void launch_blend(const uint2 *ranges, const uint32_t *vals, const uint64_t *packed, uint32_t idx_mask,
                   const Splats &sp, int64_t ncap, const vm3dgs_camera &cam, const float bg[3], float *image,
-                  uint32_t *order, uint32_t *work, cudaStream_t st);
+                  uint32_t *order, uint32_t *work, const CUtensorMap *rec_map, Ctl *ctl, cudaStream_t st);
+// The 2-D tensor map of n splat records (12 floats a row, one row per box):
+// false when the driver refuses it.
+bool encode_rec_map(const float4 *rec, int64_t n, CUtensorMap *out);
 
 }  // namespace vm
 
@@ -333,6 +338,8 @@ struct vm3dgs_renderer {
   vm::KeyFormat kf{32, 0, 32, 0u, false};  // of the last sort
   bool maps_ok = false;
   vm::ProjMaps maps{};
+  bool rec_maps_ok = false;        // the blend stages splat records by TMA
+  CUtensorMap rec_map[vm::kContexts];
   float scene_center[3] = {0, 0, 0}, scene_half = 1.0f;
   // captured batch
   cudaGraph_t graph = nullptr;

@@ -57,4 +57,27 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+// Contiguous bulk copy of `bytes` (a multiple of 16) from global memory at
+// src (16-byte aligned) into shared memory at dst (16-byte aligned);
+// completes `bar` with its byte count.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Four rows r0..r3 (any order, repeats allowed) of a 2-D tensor map whose
+// box is one row high, column c (its inner coordinate, a multiple of 16
+// bytes), into shared memory at dst (128-byte aligned), one after another;
+// completes `bar` with 4 rows' bytes.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, int c, int r0, int r1, int r2, int r3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 }  // namespace vm
