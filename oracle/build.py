@@ -670,6 +670,12 @@ class BuildParams:
     kmeans_iters: int = 10
     kmeans_scale: float = 0.0       # 0: fanout^(1/3)
     kmeans_attr_weight: float = 0.1
+    # paging "mesh": the proxy of Sec. 3.1 (ellipsoid slices, closing,
+    # surface, QEM) and pages by nearest triangle (Sec. 3.2)
+    mesh_kappa: float = 2.0          # ellipsoid of mesh_kappa sigma
+    mesh_op_min: float = 0.1         # Gaussians below this opacity do not occupy
+    mesh_closing: int = 1            # closing radius in voxels
+    mesh_qem_ratio: float = 0.25     # triangles kept by the simplification
 
 
 @dataclass
@@ -694,6 +700,8 @@ class Scene:
 
 def build_scene(raw, bp: BuildParams) -> Scene:
     dec = decode(raw, bp.lo, bp.hi)
+    if bp.paging == "mesh":
+        return _build_scene_mesh(dec, bp)
     codes = morton_codes(dec["pos"], bp.lo, bp.hi)
     if bp.paging == "morton":
         order, starts, counts = morton_pages(codes, bp.page_size)
@@ -710,3 +718,36 @@ def build_scene(raw, bp: BuildParams) -> Scene:
                                bp.seed, bp.links)
     return Scene(bp, len(starts), levels, err, counts, pages["src"], dec["src"], px["verts"], px["tris"],
                  px["face_page"], px["link_ptr"], px["link_col"], px)
+
+
+def _build_scene_mesh(dec, bp):
+    """Paging "mesh": the proxy of Sec. 3.1, pages by nearest triangle with
+    subdivision and merging (Sec. 3.2), links from the mesh (Sec. 3.3), then
+    the LOD of the other pagings."""
+    from . import mesh as om
+    mp = om.mesh_proxy(dec, bp.lo, bp.hi, bp.voxel, bp.mesh_kappa, bp.mesh_op_min, bp.mesh_closing,
+                       bp.mesh_qem_ratio)
+    asg = om.assign_pages(dec["pos"], mp["verts"], mp["tris"], bp.page_size)
+    counts = asg["counts"].astype(np.int64)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    pages = paged_arrays(dec, asg["order"], starts, counts, bp.page_size)
+    if bp.lod_method == "kmeans":
+        levels, err, _ = lod_build_kmeans(pages, bp.lod_levels, bp.lod_fanout, bp.kmeans_iters, bp.kmeans_scale,
+                                          bp.kmeans_attr_weight)
+    else:
+        levels, err = lod_build(pages, bp.lod_levels, bp.lod_fanout)
+    n_pages = len(counts)
+    slot = np.arange(bp.page_size)[None, :]
+    valid = slot < counts[:, None]
+    own = np.broadcast_to(np.arange(n_pages)[:, None], valid.shape)[valid]
+    vid = (np.arange(n_pages)[:, None] * bp.page_size + slot)[valid].astype(np.int64)
+    R = quat_to_rot(pages["rot"][valid])
+    if bp.links:
+        link_ptr, link_col = om.mesh_links(pages["pos"][valid], R, pages["scale"][valid], own, vid, asg["verts"],
+                                           asg["tris"], asg["face_page"], n_pages, bp.link_samples, bp.link_sigma,
+                                           bp.seed)
+    else:
+        link_ptr, link_col = np.zeros(n_pages + 1, np.int64), np.zeros(0, np.int32)
+    px = dict(mesh=mp, assign=asg)
+    return Scene(bp, n_pages, levels, err, counts, pages["src"], dec["src"], asg["verts"].astype(np.float32),
+                 asg["tris"].astype(np.int32), asg["face_page"].astype(np.int32), link_ptr, link_col, px)
