@@ -98,6 +98,25 @@ typedef struct {
   int32_t kmeans_iters;
   double kmeans_scale;
   double kmeans_attr_weight;
+  /* paging = 2, the paper's mesh proxy and page assignment (Sec. 3.1, 3.2),
+   * computed on the current CUDA device: the scene box is sampled at voxel
+   * centres lo + (i + 1/2) voxel; a sample point is occupied when it lies in
+   * the mesh_kappa-sigma ellipsoid of a Gaussian of opacity >= mesh_op_min
+   * (the points of each scene slice inside the ellipse where the slice cuts
+   * the ellipsoid); the occupancy is closed with the cube of radius
+   * mesh_closing voxels; its boundary is extracted cube by cube from the 6
+   * tetrahedra of each cube (vertices at inside-outside midpoints); quadric
+   * edge collapses keep mesh_qem_ratio of the triangles.  Gaussians go to
+   * their nearest triangle; a triangle with more than page_size is split at
+   * the midpoint of its first edge (rotated vertex order) until none has;
+   * triangles merge breadth-first into pages of at most page_size (a
+   * triangle that would overflow starts the next page; the nearest
+   * unassigned triangle continues a page without neighbours left).  Links:
+   * the nearest triangle of each link sample.  The proxy is that mesh. */
+  double mesh_kappa;
+  double mesh_op_min;
+  int32_t mesh_closing;
+  double mesh_qem_ratio;
 } vm3dgs_build_params;
 
 /* Pinhole camera, OpenCV axes (+x right, +y down, +z forward). */
@@ -444,6 +463,31 @@ int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const vm3dgs_camer
 #define VM3DGS_NOALLOC_MAX_PAIRS (1 << 19)
 int vm3dgs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, int64_t n, int32_t key_bits,
                               int32_t *status_dev, void *stream);
+
+/* ------------------------------------------------ mesh proxy, host steps
+ * The host steps of vm3dgs_build_pages with paging = 2, callable alone (no
+ * GPU needed) to inspect or test them.
+ * vm3dgs_mesh_simplify: quadric edge collapses (Sec. 3.1: "simplified using
+ * a quadric error metric") of the mesh (verts [nv][3] FP64, tris [nt][3]) in
+ * place, until at most target triangles live; the surviving vertices keep
+ * their order, the triangles theirs; *nv_out, *nt_out the new counts.
+ * vm3dgs_mesh_assign_pages: page assignment of Sec. 3.2 for n means (FP32
+ * xyz): nearest triangle, subdivision of triangles holding more than
+ * page_size, greedy merging.  Writes the subdivided mesh (verts_out up to
+ * cap_v vertices, tris_out and face_page_out up to cap_t triangles), the
+ * means in page order (order_out[n]), the pages' counts (counts_out, at
+ * most n entries) and, if parent_out is not null, each page's parent (-1, or
+ * for the extra pages of a triangle whose means splitting could not bring
+ * within page_size -- 16 splits in a row that moved them all to one child --
+ * the page that triangle carries; the build links them from it);
+ * sizes_out[3] = vertices, triangles, pages (also when the caps are too
+ * small: VM3DGS_E_CAPACITY).  E_INVAL for bad arrays. */
+int vm3dgs_mesh_simplify(double *verts, int64_t nv, int32_t *tris, int64_t nt, int64_t target, int64_t *nv_out,
+                         int64_t *nt_out);
+int vm3dgs_mesh_assign_pages(int64_t n, const float *mu, int64_t page_size, const double *verts, int64_t nv,
+                             const int32_t *tris, int64_t nt, int64_t cap_v, double *verts_out, int64_t cap_t,
+                             int32_t *tris_out, int32_t *face_page_out, int64_t *order_out, int64_t *counts_out,
+                             int64_t *parent_out, int64_t *sizes_out);
 
 const char *vm3dgs_last_error(void);
 const char *vm3dgs_version(void);

@@ -745,7 +745,7 @@ def _build_scene_mesh(dec, bp):
     if bp.links:
         link_ptr, link_col = om.mesh_links(pages["pos"][valid], R, pages["scale"][valid], own, vid, asg["verts"],
                                            asg["tris"], asg["face_page"], n_pages, bp.link_samples, bp.link_sigma,
-                                           bp.seed)
+                                           bp.seed, asg["parent"])
     else:
         link_ptr, link_col = np.zeros(n_pages + 1, np.int64), np.zeros(0, np.int32)
     px = dict(mesh=mp, assign=asg)

@@ -41,15 +41,23 @@ Steps, with the readings taken where the paper leaves a choice open:
              holding more than page_size means is split at the midpoint of
              its first edge (v0, v1) into (v2, v0, m) and (v1, v2, m) (the
              vertex order rotates, so the next split of a child takes
-             another edge), its means going to the nearer child (ties: the
-             first); repeated until none holds more.  Triangles with means
+             another edge), its means going to the child with the nearer
+             centroid (ties: the first; means whose nearest point on the
+             surface is a vertex could never be separated by nearest
+             distance); repeated until none holds more, except that a
+             triangle whose splits moved all its means to one child 16 times
+             in a row is not split again (means far off the surface on one
+             side of it would split it forever).  Triangles with means
              then merge into pages: in ascending triangle order, a page grows
              breadth-first over triangles sharing a vertex (neighbours in
              ascending id) while its count stays within page_size; a triangle
              that would overflow it becomes the base of the next page; when
              no neighbour is left the unassigned triangle nearest (centroid
              distance, ties to the lower id) to the page's base continues it.
-             A triangle's page is -1 when it holds no mean.
+             An over-full triangle starts a page of its own and its means fill
+             it and the pages after it, in order; those extra pages are linked
+             from the triangle's page.  A triangle's page is -1 when it holds
+             no mean.
 """
 from __future__ import annotations
 
@@ -102,7 +110,7 @@ def occupancy(pos, scale, rot, opacity, lo, h, dims, kappa, op_min):
     h32 = F32(h)
     lo32 = lo.astype(F32)
     for g in range(len(mu)):
-        if not opacity[g] >= op_min:
+        if not F32(opacity[g]) >= F32(op_min):
             continue
         # a box that holds every sample point the FP32 test can accept
         Sig = (R[g].astype(np.float64) * s[g].astype(np.float64) ** 2) @ R[g].astype(np.float64).T
@@ -445,11 +453,15 @@ def nearest_triangle(p, verts, tris, chunk=4096):
     return arg
 
 
+FUTILE_SPLITS = 16   # a chain of splits that separate nothing ends here
+
+
 def assign_pages(mu, verts, tris, page_size):
     """Nearest-triangle assignment, subdivision and greedy merging.
     Returns dict(verts, tris, face_page [nt] (-1: no page), page_of [n] per
-    mean, order [n] means in page order (page, triangle, index), counts
-    [n_pages])."""
+    mean, face_of [n], order [n] means in page order (page, triangle,
+    index), counts [n_pages], parent [n_pages]: -1, or for the extra pages of
+    an over-full triangle the page that triangle carries)."""
     V = [np.asarray(v, np.float64) for v in verts]
     T = [list(map(int, t)) for t in tris]
     mu = np.asarray(mu, np.float64)
@@ -457,6 +469,8 @@ def assign_pages(mu, verts, tris, page_size):
     members = [[] for _ in T]
     for i, f in enumerate(face):
         members[f].append(i)
+    fut = [0] * len(T)
+    orig = list(range(len(T)))     # the input triangle each one lies in
     queue = [f for f in range(len(T)) if len(members[f]) > page_size]
     qi = 0
     while qi < len(queue):
@@ -470,13 +484,23 @@ def assign_pages(mu, verts, tris, page_size):
         g = len(T) - 1
         members.append([])
         pts = mu[members[f]]
-        d_f = point_triangle_dist2(pts, V[T[f][0]], V[T[f][1]], V[T[f][2]])
-        d_g = point_triangle_dist2(pts, V[T[g][0]], V[T[g][1]], V[T[g][2]])
+        # the child of the nearer centroid: means sharing their nearest point
+        # on the surface (a vertex) still separate
+        c_f = (V[T[f][0]] + V[T[f][1]] + V[T[f][2]]) / 3.0
+        c_g = (V[T[g][0]] + V[T[g][1]] + V[T[g][2]]) / 3.0
+        d_f = _dist2(pts, c_f)
+        d_g = _dist2(pts, c_g)
         old = members[f]
         members[f] = [i for i, a, b in zip(old, d_f, d_g) if a <= b]
         members[g] = [i for i, a, b in zip(old, d_f, d_g) if a > b]
+        # splits that move every mean to one child count towards FUTILE_SPLITS
+        ff = fut[f] + 1 if not members[g] else 0
+        fg = fut[f] + 1 if not members[f] else 0
+        fut[f] = ff
+        fut.append(fg)
+        orig.append(orig[f])
         for h in (f, g):
-            if len(members[h]) > page_size:
+            if len(members[h]) > page_size and fut[h] < FUTILE_SPLITS:
                 queue.append(h)
     nt = len(T)
     cnt = [len(members[f]) for f in range(nt)]
@@ -489,6 +513,7 @@ def assign_pages(mu, verts, tris, page_size):
     cen = np.array([(V[t[0]] + V[t[1]] + V[t[2]]) / 3.0 for t in T]).reshape(-1, 3)
     page = [-1] * nt
     todo = [f for f in range(nt) if cnt[f] > 0]
+    parent = []
     n_pages = 0
     next_base = None
     ti = 0
@@ -504,6 +529,7 @@ def assign_pages(mu, verts, tris, page_size):
             next_base = None
         pid = n_pages
         n_pages += 1
+        parent.append(-1)
         total = 0
         frontier = [base]
         seen = {base}
@@ -512,12 +538,17 @@ def assign_pages(mu, verts, tris, page_size):
                 f = frontier.pop(0)
                 if page[f] >= 0 or cnt[f] == 0:
                     continue
-                if total + cnt[f] > page_size:
+                if total + cnt[f] > page_size and not (total == 0 and cnt[f] > page_size):
                     next_base = f
                     frontier = []
                     break
                 page[f] = pid
                 total += cnt[f]
+                if cnt[f] > page_size:
+                    # an over-full triangle: its means fill this page and the next ones
+                    extra = (cnt[f] + page_size - 1) // page_size - 1
+                    parent.extend([pid] * extra)
+                    n_pages += extra
                 for g in nbrs[f]:
                     if g not in seen and page[g] < 0:
                         seen.add(g)
@@ -533,12 +564,21 @@ def assign_pages(mu, verts, tris, page_size):
             seen.add(f)
             frontier.append(f)
     face_page = np.array(page, np.int64)
-    page_of = np.array([face_page[f] for f in _member_face(members, len(mu))], np.int64)
     face_of = _member_face(members, len(mu))
+    page_of = np.zeros(len(mu), np.int64)
+    for f in range(nt):
+        for k, i in enumerate(members[f]):
+            page_of[i] = face_page[f] + k // page_size
     order = np.lexsort((np.arange(len(mu)), face_of, page_of))
     counts = np.bincount(page_of, minlength=n_pages)
     return dict(verts=np.array(V), tris=np.array(T, np.int64).reshape(-1, 3), face_page=face_page, page_of=page_of,
-                face_of=face_of, order=order, counts=counts, n_pages=n_pages)
+                face_of=face_of, order=order, counts=counts, n_pages=n_pages, parent=np.array(parent, np.int64),
+                orig=np.array(orig, np.int64))
+
+
+def _dist2(p, c):
+    e = np.asarray(p, np.float64) - c
+    return (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]
 
 
 def _member_face(members, n):
@@ -548,12 +588,13 @@ def _member_face(members, n):
     return out
 
 
-def mesh_links(mu, R, scale, own_page, vid, verts, tris, face_page, n_pages, n_samples, k_sigma, seed):
+def mesh_links(mu, R, scale, own_page, vid, verts, tris, face_page, n_pages, n_samples, k_sigma, seed, parent=None):
     """Page links from the mesh (Sec. 3.3 "Page Linking"): K samples per
     Gaussian in its k-sigma ellipsoid (the sampling of the voxel proxy's links,
     link_uniforms), each mapped to its nearest triangle; a triangle whose page
-    q differs from the Gaussian's page p gives the link q -> p.  Returns the
-    CSR (link_ptr [n_pages + 1], link_col)."""
+    q differs from the Gaussian's page p gives the link q -> p; the extra
+    pages of an over-full triangle are linked from its page (parent).
+    Returns the CSR (link_ptr [n_pages + 1], link_col)."""
     from .build import link_uniforms
     lq, lp = [], []
     if n_samples > 0 and len(mu):
@@ -567,6 +608,10 @@ def mesh_links(mu, R, scale, own_page, vid, verts, tris, face_page, n_pages, n_s
         own = np.repeat(np.asarray(own_page, np.int64)[:, None], n_samples, 1)
         sel = (q >= 0) & (q != own)
         lq, lp = q[sel], own[sel]
+    if parent is not None and np.any(np.asarray(parent) >= 0):
+        extra = np.flatnonzero(np.asarray(parent) >= 0)
+        lq = np.concatenate([np.asarray(lq, np.int64), np.asarray(parent)[extra]])
+        lp = np.concatenate([np.asarray(lp, np.int64), extra])
     if len(lq):
         uniq = np.unique(np.asarray(lq, np.int64) * n_pages + np.asarray(lp, np.int64))
         lq, lp = uniq // n_pages, uniq % n_pages

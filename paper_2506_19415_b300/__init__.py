@@ -44,7 +44,8 @@ class BuildParams(ctypes.Structure):
                 ("lo", c_d * 3), ("hi", c_d * 3), ("voxel", c_d), ("kappa", c_d), ("closing", c_i32),
                 ("link_samples", c_i32), ("link_sigma", c_d), ("seed", c_u64), ("links", c_i32), ("fp16", c_i32),
                 ("n_threads", c_i32), ("lod_method", c_i32), ("kmeans_iters", c_i32), ("kmeans_scale", c_d),
-                ("kmeans_attr_weight", c_d)]
+                ("kmeans_attr_weight", c_d), ("mesh_kappa", c_d), ("mesh_op_min", c_d), ("mesh_closing", c_i32),
+                ("mesh_qem_ratio", c_d)]
 
 
 class Camera(ctypes.Structure):
@@ -127,6 +128,9 @@ _SIGS = {
     "vm3dgs_batch_graph_capture": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_p],
     "vm3dgs_batch_graph_launch": [c_p, ctypes.POINTER(Camera), c_i32, c_p],
     "vm3dgs_autotune_tiles": [c_p, ctypes.POINTER(Camera), c_i32, ctypes.POINTER(c_p), c_i32, c_p],
+    "vm3dgs_mesh_simplify": [c_p, c_i64, c_p, c_i64, c_i64, c_p, c_p],
+    "vm3dgs_mesh_assign_pages": [c_i64, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_p, c_p, c_p, c_p,
+                                 c_p, c_p],
     "vm3dgs_last_error": [],
     "vm3dgs_version": [],
 }
@@ -190,7 +194,7 @@ def camera_array(cams):
 @dataclass
 class BuildConfig:
     page_size: int = 256
-    paging: str = "morton"       # or "octree"
+    paging: str = "morton"       # or "octree", or "mesh" (the paper's mesh proxy, Sec. 3.1-3.2; needs a GPU)
     lod_levels: int = 1
     lod_fanout: int = 8
     lo: tuple = (-5.0, -5.0, -5.0)
@@ -208,10 +212,18 @@ class BuildConfig:
     kmeans_iters: int = 10
     kmeans_scale: float = 0.0    # 0: lod_fanout^(1/3)
     kmeans_attr_weight: float = 0.1
+    mesh_kappa: float = 2.0      # paging "mesh": ellipsoid of mesh_kappa sigma
+    mesh_op_min: float = 0.1     # Gaussians below this opacity do not occupy
+    mesh_closing: int = 1        # closing radius in voxels
+    mesh_qem_ratio: float = 0.25 # triangles kept by the simplification
 
     def struct(self) -> BuildParams:
         b = BuildParams()
-        b.page_size, b.paging = self.page_size, 0 if self.paging == "morton" else 1
+        if self.paging not in ("morton", "octree", "mesh"):
+            raise ValueError("paging is 'morton', 'octree' or 'mesh'")
+        b.page_size, b.paging = self.page_size, {"morton": 0, "octree": 1, "mesh": 2}[self.paging]
+        b.mesh_kappa, b.mesh_op_min, b.mesh_closing = self.mesh_kappa, self.mesh_op_min, self.mesh_closing
+        b.mesh_qem_ratio = self.mesh_qem_ratio
         b.lod_levels, b.lod_fanout = self.lod_levels, self.lod_fanout
         b.lo[:] = [float(v) for v in self.lo]
         b.hi[:] = [float(v) for v in self.hi]
@@ -619,3 +631,45 @@ def vm3dgs_sort_pairs_noalloc(keys, vals, n, key_bits, status=None, stream=None)
     _check(_lib.vm3dgs_sort_pairs_noalloc(c_p(keys.data_ptr()), c_p(vals.data_ptr()), int(n), int(key_bits),
                                           c_p(status.data_ptr()) if status is not None else None,
                                           _stream_ptr(stream)))
+
+
+# --------------------------------------------------------------------------- mesh proxy host steps
+def _np_ptr(a):
+    return c_p(a.ctypes.data)
+
+
+def vm3dgs_mesh_simplify(verts, tris, target):
+    """Quadric edge collapses of a mesh (the host step of the mesh proxy);
+    returns (verts [nv,3] float64, tris [nt,3] int32)."""
+    import numpy as np
+    V = np.ascontiguousarray(verts, np.float64).reshape(-1, 3).copy()
+    T = np.ascontiguousarray(tris, np.int32).reshape(-1, 3).copy()
+    nv, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.vm3dgs_mesh_simplify(_np_ptr(V), len(V), _np_ptr(T), len(T), int(target), ctypes.byref(nv),
+                                     ctypes.byref(nt)))
+    return V[:nv.value].copy(), T[:nt.value].copy()
+
+
+def vm3dgs_mesh_assign_pages(mu, page_size, verts, tris):
+    """Page assignment by nearest triangle with subdivision and merging (the
+    host step of paging "mesh"); returns dict(verts, tris, face_page, order,
+    counts)."""
+    import numpy as np
+    mu = np.ascontiguousarray(mu, np.float32).reshape(-1, 3)
+    V = np.ascontiguousarray(verts, np.float64).reshape(-1, 3)
+    T = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+    n = len(mu)
+    cap_v, cap_t = len(V) + 18 * n + 16, len(T) + 18 * n + 16   # splits: at most 17 per mean
+    vo = np.zeros((cap_v, 3), np.float64)
+    to = np.zeros((cap_t, 3), np.int32)
+    fp = np.zeros(cap_t, np.int32)
+    order = np.zeros(max(n, 1), np.int64)
+    counts = np.zeros(max(n, 1), np.int64)
+    parent = np.zeros(max(n, 1), np.int64)
+    sizes = np.zeros(3, np.int64)
+    _check(_lib.vm3dgs_mesh_assign_pages(n, _np_ptr(mu), int(page_size), _np_ptr(V), len(V), _np_ptr(T), len(T),
+                                         cap_v, _np_ptr(vo), cap_t, _np_ptr(to), _np_ptr(fp), _np_ptr(order),
+                                         _np_ptr(counts), _np_ptr(parent), _np_ptr(sizes)))
+    nv, nt, np_ = (int(x) for x in sizes)
+    return dict(verts=vo[:nv].copy(), tris=to[:nt].copy(), face_page=fp[:nt].copy(), order=order[:n].copy(),
+                counts=counts[:np_].copy(), parent=parent[:np_].copy())

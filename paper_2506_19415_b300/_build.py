@@ -15,12 +15,12 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 # kernels whose discrete results are fp32 formulas evaluated exactly as written
-EXACT = {"k_project.cu", "k_feedback.cu", "k_residency.cu", "k_prefetch.cu"}
+EXACT = {"k_project.cu", "k_feedback.cu", "k_residency.cu", "k_prefetch.cu", "k_mesh.cu"}
 CU = ["k_project.cu", "k_feedback.cu", "k_residency.cu", "k_stream.cu", "k_sort.cu", "k_blend.cu", "renderer.cu",
       "k_mlp.cu", "prefetcher.cu", "k_prefetch.cu",
-      "sort_noalloc.cu", "batch.cu"]
-CPP = ["build_pages.cpp", "scene.cpp"]
-HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh", "block_sel.cuh", "tma.cuh", "coverage.cuh"]
+      "sort_noalloc.cu", "batch.cu", "k_mesh.cu"]
+CPP = ["build_pages.cpp", "scene.cpp", "mesh_proxy.cpp"]
+HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh", "block_sel.cuh", "tma.cuh", "coverage.cuh", "mesh.h"]
 
 
 def _newer(src_list, target):

@@ -36,6 +36,7 @@
 #include <utility>
 #include <vector>
 
+#include "mesh.h"
 #include "scene.h"
 
 namespace {
@@ -410,8 +411,14 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
       !in->op_logit || !in->f_dc || (in->sh_degree > 0 && !in->f_rest))
     return fail(VM3DGS_E_INVAL, "bad Gaussian arrays");
   if (bp->page_size <= 0 || bp->lod_levels < 1 || bp->lod_levels > kMaxLevels || bp->lod_fanout < 2 ||
-      bp->voxel <= 0 || bp->link_samples < 0)
+      bp->voxel <= 0 || bp->link_samples < 0 || bp->paging < 0 || bp->paging > 2)
     return fail(VM3DGS_E_INVAL, "bad build parameters");
+  if (bp->paging == 2 && (!(bp->mesh_kappa > 0) || bp->mesh_closing < 0 || !(bp->mesh_qem_ratio > 0) ||
+                          !(bp->mesh_qem_ratio <= 1)))
+    return fail(VM3DGS_E_INVAL, "bad mesh proxy parameters");
+  for (int a = 0; a < 3 && bp->paging == 2; ++a)
+    if (std::ceil((bp->hi[a] - bp->lo[a]) / bp->voxel) > 1000000.0)
+      return fail(VM3DGS_E_INVAL, "mesh proxy grid too fine (more than 1e6 samples along an axis)");
   if (bp->lod_method < 0 || bp->lod_method > 1 ||
       (bp->lod_method == 1 && (bp->kmeans_iters < 1 || !(bp->kmeans_scale >= 0) || !(bp->kmeans_attr_weight >= 0))))
     return fail(VM3DGS_E_INVAL, "bad LOD method parameters");
@@ -436,6 +443,40 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
   S->rec32 = rec_bytes32(K);
   S->rec16 = bp->fp16 ? rec_bytes16(K) : 0;
 
+  // ---- paging
+  std::vector<int64_t> starts, counts;
+  std::vector<int64_t> order(d.n);
+  std::vector<double> mverts;           // paging 2: the mesh proxy (Sec. 3.1) and its triangles' pages
+  std::vector<int32_t> mtris, mface;
+  std::vector<int64_t> mparent;         // extra pages of an over-full triangle: the page it carries
+  if (bp->paging == 2) {
+    MeshGrid g;
+    for (int a = 0; a < 3; ++a) {
+      g.lo[a] = bp->lo[a];
+      g.n[a] = (int64_t)std::ceil((bp->hi[a] - bp->lo[a]) / bp->voxel);
+    }
+    g.h = bp->voxel;
+    std::vector<uint8_t> closed;
+    std::vector<int32_t> D;
+    std::string err;
+    if (!mesh_occupancy(g, d.n, d.pos.data(), d.scale.data(), d.rot.data(), d.opac.data(), (float)bp->mesh_kappa,
+                        bp->mesh_op_min, bp->mesh_closing, closed, nullptr, err) ||
+        !mesh_surface(g, closed, D, mtris, err)) {
+      delete S;
+      return fail(VM3DGS_E_CUDA, "mesh proxy: " + err);
+    }
+    mverts.resize(D.size());
+    for (size_t i = 0; i < D.size(); ++i) mverts[i] = g.lo[i % 3] + (double)D[i] * (0.5 * g.h);
+    const int64_t ntri = (int64_t)mtris.size() / 3;
+    if (ntri > 0) qem_simplify(mverts, mtris, std::max<int64_t>(4, (int64_t)((double)ntri * bp->mesh_qem_ratio)));
+    if (mtris.empty() && d.n > 0) {
+      delete S;
+      return fail(VM3DGS_E_INVAL, "mesh proxy is empty (no Gaussian occupies a sample point)");
+    }
+    assign_pages(d.n, d.pos.data(), ps, mverts, mtris, mface, order, counts, mparent);
+    int64_t acc = 0;
+    for (int64_t c : counts) { starts.push_back(acc); acc += c; }
+  } else {
   // ---- Morton codes and paging
   std::vector<uint64_t> code(d.n);
 #pragma omp parallel for schedule(static)
@@ -452,11 +493,9 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < d.n; ++i) ci[i] = {code[i], i};
   __gnu_parallel::sort(ci.begin(), ci.end());
-  std::vector<int64_t> order(d.n);
   std::vector<uint64_t> sc(d.n);
   for (int64_t i = 0; i < d.n; ++i) { order[i] = ci[i].second; sc[i] = ci[i].first; }
   std::vector<std::pair<uint64_t, int64_t>>().swap(ci);
-  std::vector<int64_t> starts, counts;
   if (bp->paging == 0) {
     for (int64_t s = 0; s < d.n; s += ps) { starts.push_back(s); counts.push_back(std::min(ps, d.n - s)); }
   } else {
@@ -472,6 +511,7 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
       }
     }
     if (cs >= 0) { starts.push_back(cs); counts.push_back(cn); }
+  }
   }
   const int64_t NP = (int64_t)starts.size();
   S->n_pages = (int32_t)NP;
@@ -628,12 +668,74 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
     }
   }
 
+  const float *L0 = (const float *)(S->data32 + S->off32[0]);
+  // ---- link samples
+  const int KS = bp->link_samples;
+  const double twopi = 2.0 * 3.14159265358979323846, pi = 3.14159265358979323846;
+  auto sample_point = [&](int64_t p, int64_t s, int j, double *x) {
+    const float *blk = L0 + p * ps * NA;
+    const uint64_t vid = (uint64_t)(p * ps + s);
+    double u[3];
+    for (int a = 0; a < 3; ++a)
+      u[a] = (double)(splitmix64(((vid * (uint64_t)KS + (uint64_t)j) * 4ull + (uint64_t)a) ^ bp->seed) >> 11) *
+             (1.0 / 9007199254740992.0);
+    double r = u[0], th = twopi * u[1], ph = pi * u[2];
+    double e[3] = {r * std::sin(ph) * std::cos(th), r * std::sin(ph) * std::sin(th), r * std::cos(ph)};
+    double q[4] = {blk[6 * ps + s], blk[7 * ps + s], blk[8 * ps + s], blk[9 * ps + s]};
+    double R[3][3];
+    quat_to_rot(q, R);
+    double loc[3];
+    for (int a = 0; a < 3; ++a) loc[a] = bp->link_sigma * (double)blk[(3 + a) * ps + s] * e[a];
+    for (int a = 0; a < 3; ++a) x[a] = (double)blk[a * ps + s] + ((R[a][0] * loc[0] + R[a][1] * loc[1]) + R[a][2] * loc[2]);
+  };
+  if (bp->paging == 2) {
+    // ---- links from the mesh (Sec. 3.3): the nearest triangle of each sample
+    std::vector<uint64_t> mpairs;
+    if (bp->links && KS > 0) {
+      TriIndex *ix = tri_index_build(mverts, mtris);
+      std::vector<std::vector<uint64_t>> tl(omp_get_max_threads());
+#pragma omp parallel for schedule(dynamic, 4)
+      for (int64_t p = 0; p < NP; ++p) {
+        auto &mine = tl[omp_get_thread_num()];
+        for (int64_t s = 0; s < counts[p]; ++s)
+          for (int j = 0; j < KS; ++j) {
+            double x[3];
+            sample_point(p, s, j, x);
+            const int32_t f = tri_index_nearest(ix, x);
+            const int32_t q = f >= 0 ? mface[f] : -1;
+            if (q >= 0 && q != p) mine.push_back((uint64_t)q * (uint64_t)NP + (uint64_t)p);
+          }
+      }
+      tri_index_free(ix);
+      for (auto &t : tl) mpairs.insert(mpairs.end(), t.begin(), t.end());
+    }
+    if (bp->links) {
+      for (int64_t q = 0; q < NP; ++q)
+        if (mparent[q] >= 0) mpairs.push_back((uint64_t)mparent[q] * (uint64_t)NP + (uint64_t)q);
+      __gnu_parallel::sort(mpairs.begin(), mpairs.end());
+      mpairs.erase(std::unique(mpairs.begin(), mpairs.end()), mpairs.end());
+    }
+    S->link_ptr.assign(NP + 1, 0);
+    S->link_col.resize(mpairs.size());
+    for (size_t i = 0; i < mpairs.size(); ++i) {
+      S->link_ptr[mpairs[i] / NP + 1]++;
+      S->link_col[i] = (int32_t)(mpairs[i] % NP);
+    }
+    for (int64_t p = 0; p < NP; ++p) S->link_ptr[p + 1] += S->link_ptr[p];
+    S->verts.resize(mverts.size());
+    for (size_t i = 0; i < mverts.size(); ++i) S->verts[i] = (float)mverts[i];
+    S->tris = mtris;
+    S->face_page = mface;
+    finish_scene(S);
+    *out = S;
+    return VM3DGS_OK;
+  }
+
   // ---- voxel proxy
   Grid G;
   for (int a = 0; a < 3; ++a) { G.lo[a] = bp->lo[a]; G.n[a] = (int64_t)std::ceil((bp->hi[a] - bp->lo[a]) / bp->voxel); }
   G.h = bp->voxel;
   const int64_t NV = G.total();
-  const float *L0 = (const float *)(S->data32 + S->off32[0]);
   // real Gaussians in (page, slot) order
   std::vector<int64_t> gstart(NP + 1, 0);
   for (int64_t p = 0; p < NP; ++p) gstart[p + 1] = gstart[p] + counts[p];
@@ -759,25 +861,6 @@ extern "C" int vm3dgs_build_pages(const vm3dgs_gaussians *in, const vm3dgs_build
           if (d2 < best_d || (d2 == best_d && l < best)) { best_d = d2; best = l; }
         }
     return best;
-  };
-  // ---- link samples
-  const int KS = bp->link_samples;
-  const double twopi = 2.0 * 3.14159265358979323846, pi = 3.14159265358979323846;
-  auto sample_point = [&](int64_t p, int64_t s, int j, double *x) {
-    const float *blk = L0 + p * ps * NA;
-    const uint64_t vid = (uint64_t)(p * ps + s);
-    double u[3];
-    for (int a = 0; a < 3; ++a)
-      u[a] = (double)(splitmix64(((vid * (uint64_t)KS + (uint64_t)j) * 4ull + (uint64_t)a) ^ bp->seed) >> 11) *
-             (1.0 / 9007199254740992.0);
-    double r = u[0], th = twopi * u[1], ph = pi * u[2];
-    double e[3] = {r * std::sin(ph) * std::cos(th), r * std::sin(ph) * std::sin(th), r * std::cos(ph)};
-    double q[4] = {blk[6 * ps + s], blk[7 * ps + s], blk[8 * ps + s], blk[9 * ps + s]};
-    double R[3][3];
-    quat_to_rot(q, R);
-    double loc[3];
-    for (int a = 0; a < 3; ++a) loc[a] = bp->link_sigma * (double)blk[(3 + a) * ps + s] * e[a];
-    for (int a = 0; a < 3; ++a) x[a] = (double)blk[a * ps + s] + ((R[a][0] * loc[0] + R[a][1] * loc[1]) + R[a][2] * loc[2]);
   };
   if (KS > 0) {
     // unmarked face voxels take the page with the most samples in them

@@ -219,10 +219,11 @@ def test_point_triangle_distance_against_dense_sampling():
 
 def test_page_assignment_partitions_and_respects_page_size():
     """Means around the surface of a voxel ball: every mean in exactly one
-    page, its triangle the nearest (checked against the distances to every
-    triangle), no triangle and no page above page_size, subdivision keeps the
-    surface's area, triangles without means carry no page, and merging makes
-    far fewer pages than triangles with means."""
+    page, its triangle lying inside the triangle nearest to it before the
+    subdivision (checked against the distances to every original triangle),
+    no triangle and no page above page_size, subdivision keeps the surface's
+    area, triangles without means carry no page, and merging makes far fewer
+    pages than triangles with means."""
     rng = np.random.default_rng(8)
     n = 10
     z, y, x = np.mgrid[0:n, 0:n, 0:n]
@@ -240,12 +241,18 @@ def test_page_assignment_partitions_and_respects_page_size():
         return 0.5 * np.linalg.norm(np.cross(Vv[Tt[:, 1]] - Vv[Tt[:, 0]], Vv[Tt[:, 2]] - Vv[Tt[:, 0]]), axis=1).sum()
     assert abs(area(V2, T2) - area(V, T)) < 1e-9 * area(V, T)
     face_of = asg["face_of"]
-    d2 = np.stack([om.point_triangle_dist2(mu, V2[t[0]], V2[t[1]], V2[t[2]]) for t in T2], 1)
+    d2 = np.stack([om.point_triangle_dist2(mu, V[t[0]], V[t[1]], V[t[2]]) for t in T], 1)
+    parent = asg["orig"]   # the input triangle a final one lies in
     # (the nearest; equally near triangles sharing an edge may differ in the last bits)
-    assert np.all(d2[np.arange(len(mu)), face_of] <= d2.min(1) * (1 + 1e-12) + 1e-15)
+    assert np.all(d2[np.arange(len(mu)), parent[face_of]] <= d2.min(1) * (1 + 1e-12) + 1e-15)
+    # every final triangle lies in its input triangle (its vertices do)
+    for f in range(len(T2)):
+        t = T[parent[f]]
+        assert np.all(om.point_triangle_dist2(V2[T2[f]], V[t[0]], V[t[1]], V[t[2]]) < 1e-18)
     per_face = np.bincount(face_of, minlength=len(T2))
     assert per_face.max() <= page_size
     assert np.all((fp >= 0) == (per_face > 0))
+    assert np.all(asg["parent"] == -1)
     counts = asg["counts"]
     assert counts.sum() == len(mu) and counts.max() <= page_size
     assert np.array_equal(np.sort(asg["order"]), np.arange(len(mu)))
@@ -283,3 +290,20 @@ def test_build_scene_with_the_mesh_proxy():
                                          budget_bytes=1 << 40, lod=False))
     out = oracle.frame(sc, pt, cam, ds=4, render_image=False)
     assert len(out["pages"]) > 0 and out["direct"].sum() > 0
+
+
+def test_over_full_triangle_spills_into_linked_pages():
+    """Means far off a small mesh on one side of it: splitting cannot
+    separate them (the futile-split limit ends it), so the triangle keeps
+    more than page_size means, which fill its page and extra pages whose
+    parent is that page; every page stays within page_size."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], np.float64)
+    T = np.array([[0, 1, 2], [1, 3, 2]])
+    rng = np.random.default_rng(11)
+    mu = np.array([5.0, 5.0, 3.0]) + rng.normal(0, 0.05, (300, 3))
+    asg = om.assign_pages(mu, V, T, 64)
+    assert asg["counts"].max() <= 64 and asg["counts"].sum() == 300
+    par = asg["parent"]
+    assert np.any(par >= 0)
+    assert all(asg["face_page"][asg["face_page"] >= 0].tolist().count(q) >= 1 for q in set(par[par >= 0]))
+    assert np.array_equal(np.sort(asg["order"]), np.arange(300))
