@@ -131,10 +131,36 @@ __global__ void __launch_bounds__(kScanThreads) scan_offsets_kernel(const Ctl *c
 }
 
 // Rectangle position (row-major) of the q-th covered tile of a splat whose
-// rectangle has at most 64 tiles (m: its tile mask).
+// rectangle has at most 64 tiles (m: its tile mask, q < popcount(m)): the
+// q-th set bit, by halving the word with population counts.
 __device__ __forceinline__ uint32_t covered_tile(uint64_t m, uint32_t q) {
-  const uint32_t lo = (uint32_t)m, c = __popc(lo);
-  return q < c ? __fns(lo, 0, (int)q + 1) : 32u + __fns((uint32_t)(m >> 32), 0, (int)(q - c) + 1);
+  uint32_t pos = 0, x = (uint32_t)m, c = __popc(x);
+  if (q >= c) {
+    q -= c;
+    pos = 32;
+    x = (uint32_t)(m >> 32);
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    c = __popc(x & ((1u << h) - 1u));
+    if (q >= c) {
+      q -= c;
+      pos += (uint32_t)h;
+      x >>= h;
+    }
+  }
+  return pos;
+}
+
+// n / w for n < 64 and 1 <= w <= 64 by one multiply: with
+// mag = ceil(2^16 / w), n * mag / 2^16 exceeds n / w by less than
+// 64 / 2^16, below the gap 1/w between n / w and the next integer
+__device__ __forceinline__ uint32_t div_small(uint32_t n, uint32_t mag) { return (n * mag) >> 16; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
 }
 
 // Where a splat's pairs go: its view's image and tile size, the view's first
@@ -159,19 +185,6 @@ struct EmitViews {
   }
 };
 
-// (tx, ty) of the q-th pair of a splat whose rectangle has more than 64
-// tiles, walking its rows with the tile rule (one lane)
-__device__ __forceinline__ int2 nth_tile_by_rows(const SplatEllipse &el, uint32_t q, int x0, int x1, int y0, int y1,
-                                                 const TileGeom &tg) {
-  for (int ty = y0; ty < y1; ++ty) {
-    const int2 sp2 = row_span(el, ty, x0, x1, tg);
-    const uint32_t n = sp2.y > sp2.x ? (uint32_t)(sp2.y - sp2.x) : 0u;
-    if (q < n) return make_int2(sp2.x + (int)q, ty);
-    q -= n;
-  }
-  return make_int2(x0, y0);  // not reached while the count agrees with the rule
-}
-
 // adds n to the depth-field digits 0 .. dpass-1 of the shifted key kd
 __device__ __forceinline__ void count_run(uint32_t (*hs)[256], uint64_t kd, int dpass, uint32_t n) {
   for (int d = 0; d < dpass; ++d) atomicAdd(&hs[d][(kd >> (8 * d)) & 255u], n);
@@ -187,9 +200,10 @@ struct PairOut {
   uint32_t (*hs)[256];
   bool hist;
   int lo_bit, passes, dpass;  // digits 0 .. dpass-1 lie in the depth field (counted once per splat)
-  __device__ __forceinline__ void put(int64_t j, uint32_t tile, uint64_t dkey, uint32_t i) const {
+  // (valid: this lane has a pair)
+  __device__ __forceinline__ void put(bool valid, int64_t j, uint32_t tile, uint64_t dkey, uint32_t i) const {
     const uint64_t key = ((uint64_t)tile << kf.tshift) | dkey;
-    if (j < M) {
+    if (valid && j < M) {
       if (kf.packed) {
         keys[j] = key | (uint64_t)i;
       } else {
@@ -197,7 +211,7 @@ struct PairOut {
         vals[j] = i;
       }
     }
-    if (hist) {
+    if (hist && valid) {
       const uint64_t kd = key >> lo_bit;
       for (int d = dpass; d < passes; ++d) atomicAdd(&hs[d][(kd >> (8 * d)) & 255u], 1u);
     }
@@ -236,6 +250,44 @@ __device__ __forceinline__ void hist_flush(const SortHist &sh, uint32_t (*hs)[25
 constexpr uint32_t kSmallSplat = 32;  // pairs a splat may have to be dealt out with others
 constexpr uint32_t kPiece = 256;      // pairs per piece of a larger splat
 
+// Pairs [qa, qb) of splat i whose rectangle has more than 64 tiles, by the
+// whole warp: its rows are walked 32 at a time (a lane per row computes the
+// row's run of kept columns, a warp scan gives the rows' first pairs, and each
+// pair in those rows finds its row by a binary search over the scan).
+__device__ __forceinline__ void emit_rows(const PairOut &po, const SplatEllipse &el, int x0, int x1, int y0, int y1,
+                                          uint32_t qa, uint32_t qb, uint32_t off, uint64_t dkey, uint32_t i,
+                                          const TileGeom &tg, int tgx, int toff, int lane) {
+  uint32_t base = 0;  // pairs in the rows before this group of 32
+  for (int r0 = y0; r0 < y1 && base < qb; r0 += 32) {
+    const int ty = r0 + lane;
+    const int2 sp2 = ty < y1 ? row_span(el, ty, x0, x1, tg) : make_int2(0, 0);
+    const uint32_t nr = sp2.y > sp2.x ? (uint32_t)(sp2.y - sp2.x) : 0u;
+    uint32_t incl = nr;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t lo = max(qa, base), hi = min(qb, base + tot);
+    for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
+      const uint32_t q = g0 + (uint32_t)lane, rel = q - base;
+      // row: the number of rows whose inclusive count is <= rel
+      int L = 0;
+#pragma unroll
+      for (int st = 16; st >= 1; st >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, L + st - 1);
+        if (v <= rel) L += st;
+      }
+      L = min(L, 31);
+      const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Ln = __shfl_sync(0xffffffffu, nr, L);
+      const int Lc0 = __shfl_sync(0xffffffffu, sp2.x, L);
+      po.put(q < hi, (int64_t)off + q, (uint32_t)(toff + (r0 + L) * tgx + Lc0 + (int)(rel - (Li - Ln))), dkey, i);
+    }
+    base += tot;
+  }
+}
+
 // Pair emission (pairs of a splat: its kept tiles in row-major order, at its
 // scanned offset), part 1: a warp takes 32 consecutive splats, a lane each,
 // with coalesced loads of their records.  The pairs of the splats with at
@@ -243,9 +295,10 @@ constexpr uint32_t kPiece = 256;      // pairs per piece of a larger splat
 // writes pair g of the concatenation, its splat found by a binary search over
 // the lanes' inclusive counts and its record fetched by shuffles), so stores
 // are contiguous and no lane walks the offsets; a pair's tile comes from the
-// splat's tile mask, or, for a rectangle of more than 64 tiles, from a walk
-// over its rows with the tile rule.  Larger splats are cut into pieces of
-// kPiece pairs, listed for part 2.  Digits that lie in the depth field are
+// splat's tile mask.  A splat of at most 32 pairs whose rectangle has more
+// than 64 tiles (no mask) has its rows walked by the whole warp (emit_rows).
+// Larger splats are cut into pieces of kPiece pairs, listed for part 2.
+// Digits that lie in the depth field are
 // the same for all pairs of a splat and are counted once per splat.  With
 // sh.hist the kernel also counts the sort's digits (shared-memory histograms
 // merged into sh.hist) and clears the sort's look-back words and tile
@@ -291,16 +344,23 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
     const uint32_t cnt = cur.cnt;
     uint32_t off = 0, rx = 0, ry = 0;
     uint64_t tm = 0, dkey = 0;
+    // dealt out here: splats of at most 32 pairs whose tiles the mask lists;
+    // those of at most 32 pairs in a rectangle of more than 64 tiles (no
+    // mask) are walked by the warp together below; larger ones are pieces
+    const uint32_t rw = (cur.rx >> 16) - (cur.rx & 0xFFFFu), rh = (cur.ry >> 16) - (cur.ry & 0xFFFFu);
     const bool big = cnt > kSmallSplat;
-    if (cnt && !big) {
+    const bool rows = cnt && !big && rw * rh > 64u;
+    uint32_t mag = 0;
+    if (cnt && !big && !rows) {
       off = cur.off;
       rx = cur.rx;
       ry = cur.ry;
       tm = cur.tm;
+      mag = (65536u + rw - 1u) / rw;
       dkey = depth_key(cur.db, kf);
       if (po.hist) count_run(hs, dkey >> po.lo_bit, po.dpass, cnt);
     }
-    const uint32_t small = big ? 0u : cnt;
+    const uint32_t small = (big || rows) ? 0u : cnt;
     uint32_t incl = small;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -321,29 +381,34 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
       const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Ln = __shfl_sync(0xffffffffu, small, L);
       const uint32_t Lrx = __shfl_sync(0xffffffffu, rx, L), Lry = __shfl_sync(0xffffffffu, ry, L);
       const uint64_t Ltm = __shfl_sync(0xffffffffu, tm, L), Ld = __shfl_sync(0xffffffffu, dkey, L);
-      const uint32_t Loff = __shfl_sync(0xffffffffu, off, L);
-      if (g < total) {
-        const int64_t si = b + L;
-        const uint32_t q = g - (Li - Ln);
-        const int x0 = (int)(Lrx & 0xFFFFu), x1 = (int)(Lrx >> 16), y0 = (int)(Lry & 0xFFFFu), y1 = (int)(Lry >> 16);
-        const int w = x1 - x0;
-        TileGeom tg;
-        int tgx, toff;
-        ev.of(si, Nv, tg, tgx, toff);
-        int tx, ty;
-        if (w * (y1 - y0) <= 64) {
-          const uint32_t qt = covered_tile(Ltm, q);
-          tx = x0 + (int)(qt % (uint32_t)w);
-          ty = y0 + (int)(qt / (uint32_t)w);
-        } else {
-          const float4 s0 = sp.rec[3 * si];
-          const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.rec[3 * si + 1].x);
-          const int2 t = nth_tile_by_rows(el, q, x0, x1, y0, y1, tg);
-          tx = t.x;
-          ty = t.y;
-        }
-        po.put((int64_t)Loff + q, (uint32_t)(toff + ty * tgx + tx), Ld, (uint32_t)si);
-      }
+      const uint32_t Loff = __shfl_sync(0xffffffffu, off, L), Lmag = __shfl_sync(0xffffffffu, mag, L);
+      const bool valid = g < total;
+      const int64_t si = b + L;
+      const uint32_t q = g - (Li - Ln);
+      const uint32_t x0 = Lrx & 0xFFFFu, w = (Lrx >> 16) - x0, y0 = Lry & 0xFFFFu;
+      TileGeom tg;
+      int tgx, toff;
+      ev.of(si, Nv, tg, tgx, toff);
+      const uint32_t qt = valid ? covered_tile(Ltm, q) : 0u;
+      const uint32_t dy = div_small(qt, Lmag);
+      const uint32_t tx = x0 + (qt - dy * w), ty = y0 + dy;
+      po.put(valid, (int64_t)Loff + q, (uint32_t)toff + ty * (uint32_t)tgx + tx, Ld, (uint32_t)si);
+    }
+    // splats of a few pairs in a large rectangle: the warp walks each one's rows
+    for (uint32_t m = __ballot_sync(0xffffffffu, rows); m; m &= m - 1u) {
+      const int L = __ffs(m) - 1;
+      const int64_t si = b + L;
+      const uint32_t Lrx = __shfl_sync(0xffffffffu, cur.rx, L), Lry = __shfl_sync(0xffffffffu, cur.ry, L);
+      const uint32_t Lcnt = __shfl_sync(0xffffffffu, cnt, L), Loff = __shfl_sync(0xffffffffu, cur.off, L);
+      const uint64_t Ld = depth_key(__shfl_sync(0xffffffffu, cur.db, L), kf);
+      if (po.hist && lane == L) count_run(hs, Ld >> po.lo_bit, po.dpass, Lcnt);
+      TileGeom tg;
+      int tgx, toff;
+      ev.of(si, Nv, tg, tgx, toff);
+      const float4 s0 = sp.rec[3 * si];
+      const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.rec[3 * si + 1].x);
+      emit_rows(po, el, (int)(Lrx & 0xFFFFu), (int)(Lrx >> 16), (int)(Lry & 0xFFFFu), (int)(Lry >> 16), 0u, Lcnt, Loff,
+                Ld, (uint32_t)si, tg, tgx, toff, lane);
     }
     // larger splats: their pieces to the list (one reservation per warp)
     const uint32_t np = big ? (cnt + kPiece - 1) / kPiece : 0u;
@@ -381,10 +446,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, in
 }
 
 // Pair emission, part 2: a warp per piece of kPiece pairs of a larger splat.
-// A rectangle of at most 64 tiles reads its tile mask; a larger one is walked
-// 32 rows at a time (a lane per row computes the row's run of kept columns,
-// a warp scan gives the rows' first pairs, and each pair of the piece in
-// those rows finds its row by a binary search over the scan).
+// A rectangle of at most 64 tiles reads its tile mask; a larger one has its
+// rows walked by the warp (emit_rows).
 __global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats sp, int64_t ncap, EmitViews ev,
                                                           const uint32_t *offsets, uint64_t *keys, uint32_t *vals,
                                                           int64_t pair_cap, KeyFormat kf, SortHist sh,
@@ -417,45 +480,20 @@ __global__ void __launch_bounds__(256) emit_pieces_kernel(const Ctl *ctl, Splats
     const uint32_t qa = k * kPiece, qb = min(cnt, qa + kPiece);
     if (w * (y1 - y0) <= 64) {
       const uint64_t tm = sp.tmask[i];
-      for (uint32_t q = qa + lane; q < qb; q += 32) {
-        const uint32_t qt = covered_tile(tm, q);
-        po.put((int64_t)off + q, (uint32_t)(toff + (y0 + (int)(qt / (uint32_t)w)) * tgx + x0 + (int)(qt % (uint32_t)w)),
-               dkey, (uint32_t)i);
+      const uint32_t mag = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
+      for (uint32_t q0 = qa; q0 < qb; q0 += 32) {
+        const uint32_t q = q0 + (uint32_t)lane;
+        const bool valid = q < qb;
+        const uint32_t qt = valid ? covered_tile(tm, q) : 0u;
+        const uint32_t dy = div_small(qt, mag);
+        po.put(valid, (int64_t)off + q, (uint32_t)(toff + (y0 + (int)dy) * tgx + x0 + (int)(qt - dy * (uint32_t)w)), dkey,
+               (uint32_t)i);
       }
       continue;
     }
     const float4 s0 = sp.rec[3 * i];
     const SplatEllipse el = splat_ellipse(s0.x, s0.y, s0.z, s0.w, sp.rec[3 * i + 1].x);
-    uint32_t base = 0;  // pairs in the rows before this group of 32
-    for (int r0 = y0; r0 < y1 && base < qb; r0 += 32) {
-      const int ty = r0 + lane;
-      const int2 sp2 = ty < y1 ? row_span(el, ty, x0, x1, tg) : make_int2(0, 0);
-      const uint32_t nr = sp2.y > sp2.x ? (uint32_t)(sp2.y - sp2.x) : 0u;
-      uint32_t incl = nr;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
-      }
-      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-      const uint32_t lo = max(qa, base), hi = min(qb, base + tot);
-      for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
-        const uint32_t q = g0 + (uint32_t)lane, rel = q - base;
-        // row: the number of rows whose inclusive count is <= rel
-        int L = 0;
-#pragma unroll
-        for (int st = 16; st >= 1; st >>= 1) {
-          const uint32_t v = __shfl_sync(0xffffffffu, incl, L + st - 1);
-          if (v <= rel) L += st;
-        }
-        L = min(L, 31);
-        const uint32_t Li = __shfl_sync(0xffffffffu, incl, L), Ln = __shfl_sync(0xffffffffu, nr, L);
-        const int Lc0 = __shfl_sync(0xffffffffu, sp2.x, L);
-        if (q < hi) po.put((int64_t)off + q, (uint32_t)(toff + (r0 + L) * tgx + Lc0 + (int)(rel - (Li - Ln))), dkey,
-                           (uint32_t)i);
-      }
-      base += tot;
-    }
+    emit_rows(po, el, x0, x1, y0, y1, qa, qb, off, dkey, (uint32_t)i, tg, tgx, toff, lane);
   }
   if (sh.hist) hist_flush(sh, hs);
 }
@@ -487,12 +525,6 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const Ctl *ctl, const ui
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ntiles * 256; j += stride) lb[j] = 0;
   }
   if (blockIdx.x == 0 && threadIdx.x < kMaxPasses) tile_ctr[threadIdx.x] = 0;
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
 }
 
 // Lanes of the warp holding the same digit as this lane (d < 0: an empty
@@ -600,6 +632,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
     uint32_t wpre = 0;
     for (int w = 0; w < warp; ++w) wpre += s_scan[w];
     s_doff[tid] = wpre + x - cnt;
+    __syncthreads();
+    // the tile in digit order in shared memory (its keys leave the registers
+    // before the look-back)
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const int d = dg[it];
+      if (d < 0) continue;
+      const uint32_t pos = s_doff[d] + s_wc[warp * 256 + d] + rk[it];
+      s_keys[pos] = k[it];
+      if (VALS) s_vals[pos] = v[it];
+    }
     // decoupled look-back, kLookWindow predecessors per round trip: the
     // words of tiles j, j-1, .. are read together and summed from the nearest
     // until an inclusive one (done) or one not yet published (read again from
@@ -637,15 +680,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) onesweep_kernel(Ctl *ctl, con
       *st = kFlagInc | ((excl + cnt) & kValMask);
     }
     s_glob[tid] = dbase + excl;
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-      const int d = dg[it];
-      if (d < 0) continue;
-      const uint32_t pos = s_doff[d] + s_wc[warp * 256 + d] + rk[it];
-      s_keys[pos] = k[it];
-      if (VALS) s_vals[pos] = v[it];
-    }
     __syncthreads();
     const int nvalid = (int)((M - t0) < kSortTile ? (M - t0) : kSortTile);
     for (int i = tid; i < nvalid; i += kSortThreads) {
