@@ -751,3 +751,75 @@ def _build_scene_mesh(dec, bp):
     px = dict(mesh=mp, assign=asg)
     return Scene(bp, n_pages, levels, err, counts, pages["src"], dec["src"], asg["verts"].astype(np.float32),
                  asg["tris"].astype(np.int32), asg["face_page"].astype(np.int32), link_ptr, link_col, px)
+
+
+# --------------------------------------------------------------------------- SH codebook (compressed pages)
+def sh_rest(sh):
+    """The view-dependent SH coefficients of [..., K, 3] arrays as vectors of
+    3 (K - 1) values in (coefficient, channel) order."""
+    return sh[..., 1:, :].reshape(sh.shape[:-2] + (3 * (sh.shape[-2] - 1),))
+
+
+def nearest_code(X, cb):
+    """Index of the nearest codeword (squared Euclidean distance in FP64, the
+    features summed in order, lowest index on a tie) for every row of X."""
+    C = cb.astype(np.float64)
+    d = np.zeros((len(X), len(C)))
+    for a in range(X.shape[1]):
+        t = X[:, None, a] - C[None, :, a]
+        d += t * t
+    return d.argmin(1)
+
+
+def quantize_sh(levels, n_codes, iters=10, n_train=65536):
+    """Vector quantisation of the view-dependent SH coefficients (bands 1..3)
+    into a codebook of n_codes vectors: the compression Sec. 6 leaves to
+    future work (codebooks of quantised attributes kept in GPU memory, so
+    that pages carry an index instead of the coefficients; the k-means
+    quantisation of SH is the related work of Sec. 2, Compression).
+      training set  the real (opacity > 0) level-0 Gaussians in slot order;
+                    when there are more than n_train, the ones at positions
+                    floor(j T / n_train), j < n_train
+      codebook      Lloyd's iterations (kmeans_lloyd) from the training
+                    vectors at positions floor(j T' / n_codes), rounded to fp32
+      codes         every Gaussian of every level (padding included) gets the
+                    nearest fp32 codeword (nearest_code)
+    Returns (codebook [n_codes, 3 (K - 1)] f32, codes: per level an int32
+    array [n_pages, m_l])."""
+    L0 = levels[0]
+    K = L0["sh"].shape[2]
+    if K < 2:
+        raise ValueError("SH degree 0: no view-dependent coefficients to quantise")
+    X0 = sh_rest(L0["sh"]).reshape(-1, 3 * (K - 1)).astype(np.float64)
+    T_all = X0[L0["opacity"].reshape(-1) > 0]
+    T = len(T_all)
+    nt = min(T, int(n_train))
+    if nt < n_codes or n_codes < 1:
+        raise ValueError("fewer training Gaussians than codes")
+    train = T_all[[j * T // nt for j in range(nt)]]
+    _, C = kmeans_lloyd(train, train[[j * nt // n_codes for j in range(n_codes)]], iters)
+    cb = C.astype(np.float32)
+    codes = []
+    for L in levels:
+        n_pages, m = L["opacity"].shape
+        X = sh_rest(L["sh"]).reshape(-1, 3 * (K - 1)).astype(np.float64)
+        codes.append(nearest_code(X, cb).astype(np.int32).reshape(n_pages, m))
+    return cb, codes
+
+
+def vq_levels(levels, cb, codes):
+    """The attributes a VQ page record carries, decoded: position and opacity
+    fp32; scale, rotation and the SH band 0 rounded to fp16; bands 1..3 the
+    Gaussian's codeword."""
+    out = []
+    for L, c in zip(levels, codes):
+        L = dict(L)
+        K = L["sh"].shape[2]
+        sh = np.empty_like(L["sh"])
+        sh[:, :, 0, :] = L["sh"][:, :, 0, :].astype(np.float16).astype(np.float32)
+        sh[:, :, 1:, :] = cb[c].reshape(c.shape + (K - 1, 3))
+        L["sh"] = sh
+        for k in ("scale", "rot"):
+            L[k] = L[k].astype(np.float16).astype(np.float32)
+        out.append(L)
+    return out
