@@ -134,7 +134,8 @@ typedef struct {
   int32_t feedback_ds;     /* visibility buffer is ceil(W/ds) x ceil(H/ds); ceil(max_height/ds) <= 16000 */
   int32_t links;           /* follow page links in the reduction */
   int32_t lod;             /* choose levels by screen-space error, adapt the threshold */
-  int32_t fp16_pool;       /* pool holds fp16 records (scene built with fp16 = 1) */
+  int32_t fp16_pool;       /* pool records: 0 fp32; 1 fp16 (scene built with fp16 = 1); 2 VQ with the
+                              SH codebook (after vm3dgs_scene_quantize_sh); all arithmetic is FP32 */
   float usage_lo, usage_hi;/* target band of pool usage (0.5, 0.8) */
   float tau0, step0;       /* initial screen-space error threshold and step, pixels */
   int32_t max_width, max_height; /* largest view rendered */
@@ -187,6 +188,8 @@ typedef struct {
   int64_t n_verts;
   int64_t n_links;
   int64_t host_bytes;      /* all page data held */
+  int32_t record_bytes_vq; /* VQ record (40 bytes), 0 until vm3dgs_scene_quantize_sh */
+  int32_t n_codes;         /* SH codebook entries, 0 until then */
 } vm3dgs_scene_info;
 
 /* Offline preparation (Sec. 3): decode (Sec. 3.5), page (Sec. 3.2), LOD
@@ -232,7 +235,9 @@ enum {
   VM3DGS_SCENE_TRIS = 6,        /* int32 [n_tris][3] */
   VM3DGS_SCENE_FACE_PAGE = 7,   /* int32 [n_tris] */
   VM3DGS_SCENE_LINK_PTR = 8,    /* int64 [n_pages+1] */
-  VM3DGS_SCENE_LINK_COL = 9     /* int32 [n_links] */
+  VM3DGS_SCENE_LINK_COL = 9,    /* int32 [n_links] */
+  VM3DGS_SCENE_CODEBOOK = 10,   /* float [n_codes][3 (K - 1)] SH codebook */
+  VM3DGS_SCENE_PAGES_VQ = 11    /* the level's page blocks in the VQ record */
 };
 int vm3dgs_scene_export(const vm3dgs_scene *s, int32_t what, int32_t level, void *dst, int64_t bytes,
                         int64_t *needed);
@@ -260,7 +265,34 @@ void vm3dgs_scene_destroy(vm3dgs_scene *s);
 int vm3dgs_scene_save(const vm3dgs_scene *s, const char *path);
 int vm3dgs_scene_open(const char *path, vm3dgs_scene **out);
 
+/* Compressed pages (Sec. 6 leaves them to future work: codebooks of
+ * quantised attributes kept in GPU memory, so that pages carry an index and
+ * less data is copied; Sec. 2, Compression, names k-means vector
+ * quantisation of the spherical harmonics).  Adds to the scene an SH
+ * codebook and a third page record, the VQ record (40 bytes at any SH
+ * degree, against 128 fp16 / 236 fp32 bytes at degree 3):
+ *   floats   position x, y, z, opacity
+ *   16 bit   scale (3), rotation (4), SH band 0 (3) as half; the index of
+ *            the Gaussian's codeword for SH bands 1..3; one padding word
+ * Codebook: n_codes vectors of the 3 (K - 1) view-dependent coefficients,
+ * (coefficient, channel) order, by Lloyd's iterations (at most `iters`,
+ * stopping when an assignment repeats; squared Euclidean distance in FP64,
+ * features summed in order, lowest index on a tie; a codeword without
+ * vectors stays) on the real level-0 Gaussians in slot order, or, when there
+ * are more than n_train, those at positions floor(j T / n_train); started
+ * from the training vectors at floor(j T' / n_codes); rounded to fp32.  Every
+ * Gaussian of every level (padding too) takes the nearest fp32 codeword.
+ * Host computation (OpenMP); the records are the scene's own memory.  A
+ * renderer with params.fp16_pool = 2 holds VQ records in its pool and the
+ * codebook in its scratch.  E_INVAL: SH degree 0, n_codes outside
+ * 1..65536, fewer training Gaussians than codes; E_STATE: the scene already
+ * holds VQ records (they are made once, before any renderer uses them).
+ * Not written by vm3dgs_scene_save (quantise again after opening). */
+int vm3dgs_scene_quantize_sh(vm3dgs_scene *s, int32_t n_codes, int32_t iters, int64_t n_train);
+
 /* Device memory the caller must provide for a renderer. */
+/* fp16_pool selects the record: 0 fp32, 1 fp16, 2 VQ (E_STATE if the scene
+ * lacks it) */
 int vm3dgs_pool_slot_bytes(const vm3dgs_scene *s, int32_t fp16_pool, int64_t *out);
 int vm3dgs_scratch_bytes(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t pool_bytes, int64_t *out);
 

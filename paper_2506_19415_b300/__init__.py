@@ -77,7 +77,8 @@ class Stats(ctypes.Structure):
 class SceneInfo(ctypes.Structure):
     _fields_ = [("n_pages", c_i32), ("page_size", c_i32), ("lod_levels", c_i32), ("lod_fanout", c_i32),
                 ("sh_degree", c_i32), ("n_gaussians", c_i64), ("record_bytes", c_i32), ("record_bytes16", c_i32),
-                ("n_tris", c_i64), ("n_verts", c_i64), ("n_links", c_i64), ("host_bytes", c_i64)]
+                ("n_tris", c_i64), ("n_verts", c_i64), ("n_links", c_i64), ("host_bytes", c_i64),
+                ("record_bytes_vq", c_i32), ("n_codes", c_i32)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "vm3dgs_scene_destroy": [c_p],
     "vm3dgs_scene_save": [c_p, ctypes.c_char_p],
     "vm3dgs_scene_open": [ctypes.c_char_p, ctypes.POINTER(c_p)],
+    "vm3dgs_scene_quantize_sh": [c_p, c_i32, c_i32, c_i64],
     "vm3dgs_pool_slot_bytes": [c_p, c_i32, ctypes.POINTER(c_i64)],
     "vm3dgs_scratch_bytes": [c_p, ctypes.POINTER(Params), c_i64, ctypes.POINTER(c_i64)],
     "vm3dgs_renderer_create": [c_p, ctypes.POINTER(Params), c_p, c_i64, c_p, c_i64, c_p, ctypes.POINTER(c_p)],
@@ -144,7 +146,9 @@ EXPORTED = tuple(_SIGS)
 
 # scene export / debug items (mirror the enums of include/vm3dgs.h)
 SCENE_PAGE_COUNT, SCENE_PAGE_SRC, SCENE_PAGES, SCENE_PAGES16, SCENE_ERR, SCENE_VERTS, SCENE_TRIS, \
-    SCENE_FACE_PAGE, SCENE_LINK_PTR, SCENE_LINK_COL = range(10)
+    SCENE_FACE_PAGE, SCENE_LINK_PTR, SCENE_LINK_COL, SCENE_CODEBOOK, SCENE_PAGES_VQ = range(12)
+# pool record formats (RenderConfig.fp16_pool; True / False stand for 1 / 0)
+POOL_FP32, POOL_FP16, POOL_VQ = 0, 1, 2
 (DBG_FEEDBACK, DBG_REQ, DBG_DIRECT, DBG_REQUESTS, DBG_PT_LOD, DBG_PT_LAST, DBG_PT_SLOT, DBG_COPIES, DBG_DRAW,
  DBG_MISSING, DBG_SPLAT_RECT, DBG_SPLAT_DEPTH, DBG_SPLAT_RADIUS, DBG_KEYS, DBG_VALUES, DBG_RANGES, DBG_SPLAT_XY,
  DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK, DBG_SPLAT_TOUCHED) = range(23)
@@ -265,6 +269,26 @@ class Scene:
 
     def m(self, l):
         return self.info.page_size // self.info.lod_fanout ** l
+
+    def quantize_sh(self, n_codes, iters=10, n_train=65536):
+        """Adds the SH codebook and the VQ page records (compressed pages,
+        pool format POOL_VQ); the scene must not have them yet."""
+        _check(_lib.vm3dgs_scene_quantize_sh(self.h, int(n_codes), int(iters), int(n_train)))
+        inf = SceneInfo()
+        _check(_lib.vm3dgs_scene_info_get(self.h, ctypes.byref(inf)))
+        self.info = inf
+
+    def codebook(self):
+        """The SH codebook as [n_codes, 3 (K - 1)] float32."""
+        return self.export(SCENE_CODEBOOK, 0, np.float32).reshape(self.info.n_codes, -1)
+
+    def vq_codes(self, level=0):
+        """The codebook index of every Gaussian of a level, [n_pages, m] int32
+        (16-bit row 10 of the VQ record)."""
+        m = self.m(level)
+        b = self.export(SCENE_PAGES_VQ, level).reshape(self.info.n_pages, -1)
+        h = b[:, 16 * m:].copy().view(np.uint16).reshape(self.info.n_pages, 12, m)
+        return h[:, 10, :].astype(np.int32)
 
     def pages(self, level=0, fp16=False):
         """Page blocks of a level as [n_pages, bytes] uint8."""

@@ -19,7 +19,7 @@ EXACT = {"k_project.cu", "k_feedback.cu", "k_residency.cu", "k_prefetch.cu", "k_
 CU = ["k_project.cu", "k_feedback.cu", "k_residency.cu", "k_stream.cu", "k_sort.cu", "k_blend.cu", "renderer.cu",
       "k_mlp.cu", "prefetcher.cu", "k_prefetch.cu",
       "sort_noalloc.cu", "batch.cu", "k_mesh.cu"]
-CPP = ["build_pages.cpp", "scene.cpp", "mesh_proxy.cpp"]
+CPP = ["build_pages.cpp", "scene.cpp", "mesh_proxy.cpp", "vq.cpp"]
 HEADERS = ["renderer.cuh", "scene.h", "mlp.cuh", "prefetcher.cuh", "block_sel.cuh", "tma.cuh", "coverage.cuh", "mesh.h"]
 
 

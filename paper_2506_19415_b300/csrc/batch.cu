@@ -75,7 +75,8 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   pa.page_size = s->page_size;
   pa.fanout = s->fanout;
   pa.K = s->K;
-  pa.fp16 = r->fp16;
+  pa.fmt = r->fmt;
+  pa.codebook = r->fmt == kFmtVQ ? r->at<float>(r->lay.codebook) : nullptr;
   pa.ncap = r->dims.ncap;
   pa.sp = sp;
   const int n = t.n;

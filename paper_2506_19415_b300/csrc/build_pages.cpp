@@ -124,8 +124,10 @@ void rot_to_quat(const double R[3][3], double *q) {
   for (int i = 0; i < 4; ++i) q[i] = sg * q[i] / n;
 }
 
+}  // namespace
+
 // IEEE binary32 -> binary16, round to nearest even (handles subnormals, overflow to inf)
-uint16_t f32_to_f16(float f) {
+uint16_t vm::f32_to_f16(float f) {
   uint32_t x;
   std::memcpy(&x, &f, 4);
   uint32_t sign = (x >> 16) & 0x8000u;
@@ -149,6 +151,9 @@ uint16_t f32_to_f16(float f) {
   if (rem > 0x1000u || (rem == 0x1000u && (h & 1))) ++h;   // may carry into the exponent: still correct
   return (uint16_t)(sign | h);
 }
+
+namespace {
+using vm::f32_to_f16;
 
 struct Decoded {
   int64_t n = 0;

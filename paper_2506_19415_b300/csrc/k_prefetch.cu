@@ -414,7 +414,7 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   sa.copies = a.copies;
   sa.copy_seg = a.copy_seg;
   sa.host = r->host_dev;
-  for (int l = 0; l < s->levels; ++l) sa.level_off[l] = r->fp16 ? s->off16[l] : s->off32[l];
+  for (int l = 0; l < s->levels; ++l) sa.level_off[l] = s->fmt_off(r->fmt)[l];
   sa.page_size = s->page_size;
   sa.fanout = s->fanout;
   sa.rec = r->rec;

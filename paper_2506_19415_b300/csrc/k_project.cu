@@ -16,7 +16,9 @@
 // of a slot is a contiguous block of m_l Gaussians in structure-of-arrays
 // form (attribute a of Gaussian g at a * m_l + g), so consecutive threads
 // read consecutive words of every attribute.  fp16 pools keep position and
-// opacity in float and scale, rotation and SH in half.
+// opacity in float and scale, rotation and SH in half; VQ pools (compressed
+// pages) keep SH band 0 in half and the index of a codeword of the SH
+// codebook (in device memory) for bands 1..3.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -27,32 +29,39 @@
 namespace vm {
 namespace {
 
-template <int K, bool F16>
+// FMT: kFmt32 (all attributes float rows), kFmt16 (position and opacity
+// float rows, the rest half rows) or kFmtVQ (as kFmt16 for SH band 0, the
+// codebook index of bands 1..3 in 16-bit row 10).
+template <int K, int FMT>
 struct Rec {
   // attribute loaders for one Gaussian of a block of m
   __device__ static float pos(const uint8_t *b, int m, int g, int a) {
     return reinterpret_cast<const float *>(b)[(int64_t)a * m + g];
   }
   __device__ static float opac(const uint8_t *b, int m, int g) {
-    return reinterpret_cast<const float *>(b)[(int64_t)(F16 ? 3 : 10) * m + g];
+    return reinterpret_cast<const float *>(b)[(int64_t)(FMT != kFmt32 ? 3 : 10) * m + g];
+  }
+  __device__ static const uint16_t *row16(const uint8_t *b, int m, int h) {
+    return reinterpret_cast<const uint16_t *>(b + (int64_t)16 * m) + (int64_t)h * m;
   }
   __device__ static float half_at(const uint8_t *b, int m, int g, int h) {
-    const __half *hp = reinterpret_cast<const __half *>(b + (int64_t)16 * m);
-    return __half2float(hp[(int64_t)h * m + g]);
+    return __half2float(__ushort_as_half(row16(b, m, h)[g]));
   }
   __device__ static float scale(const uint8_t *b, int m, int g, int a) {
-    if (F16) return half_at(b, m, g, a);
+    if (FMT != kFmt32) return half_at(b, m, g, a);
     return reinterpret_cast<const float *>(b)[(int64_t)(3 + a) * m + g];
   }
   __device__ static float rot(const uint8_t *b, int m, int g, int a) {
-    if (F16) return half_at(b, m, g, 3 + a);
+    if (FMT != kFmt32) return half_at(b, m, g, 3 + a);
     return reinterpret_cast<const float *>(b)[(int64_t)(6 + a) * m + g];
   }
+  // (VQ: band 0 only; bands 1..3 come from the codeword)
   __device__ static float sh(const uint8_t *b, int m, int g, int k, int c) {
-    if (F16) return half_at(b, m, g, 7 + 3 * k + c);
+    if (FMT != kFmt32) return half_at(b, m, g, 7 + 3 * k + c);
     return reinterpret_cast<const float *>(b)[(int64_t)(11 + 3 * k + c) * m + g];
   }
-  static constexpr int kRec = F16 ? rec_bytes16(K) : rec_bytes32(K);
+  __device__ static uint32_t code(const uint8_t *b, int m, int g) { return row16(b, m, 10)[g]; }
+  static constexpr int kRec = FMT == kFmtVQ ? rec_bytes_vq() : FMT == kFmt16 ? rec_bytes16(K) : rec_bytes32(K);
 };
 
 // real SH basis (l <= 3, m = -l..l), Condon-Shortley phase; the constants are
@@ -68,36 +77,52 @@ struct Rec {
 #define SHC3D 0.3731763325901154f
 #define SHC3E 1.445305721320277f
 
-// Attributes of Gaussian g of a level block of m Gaussians in the pool.
-template <int K, bool F16>
+// Attributes of Gaussian g of a level block of m Gaussians in the pool; for
+// VQ pools cw is its codeword (bands 1..3 of the SH).
+template <int K, int FMT>
 struct GlobalSrc {
-  using R = Rec<K, F16>;
+  using R = Rec<K, FMT>;
   const uint8_t *blk;
   int m, g;
+  const float *cw;
+  __device__ GlobalSrc(const uint8_t *b, int m_, int g_, const float *codebook) : blk(b), m(m_), g(g_), cw(nullptr) {
+    if (FMT == kFmtVQ) cw = codebook + (int64_t)R::code(b, m_, g_) * (3 * (K - 1));
+  }
   __device__ float pos(int a) const { return R::pos(blk, m, g, a); }
   __device__ float opac() const { return R::opac(blk, m, g); }
   __device__ float scale(int a) const { return R::scale(blk, m, g, a); }
   __device__ float rot(int a) const { return R::rot(blk, m, g, a); }
-  __device__ float sh(int k, int c) const { return R::sh(blk, m, g, k, c); }
+  __device__ float sh(int k, int c) const {
+    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 3 * (k - 1) + c);
+    return R::sh(blk, m, g, k, c);
+  }
 };
 
 // The same attributes staged in shared memory: the record's float rows (A)
-// and half rows (B) of a chunk of CH Gaussians, row after row.
-template <int K, bool F16, int CH>
+// and 16-bit rows (B) of a chunk of CH Gaussians, row after row.
+template <int K, int FMT, int CH>
 struct SharedSrc {
   const float *A;
   const __half *B;
   int g;
+  const float *cw;
+  __device__ SharedSrc(const float *a, const __half *b, int g_, const float *codebook) : A(a), B(b), g(g_), cw(nullptr) {
+    if (FMT == kFmtVQ)
+      cw = codebook + (int64_t)__half_as_ushort(B[10 * CH + g_]) * (3 * (K - 1));
+  }
   __device__ float half_at(int h) const { return __half2float(B[h * CH + g]); }
   __device__ float pos(int a) const { return A[a * CH + g]; }
-  __device__ float opac() const { return A[(F16 ? 3 : 10) * CH + g]; }
-  __device__ float scale(int a) const { return F16 ? half_at(a) : A[(3 + a) * CH + g]; }
-  __device__ float rot(int a) const { return F16 ? half_at(3 + a) : A[(6 + a) * CH + g]; }
-  __device__ float sh(int k, int c) const { return F16 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * CH + g]; }
+  __device__ float opac() const { return A[(FMT != kFmt32 ? 3 : 10) * CH + g]; }
+  __device__ float scale(int a) const { return FMT != kFmt32 ? half_at(a) : A[(3 + a) * CH + g]; }
+  __device__ float rot(int a) const { return FMT != kFmt32 ? half_at(3 + a) : A[(6 + a) * CH + g]; }
+  __device__ float sh(int k, int c) const {
+    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 3 * (k - 1) + c);
+    return FMT != kFmt32 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * CH + g];
+  }
 };
 
 // Projects one Gaussian for one camera and writes splat record out.
-template <int K, bool F16, class Src>
+template <int K, int FMT, class Src>
 __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const Src &src, int64_t out) {
   const float *V = cam.view;
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w;
@@ -238,9 +263,9 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
   sp.tmask[out] = tmask;
 }
 
-template <int K, bool F16>
+template <int K, int FMT>
 __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_camera cam) {
-  using R = Rec<K, F16>;
+  using R = Rec<K, FMT>;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
   if (blockIdx.x == 0 && threadIdx.x == 0) a.rctl->r_drawn = a.ctl->draw_gauss;
   const int nd = a.ctl->n_draw;
@@ -266,14 +291,14 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_came
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, F16>(a.sp, cam, GlobalSrc<K, F16>{blk, m, g}, i);
+    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), i);
   }
 }
 
 // All views at once: blockIdx.y is the view; splat record v * N + i.
-template <int K, bool F16>
+template <int K, int FMT>
 __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, const ViewTable *views) {
-  using R = Rec<K, F16>;
+  using R = Rec<K, FMT>;
   const int v = blockIdx.y;
   if (v >= views->n) return;
   const vm3dgs_camera cam = views->cam[v];
@@ -301,24 +326,24 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, F16>(a.sp, cam, GlobalSrc<K, F16>{blk, m, g}, (int64_t)v * N + i);
+    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), (int64_t)v * N + i);
   }
 }
 
 // Projection with the records staged by tile loads of the tensor memory
 // accelerator: a CTA of 128 threads takes items of two 64-Gaussian chunks
 // (every level block is a multiple of 64); warp 0 finds their draw entries
-// and issues the tile loads (float rows, and half rows for fp16 pools) of the
+// and issues the tile loads (float rows, and 16-bit rows for fp16 and VQ pools) of the
 // next item while the CTA projects the current one from shared memory (two
 // stages).  A wait that expires records VM3DGS_E_TIMEOUT and ends the CTA
 // after its copies in flight have landed.
 constexpr int kMbarPolls = 1 << 20;
 
 // CH Gaussians per chunk (64 or 32), 128 / CH chunks per CTA of 128 threads
-template <int K, bool F16, int CH>
+template <int K, int FMT, int CH>
 struct TmaShape {
-  static constexpr int NA = F16 ? 4 : 11 + 3 * K;                // float rows
-  static constexpr int NH = F16 ? ((7 + 3 * K + 1) & ~1) : 0;    // half rows
+  static constexpr int NA = FMT != kFmt32 ? 4 : n_attr32(K);                              // float rows
+  static constexpr int NH = FMT == kFmtVQ ? kHalfVQ : FMT == kFmt16 ? n_half16(K) : 0;   // 16-bit rows
   static constexpr int ABYTES = NA * CH * 4, BBYTES = NH * CH * 2;
   static constexpr int CHUNK = ABYTES + BBYTES;
   static constexpr int PER = 128 / CH;                            // chunks per CTA item
@@ -326,10 +351,10 @@ struct TmaShape {
   static constexpr int SMEM = 2 * STAGE + 64;                     // + barriers
 };
 
-template <int K, bool F16, int CH>
+template <int K, int FMT, int CH>
 __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_camera cam,
                                                           const __grid_constant__ ProjMaps maps) {
-  using S = TmaShape<K, F16, CH>;
+  using S = TmaShape<K, FMT, CH>;
   constexpr int kChunk = CH, kChunksPerCta = S::PER;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
@@ -382,7 +407,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
         const int u = d.z * sub + d.w;  // level block of the whole pool
         const int g0 = (int)((it * kChunksPerCta + j) * kChunk - a.draw_off[e[j]]);
         tma_load_3d(buf + j * S::CHUNK, &maps.a[d.y], g0, 0, u, &bar[stg]);
-        if (F16) tma_load_3d(buf + j * S::CHUNK + S::ABYTES, &maps.b[d.y], g0, 0, u, &bar[stg]);
+        if (FMT != kFmt32) tma_load_3d(buf + j * S::CHUNK + S::ABYTES, &maps.b[d.y], g0, 0, u, &bar[stg]);
       }
     }
     __syncwarp();
@@ -413,9 +438,9 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
     const int64_t c = item * kChunksPerCta + ch;
     if (c < nchunks) {
       const uint8_t *buf = smem + stg * S::STAGE + ch * S::CHUNK;
-      const SharedSrc<K, F16, CH> src{reinterpret_cast<const float *>(buf),
-                                  reinterpret_cast<const __half *>(buf + S::ABYTES), g};
-      project_one<K, F16>(a.sp, cam, src, c * kChunk + g);
+      const SharedSrc<K, FMT, CH> src(reinterpret_cast<const float *>(buf),
+                                      reinterpret_cast<const __half *>(buf + S::ABYTES), g, a.codebook);
+      project_one<K, FMT>(a.sp, cam, src, c * kChunk + g);
     }
     __syncthreads();  // the stage is refilled by the next-but-one item
   }
@@ -438,41 +463,47 @@ void launch_kb(const ProjectArgs &a, const ViewTable *views, int n_views, cudaSt
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, (unsigned)n_views);
-  if (a.fp16)
-    project_batched_kernel<K, true><<<grid, 256, 0, st>>>(a, views);
+  if (a.fmt == kFmtVQ)
+    project_batched_kernel<K, kFmtVQ><<<grid, 256, 0, st>>>(a, views);
+  else if (a.fmt == kFmt16)
+    project_batched_kernel<K, kFmt16><<<grid, 256, 0, st>>>(a, views);
   else
-    project_batched_kernel<K, false><<<grid, 256, 0, st>>>(a, views);
+    project_batched_kernel<K, kFmt32><<<grid, 256, 0, st>>>(a, views);
 }
 
-template <int K, bool F16, int CH>
+template <int K, int FMT, int CH>
 void launch_tma(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
-  using S = TmaShape<K, F16, CH>;
+  using S = TmaShape<K, FMT, CH>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(project_tma_kernel<K, F16, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    prefer_shared((const void *)project_tma_kernel<K, F16, CH>);
+    cudaFuncSetAttribute(project_tma_kernel<K, FMT, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    prefer_shared((const void *)project_tma_kernel<K, FMT, CH>);
     attr = true;
   }
-  project_tma_kernel<K, F16, CH>
-      <<<full_wave((const void *)project_tma_kernel<K, F16, CH>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
+  project_tma_kernel<K, FMT, CH>
+      <<<full_wave((const void *)project_tma_kernel<K, FMT, CH>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
 }
 
 template <int K>
 void launch_k(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
   if (a.maps) {
     if (a.maps->chunk == 64)
-      a.fp16 ? launch_tma<K, true, 64>(a, cam, st) : launch_tma<K, false, 64>(a, cam, st);
+      a.fmt == kFmtVQ ? launch_tma<K, kFmtVQ, 64>(a, cam, st)
+      : a.fmt == kFmt16 ? launch_tma<K, kFmt16, 64>(a, cam, st) : launch_tma<K, kFmt32, 64>(a, cam, st);
     else
-      a.fp16 ? launch_tma<K, true, 32>(a, cam, st) : launch_tma<K, false, 32>(a, cam, st);
+      a.fmt == kFmtVQ ? launch_tma<K, kFmtVQ, 32>(a, cam, st)
+      : a.fmt == kFmt16 ? launch_tma<K, kFmt16, 32>(a, cam, st) : launch_tma<K, kFmt32, 32>(a, cam, st);
     return;
   }
   int64_t blocks = (a.ncap + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   if (blocks < 1) blocks = 1;
-  if (a.fp16)
-    project_kernel<K, true><<<(unsigned)blocks, 256, 0, st>>>(a, cam);
+  if (a.fmt == kFmtVQ)
+    project_kernel<K, kFmtVQ><<<(unsigned)blocks, 256, 0, st>>>(a, cam);
+  else if (a.fmt == kFmt16)
+    project_kernel<K, kFmt16><<<(unsigned)blocks, 256, 0, st>>>(a, cam);
   else
-    project_kernel<K, false><<<(unsigned)blocks, 256, 0, st>>>(a, cam);
+    project_kernel<K, kFmt32><<<(unsigned)blocks, 256, 0, st>>>(a, cam);
 }
 
 }  // namespace
@@ -495,7 +526,7 @@ void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t
   }
 }
 
-bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, bool fp16, ProjMaps *out) {
+bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, int fmt, ProjMaps *out) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     void *fn = nullptr;
@@ -516,9 +547,9 @@ bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, boo
   const int kChunk = chunk;
   out->chunk = chunk;
   const int K = s->K;
-  const cuuint32_t NA = fp16 ? 4u : (cuuint32_t)(11 + 3 * K);
-  const cuuint32_t NH = fp16 ? (cuuint32_t)((7 + 3 * K + 1) & ~1) : 0u;
-  const int64_t rec = fp16 ? s->rec16 : s->rec32;
+  const cuuint32_t NA = fmt != kFmt32 ? 4u : (cuuint32_t)n_attr32(K);
+  const cuuint32_t NH = fmt == kFmtVQ ? (cuuint32_t)kHalfVQ : fmt == kFmt16 ? (cuuint32_t)n_half16(K) : 0u;
+  const int64_t rec = s->fmt_rec(fmt);
   int64_t sub = 1;
   for (int l = 0; l < s->levels; ++l) {
     const int64_t m = s->page_size / sub;
@@ -531,7 +562,7 @@ bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, boo
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
-    if (fp16) {
+    if (fmt != kFmt32) {
       const cuuint32_t boxB[3] = {(cuuint32_t)kChunk, NH, 1};
       const cuuint64_t dimB[3] = {(cuuint64_t)m, NH, nsub};
       const cuuint64_t strB[2] = {(cuuint64_t)(m * 2), (cuuint64_t)(m * rec)};

@@ -115,6 +115,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
+  d.cb_floats = p->fp16_pool == kFmtVQ ? (int64_t)s->codebook.size() : 0;
   return d;
 }
 
@@ -172,6 +173,7 @@ Layout make_layout(const Dims &d) {
   L.pf_base = take(16);
   L.pf_req = take(4 * NP);
   L.views = take(sizeof(ViewTable));
+  L.codebook = take(4 * d.cb_floats);
   for (int k = 0; k < kContexts; ++k) {
     CtxLayout &C = L.cx[k];
     C.ctl = take(sizeof(Ctl));
@@ -218,8 +220,10 @@ using namespace vm;
 
 extern "C" int vm3dgs_pool_slot_bytes(const vm3dgs_scene *s, int32_t fp16_pool, int64_t *out) {
   if (!s || !out) return fail(VM3DGS_E_INVAL, "null argument");
-  if (fp16_pool && !s->rec16) return fail(VM3DGS_E_STATE, "scene built without fp16 records");
-  *out = (int64_t)s->page_size * (fp16_pool ? s->rec16 : s->rec32);
+  if (fp16_pool < kFmt32 || fp16_pool > kFmtVQ) return fail(VM3DGS_E_INVAL, "pool format must be 0, 1 or 2");
+  if (fp16_pool == kFmt16 && !s->rec16) return fail(VM3DGS_E_STATE, "scene built without fp16 records");
+  if (fp16_pool == kFmtVQ && !s->data_vq) return fail(VM3DGS_E_STATE, "scene has no VQ records (vm3dgs_scene_quantize_sh)");
+  *out = (int64_t)s->page_size * s->fmt_rec(fp16_pool);
   return VM3DGS_OK;
 }
 
@@ -263,8 +267,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   r->pool_bytes = pool_bytes;
   r->slot_bytes = slot;
   r->P = (int32_t)P;
-  r->fp16 = p->fp16_pool != 0;
-  r->rec = r->fp16 ? s->rec16 : s->rec32;
+  r->fmt = p->fp16_pool;
+  r->rec = s->fmt_rec(r->fmt);
   r->scratch = (uint8_t *)scratch_dev;
   r->dims = d;
   r->lay = L;
@@ -272,10 +276,10 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   // page-lock the pages the GPU will pull, once per scene; a scene mapped
   // from a file is read by the host into a page-locked staging buffer instead
   auto *ms = const_cast<vm3dgs_scene *>(s);
-  uint8_t *data = r->fp16 ? ms->data16 : ms->data32;
-  const int64_t bytes = r->fp16 ? ms->bytes16 : ms->bytes32;
-  bool &reg = r->fp16 ? ms->registered16 : ms->registered32;
-  if (ms->mapped) {
+  uint8_t *data = ms->fmt_data(r->fmt);
+  const int64_t bytes = ms->fmt_bytes(r->fmt);
+  bool &reg = ms->fmt_registered(r->fmt);
+  if (ms->mapped && r->fmt != kFmtVQ) {
     r->staged = true;
     const size_t sbytes = (size_t)((p->staging_bytes + 4095) / 4096 * 4096);
     if (!cuda_ok(cudaHostAlloc((void **)&r->staging, sbytes > 0 ? sbytes : 4096, cudaHostAllocMapped), "cudaHostAlloc",
@@ -313,7 +317,10 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
     ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.clusters), cl.data(), sizeof(Cluster) * (size_t)r->ncl,
                                   cudaMemcpyHostToDevice), "copy", &rc);
   }
-  r->maps_ok = encode_proj_maps(s, r->pool, P, r->fp16, &r->maps);
+  r->maps_ok = encode_proj_maps(s, r->pool, P, r->fmt, &r->maps);
+  if (r->fmt == kFmtVQ)
+    ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.codebook), s->codebook.data(), 4 * s->codebook.size(),
+                                       cudaMemcpyHostToDevice, st), "copy", &rc);
   r->rec_maps_ok = true;
   for (int k = 0; k < kContexts; ++k)
     r->rec_maps_ok = r->rec_maps_ok && encode_rec_map(r->at<float4>(L.cx[k].splat_rec), d.ncap, &r->rec_map[k]);
@@ -503,12 +510,12 @@ void CUDART_CB gather_staged(void *user) {
     for (int i = 0; i <= n; ++i) r->h_off[i] = 0;
     return;
   }
-  const uint8_t *base = r->fp16 ? s->data16 : s->data32;
+  const uint8_t *base = s->fmt_data(r->fmt);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int i = 0; i < n; ++i) {
     const int4 c = r->h_copies[i];
     const int64_t pb = (int64_t)s->m(c.y) * r->rec;
-    const int64_t lo = r->fp16 ? s->off16[c.y] : s->off32[c.y];
+    const int64_t lo = s->fmt_off(r->fmt)[c.y];
     std::memcpy(r->staging + r->h_off[i], base + lo + (int64_t)c.x * pb, (size_t)pb);
   }
 }
@@ -584,7 +591,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   sa.copies = a.copies;
   sa.copy_seg = a.copy_seg;
   sa.host = r->host_dev;
-  for (int l = 0; l < s->levels; ++l) sa.level_off[l] = r->fp16 ? s->off16[l] : s->off32[l];
+  for (int l = 0; l < s->levels; ++l) sa.level_off[l] = s->fmt_off(r->fmt)[l];
   sa.page_size = s->page_size;
   sa.fanout = s->fanout;
   sa.rec = r->rec;
@@ -701,7 +708,8 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
   pa.page_size = s->page_size;
   pa.fanout = s->fanout;
   pa.K = s->K;
-  pa.fp16 = r->fp16;
+  pa.fmt = r->fmt;
+  pa.codebook = r->fmt == kFmtVQ ? r->at<float>(r->lay.codebook) : nullptr;
   pa.ncap = r->dims.ncap;
   pa.sp = sp;
   pa.maps = r->maps_ok ? &r->maps : nullptr;

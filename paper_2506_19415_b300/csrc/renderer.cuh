@@ -61,7 +61,7 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
       clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
-      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, total;
+      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, codebook, total;
   CtxLayout cx[kContexts];
 };
 
@@ -72,6 +72,7 @@ struct Dims {
   int64_t ncl_cap;  // proxy clusters (at most 32 triangles of one page each)
   int64_t piece_cap;  // pieces of 256 pairs of the splats with more than 32 pairs (at most pairs / 28)
   int64_t nviews;  // views a batch may hold (max_views)
+  int64_t cb_floats;  // VQ pools: floats of the SH codebook (0 otherwise)
 };
 
 Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P);
@@ -159,7 +160,7 @@ struct StreamArgs {
   const int32_t *count;         // number of copies (device)
   const int4 *copies;
   const int64_t *copy_seg;
-  const uint8_t *host;          // device-visible pointer to the scene's page data (fp32 or fp16)
+  const uint8_t *host;          // device-visible pointer to the scene's page data (the pool's record)
   const int64_t *staged_off;    // null, or the byte offset in `host` of each copy (a staging buffer)
   int64_t level_off[kMaxLevels];
   int32_t page_size, fanout, rec;
@@ -169,7 +170,7 @@ struct StreamArgs {
 void launch_stream(const StreamArgs &a, cudaStream_t st);
 
 // Tensor maps of the pool, one per level: the record's float rows (a) and,
-// for fp16 pools, its half rows (b), each as (Gaussian of the level block,
+// for fp16 and VQ pools, its 16-bit rows (b), each as (Gaussian of the level block,
 // row, level block of the whole pool), loaded `chunk` Gaussians at a time
 // (64, or 32 when a level block holds 32 Gaussians).
 struct ProjMaps {
@@ -184,14 +185,15 @@ struct ProjectArgs {
   const int64_t *draw_off;
   const uint8_t *pool;
   int64_t slot_bytes;
-  int32_t page_size, fanout, K, fp16;
+  int32_t page_size, fanout, K, fmt;  // fmt: kFmt32, kFmt16 or kFmtVQ
+  const float *codebook;              // VQ pools: the SH codebook [codes][3 (K - 1)] in device memory
   int64_t ncap;
   Splats sp;
   const ProjMaps *maps;  // host copy; null: gather from the pool with plain loads
 };
 // Encodes the pool's tensor maps; false when a level block is not a multiple
 // of 32 Gaussians or the driver refuses (the projection then gathers).
-bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, bool fp16, ProjMaps *out);
+bool encode_proj_maps(const vm3dgs_scene *s, const uint8_t *pool, int64_t P, int fmt, ProjMaps *out);
 void launch_project(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st);
 
 // Cameras of a batched render, in device memory.
@@ -297,7 +299,7 @@ struct vm3dgs_renderer {
   int64_t pool_bytes = 0, slot_bytes = 0;
   int32_t P = 0;
   int32_t rec = 0;
-  bool fp16 = false;
+  int32_t fmt = 0;  // pool record: vm::kFmt32, kFmt16 or kFmtVQ
   uint8_t *scratch = nullptr;
   vm::Dims dims{};
   vm::Layout lay{};

@@ -63,6 +63,9 @@ void finish_scene(vm3dgs_scene *S) {
 }  // namespace vm
 
 vm3dgs_scene::~vm3dgs_scene() {
+  // (VQ records are built in host memory, for mapped scenes too)
+  if (registered_vq && data_vq) cudaHostUnregister(data_vq);
+  std::free(data_vq);
   if (mapped) {
     if (map_base) munmap(map_base, map_len);
     return;
@@ -224,7 +227,9 @@ extern "C" int vm3dgs_scene_info_get(const vm3dgs_scene *s, vm3dgs_scene_info *o
   o->n_tris = (int64_t)s->face_page.size();
   o->n_verts = (int64_t)s->verts.size() / 3;
   o->n_links = (int64_t)s->link_col.size();
-  o->host_bytes = s->bytes32 + s->bytes16;
+  o->host_bytes = s->bytes32 + s->bytes16 + s->bytes_vq;
+  o->record_bytes_vq = s->data_vq ? s->rec_vq : 0;
+  o->n_codes = s->data_vq ? s->n_codes : 0;
   return VM3DGS_OK;
 }
 
@@ -258,6 +263,12 @@ extern "C" int vm3dgs_scene_export(const vm3dgs_scene *s, int32_t what, int32_t 
       return copy_out(s->face_page.data(), 4 * (int64_t)s->face_page.size(), dst, bytes, needed);
     case VM3DGS_SCENE_LINK_PTR: return copy_out(s->link_ptr.data(), 8 * (int64_t)s->link_ptr.size(), dst, bytes, needed);
     case VM3DGS_SCENE_LINK_COL: return copy_out(s->link_col.data(), 4 * (int64_t)s->link_col.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_CODEBOOK:
+      if (!s->data_vq) return vm::fail(VM3DGS_E_STATE, "scene has no SH codebook");
+      return copy_out(s->codebook.data(), 4 * (int64_t)s->codebook.size(), dst, bytes, needed);
+    case VM3DGS_SCENE_PAGES_VQ:
+      if (!s->data_vq) return vm::fail(VM3DGS_E_STATE, "scene has no VQ records");
+      return copy_out(s->data_vq + s->off_vq[level], NP * s->m(level) * (int64_t)s->rec_vq, dst, bytes, needed);
     default: return vm::fail(VM3DGS_E_INVAL, "unknown export item");
   }
 }

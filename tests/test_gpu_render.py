@@ -20,10 +20,13 @@ def v():
     return mod
 
 
-def _full_render(v, raw, sc, cam, fp16=False, separate_values=False, sort_mode=0):
+def _full_render(v, raw, sc, cam, fp16=False, separate_values=False, sort_mode=0, vq_codes=0):
     scene = import_scene(v, raw, sc, fp16=fp16)
+    if vq_codes:
+        scene.quantize_sh(vq_codes, 8)
     cfg = v.RenderConfig(max_width=cam.width, max_height=cam.height, lod=False, staging_bytes=1 << 40,
-                         fp16_pool=fp16, separate_values=separate_values, sort_mode=sort_mode)
+                         fp16_pool=v.POOL_VQ if vq_codes else fp16, separate_values=separate_values,
+                         sort_mode=sort_mode)
     r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
     r.request_all()
     r.update_residency()
@@ -103,8 +106,9 @@ def test_crowded_tiles(v):
 def test_large_splat_binning(v, tile):
     """Gaussians close to a ragged 250x131 view, half of them stretched along
     one axis: many rectangles hold more than 64 tiles, some with at most 32
-    kept tiles (dealt out by lanes walking their rows) and some with more
-    (cut into pieces of 256 pairs whose rows a warp walks).  Tile counts, keys, values and
+    kept tiles (their rows walked by the whole warp in the first emission
+    kernel) and some with more (cut into pieces of 256 pairs whose rows a
+    warp walks).  Tile counts, keys, values and
     ranges equal the oracle's bit for bit; the image is within tolerance."""
     raw = scenegen.uniform_scene(n=6000, seed=41, lo=-1.6, hi=1.6, ls_mu=-3.2, ls_sd=0.6, sh_degree=1)
     raw.log_scale[::2, 0] += np.float32(2.0)
@@ -192,3 +196,34 @@ def test_fp16_pool_parity_and_psnr(v):
     mse = np.mean((np.clip(img, 0, 1) - np.clip(ref32["image"], 0, 1)) ** 2)
     psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
     assert psnr >= 45.0, psnr
+
+
+def test_vq_pool_parity(v):
+    """Compressed pages (VQ records, a 128-code SH codebook) through the
+    TMA-staged projection: discrete results equal the oracle run on the
+    attributes the records decode to, the image within the FP32 tolerance;
+    the PSNR against the FP64 render of the fp32 scene is reported."""
+    import dataclasses
+    from oracle import build as ob
+    raw = scenegen.blob_scene(n=20000, n_blobs=20, lo=-4.0, hi=4.0, blob_sigma=0.4, seed=31)
+    bp = ob.BuildParams(page_size=512, paging="octree", lo=(-8, -8, -8), hi=(8, 8, 8), voxel=0.5, kappa=1.0,
+                        link_samples=0)
+    sc = ob.build_scene(raw, bp)
+    cam = scenegen.look_at((0, -14, 3), (0, 0, 0), (0, 0, 1), 256, 192, 60.0)
+    r, img, st = _full_render(v, raw, sc, cam, vq_codes=128)
+    assert st["staged_projection"] == 1
+    cb, codes = ob.quantize_sh(sc.levels, 128, 8)
+    gq, vid = oracle.full_scene(dataclasses.replace(sc, levels=ob.vq_levels(sc.levels, cb, codes)))
+    refq = oracle.render(gq, vid, cam)
+    N = len(vid)
+    rect = r.debug(v.DBG_SPLAT_RECT, np.int32).reshape(N, 4)
+    vis = refq["proj"]["vis"] != 0
+    np.testing.assert_array_equal(rect[vis], refq["proj"]["rect"][vis])
+    np.testing.assert_array_equal(r.debug(v.DBG_KEYS, np.uint64), refq["keys"])
+    np.testing.assert_allclose(r.debug(v.DBG_SPLAT_RGB, np.float32).reshape(N, 3)[vis], refq["proj"]["rgb"][vis],
+                               rtol=2e-5, atol=2e-6)
+    compare_image(img, refq)
+    g, _ = oracle.full_scene(sc)
+    ref32 = oracle.render(g, vid, cam)
+    mse = np.mean((np.clip(img, 0, 1) - np.clip(ref32["image"], 0, 1)) ** 2)
+    print("VQ pool PSNR against the FP64 fp32-scene render: %.2f dB" % (10 * np.log10(1.0 / max(mse, 1e-30))))

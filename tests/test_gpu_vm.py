@@ -24,21 +24,35 @@ def v():
 
 
 def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=True, tau0=1.0, check_images=(),
-                    fp16=False):
+                    fp16=False, vq_codes=0):
+    """vq_codes > 0: the pool holds VQ records (compressed pages) with an SH
+    codebook of that many codes; images are compared with the oracle run on
+    the attributes those records decode to."""
     scene = import_scene(v, raw, sc, fp16=fp16)
     W, H = cams[0].width, cams[0].height
+    fmt = int(fp16)
     rec = scene.info.record_bytes16 if fp16 else scene.info.record_bytes
+    if vq_codes:
+        import dataclasses
+        from oracle import build as ob
+        scene.quantize_sh(vq_codes, 6)
+        cb, codes = ob.quantize_sh(sc.levels, vq_codes, 6)
+        np.testing.assert_array_equal(scene.codebook(), cb)
+        fmt, rec = v.POOL_VQ, scene.info.record_bytes_vq
     budget = budget_pages * sc.params.page_size * rec
     cfg = v.RenderConfig(max_width=W, max_height=H, lod=lod, links=links, staging_bytes=budget, tau0=tau0,
-                         fp16_pool=fp16)
+                         fp16_pool=fmt)
     r = v.Renderer(scene, cfg, pool_slots=pool_slots)
     rp = rs.ResidencyParams(n_entries=pool_slots, page_size=sc.params.page_size, levels=len(sc.levels),
                             fanout=sc.params.lod_fanout, record_bytes=rec, budget_bytes=budget, lod=lod, tau0=tau0)
     pt = rs.PageTable(rp)
     smax = sc.params.lod_fanout ** (len(sc.levels) - 1)
     host_pages = [scene.pages(l, fp16=fp16) for l in range(len(sc.levels))]
-    # images of an fp16 pool are compared with the oracle on the attributes it stores
+    # images of an fp16 or VQ pool are compared with the oracle on the attributes it stores
     osc = round16_scene(sc) if fp16 else sc
+    if vq_codes:
+        host_pages = [scene.export(v.SCENE_PAGES_VQ, l).reshape(sc.n_pages, -1) for l in range(len(sc.levels))]
+        osc = dataclasses.replace(sc, levels=ob.vq_levels(sc.levels, cb, codes))
     for f, cam in enumerate(cams):
         r.render_feedback([cam])
         r.update_residency()
@@ -226,3 +240,13 @@ def test_feedback_on_own_stream_matches_one_stream(v, fp16, mode):
               "acc_requested", "pairs", "drawn_gaussians"):
         assert sa[k] == sb[k], k
     assert sb["status"] == 0
+
+
+def test_city_lod_trajectory_vq(v):
+    """Compressed pages: VQ records (40 bytes) in the pool with a 64-code SH
+    codebook, three LOD levels of pages of 512 with fanout 8 (level blocks of
+    8: the gathering projection), page table and images against the oracle."""
+    raw, sc = city_scene()
+    cams = [city_cam(160.0, k) for k in range(10)]
+    _run_trajectory(v, raw, sc, cams, pool_slots=8, budget_pages=5, lod=True, tau0=2.0, check_images=(0, 5, 9),
+                    vq_codes=64)
