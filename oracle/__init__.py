@@ -219,16 +219,24 @@ def float_bits(f):
 
 
 # --------------------------------------------------------------------------- frame
-def gather_draw(scene, draw):
-    """Gaussians of the draw list [(p, l, e, s)] in draw order, with virtual ids p*page_size + slot."""
+def gather_draw(scene, draw, weights=None):
+    """Gaussians of the draw list [(p, l, e, s)] in draw order, with virtual
+    ids 2 p page_size + k page_size + slot (k: the item's rank among the
+    page's items, 1 for the old level of a cross-fade); weights (optional,
+    float32 per item) scale the opacities in float32."""
     ps = scene.params.page_size
     parts = {k: [] for k in ("pos", "scale", "rot", "opacity", "sh")}
     vids = []
-    for (p, l, e, s) in draw:
+    prev = None
+    for i, (p, l, e, s) in enumerate(draw):
         lv = scene.levels[l]
         for k in parts:
             parts[k].append(lv[k][p])
-        vids.append(p * ps + np.arange(lv["opacity"].shape[1], dtype=np.int64))
+        if weights is not None and weights[i] != np.float32(1):
+            parts["opacity"][-1] = (lv["opacity"][p] * np.float32(weights[i])).astype(np.float32)
+        k = 1 if prev == p else 0
+        prev = p
+        vids.append((2 * p + k) * ps + np.arange(lv["opacity"].shape[1], dtype=np.int64))
     if not draw:
         K = scene.levels[0]["sh"].shape[2]
         return dict(pos=np.zeros((0, 3), np.float32), scale=np.zeros((0, 3), np.float32),
@@ -253,7 +261,7 @@ def frame(scene, pt, cam, ds=4, links=True, render_image=True):
     up = residency.update(pt, pages, enc, di, lv)
     out = dict(buf=buf, req=req, direct=direct, pages=pages, enc=enc, levels=lv, update=up, tau=pt.tau)
     if render_image:
-        g, vid = gather_draw(scene, up["draw"])
+        g, vid = gather_draw(scene, up["draw"], up["draw_w"])
         out["render"] = render(g, vid, cam)
     residency.control(pt, up["usage"], up["draw"])
     return out

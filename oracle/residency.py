@@ -32,6 +32,18 @@ Readings where the paper is silent, written out as a sequential definition
           missing.  A fresh entry forgets everything it held.
   draw    stage-one matches plus placements, ascending virtual page.
   usage   drawn Gaussian capacity / (entries * page size).
+  fade    (LOD cross-fade, fade_frames F > 0; the blending between levels
+          that Sec. 4.1 and 4.3 leave to a renderer with 3DGS alpha blending,
+          with both levels resident during the transition): per requested
+          page, state (cur = level drawn last frame, from, age); a running
+          fade ages by one and ends at age F or when the page returns to
+          `from`; a page drawn last frame at cur != its requested level
+          starts a fade from cur (age 0).  A fading page also requests
+          `from`: stage one keeps that copy required if it is resident (it
+          is never copied); it is drawn after the page's own item with
+          opacity weight 1 - w and the new level with w = (age+1)/(F+1), in
+          float32 (one item alone: weight 1).  Pages not requested forget
+          their state.
   control usage > hi: tau += step; usage < lo and a level > 0 drawn:
           tau = max(0, tau - step); before moving, step *= 1.01 when the last
           move (within 10 frames) had the same direction, *= 0.99 when it
@@ -59,6 +71,7 @@ class ResidencyParams:
     usage_hi: float = 0.8
     tau0: float = 1.0
     step0: float = 0.1
+    fade_frames: int = 0
 
     def m(self, l):
         return self.page_size // (self.fanout ** l)
@@ -79,6 +92,7 @@ class PageTable:
         self.last_dir = 0
         self.last_move = -1000
         self.frame = 0
+        self.fade = {}          # page -> [cur, from, age] (cross-fade state)
 
 
 def float_from_bits(u):
@@ -108,9 +122,28 @@ def update(pt: PageTable, pages, enc, direct, levels):
     P = rp.n_entries
     frame = pt.frame
     req_level = {int(p): int(l) for p, l in zip(pages, levels)}
+    # ---- cross-fade state
+    F = rp.fade_frames
+    fade_level = {}
+    if F > 0:
+        state = {}
+        for p in sorted(req_level):
+            l = req_level[p]
+            cur, frm, age = pt.fade.get(p, (-1, -1, 0))
+            if frm >= 0:
+                age += 1
+                if age >= F or frm == l:
+                    frm = -1
+            if cur >= 0 and l != cur:
+                frm, age = cur, 0
+            state[p] = [cur, frm, age]
+            if frm >= 0:
+                fade_level[p] = frm
+        pt.fade = state
     # ---- stage 1
     required = np.zeros_like(pt.slot, dtype=bool)
     matched = set()
+    fade_slot = {}
     for e in range(P):
         l = pt.lod[e]
         if l < 0:
@@ -120,6 +153,9 @@ def update(pt: PageTable, pages, enc, direct, levels):
             if p >= 0 and req_level.get(p, -1) == l:
                 required[e, s] = True
                 matched.add(p)
+            elif p >= 0 and fade_level.get(p, -1) == l:
+                required[e, s] = True
+                fade_slot[p] = (e, s)
     any_req = required.any(1)
     pt.last_used[any_req] = frame
     # ---- stage 2
@@ -165,16 +201,32 @@ def update(pt: PageTable, pages, enc, direct, levels):
                 pt.slot[e, s] = r[0]
                 placed.append((r[0], l, e, s))
     placed.sort(key=lambda t: rank[t[0]])
-    draw = [(int(pt.slot[e, s]), int(pt.lod[e]), e, s) for e in range(P) for s in range(rp.fanout ** max(pt.lod[e], 0))
-            if pt.lod[e] >= 0 and required[e, s]]
-    draw += placed
-    draw.sort(key=lambda t: t[0])
+    own = [(int(pt.slot[e, s]), int(pt.lod[e]), e, s) for e in range(P) for s in range(rp.fanout ** max(pt.lod[e], 0))
+           if pt.lod[e] >= 0 and required[e, s] and req_level.get(int(pt.slot[e, s]), -1) == pt.lod[e]]
+    own += placed
+    items = [(t, 0) for t in own] + [((p, fade_level[p], e, s), 1) for p, (e, s) in fade_slot.items()]
+    items.sort(key=lambda it: (it[0][0], it[1]))
+    draw = [t for t, _ in items]
+    n_items = {}
+    for t in draw:
+        n_items[t[0]] = n_items.get(t[0], 0) + 1
+    draw_w = []
+    for t, k in items:
+        w = F32(1)
+        if n_items[t[0]] == 2:
+            wn = F32(pt.fade[t[0]][2] + 1) / F32(F + 1)
+            w = wn if k == 0 else F32(F32(1) - wn)
+        draw_w.append(w)
+    if F > 0:
+        drawn_level = {t[0]: t[1] for t, k in items if k == 0}
+        for p in pt.fade:
+            pt.fade[p][0] = drawn_level.get(p, -1)
     used = sum(rp.m(t[1]) for t in draw)
     usage = F32(used) / F32(P * rp.page_size) if P > 0 else F32(0)
     streamed_bytes = sum(rp.page_bytes(t[1]) for t in placed)
-    return dict(copies=placed, draw=draw, missing=sorted(missing), usage=usage, resident=len(matched),
+    return dict(copies=placed, draw=draw, draw_w=draw_w, missing=sorted(missing), usage=usage, resident=len(matched),
                 streamed_pages=len(placed), streamed_bytes=streamed_bytes, required=len(pages),
-                direct=int(np.sum(np.asarray(direct) != 0)))
+                direct=int(np.sum(np.asarray(direct) != 0)), fading=sum(1 for v in n_items.values() if v == 2))
 
 
 def control(pt: PageTable, usage, draw):
