@@ -18,6 +18,8 @@ Synthetic, seeded inputs (scenegen); no dataset.
   python bench.py --table pagesize|buffer (the page-size / buffer-size tables of Sec. 5)
   python bench.py --table lod            (k-means LOD against moment matching: time and PSNR)
   python bench.py --table disk           (the scene from a memory-mapped file through a staging buffer)
+  python bench.py --table quality        (page links x LOD ablation on a 500-page buffer: PSNR / SSIM, Sec. 5.2)
+  python bench.py --table vq             (compressed pages: SH codebook against the fp16 pool)
 """
 from __future__ import annotations
 
@@ -1001,6 +1003,188 @@ def lod_table(args, every=25):
                       "timing": "CUDA events per stage, every call on one stream", "rows": rows}))
 
 
+def ssim(x, y):
+    """Mean SSIM of two [3, H, W] images in [0, 1] (Wang et al. 2004: Gaussian
+    window sigma 1.5 truncated at 11 px, C1 = 0.01^2, C2 = 0.03^2), averaged
+    over the channels."""
+    from scipy.ndimage import gaussian_filter
+    f = lambda a: gaussian_filter(a, sigma=1.5, truncate=3.5, mode="reflect")
+    out = []
+    for c in range(x.shape[0]):
+        a, b = x[c], y[c]
+        ma, mb = f(a), f(b)
+        va, vb, cab = f(a * a) - ma * ma, f(b * b) - mb * mb, f(a * b) - ma * mb
+        c1, c2 = 0.01 ** 2, 0.03 ** 2
+        out.append(float((((2 * ma * mb + c1) * (2 * cab + c2)) / ((ma * ma + mb * mb + c1) * (va + vb + c2))).mean()))
+    return float(np.mean(out))
+
+
+def quality_table(args, every=25, pools=(500, 250)):
+    """The ablation of Sec. 5.2 (its PSNR/SSIM table): images rendered with
+    virtual memory, with and without page links and with and without LOD, on
+    buffers of 500 pages (the paper's; here none of the arms fills it) and of
+    250 (which the links fill, so LOD has to coarsen), against the same view
+    rendered without virtual
+    memory (every level-0 page resident), for the paper's mesh proxy (Sec.
+    3.1-3.3, paging "mesh") and for the voxel-face proxy.  A 12.5M-Gaussian
+    city patch (1 km, 1250 boxes, SH3, pages of 4096, 3 LOD levels), fp16
+    pools, the street-level walk; every `every`-th frame is compared."""
+    import torch
+    import paper_2506_19415_b300 as v
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    base = workload("citypatch")
+    frames, warm = min(args.steps, 300), args.warmup
+    cams = base["path"](base["frames"])
+    width, height = cams[0].width, cams[0].height
+    st = torch.cuda.current_stream()
+    raw = base["gen"]()
+    out_rows, proxies = [], []
+    for proxy, extra in (("mesh (Sec. 3.1-3.3)", dict(paging="mesh", mesh_kappa=2.0, mesh_op_min=0.1, mesh_closing=1,
+                                                      mesh_qem_ratio=0.25)),
+                         ("voxel faces", dict(paging="octree"))):
+        t0 = time.time()
+        scene = v.vm3dgs_build_pages(raw, v.BuildConfig(**dict(base["build"], **extra), seed=77))
+        t_build = time.time() - t0
+        proxies.append(dict(proxy=proxy, build_s=round(t_build, 1), pages=int(scene.info.n_pages),
+                            proxy_triangles=int(scene.info.n_tris), links=int(scene.info.n_links)))
+        # (no copy budget: every page is resident from the first sampled frame on)
+        ref = v.Renderer(scene, v.RenderConfig(staging_bytes=1 << 40, feedback_ds=4, links=False, lod=False,
+                                               fp16_pool=True, max_width=width, max_height=height, max_pairs=64 << 20),
+                         pool_slots=scene.info.n_pages)
+        arms = []
+        # the paper's four rows on each pool, and the first two again with a
+        # full-resolution visibility buffer (what the lower feedback
+        # resolution costs)
+        confs = [(pool, links, lod, 4) for pool in pools for links in (True, False) for lod in (True, False)]
+        confs += [(pools[0], True, True, 1), (pools[0], True, False, 1)]
+        for pool_pages, links, lod, ds in confs:
+            cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=ds, links=links, lod=lod,
+                                 fp16_pool=True, max_width=width, max_height=height, tau0=1.0, step0=0.1,
+                                 max_pairs=32 << 20)
+            arms.append(dict(pool=pool_pages, links=links, lod=lod, ds=ds, r=v.Renderer(scene, cfg, pool_slots=pool_pages),
+                             mse=[], ssim=[], usage=[], required=[], missing=[], tau=[]))
+        img_ref = torch.empty((3, height, width), dtype=torch.float32, device="cuda")
+        img = torch.empty_like(img_ref)
+        for i in range(warm + frames):
+            c = [cams[i % len(cams)]]
+            sample = i >= warm and (i - warm) % every == 0
+            if sample:
+                ref.request_all(st)
+                ref.update_residency(st)
+                ref.render(c, [img_ref], st)
+                y = img_ref.clamp(0.0, 1.0).double()
+                yh = y.cpu().numpy()
+            for a in arms:
+                r = a["r"]
+                r.render_feedback(c, st)
+                r.update_residency(st)
+                r.render(c, [img], st)
+                if not sample:
+                    continue
+                s = r.stats(st)
+                if s["status"] != 0:
+                    raise RuntimeError("renderer status %d" % s["status"])
+                x = img.clamp(0.0, 1.0).double()
+                a["mse"].append(float(((x - y) ** 2).mean()))
+                a["ssim"].append(ssim(x.cpu().numpy(), yh))
+                a["usage"].append(s["usage"])
+                a["required"].append(s["requested"])
+                a["missing"].append(s["missing"])
+                a["tau"].append(s["tau"])
+        psnr = lambda e: round(10.0 * math.log10(1.0 / e), 3) if e > 0 else None  # None: identical images
+        for a in arms:
+            mse = np.asarray(a["mse"])
+            out_rows.append(dict(proxy=proxy, pool_pages=a["pool"], page_links=a["links"], lod=a["lod"],
+                                 feedback_ds=a["ds"], mse_mean=float(mse.mean()),
+                                 psnr_db_pooled=psnr(float(mse.mean())),
+                                 psnr_db_worst_frame=psnr(float(mse.max())), ssim_mean=round(float(np.mean(a["ssim"])), 4),
+                                 required_pages_mean=round(float(np.mean(a["required"])), 1),
+                                 usage_mean=round(float(np.mean(a["usage"])), 3),
+                                 missing_pages_mean=round(float(np.mean(a["missing"])), 2),
+                                 tau_last=round(float(a["tau"][-1]), 3)))
+        del arms, ref, scene
+        torch.cuda.empty_cache()
+    print(json.dumps({"table": "quality", "workload": base["name"] + "; fp16 pools of %s pages" % (pools,),
+                      "frames": frames, "warmup": warm, "compared": "every %dth frame" % every,
+                      "reference": "the same view rendered without virtual memory: every level-0 page resident, "
+                                   "no feedback", "proxies": proxies, "rows": out_rows}))
+
+
+def vq_table(args, n_codes=1024, every=25):
+    """Compressed pages (the SH codebook of vm3dgs_scene_quantize_sh) on the
+    50M-Gaussian city: the fp16 pool against VQ pools of the same 2 GiB and of
+    the fp16 pool's slot count (equal pages, a third of the bytes).  Frames/s
+    of the overlapped frame loop (as the headline arm, without the
+    prefetcher), per-stage kernel times of a one-stream pass, bytes streamed,
+    and the PSNR of the VQ images against the fp16 pool's on every `every`-th
+    frame of a one-stream lockstep pass from a cold start."""
+    import torch
+    import paper_2506_19415_b300 as v
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    W = workload(args.config)
+    scene, t_gen, t_build = build_scene(W)
+    t0 = time.time()
+    scene.quantize_sh(n_codes, 10, 65536)
+    t_vq = time.time() - t0
+    cams = W["path"](W["frames"])
+    width, height = cams[0].width, cams[0].height
+    copy_stream = torch.cuda.Stream()
+    slots16 = W["pool_bytes"] // v.vm3dgs_pool_slot_bytes(scene, v.POOL_FP16)
+    arms = [("fp16 pool", v.POOL_FP16, None), ("VQ pool, same bytes", v.POOL_VQ, None),
+            ("VQ pool, the fp16 slot count", v.POOL_VQ, slots16)]
+
+    def renderer(fmt, slots):
+        cfg = v.RenderConfig(staging_bytes=40 * 2048 * 236, feedback_ds=4, links=True, lod=W["lod"], fp16_pool=fmt,
+                             max_width=width, max_height=height, tau0=1.0, step0=0.1)
+        if slots is not None:
+            return v.Renderer(scene, cfg, pool_slots=slots)
+        return v.Renderer(scene, cfg, pool_bytes=W["pool_bytes"])
+
+    rows = []
+    steps = min(args.steps, 300)
+    for label, fmt, slots in arms:
+        r = renderer(fmt, slots)
+        run = run_arm(v, r, cams, args.warmup, steps, copy_stream, preroll=PREROLL)
+        ser = run_arm(v, r, cams, args.warmup, min(steps, 100), copy_stream, timing=True, serial=True,
+                      preroll=PREROLL)
+        n = max(ser["stats"]["acc_frames"], 1)
+        st = run["stats"]
+        fr = max(st["acc_frames"], 1)
+        rows.append(dict(arm=label, pool_slots=int(r.n_slots),
+                         record_bytes=int(scene.info.record_bytes_vq if fmt == v.POOL_VQ else scene.info.record_bytes16),
+                         frames_per_s=round(1000.0 * steps / run["ms"], 2), ms_per_frame=round(run["ms"] / steps, 4),
+                         stage_ms_one_stream={k: round(x / n, 4) for k, x in zip(v.STAGES, ser["stage"][0])},
+                         streamed_bytes_per_frame=st["acc_streamed_bytes"] / fr,
+                         missing_per_frame=st["acc_missing"] / fr, drawn_gaussians_per_frame=st["acc_drawn_gaussians"] / fr,
+                         tau=st["tau"], usage=st["usage"]))
+        del r
+        torch.cuda.empty_cache()
+    # image quality: the VQ pool (same bytes) against the fp16 pool, lockstep
+    rs = [renderer(v.POOL_FP16, None), renderer(v.POOL_VQ, slots16)]
+    stq = torch.cuda.current_stream()
+    imgs = [torch.empty((3, height, width), dtype=torch.float32, device="cuda") for _ in rs]
+    psnr = []
+    for f in range(0, 301):
+        for k, r in enumerate(rs):
+            r.render_feedback([cams[f]], stq)
+            r.update_residency(stq)
+            r.render([cams[f]], [imgs[k]], stq)
+        if f and f % every == 0:
+            a, b = (im.clamp(0.0, 1.0).double() for im in imgs)
+            mse = float(((a - b) ** 2).mean())
+            psnr.append(round(10.0 * math.log10(1.0 / max(mse, 1e-30)), 2))
+    same = rs[0].stats(stq)["drawn_gaussians"] == rs[1].stats(stq)["drawn_gaussians"]
+    print(json.dumps({"table": "vq", "workload": W["name"], "codes": n_codes, "code_dim": int(scene.codebook().shape[1]),
+                      "build_s": {"generate": round(t_gen, 1), "pages": round(t_build, 1), "quantize": round(t_vq, 1)},
+                      "host_bytes": int(scene.info.host_bytes), "frames": steps, "warmup": args.warmup,
+                      "rows": rows,
+                      "psnr_vq_vs_fp16_db": psnr, "psnr_frames": list(range(every, 301, every)),
+                      "psnr_same_draw_list": bool(same),
+                      "psnr_note": "VQ pool with the fp16 slot count against the fp16 pool, one stream, cold start; "
+                                   "images clamped to [0, 1]; the SH of this synthetic scene are independent "
+                                   "normal draws (no structure for a codebook to exploit)"}))
+
+
 def disk_table(args):
     """Sec. 3.5 / Sec. 4.1 "Transfer": the scene saved to a file and opened
     as a read-only mapping, its pages gathered by host threads into a
@@ -1068,7 +1252,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-prefetch", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--table", choices=("pagesize", "buffer", "lod", "disk"), default=None,
+    ap.add_argument("--table", choices=("pagesize", "buffer", "lod", "disk", "quality", "vq"), default=None,
                     help="print the page-size or buffer-size table of Sec. 5, the LOD comparison or the "
                          "file-backed scene measurement instead of the benchmark line")
     ap.add_argument("--scene-dir", default=None, help="directory for the scene file of --table disk")
@@ -1081,6 +1265,10 @@ def main():
         lod_table(args)
     elif args.table == "disk":
         disk_table(args)
+    elif args.table == "quality":
+        quality_table(args)
+    elif args.table == "vq":
+        vq_table(args)
     elif args.table is not None:
         paging_tables(args)
     else:

@@ -149,6 +149,15 @@ typedef struct {
                               look-back; the default), 1 = all passes in one cooperative launch (a chunk per CTA,
                               bounded grid barriers; where the device supports cooperative launches, else as 0).
                               Same sorted pairs either way. */
+  int32_t lod_fade_frames; /* LOD cross-fade (Sec. 4.1 and 4.3 leave blending between levels, with both levels
+                              resident during a transition, to a renderer with 3DGS alpha blending): 0 = off; F in
+                              1..255: a page drawn last frame at a level other than the one it now needs keeps its
+                              old copy required (if resident; it is never copied for this) for F frames and is
+                              drawn at both levels, the old one after the new with opacity weight 1 - w, the new
+                              one with w = (age + 1) / (F + 1) (float32; one of them alone: weight 1); the fade
+                              ends at age F or when the page needs its old level again; a page not requested
+                              forgets its fade.  Draw lists may then hold two items of a page (the draw list
+                              capacity is 2 n_pages). */
 } vm3dgs_params;
 
 typedef struct {
@@ -176,6 +185,7 @@ typedef struct {
    * widths in bits (index 0 when the index travels in a value array, i.e.
    * key_packed = 0); the sort orders the key's tile and depth fields */
   int32_t key_tile_bits, key_depth_bits, key_index_bits, key_packed;
+  int32_t fading;          /* pages drawn at two levels this frame (LOD cross-fade) */
 } vm3dgs_stats;
 
 typedef struct {
@@ -383,7 +393,8 @@ enum {
                                 meets its 3-sigma ellipse, by the row rule of Sec. 4.2's tiled rendering reading) as
                                 row-major bits of a rectangle of at most 64 tiles; 0 for larger rectangles and culled
                                 splats */
-  VM3DGS_DBG_SPLAT_TOUCHED = 22 /* uint32 [N] number of the splat's tiles (0 if culled) */
+  VM3DGS_DBG_SPLAT_TOUCHED = 22, /* uint32 [N] number of the splat's tiles (0 if culled) */
+  VM3DGS_DBG_DRAW_W = 23        /* float [n_draw] opacity weight of each draw item (LOD cross-fade; else 1) */
 };
 int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *host_dst, int64_t bytes, int64_t *needed, void *stream);
 

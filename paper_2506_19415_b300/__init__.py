@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
     _fields_ = [("staging_bytes", c_i64), ("feedback_ds", c_i32), ("links", c_i32), ("lod", c_i32),
                 ("fp16_pool", c_i32), ("usage_lo", c_f), ("usage_hi", c_f), ("tau0", c_f), ("step0", c_f),
                 ("max_width", c_i32), ("max_height", c_i32), ("max_views", c_i32), ("max_pairs", c_i64),
-                ("bg", c_f * 3), ("separate_values", c_i32), ("sort_mode", c_i32)]
+                ("bg", c_f * 3), ("separate_values", c_i32), ("sort_mode", c_i32), ("lod_fade_frames", c_i32)]
 
 
 class Stats(ctypes.Structure):
@@ -68,7 +68,7 @@ class Stats(ctypes.Structure):
                 ("acc_streamed_bytes", c_i64), ("acc_streamed_pages", c_i64), ("acc_missing", c_i64),
                 ("acc_requested", c_i64), ("acc_prefetched_pages", c_i64), ("acc_prefetched_bytes", c_i64),
                 ("acc_prefetch_hits", c_i64), ("staged_projection", c_i32), ("key_tile_bits", c_i32),
-                ("key_depth_bits", c_i32), ("key_index_bits", c_i32), ("key_packed", c_i32)]
+                ("key_depth_bits", c_i32), ("key_index_bits", c_i32), ("key_packed", c_i32), ("fading", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -151,7 +151,7 @@ SCENE_PAGE_COUNT, SCENE_PAGE_SRC, SCENE_PAGES, SCENE_PAGES16, SCENE_ERR, SCENE_V
 POOL_FP32, POOL_FP16, POOL_VQ = 0, 1, 2
 (DBG_FEEDBACK, DBG_REQ, DBG_DIRECT, DBG_REQUESTS, DBG_PT_LOD, DBG_PT_LAST, DBG_PT_SLOT, DBG_COPIES, DBG_DRAW,
  DBG_MISSING, DBG_SPLAT_RECT, DBG_SPLAT_DEPTH, DBG_SPLAT_RADIUS, DBG_KEYS, DBG_VALUES, DBG_RANGES, DBG_SPLAT_XY,
- DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK, DBG_SPLAT_TOUCHED) = range(23)
+ DBG_SPLAT_CONIC, DBG_SPLAT_RGB, DBG_POOL, DBG_RASTER, DBG_SPLAT_TMASK, DBG_SPLAT_TOUCHED, DBG_DRAW_W) = range(24)
 
 
 STAGES = ("feedback", "residency", "stream", "project", "scan_emit", "sort", "ranges", "blend", "prefetch", "sort_prep")
@@ -375,6 +375,7 @@ class RenderConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     separate_values: bool = False   # True: always sort (key, splat) pairs instead of packed keys
     sort_mode: int = 0              # 0: a onesweep launch per pass; 1: one cooperative launch for all passes
+    lod_fade_frames: int = 0        # LOD cross-fade length in frames (0: off)
 
     def struct(self) -> Params:
         p = Params()
@@ -384,6 +385,7 @@ class RenderConfig:
         p.bg[:] = [float(v) for v in self.bg]
         p.separate_values = int(self.separate_values)
         p.sort_mode = int(self.sort_mode)
+        p.lod_fade_frames = int(self.lod_fade_frames)
         return p
 
 

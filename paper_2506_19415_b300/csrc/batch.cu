@@ -70,6 +70,7 @@ int enqueue_batch(vm3dgs_renderer *r, const ViewTable &t, cudaStream_t st, bool 
   pa.rctl = ctl;
   pa.draw = r->at<int4>(r->lay.draw);
   pa.draw_off = r->at<int64_t>(r->lay.draw_off);
+  pa.draw_w = r->prm.lod_fade_frames > 0 ? r->at<float>(r->lay.draw_w) : nullptr;
   pa.pool = r->pool;
   pa.slot_bytes = r->slot_bytes;
   pa.page_size = s->page_size;

@@ -122,14 +122,16 @@ struct SharedSrc {
 };
 
 // Projects one Gaussian for one camera and writes splat record out.
+// wt: the draw item's opacity weight (1, or a cross-fade weight in (0, 1))
 template <int K, int FMT, class Src>
-__device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const Src &src, int64_t out) {
+__device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camera &cam, const Src &src, int64_t out,
+                                            float wt) {
   const float *V = cam.view;
   const int gx = (cam.width + cam.tile_w - 1) / cam.tile_w;
   const int gy = (cam.height + cam.tile_h - 1) / cam.tile_h;
   const float TW = (float)cam.tile_w, TH = (float)cam.tile_h;
   float x = src.pos(0), y = src.pos(1), z = src.pos(2);
-  float o = src.opac();
+  float o = src.opac() * wt;
   // a culled splat: no tiles, zero rectangle, depth and radius
   auto culled = [&]() {
     sp.touched[out] = 0;
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, vm3dgs_came
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), i);
+    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), i, a.draw_w ? a.draw_w[j] : 1.0f);
   }
 }
 
@@ -326,7 +328,8 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
     for (int l = 0; l < it.y; ++l) m /= a.fanout;
     const int g = (int)(i - a.draw_off[j]);
     const uint8_t *blk = a.pool + (int64_t)it.z * a.slot_bytes + (int64_t)it.w * m * R::kRec;
-    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), (int64_t)v * N + i);
+    project_one<K, FMT>(a.sp, cam, GlobalSrc<K, FMT>(blk, m, g, a.codebook), (int64_t)v * N + i,
+                        a.draw_w ? a.draw_w[j] : 1.0f);
   }
 }
 
@@ -358,6 +361,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
   constexpr int kChunk = CH, kChunksPerCta = S::PER;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
+  __shared__ float s_w[2][kChunksPerCta];  // opacity weight of each chunk's draw item, per stage
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
   if (blockIdx.x == 0 && tid == 0) a.rctl->r_drawn = a.ctl->draw_gauss;
@@ -402,6 +406,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
       for (int j = 0; j < kChunksPerCta; ++j) {
         if (e[j] < 0) continue;
         const int4 d = a.draw[e[j]];
+        s_w[stg][j] = a.draw_w ? a.draw_w[e[j]] : 1.0f;
         int sub = 1;
         for (int l = 0; l < d.y; ++l) sub *= a.fanout;
         const int u = d.z * sub + d.w;  // level block of the whole pool
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
       const uint8_t *buf = smem + stg * S::STAGE + ch * S::CHUNK;
       const SharedSrc<K, FMT, CH> src(reinterpret_cast<const float *>(buf),
                                       reinterpret_cast<const __half *>(buf + S::ABYTES), g, a.codebook);
-      project_one<K, FMT>(a.sp, cam, src, c * kChunk + g);
+      project_one<K, FMT>(a.sp, cam, src, c * kChunk + g, s_w[stg][ch]);
     }
     __syncthreads();  // the stage is refilled by the next-but-one item
   }

@@ -21,6 +21,14 @@
 //              sort of all free entries)
 //   lists      copy list (priority order) with 64 KiB copy segments, missing
 //              list and draw list (ascending page) with Gaussian offsets
+//   fade       (LOD cross-fade, fade_frames F > 0) per requested page: a
+//              running fade ages by one and ends at age F or when the page
+//              needs its old level again; a page drawn last frame at another
+//              level starts one from that level; stage 1 keeps the old level's
+//              copy required while the fade runs (it is never copied), and
+//              the draw list holds it after the page's own item, with opacity
+//              weights 1 - w and w = (age + 1) / (F + 1); pages not requested
+//              forget their fade
 //   control    usage = drawn Gaussian capacity / pool capacity; above the
 //              band tau grows by step, below it (with a level > 0 drawn) tau
 //              shrinks (not below 0); step *1.01 after a same-direction move
@@ -76,7 +84,7 @@ __device__ void bscan_n(const int64_t *v, int64_t *pre, int64_t *total, MScan<N>
 __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   extern __shared__ uint64_t s_keys[];
   __shared__ ScanSmem sm;
-  __shared__ MScan<4> sm4;
+  __shared__ MScan<5> sm4;
   __shared__ int m_l[kMaxLevels], S_l[kMaxLevels];
   __shared__ int n_lvl[kMaxLevels], open_cnt[kMaxLevels], open_base[kMaxLevels], fresh_start[kMaxLevels + 1];
   __shared__ int s_nfree, s_hits;
@@ -107,7 +115,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       const int p = p0 + k;
       r[k] = p < NP ? a.req[p] : 0u;
       dflag[k] = (p < NP && r[k] != 0u) ? (int)a.direct[p] : 0;
-      if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; }
+      if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; a.fade_lev[p] = -1; a.fade_info[p] = -1; }
       v2[0] += r[k] != 0u;
       v2[1] += dflag[k];
     }
@@ -136,6 +144,32 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     a.reqlev[q.x] = lev;
   }
   __syncthreads();
+  // ---- 2b. cross-fade state (state word: cur + 1 | (from + 1) << 8 | age << 16)
+  const int F = a.fade_frames;
+  if (F > 0) {
+    for (int p = tid; p < NP; p += RT) {
+      const int l = a.reqlev[p];
+      if (l < 0) {
+        a.fade_state[p] = 0;
+        continue;
+      }
+      const int32_t w = a.fade_state[p];
+      const int cur = (w & 0xFF) - 1;
+      int frm = ((w >> 8) & 0xFF) - 1, age = (w >> 16) & 0xFFFF;
+      if (frm >= 0) {
+        ++age;
+        if (age >= F || frm == l) frm = -1;
+      }
+      if (cur >= 0 && l != cur) {
+        frm = cur;
+        age = 0;
+      }
+      if (frm < 0) age = 0;
+      a.fade_state[p] = (cur + 1) | ((frm + 1) << 8) | (age << 16);
+      a.fade_lev[p] = frm;
+    }
+    __syncthreads();
+  }
   // ---- 3. stage 1
   for (int e = tid; e < P; e += RT) {
     const int l = a.pt_lod[e];
@@ -145,12 +179,18 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
         const int64_t k = (int64_t)e * Smax + s;
         const int p = a.pt_slot[k];
         const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
-        a.required[k] = (uint8_t)r;
+        // the old level of a running cross-fade, when resident, stays required
+        const int rf = (!r && p >= 0 && a.fade_lev[p] == l) ? 1 : 0;
+        a.required[k] = (uint8_t)(r | rf);
         if (r) {
           a.matched[p] = 1;
           a.draw_info[p] = (int)k;
           any = 1;
           if (a.pf_flag[k]) { atomicAdd(&s_hits, 1); a.pf_flag[k] = 0; }
+        }
+        if (rf) {
+          a.fade_info[p] = (int)k;
+          any = 1;
         }
       }
     }
@@ -372,49 +412,76 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   // non-admitted requests are missing too
   for (int i = (int)nadm + tid; i < nu; i += RT) a.matched[(int)(a.ukeys[i] & 0x7FFFFFFFull)] = 2;
   __syncthreads();
-  // ---- 12. missing list and draw list, ascending page; draw offsets
-  int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0;
+  // ---- 12. missing list and draw list, ascending page (a fading page: its
+  // own item, then its old level's); draw offsets and weights
+  int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0, nfade = 0;
   for (int c = 0; c < NP; c += RT * kPer) {
     const int p0 = c + tid * kPer;
-    int fm[kPer], fd[kPer];
+    int fm[kPer], fd[kPer], ff[kPer];
     int64_t g[kPer];
-    int64_t v4[4] = {0, 0, 0, 0};
+    int64_t v5[5] = {0, 0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int p = p0 + k;
-      fm[k] = 0; fd[k] = 0; g[k] = 0;
+      fm[k] = 0; fd[k] = 0; ff[k] = 0; g[k] = 0;
       if (p < NP) {
         fm[k] = a.matched[p] == 2;
         fd[k] = a.draw_info[p] >= 0 && !fm[k];
+        ff[k] = a.fade_info[p] >= 0;
         if (fd[k]) {
           const int lv = a.reqlev[p];
-          g[k] = m_l[lv];
-          v4[3] += lv > 0;
+          g[k] += m_l[lv];
+          v5[3] += lv > 0;
+        }
+        if (ff[k]) {
+          const int lv = a.fade_lev[p];
+          g[k] += m_l[lv];
+          v5[3] += lv > 0;
         }
       }
-      v4[0] += fm[k];
-      v4[1] += fd[k];
-      v4[2] += g[k];
+      v5[0] += fm[k];
+      v5[1] += fd[k] + ff[k];
+      v5[2] += g[k];
+      v5[4] += fd[k] & ff[k];
     }
-    int64_t pre4[4], tot4[4];
-    bscan_n<4>(v4, pre4, tot4, sm4);
-    int64_t om = nmiss + pre4[0], od = ndraw + pre4[1], og = gsum + pre4[2];
+    int64_t pre5[5], tot5[5];
+    bscan_n<5>(v5, pre5, tot5, sm4);
+    int64_t om = nmiss + pre5[0], od = ndraw + pre5[1], og = gsum + pre5[2];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int p = p0 + k;
       if (fm[k]) a.missing[om++] = p;
+      // weights: the new level (age + 1) / (F + 1), the old 1 - that
+      float wn = 1.0f, wo = 1.0f;
+      if (fd[k] && ff[k]) {
+        wn = (float)(((a.fade_state[p] >> 16) & 0xFFFF) + 1) / (float)(F + 1);
+        wo = 1.0f - wn;
+      }
       if (fd[k]) {
         const int slot = a.draw_info[p];
         a.draw[od] = make_int4(p, a.reqlev[p], slot / Smax, slot % Smax);
         a.draw_off[od] = og;
+        a.draw_w[od] = wn;
         ++od;
-        og += g[k];
+        og += m_l[a.reqlev[p]];
       }
+      if (ff[k]) {
+        const int slot = a.fade_info[p];
+        a.draw[od] = make_int4(p, a.fade_lev[p], slot / Smax, slot % Smax);
+        a.draw_off[od] = og;
+        a.draw_w[od] = wo;
+        ++od;
+        og += m_l[a.fade_lev[p]];
+      }
+      // the level drawn this frame, for the next frame's fade
+      if (F > 0 && p < NP && a.reqlev[p] >= 0)
+        a.fade_state[p] = (a.fade_state[p] & ~0xFF) | (fd[k] ? a.reqlev[p] + 1 : 0);
     }
-    nmiss += tot4[0];
-    ndraw += tot4[1];
-    gsum += tot4[2];
-    nlod += tot4[3];
+    nmiss += tot5[0];
+    ndraw += tot5[1];
+    gsum += tot5[2];
+    nlod += tot5[3];
+    nfade += tot5[4];
   }
   if (tid == 0) {
     a.draw_off[ndraw] = gsum;
@@ -429,6 +496,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     ctl->n_missing = (int)nmiss;
     ctl->n_resident = (int)(nreq - nu);
     ctl->n_free = s_nfree;
+    ctl->n_fading = (int)nfade;
     ctl->draw_gauss = gsum;
     ctl->acc_frames += 1;
     ctl->acc_draw_gauss += gsum;

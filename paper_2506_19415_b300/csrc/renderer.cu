@@ -143,8 +143,13 @@ Layout make_layout(const Dims &d) {
   L.admitted_pos = take(4 * NP);
   L.copies = take(16 * NP);
   L.copy_seg = take(8 * (NP + 1));
-  L.draw = take(16 * NP);
-  L.draw_off = take(8 * (NP + 1));
+  // (a page may be drawn at two levels during an LOD cross-fade)
+  L.draw = take(16 * 2 * NP);
+  L.draw_off = take(8 * (2 * NP + 1));
+  L.draw_w = take(4 * 2 * NP);
+  L.fade_state = take(4 * NP);
+  L.fade_lev = take(4 * NP);
+  L.fade_info = take(4 * NP);
   L.missing = take(4 * NP);
   L.pt_lod = take(4 * P);
   L.pt_last = take(4 * P);
@@ -246,6 +251,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   if (p->feedback_ds < 1 || p->max_width < 1 || p->max_height < 1 || p->staging_bytes < 0 ||
       !(p->usage_lo >= 0) || !(p->usage_hi >= p->usage_lo) || !(p->tau0 >= 0) || !(p->step0 > 0))
     return fail(VM3DGS_E_INVAL, "bad renderer parameters");
+  if (p->lod_fade_frames < 0 || p->lod_fade_frames > 255)
+    return fail(VM3DGS_E_INVAL, "lod_fade_frames must be 0..255");
   if ((p->max_height + p->feedback_ds - 1) / p->feedback_ds > 16000)
     return fail(VM3DGS_E_INVAL, "feedback buffer taller than 16000 rows (max_height / feedback_ds)");
   if (s->m(s->levels - 1) % 4 != 0) return fail(VM3DGS_E_INVAL, "smallest level page must hold a multiple of 4");
@@ -341,6 +348,7 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_last), 0xFF, 4 * P, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_slot), 0xFF, 4 * P * d.Smax, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_flag), 0, P * d.Smax, st), "memset", &rc);
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.fade_state), 0, 4 * d.NP, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_count), 0, 16, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.centroid), s->centroid.data(), 4 * s->centroid.size(),
                                      cudaMemcpyHostToDevice, st), "copy", &rc);
@@ -556,6 +564,11 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   a.copy_seg = r->at<int64_t>(r->lay.copy_seg);
   a.draw = r->at<int4>(r->lay.draw);
   a.draw_off = r->at<int64_t>(r->lay.draw_off);
+  a.draw_w = r->at<float>(r->lay.draw_w);
+  a.fade_state = r->at<int32_t>(r->lay.fade_state);
+  a.fade_lev = r->at<int32_t>(r->lay.fade_lev);
+  a.fade_info = r->at<int32_t>(r->lay.fade_info);
+  a.fade_frames = r->prm.lod_fade_frames;
   a.missing = r->at<int32_t>(r->lay.missing);
   a.pt_lod = r->at<int32_t>(r->lay.pt_lod);
   a.pt_last = r->at<int32_t>(r->lay.pt_last);
@@ -703,6 +716,7 @@ extern "C" int vm3dgs_render(vm3dgs_renderer *r, const vm3dgs_camera *cams, int3
   pa.rctl = ctl;
   pa.draw = r->at<int4>(r->lay.draw);
   pa.draw_off = r->at<int64_t>(r->lay.draw_off);
+  pa.draw_w = r->prm.lod_fade_frames > 0 ? r->at<float>(r->lay.draw_w) : nullptr;
   pa.pool = r->pool;
   pa.slot_bytes = r->slot_bytes;
   pa.page_size = s->page_size;
@@ -819,6 +833,7 @@ extern "C" int vm3dgs_get_stats(vm3dgs_renderer *r, vm3dgs_stats *out, void *str
   out->direct = c.n_direct;
   out->resident = c.n_resident;
   out->missing = c.n_missing;
+  out->fading = c.n_fading;
   out->streamed_pages = c.n_copies;
   out->streamed_bytes = c.streamed_bytes;
   out->drawn_pages = c.n_draw;
@@ -912,6 +927,7 @@ extern "C" int vm3dgs_debug_read(vm3dgs_renderer *r, int32_t what, void *dst, in
     case VM3DGS_DBG_SPLAT_RADIUS: src = r->at<void>(C.splat_radius); n = 4 * N; break;
     case VM3DGS_DBG_SPLAT_TMASK: src = r->at<void>(C.splat_tmask); n = 8 * N; break;
     case VM3DGS_DBG_SPLAT_TOUCHED: src = r->at<void>(C.splat_touched); n = 4 * N; break;
+    case VM3DGS_DBG_DRAW_W: src = r->at<void>(L.draw_w); n = 4 * (int64_t)c.n_draw; break;
     case VM3DGS_DBG_KEYS:
     case VM3DGS_DBG_VALUES: {
       // the sorted pairs as (tile << 32 | bits(depth), splat), whatever the

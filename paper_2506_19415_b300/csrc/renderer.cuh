@@ -16,7 +16,7 @@ namespace vm {
 // Device control block: per-frame counters, controller state, error word.
 struct Ctl {
   int32_t n_req, n_direct, n_unmatched, n_admitted, n_copies, n_draw, n_missing, n_resident;
-  int32_t n_free, pad0;
+  int32_t n_free, n_fading;  // n_fading: pages drawn at two levels (LOD cross-fade)
   int64_t draw_gauss;      // Gaussians of the draw list
   int64_t pairs;           // pairs of the last rendered view
   int64_t r_drawn;         // draw_gauss as the last projection read it: the scan and emission
@@ -61,7 +61,8 @@ struct Layout {
   int64_t ctl, fb, req, direct, reqlev, matched, draw_info, requests, ukeys, free_keys, open_list, open_off,
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
       clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
-      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, codebook, total;
+      pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, codebook, fade_state,
+      fade_lev, fade_info, draw_w, total;
   CtxLayout cx[kContexts];
 };
 
@@ -145,6 +146,12 @@ struct ResidencyArgs {
   int32_t *missing;
   int32_t *pt_lod, *pt_last, *pt_slot;
   uint8_t *required, *any_req, *pf_flag;
+  // LOD cross-fade: per page the persistent state (level drawn last frame
+  // + 1, fade's old level + 1, age; 0 = none), this frame's old level (-1
+  // none) and its required slot (-1 none); weights of the draw items
+  int32_t *fade_state, *fade_lev, *fade_info;
+  float *draw_w;
+  int32_t fade_frames;
   const float *err;
   int32_t NP, P, Smax, levels, fanout, page_size;
   int32_t lod_on;
@@ -183,6 +190,7 @@ struct ProjectArgs {
   Ctl *rctl;        // the render context's control block (receives the drawn count as projected)
   const int4 *draw;
   const int64_t *draw_off;
+  const float *draw_w;  // opacity weight of each draw item (LOD cross-fade)
   const uint8_t *pool;
   int64_t slot_bytes;
   int32_t page_size, fanout, K, fmt;  // fmt: kFmt32, kFmt16 or kFmtVQ

@@ -24,10 +24,11 @@ def v():
 
 
 def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=True, tau0=1.0, check_images=(),
-                    fp16=False, vq_codes=0):
+                    fp16=False, vq_codes=0, fade=0, step0=0.1):
     """vq_codes > 0: the pool holds VQ records (compressed pages) with an SH
     codebook of that many codes; images are compared with the oracle run on
-    the attributes those records decode to."""
+    the attributes those records decode to.  fade > 0: LOD cross-fade of
+    that many frames (draw weights compared too)."""
     scene = import_scene(v, raw, sc, fp16=fp16)
     W, H = cams[0].width, cams[0].height
     fmt = int(fp16)
@@ -41,15 +42,17 @@ def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=
         fmt, rec = v.POOL_VQ, scene.info.record_bytes_vq
     budget = budget_pages * sc.params.page_size * rec
     cfg = v.RenderConfig(max_width=W, max_height=H, lod=lod, links=links, staging_bytes=budget, tau0=tau0,
-                         fp16_pool=fmt)
+                         fp16_pool=fmt, lod_fade_frames=fade, step0=step0)
     r = v.Renderer(scene, cfg, pool_slots=pool_slots)
     rp = rs.ResidencyParams(n_entries=pool_slots, page_size=sc.params.page_size, levels=len(sc.levels),
-                            fanout=sc.params.lod_fanout, record_bytes=rec, budget_bytes=budget, lod=lod, tau0=tau0)
+                            fanout=sc.params.lod_fanout, record_bytes=rec, budget_bytes=budget, lod=lod, tau0=tau0,
+                            fade_frames=fade, step0=step0)
     pt = rs.PageTable(rp)
     smax = sc.params.lod_fanout ** (len(sc.levels) - 1)
     host_pages = [scene.pages(l, fp16=fp16) for l in range(len(sc.levels))]
     # images of an fp16 or VQ pool are compared with the oracle on the attributes it stores
     osc = round16_scene(sc) if fp16 else sc
+    faded = []
     if vq_codes:
         host_pages = [scene.export(v.SCENE_PAGES_VQ, l).reshape(sc.n_pages, -1) for l in range(len(sc.levels))]
         osc = dataclasses.replace(sc, levels=ob.vq_levels(sc.levels, cb, codes))
@@ -78,6 +81,9 @@ def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=
                                       np.array(up["copies"], np.int32).reshape(-1, 4))
         draw = r.debug(v.DBG_DRAW, np.int32).reshape(-1, 4)
         np.testing.assert_array_equal(draw, np.array(up["draw"], np.int32).reshape(-1, 4))
+        np.testing.assert_array_equal(r.debug(v.DBG_DRAW_W, np.float32), np.array(up["draw_w"], np.float32))
+        assert st["fading"] == up["fading"]
+        faded.append(up["fading"])
         np.testing.assert_array_equal(r.debug(v.DBG_MISSING, np.int32), np.array(up["missing"], np.int32))
         assert st["usage"] == np.float32(up["usage"])
         assert st["tau"] == np.float32(pt.tau)
@@ -89,6 +95,7 @@ def _run_trajectory(v, raw, sc, cams, pool_slots, budget_pages, lod=True, links=
             np.testing.assert_array_equal(pool[e, s * len(blk):(s + 1) * len(blk)], blk)
         if f in check_images:
             compare_image(img, ref["render"])
+    r.faded = faded
     return r
 
 
@@ -250,3 +257,22 @@ def test_city_lod_trajectory_vq(v):
     cams = [city_cam(160.0, k) for k in range(10)]
     _run_trajectory(v, raw, sc, cams, pool_slots=8, budget_pages=5, lod=True, tau0=2.0, check_images=(0, 5, 9),
                     vq_codes=64)
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_city_lod_trajectory_fade(v, fp16):
+    """LOD cross-fade of 4 frames along a walk whose pages change level: page
+    table, the draw list with both levels of fading pages and its weights,
+    and images (opacities scaled by the weights) against the oracle; fp16
+    pools go through the TMA-staged projection (pages of 512, fanout 4)."""
+    if fp16:
+        raw, sc = city_scene(levels=3, fanout=4, page_size=512)
+    else:
+        raw, sc = city_scene()
+    # a dolly towards the city while the controller lowers tau (a large
+    # initial tau and step): many pages move to finer levels
+    cams = [scenegen.look_at((80, -260 + 15 * k, 40 - 2 * k), (80, 80, 0), (0, 0, 1), 200, 120, 60.0, (16, 16))
+            for k in range(16)]
+    r = _run_trajectory(v, raw, sc, cams, pool_slots=24, budget_pages=12, lod=True, tau0=10.0, step0=1.5,
+                        check_images=(2, 5, 9, 14), fp16=fp16, fade=4)
+    assert sum(r.faded) > 20
