@@ -148,20 +148,31 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(GemmArgs g) {
   }
 }
 
-// Batch-1 inference: y[n] = x . B[:, n] (+ bias, ReLU), a thread per output
-// column n (coalesced rows of B), the input row staged in shared memory.
-constexpr int kGemvThreads = 256, kGemvMaxK = 1024;
+// Batch-1 inference: y[n] = x . B[:, n] (+ bias, ReLU).  A CTA takes 32
+// output columns (a warp reads 32 consecutive weights of a row) and splits
+// the K rows over its 8 warps (warp w: rows w, w + 8, ...); the 8 partial
+// sums are added in warp order from shared memory.  The input row is staged
+// in shared memory.
+constexpr int kGemvThreads = 256, kGemvMaxK = 1024, kGemvCols = 32, kGemvSplit = kGemvThreads / kGemvCols;
 __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemmArgs g) {
   __shared__ float xs[kGemvMaxK];
+  __shared__ float part[kGemvSplit][kGemvCols];
   for (int k = threadIdx.x; k < g.K; k += kGemvThreads) xs[k] = __bfloat162float(g.A[k]);
   __syncthreads();
-  const int n = blockIdx.x * kGemvThreads + threadIdx.x;
-  if (n >= g.N) return;
-  const __nv_bfloat16 *b = g.B + n;
+  const int c = threadIdx.x % kGemvCols, w = threadIdx.x / kGemvCols;
+  const int n = blockIdx.x * kGemvCols + c;
   float acc = 0.0f;
+  if (n < g.N) {
+    const __nv_bfloat16 *b = g.B + n;
 #pragma unroll 8
-  for (int k = 0; k < g.K; ++k) acc += xs[k] * __bfloat162float(b[(int64_t)k * g.ldb]);
-  float v = acc;
+    for (int k = w; k < g.K; k += kGemvSplit) acc += xs[k] * __bfloat162float(b[(int64_t)k * g.ldb]);
+  }
+  part[w][c] = acc;
+  __syncthreads();
+  if (w != 0 || n >= g.N) return;
+  float v = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kGemvSplit; ++j) v += part[j][c];
   if (g.bias) v += g.bias[n];
   if (g.relu) v = v > 0.0f ? v : 0.0f;
   if (g.C) g.C[n] = v;
@@ -239,7 +250,7 @@ void launch_gemv(const GemmArgs &g, cudaStream_t st) {
     launch_gemm(g, st);
     return;
   }
-  gemv_kernel<<<(g.N + kGemvThreads - 1) / kGemvThreads, kGemvThreads, 0, st>>>(g);
+  gemv_kernel<<<(g.N + kGemvCols - 1) / kGemvCols, kGemvThreads, 0, st>>>(g);
 }
 
 void launch_bce_grad(const float *logit, const float *target, const float *mask, int64_t n, float inv_n, float *dy,

@@ -84,7 +84,7 @@ __device__ void bscan_n(const int64_t *v, int64_t *pre, int64_t *total, MScan<N>
 __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   extern __shared__ uint64_t s_keys[];
   __shared__ ScanSmem sm;
-  __shared__ MScan<5> sm4;
+  __shared__ MScan<4> sm4;
   __shared__ int m_l[kMaxLevels], S_l[kMaxLevels];
   __shared__ int n_lvl[kMaxLevels], open_cnt[kMaxLevels], open_base[kMaxLevels], fresh_start[kMaxLevels + 1];
   __shared__ int s_nfree, s_hits;
@@ -115,7 +115,12 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       const int p = p0 + k;
       r[k] = p < NP ? a.req[p] : 0u;
       dflag[k] = (p < NP && r[k] != 0u) ? (int)a.direct[p] : 0;
-      if (p < NP) { a.reqlev[p] = -1; a.matched[p] = 0; a.draw_info[p] = -1; a.fade_lev[p] = -1; a.fade_info[p] = -1; }
+      if (p < NP) {
+        a.reqlev[p] = -1;
+        a.matched[p] = 0;
+        a.draw_info[p] = -1;
+        if (a.fade_frames > 0) { a.fade_lev[p] = -1; a.fade_info[p] = -1; }
+      }
       v2[0] += r[k] != 0u;
       v2[1] += dflag[k];
     }
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
         const int p = a.pt_slot[k];
         const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
         // the old level of a running cross-fade, when resident, stays required
-        const int rf = (!r && p >= 0 && a.fade_lev[p] == l) ? 1 : 0;
+        const int rf = (a.fade_frames > 0 && !r && p >= 0 && a.fade_lev[p] == l) ? 1 : 0;
         a.required[k] = (uint8_t)(r | rf);
         if (r) {
           a.matched[p] = 1;
@@ -413,40 +418,39 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   for (int i = (int)nadm + tid; i < nu; i += RT) a.matched[(int)(a.ukeys[i] & 0x7FFFFFFFull)] = 2;
   __syncthreads();
   // ---- 12. missing list and draw list, ascending page (a fading page: its
-  // own item, then its old level's); draw offsets and weights
+  // own item, then its old level's); draw offsets and weights.  Counts are
+  // scanned two to a word (missing | items << 32, levels > 0 | fading << 32:
+  // each below 2^31)
   int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0, nfade = 0;
   for (int c = 0; c < NP; c += RT * kPer) {
     const int p0 = c + tid * kPer;
     int fm[kPer], fd[kPer], ff[kPer];
-    int64_t g[kPer];
-    int64_t v5[5] = {0, 0, 0, 0, 0};
+    int64_t v3[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int p = p0 + k;
-      fm[k] = 0; fd[k] = 0; ff[k] = 0; g[k] = 0;
+      fm[k] = 0; fd[k] = 0; ff[k] = 0;
       if (p < NP) {
         fm[k] = a.matched[p] == 2;
         fd[k] = a.draw_info[p] >= 0 && !fm[k];
-        ff[k] = a.fade_info[p] >= 0;
+        ff[k] = F > 0 && a.fade_info[p] >= 0;
         if (fd[k]) {
           const int lv = a.reqlev[p];
-          g[k] += m_l[lv];
-          v5[3] += lv > 0;
+          v3[1] += m_l[lv];
+          v3[2] += lv > 0;
         }
         if (ff[k]) {
           const int lv = a.fade_lev[p];
-          g[k] += m_l[lv];
-          v5[3] += lv > 0;
+          v3[1] += m_l[lv];
+          v3[2] += lv > 0;
         }
       }
-      v5[0] += fm[k];
-      v5[1] += fd[k] + ff[k];
-      v5[2] += g[k];
-      v5[4] += fd[k] & ff[k];
+      v3[0] += (int64_t)fm[k] | ((int64_t)(fd[k] + ff[k]) << 32);
+      v3[2] += (int64_t)(fd[k] & ff[k]) << 32;
     }
-    int64_t pre5[5], tot5[5];
-    bscan_n<5>(v5, pre5, tot5, sm4);
-    int64_t om = nmiss + pre5[0], od = ndraw + pre5[1], og = gsum + pre5[2];
+    int64_t pre3[3], tot3[3];
+    bscan_n<3>(v3, pre3, tot3, *reinterpret_cast<MScan<3> *>(&sm4));
+    int64_t om = nmiss + (pre3[0] & 0xFFFFFFFF), od = ndraw + (pre3[0] >> 32), og = gsum + pre3[1];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int p = p0 + k;
@@ -459,29 +463,31 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
       }
       if (fd[k]) {
         const int slot = a.draw_info[p];
-        a.draw[od] = make_int4(p, a.reqlev[p], slot / Smax, slot % Smax);
+        const int lv = a.reqlev[p];
+        a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
         a.draw_off[od] = og;
         a.draw_w[od] = wn;
         ++od;
-        og += m_l[a.reqlev[p]];
+        og += m_l[lv];
       }
       if (ff[k]) {
         const int slot = a.fade_info[p];
-        a.draw[od] = make_int4(p, a.fade_lev[p], slot / Smax, slot % Smax);
+        const int lv = a.fade_lev[p];
+        a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
         a.draw_off[od] = og;
         a.draw_w[od] = wo;
         ++od;
-        og += m_l[a.fade_lev[p]];
+        og += m_l[lv];
       }
       // the level drawn this frame, for the next frame's fade
       if (F > 0 && p < NP && a.reqlev[p] >= 0)
         a.fade_state[p] = (a.fade_state[p] & ~0xFF) | (fd[k] ? a.reqlev[p] + 1 : 0);
     }
-    nmiss += tot5[0];
-    ndraw += tot5[1];
-    gsum += tot5[2];
-    nlod += tot5[3];
-    nfade += tot5[4];
+    nmiss += tot3[0] & 0xFFFFFFFF;
+    ndraw += tot3[0] >> 32;
+    gsum += tot3[1];
+    nlod += tot3[2] & 0xFFFFFFFF;
+    nfade += tot3[2] >> 32;
   }
   if (tid == 0) {
     a.draw_off[ndraw] = gsum;
