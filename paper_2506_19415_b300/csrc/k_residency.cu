@@ -35,6 +35,8 @@
 //              within 10 frames, *0.99 after a reversal within 10 frames.
 // Compiled with -fmad=false (the LOD test and the controller are fp32
 // formulas evaluated exactly as written).
+#include <type_traits>
+
 #include "block_sel.cuh"
 #include "renderer.cuh"
 
@@ -175,33 +177,40 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     }
     __syncthreads();
   }
-  // ---- 3. stage 1
-  for (int e = tid; e < P; e += RT) {
-    const int l = a.pt_lod[e];
-    int any = 0;
-    if (l >= 0) {
-      for (int s = 0; s < S_l[l]; ++s) {
-        const int64_t k = (int64_t)e * Smax + s;
-        const int p = a.pt_slot[k];
-        const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
-        // the old level of a running cross-fade, when resident, stays required
-        const int rf = (a.fade_frames > 0 && !r && p >= 0 && a.fade_lev[p] == l) ? 1 : 0;
-        a.required[k] = (uint8_t)(r | rf);
-        if (r) {
-          a.matched[p] = 1;
-          a.draw_info[p] = (int)k;
-          any = 1;
-          if (a.pf_flag[k]) { atomicAdd(&s_hits, 1); a.pf_flag[k] = 0; }
-        }
-        if (rf) {
-          a.fade_info[p] = (int)k;
-          any = 1;
+  // ---- 3. stage 1 (a copy of the loop without the fade's test when it is off)
+  auto stage1 = [&](auto fade_on) {
+    constexpr bool FADE = decltype(fade_on)::value;
+    for (int e = tid; e < P; e += RT) {
+      const int l = a.pt_lod[e];
+      int any = 0;
+      if (l >= 0) {
+        for (int s = 0; s < S_l[l]; ++s) {
+          const int64_t k = (int64_t)e * Smax + s;
+          const int p = a.pt_slot[k];
+          const int r = (p >= 0 && a.reqlev[p] == l) ? 1 : 0;
+          // the old level of a running cross-fade, when resident, stays required
+          const int rf = (FADE && !r && p >= 0 && a.fade_lev[p] == l) ? 1 : 0;
+          a.required[k] = (uint8_t)(r | rf);
+          if (r) {
+            a.matched[p] = 1;
+            a.draw_info[p] = (int)k;
+            any = 1;
+            if (a.pf_flag[k]) { atomicAdd(&s_hits, 1); a.pf_flag[k] = 0; }
+          }
+          if (FADE && rf) {
+            a.fade_info[p] = (int)k;
+            any = 1;
+          }
         }
       }
+      a.any_req[e] = (uint8_t)any;
+      if (any) a.pt_last[e] = frame;
     }
-    a.any_req[e] = (uint8_t)any;
-    if (any) a.pt_last[e] = frame;
-  }
+  };
+  if (F > 0)
+    stage1(std::true_type{});
+  else
+    stage1(std::false_type{});
   __syncthreads();
   // ---- 4. unmatched requests as priority keys
   int64_t nu = 0;
@@ -422,73 +431,80 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
   // scanned two to a word (missing | items << 32, levels > 0 | fading << 32:
   // each below 2^31)
   int64_t nmiss = 0, ndraw = 0, gsum = 0, nlod = 0, nfade = 0;
-  for (int c = 0; c < NP; c += RT * kPer) {
-    const int p0 = c + tid * kPer;
-    int fm[kPer], fd[kPer], ff[kPer];
-    int64_t v3[3] = {0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int p = p0 + k;
-      fm[k] = 0; fd[k] = 0; ff[k] = 0;
-      if (p < NP) {
-        fm[k] = a.matched[p] == 2;
-        fd[k] = a.draw_info[p] >= 0 && !fm[k];
-        ff[k] = F > 0 && a.fade_info[p] >= 0;
+  auto step12 = [&](auto fade_on) {
+    constexpr bool FADE = decltype(fade_on)::value;
+    for (int c = 0; c < NP; c += RT * kPer) {
+      const int p0 = c + tid * kPer;
+      int fm[kPer], fd[kPer], ff[kPer];
+      int64_t v3[3] = {0, 0, 0};
+  #pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int p = p0 + k;
+        fm[k] = 0; fd[k] = 0; ff[k] = 0;
+        if (p < NP) {
+          fm[k] = a.matched[p] == 2;
+          fd[k] = a.draw_info[p] >= 0 && !fm[k];
+          ff[k] = FADE && a.fade_info[p] >= 0;
+          if (fd[k]) {
+            const int lv = a.reqlev[p];
+            v3[1] += m_l[lv];
+            v3[2] += lv > 0;
+          }
+          if (FADE && ff[k]) {
+            const int lv = a.fade_lev[p];
+            v3[1] += m_l[lv];
+            v3[2] += lv > 0;
+          }
+        }
+        v3[0] += (int64_t)fm[k] | ((int64_t)(fd[k] + ff[k]) << 32);
+        v3[2] += (int64_t)(fd[k] & ff[k]) << 32;
+      }
+      int64_t pre3[3], tot3[3];
+      bscan_n<3>(v3, pre3, tot3, *reinterpret_cast<MScan<3> *>(&sm4));
+      int64_t om = nmiss + (pre3[0] & 0xFFFFFFFF), od = ndraw + (pre3[0] >> 32), og = gsum + pre3[1];
+  #pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int p = p0 + k;
+        if (fm[k]) a.missing[om++] = p;
+        // weights: the new level (age + 1) / (F + 1), the old 1 - that
+        float wn = 1.0f, wo = 1.0f;
+        if (FADE && fd[k] && ff[k]) {
+          wn = (float)(((a.fade_state[p] >> 16) & 0xFFFF) + 1) / (float)(F + 1);
+          wo = 1.0f - wn;
+        }
         if (fd[k]) {
+          const int slot = a.draw_info[p];
           const int lv = a.reqlev[p];
-          v3[1] += m_l[lv];
-          v3[2] += lv > 0;
+          a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
+          a.draw_off[od] = og;
+          a.draw_w[od] = wn;
+          ++od;
+          og += m_l[lv];
         }
-        if (ff[k]) {
+        if (FADE && ff[k]) {
+          const int slot = a.fade_info[p];
           const int lv = a.fade_lev[p];
-          v3[1] += m_l[lv];
-          v3[2] += lv > 0;
+          a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
+          a.draw_off[od] = og;
+          a.draw_w[od] = wo;
+          ++od;
+          og += m_l[lv];
         }
+        // the level drawn this frame, for the next frame's fade
+        if (FADE && p < NP && a.reqlev[p] >= 0)
+          a.fade_state[p] = (a.fade_state[p] & ~0xFF) | (fd[k] ? a.reqlev[p] + 1 : 0);
       }
-      v3[0] += (int64_t)fm[k] | ((int64_t)(fd[k] + ff[k]) << 32);
-      v3[2] += (int64_t)(fd[k] & ff[k]) << 32;
+      nmiss += tot3[0] & 0xFFFFFFFF;
+      ndraw += tot3[0] >> 32;
+      gsum += tot3[1];
+      nlod += tot3[2] & 0xFFFFFFFF;
+      nfade += tot3[2] >> 32;
     }
-    int64_t pre3[3], tot3[3];
-    bscan_n<3>(v3, pre3, tot3, *reinterpret_cast<MScan<3> *>(&sm4));
-    int64_t om = nmiss + (pre3[0] & 0xFFFFFFFF), od = ndraw + (pre3[0] >> 32), og = gsum + pre3[1];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int p = p0 + k;
-      if (fm[k]) a.missing[om++] = p;
-      // weights: the new level (age + 1) / (F + 1), the old 1 - that
-      float wn = 1.0f, wo = 1.0f;
-      if (fd[k] && ff[k]) {
-        wn = (float)(((a.fade_state[p] >> 16) & 0xFFFF) + 1) / (float)(F + 1);
-        wo = 1.0f - wn;
-      }
-      if (fd[k]) {
-        const int slot = a.draw_info[p];
-        const int lv = a.reqlev[p];
-        a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
-        a.draw_off[od] = og;
-        a.draw_w[od] = wn;
-        ++od;
-        og += m_l[lv];
-      }
-      if (ff[k]) {
-        const int slot = a.fade_info[p];
-        const int lv = a.fade_lev[p];
-        a.draw[od] = make_int4(p, lv, slot / Smax, slot % Smax);
-        a.draw_off[od] = og;
-        a.draw_w[od] = wo;
-        ++od;
-        og += m_l[lv];
-      }
-      // the level drawn this frame, for the next frame's fade
-      if (F > 0 && p < NP && a.reqlev[p] >= 0)
-        a.fade_state[p] = (a.fade_state[p] & ~0xFF) | (fd[k] ? a.reqlev[p] + 1 : 0);
-    }
-    nmiss += tot3[0] & 0xFFFFFFFF;
-    ndraw += tot3[0] >> 32;
-    gsum += tot3[1];
-    nlod += tot3[2] & 0xFFFFFFFF;
-    nfade += tot3[2] >> 32;
-  }
+  };
+  if (F > 0)
+    step12(std::true_type{});
+  else
+    step12(std::false_type{});
   if (tid == 0) {
     a.draw_off[ndraw] = gsum;
     ctl->n_req = (int)nreq;
