@@ -151,16 +151,16 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
     a.reqlev[q.x] = lev;
   }
   __syncthreads();
-  // ---- 2b. cross-fade state (state word: cur + 1 | (from + 1) << 8 | age << 16)
+  // ---- 2b. cross-fade state of the requested pages (state word: cur + 1 |
+  // (from + 1) << 8 | age << 16, valid only when stamped with the previous
+  // frame: a page not requested last frame starts from nothing)
   const int F = a.fade_frames;
   if (F > 0) {
-    for (int p = tid; p < NP; p += RT) {
-      const int l = a.reqlev[p];
-      if (l < 0) {
-        a.fade_state[p] = 0;
-        continue;
-      }
-      const int32_t w = a.fade_state[p];
+    for (int i = tid; i < nreq; i += RT) {
+      const int p = a.requests[i].x;
+      const int l = a.requests[i].w;
+      const int32_t w = a.fade_frame[p] == frame - 1 ? a.fade_state[p] : 0;
+      a.fade_frame[p] = frame;
       const int cur = (w & 0xFF) - 1;
       int frm = ((w >> 8) & 0xFF) - 1, age = (w >> 16) & 0xFFFF;
       if (frm >= 0) {

@@ -303,7 +303,7 @@ __device__ __forceinline__ void emit_rows(const PairOut &po, const SplatEllipse 
 // sh.hist the kernel also counts the sort's digits (shared-memory histograms
 // merged into sh.hist) and clears the sort's look-back words and tile
 // counters.  A batch (ev.vt) emits the records of all its views.
-__global__ void __launch_bounds__(256) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, int views, EmitViews ev,
+__global__ void __launch_bounds__(256, 4) emit_kernel(const Ctl *ctl, Splats sp, int64_t ncap, int views, EmitViews ev,
                                                    const uint32_t *offsets, uint64_t *keys, uint32_t *vals,
                                                    int64_t pair_cap, KeyFormat kf, SortHist sh, uint64_t *pieces,
                                                    uint32_t *piece_ctr, int64_t piece_cap, uint2 *ranges, int ntiles) {

@@ -148,6 +148,7 @@ Layout make_layout(const Dims &d) {
   L.draw_off = take(8 * (2 * NP + 1));
   L.draw_w = take(4 * 2 * NP);
   L.fade_state = take(4 * NP);
+  L.fade_frame = take(4 * NP);
   L.fade_lev = take(4 * NP);
   L.fade_info = take(4 * NP);
   L.missing = take(4 * NP);
@@ -349,6 +350,8 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pt_slot), 0xFF, 4 * P * d.Smax, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_flag), 0, P * d.Smax, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.fade_state), 0, 4 * d.NP, st), "memset", &rc);
+  // (a stamp no frame number - 1 can equal)
+  ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.fade_frame), 0x80, 4 * d.NP, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemsetAsync(r->at<void>(L.pf_count), 0, 16, st), "memset", &rc);
   ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.centroid), s->centroid.data(), 4 * s->centroid.size(),
                                      cudaMemcpyHostToDevice, st), "copy", &rc);
@@ -566,6 +569,7 @@ extern "C" int vm3dgs_update_residency(vm3dgs_renderer *r, void *stream, void *c
   a.draw_off = r->at<int64_t>(r->lay.draw_off);
   a.draw_w = r->at<float>(r->lay.draw_w);
   a.fade_state = r->at<int32_t>(r->lay.fade_state);
+  a.fade_frame = r->at<int32_t>(r->lay.fade_frame);
   a.fade_lev = r->at<int32_t>(r->lay.fade_lev);
   a.fade_info = r->at<int32_t>(r->lay.fade_info);
   a.fade_frames = r->prm.lod_fade_frames;

@@ -62,7 +62,7 @@ struct Layout {
       admitted_pos, copies, copy_seg, draw, draw_off, missing, pt_lod, pt_last, pt_slot, required, any_req, tri_v,
       clusters, link_ptr, link_col, err, raster_queue, raster_count, raster_vis, raster_clip, raster_bands, raster_live, dreq, centroid,
       pf_flag, pf_mask, pf_cand, pf_copies, pf_copy_seg, pf_count, pf_base, pf_req, views, codebook, fade_state,
-      fade_lev, fade_info, draw_w, total;
+      fade_frame, fade_lev, fade_info, draw_w, total;
   CtxLayout cx[kContexts];
 };
 
@@ -149,7 +149,7 @@ struct ResidencyArgs {
   // LOD cross-fade: per page the persistent state (level drawn last frame
   // + 1, fade's old level + 1, age; 0 = none), this frame's old level (-1
   // none) and its required slot (-1 none); weights of the draw items
-  int32_t *fade_state, *fade_lev, *fade_info;
+  int32_t *fade_state, *fade_frame, *fade_lev, *fade_info;
   float *draw_w;
   int32_t fade_frames;
   const float *err;
