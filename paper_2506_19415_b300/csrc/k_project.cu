@@ -86,16 +86,18 @@ struct GlobalSrc {
   int m, g;
   const float *cw;
   __device__ GlobalSrc(const uint8_t *b, int m_, int g_, const float *codebook) : blk(b), m(m_), g(g_), cw(nullptr) {
-    if (FMT == kFmtVQ) cw = codebook + (int64_t)R::code(b, m_, g_) * (3 * (K - 1));
+    if (FMT == kFmtVQ) cw = codebook + (int64_t)R::code(b, m_, g_) * kCodeRow;
   }
   __device__ float pos(int a) const { return R::pos(blk, m, g, a); }
   __device__ float opac() const { return R::opac(blk, m, g); }
   __device__ float scale(int a) const { return R::scale(blk, m, g, a); }
   __device__ float rot(int a) const { return R::rot(blk, m, g, a); }
   __device__ float sh(int k, int c) const {
-    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 3 * (k - 1) + c);
+    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 16 * c + (k - 1));
     return R::sh(blk, m, g, k, c);
   }
+  // VQ: channel c's coefficients of bands 1..3, four at a time
+  __device__ float4 cw4(int c, int v) const { return __ldg(reinterpret_cast<const float4 *>(cw + 16 * c) + v); }
 };
 
 // The same attributes staged in shared memory: the record's float rows (A)
@@ -108,7 +110,7 @@ struct SharedSrc {
   const float *cw;
   __device__ SharedSrc(const float *a, const __half *b, int g_, const float *codebook) : A(a), B(b), g(g_), cw(nullptr) {
     if (FMT == kFmtVQ)
-      cw = codebook + (int64_t)__half_as_ushort(B[10 * CH + g_]) * (3 * (K - 1));
+      cw = codebook + (int64_t)__half_as_ushort(B[10 * CH + g_]) * kCodeRow;
   }
   __device__ float half_at(int h) const { return __half2float(B[h * CH + g]); }
   __device__ float pos(int a) const { return A[a * CH + g]; }
@@ -116,9 +118,10 @@ struct SharedSrc {
   __device__ float scale(int a) const { return FMT != kFmt32 ? half_at(a) : A[(3 + a) * CH + g]; }
   __device__ float rot(int a) const { return FMT != kFmt32 ? half_at(3 + a) : A[(6 + a) * CH + g]; }
   __device__ float sh(int k, int c) const {
-    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 3 * (k - 1) + c);
+    if (FMT == kFmtVQ && k > 0) return __ldg(cw + 16 * c + (k - 1));
     return FMT != kFmt32 ? half_at(7 + 3 * k + c) : A[(11 + 3 * k + c) * CH + g];
   }
+  __device__ float4 cw4(int c, int v) const { return __ldg(reinterpret_cast<const float4 *>(cw + 16 * c) + v); }
 };
 
 // Projects one Gaussian for one camera and writes splat record out.
@@ -249,8 +252,21 @@ __device__ __forceinline__ void project_one(const Splats &sp, const vm3dgs_camer
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float s = 0.0f;
+    if constexpr (FMT == kFmtVQ) {
+      // bands 1..3 from the codeword by 16-byte loads, summed in k order
+      s = __fmaf_rn(src.sh(0, c), Y[0], s);
 #pragma unroll
-    for (int k = 0; k < K; ++k) s = __fmaf_rn(src.sh(k, c), Y[k], s);
+      for (int v = 0; v < (K + 2) / 4; ++v) {
+        const float4 t = src.cw4(c, v);
+        const float q[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (1 + 4 * v + i < K) s = __fmaf_rn(q[i], Y[1 + 4 * v + i], s);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s = __fmaf_rn(src.sh(k, c), Y[k], s);
+    }
     s += 0.5f;
     rgb[c] = s > 0.0f ? s : 0.0f;
   }

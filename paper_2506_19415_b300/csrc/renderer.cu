@@ -115,7 +115,7 @@ Dims make_dims(const vm3dgs_scene *s, const vm3dgs_params *p, int64_t P) {
   d.raster_cap = 2 * (d.ntri < (int64_t(1) << 20) ? (d.ntri > 0 ? d.ntri : 1) : (int64_t(1) << 20));
   d.ukey_cap = (int)pow2_at_least(d.NP > 0 ? d.NP : 1);
   d.free_cap = (int)pow2_at_least(P > 0 ? P : 1);
-  d.cb_floats = p->fp16_pool == kFmtVQ ? (int64_t)s->codebook.size() : 0;
+  d.cb_floats = p->fp16_pool == kFmtVQ ? (int64_t)s->n_codes * kCodeRow : 0;
   return d;
 }
 
@@ -326,9 +326,17 @@ extern "C" int vm3dgs_renderer_create(const vm3dgs_scene *s, const vm3dgs_params
                                   cudaMemcpyHostToDevice), "copy", &rc);
   }
   r->maps_ok = encode_proj_maps(s, r->pool, P, r->fmt, &r->maps);
-  if (r->fmt == kFmtVQ)
-    ok = ok && cuda_ok(cudaMemcpyAsync(r->at<void>(L.codebook), s->codebook.data(), 4 * s->codebook.size(),
-                                       cudaMemcpyHostToDevice, st), "copy", &rc);
+  if (r->fmt == kFmtVQ) {
+    // device rows of kCodeRow floats: channel c's bands-1..3 coefficients
+    // at [16 c, 16 c + K - 1) (zero padded), for aligned 16-byte loads
+    std::vector<float> rows((size_t)s->n_codes * kCodeRow, 0.0f);
+    for (int j = 0; j < s->n_codes; ++j)
+      for (int k = 1; k < s->K; ++k)
+        for (int c = 0; c < 3; ++c)
+          rows[(size_t)j * kCodeRow + 16 * c + (k - 1)] = s->codebook[(size_t)j * s->code_dim + 3 * (k - 1) + c];
+    ok = ok && cuda_ok(cudaMemcpy(r->at<void>(L.codebook), rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice),
+                       "copy", &rc);
+  }
   r->rec_maps_ok = true;
   for (int k = 0; k < kContexts; ++k)
     r->rec_maps_ok = r->rec_maps_ok && encode_rec_map(r->at<float4>(L.cx[k].splat_rec), d.ncap, &r->rec_map[k]);

@@ -43,6 +43,9 @@ constexpr int kHalfVQ = 12;
 VM_HD constexpr int rec_bytes_vq() { return 16 + 2 * kHalfVQ; }
 // pool formats: 0 fp32 records, 1 fp16 records, 2 VQ records
 constexpr int kFmt32 = 0, kFmt16 = 1, kFmtVQ = 2;
+// a codeword in device memory: per channel c its bands-1..3 coefficients at
+// floats [16 c, 16 c + K - 1), zero padded (aligned 16-byte loads)
+constexpr int kCodeRow = 48;
 
 }  // namespace vm
 
