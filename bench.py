@@ -341,6 +341,14 @@ def run_arm(v, r, cams, warmup, steps, copy_stream=None, e2e=False, timing=False
 # until a capture of the current kernel exists.
 SORT_DRAM_BYTES_PER_PAIR_PASS = None
 
+# The blend's binding bound is instruction issue, not memory: the pipe
+# utilisation of one blend launch from an ncu --set full capture (1M-Gaussian
+# city at 1080p, fp16 pool, the full-size parity test's frame 1), which the
+# bench cannot read live.
+BLEND_ISSUE = {"issue_active_pct": 79.4, "alu_pipe_pct": 56.2, "fma_pipe_pct": 35.3, "dram_pct_of_peak": 1.4,
+               "source": "ncu --set full, one launch (smsp__issue_active, sm__pipe_alu_cycles_active, "
+                         "sm__pipe_fma_cycles_active, gpu__dram_throughput)"}
+
 
 def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
     """Roofline of the dominant kernel (the radix sort) and of the gather
@@ -378,6 +386,7 @@ def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
         a = b / t / 1e9 if t > 0 else 0.0
         detail[k] = {"achieved": round(a, 1), "frac": round(a / peak, 4), "us_per_launch": round(t * 1e6, 2),
                      "algorithmic_bytes_per_launch": int(b), "per_unit": note}
+    detail["blend"]["alu"] = BLEND_ISSUE
     if alt_sort is not None:
         detail["sort_cooperative"] = alt_sort
     coop = per_view < passes

@@ -270,12 +270,12 @@ bool mesh_occupancy(const MeshGrid &g, int64_t n, const float *pos, const float 
 
 bool mesh_surface(const MeshGrid &g, const std::vector<uint8_t> &closed, std::vector<int32_t> &D,
                   std::vector<int32_t> &tris, std::string &err) {
-  static bool table_ready = false;
-  static CaseTable table;
-  if (!table_ready) {
-    make_table(table);
-    table_ready = true;
-  }
+  // (built once, thread-safely, on first use)
+  static const CaseTable table = [] {
+    CaseTable t;
+    make_table(t);
+    return t;
+  }();
   if (!ok_or(cudaMemcpyToSymbol(c_table, &table, sizeof(table)), "case table", err)) return false;
   const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
   const int64_t NV = (int64_t)nx * ny * nz, NC = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);

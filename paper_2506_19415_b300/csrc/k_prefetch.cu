@@ -402,12 +402,8 @@ extern "C" int vm3dgs_prefetch(vm3dgs_renderer *r, vm3dgs_prefetcher *p, const v
   a.threshold = threshold;
   a.f_px = cam->fy;
   for (int k = 0; k < 3; ++k) a.campos[k] = cam->campos[k];
-  static bool attr = false;
   const int smem = kSmemKeys * (int)sizeof(uint64_t);
-  if (!attr) {
-    cudaFuncSetAttribute(place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  max_dynamic_smem((const void *)place_kernel, smem);
   place_kernel<<<1, RT, smem, st>>>(a);
   StreamArgs sa{};
   sa.count = a.count;

@@ -495,12 +495,8 @@ void launch_kb(const ProjectArgs &a, const ViewTable *views, int n_views, cudaSt
 template <int K, int FMT, int CH>
 void launch_tma(const ProjectArgs &a, const vm3dgs_camera &cam, cudaStream_t st) {
   using S = TmaShape<K, FMT, CH>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(project_tma_kernel<K, FMT, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    prefer_shared((const void *)project_tma_kernel<K, FMT, CH>);
-    attr = true;
-  }
+  max_dynamic_smem((const void *)project_tma_kernel<K, FMT, CH>, S::SMEM);
+  prefer_shared((const void *)project_tma_kernel<K, FMT, CH>);
   project_tma_kernel<K, FMT, CH>
       <<<full_wave((const void *)project_tma_kernel<K, FMT, CH>, 128, S::SMEM), 128, S::SMEM, st>>>(a, cam, *a.maps);
 }

@@ -555,12 +555,8 @@ __global__ void __launch_bounds__(RT) residency_kernel(ResidencyArgs a) {
 }  // namespace
 
 void launch_residency(const ResidencyArgs &a, cudaStream_t st) {
-  static bool attr = false;
   const int smem = kSmemKeys * (int)sizeof(uint64_t);
-  if (!attr) {
-    cudaFuncSetAttribute(residency_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  max_dynamic_smem((const void *)residency_kernel, smem);
   residency_kernel<<<1, RT, smem, st>>>(a);
 }
 

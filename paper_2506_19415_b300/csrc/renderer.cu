@@ -51,6 +51,19 @@ void prefer_shared(const void *kernel) {
   done[key] = true;
 }
 
+void max_dynamic_smem(const void *kernel, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<uint64_t, int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = (uint64_t)(uintptr_t)kernel ^ ((uint64_t)dev << 56);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done[key] = bytes;
+}
+
 int wave_grid(const void *kernel, int threads, size_t smem, int64_t n, int64_t per_block) {
   const int64_t need = per_block > 0 ? (n + per_block - 1) / per_block : 1;
   const int64_t g = std::min<int64_t>(need, full_wave(kernel, threads, smem));

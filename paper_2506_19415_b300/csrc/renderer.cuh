@@ -93,6 +93,9 @@ int full_wave(const void *kernel, int threads, size_t smem);
 // Asks for the largest shared-memory carveout for a kernel that lives on
 // shared memory (so that as many CTAs fit as registers allow); once per kernel.
 void prefer_shared(const void *kernel);
+// Raises a kernel's dynamic shared-memory limit to `bytes`, once per kernel
+// and device (kernel attributes belong to a device).
+void max_dynamic_smem(const void *kernel, int bytes);
 // min(blocks needed for n items at `per_block` items each, full_wave), >= 1
 int wave_grid(const void *kernel, int threads, size_t smem, int64_t n, int64_t per_block);
 
