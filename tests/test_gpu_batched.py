@@ -212,3 +212,45 @@ def test_multi_camera_feedback_against_oracle(v):
     reqs = r.debug(v.DBG_REQUESTS, np.int32).reshape(-1, 4)
     np.testing.assert_array_equal(reqs[:, 0], np.flatnonzero(req))
     np.testing.assert_array_equal(reqs[:, 1].view(np.uint32), req[req != 0])
+
+
+def test_batched_vq_pool_equals_single_views(v):
+    """The batched projection reads VQ records and the codebook as the
+    single-view projection does."""
+    sc, scene = _scene(v)
+    scene.quantize_sh(64, 4)
+    cams = _views(4, [(16, 16), (8, 8)])
+    cfg = v.RenderConfig(max_width=640, max_height=400, lod=False, fp16_pool=v.POOL_VQ, max_views=8,
+                         staging_bytes=1 << 40)
+    r = v.Renderer(scene, cfg, pool_slots=sc.n_pages)
+    r.request_all()
+    r.update_residency()
+    singles = [r.render([c])[0].cpu().numpy() for c in cams]
+    imgs = [im.cpu().numpy() for im in r.render_batched(cams)]
+    for a, b in zip(imgs, singles):
+        np.testing.assert_allclose(a, b, atol=2e-6)
+    assert r.stats()["status"] == 0
+
+
+def test_batched_cross_fade_equals_single_views(v):
+    """With an LOD cross-fade running, the batched projection applies the
+    draw items' opacity weights as the single-view projection does."""
+    from _common import city_scene
+    raw, sc = city_scene()
+    scene = import_scene(v, raw, sc)
+    cfg = v.RenderConfig(max_width=200, max_height=120, lod=True, max_views=4, staging_bytes=12 * 512 * 236,
+                         tau0=10.0, step0=1.5, lod_fade_frames=4)
+    r = v.Renderer(scene, cfg, pool_slots=24)
+    faded = 0
+    for k in range(10):
+        cams = [scenegen.look_at((80, -260 + 15 * k, 40 - 2 * k), (80, 80, 0), (0, 0, 1), 200, 120, 60.0, (16, 16)),
+                scenegen.look_at((60, -250 + 15 * k, 30), (80, 80, 0), (0, 0, 1), 160, 96, 70.0, (8, 8))]
+        r.render_feedback(cams)
+        r.update_residency()
+        st = r.stats()
+        faded += st["fading"]
+        singles = [r.render([c])[0].cpu().numpy() for c in cams]
+        imgs = [im.cpu().numpy() for im in r.render_batched(cams)]
+        for a, b in zip(imgs, singles):
+            np.testing.assert_allclose(a, b, atol=2e-6)
+    assert faded > 0 and r.stats()["status"] == 0

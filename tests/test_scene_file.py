@@ -54,3 +54,17 @@ def test_bad_scene_files_rejected(tmp_path):
     (tmp_path / "fields.vm3dgs").write_bytes(bytes(wrong))
     with pytest.raises(v.Vm3dgsError):
         v.vm3dgs_scene_open(tmp_path / "fields.vm3dgs")
+
+
+def test_quantize_after_open(tmp_path):
+    """Compressed pages are not written to scene files: quantising an opened
+    scene gives the codebook and VQ records of quantising the original."""
+    sc = _scene()
+    path = tmp_path / "city.vm3dgs"
+    sc.save(path)
+    op = v.vm3dgs_scene_open(path)
+    sc.quantize_sh(24, 4, 4000)
+    op.quantize_sh(24, 4, 4000)
+    np.testing.assert_array_equal(op.codebook(), sc.codebook())
+    for l in range(sc.info.lod_levels):
+        np.testing.assert_array_equal(op.export(v.SCENE_PAGES_VQ, l), sc.export(v.SCENE_PAGES_VQ, l))
