@@ -95,8 +95,8 @@ __device__ void raster_serial(const Tri &t, int Wf, uint64_t *fb) {
   bool own[3];
   float farea;
   edges(t, dxe, dye, own, &farea);
-  const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
-  for (int64_t q = 0; q < npx; ++q) shade(t, dxe, dye, own, farea, t.i0 + q % bw, t.j0 + q / bw, Wf, fb);
+  for (int64_t j = t.j0; j <= t.j1; ++j)
+    for (int64_t i = t.i0; i <= t.i1; ++i) shade(t, dxe, dye, own, farea, i, j, Wf, fb);
 }
 
 struct RasterQueues {
@@ -544,8 +544,21 @@ __global__ void __launch_bounds__(256) raster_medium_kernel(const QTri *queue, c
     bool own[3];
     float farea;
     edges(t, dxe, dye, own, &farea);
-    const int64_t bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
-    for (int64_t p = lane; p < npx; p += 32) shade(t, dxe, dye, own, farea, t.i0 + p % bw, t.j0 + p / bw, Wf, fb);
+    // (a medium box holds at most kMediumPx pixels: 32-bit indices) the
+    // lane's pixels p = lane, lane + 32, ... as (column, row), stepped by
+    // 32 = s_dy rows + s_dx columns with one carry, without a division a pixel
+    const int bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
+    const int s_dy = 32 / bw, s_dx = 32 - s_dy * bw;
+    int dy = lane / bw, dx = lane - dy * bw;
+    for (int p = lane; p < npx; p += 32) {
+      shade(t, dxe, dye, own, farea, t.i0 + dx, t.j0 + dy, Wf, fb);
+      dx += s_dx;
+      dy += s_dy;
+      if (dx >= bw) {
+        dx -= bw;
+        ++dy;
+      }
+    }
   }
 }
 
