@@ -77,6 +77,29 @@ __device__ __forceinline__ void shade(const Tri &t, const int64_t *dxe, const in
   atomicMin(reinterpret_cast<unsigned long long *>(fb + j * Wf + i), (unsigned long long)key);
 }
 
+// The edge functions at the centre of pixel (i, j), as shade() computes them.
+__device__ __forceinline__ void edge_values(const Tri &t, const int64_t *dxe, const int64_t *dye, int64_t i, int64_t j,
+                                            int64_t *E) {
+  const int ea[3] = {1, 2, 0};
+  const int64_t px = i * 256 + 128, py = j * 256 + 128;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) E[k] = dxe[k] * (py - (int64_t)t.Y[ea[k]]) - dye[k] * (px - (int64_t)t.X[ea[k]]);
+}
+
+// shade() with the pixel's edge values already known (equal to those
+// shade() would compute: the edge functions are exact integer affine maps,
+// so stepping them by integer increments gives the same values)
+__device__ __forceinline__ void shade_e(const Tri &t, const int64_t *E, const bool *own, float farea, int64_t i,
+                                        int64_t j, int Wf, uint64_t *fb) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (!(E[k] > 0 || (E[k] == 0 && own[k]))) return;
+  const float s = (__ll2float_rn(E[0]) * t.W[0] + __ll2float_rn(E[1]) * t.W[1]) + __ll2float_rn(E[2]) * t.W[2];
+  const float zp = farea / s;
+  const uint64_t key = ((uint64_t)__float_as_uint(zp) << 32) | t.page1;
+  atomicMin(reinterpret_cast<unsigned long long *>(fb + j * Wf + i), (unsigned long long)key);
+}
+
 __device__ __forceinline__ void edges(const Tri &t, int64_t *dxe, int64_t *dye, bool *own, float *farea) {
   const int ea[3] = {1, 2, 0}, eb[3] = {2, 0, 1};
 #pragma unroll
@@ -547,16 +570,29 @@ __global__ void __launch_bounds__(256) raster_medium_kernel(const QTri *queue, c
     // (a medium box holds at most kMediumPx pixels: 32-bit indices) the
     // lane's pixels p = lane, lane + 32, ... as (column, row), stepped by
     // 32 = s_dy rows + s_dx columns with one carry, without a division a pixel
+    // The edge values step with the pixel: a pixel (di, dj) further adds
+    // 256 (dxe dj - dye di) to each.
     const int bw = t.i1 - t.i0 + 1, npx = bw * (t.j1 - t.j0 + 1);
     const int s_dy = 32 / bw, s_dx = 32 - s_dy * bw;
     int dy = lane / bw, dx = lane - dy * bw;
+    int64_t E[3], dstep[3], dcarry[3];
+    edge_values(t, dxe, dye, t.i0 + dx, t.j0 + dy, E);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dstep[k] = 256 * (dxe[k] * s_dy - dye[k] * s_dx);
+      dcarry[k] = 256 * (dxe[k] + dye[k] * bw);
+    }
     for (int p = lane; p < npx; p += 32) {
-      shade(t, dxe, dye, own, farea, t.i0 + dx, t.j0 + dy, Wf, fb);
+      shade_e(t, E, own, farea, t.i0 + dx, t.j0 + dy, Wf, fb);
       dx += s_dx;
       dy += s_dy;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) E[k] += dstep[k];
       if (dx >= bw) {
         dx -= bw;
         ++dy;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) E[k] += dcarry[k];
       }
     }
   }
@@ -602,7 +638,15 @@ __global__ void __launch_bounds__(256) raster_huge_kernel(const QTri *queue, con
           lo_i = max(lo_i, -floordiv(A, -B));
         }
       }
-      for (int64_t i = lo_i + lane; i <= hi_i; i += 32) shade(t, dxe, dye, own, farea, i, j, Wf, fb);
+      if (lo_i + lane <= hi_i) {
+        int64_t E[3];
+        edge_values(t, dxe, dye, lo_i + lane, j, E);
+        for (int64_t i = lo_i + lane; i <= hi_i; i += 32) {
+          shade_e(t, E, own, farea, i, j, Wf, fb);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) E[k] -= dye[k] * (256 * 32);
+        }
+      }
     }
   }
 }
