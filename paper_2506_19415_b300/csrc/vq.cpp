@@ -158,27 +158,27 @@ extern "C" int vm3dgs_scene_quantize_sh(vm3dgs_scene *s, int32_t n_codes, int32_
       return fail(VM3DGS_E_NOMEM, "codes");
     }
     for (int64_t p0 = 0; p0 < NP; p0 += chunk) {
-    const int64_t np = NP - p0 < chunk ? NP - p0 : chunk, n = np * m;
+      const int64_t np = NP - p0 < chunk ? NP - p0 : chunk, n = np * m;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) rest_of(Ll + (p0 + i / m) * m * NA, m, i % m, K, &Xl[(size_t)(i * D)]);
-    nearest(D, Xl.data(), n, C.data(), k, code.data());
+      for (int64_t i = 0; i < n; ++i) rest_of(Ll + (p0 + i / m) * m * NA, m, i % m, K, &Xl[(size_t)(i * D)]);
+      nearest(D, Xl.data(), n, C.data(), k, code.data());
 #pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < np; ++q) {
-      const int64_t p = p0 + q;
-      const float *src = Ll + p * m * NA;
-      uint8_t *dst = data + off[l] + p * m * rec;
-      float *f = (float *)dst;
-      uint16_t *h = (uint16_t *)(dst + 16 * m);
-      for (int64_t g = 0; g < m; ++g) {
-        for (int a = 0; a < 3; ++a) f[a * m + g] = src[a * m + g];
-        f[3 * m + g] = src[10 * m + g];
-        for (int a = 0; a < 3; ++a) h[a * m + g] = f32_to_f16(src[(3 + a) * m + g]);
-        for (int a = 0; a < 4; ++a) h[(3 + a) * m + g] = f32_to_f16(src[(6 + a) * m + g]);
-        for (int c = 0; c < 3; ++c) h[(7 + c) * m + g] = f32_to_f16(src[(11 + c) * m + g]);
-        h[10 * m + g] = (uint16_t)code[(size_t)(q * m + g)];
-        h[11 * m + g] = 0;
+      for (int64_t q = 0; q < np; ++q) {
+        const int64_t p = p0 + q;
+        const float *src = Ll + p * m * NA;
+        uint8_t *dst = data + off[l] + p * m * rec;
+        float *f = (float *)dst;
+        uint16_t *h = (uint16_t *)(dst + 16 * m);
+        for (int64_t g = 0; g < m; ++g) {
+          for (int a = 0; a < 3; ++a) f[a * m + g] = src[a * m + g];
+          f[3 * m + g] = src[10 * m + g];
+          for (int a = 0; a < 3; ++a) h[a * m + g] = f32_to_f16(src[(3 + a) * m + g]);
+          for (int a = 0; a < 4; ++a) h[(3 + a) * m + g] = f32_to_f16(src[(6 + a) * m + g]);
+          for (int c = 0; c < 3; ++c) h[(7 + c) * m + g] = f32_to_f16(src[(11 + c) * m + g]);
+          h[10 * m + g] = (uint16_t)code[(size_t)(q * m + g)];
+          h[11 * m + g] = 0;
+        }
       }
-    }
     }
   }
   s->registered_vq = false;
