@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
   __shared__ __align__(16) uint64_t s_key[BS + 2];  // the batch's sorted keys (or values), bulk-copied
   __shared__ __align__(8) uint64_t s_bar[2];        // [0] keys, [1] records
   __shared__ uint8_t s_blocks[BS];      // bit w: the alpha box meets warp w's block
-  __shared__ uint16_t s_list[NW][BS];   // per warp, the staged splats meeting its block, in order
+  __shared__ uint16_t s_list[NW][BS];   // per warp, the record slots of the staged splats meeting its block, in order
   __shared__ uint32_t s_tile;
   const int W = cam.width, H = cam.height;
   const int gx = (W + TW - 1) / TW;
@@ -276,12 +276,12 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
       const int j = c0 + lane;
       const bool meets = j < cnt && ((s_blocks[j] >> warp) & 1u);
       const uint32_t bal = __ballot_sync(0xffffffffu, meets);
-      if (meets) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)j;
+      if (meets) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)rec_slot(j);
       nl += __popc(bal);
     }
     __syncwarp();
     for (int i = 0; i < nl && !(done0 && done1); ++i) {
-      const int o = rec_slot(s_list[warp][i]);
+      const int o = s_list[warp][i];
       const float4 a = s_rec[o], b = s_rec[o + 1];
       // both pixels share x: the exponents of the two in packed FP32 pairs
       const float dx = a.x - fx;
