@@ -51,10 +51,19 @@ __device__ __forceinline__ float4 alpha_box(const float4 &s0, const float4 &s1) 
   return make_float4(s0.x - xr, s0.x + xr, s0.y - yr, s0.y + yr);
 }
 
+// 2^t for a log2-alpha that passed the skip test (t >= log2(1/255), so the
+// argument and the result are normal numbers and flushing subnormals changes
+// nothing): the hardware base-2 exponential, PTX ex2.approx.ftz
+__device__ __forceinline__ float exp2_alpha(float t) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+
 // one pixel whose log2-alpha t passed the skip test
 __device__ __forceinline__ void accumulate(float t, const float4 &b, float c, float &T, float &C0, float &C1, float &C2,
                                            bool &done) {
-  const float alpha = fminf(0.99f, exp2f(t));
+  const float alpha = fminf(0.99f, exp2_alpha(t));
   const float tT = T * (1.0f - alpha);
   if (tT < 1e-4f) {
     done = true;
@@ -75,7 +84,7 @@ __device__ __forceinline__ void blend_one(const float4 &a, const float4 &b, floa
   if (q > 0.0f) return;
   const float t = q + b.y;
   if (t < LOG2_SKIP) return;
-  const float alpha = fminf(0.99f, exp2f(t));
+  const float alpha = fminf(0.99f, exp2_alpha(t));
   const float tT = T * (1.0f - alpha);
   if (tT < 1e-4f) { done = true; return; }
   const float w = alpha * T;
