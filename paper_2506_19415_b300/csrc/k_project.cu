@@ -354,8 +354,13 @@ __global__ void __launch_bounds__(256) project_batched_kernel(ProjectArgs a, con
 // (every level block is a multiple of 64); warp 0 finds their draw entries
 // and issues the tile loads (float rows, and 16-bit rows for fp16 and VQ pools) of the
 // next item while the CTA projects the current one from shared memory (two
-// stages).  A wait that expires records VM3DGS_E_TIMEOUT and ends the CTA
-// after its copies in flight have landed.
+// stages).  The stages are handed over by mbarriers alone, with no CTA-wide
+// barrier per item: a stage's `full` barrier completes when its loads have
+// landed, its `empty` barrier when all four warps have projected from it, and
+// warp 0 refills a stage only after its `empty` phase, so a warp that is done
+// with an item goes on to the next one without waiting for the others.  A
+// wait that expires records VM3DGS_E_TIMEOUT and ends the warp's loop; warp
+// 0's copies still in flight land before the CTA ends.
 constexpr int kMbarPolls = 1 << 20;
 
 // CH Gaussians per chunk (64 or 32), 128 / CH chunks per CTA of 128 threads
@@ -367,7 +372,7 @@ struct TmaShape {
   static constexpr int CHUNK = ABYTES + BBYTES;
   static constexpr int PER = 128 / CH;                            // chunks per CTA item
   static constexpr int STAGE = PER * CHUNK;
-  static constexpr int SMEM = 2 * STAGE + 64;                     // + barriers
+  static constexpr int SMEM = 2 * STAGE + 64;                     // + barriers (full[2], empty[2])
 };
 
 template <int K, int FMT, int CH>
@@ -376,7 +381,9 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
   using S = TmaShape<K, FMT, CH>;
   constexpr int kChunk = CH, kChunksPerCta = S::PER;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE);  // full[0..1]
+  uint64_t *empty = bar + 2;                                             // empty[0..1]
+  constexpr int kWarps = 128 / 32;
   __shared__ float s_w[2][kChunksPerCta];  // opacity weight of each chunk's draw item, per stage
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.ctl->draw_gauss < a.ncap ? a.ctl->draw_gauss : a.ncap;
@@ -387,6 +394,8 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&empty[0], kWarps);
+    mbar_init(&empty[1], kWarps);
     mbar_init_fence();
   }
   __syncthreads();
@@ -434,26 +443,36 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
     __syncwarp();
   };
   int64_t item = blockIdx.x;
-  int pending = 0;  // bit s: stage s has loads in flight
-  if (item < nitems) {
-    if (warp == 0) issue(item, 0);
+  int pending = 0;  // (warp 0) bit s: stage s holds loads it issued and has not yet waited for
+  if (item < nitems && warp == 0) {
+    issue(item, 0);
     pending = 1;
   }
-  uint32_t parity[2] = {0u, 0u};
+  uint32_t parity = 0u;   // bit s: phase parity of full[s] this warp waits for next
+  uint32_t eparity = 0u;  // (warp 0) bit s: phase parity of empty[s] it waits for next
   bool timed_out = false;
   for (int k = 0; item < nitems; ++k, item += gridDim.x) {
     const int stg = k & 1;
     const int64_t next = item + gridDim.x;
-    if (next < nitems) {
-      if (warp == 0) issue(next, stg ^ 1);
+    if (warp == 0 && next < nitems) {
+      // stage stg ^ 1 last held item k - 1: all warps must have released it
+      if (k >= 1) {
+        const bool ok = mbar_wait(&empty[stg ^ 1], (eparity >> (stg ^ 1)) & 1u, kMbarPolls);
+        if (__any_sync(0xffffffffu, !ok)) {
+          timed_out = true;
+          break;
+        }
+        eparity ^= 1u << (stg ^ 1);
+      }
+      issue(next, stg ^ 1);
       pending |= 1 << (stg ^ 1);
     }
-    const bool ok = mbar_wait(&bar[stg], parity[stg], kMbarPolls);
-    if (__syncthreads_or(!ok)) {
+    const bool ok = mbar_wait(&bar[stg], (parity >> stg) & 1u, kMbarPolls);
+    if (__any_sync(0xffffffffu, !ok)) {
       timed_out = true;
       break;
     }
-    parity[stg] ^= 1u;
+    parity ^= 1u << stg;
     pending &= ~(1 << stg);
     const int ch = tid / kChunk, g = tid % kChunk;
     const int64_t c = item * kChunksPerCta + ch;
@@ -463,17 +482,16 @@ __global__ void __launch_bounds__(128) project_tma_kernel(ProjectArgs a, vm3dgs_
                                       reinterpret_cast<const __half *>(buf + S::ABYTES), g, a.codebook);
       project_one<K, FMT>(a.sp, cam, src, c * kChunk + g, s_w[stg][ch]);
     }
-    __syncthreads();  // the stage is refilled by the next-but-one item
+    // this warp is done with the stage (and with its chunk weights)
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[stg]);
   }
-  if (timed_out) {
-    if (tid == 0) {
-      atomicCAS(const_cast<int32_t *>(&a.ctl->status), 0, VM3DGS_E_TIMEOUT);
-      // let the copies still in flight land before the CTA's memory goes
-      for (int s2 = 0; s2 < 2; ++s2)
-        if (pending & (1 << s2)) mbar_wait(&bar[s2], parity[s2], kMbarPolls);
-    }
-    __syncthreads();
-  }
+  if (timed_out && lane == 0) atomicCAS(const_cast<int32_t *>(&a.ctl->status), 0, VM3DGS_E_TIMEOUT);
+  // the CTA's memory stays until warp 0's copies still in flight have landed
+  // (none unless a wait expired)
+  if (warp == 0 && lane == 0)
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (pending & (1 << s2)) mbar_wait(&bar[s2], (parity >> s2) & 1u, kMbarPolls);
 }
 
 template <int K>
