@@ -158,7 +158,7 @@ constexpr int kBlendPolls = 1 << 20;  // bound of each staging wait (try_wait po
 __device__ __forceinline__ int rec_slot(int j) { return (j >> 2) * 16 + (j & 3) * 3; }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, const uint32_t *vals,
+__global__ void __launch_bounds__(TW *TH / 2, 8) blend_kernel(const uint2 *ranges, const uint32_t *vals,
                                                           const uint64_t *packed, uint32_t idx_mask, Splats sp,
                                                           uint32_t ncap, vm3dgs_camera cam, float bg0, float bg1,
                                                           float bg2, float *img, const uint32_t *order,
@@ -289,23 +289,44 @@ __global__ void __launch_bounds__(TW *TH / 2) blend_kernel(const uint2 *ranges, 
       nl += __popc(bal);
     }
     __syncwarp();
-    for (int i = 0; i < nl && !(done0 && done1); ++i) {
-      const int o = s_list[warp][i];
-      const float4 a = s_rec[o], b = s_rec[o + 1];
-      // both pixels share x: the exponents of the two in packed FP32 pairs
+    // both pixels share x: the exponents of the two in packed FP32 pairs
+    auto expo = [&](const float4 &a, const float4 &b, float2 &q, float2 &t) {
       const float dx = a.x - fx;
       const float2 dy = __fadd2_rn(make_float2(a.y, a.y), make_float2(-fy0, -fy1));
       const float ad = a.z * dx;
       const float2 inner = __ffma2_rn(make_float2(a.w, a.w), dy, make_float2(ad, ad));
       const float2 cdy = __fmul2_rn(make_float2(b.x, b.x), dy);
-      const float2 q = __ffma2_rn(make_float2(dx, dx), inner, __fmul2_rn(cdy, dy));
-      const float2 t = __fadd2_rn(q, make_float2(b.y, b.y));
+      q = __ffma2_rn(make_float2(dx, dx), inner, __fmul2_rn(cdy, dy));
+      t = __fadd2_rn(q, make_float2(b.y, b.y));
+    };
+    auto composite = [&](int o, const float4 &b, const float2 &q, const float2 &t) {
       const bool go0 = !done0 && q.x <= 0.0f && t.x >= LOG2_SKIP;
       const bool go1 = !done1 && q.y <= 0.0f && t.y >= LOG2_SKIP;
-      if (!(go0 || go1)) continue;
+      if (!(go0 || go1)) return;
       const float c = s_rec[o + 2].x;
       if (go0) accumulate(t.x, b, c, T0, A0, B0, D0, done0);
       if (go1) accumulate(t.y, b, c, T1, A1, B1, D1, done1);
+    };
+    // two splats a round: their loads and exponents are independent and go
+    // together; they are composited in list order (the second sees the
+    // first's transmittance and stop flags), so every pixel takes the same
+    // operations in the same order as one splat a round
+    int i = 0;
+    for (; i + 1 < nl && !(done0 && done1); i += 2) {
+      const int o1 = s_list[warp][i], o2 = s_list[warp][i + 1];
+      const float4 a1 = s_rec[o1], b1 = s_rec[o1 + 1], a2 = s_rec[o2], b2 = s_rec[o2 + 1];
+      float2 q1, t1, q2, t2;
+      expo(a1, b1, q1, t1);
+      expo(a2, b2, q2, t2);
+      composite(o1, b1, q1, t1);
+      composite(o2, b2, q2, t2);
+    }
+    if (i < nl && !(done0 && done1)) {
+      const int o = s_list[warp][i];
+      const float4 a = s_rec[o], b = s_rec[o + 1];
+      float2 q, t;
+      expo(a, b, q, t);
+      composite(o, b, q, t);
     }
   }
   const int64_t HW = (int64_t)W * H;
