@@ -347,7 +347,7 @@ SORT_DRAM_BYTES_PER_PAIR_PASS = None
 # bench cannot read live.
 BLEND_ISSUE = {"issue_active_pct": 77.1, "alu_pipe_pct": 51.7, "fma_pipe_pct": 33.8, "dram_pct_of_peak": 1.6,
                "source": "ncu --set full, one launch (smsp__issue_active, sm__pipe_alu_cycles_active, "
-                         "sm__pipe_fma_cycles_active, gpu__dram_throughput)"}
+                         "sm__pipe_fma_cycles_active, gpu__dram_throughput), of the kernel before its two-splat walk"}
 
 
 def roofline(v, stage, stats, peaks, rec16, width, height, alt_sort=None):
